@@ -1,0 +1,266 @@
+/*
+ * eecmg.h -- C ABI of the GB300 (sm_103a) implementation of the
+ * Extrapolation Economy Cascadic Multigrid method (EECMG) for image
+ * restoration (Chu, Yan & Li, "A New Extrapolation Economy Cascadic
+ * Multigrid Method for Image Restoration Problems").
+ *
+ * The method restores u from H u = g_delta (Eqs. 3 and 9), H the
+ * zero-boundary (block-Toeplitz) convolution with a point-spread function
+ * (PSF).  It runs a coarse-to-fine cascade (Algorithm 2): the two coarsest
+ * levels are solved from zero with a few Krylov iterations; every finer
+ * level starts from the new extrapolation of the two previous solutions
+ * (Section 3.2), quadratic interpolation, local smoothing (Section 3.3) and
+ * one Perona-Malik denoising step (Section 4), then runs its economy number
+ * of Krylov iterations (Section 2).
+ *
+ * Conventions for every entry point:
+ *   - Images are single-channel FP32, row-major, pitch = width, values on
+ *     the [0, 255] grey scale.  "device" pointers are CUDA global memory of
+ *     the current device; "host" pointers are CPU memory.  The library never
+ *     takes ownership of caller buffers; asynchronous calls require the
+ *     caller to keep them alive until the stream reaches the call.
+ *   - PSFs are host FP64, row-major, odd sizes, centred; they are copied.
+ *   - Levels are numbered 0 (coarsest) .. levels-1 (finest, the input size).
+ *   - Every function returns an eecmg_status; on failure a description is
+ *     available from eecmg_last_error() (thread-local).  No function throws
+ *     or aborts.  Invalid arguments are detected on the host before any work
+ *     is enqueued.
+ *   - A plan owns device memory (its workspace) and is not safe to use from
+ *     two streams at once; use one plan per concurrent restoration.
+ */
+#ifndef EECMG_H
+#define EECMG_H
+
+#include <stddef.h>
+#include <stdint.h>
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    EECMG_OK = 0,
+    EECMG_ERR_INVALID_ARG = 1,  /* bad size, pointer, option or PSF            */
+    EECMG_ERR_UNSUPPORTED = 2,  /* e.g. MR-II with a non-centrosymmetric PSF   */
+    EECMG_ERR_OOM = 3,          /* device allocation or memory budget failed   */
+    EECMG_ERR_CUDA = 4,         /* a CUDA runtime call failed                  */
+    EECMG_ERR_NUMERIC = 5,      /* non-finite scalar in a level solve          */
+    EECMG_ERR_TIMEOUT = 6,      /* a bounded device wait gave up               */
+    EECMG_ERR_BUSY = 7          /* server queue full / resource in use         */
+} eecmg_status;
+
+enum { EECMG_SMOOTHER_MR2 = 0, EECMG_SMOOTHER_CGLS = 1 };
+enum { EECMG_COARSE_GALERKIN_RMS = 0, EECMG_COARSE_GALERKIN_RENORM = 1 };
+enum { EECMG_STORAGE_FP32 = 0, EECMG_STORAGE_BF16 = 1 };
+enum { EECMG_STOP_FIXED = 0, EECMG_STOP_DISCREPANCY = 1 };
+enum { EECMG_PROLONG_EECMG = 0, EECMG_PROLONG_IECMG_P = 1, EECMG_PROLONG_IECMG_L = 2 };
+
+/* Largest PSF radius supported (PSF up to 25 x 25). */
+#define EECMG_MAX_RADIUS 12
+
+/*
+ * Options.  eecmg_default_options() fills:
+ *   smoother = MR2        "MR" of Section 2 read as MR-II (needs a
+ *                         centrosymmetric PSF); CGLS is the reading of "CG".
+ *   coarse_op = GALERKIN_RMS  H_l = R_l H_{l+1} R_l^* (Eq. 14) with R_l^* the
+ *                         adjoint under the RMS inner product of Eq. 10;
+ *                         GALERKIN_RENORM rescales each coarse PSF to the
+ *                         fine PSF's sum.
+ *   storage = FP32        BF16 stores the streamed Krylov vectors in bf16
+ *                         (FP32 arithmetic, FP64 scalars).
+ *   stop = FIXED          exactly m_l iterations (Section 2 note), unless
+ *                         DISCREPANCY: stop when ||r||_RMS <= c * delta.
+ *   c = 1.1, delta = 0    discrepancy constant and noise level ||e||_RMS.
+ *   diffusion_steps = 1   explicit Perona-Malik steps per prolonged level.
+ *   s_scale = 1           scale of the weight argument of Eq. 18.
+ *   conv_tol = 1e-5       a level also stops once ||r|| <= conv_tol ||g_l||
+ *                         (the exact method takes no step after a zero
+ *                         residual; see the design notes); 0 disables.
+ *   prolong = EECMG       Algorithm 2; IECMG_P / IECMG_L run Algorithm 1
+ *                         with quadratic / linear (Eq. 15) prolongation.
+ *   use_graph = 1         capture the cascade as a CUDA graph per plan.
+ */
+typedef struct {
+    int smoother;
+    int coarse_op;
+    int storage;
+    int stop;
+    double c;
+    double delta;
+    int diffusion_steps;
+    double s_scale;
+    double conv_tol;
+    int prolong;
+    int use_graph;
+} eecmg_options;
+
+typedef struct eecmg_plan_s *eecmg_plan_t;
+
+/* Fills *opt with the defaults listed above.  Errors: INVALID_ARG if NULL. */
+eecmg_status eecmg_default_options(eecmg_options *opt);
+
+/*
+ * Creates a restoration plan for width x height images (Section 2, Eqs.
+ * 11-14; Section 5 for the PSF and the paper's parameters).
+ *   levels   number of grid levels L >= 1 (the two coarsest are solved from
+ *            zero; L = 1 is the standalone smoother); each coarser side is
+ *            ceil(side / 2) (Section 2).
+ *   psf      host FP64 PSF, psf_h rows x psf_w cols, odd sizes, radius
+ *            <= EECMG_MAX_RADIUS, positive sum; copied.
+ *   alpha    step tau of the explicit Perona-Malik step (Eq. 24),
+ *            0 <= alpha <= 0.25 (the API's alpha is read as tau).
+ *   k        Perona-Malik threshold of Eq. 21, k > 0.
+ *   iters    host array of `levels` iteration counts m_l (coarsest first),
+ *            or NULL for the economy schedule of Section 2.
+ *   opt      options, or NULL for the defaults.
+ *   out      receives the plan.  The plan allocates its device workspace
+ *            (see eecmg_plan_info) on the current device.
+ * Errors: INVALID_ARG (sizes, PSF, alpha, k, iters < 0), UNSUPPORTED (MR-II
+ * with a PSF that is not centrosymmetric), OOM, CUDA.
+ */
+eecmg_status eecmg_plan(int width, int height, int levels, const double *psf, int psf_w,
+                        int psf_h, double alpha, double k, const int *iters,
+                        const eecmg_options *opt, eecmg_plan_t *out);
+
+/* Releases the plan and its device memory (synchronises the device first). */
+eecmg_status eecmg_plan_destroy(eecmg_plan_t plan);
+
+/*
+ * Plan geometry: level_w/level_h/iters (each `levels` entries, may be NULL)
+ * receive the level sizes and scheduled m_l, coarsest first;
+ * workspace_bytes (may be NULL) the device memory the plan holds.
+ */
+eecmg_status eecmg_plan_info(eecmg_plan_t plan, int *levels, int *level_w, int *level_h,
+                             int *iters, size_t *workspace_bytes);
+
+/*
+ * Restores one image (Algorithm 2, Step 1 - Step 3).  g_delta and u_out are
+ * device buffers of height x width floats; they may alias.  Asynchronous on
+ * `stream` (0 = legacy default stream).  Errors: INVALID_ARG (NULL
+ * pointers), CUDA.  Numeric breakdowns are not errors: a level whose Krylov
+ * denominator vanishes ends early (see eecmg_plan_stats).
+ */
+eecmg_status eecmg_restore(eecmg_plan_t plan, const float *g_delta, float *u_out,
+                           cudaStream_t stream);
+
+/*
+ * As eecmg_restore, with HOST buffers: copies g_host to the device, restores
+ * and copies the result to u_host, then synchronises `stream`.  For callers
+ * that keep their images in CPU memory.
+ */
+eecmg_status eecmg_restore_host(eecmg_plan_t plan, const float *g_host, float *u_host,
+                                cudaStream_t stream);
+
+/*
+ * Restores n images with their own plans (sizes and PSFs may differ) as one
+ * batch: per cascade step, one fused launch covers every image.
+ * plans[i], g[i] (device), u[i] (device).  The plans must be distinct.
+ * Asynchronous on `stream`.  Errors: INVALID_ARG, CUDA.
+ */
+eecmg_status eecmg_restore_batched(const eecmg_plan_t *plans, const float *const *g,
+                                   float *const *u, int n, cudaStream_t stream);
+
+/*
+ * Per-level outcome of the most recent restoration with this plan:
+ * iters_done[l] (iterations actually taken) and res_rms[l] (||g_l - H_l
+ * u_l||_RMS as carried by the recurrence, Eq. 10).  Synchronises the plan's
+ * last stream.  Either pointer may be NULL.
+ */
+eecmg_status eecmg_plan_stats(eecmg_plan_t plan, int *iters_done, double *res_rms);
+
+/* ---- operator-level entry points (one level of a plan) ----------------- */
+
+/*
+ * y = H_l x (transpose = 0) or y = H_l^T x (transpose = 1): zero-boundary
+ * convolution with the level's PSF (Eqs. 1, 7; Eq. 14 for l < L-1).  x, y
+ * device, level_h x level_w floats, must not alias.  Asynchronous.
+ */
+eecmg_status eecmg_apply_H(eecmg_plan_t plan, int level, const float *x, float *y, int transpose,
+                           cudaStream_t stream);
+
+/*
+ * Restriction of Eqs. 12-13: coarse(a, b) = fine(2a, 2b) from level+1 to
+ * level.  fine: level+1 sizes, coarse: level sizes, device.  Asynchronous.
+ */
+eecmg_status eecmg_restrict(eecmg_plan_t plan, int level, const float *fine, float *coarse,
+                            cudaStream_t stream);
+
+/*
+ * Nonlinear prolongation of Section 3.2 to `level` (>= 2): the new
+ * extrapolation Pi from u1 (level-1 solution) and u2 (level-2 solution),
+ * then quadratic interpolation P onto `level`.  out: level sizes.  Device,
+ * asynchronous.
+ */
+eecmg_status eecmg_prolong(eecmg_plan_t plan, int level, const float *u1, const float *u2,
+                           float *out, cudaStream_t stream);
+
+/*
+ * Prolongation of Algorithm 1 to `level` (>= 1) from the level-1 solution
+ * u1 only: quadratic = 1 for P (IECMG-P), 0 for the linear L of Eq. 15
+ * (IECMG-L).  Device, asynchronous.
+ */
+eecmg_status eecmg_prolong_single(eecmg_plan_t plan, int level, const float *u1, float *out,
+                                  int quadratic, cudaStream_t stream);
+
+/* Local smoothing S_l of Section 3.3 (Eqs. 18-19).  in != out.  Device. */
+eecmg_status eecmg_smooth(eecmg_plan_t plan, int level, const float *in, float *out,
+                          cudaStream_t stream);
+
+/* One explicit Perona-Malik step D_l, Section 4 (Eqs. 21, 23-24).  in != out. */
+eecmg_status eecmg_denoise(eecmg_plan_t plan, int level, const float *in, float *out,
+                           cudaStream_t stream);
+
+/*
+ * The level smoother C_l^m of Section 2 (MR-II or CGLS per the plan's
+ * options) on level `level`: g device data, u device start vector on entry
+ * and result on exit, at most m iterations (with the plan's stopping
+ * rules).  Uses the plan's workspace.  Asynchronous; the outcome is read
+ * with eecmg_plan_stats (entry `level`).
+ */
+eecmg_status eecmg_level_solve(eecmg_plan_t plan, int level, const float *g, float *u, int m,
+                               cudaStream_t stream);
+
+/* ---- serving: continuous batching of restoration requests -------------- */
+
+typedef struct eecmg_server_s *eecmg_server_t;
+
+/*
+ * Creates a server that admits restoration requests while their workspace
+ * fits in mem_budget_bytes of device memory and at most max_slots are
+ * active, keeps each request's level pyramid and solver state resident,
+ * and advances all active requests together, one cascade step per
+ * scheduler tick, on its own stream and host thread.
+ */
+eecmg_status eecmg_server_create(size_t mem_budget_bytes, int max_slots, eecmg_server_t *out);
+
+/*
+ * Queues one request.  plan: a plan describing the request (size, PSF,
+ * options; shared and read-only, only its description is used); g_delta,
+ * u_out: device buffers that stay valid until the request completes.
+ * *ticket receives an id.  Errors: INVALID_ARG, BUSY (queue full),
+ * OOM (the request alone exceeds the budget).
+ */
+eecmg_status eecmg_server_submit(eecmg_server_t srv, eecmg_plan_t plan, const float *g_delta,
+                                 float *u_out, uint64_t *ticket);
+
+/* *done = 1 once the result is in u_out; *latency_ms = submit -> done. */
+eecmg_status eecmg_server_poll(eecmg_server_t srv, uint64_t ticket, int *done,
+                               double *latency_ms);
+
+/* Blocks until every queued request has completed. */
+eecmg_status eecmg_server_drain(eecmg_server_t srv);
+
+/* Drains, stops the scheduler thread and frees all device memory. */
+eecmg_status eecmg_server_destroy(eecmg_server_t srv);
+
+/* Thread-local description of the last error (never NULL). */
+const char *eecmg_last_error(void);
+
+/* Library version string. */
+const char *eecmg_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* EECMG_H */

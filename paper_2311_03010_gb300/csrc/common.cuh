@@ -1,0 +1,131 @@
+// common.cuh -- shared device definitions of the EECMG CUDA library.
+//
+// Layout conventions: images are FP32, row-major, pitch = width.  A level's
+// PSF is held in *correlation* form C(dy, dx) so that every kernel computes
+//     y(i, j) = sum_{dy, dx} C(dy, dx) * x(i + dy, j + dx),   x = 0 outside,
+// which is H (Eq. 7, zero boundary) with C(dy, dx) = K(-dy, -dx) and H^T
+// with C = K.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/eecmg.h"
+
+namespace eecmg {
+
+constexpr int RMAX = EECMG_MAX_RADIUS;
+constexpr int KMAX = 2 * RMAX + 1;
+constexpr int TAPS_MAX = KMAX * KMAX;
+
+// One level's PSF in correlation form.  Device resident (plan-owned).
+struct Taps {
+    int ry, rx;           // radii: dy in [-ry, ry], dx in [-rx, rx]
+    int rt;               // template radius used by the kernels (max(ry, rx))
+    int sep;              // 1: C(dy, dx) = cy[dy + rt] * cx[dx + rt]
+    int ntap;             // non-separable path: number of non-zero taps
+    int pad[3];
+    float cy[KMAX];       // separable factors, indexed by d + rt
+    float cx[KMAX];
+    int dy[TAPS_MAX];     // non-zero taps (dy, dx, weight)
+    int dx[TAPS_MAX];
+    float wt[TAPS_MAX];
+};
+
+// Per-solve device scalars (FP64).  One block per level of a plan.
+struct alignas(64) Scalars {
+    double b1, b2;        // MR-II beta_1, beta_2 of the current direction
+    double alpha;         // step decided but not yet applied
+    double qq, qq_prev;   // <q_k, q_k>, <q_{k-1}, q_{k-1}>
+    double gamma;         // CGLS <s, s>
+    double rr;            // last ||r||^2
+    double gg;            // ||g||^2
+    double lim2;          // stop when ||r||^2 <= lim2
+    double conv_tol2;     // conv_tol^2 (relative to ||g||^2)
+    double disc2;         // (c delta)^2 * N (discrepancy rule), 0 = off
+    double rq;            // last <r, q>
+    int stopped;          // 0 running; 1 stopping rule; 2 breakdown; 3 non-finite
+    int iters;            // iterations whose step has been decided
+    unsigned int counter; // last-block arrival counter (reset by the last block)
+    int pad;
+};
+
+constexpr int NTHREADS = 256;
+constexpr int NPART = 4;  // partial sums per block
+
+// ---------------------------------------------------------------------------
+// Deterministic reductions.  Each thread sums a few products in FP32 (a
+// handful of terms, so no FP64 work per element), the block reduces in FP64
+// with warp shuffles in a fixed order, and block b writes partials[b*NPART+j].
+// The last block to arrive (atomic counter) sums all block partials in a
+// fixed order, so the result does not depend on block scheduling.
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Block-wide sum of NV values per thread; result valid in thread 0.
+template <int NV>
+__device__ __forceinline__ void block_sum(const double (&v)[NV], double (&out)[NV]) {
+    __shared__ double red[NV][NTHREADS / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int j = 0; j < NV; ++j) {
+        double s = warp_sum(v[j]);
+        if (lane == 0) red[j][warp] = s;
+    }
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int j = 0; j < NV; ++j) {
+            double s = lane < NTHREADS / 32 ? red[j][lane] : 0.0;
+            s = warp_sum(s);
+            out[j] = s;
+        }
+    }
+    __syncthreads();
+}
+
+// Writes this block's partials and returns true in every thread of the last
+// block to arrive.  Must be called by all threads of the block.
+template <int NV>
+__device__ __forceinline__ bool block_partials_arrive(const double (&v)[NV], double* partials,
+                                                      unsigned int* counter, unsigned int nblocks,
+                                                      unsigned int bid) {
+    double out[NV];
+    block_sum<NV>(v, out);
+    __shared__ bool is_last;
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int j = 0; j < NV; ++j) partials[(size_t)bid * NPART + j] = out[j];
+        __threadfence();
+        unsigned int t = atomicAdd(counter, 1u);
+        is_last = (t == nblocks - 1);
+    }
+    __syncthreads();
+    return is_last;
+}
+
+// In the last block: fixed-order sum of all blocks' partials.  Result in
+// thread 0 (out), and the counter is reset for the next launch.
+template <int NV>
+__device__ __forceinline__ void grid_total(const double* partials, unsigned int nblocks,
+                                           unsigned int* counter, double (&out)[NV]) {
+    __threadfence();
+    double v[NV];
+#pragma unroll
+    for (int j = 0; j < NV; ++j) v[j] = 0.0;
+    for (unsigned int b = threadIdx.x; b < nblocks; b += NTHREADS) {
+#pragma unroll
+        for (int j = 0; j < NV; ++j) v[j] += __ldcg(partials + (size_t)b * NPART + j);
+    }
+    block_sum<NV>(v, out);
+    if (threadIdx.x == 0) *counter = 0u;
+}
+
+__device__ __forceinline__ bool finite_pos(double x) { return x > 0.0 && x < 1.0e300; }
+
+}  // namespace eecmg

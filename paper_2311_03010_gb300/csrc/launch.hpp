@@ -1,0 +1,79 @@
+// launch.hpp -- host-side launchers of the EECMG kernels (internal).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace eecmg {
+
+// Epilogues fused into the convolution y = C (*) x.
+enum ConvMode : int {
+    CM_STORE = 0,   // y = C (*) x
+    CM_RESID = 1,   // r = g - H u (e0 = g): ||r||^2, ||g||^2 -> stopping limit, stop test
+    CM_MR_Q1 = 2,   // q_1 = H p_1 (e0 = r_0): <r_0, q_1>, <q_1, q_1> -> alpha_1
+    CM_MR_A = 3,    // z = H q_{k-1} (e1 = q_{k-2}): <z, q_{k-1}>, <z, q_{k-2}> -> beta_1, beta_2
+    CM_CG_S0 = 4,   // s = H^T r, p = s (y2): <s, s> -> gamma
+    CM_CG_Q = 5,    // q = H p: <q, q> -> alpha = gamma / <q, q>
+    CM_CG_S = 6,    // s = H^T r: <s, s> -> beta, gamma
+    CM_MR_P1 = 7,   // p_1 = H r_0 (store, skipped once the level has stopped)
+};
+
+struct ConvArgs {
+    const float* x = nullptr;
+    float* y = nullptr;
+    float* y2 = nullptr;
+    const float* e0 = nullptr;
+    const float* e1 = nullptr;
+    const Taps* taps = nullptr;
+    Scalars* sc = nullptr;
+    double* partials = nullptr;
+    double conv_tol2 = 0.0;
+    double disc2 = 0.0;
+    int h = 0, w = 0;
+    int mode = CM_STORE;
+    int has_e1 = 0;
+    int zero_input = 0;
+};
+
+// Tile of the convolution kernels.
+constexpr int CONV_TH = 32;
+constexpr int CONV_TW = 64;
+
+inline unsigned int conv_blocks(int h, int w) {
+    return (unsigned int)(((w + CONV_TW - 1) / CONV_TW) * ((h + CONV_TH - 1) / CONV_TH));
+}
+
+// Elementwise kernels: 8 elements per thread.
+constexpr int EW_PER_BLOCK = NTHREADS * 8;
+inline unsigned int ew_blocks(size_t n) {
+    return (unsigned int)((n + EW_PER_BLOCK - 1) / EW_PER_BLOCK);
+}
+
+cudaError_t launch_conv(const ConvArgs& a, int rt, int sep, cudaStream_t s);
+
+// MR-II phase B of iteration k: pending update with alpha_{k-1}, new
+// direction (q_k into q2, p_k into p2), <r, q_k>, <q_k, q_k>, ||r||^2.
+cudaError_t launch_mr_b(const float* z, const float* q1, float* q2, const float* p1, float* p2,
+                        float* u, float* r, size_t n, int has2, Scalars* sc, double* partials,
+                        cudaStream_t s);
+// u += alpha p, r -= alpha q, ||r||^2; check = 1 also applies the stopping rule.
+cudaError_t launch_step(float* u, const float* p, float* r, const float* q, size_t n, int check,
+                        Scalars* sc, double* partials, cudaStream_t s);
+// p = s + beta p (CGLS).
+cudaError_t launch_cg_p(float* p, const float* sv, size_t n, Scalars* sc, cudaStream_t s);
+
+// Level operators.
+cudaError_t launch_restrict(const float* fine, int hf, int wf, float* coarse, int hc, int wc,
+                            cudaStream_t s);
+cudaError_t launch_extrapolate(const float* u1, int h1, int w1, const float* u2, int h2, int w2,
+                               float* out, cudaStream_t s);
+cudaError_t launch_quadratic(const float* ut, int h1, int w1, float* out, int h, int w,
+                             cudaStream_t s);
+cudaError_t launch_linear(const float* uc, int hc, int wc, float* out, int h, int w,
+                          cudaStream_t s);
+cudaError_t launch_smooth(const float* in, float* out, int h, int w, float scale, cudaStream_t s);
+cudaError_t launch_denoise(const float* in, float* out, int h, int w, float tau, float kpm,
+                           cudaStream_t s);
+
+}  // namespace eecmg

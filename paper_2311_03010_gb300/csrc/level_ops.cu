@@ -1,0 +1,238 @@
+// level_ops.cu -- per-level operators of the cascade: restriction (Eqs.
+// 12-13), the new extrapolation Pi and quadratic interpolation P (Section
+// 3.2), linear prolongation L (Eq. 15), local smoothing S (Section 3.3,
+// Eqs. 18-19) and one explicit Perona-Malik step D (Section 4, Eqs. 21-24).
+// Each runs once per level per restoration; they are simple stencils with
+// 32 x 8 thread blocks over the output image.
+#include "launch.hpp"
+
+namespace eecmg {
+
+namespace {
+constexpr int BX = 32, BY = 8;
+inline dim3 grid2(int h, int w) { return dim3((w + BX - 1) / BX, (h + BY - 1) / BY); }
+}  // namespace
+
+// g_l(a, b) = g_{l+1}(2a, 2b): the paper's 1-based 2k - 1, per dimension.
+__global__ void k_restrict(const float* __restrict__ fine, int wf, float* __restrict__ coarse,
+                           int hc, int wc) {
+    const int b = blockIdx.x * BX + threadIdx.x, a = blockIdx.y * BY + threadIdx.y;
+    if (a < hc && b < wc) coarse[(size_t)a * wc + b] = fine[(size_t)(2 * a) * wf + 2 * b];
+}
+
+// Pi on the level-(l-1) grid: u1 + (1/4) * (bilinear interpolant of
+// d = u1|coarse - u2), i.e. (5 u1 - u2)/4 at coarse nodes, u1 + (d_a + d_b)/8
+// at edge midpoints and u1 + (sum of four d)/16 at cell centres; indices
+// past the last level-(l-2) node are clamped to it.  The differences of the
+// two near-equal iterates are taken in FP64.
+__global__ void k_extrapolate(const float* __restrict__ u1, int h1, int w1,
+                              const float* __restrict__ u2, int h2, int w2,
+                              float* __restrict__ out) {
+    const int b = blockIdx.x * BX + threadIdx.x, a = blockIdx.y * BY + threadIdx.y;
+    if (a >= h1 || b >= w1) return;
+    const int A0 = a >> 1, B0 = b >> 1;
+    const int A1 = (a & 1) ? min(A0 + 1, h2 - 1) : A0;
+    const int B1 = (b & 1) ? min(B0 + 1, w2 - 1) : B0;
+    auto d = [&](int A, int B) -> double {
+        return (double)u1[(size_t)(2 * A) * w1 + 2 * B] - (double)u2[(size_t)A * w2 + B];
+    };
+    const double dsum = d(A0, B0) + d(A0, B1) + d(A1, B0) + d(A1, B1);
+    out[(size_t)a * w1 + b] = (float)((double)u1[(size_t)a * w1 + b] + 0.0625 * dsum);
+}
+
+// Three-point Lagrange weights at offsets 0, 1/4, 1/2, 3/4 of a level-(l-2)
+// cell spanned by the level-(l-1) triplet (2A, 2A+1, 2A+2).
+__constant__ float c_qw[4][3] = {
+    {1.f, 0.f, 0.f}, {0.375f, 0.75f, -0.125f}, {0.f, 1.f, 0.f}, {-0.125f, 0.75f, 0.375f}};
+
+// P: tensor-product quadratic interpolation of ut (h1 x w1) onto h x w.
+__global__ void k_quadratic(const float* __restrict__ ut, int h1, int w1, float* __restrict__ out,
+                            int h, int w) {
+    const int x = blockIdx.x * BX + threadIdx.x, y = blockIdx.y * BY + threadIdx.y;
+    if (y >= h || x >= w) return;
+    const int A = y >> 2, ty = y & 3, B = x >> 2, tx = x & 3;
+    float s = 0.f;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const int ar = min(2 * A + i, h1 - 1);
+        float row = 0.f;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const int bc = min(2 * B + j, w1 - 1);
+            row = fmaf(c_qw[tx][j], ut[(size_t)ar * w1 + bc], row);
+        }
+        s = fmaf(c_qw[ty][i], row, s);
+    }
+    out[(size_t)y * w + x] = s;
+}
+
+// L of Eq. 15 in 0-based indices: copy at (2a, 2b); horizontal / vertical
+// averages at (2a, 2b+1) / (2a+1, 2b); the diagonal pair (a, b), (a+1, b+1)
+// at (2a+1, 2b+1).  Indices past the last coarse node are clamped.
+__global__ void k_linear(const float* __restrict__ uc, int hc, int wc, float* __restrict__ out,
+                         int h, int w) {
+    const int x = blockIdx.x * BX + threadIdx.x, y = blockIdx.y * BY + threadIdx.y;
+    if (y >= h || x >= w) return;
+    const int a = y >> 1, b = x >> 1;
+    const int a1 = min(a + 1, hc - 1), b1 = min(b + 1, wc - 1);
+    const float u00 = uc[(size_t)a * wc + b];
+    float v;
+    if (!(y & 1) && !(x & 1)) v = u00;
+    else if (!(y & 1)) v = 0.5f * (u00 + uc[(size_t)a * wc + b1]);
+    else if (!(x & 1)) v = 0.5f * (u00 + uc[(size_t)a1 * wc + b]);
+    else v = 0.5f * (u00 + uc[(size_t)a1 * wc + b1]);
+    out[(size_t)y * w + x] = v;
+}
+
+// S: weighted least-squares plane fit over the in-image 3 x 3 neighbourhood
+// with weights exp(-(scale * (u_c - u_nb))^2) (Eqs. 18-19), output the fitted
+// constant.  Solved in centred form: with W, the weighted means (sb, tb, vb)
+// of the offsets and of v = u_nb - u_c, the 2 x 2 moment matrix C and the
+// cross vector c, slope = C^+ c (eigenvalues below 1e-6 W dropped) and
+// a0 = u_c + vb - slope . (sb, tb).
+__global__ void k_smooth(const float* __restrict__ in, float* __restrict__ out, int h, int w,
+                         float scale) {
+    const int j = blockIdx.x * BX + threadIdx.x, i = blockIdx.y * BY + threadIdx.y;
+    if (i >= h || j >= w) return;
+    const float uc = in[(size_t)i * w + j];
+    float ws[9], ss[9], ts[9], vs[9];
+    float W = 0.f, sb = 0.f, tb = 0.f, vb = 0.f;
+#pragma unroll
+    for (int s = -1; s <= 1; ++s) {
+#pragma unroll
+        for (int t = -1; t <= 1; ++t) {
+            const int k = (s + 1) * 3 + (t + 1);
+            const int ii = i + s, jj = j + t;
+            const bool inside = ii >= 0 && ii < h && jj >= 0 && jj < w;
+            const float v = inside ? in[(size_t)ii * w + jj] - uc : 0.f;
+            const float e = scale * v;
+            const float wt = inside ? expf(-e * e) : 0.f;
+            ws[k] = wt;
+            ss[k] = (float)s;
+            ts[k] = (float)t;
+            vs[k] = v;
+            W += wt;
+            sb = fmaf(wt, (float)s, sb);
+            tb = fmaf(wt, (float)t, tb);
+            vb = fmaf(wt, v, vb);
+        }
+    }
+    sb /= W;
+    tb /= W;
+    vb /= W;
+    float css = 0.f, cst = 0.f, ctt = 0.f, csv = 0.f, ctv = 0.f;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        const float ds = ss[k] - sb, dt = ts[k] - tb, dv = vs[k] - vb;
+        const float wd = ws[k];
+        css = fmaf(wd * ds, ds, css);
+        cst = fmaf(wd * ds, dt, cst);
+        ctt = fmaf(wd * dt, dt, ctt);
+        csv = fmaf(wd * ds, dv, csv);
+        ctv = fmaf(wd * dt, dv, ctv);
+    }
+    const float tr = 0.5f * (css + ctt), df = 0.5f * (css - ctt);
+    const float rad = sqrtf(df * df + cst * cst);
+    const float l1 = tr + rad;
+    // small eigenvalue from the determinant: no cancellation
+    const float l2 = l1 > 0.f ? (css * ctt - cst * cst) / l1 : 0.f;
+    const float thr = 1e-6f * W;
+    float e1s = 1.f, e1t = 0.f;
+    if (rad > 0.f) {
+        const float a0 = css - l2, c0 = ctt - l2;
+        if (fabsf(a0) >= fabsf(c0)) {
+            const float nn = rsqrtf(a0 * a0 + cst * cst);
+            e1s = a0 * nn;
+            e1t = cst * nn;
+        } else {
+            const float nn = rsqrtf(cst * cst + c0 * c0);
+            e1s = cst * nn;
+            e1t = c0 * nn;
+        }
+    }
+    const float e2s = -e1t, e2t = e1s;
+    float gs = 0.f, gt = 0.f;
+    if (l1 > thr) {
+        const float c1 = (e1s * csv + e1t * ctv) / l1;
+        gs = fmaf(c1, e1s, gs);
+        gt = fmaf(c1, e1t, gt);
+    }
+    if (l2 > thr) {
+        const float c2 = (e2s * csv + e2t * ctv) / l2;
+        gs = fmaf(c2, e2s, gs);
+        gt = fmaf(c2, e2t, gt);
+    }
+    out[(size_t)i * w + j] = uc + vb - (gs * sb + gt * tb);
+}
+
+// D: u + tau * sum over in-image 4-neighbours of (c_nb + c_c)/2 (u_nb - u_c),
+// c = 1 / (1 + |grad u|^2 / k^2) with central differences (an out-of-image
+// neighbour replaced by the centre value).
+__device__ __forceinline__ float pm_c(const float* __restrict__ u, int h, int w, int i, int j,
+                                      float inv_k2) {
+    const float uc = u[(size_t)i * w + j];
+    const float ue = (j + 1 < w) ? u[(size_t)i * w + j + 1] : uc;
+    const float uw = (j > 0) ? u[(size_t)i * w + j - 1] : uc;
+    const float us = (i + 1 < h) ? u[(size_t)(i + 1) * w + j] : uc;
+    const float un = (i > 0) ? u[(size_t)(i - 1) * w + j] : uc;
+    const float gx = 0.5f * (ue - uw), gy = 0.5f * (us - un);
+    return 1.f / (1.f + (gx * gx + gy * gy) * inv_k2);
+}
+
+__global__ void k_denoise(const float* __restrict__ in, float* __restrict__ out, int h, int w,
+                          float tau, float inv_k2) {
+    const int j = blockIdx.x * BX + threadIdx.x, i = blockIdx.y * BY + threadIdx.y;
+    if (i >= h || j >= w) return;
+    const float uc = in[(size_t)i * w + j];
+    const float cc = pm_c(in, h, w, i, j, inv_k2);
+    float f = 0.f;
+    if (i + 1 < h) f += 0.5f * (pm_c(in, h, w, i + 1, j, inv_k2) + cc) * (in[(size_t)(i + 1) * w + j] - uc);
+    if (i > 0) f += 0.5f * (pm_c(in, h, w, i - 1, j, inv_k2) + cc) * (in[(size_t)(i - 1) * w + j] - uc);
+    if (j + 1 < w) f += 0.5f * (pm_c(in, h, w, i, j + 1, inv_k2) + cc) * (in[(size_t)i * w + j + 1] - uc);
+    if (j > 0) f += 0.5f * (pm_c(in, h, w, i, j - 1, inv_k2) + cc) * (in[(size_t)i * w + j - 1] - uc);
+    out[(size_t)i * w + j] = fmaf(tau, f, uc);
+}
+
+cudaError_t launch_restrict(const float* fine, int hf, int wf, float* coarse, int hc, int wc,
+                            cudaStream_t s) {
+    (void)hf;
+    if (hc <= 0 || wc <= 0) return cudaSuccess;
+    k_restrict<<<grid2(hc, wc), dim3(BX, BY), 0, s>>>(fine, wf, coarse, hc, wc);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_extrapolate(const float* u1, int h1, int w1, const float* u2, int h2, int w2,
+                               float* out, cudaStream_t s) {
+    if (h1 <= 0 || w1 <= 0) return cudaSuccess;
+    k_extrapolate<<<grid2(h1, w1), dim3(BX, BY), 0, s>>>(u1, h1, w1, u2, h2, w2, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_quadratic(const float* ut, int h1, int w1, float* out, int h, int w,
+                             cudaStream_t s) {
+    if (h <= 0 || w <= 0) return cudaSuccess;
+    k_quadratic<<<grid2(h, w), dim3(BX, BY), 0, s>>>(ut, h1, w1, out, h, w);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_linear(const float* uc, int hc, int wc, float* out, int h, int w,
+                          cudaStream_t s) {
+    if (h <= 0 || w <= 0) return cudaSuccess;
+    k_linear<<<grid2(h, w), dim3(BX, BY), 0, s>>>(uc, hc, wc, out, h, w);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_smooth(const float* in, float* out, int h, int w, float scale, cudaStream_t s) {
+    if (h <= 0 || w <= 0) return cudaSuccess;
+    k_smooth<<<grid2(h, w), dim3(BX, BY), 0, s>>>(in, out, h, w, scale);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_denoise(const float* in, float* out, int h, int w, float tau, float kpm,
+                           cudaStream_t s) {
+    if (h <= 0 || w <= 0) return cudaSuccess;
+    k_denoise<<<grid2(h, w), dim3(BX, BY), 0, s>>>(in, out, h, w, tau, 1.f / (kpm * kpm));
+    return cudaGetLastError();
+}
+
+}  // namespace eecmg

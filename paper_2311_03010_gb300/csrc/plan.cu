@@ -1,0 +1,666 @@
+// plan.cu -- planner, cascade driver and C ABI of the EECMG library.
+//
+// A plan fixes the level sizes (Section 2: each coarser side is ceil(n/2)),
+// the per-level PSFs of the Galerkin coarse operators (Eq. 14), the
+// economy iteration schedule (Section 2) and a device workspace.  A
+// restoration enqueues Algorithm 2 on a stream without any host round trip
+// (all Krylov scalars are decided on the device) and is captured once as a
+// CUDA graph, then replayed.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "launch.hpp"
+#include "plan.hpp"
+
+using namespace eecmg;
+
+namespace eecmg {
+
+thread_local std::string g_last_error = "no error";
+
+eecmg_status set_error(eecmg_status st, const std::string& msg) {
+    g_last_error = msg;
+    return st;
+}
+
+// Economy schedule m_l (Section 2) in exact integer arithmetic, l = 1..L:
+//   l > L/2:  m_l = ceil((L - L/2)^2 4^(L-l)) = ceil(L^2 4^(L-l) / 4)
+//   l <= L/2: m_l = ceil((L - 1.5 l) 4^(l-1)) = ceil((2L - 3l) 4^(l-1) / 2)
+// and at least 1 ("the smallest positive integer not less than t").
+int schedule_m(int L, int l) {
+    long long v;
+    if (2 * l > L) {
+        long long num = (long long)L * L;
+        for (int i = 0; i < L - l; ++i) num *= 4;
+        v = (num + 3) / 4;
+    } else {
+        long long num = 2LL * L - 3LL * l;
+        for (int i = 0; i < l - 1; ++i) num *= 4;
+        v = num > 0 ? (num + 1) / 2 : 1;
+    }
+    return v < 1 ? 1 : (int)v;
+}
+
+}  // namespace eecmg
+
+namespace {
+
+#define CK(call)                                                                          \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess)                                                            \
+            return set_error(EECMG_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+// Host PSF in convolution form, kh x kw, centred.
+struct Psf {
+    int kh = 1, kw = 1;
+    std::vector<double> k{1.0};
+    double at(int p, int q) const { return k[(size_t)(p + kh / 2) * kw + (q + kw / 2)]; }
+};
+
+// Eq. 14 with the RMS adjoint: K_c(p, q) = rho * K(2p, 2q).
+Psf coarsen(const Psf& f, double rho) {
+    Psf c;
+    const int ry = f.kh / 2 / 2, rx = f.kw / 2 / 2;
+    c.kh = 2 * ry + 1;
+    c.kw = 2 * rx + 1;
+    c.k.assign((size_t)c.kh * c.kw, 0.0);
+    for (int p = -ry; p <= ry; ++p)
+        for (int q = -rx; q <= rx; ++q) c.k[(size_t)(p + ry) * c.kw + (q + rx)] = rho * f.at(2 * p, 2 * q);
+    return c;
+}
+
+bool centrosymmetric(const Psf& f) {
+    double mx = 0.0;
+    for (double v : f.k) mx = std::fmax(mx, std::fabs(v));
+    for (int p = -f.kh / 2; p <= f.kh / 2; ++p)
+        for (int q = -f.kw / 2; q <= f.kw / 2; ++q)
+            if (std::fabs(f.at(p, q) - f.at(-p, -q)) > 1e-12 * mx) return false;
+    return true;
+}
+
+// Fills the device descriptor (correlation form) for H (transpose = 0:
+// C(dy, dx) = K(-dy, -dx)) or H^T (C = K).  Separable PSFs K = a b^T are
+// detected to FP64 rounding and stored as two factors.
+void make_taps(const Psf& f, bool transpose, Taps* t) {
+    std::memset(t, 0, sizeof(Taps));
+    const int ry = f.kh / 2, rx = f.kw / 2;
+    const int rt = ry > rx ? ry : rx;
+    t->ry = ry;
+    t->rx = rx;
+    t->rt = rt;
+    auto C = [&](int dy, int dx) { return transpose ? f.at(dy, dx) : f.at(-dy, -dx); };
+    // separability: K = a b^T through the largest entry
+    int p0 = 0, q0 = 0;
+    double mx = -1.0;
+    for (int p = -ry; p <= ry; ++p)
+        for (int q = -rx; q <= rx; ++q)
+            if (std::fabs(C(p, q)) > mx) {
+                mx = std::fabs(C(p, q));
+                p0 = p;
+                q0 = q;
+            }
+    bool sep = mx > 0.0;
+    if (sep) {
+        const double k00 = C(p0, q0);
+        const double sc = 1.0 / std::sqrt(std::fabs(k00));
+        const double sg = k00 < 0 ? -1.0 : 1.0;
+        std::vector<double> a(2 * ry + 1), b(2 * rx + 1);
+        for (int p = -ry; p <= ry; ++p) a[p + ry] = C(p, q0) * sc;
+        for (int q = -rx; q <= rx; ++q) b[q + rx] = C(p0, q) * sc * sg;
+        for (int p = -ry; p <= ry && sep; ++p)
+            for (int q = -rx; q <= rx; ++q)
+                if (std::fabs(C(p, q) - a[p + ry] * b[q + rx]) > 1e-12 * mx) {
+                    sep = false;
+                    break;
+                }
+        if (sep) {
+            for (int p = -ry; p <= ry; ++p) t->cy[p + rt] = (float)a[p + ry];
+            for (int q = -rx; q <= rx; ++q) t->cx[q + rt] = (float)b[q + rx];
+        }
+    }
+    t->sep = sep ? 1 : 0;
+    int n = 0;
+    for (int dy = -ry; dy <= ry; ++dy)
+        for (int dx = -rx; dx <= rx; ++dx) {
+            const double v = C(dy, dx);
+            if (v != 0.0) {
+                t->dy[n] = dy;
+                t->dx[n] = dx;
+                t->wt[n] = (float)v;
+                ++n;
+            }
+        }
+    t->ntap = n;
+}
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// cascade enqueue
+// ---------------------------------------------------------------------------
+
+namespace eecmg {
+
+eecmg_status solve_level_enqueue(eecmg_plan_s* P, int l, const float* g, float* u, int m,
+                                 bool zero_start, cudaStream_t s) {
+    LevelPlan& L = P->lv[l];
+    const size_t n = (size_t)L.h * L.w;
+    Scalars* sc = P->sc + l;
+    const Taps* tH = P->dtaps + 2 * l;
+    const Taps* tHT = P->dtaps + 2 * l + 1;
+    const int rt = L.rt, sepH = L.sepH, sepHT = L.sepHT;
+
+    ConvArgs ra;
+    ra.x = u;
+    ra.y = P->r;
+    ra.e0 = g;
+    ra.taps = tH;
+    ra.sc = sc;
+    ra.partials = P->partials;
+    ra.conv_tol2 = P->conv_tol2;
+    ra.disc2 = L.disc2;
+    ra.h = L.h;
+    ra.w = L.w;
+    ra.mode = CM_RESID;
+    ra.zero_input = zero_start ? 1 : 0;
+    CK(launch_conv(ra, rt, sepH, s));
+    if (m <= 0) return EECMG_OK;
+
+    if (P->opt.smoother == EECMG_SMOOTHER_MR2) {
+        ConvArgs c;
+        c.taps = tH;
+        c.sc = sc;
+        c.partials = P->partials;
+        c.h = L.h;
+        c.w = L.w;
+        // p_1 = H r_0
+        c.x = P->r;
+        c.y = P->p[1];
+        c.mode = CM_MR_P1;
+        CK(launch_conv(c, rt, sepH, s));
+        // q_1 = H p_1, alpha_1
+        c.x = P->p[1];
+        c.y = P->q[1];
+        c.e0 = P->r;
+        c.mode = CM_MR_Q1;
+        CK(launch_conv(c, rt, sepH, s));
+        for (int k = 2; k <= m; ++k) {
+            const int cur = k & 1, prev = cur ^ 1;
+            c.x = P->q[prev];
+            c.y = P->z;
+            c.e0 = nullptr;
+            c.e1 = P->q[cur];
+            c.has_e1 = k >= 3;
+            c.mode = CM_MR_A;
+            CK(launch_conv(c, rt, sepH, s));
+            CK(launch_mr_b(P->z, P->q[prev], P->q[cur], P->p[prev], P->p[cur], u, P->r, n, k >= 3,
+                           sc, P->partials, s));
+        }
+        CK(launch_step(u, P->p[m & 1], P->r, P->q[m & 1], n, 0, sc, P->partials, s));
+    } else {
+        float* sv = P->z;
+        float* pv = P->p[0];
+        float* qv = P->q[0];
+        ConvArgs c;
+        c.sc = sc;
+        c.partials = P->partials;
+        c.h = L.h;
+        c.w = L.w;
+        c.x = P->r;
+        c.y = sv;
+        c.y2 = pv;
+        c.taps = tHT;
+        c.mode = CM_CG_S0;
+        CK(launch_conv(c, rt, sepHT, s));
+        for (int k = 1; k <= m; ++k) {
+            ConvArgs q = c;
+            q.x = pv;
+            q.y = qv;
+            q.y2 = nullptr;
+            q.taps = tH;
+            q.mode = CM_CG_Q;
+            CK(launch_conv(q, rt, sepH, s));
+            CK(launch_step(u, pv, P->r, qv, n, 1, sc, P->partials, s));
+            if (k < m) {
+                ConvArgs t = c;
+                t.y2 = nullptr;
+                t.mode = CM_CG_S;
+                CK(launch_conv(t, rt, sepHT, s));
+                CK(launch_cg_p(pv, sv, n, sc, s));
+            }
+        }
+    }
+    return EECMG_OK;
+}
+
+// Starting guess of level l >= the number of zero-started levels, written
+// into u_l (Algorithm 2 Step 2 items 1-4, or Algorithm 1 Step 2 items 1-3).
+eecmg_status prolong_enqueue(eecmg_plan_s* P, int l, cudaStream_t s) {
+    LevelPlan& L = P->lv[l];
+    LevelPlan& L1 = P->lv[l - 1];
+    float* up = P->z;  // prolonged, level l
+    if (P->opt.prolong == EECMG_PROLONG_EECMG) {
+        LevelPlan& L2 = P->lv[l - 2];
+        float* ext = P->q[0];  // on the level-(l-1) grid
+        CK(launch_extrapolate(L1.u, L1.h, L1.w, L2.u, L2.h, L2.w, ext, s));
+        CK(launch_quadratic(ext, L1.h, L1.w, up, L.h, L.w, s));
+    } else if (P->opt.prolong == EECMG_PROLONG_IECMG_P) {
+        CK(launch_quadratic(L1.u, L1.h, L1.w, up, L.h, L.w, s));
+    } else {
+        CK(launch_linear(L1.u, L1.h, L1.w, up, L.h, L.w, s));
+    }
+    float* sm = P->p[0];
+    CK(launch_smooth(up, sm, L.h, L.w, (float)P->opt.s_scale, s));
+    const int steps = P->opt.diffusion_steps;
+    if (steps <= 0) {
+        CK(cudaMemcpyAsync(L.u, sm, sizeof(float) * L.h * L.w, cudaMemcpyDeviceToDevice, s));
+        return EECMG_OK;
+    }
+    float* cur = sm;
+    for (int d = 0; d < steps; ++d) {
+        float* nxt = (d == steps - 1) ? L.u : (cur == sm ? up : sm);
+        CK(launch_denoise(cur, nxt, L.h, L.w, (float)P->tau, (float)P->kpm, s));
+        cur = nxt;
+    }
+    return EECMG_OK;
+}
+
+eecmg_status cascade_enqueue(eecmg_plan_s* P, cudaStream_t s) {
+    const int L = P->L;
+    for (int l = L - 1; l > 0; --l)
+        CK(launch_restrict(P->lv[l].g, P->lv[l].h, P->lv[l].w, P->lv[l - 1].g, P->lv[l - 1].h,
+                           P->lv[l - 1].w, s));
+    const int nzero = P->opt.prolong == EECMG_PROLONG_EECMG ? 2 : 1;
+    for (int l = 0; l < L; ++l) {
+        const bool zero = l < nzero;
+        if (zero) {
+            CK(cudaMemsetAsync(P->lv[l].u, 0, sizeof(float) * P->lv[l].h * P->lv[l].w, s));
+        } else {
+            eecmg_status st = prolong_enqueue(P, l, s);
+            if (st != EECMG_OK) return st;
+        }
+        eecmg_status st = solve_level_enqueue(P, l, P->lv[l].g, P->lv[l].u, P->lv[l].m, zero, s);
+        if (st != EECMG_OK) return st;
+    }
+    return EECMG_OK;
+}
+
+eecmg_status run_cascade(eecmg_plan_s* P, cudaStream_t s) {
+    if (!P->opt.use_graph) return cascade_enqueue(P, s);
+    if (!P->gexec) {
+        CK(cudaStreamBeginCapture(P->cap_stream, cudaStreamCaptureModeThreadLocal));
+        eecmg_status st = cascade_enqueue(P, P->cap_stream);
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamEndCapture(P->cap_stream, &graph);
+        if (st != EECMG_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return st;
+        }
+        if (e != cudaSuccess) return set_error(EECMG_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+        e = cudaGraphInstantiate(&P->gexec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            P->gexec = nullptr;
+            return set_error(EECMG_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+        }
+    }
+    CK(cudaGraphLaunch(P->gexec, s));
+    return EECMG_OK;
+}
+
+}  // namespace eecmg
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+
+extern "C" {
+
+const char* eecmg_last_error(void) { return g_last_error.c_str(); }
+
+const char* eecmg_version(void) { return "eecmg-gb300 0.1 (sm_103a)"; }
+
+eecmg_status eecmg_default_options(eecmg_options* o) {
+    if (!o) return set_error(EECMG_ERR_INVALID_ARG, "eecmg_default_options: NULL");
+    o->smoother = EECMG_SMOOTHER_MR2;
+    o->coarse_op = EECMG_COARSE_GALERKIN_RMS;
+    o->storage = EECMG_STORAGE_FP32;
+    o->stop = EECMG_STOP_FIXED;
+    o->c = 1.1;
+    o->delta = 0.0;
+    o->diffusion_steps = 1;
+    o->s_scale = 1.0;
+    o->conv_tol = 1e-5;
+    o->prolong = EECMG_PROLONG_EECMG;
+    o->use_graph = 1;
+    return EECMG_OK;
+}
+
+eecmg_status eecmg_plan(int width, int height, int levels, const double* psf, int psf_w, int psf_h,
+                        double alpha, double k, const int* iters, const eecmg_options* opt,
+                        eecmg_plan_t* out) {
+    if (!out) return set_error(EECMG_ERR_INVALID_ARG, "eecmg_plan: out is NULL");
+    *out = nullptr;
+    if (width < 1 || height < 1 || levels < 1 || levels > 30)
+        return set_error(EECMG_ERR_INVALID_ARG, "eecmg_plan: need width, height >= 1 and 1 <= levels <= 30");
+    if (!psf || psf_w < 1 || psf_h < 1 || !(psf_w & 1) || !(psf_h & 1))
+        return set_error(EECMG_ERR_INVALID_ARG, "eecmg_plan: PSF must be non-NULL with odd sizes");
+    if (psf_w / 2 > EECMG_MAX_RADIUS || psf_h / 2 > EECMG_MAX_RADIUS)
+        return set_error(EECMG_ERR_INVALID_ARG, "eecmg_plan: PSF radius exceeds EECMG_MAX_RADIUS");
+    if (!(alpha >= 0.0 && alpha <= 0.25))
+        return set_error(EECMG_ERR_INVALID_ARG, "eecmg_plan: alpha (tau) must be in [0, 0.25]");
+    if (!(k > 0.0) || !std::isfinite(k)) return set_error(EECMG_ERR_INVALID_ARG, "eecmg_plan: k must be > 0");
+    eecmg_options o;
+    eecmg_default_options(&o);
+    if (opt) o = *opt;
+    if (o.smoother < 0 || o.smoother > 1 || o.coarse_op < 0 || o.coarse_op > 1 || o.storage < 0 ||
+        o.storage > 1 || o.stop < 0 || o.stop > 1 || o.prolong < 0 || o.prolong > 2 ||
+        o.diffusion_steps < 0 || !(o.conv_tol >= 0.0) || !(o.s_scale >= 0.0))
+        return set_error(EECMG_ERR_INVALID_ARG, "eecmg_plan: invalid option value");
+    if (o.stop == EECMG_STOP_DISCREPANCY && (!(o.c > 0.0) || !(o.delta >= 0.0)))
+        return set_error(EECMG_ERR_INVALID_ARG, "eecmg_plan: discrepancy rule needs c > 0, delta >= 0");
+    if (o.storage != EECMG_STORAGE_FP32)
+        return set_error(EECMG_ERR_UNSUPPORTED, "eecmg_plan: BF16 storage is not available in this build");
+    double sum = 0.0;
+    for (int i = 0; i < psf_w * psf_h; ++i) {
+        if (!std::isfinite(psf[i])) return set_error(EECMG_ERR_INVALID_ARG, "eecmg_plan: PSF has non-finite entries");
+        sum += psf[i];
+    }
+    if (!(sum > 0.0)) return set_error(EECMG_ERR_INVALID_ARG, "eecmg_plan: PSF sum must be positive");
+    if (iters)
+        for (int l = 0; l < levels; ++l)
+            if (iters[l] < 0) return set_error(EECMG_ERR_INVALID_ARG, "eecmg_plan: negative iteration count");
+
+    Psf fine;
+    fine.kh = psf_h;
+    fine.kw = psf_w;
+    fine.k.assign(psf, psf + (size_t)psf_w * psf_h);
+    if (o.smoother == EECMG_SMOOTHER_MR2 && !centrosymmetric(fine))
+        return set_error(EECMG_ERR_UNSUPPORTED,
+                         "eecmg_plan: MR-II needs a symmetric H (centrosymmetric PSF); use CGLS");
+
+    auto* P = new (std::nothrow) eecmg_plan_s();
+    if (!P) return set_error(EECMG_ERR_OOM, "eecmg_plan: host allocation failed");
+    P->W = width;
+    P->H = height;
+    P->L = levels;
+    P->tau = alpha;
+    P->kpm = k;
+    P->opt = o;
+    P->conv_tol2 = o.conv_tol * o.conv_tol;
+    CK(cudaGetDevice(&P->device));
+    P->lv.resize(levels);
+    P->lv[levels - 1].h = height;
+    P->lv[levels - 1].w = width;
+    for (int l = levels - 1; l > 0; --l) {
+        P->lv[l - 1].h = (P->lv[l].h + 1) / 2;
+        P->lv[l - 1].w = (P->lv[l].w + 1) / 2;
+    }
+    std::vector<Psf> psfs(levels);
+    psfs[levels - 1] = fine;
+    for (int l = levels - 1; l > 0; --l) {
+        const double rho = ((double)P->lv[l].h * P->lv[l].w) / ((double)P->lv[l - 1].h * P->lv[l - 1].w);
+        psfs[l - 1] = coarsen(psfs[l], rho);
+        if (o.coarse_op == EECMG_COARSE_GALERKIN_RENORM) {
+            double s = 0.0;
+            for (double v : psfs[l - 1].k) s += v;
+            if (s != 0.0)
+                for (double& v : psfs[l - 1].k) v *= sum / s;
+        }
+    }
+    std::vector<Taps> htaps(2 * levels);
+    size_t max_n = 0, sum_n = 0;
+    for (int l = 0; l < levels; ++l) {
+        LevelPlan& L = P->lv[l];
+        L.m = iters ? iters[l] : schedule_m(levels, l + 1);
+        make_taps(psfs[l], false, &htaps[2 * l]);
+        make_taps(psfs[l], true, &htaps[2 * l + 1]);
+        L.rt = htaps[2 * l].rt;
+        L.sepH = htaps[2 * l].sep;
+        L.sepHT = htaps[2 * l + 1].sep;
+        const size_t n = (size_t)L.h * L.w;
+        L.disc2 = o.stop == EECMG_STOP_DISCREPANCY ? (o.c * o.delta) * (o.c * o.delta) * (double)n : 0.0;
+        max_n = n > max_n ? n : max_n;
+        sum_n += n;
+    }
+    const size_t fine_n = (size_t)width * height;
+    size_t max_blocks = 1;
+    for (int l = 0; l < levels; ++l) {
+        const size_t n = (size_t)P->lv[l].h * P->lv[l].w;
+        size_t b = conv_blocks(P->lv[l].h, P->lv[l].w);
+        if (ew_blocks(n) > b) b = ew_blocks(n);
+        if (b > max_blocks) max_blocks = b;
+    }
+    (void)fine_n;
+    // workspace: g and u pyramids, six solver vectors, taps, scalars, partials
+    size_t off = 0;
+    std::vector<size_t> g_off(levels), u_off(levels);
+    for (int l = 0; l < levels; ++l) {
+        g_off[l] = off;
+        off = align_up(off + sizeof(float) * P->lv[l].h * P->lv[l].w, 256);
+    }
+    for (int l = 0; l < levels; ++l) {
+        u_off[l] = off;
+        off = align_up(off + sizeof(float) * P->lv[l].h * P->lv[l].w, 256);
+    }
+    size_t vec_off[6];
+    for (int i = 0; i < 6; ++i) {
+        vec_off[i] = off;
+        off = align_up(off + sizeof(float) * max_n, 256);
+    }
+    const size_t taps_off = off;
+    off = align_up(off + sizeof(Taps) * 2 * levels, 256);
+    const size_t sc_off = off;
+    off = align_up(off + sizeof(Scalars) * levels, 256);
+    const size_t part_off = off;
+    off = align_up(off + sizeof(double) * NPART * max_blocks, 256);
+    P->ws_bytes = off;
+    cudaError_t e = cudaMalloc((void**)&P->ws, off);
+    if (e != cudaSuccess) {
+        delete P;
+        cudaGetLastError();
+        return set_error(EECMG_ERR_OOM, std::string("eecmg_plan: workspace allocation failed: ") + cudaGetErrorString(e));
+    }
+    for (int l = 0; l < levels; ++l) {
+        P->lv[l].g = (float*)(P->ws + g_off[l]);
+        P->lv[l].u = (float*)(P->ws + u_off[l]);
+    }
+    P->r = (float*)(P->ws + vec_off[0]);
+    P->z = (float*)(P->ws + vec_off[1]);
+    P->p[0] = (float*)(P->ws + vec_off[2]);
+    P->p[1] = (float*)(P->ws + vec_off[3]);
+    P->q[0] = (float*)(P->ws + vec_off[4]);
+    P->q[1] = (float*)(P->ws + vec_off[5]);
+    P->dtaps = (Taps*)(P->ws + taps_off);
+    P->sc = (Scalars*)(P->ws + sc_off);
+    P->partials = (double*)(P->ws + part_off);
+    P->max_blocks = max_blocks;
+    auto cleanup = [&](cudaError_t err, const char* what) {
+        cudaFree(P->ws);
+        if (P->cap_stream) cudaStreamDestroy(P->cap_stream);
+        delete P;
+        return set_error(EECMG_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(err));
+    };
+    e = cudaMemset(P->ws, 0, off);
+    if (e != cudaSuccess) return cleanup(e, "eecmg_plan: memset");
+    e = cudaMemcpy(P->dtaps, htaps.data(), sizeof(Taps) * 2 * levels, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cleanup(e, "eecmg_plan: taps upload");
+    e = cudaStreamCreateWithFlags(&P->cap_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cleanup(e, "eecmg_plan: stream");
+    *out = P;
+    return EECMG_OK;
+}
+
+eecmg_status eecmg_plan_destroy(eecmg_plan_t P) {
+    if (!P) return EECMG_OK;
+    cudaDeviceSynchronize();
+    if (P->gexec) cudaGraphExecDestroy(P->gexec);
+    if (P->cap_stream) cudaStreamDestroy(P->cap_stream);
+    cudaFree(P->ws);
+    delete P;
+    return EECMG_OK;
+}
+
+eecmg_status eecmg_plan_info(eecmg_plan_t P, int* levels, int* level_w, int* level_h, int* iters,
+                             size_t* workspace_bytes) {
+    if (!P) return set_error(EECMG_ERR_INVALID_ARG, "eecmg_plan_info: NULL plan");
+    if (levels) *levels = P->L;
+    for (int l = 0; l < P->L; ++l) {
+        if (level_w) level_w[l] = P->lv[l].w;
+        if (level_h) level_h[l] = P->lv[l].h;
+        if (iters) iters[l] = P->lv[l].m;
+    }
+    if (workspace_bytes) *workspace_bytes = P->ws_bytes;
+    return EECMG_OK;
+}
+
+eecmg_status eecmg_restore(eecmg_plan_t P, const float* g, float* u, cudaStream_t s) {
+    if (!P || !g || !u) return set_error(EECMG_ERR_INVALID_ARG, "eecmg_restore: NULL argument");
+    const size_t bytes = sizeof(float) * P->W * P->H;
+    LevelPlan& F = P->lv[P->L - 1];
+    if (g != F.g) CK(cudaMemcpyAsync(F.g, g, bytes, cudaMemcpyDeviceToDevice, s));
+    eecmg_status st = run_cascade(P, s);
+    if (st != EECMG_OK) return st;
+    if (u != F.u) CK(cudaMemcpyAsync(u, F.u, bytes, cudaMemcpyDeviceToDevice, s));
+    P->last_stream = s;
+    return EECMG_OK;
+}
+
+eecmg_status eecmg_restore_host(eecmg_plan_t P, const float* g, float* u, cudaStream_t s) {
+    if (!P || !g || !u) return set_error(EECMG_ERR_INVALID_ARG, "eecmg_restore_host: NULL argument");
+    const size_t bytes = sizeof(float) * P->W * P->H;
+    LevelPlan& F = P->lv[P->L - 1];
+    CK(cudaMemcpyAsync(F.g, g, bytes, cudaMemcpyHostToDevice, s));
+    eecmg_status st = run_cascade(P, s);
+    if (st != EECMG_OK) return st;
+    CK(cudaMemcpyAsync(u, F.u, bytes, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    P->last_stream = s;
+    return EECMG_OK;
+}
+
+eecmg_status eecmg_plan_stats(eecmg_plan_t P, int* iters_done, double* res_rms) {
+    if (!P) return set_error(EECMG_ERR_INVALID_ARG, "eecmg_plan_stats: NULL plan");
+    CK(cudaStreamSynchronize(P->last_stream));
+    CK(cudaStreamSynchronize(P->cap_stream));
+    std::vector<Scalars> h(P->L);
+    CK(cudaMemcpy(h.data(), P->sc, sizeof(Scalars) * P->L, cudaMemcpyDeviceToHost));
+    bool numeric = false;
+    for (int l = 0; l < P->L; ++l) {
+        if (iters_done) iters_done[l] = h[l].iters;
+        if (res_rms) res_rms[l] = std::sqrt(h[l].rr / ((double)P->lv[l].h * P->lv[l].w));
+        if (h[l].stopped == 3) numeric = true;
+    }
+    if (numeric) return set_error(EECMG_ERR_NUMERIC, "eecmg_plan_stats: a level produced a non-finite scalar");
+    return EECMG_OK;
+}
+
+static eecmg_status check_level(eecmg_plan_t P, int level, const char* who) {
+    if (!P) return set_error(EECMG_ERR_INVALID_ARG, std::string(who) + ": NULL plan");
+    if (level < 0 || level >= P->L) return set_error(EECMG_ERR_INVALID_ARG, std::string(who) + ": level out of range");
+    return EECMG_OK;
+}
+
+eecmg_status eecmg_apply_H(eecmg_plan_t P, int level, const float* x, float* y, int transpose,
+                           cudaStream_t s) {
+    eecmg_status st = check_level(P, level, "eecmg_apply_H");
+    if (st != EECMG_OK) return st;
+    if (!x || !y || x == y) return set_error(EECMG_ERR_INVALID_ARG, "eecmg_apply_H: NULL or aliased buffers");
+    LevelPlan& L = P->lv[level];
+    ConvArgs a;
+    a.x = x;
+    a.y = y;
+    a.h = L.h;
+    a.w = L.w;
+    a.taps = P->dtaps + 2 * level + (transpose ? 1 : 0);
+    a.mode = CM_STORE;
+    CK(launch_conv(a, L.rt, transpose ? L.sepHT : L.sepH, s));
+    return EECMG_OK;
+}
+
+eecmg_status eecmg_restrict(eecmg_plan_t P, int level, const float* fine, float* coarse,
+                            cudaStream_t s) {
+    eecmg_status st = check_level(P, level, "eecmg_restrict");
+    if (st != EECMG_OK) return st;
+    if (level + 1 >= P->L) return set_error(EECMG_ERR_INVALID_ARG, "eecmg_restrict: level must be < levels - 1");
+    if (!fine || !coarse) return set_error(EECMG_ERR_INVALID_ARG, "eecmg_restrict: NULL buffer");
+    LevelPlan& F = P->lv[level + 1];
+    LevelPlan& C = P->lv[level];
+    CK(launch_restrict(fine, F.h, F.w, coarse, C.h, C.w, s));
+    return EECMG_OK;
+}
+
+eecmg_status eecmg_prolong(eecmg_plan_t P, int level, const float* u1, const float* u2, float* out,
+                           cudaStream_t s) {
+    eecmg_status st = check_level(P, level, "eecmg_prolong");
+    if (st != EECMG_OK) return st;
+    if (level < 2) return set_error(EECMG_ERR_INVALID_ARG, "eecmg_prolong: level must be >= 2");
+    if (!u1 || !u2 || !out) return set_error(EECMG_ERR_INVALID_ARG, "eecmg_prolong: NULL buffer");
+    LevelPlan& L = P->lv[level];
+    LevelPlan& L1 = P->lv[level - 1];
+    LevelPlan& L2 = P->lv[level - 2];
+    CK(launch_extrapolate(u1, L1.h, L1.w, u2, L2.h, L2.w, P->q[0], s));
+    CK(launch_quadratic(P->q[0], L1.h, L1.w, out, L.h, L.w, s));
+    return EECMG_OK;
+}
+
+eecmg_status eecmg_prolong_single(eecmg_plan_t P, int level, const float* u1, float* out,
+                                  int quadratic, cudaStream_t s) {
+    eecmg_status st = check_level(P, level, "eecmg_prolong_single");
+    if (st != EECMG_OK) return st;
+    if (level < 1) return set_error(EECMG_ERR_INVALID_ARG, "eecmg_prolong_single: level must be >= 1");
+    if (!u1 || !out) return set_error(EECMG_ERR_INVALID_ARG, "eecmg_prolong_single: NULL buffer");
+    LevelPlan& L = P->lv[level];
+    LevelPlan& L1 = P->lv[level - 1];
+    if (quadratic)
+        CK(launch_quadratic(u1, L1.h, L1.w, out, L.h, L.w, s));
+    else
+        CK(launch_linear(u1, L1.h, L1.w, out, L.h, L.w, s));
+    return EECMG_OK;
+}
+
+eecmg_status eecmg_smooth(eecmg_plan_t P, int level, const float* in, float* out, cudaStream_t s) {
+    eecmg_status st = check_level(P, level, "eecmg_smooth");
+    if (st != EECMG_OK) return st;
+    if (!in || !out || in == out) return set_error(EECMG_ERR_INVALID_ARG, "eecmg_smooth: NULL or aliased buffers");
+    CK(launch_smooth(in, out, P->lv[level].h, P->lv[level].w, (float)P->opt.s_scale, s));
+    return EECMG_OK;
+}
+
+eecmg_status eecmg_denoise(eecmg_plan_t P, int level, const float* in, float* out, cudaStream_t s) {
+    eecmg_status st = check_level(P, level, "eecmg_denoise");
+    if (st != EECMG_OK) return st;
+    if (!in || !out || in == out) return set_error(EECMG_ERR_INVALID_ARG, "eecmg_denoise: NULL or aliased buffers");
+    CK(launch_denoise(in, out, P->lv[level].h, P->lv[level].w, (float)P->tau, (float)P->kpm, s));
+    return EECMG_OK;
+}
+
+eecmg_status eecmg_level_solve(eecmg_plan_t P, int level, const float* g, float* u, int m,
+                               cudaStream_t s) {
+    eecmg_status st = check_level(P, level, "eecmg_level_solve");
+    if (st != EECMG_OK) return st;
+    if (!g || !u || m < 0) return set_error(EECMG_ERR_INVALID_ARG, "eecmg_level_solve: bad arguments");
+    st = solve_level_enqueue(P, level, g, u, m, false, s);
+    P->last_stream = s;
+    return st;
+}
+
+eecmg_status eecmg_restore_batched(const eecmg_plan_t* plans, const float* const* g, float* const* u,
+                                   int n, cudaStream_t s) {
+    if (n < 0 || (n > 0 && (!plans || !g || !u)))
+        return set_error(EECMG_ERR_INVALID_ARG, "eecmg_restore_batched: bad arguments");
+    for (int i = 0; i < n; ++i) {
+        eecmg_status st = eecmg_restore(plans[i], g[i], u[i], s);
+        if (st != EECMG_OK) return st;
+    }
+    return EECMG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,54 @@
+// plan.hpp -- the plan object behind eecmg_plan_t (internal).
+#pragma once
+
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+
+namespace eecmg {
+
+struct LevelPlan {
+    int h = 0, w = 0;   // rows, cols
+    int m = 0;          // scheduled iterations
+    int rt = 0;         // kernel template radius
+    int sepH = 0, sepHT = 0;
+    double disc2 = 0.0; // (c delta)^2 N_l, discrepancy rule
+    float* g = nullptr; // data pyramid (workspace)
+    float* u = nullptr; // level solution (workspace)
+};
+
+eecmg_status set_error(eecmg_status st, const std::string& msg);
+int schedule_m(int L, int l);
+
+}  // namespace eecmg
+
+struct eecmg_plan_s {
+    int W = 0, H = 0, L = 0;
+    double tau = 0.2, kpm = 10.0;
+    double conv_tol2 = 0.0;
+    eecmg_options opt{};
+    int device = 0;
+    std::vector<eecmg::LevelPlan> lv;
+    char* ws = nullptr;
+    size_t ws_bytes = 0;
+    size_t max_blocks = 0;
+    eecmg::Taps* dtaps = nullptr;     // [2l] = H_l, [2l+1] = H_l^T
+    eecmg::Scalars* sc = nullptr;     // one per level
+    double* partials = nullptr;
+    float* r = nullptr;
+    float* z = nullptr;
+    float* p[2] = {nullptr, nullptr};
+    float* q[2] = {nullptr, nullptr};
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    cudaStream_t last_stream = nullptr;
+};
+
+namespace eecmg {
+eecmg_status solve_level_enqueue(eecmg_plan_s* P, int l, const float* g, float* u, int m,
+                                 bool zero_start, cudaStream_t s);
+eecmg_status prolong_enqueue(eecmg_plan_s* P, int l, cudaStream_t s);
+eecmg_status cascade_enqueue(eecmg_plan_s* P, cudaStream_t s);
+eecmg_status run_cascade(eecmg_plan_s* P, cudaStream_t s);
+}  // namespace eecmg

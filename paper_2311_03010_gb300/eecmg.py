@@ -1,0 +1,307 @@
+"""Python binding of the EECMG C ABI (include/eecmg.h), by ctypes.
+
+Argument marshalling only: every step of the method runs in the CUDA
+library ``libeecmg.so``.  Device buffers are passed as torch CUDA tensors
+(float32, contiguous) or raw integer addresses; streams as
+``torch.cuda.Stream`` objects, raw ``cudaStream_t`` integers, or None (the
+current torch stream when torch is loaded, else the legacy default stream).
+Functions keep the C names; errors raise ``EecmgError``.
+
+The library must have been built (``build_lib.build()``); if it is missing
+this module raises at load time rather than falling back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libeecmg.so")
+
+STATUS = {0: "EECMG_OK", 1: "EECMG_ERR_INVALID_ARG", 2: "EECMG_ERR_UNSUPPORTED",
+          3: "EECMG_ERR_OOM", 4: "EECMG_ERR_CUDA", 5: "EECMG_ERR_NUMERIC",
+          6: "EECMG_ERR_TIMEOUT", 7: "EECMG_ERR_BUSY"}
+
+SMOOTHER = {"mr2": 0, "cgls": 1}
+COARSE = {"rms": 0, "renorm": 1}
+STORAGE = {"fp32": 0, "bf16": 1}
+STOP = {"fixed": 0, "discrepancy": 1}
+PROLONG = {"eecmg": 0, "iecmg_p": 1, "iecmg_l": 2}
+
+
+class EecmgError(RuntimeError):
+    def __init__(self, func, status, msg):
+        super().__init__(f"{func}: {STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class eecmg_options(ctypes.Structure):
+    _fields_ = [
+        ("smoother", ctypes.c_int),
+        ("coarse_op", ctypes.c_int),
+        ("storage", ctypes.c_int),
+        ("stop", ctypes.c_int),
+        ("c", ctypes.c_double),
+        ("delta", ctypes.c_double),
+        ("diffusion_steps", ctypes.c_int),
+        ("s_scale", ctypes.c_double),
+        ("conv_tol", ctypes.c_double),
+        ("prolong", ctypes.c_int),
+        ("use_graph", ctypes.c_int),
+    ]
+
+
+_VP = ctypes.c_void_p
+_I = ctypes.c_int
+_D = ctypes.c_double
+_PI = ctypes.POINTER(ctypes.c_int)
+_PD = ctypes.POINTER(ctypes.c_double)
+
+# name -> argtypes (all return eecmg_status unless listed in _RESTYPES)
+_SIGS = {
+    "eecmg_default_options": [ctypes.POINTER(eecmg_options)],
+    "eecmg_plan": [_I, _I, _I, _PD, _I, _I, _D, _D, _PI, ctypes.POINTER(eecmg_options),
+                   ctypes.POINTER(_VP)],
+    "eecmg_plan_destroy": [_VP],
+    "eecmg_plan_info": [_VP, _PI, _PI, _PI, _PI, ctypes.POINTER(ctypes.c_size_t)],
+    "eecmg_restore": [_VP, _VP, _VP, _VP],
+    "eecmg_restore_host": [_VP, _VP, _VP, _VP],
+    "eecmg_restore_batched": [ctypes.POINTER(_VP), ctypes.POINTER(_VP), ctypes.POINTER(_VP), _I,
+                              _VP],
+    "eecmg_plan_stats": [_VP, _PI, _PD],
+    "eecmg_apply_H": [_VP, _I, _VP, _VP, _I, _VP],
+    "eecmg_restrict": [_VP, _I, _VP, _VP, _VP],
+    "eecmg_prolong": [_VP, _I, _VP, _VP, _VP, _VP],
+    "eecmg_prolong_single": [_VP, _I, _VP, _VP, _I, _VP],
+    "eecmg_smooth": [_VP, _I, _VP, _VP, _VP],
+    "eecmg_denoise": [_VP, _I, _VP, _VP, _VP],
+    "eecmg_level_solve": [_VP, _I, _VP, _VP, _I, _VP],
+    "eecmg_server_create": [ctypes.c_size_t, _I, ctypes.POINTER(_VP)],
+    "eecmg_server_submit": [_VP, _VP, _VP, _VP, ctypes.POINTER(ctypes.c_uint64)],
+    "eecmg_server_poll": [_VP, ctypes.c_uint64, _PI, _PD],
+    "eecmg_server_drain": [_VP],
+    "eecmg_server_destroy": [_VP],
+    "eecmg_last_error": [],
+    "eecmg_version": [],
+}
+_RESTYPES = {"eecmg_last_error": ctypes.c_char_p, "eecmg_version": ctypes.c_char_p}
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Loads libeecmg.so; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"EECMG CUDA library not built: {path} is missing "
+                           "(run paper_2311_03010_gb300.build_lib.build())")
+    lib = ctypes.CDLL(path)
+    for name, args in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = _RESTYPES.get(name, ctypes.c_int)
+    _lib = lib
+    return lib
+
+
+def _call(name, *args):
+    lib = load()
+    st = getattr(lib, name)(*args)
+    if st != 0:
+        raise EecmgError(name, st, lib.eecmg_last_error().decode())
+
+
+def _ptr(x):
+    """Device (or host) address of a tensor / array / int."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):  # torch tensor
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        if str(x.dtype) != "torch.float32":
+            raise ValueError("tensor must be float32")
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        if x.dtype != np.float32 or not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous float32")
+        return x.ctypes.data
+    raise TypeError(f"cannot take the address of {type(x)}")
+
+
+def _stream(s):
+    if s is None:
+        try:
+            import torch
+
+            if torch.cuda.is_available() and torch.cuda.is_initialized():
+                return torch.cuda.current_stream().cuda_stream
+        except ImportError:
+            pass
+        return None
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+def eecmg_version() -> str:
+    return load().eecmg_version().decode()
+
+
+def eecmg_last_error() -> str:
+    return load().eecmg_last_error().decode()
+
+
+def eecmg_default_options(**kw) -> eecmg_options:
+    o = eecmg_options()
+    _call("eecmg_default_options", ctypes.byref(o))
+    for k, v in kw.items():
+        table = {"smoother": SMOOTHER, "coarse_op": COARSE, "storage": STORAGE, "stop": STOP,
+                 "prolong": PROLONG}.get(k)
+        setattr(o, k, table[v] if (table and isinstance(v, str)) else v)
+    return o
+
+
+def eecmg_plan(width, height, levels, psf, alpha=0.2, k=10.0, iters=None, opt=None, **kw):
+    """Returns an opaque plan handle (int).  kw are option overrides."""
+    psf = np.ascontiguousarray(psf, dtype=np.float64)
+    if opt is None:
+        opt = eecmg_default_options(**kw)
+    it = None
+    if iters is not None:
+        it = (ctypes.c_int * levels)(*[int(v) for v in iters])
+    h = _VP()
+    _call("eecmg_plan", int(width), int(height), int(levels), psf.ctypes.data_as(_PD),
+          psf.shape[1], psf.shape[0], float(alpha), float(k), it, ctypes.byref(opt),
+          ctypes.byref(h))
+    return h.value
+
+
+def eecmg_plan_destroy(plan):
+    _call("eecmg_plan_destroy", plan)
+
+
+def eecmg_plan_info(plan):
+    n = _I()
+    _call("eecmg_plan_info", plan, ctypes.byref(n), None, None, None, None)
+    L = n.value
+    w = (_I * L)()
+    hh = (_I * L)()
+    m = (_I * L)()
+    ws = ctypes.c_size_t()
+    _call("eecmg_plan_info", plan, None, w, hh, m, ctypes.byref(ws))
+    return {"levels": L, "w": list(w), "h": list(hh), "iters": list(m),
+            "workspace_bytes": ws.value}
+
+
+def eecmg_restore(plan, g, u, stream=None):
+    _call("eecmg_restore", plan, _ptr(g), _ptr(u), _stream(stream))
+
+
+def eecmg_restore_host(plan, g, u, stream=None):
+    _call("eecmg_restore_host", plan, _ptr(g), _ptr(u), _stream(stream))
+
+
+def eecmg_restore_batched(plans, gs, us, stream=None):
+    n = len(plans)
+    P = (_VP * n)(*plans)
+    G = (_VP * n)(*[_ptr(x) for x in gs])
+    U = (_VP * n)(*[_ptr(x) for x in us])
+    _call("eecmg_restore_batched", P, G, U, n, _stream(stream))
+
+
+def eecmg_plan_stats(plan):
+    L = eecmg_plan_info(plan)["levels"]
+    it = (_I * L)()
+    res = (_D * L)()
+    _call("eecmg_plan_stats", plan, it, res)
+    return list(it), list(res)
+
+
+def eecmg_apply_H(plan, level, x, y, transpose=0, stream=None):
+    _call("eecmg_apply_H", plan, int(level), _ptr(x), _ptr(y), int(transpose), _stream(stream))
+
+
+def eecmg_restrict(plan, level, fine, coarse, stream=None):
+    _call("eecmg_restrict", plan, int(level), _ptr(fine), _ptr(coarse), _stream(stream))
+
+
+def eecmg_prolong(plan, level, u1, u2, out, stream=None):
+    _call("eecmg_prolong", plan, int(level), _ptr(u1), _ptr(u2), _ptr(out), _stream(stream))
+
+
+def eecmg_prolong_single(plan, level, u1, out, quadratic=1, stream=None):
+    _call("eecmg_prolong_single", plan, int(level), _ptr(u1), _ptr(out), int(quadratic),
+          _stream(stream))
+
+
+def eecmg_smooth(plan, level, x, y, stream=None):
+    _call("eecmg_smooth", plan, int(level), _ptr(x), _ptr(y), _stream(stream))
+
+
+def eecmg_denoise(plan, level, x, y, stream=None):
+    _call("eecmg_denoise", plan, int(level), _ptr(x), _ptr(y), _stream(stream))
+
+
+def eecmg_level_solve(plan, level, g, u, m, stream=None):
+    _call("eecmg_level_solve", plan, int(level), _ptr(g), _ptr(u), int(m), _stream(stream))
+
+
+def eecmg_server_create(mem_budget_bytes, max_slots):
+    h = _VP()
+    _call("eecmg_server_create", ctypes.c_size_t(int(mem_budget_bytes)), int(max_slots),
+          ctypes.byref(h))
+    return h.value
+
+
+def eecmg_server_submit(srv, plan, g, u):
+    t = ctypes.c_uint64()
+    _call("eecmg_server_submit", srv, plan, _ptr(g), _ptr(u), ctypes.byref(t))
+    return t.value
+
+
+def eecmg_server_poll(srv, ticket):
+    done = _I()
+    lat = _D()
+    _call("eecmg_server_poll", srv, ctypes.c_uint64(ticket), ctypes.byref(done),
+          ctypes.byref(lat))
+    return bool(done.value), lat.value
+
+
+def eecmg_server_drain(srv):
+    _call("eecmg_server_drain", srv)
+
+
+def eecmg_server_destroy(srv):
+    _call("eecmg_server_destroy", srv)
+
+
+class Plan:
+    """Owning wrapper of an eecmg_plan_t (destroyed with the object)."""
+
+    def __init__(self, width, height, levels, psf, alpha=0.2, k=10.0, iters=None, **opts):
+        self.width, self.height, self.levels = int(width), int(height), int(levels)
+        self.handle = eecmg_plan(width, height, levels, psf, alpha, k, iters, **opts)
+        self.info = eecmg_plan_info(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            eecmg_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def restore(self, g, u, stream=None):
+        eecmg_restore(self.handle, g, u, stream)
+
+    def stats(self):
+        return eecmg_plan_stats(self.handle)

@@ -1,0 +1,75 @@
+"""The C-ABI library builds, loads without a GPU, and exports every declared entry point.
+
+Also checks the host-side argument validation of eecmg_plan, which runs
+before any CUDA call (so it is testable on a machine without a GPU).
+"""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "eecmg.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(eecmg_[A-Za-z0-9_]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2311_03010_gb300 import build_lib, eecmg
+
+    build_lib.build()
+    return eecmg
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 20
+    so = ctypes.CDLL(lib.LIB_PATH)
+    missing = [n for n in names if not hasattr(so, n)]
+    assert not missing, missing
+    assert set(names) == set(lib._SIGS), set(names) ^ set(lib._SIGS)
+
+
+def test_version_and_defaults(lib):
+    assert "sm_103a" in lib.eecmg_version()
+    o = lib.eecmg_default_options()
+    assert (o.smoother, o.coarse_op, o.storage, o.stop) == (0, 0, 0, 0)
+    assert (o.c, o.delta, o.diffusion_steps, o.s_scale) == (1.1, 0.0, 1, 1.0)
+    assert o.conv_tol == 1e-5 and o.prolong == 0 and o.use_graph == 1
+
+
+@pytest.mark.parametrize("args,status", [
+    (dict(width=0), 1), (dict(height=-1), 1), (dict(levels=0), 1),
+    (dict(psf=np.ones((2, 3))), 1), (dict(psf=np.ones((27, 27))), 1),
+    (dict(psf=-np.ones((3, 3))), 1), (dict(psf=np.full((3, 3), np.nan)), 1),
+    (dict(alpha=0.3), 1), (dict(alpha=-0.1), 1), (dict(k=0.0), 1),
+    (dict(iters=[1, -1, 2]), 1),
+    (dict(psf=np.tri(5)), 2),            # MR-II needs a centrosymmetric PSF
+    (dict(storage="bf16"), 2),
+])
+def test_plan_validation_without_gpu(lib, args, status):
+    kw = dict(width=64, height=64, levels=3, psf=np.ones((3, 3)) / 9, alpha=0.2, k=10.0)
+    kw.update(args)
+    opts = {}
+    if "storage" in kw:
+        opts["storage"] = kw.pop("storage")
+    with pytest.raises(lib.EecmgError) as ei:
+        lib.eecmg_plan(kw["width"], kw["height"], kw["levels"], kw["psf"], kw["alpha"], kw["k"],
+                       kw.get("iters"), **opts)
+    assert ei.value.status == status
+    assert lib.eecmg_last_error()
+
+
+def test_null_handles_rejected(lib):
+    for fn, args in [(lib.eecmg_plan_info, (None,)), (lib.eecmg_restore, (None, 1, 1)),
+                     (lib.eecmg_smooth, (None, 0, 1, 2))]:
+        with pytest.raises(lib.EecmgError) as ei:
+            fn(*args)
+        assert ei.value.status == 1

@@ -1,0 +1,208 @@
+"""GPU parity of the level smoothers and of the whole cascade (C ABI) vs the FP64 oracle.
+
+Tolerances: the FP32 path against the FP64 oracle, at the same iteration
+schedule, must give rel-L2 <= 1e-4 and |delta PSNR| <= 0.01 dB (the
+tolerance the specification states for the FP32 path), and the same number
+of iterations on every level.  Single-level solves on moderately
+conditioned operators are held to rel-L2 <= 1e-5.
+"""
+import numpy as np
+import pytest
+
+from gpu_helpers import dev, host, oracle_threads, rel_l2, require_gpu
+
+pytestmark = pytest.mark.gpu
+
+FP32_REL = 1e-4
+FP32_DPSNR = 0.01
+
+
+@pytest.fixture(scope="module")
+def gpu():
+    return require_gpu()
+
+
+@pytest.mark.parametrize("smoother", ["mr2", "cgls"])
+@pytest.mark.parametrize("psfname", ["gauss", "motion"])
+@pytest.mark.parametrize("shape", [(33, 65), (128, 128), (1, 1), (2, 3)])
+def test_level_solve(gpu, orc, smoother, psfname, shape):
+    torch, E = gpu
+    from paper_2311_03010_gb300 import synth
+
+    psf = synth.gaussian_psf(1.5, 4) if psfname == "gauss" else synth.motion_psf(9, 30.0)
+    h, w = shape
+    rng = np.random.default_rng(60)
+    u_true = synth.synthetic_image(h, w, 61) if h * w > 16 else rng.uniform(0, 255, shape)
+    g = (orc.apply_H(psf, u_true) + rng.normal(0, 1.0, shape)).astype(np.float32)
+    u0 = rng.uniform(0, 255, shape).astype(np.float32)
+    plan = E.Plan(w, h, 1, psf, smoother=smoother)
+    for m in (1, 2, 5, 12):
+        ud = dev(torch, u0)
+        E.eecmg_level_solve(plan.handle, 0, dev(torch, g), ud, m)
+        it, res = plan.stats()
+        ref, k, rres = getattr(orc, smoother)(psf, g.astype(np.float64), u0.astype(np.float64), m,
+                                              conv_tol=orc.CONV_TOL)
+        assert it[0] == k, (m, it, k)
+        assert rel_l2(host(ud), ref) <= 1e-5, (m, rel_l2(host(ud), ref))
+        assert res[0] == pytest.approx(rres, rel=1e-3, abs=1e-6)
+    plan.close()
+
+
+def _cascade_case(name):
+    from paper_2311_03010_gb300 import synth
+
+    if name == "cfg1":
+        return synth.make_problem(64, 64, 1000, synth.gaussian_psf(1.5, 4), 0.01, texture=False), 3
+    if name == "cfg2_1pct":
+        return synth.make_problem(512, 512, 2000, synth.gaussian_psf(2.5, 7), 0.01, noise_seed=2001), 5
+    if name == "cfg2_5pct":
+        return synth.make_problem(512, 512, 2000, synth.gaussian_psf(2.5, 7), 0.05, noise_seed=2002), 5
+    if name == "rect_motion":
+        return synth.make_problem(45, 70, 77, synth.motion_psf(7, 30.0), 0.02), 4
+    if name == "odd_gauss":
+        return synth.make_problem(97, 131, 78, synth.gaussian_psf(2.0, 6), 0.02), 4
+    raise KeyError(name)
+
+
+def check_cascade(torch, E, orc, p, L, **opts):
+    h, w = p.g.shape
+    plan = E.Plan(w, h, L, p.psf, **opts)
+    gd = dev(torch, p.g)
+    ud = torch.empty_like(gd)
+    plan.restore(gd, ud)
+    it, res = plan.stats()
+    u = host(ud)
+    orc.set_threads(oracle_threads())
+    okw = {k: v for k, v in opts.items() if k in ("smoother", "coarse_op", "prolong")}
+    ref, rit, rres = orc.cascade(p.g.astype(np.float64), L, p.psf, **okw)
+    orc.set_threads(1)
+    err = rel_l2(u, ref)
+    dpsnr = abs(orc.psnr(p.u, u) - orc.psnr(p.u, ref))
+    plan.close()
+    return it, rit, err, dpsnr, u
+
+
+@pytest.mark.parametrize("name", ["cfg1", "cfg2_1pct", "cfg2_5pct", "rect_motion", "odd_gauss"])
+@pytest.mark.parametrize("smoother", ["mr2", "cgls"])
+def test_cascade_matches_oracle(gpu, orc, name, smoother):
+    torch, E = gpu
+    p, L = _cascade_case(name)
+    it, rit, err, dpsnr, _ = check_cascade(torch, E, orc, p, L, smoother=smoother)
+    assert it == rit
+    assert err <= FP32_REL, err
+    assert dpsnr <= FP32_DPSNR, dpsnr
+
+
+@pytest.mark.parametrize("prolong", ["iecmg_p", "iecmg_l"])
+@pytest.mark.parametrize("coarse_op", ["rms", "renorm"])
+def test_algorithm1_and_renorm_match_oracle(gpu, orc, prolong, coarse_op):
+    torch, E = gpu
+    p, L = _cascade_case("odd_gauss")
+    it, rit, err, dpsnr, _ = check_cascade(torch, E, orc, p, L, smoother="mr2", prolong=prolong,
+                                           coarse_op=coarse_op)
+    assert it == rit and err <= FP32_REL and dpsnr <= FP32_DPSNR
+    it, rit, err, dpsnr, _ = check_cascade(torch, E, orc, p, L, smoother="cgls",
+                                           coarse_op=coarse_op)
+    assert it == rit and err <= FP32_REL and dpsnr <= FP32_DPSNR
+
+
+def test_delta_psf_returns_data(gpu):
+    torch, E = gpu
+    rng = np.random.default_rng(62)
+    for (h, w, L) in [(64, 64, 3), (37, 50, 4), (1, 1, 1), (2, 3, 3)]:
+        g = rng.uniform(0, 255, (h, w)).astype(np.float32)
+        psf = np.zeros((3, 3))
+        psf[1, 1] = 1.0
+        for smo in ("mr2", "cgls"):
+            plan = E.Plan(w, h, L, psf, smoother=smo)
+            gd = dev(torch, g)
+            ud = torch.empty_like(gd)
+            plan.restore(gd, ud)
+            assert np.abs(host(ud) - g).max() <= 1e-4
+            plan.close()
+
+
+def test_graph_eager_deterministic(gpu):
+    """Graph replay, eager enqueue and repeated runs are bitwise identical."""
+    torch, E = gpu
+    p, L = _cascade_case("odd_gauss")
+    h, w = p.g.shape
+    gd = dev(torch, p.g)
+    outs = []
+    for use_graph in (1, 0):
+        plan = E.Plan(w, h, L, p.psf, use_graph=use_graph)
+        for _ in range(2):
+            ud = torch.empty_like(gd)
+            plan.restore(gd, ud)
+            outs.append(host(ud))
+        plan.close()
+    for o in outs[1:]:
+        assert np.array_equal(o, outs[0])
+
+
+def test_host_entry_point_equals_device(gpu):
+    torch, E = gpu
+    p, L = _cascade_case("cfg1")
+    h, w = p.g.shape
+    plan = E.Plan(w, h, L, p.psf)
+    gd = dev(torch, p.g)
+    ud = torch.empty_like(gd)
+    plan.restore(gd, ud)
+    u_host = np.empty((h, w), np.float32)
+    E.eecmg_restore_host(plan.handle, np.ascontiguousarray(p.g), u_host, 0)
+    assert np.array_equal(u_host, host(ud).astype(np.float32))
+    plan.close()
+
+
+def test_batched_equals_single(gpu):
+    torch, E = gpu
+    cases = [_cascade_case(n) for n in ("cfg1", "rect_motion", "odd_gauss")]
+    plans, gs, us, singles = [], [], [], []
+    for (p, L) in cases:
+        h, w = p.g.shape
+        pl = E.Plan(w, h, L, p.psf)
+        gd = dev(torch, p.g)
+        ud = torch.empty_like(gd)
+        pl.restore(gd, ud)
+        singles.append(host(ud))
+        plans.append(pl)
+        gs.append(gd)
+        us.append(torch.empty_like(gd))
+    E.eecmg_restore_batched([pl.handle for pl in plans], gs, us)
+    for s, u in zip(singles, us):
+        assert np.array_equal(s, host(u))
+    for pl in plans:
+        pl.close()
+
+
+def test_invalid_arguments_rejected(gpu):
+    torch, E = gpu
+    from paper_2311_03010_gb300 import synth
+
+    with pytest.raises(E.EecmgError) as ei:
+        E.Plan(64, 64, 3, np.tri(5) / np.tri(5).sum())
+    assert ei.value.status == 2  # MR-II with a non-centrosymmetric PSF
+    plan = E.Plan(64, 64, 3, synth.gaussian_psf(1.0, 2))
+    with pytest.raises(E.EecmgError):
+        E.eecmg_apply_H(plan.handle, 5, 0, 0, 0)
+    with pytest.raises(E.EecmgError):
+        E.eecmg_restore(plan.handle, None, None)
+    plan.close()
+
+
+@pytest.mark.parametrize("size", [2048, 4096])
+@pytest.mark.parametrize("psfname", ["gauss3", "motion15"])
+def test_large_images_match_oracle(gpu, orc, size, psfname):
+    """Precision-form sizes (2048^2, 4096^2), L = 5, FP32 path vs the full FP64 oracle run."""
+    torch, E = gpu
+    from paper_2311_03010_gb300 import synth
+
+    if size == 4096 and psfname == "motion15":
+        pytest.skip("one 4096^2 oracle run (Gaussian) covers the size; motion is covered at 2048^2")
+    psf = synth.gaussian_psf(3.0, 10) if psfname == "gauss3" else synth.motion_psf(15, 30.0)
+    seed = 3000 if size == 2048 else 3001
+    p = synth.make_problem(size, size, seed, psf, 0.01)
+    it, rit, err, dpsnr, _ = check_cascade(torch, E, orc, p, 5)
+    assert it == rit
+    assert err <= FP32_REL, err
+    assert dpsnr <= FP32_DPSNR, dpsnr
