@@ -1,0 +1,343 @@
+"""Throughput benchmark of GB300 EECMG restoration (one JSON line on rank 0).
+
+Default workload (512x512 precision/parity case): one synthetic 512 x 512
+image (shapes + gradient + texture band), Gaussian PSF sigma = 2.5 on 15 x
+15, two noise draws (1 % and 5 %), 5 levels with the economy schedule,
+MR-II, FP32.  One step restores both degraded images.  Metric: Mpixel/s of
+restored fine-grid pixels.
+
+Timing: W untimed warm-up steps, then K steps, each bracketed by CUDA
+events on the launching stream; between steps a 256 MiB buffer is written
+to flush the 129 MB L2 (outside the events).  The timed region is bracketed
+by a barrier and torch.cuda.synchronize().  With torchrun (N > 1) every rank
+restores its own batch (replicas; the method has no cross-image exchange)
+and the max time over ranks is used.
+
+Extra objects: ``e2e`` (same metric through eecmg_restore_host with pinned
+host buffers, copies inside the timed region), ``roofline`` (dominant kernel
+class: algorithmic bytes / event-timed duration from a profiled eager replay
+of the same steps, vs the measured HBM copy peak), ``cpu_baseline`` (the
+FP64 CPU oracle on a bounded sample of the workload), ``clocks`` and
+``gpu_launches``.
+``--impl reference`` times the CPU oracle itself on the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    # name: (h, w, levels, psf spec, noise levels, seed, noise seeds)
+    "512x512-gauss2.5-L5": (512, 512, 5, ("gauss", 2.5, 7), (0.01, 0.05), 2000, (2001, 2002)),
+    "64x64-gauss1.5-L3": (64, 64, 3, ("gauss", 1.5, 4), (0.01,), 1000, (1001,)),
+    "2048x2048-gauss3-L5": (2048, 2048, 5, ("gauss", 3.0, 10), (0.01,), 3000, (3001,)),
+    "4096x4096-gauss3-L5": (4096, 4096, 5, ("gauss", 3.0, 10), (0.01,), 3001, (3002,)),
+    "2048x2048-motion15-L5": (2048, 2048, 5, ("motion", 15, 30.0), (0.01,), 3000, (3001,)),
+}
+DEFAULT_WORKLOAD = "512x512-gauss2.5-L5"
+
+
+def make_inputs(name):
+    from paper_2311_03010_gb300 import synth
+
+    h, w, L, spec, vs, seed, nseeds = WORKLOADS[name]
+    psf = synth.psf_from_spec(spec)
+    u = synth.synthetic_image(h, w, seed, texture=(h * w > 4096))
+    probs = []
+    for v, ns in zip(vs, nseeds):
+        g, delta = synth.degrade(u, psf, v, ns)
+        probs.append((g, delta))
+    return u, psf, L, probs
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index=0):
+        self.idx = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def cpu_baseline(name, max_seconds=12.0):
+    """The FP64 oracle on a bounded sample: whole images of the workload, repeated."""
+    import oracle
+
+    u, psf, L, probs = make_inputs(name)
+    threads = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    oracle.set_threads(threads)
+    px = 0
+    t0 = time.perf_counter()
+    n = 0
+    while True:
+        g, _ = probs[n % len(probs)]
+        oracle.cascade(g.astype(np.float64), L, psf)
+        px += g.size
+        n += 1
+        if time.perf_counter() - t0 > max_seconds or n >= 64:
+            break
+    dt = time.perf_counter() - t0
+    oracle.set_threads(1)
+    return {"value": px / dt / 1e6, "unit": "Mpixel/s", "cores": threads, "kind": "oracle",
+            "sample": f"{n} whole restorations of the {name} images (FP64 C oracle, OpenMP)",
+            "seconds": dt}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    name = args.workload
+    u, psf, L, probs = make_inputs(name)
+    import oracle
+
+    threads = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    oracle.set_threads(threads)
+    step = lambda: [oracle.cascade(g.astype(np.float64), L, psf) for (g, _) in probs]
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = time.perf_counter() - t0
+    px = sum(g.size for (g, _) in probs) * args.steps
+    val = px / dt / 1e6
+    print(json.dumps({
+        "impl": "reference", "metric": "Mpixel/s restored (EECMG, oracle-matched)", "value": val,
+        "unit": "Mpixel/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": name, "images_per_step": len(probs)},
+        "cpu_baseline": {"value": val, "unit": "Mpixel/s", "cores": threads, "kind": "oracle",
+                         "sample": f"{args.steps} steps of {len(probs)} whole restorations"},
+        "e2e": {"value": val, "unit": "Mpixel/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
+    ap.add_argument("--smoother", default="mr2", choices=["mr2", "cgls"])
+    ap.add_argument("--precise-conv", type=int, default=1)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+
+    from paper_2311_03010_gb300 import build_lib, eecmg
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0 or not os.path.exists(build_lib.LIB):
+        build_lib.build()
+    if world > 1:
+        dist.barrier()
+    eecmg.load()
+
+    name = args.workload
+    u_clean, psf, L, probs = make_inputs(name)
+    h, w = probs[0][0].shape
+    stream = torch.cuda.current_stream()
+    plans = [eecmg.Plan(w, h, L, psf, smoother=args.smoother, precise_conv=args.precise_conv)
+             for _ in probs]
+    gs = [torch.from_numpy(g).cuda() for (g, _) in probs]
+    us = [torch.empty_like(g) for g in gs]
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def step():
+        eecmg.eecmg_restore_batched([p.handle for p in plans], gs, us, stream)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    barrier()
+
+    # timed region
+    clocks = ClockSampler(local)
+    clocks.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    barrier()
+    for i in range(args.steps):
+        flush.zero_()
+        ev[i][0].record(stream)
+        step()
+        ev[i][1].record(stream)
+    barrier()
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for (a, b) in ev]
+    tot_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([tot_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot_ms = float(t.item())
+    px_step = sum(g.numel() for g in gs)
+    value = px_step * args.steps * world / (tot_ms / 1e3) / 1e6
+
+    # parity of this run's output against the oracle (first image, rank 0 only)
+    parity = None
+    if rank == 0 and not args.no_cpu_baseline:
+        import oracle
+
+        oracle.set_threads(len(os.sched_getaffinity(0)))
+        ref, _, _ = oracle.cascade(probs[0][0].astype(np.float64), L, psf, smoother=args.smoother)
+        got = us[0].double().cpu().numpy()
+        parity = {"rel_l2": float(np.linalg.norm(got - ref) / np.linalg.norm(ref)),
+                  "dpsnr_db": float(abs(oracle.psnr(u_clean, got) - oracle.psnr(u_clean, ref))),
+                  "psnr_db": float(oracle.psnr(u_clean, got))}
+        oracle.set_threads(1)
+
+    # end to end through the public host-buffer entry point (pinned memory)
+    gh = [torch.from_numpy(g).pin_memory() for (g, _) in probs]
+    uh = [torch.empty_like(x).pin_memory() for x in gh]
+    for p, a, b in zip(plans, gh, uh):
+        eecmg.eecmg_restore_host(p.handle, a.data_ptr(), b.data_ptr(), stream)
+    barrier()
+    e2e_steps = max(3, args.steps // 2)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        for p, a, b in zip(plans, gh, uh):
+            eecmg.eecmg_restore_host(p.handle, a.data_ptr(), b.data_ptr(), stream)
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    e2e_val = px_step * e2e_steps * world / e2e_s / 1e6
+
+    # profiled eager replay of the same steps: per-kernel-class event times
+    prof_steps = min(args.steps, 20)
+    for p in plans:
+        eecmg.eecmg_plan_profile(p.handle, 1)
+    for _ in range(prof_steps):
+        flush.zero_()
+        step()
+    barrier()
+    classes = {}
+    for p in plans:
+        for k, v in eecmg.eecmg_plan_profile_read(p.handle).items():
+            c = classes.setdefault(k, {"launches": 0, "ms": 0.0, "bytes": 0.0})
+            for f in c:
+                c[f] += v[f]
+        eecmg.eecmg_plan_profile(p.handle, 0)
+    launches_per_step = sum(c["launches"] for c in classes.values()) / prof_steps
+    top = max(classes.items(), key=lambda kv: kv[1]["ms"])
+    peak, peak_kind = peaks()
+    achieved = top[1]["bytes"] / (top[1]["ms"] / 1e3) / 1e9 if top[1]["ms"] > 0 else 0.0
+    prof_total = sum(c["ms"] for c in classes.values())
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(name)
+
+    if rank == 0:
+        out = {
+            "metric": "Mpixel/s restored (EECMG, oracle-matched)",
+            "value": value, "unit": "Mpixel/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": tot_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": name, "images_per_step": len(gs), "levels": L,
+                       "smoother": args.smoother, "precise_conv": args.precise_conv,
+                       "parallelism": f"replicas x{world}", "l2": "flushed between steps"},
+            "e2e": {"value": e2e_val, "unit": "Mpixel/s",
+                    "h2d_bytes_per_step": int(sum(g.numel() * 4 for g in gs)),
+                    "d2h_bytes_per_step": int(sum(g.numel() * 4 for g in gs))},
+            "gpu_launches": int(round(launches_per_step * args.steps)),
+            "roofline": {"bound": "hbm", "kernel": top[0], "achieved": achieved, "peak": peak,
+                         "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                         "peak_kind": peak_kind,
+                         "share_of_step": top[1]["ms"] / prof_total if prof_total else None,
+                         "method": f"event pairs per launch, eager replay of {prof_steps} steps"},
+            "kernel_classes_ms_per_step": {k: v["ms"] / prof_steps for k, v in classes.items()
+                                           if v["launches"]},
+            "clocks": clk,
+            "parity": parity,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(out), flush=True)
+    for p in plans:
+        p.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -80,6 +80,9 @@ enum { EECMG_PROLONG_EECMG = 0, EECMG_PROLONG_IECMG_P = 1, EECMG_PROLONG_IECMG_L
  *   prolong = EECMG       Algorithm 2; IECMG_P / IECMG_L run Algorithm 1
  *                         with quadratic / linear (Eq. 15) prolongation.
  *   use_graph = 1         capture the cascade as a CUDA graph per plan.
+ *   precise_conv = 1      compensated (error-free product + TwoSum) FP32
+ *                         accumulation in the second pass of separable
+ *                         convolutions; 0 = plain FMA accumulation.
  */
 typedef struct {
     int smoother;
@@ -93,6 +96,7 @@ typedef struct {
     double conv_tol;
     int prolong;
     int use_graph;
+    int precise_conv;
 } eecmg_options;
 
 typedef struct eecmg_plan_s *eecmg_plan_t;
@@ -168,6 +172,24 @@ eecmg_status eecmg_restore_batched(const eecmg_plan_t *plans, const float *const
  * last stream.  Either pointer may be NULL.
  */
 eecmg_status eecmg_plan_stats(eecmg_plan_t plan, int *iters_done, double *res_rms);
+
+/*
+ * Per-launch profiling (for measurement, not the paper): with enable = 1 the
+ * plan's restorations run eagerly (no graph) with a CUDA event pair around
+ * every kernel launch on the caller's stream; eecmg_plan_profile_read
+ * synchronises and returns, per kernel class, the launches, the summed
+ * event time (ms) and the summed algorithmic bytes (the reads and writes
+ * each operator needs, counted once).  Enabling or disabling resets the
+ * totals.  *n receives the number of classes; at most max are written.
+ */
+typedef struct {
+    char name[24];
+    long long launches;
+    double ms;
+    double bytes;
+} eecmg_kernel_stat;
+eecmg_status eecmg_plan_profile(eecmg_plan_t plan, int enable);
+eecmg_status eecmg_plan_profile_read(eecmg_plan_t plan, eecmg_kernel_stat *out, int max, int *n);
 
 /* ---- operator-level entry points (one level of a plan) ----------------- */
 

@@ -34,20 +34,28 @@ struct Taps {
 
 // Per-solve device scalars (FP64).  One block per level of a plan.
 struct alignas(64) Scalars {
-    double b1, b2;        // MR-II beta_1, beta_2 of the current direction
-    double alpha;         // step decided but not yet applied
-    double qq, qq_prev;   // <q_k, q_k>, <q_{k-1}, q_{k-1}>
-    double gamma;         // CGLS <s, s>
     double rr;            // last ||r||^2
     double gg;            // ||g||^2
     double lim2;          // stop when ||r||^2 <= lim2
-    double conv_tol2;     // conv_tol^2 (relative to ||g||^2)
-    double disc2;         // (c delta)^2 * N (discrepancy rule), 0 = off
-    double rq;            // last <r, q>
-    int stopped;          // 0 running; 1 stopping rule; 2 breakdown; 3 non-finite
+    int stopped;          // 0 running; 1 stopping rule; 2 breakdown (no further step);
+                          // 3 non-finite; 4 breakdown after deciding a last step
     int iters;            // iterations whose step has been decided
     unsigned int counter; // last-block arrival counter (reset by the last block)
-    int pad;
+    int pad0;
+    // MR-II, Lanczos / Givens form
+    double nrm, nrm_prev; // ||v_k||, ||v_{k-1}|| (w_k = v_k / ||v_k||)
+    double alpha;         // alpha_k = <H w_k, w_k>
+    double cs1, sn1;      // rotation G_{k-1}
+    double cs2, sn2;      // rotation G_{k-2}
+    double phi;           // pending entry of the rotated right-hand side
+    // pending step j: d_j = dw v_j - d1 d_{j-1} - d2 d_{j-2}  (= (w_j - r1 d_{j-1} -
+    // e d_{j-2}) / rho), H d_j = dinv H w_j - d1 H d_{j-1} - d2 H d_{j-2},
+    // u += tau d_j, r -= tau H d_j
+    double dw, d1, d2, dinv, tau;
+    // CGLS
+    double gamma;         // <s, s>
+    double qq;            // <q, q>
+    double cg_alpha, beta;
 };
 
 constexpr int NTHREADS = 256;

@@ -9,11 +9,17 @@
 // other PSFs (motion blur) run over their non-zero taps.  The finished tile
 // is then streamed out row-major (coalesced) through the fused epilogue,
 // whose inner products enter the deterministic grid reduction.
+//
+// PREC selects a compensated horizontal pass: each product's rounding error
+// (from an FMA) and each addition's rounding error (TwoSum) are carried in a
+// second FP32 accumulator, so the output is nearly correctly rounded.  The
+// semi-convergent Krylov levels amplify the rounding of H, and this halves
+// the FP32-vs-FP64 gap of the whole cascade at some ALU cost.
 #include "launch.hpp"
 
 namespace eecmg {
 
-template <int R, bool SEP>
+template <int R, bool SEP, bool PREC>
 __global__ void __launch_bounds__(NTHREADS) k_conv(ConvArgs a) {
     constexpr int TH = CONV_TH, TW = CONV_TW;
     constexpr int IH = TH + 2 * R, IW = TW + 2 * R;
@@ -38,7 +44,6 @@ __global__ void __launch_bounds__(NTHREADS) k_conv(ConvArgs a) {
     const int h = a.h, w = a.w;
 
     if (!a.zero_input) {
-        // taps
         if (SEP) {
             for (int d = tid; d < 2 * R + 1; d += NTHREADS) {
                 s_cy[d] = a.taps->cy[d];
@@ -94,8 +99,23 @@ __global__ void __launch_bounds__(NTHREADS) k_conv(ConvArgs a) {
 #pragma unroll
                 for (int i = 0; i < 8; ++i) {
                     float acc = 0.f;
+                    if (PREC) {
+                        float lo = 0.f;
 #pragma unroll
-                    for (int d = 0; d < 2 * R + 1; ++d) acc = fmaf(cxr[d], v[i + d], acc);
+                        for (int d = 0; d < 2 * R + 1; ++d) {
+                            const float p = __fmul_rn(cxr[d], v[i + d]);
+                            const float pe = fmaf(cxr[d], v[i + d], -p);  // exact product error
+                            const float s = __fadd_rn(acc, p);
+                            const float bp = __fsub_rn(s, acc);
+                            const float se = __fadd_rn(__fsub_rn(acc, __fsub_rn(s, bp)), __fsub_rn(p, bp));
+                            acc = s;
+                            lo = __fadd_rn(lo, __fadd_rn(pe, se));
+                        }
+                        acc = __fadd_rn(acc, lo);
+                    } else {
+#pragma unroll
+                        for (int d = 0; d < 2 * R + 1; ++d) acc = fmaf(cxr[d], v[i + d], acc);
+                    }
                     s_out[r * PO + cg * 8 + i] = acc;
                 }
             }
@@ -119,6 +139,8 @@ __global__ void __launch_bounds__(NTHREADS) k_conv(ConvArgs a) {
     }
 
     // epilogue: row-major, coalesced
+    float scale = 1.f;
+    if (mode == CM_MR_A) scale = (float)(1.0 / a.sc->nrm);
     float acc0 = 0.f, acc1 = 0.f;
     float* __restrict__ y = a.y;
 #pragma unroll
@@ -137,18 +159,19 @@ __global__ void __launch_bounds__(NTHREADS) k_conv(ConvArgs a) {
                         const float gv = __ldg(a.e0 + idx);
                         const float rv = gv - z;
                         y[idx] = rv;
+                        if (a.y2) a.y2[idx] = rv;
                         acc0 = fmaf(rv, rv, acc0);
                         acc1 = fmaf(gv, gv, acc1);
                     } break;
-                    case CM_MR_Q1: {
+                    case CM_MR_V1: {  // v_1 = H r_0, with <v, v>, <v, r_0>
                         y[idx] = z;
-                        acc0 = fmaf(__ldg(a.e0 + idx), z, acc0);
-                        acc1 = fmaf(z, z, acc1);
+                        acc0 = fmaf(z, z, acc0);
+                        acc1 = fmaf(z, s_in[(r + R) * IW + c + R], acc1);
                     } break;
-                    case CM_MR_A: {
-                        y[idx] = z;
-                        acc0 = fmaf(z, s_in[(r + R) * IW + c + R], acc0);
-                        if (a.has_e1) acc1 = fmaf(z, __ldg(a.e1 + idx), acc1);
+                    case CM_MR_A: {   // H w_k = H v_k / ||v_k||, with <H w_k, v_k>
+                        const float hz = z * scale;
+                        y[idx] = hz;
+                        acc0 = fmaf(hz, s_in[(r + R) * IW + c + R], acc0);
                     } break;
                     case CM_CG_S0: {
                         y[idx] = z;
@@ -166,7 +189,7 @@ __global__ void __launch_bounds__(NTHREADS) k_conv(ConvArgs a) {
             }
         }
     }
-    if (mode == CM_STORE || mode == CM_MR_P1) return;
+    if (mode == CM_STORE) return;
 
     const unsigned int nblocks = gridDim.x * gridDim.y;
     const unsigned int bid = blockIdx.y * gridDim.x + blockIdx.x;
@@ -183,32 +206,29 @@ __global__ void __launch_bounds__(NTHREADS) k_conv(ConvArgs a) {
             sc->gg = gg;
             const double l1 = a.conv_tol2 * gg;
             sc->lim2 = l1 > a.disc2 ? l1 : a.disc2;
-            sc->alpha = 0.0;
-            sc->b1 = sc->b2 = 0.0;
-            sc->qq = sc->qq_prev = 0.0;
-            sc->gamma = 0.0;
             sc->iters = 0;
-            sc->rq = 0.0;
             if (!(rr < 1.0e300)) sc->stopped = 3;
             else sc->stopped = (rr <= sc->lim2) ? 1 : 0;
         } break;
-        case CM_MR_Q1: {
-            const double qq = tot[1];
-            sc->rq = tot[0];
-            if (!(qq < 1.0e300)) {
+        case CM_MR_V1: {
+            const double vv = tot[0];
+            if (!(vv < 1.0e300)) {
                 sc->stopped = 3;
-            } else if (!(qq > 0.0)) {
-                sc->stopped = 2;
+            } else if (!(vv > 0.0)) {
+                sc->stopped = 2;  // H r_0 = 0: no step
             } else {
-                sc->alpha = tot[0] / qq;
-                sc->qq = qq;
-                sc->qq_prev = 0.0;
-                sc->iters = 1;
+                const double nrm = sqrt(vv);
+                sc->nrm = nrm;
+                sc->nrm_prev = 0.0;
+                sc->phi = tot[1] / nrm;  // <w_1, r_0>
+                sc->cs1 = 1.0;
+                sc->sn1 = 0.0;
+                sc->cs2 = 1.0;
+                sc->sn2 = 0.0;
             }
         } break;
         case CM_MR_A: {
-            sc->b1 = tot[0] / sc->qq;
-            sc->b2 = a.has_e1 ? tot[1] / sc->qq_prev : 0.0;
+            sc->alpha = tot[0] / sc->nrm;
         } break;
         case CM_CG_S0: {
             const double gm = tot[0];
@@ -224,13 +244,13 @@ __global__ void __launch_bounds__(NTHREADS) k_conv(ConvArgs a) {
                 sc->stopped = 2;
             } else {
                 sc->qq = qq;
-                sc->alpha = sc->gamma / qq;
+                sc->cg_alpha = sc->gamma / qq;
                 sc->iters += 1;
             }
         } break;
         case CM_CG_S: {
             const double gn = tot[0];
-            sc->b1 = gn / sc->gamma;
+            sc->beta = gn / sc->gamma;
             sc->gamma = gn;
             if (!(gn < 1.0e300)) sc->stopped = 3;
             else if (!(gn > 0.0)) sc->stopped = 2;
@@ -241,31 +261,33 @@ __global__ void __launch_bounds__(NTHREADS) k_conv(ConvArgs a) {
 }
 
 template <int R>
-static cudaError_t launch_conv_r(const ConvArgs& a, int sep, cudaStream_t s) {
+static cudaError_t launch_conv_r(const ConvArgs& a, int sep, int prec, cudaStream_t s) {
     dim3 grid((a.w + CONV_TW - 1) / CONV_TW, (a.h + CONV_TH - 1) / CONV_TH);
-    if (sep)
-        k_conv<R, true><<<grid, NTHREADS, 0, s>>>(a);
+    if (sep && prec)
+        k_conv<R, true, true><<<grid, NTHREADS, 0, s>>>(a);
+    else if (sep)
+        k_conv<R, true, false><<<grid, NTHREADS, 0, s>>>(a);
     else
-        k_conv<R, false><<<grid, NTHREADS, 0, s>>>(a);
+        k_conv<R, false, false><<<grid, NTHREADS, 0, s>>>(a);
     return cudaGetLastError();
 }
 
-cudaError_t launch_conv(const ConvArgs& a, int rt, int sep, cudaStream_t s) {
+cudaError_t launch_conv(const ConvArgs& a, int rt, int sep, int prec, cudaStream_t s) {
     if (a.h <= 0 || a.w <= 0) return cudaSuccess;
     switch (rt) {
-        case 0: return launch_conv_r<0>(a, sep, s);
-        case 1: return launch_conv_r<1>(a, sep, s);
-        case 2: return launch_conv_r<2>(a, sep, s);
-        case 3: return launch_conv_r<3>(a, sep, s);
-        case 4: return launch_conv_r<4>(a, sep, s);
-        case 5: return launch_conv_r<5>(a, sep, s);
-        case 6: return launch_conv_r<6>(a, sep, s);
-        case 7: return launch_conv_r<7>(a, sep, s);
-        case 8: return launch_conv_r<8>(a, sep, s);
-        case 9: return launch_conv_r<9>(a, sep, s);
-        case 10: return launch_conv_r<10>(a, sep, s);
-        case 11: return launch_conv_r<11>(a, sep, s);
-        case 12: return launch_conv_r<12>(a, sep, s);
+        case 0: return launch_conv_r<0>(a, sep, prec, s);
+        case 1: return launch_conv_r<1>(a, sep, prec, s);
+        case 2: return launch_conv_r<2>(a, sep, prec, s);
+        case 3: return launch_conv_r<3>(a, sep, prec, s);
+        case 4: return launch_conv_r<4>(a, sep, prec, s);
+        case 5: return launch_conv_r<5>(a, sep, prec, s);
+        case 6: return launch_conv_r<6>(a, sep, prec, s);
+        case 7: return launch_conv_r<7>(a, sep, prec, s);
+        case 8: return launch_conv_r<8>(a, sep, prec, s);
+        case 9: return launch_conv_r<9>(a, sep, prec, s);
+        case 10: return launch_conv_r<10>(a, sep, prec, s);
+        case 11: return launch_conv_r<11>(a, sep, prec, s);
+        case 12: return launch_conv_r<12>(a, sep, prec, s);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -1,85 +1,167 @@
 // krylov.cu -- elementwise phases of the level smoothers C_l^m (Section 2):
 // MR-II (reading of "MR") and CGLS (reading of "CG").
 //
+// MR-II is run in its Lanczos / Givens form: the Lanczos process on the
+// symmetric H_l started from H r_0 builds an orthonormal basis w_1..w_k of
+// K_k(H, H r_0) with H W_k = W_{k+1} T_k (T_k tridiagonal), and the iterate
+// u_k = u_0 + W_k y_k minimises ||r_0 - W_{k+1} T_k y|| + const, a small
+// least-squares problem with right-hand side c_j = <w_j, r_0> solved by
+// progressive Givens rotations (as in MINRES).  In exact arithmetic these are
+// the iterates of the three-term MR-II recurrence; in FP32 this form keeps
+// the iterates far closer to the FP64 ones.  The residual r_k = r_0 - H(u_k -
+// u_0) is carried through H d_j (from the stored H w_j) for the stopping
+// rules, exactly as the recurrence residual.
+//
 // Vectors are FP32; every inner product goes through the deterministic FP64
-// grid reduction, and the scalars (alpha, beta, norms, stop flags) are
-// decided on the device by the last block, so a whole level runs without a
-// host round trip.  Each thread handles 8 elements, strided by the block
-// size so that every load and store is coalesced.
+// grid reduction, and all scalars (Lanczos coefficients, rotations, stop
+// flags) are decided on the device by the last block.  Each thread handles
+// 8 elements strided by the block size, so loads and stores are coalesced.
+#include <math.h>
+
 #include "launch.hpp"
 
 namespace eecmg {
 
-// MR-II, phase B of iteration k >= 2 (the convolution z = H q_{k-1} and the
-// betas came from the previous launch):
-//   u += alpha_{k-1} p_{k-1},  r -= alpha_{k-1} q_{k-1}          (step k-1)
-//   q_k = z - b1 q_{k-1} - b2 q_{k-2},  p_k = q_{k-1} - b1 p_{k-1} - b2 p_{k-2}
-// q_k overwrites q_{k-2} (q2) and p_k overwrites p_{k-2} (p2) in place.
-// The last block applies the stopping rules to ||r_{k-1}|| (checked before
-// iteration k, as in the oracle), then the breakdown test on <q_k, q_k>,
-// and decides alpha_k = <r_{k-1}, q_k> / <q_k, q_k>.
+// Applies step j: d_j, H d_j, u += tau d_j, r -= tau H d_j; returns r_i.
+__device__ __forceinline__ float mr_apply_step(const MrVecs& V, int j, size_t i, float dw,
+                                               float d1, float d2, float dinv, float tau) {
+    const int sj = j & 1, sj1 = sj ^ 1;  // d_{j-1} lives in slot (j-1)&1, d_{j-2} in slot j&1
+    float dj = dw * V.v[sj][i];
+    float hj = dinv * V.aw[sj][i];
+    if (j >= 2) {
+        dj = fmaf(-d1, V.d[sj1][i], dj);
+        hj = fmaf(-d1, V.hd[sj1][i], hj);
+    }
+    if (j >= 3) {
+        dj = fmaf(-d2, V.d[sj][i], dj);
+        hj = fmaf(-d2, V.hd[sj][i], hj);
+    }
+    V.d[sj][i] = dj;
+    V.hd[sj][i] = hj;
+    V.u[i] = fmaf(tau, dj, V.u[i]);
+    const float rv = fmaf(-tau, hj, V.r[i]);
+    V.r[i] = rv;
+    return rv;
+}
+
+// Phase B of iteration k (see launch.hpp).
 __global__ void __launch_bounds__(NTHREADS)
-    k_mr_b(const float* __restrict__ z, const float* __restrict__ q1, float* q2,
-           const float* __restrict__ p1, float* p2, float* __restrict__ u, float* __restrict__ r,
-           size_t n, int has2, Scalars* sc, double* partials) {
+    k_mr_b(MrVecs V, int k, size_t n, Scalars* sc, double* partials) {
     if (*(volatile int*)&sc->stopped) return;
-    const float a = (float)sc->alpha;
-    const float b1 = (float)sc->b1;
-    const float b2 = has2 ? (float)sc->b2 : 0.f;
-    float arq = 0.f, aqq = 0.f, arr = 0.f;
+    const bool step = k >= 2;  // step k-1 is pending
+    const float dw = (float)sc->dw, d1 = (float)sc->d1, d2 = (float)sc->d2;
+    const float dinv = (float)sc->dinv, tau = (float)sc->tau;
+    const float ca = (float)(sc->alpha / sc->nrm);                  // alpha_k / ||v_k||
+    const float cb = step ? (float)(sc->nrm / sc->nrm_prev) : 0.f;  // ||v_k|| / ||v_{k-1}||
+    const int sk = k & 1, sk1 = sk ^ 1;
+    float arr = 0.f, avv = 0.f, avr = 0.f;
     const size_t base = (size_t)blockIdx.x * EW_PER_BLOCK + threadIdx.x;
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-        const size_t i = base + (size_t)j * NTHREADS;
+    for (int jj = 0; jj < 8; ++jj) {
+        const size_t i = base + (size_t)jj * NTHREADS;
         if (i < n) {
-            const float q1v = q1[i], p1v = p1[i];
-            const float rv = fmaf(-a, q1v, r[i]);
-            u[i] = fmaf(a, p1v, u[i]);
-            r[i] = rv;
-            float qk = fmaf(-b1, q1v, z[i]);
-            float pk = fmaf(-b1, p1v, q1v);
-            if (has2) {
-                qk = fmaf(-b2, q2[i], qk);
-                pk = fmaf(-b2, p2[i], pk);
+            if (step) {
+                const float rv = mr_apply_step(V, k - 1, i, dw, d1, d2, dinv, tau);
+                arr = fmaf(rv, rv, arr);
             }
-            q2[i] = qk;
-            p2[i] = pk;
-            arq = fmaf(rv, qk, arq);
-            aqq = fmaf(qk, qk, aqq);
-            arr = fmaf(rv, rv, arr);
+            // v_{k+1} = H w_k - alpha_k w_k - ||v_k|| w_{k-1}
+            float vn = fmaf(-ca, V.v[sk][i], V.aw[sk][i]);
+            if (step) vn = fmaf(-cb, V.v[sk1][i], vn);
+            V.v[sk1][i] = vn;
+            avv = fmaf(vn, vn, avv);
+            avr = fmaf(vn, V.r0[i], avr);
         }
     }
-    double v[3] = {(double)arq, (double)aqq, (double)arr};
-    if (!block_partials_arrive<3>(v, partials, &sc->counter, gridDim.x, blockIdx.x)) return;
+    double vals[3] = {(double)arr, (double)avv, (double)avr};
+    if (!block_partials_arrive<3>(vals, partials, &sc->counter, gridDim.x, blockIdx.x)) return;
     double tot[3];
     grid_total<3>(partials, gridDim.x, &sc->counter, tot);
     if (threadIdx.x != 0) return;
-    const double rr = tot[2], qq = tot[1];
-    sc->rr = rr;
-    if (!(rr < 1.0e300)) {
-        sc->stopped = 3;
-    } else if (rr <= sc->lim2) {
-        sc->stopped = 1;
-    } else if (!(qq < 1.0e300)) {
-        sc->stopped = 3;
-    } else if (!(qq > 0.0)) {
-        sc->stopped = 2;
-    } else {
-        sc->rq = tot[0];
-        sc->alpha = tot[0] / qq;
-        sc->qq_prev = sc->qq;
-        sc->qq = qq;
-        sc->iters += 1;
+    if (step) {
+        const double rr = tot[0];
+        sc->rr = rr;
+        if (!(rr < 1.0e300)) {
+            sc->stopped = 3;
+            return;
+        }
+        if (rr <= sc->lim2) {  // stopping rule on ||r_{k-1}||, before iteration k
+            sc->stopped = 1;
+            return;
+        }
     }
+    const double vv = tot[1];
+    if (!(vv < 1.0e300)) {
+        sc->stopped = 3;
+        return;
+    }
+    const double nrm_new = sqrt(vv);
+    const double c_new = vv > 0.0 ? tot[2] / nrm_new : 0.0;
+    // column k of T: ||v_k|| above the diagonal (0 for k = 1), alpha_k on it,
+    // ||v_{k+1}|| below; apply G_{k-2}, G_{k-1}, then the new rotation G_k
+    const double alpha = sc->alpha;
+    const double cpl = step ? sc->nrm : 0.0;
+    const double e = sc->sn2 * cpl;
+    const double t = sc->cs2 * cpl;
+    const double r1 = sc->cs1 * t + sc->sn1 * alpha;
+    const double a2 = -sc->sn1 * t + sc->cs1 * alpha;
+    const double rho = hypot(a2, nrm_new);
+    if (!(rho > 0.0) || !(rho < 1.0e300)) {
+        sc->stopped = rho > 0.0 ? 3 : 2;
+        return;
+    }
+    const double cs = a2 / rho, sn = nrm_new / rho;
+    const double phi = sc->phi;
+    sc->tau = cs * phi + sn * c_new;
+    sc->phi = -sn * phi + cs * c_new;
+    sc->dinv = 1.0 / rho;
+    sc->dw = 1.0 / (sc->nrm * rho);
+    sc->d1 = r1 / rho;
+    sc->d2 = e / rho;
+    sc->cs2 = sc->cs1;
+    sc->sn2 = sc->sn1;
+    sc->cs1 = cs;
+    sc->sn1 = sn;
+    sc->nrm_prev = sc->nrm;
+    sc->nrm = nrm_new;
+    sc->iters = k;
+    if (!(nrm_new > 0.0)) sc->stopped = 4;  // Krylov space exhausted: step k is the last
 }
 
-// u += alpha p, r -= alpha q, and ||r||^2.  check = 1: apply the stopping
-// rule to the new residual (CGLS, before its next iteration).
+// Applies the step decided last (its index is sc->iters) and reduces ||r||^2.
 __global__ void __launch_bounds__(NTHREADS)
-    k_step(float* __restrict__ u, const float* __restrict__ p, float* __restrict__ r,
-           const float* __restrict__ q, size_t n, int check, Scalars* sc, double* partials) {
+    k_mr_final(MrVecs V, size_t n, Scalars* sc, double* partials) {
+    const int st = *(volatile int*)&sc->stopped;
+    if (st != 0 && st != 4) return;
+    const int j = sc->iters;
+    if (j < 1) return;
+    const float dw = (float)sc->dw, d1 = (float)sc->d1, d2 = (float)sc->d2;
+    const float dinv = (float)sc->dinv, tau = (float)sc->tau;
+    float arr = 0.f;
+    const size_t base = (size_t)blockIdx.x * EW_PER_BLOCK + threadIdx.x;
+#pragma unroll
+    for (int jj = 0; jj < 8; ++jj) {
+        const size_t i = base + (size_t)jj * NTHREADS;
+        if (i < n) {
+            const float rv = mr_apply_step(V, j, i, dw, d1, d2, dinv, tau);
+            arr = fmaf(rv, rv, arr);
+        }
+    }
+    double vals[1] = {(double)arr};
+    if (!block_partials_arrive<1>(vals, partials, &sc->counter, gridDim.x, blockIdx.x)) return;
+    double tot[1];
+    grid_total<1>(partials, gridDim.x, &sc->counter, tot);
+    if (threadIdx.x != 0) return;
+    sc->rr = tot[0];
+    if (!(tot[0] < 1.0e300)) sc->stopped = 3;
+}
+
+// CGLS: u += alpha p, r -= alpha q, ||r||^2, then the stopping rule on the
+// new residual (checked before the next iteration, as in the oracle).
+__global__ void __launch_bounds__(NTHREADS)
+    k_cg_step(float* __restrict__ u, const float* __restrict__ p, float* __restrict__ r,
+              const float* __restrict__ q, size_t n, Scalars* sc, double* partials) {
     if (*(volatile int*)&sc->stopped) return;
-    const float a = (float)sc->alpha;
+    const float a = (float)sc->cg_alpha;
     float arr = 0.f;
     const size_t base = (size_t)blockIdx.x * EW_PER_BLOCK + threadIdx.x;
 #pragma unroll
@@ -99,14 +181,14 @@ __global__ void __launch_bounds__(NTHREADS)
     if (threadIdx.x != 0) return;
     sc->rr = tot[0];
     if (!(tot[0] < 1.0e300)) sc->stopped = 3;
-    else if (check && tot[0] <= sc->lim2) sc->stopped = 1;
+    else if (tot[0] <= sc->lim2) sc->stopped = 1;
 }
 
 // CGLS direction update p = s + beta p (beta decided by the H^T launch).
 __global__ void __launch_bounds__(NTHREADS)
     k_cg_p(float* __restrict__ p, const float* __restrict__ s, size_t n, Scalars* sc) {
     if (*(volatile int*)&sc->stopped) return;
-    const float b = (float)sc->b1;
+    const float b = (float)sc->beta;
     const size_t base = (size_t)blockIdx.x * EW_PER_BLOCK + threadIdx.x;
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
@@ -115,18 +197,24 @@ __global__ void __launch_bounds__(NTHREADS)
     }
 }
 
-cudaError_t launch_mr_b(const float* z, const float* q1, float* q2, const float* p1, float* p2,
-                        float* u, float* r, size_t n, int has2, Scalars* sc, double* partials,
+cudaError_t launch_mr_b(const MrVecs& V, int k, size_t n, Scalars* sc, double* partials,
                         cudaStream_t s) {
     if (n == 0) return cudaSuccess;
-    k_mr_b<<<ew_blocks(n), NTHREADS, 0, s>>>(z, q1, q2, p1, p2, u, r, n, has2, sc, partials);
+    k_mr_b<<<ew_blocks(n), NTHREADS, 0, s>>>(V, k, n, sc, partials);
     return cudaGetLastError();
 }
 
-cudaError_t launch_step(float* u, const float* p, float* r, const float* q, size_t n, int check,
-                        Scalars* sc, double* partials, cudaStream_t s) {
+cudaError_t launch_mr_final(const MrVecs& V, size_t n, Scalars* sc, double* partials,
+                            cudaStream_t s) {
     if (n == 0) return cudaSuccess;
-    k_step<<<ew_blocks(n), NTHREADS, 0, s>>>(u, p, r, q, n, check, sc, partials);
+    k_mr_final<<<ew_blocks(n), NTHREADS, 0, s>>>(V, n, sc, partials);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cg_step(float* u, const float* p, float* r, const float* q, size_t n,
+                           Scalars* sc, double* partials, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    k_cg_step<<<ew_blocks(n), NTHREADS, 0, s>>>(u, p, r, q, n, sc, partials);
     return cudaGetLastError();
 }
 

@@ -10,13 +10,12 @@ namespace eecmg {
 // Epilogues fused into the convolution y = C (*) x.
 enum ConvMode : int {
     CM_STORE = 0,   // y = C (*) x
-    CM_RESID = 1,   // r = g - H u (e0 = g): ||r||^2, ||g||^2 -> stopping limit, stop test
-    CM_MR_Q1 = 2,   // q_1 = H p_1 (e0 = r_0): <r_0, q_1>, <q_1, q_1> -> alpha_1
-    CM_MR_A = 3,    // z = H q_{k-1} (e1 = q_{k-2}): <z, q_{k-1}>, <z, q_{k-2}> -> beta_1, beta_2
+    CM_RESID = 1,   // r = g - H u (e0 = g; y2 = optional copy): ||r||^2, ||g||^2 -> limit, stop test
+    CM_MR_V1 = 2,   // v_1 = H r_0 (x = r_0): <v_1, v_1>, <v_1, r_0> -> ||v_1||, phi_1
+    CM_MR_A = 3,    // H w_k = H v_k / ||v_k|| (x = v_k): <H w_k, w_k> -> alpha_k
     CM_CG_S0 = 4,   // s = H^T r, p = s (y2): <s, s> -> gamma
     CM_CG_Q = 5,    // q = H p: <q, q> -> alpha = gamma / <q, q>
     CM_CG_S = 6,    // s = H^T r: <s, s> -> beta, gamma
-    CM_MR_P1 = 7,   // p_1 = H r_0 (store, skipped once the level has stopped)
 };
 
 struct ConvArgs {
@@ -50,17 +49,31 @@ inline unsigned int ew_blocks(size_t n) {
     return (unsigned int)((n + EW_PER_BLOCK - 1) / EW_PER_BLOCK);
 }
 
-cudaError_t launch_conv(const ConvArgs& a, int rt, int sep, cudaStream_t s);
+cudaError_t launch_conv(const ConvArgs& a, int rt, int sep, int prec, cudaStream_t s);
 
-// MR-II phase B of iteration k: pending update with alpha_{k-1}, new
-// direction (q_k into q2, p_k into p2), <r, q_k>, <q_k, q_k>, ||r||^2.
-cudaError_t launch_mr_b(const float* z, const float* q1, float* q2, const float* p1, float* p2,
-                        float* u, float* r, size_t n, int has2, Scalars* sc, double* partials,
+// MR-II (Lanczos / Givens form), phase B of iteration k: applies the
+// pending step k-1 (d, Hd, u, r), forms v_{k+1} and reduces ||r||^2,
+// <v_{k+1}, v_{k+1}>, <v_{k+1}, r_0>; the last block applies the stopping
+// rules and the Givens rotation of column k.  Buffers are indexed by step
+// parity: v[k & 1] = v_k, aw[k & 1] = H w_k, d/hd[j & 1] = d_j / H d_j.
+struct MrVecs {
+    float* v[2];
+    float* aw[2];
+    float* d[2];
+    float* hd[2];
+    float* u;
+    float* r;
+    const float* r0;
+};
+cudaError_t launch_mr_b(const MrVecs& V, int k, size_t n, Scalars* sc, double* partials,
                         cudaStream_t s);
-// u += alpha p, r -= alpha q, ||r||^2; check = 1 also applies the stopping rule.
-cudaError_t launch_step(float* u, const float* p, float* r, const float* q, size_t n, int check,
-                        Scalars* sc, double* partials, cudaStream_t s);
-// p = s + beta p (CGLS).
+// Applies the pending step (index read on the device) and reduces ||r||^2.
+cudaError_t launch_mr_final(const MrVecs& V, size_t n, Scalars* sc, double* partials,
+                            cudaStream_t s);
+// CGLS: u += alpha p, r -= alpha q, ||r||^2 and the stopping rule.
+cudaError_t launch_cg_step(float* u, const float* p, float* r, const float* q, size_t n,
+                           Scalars* sc, double* partials, cudaStream_t s);
+// CGLS: p = s + beta p.
 cudaError_t launch_cg_p(float* p, const float* sv, size_t n, Scalars* sc, cudaStream_t s);
 
 // Level operators.

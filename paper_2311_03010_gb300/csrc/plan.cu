@@ -142,6 +142,55 @@ size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 }  // namespace
 
+namespace eecmg {
+
+cudaEvent_t prof_event(Profiler& pr) {
+    if (!pr.free_events.empty()) {
+        cudaEvent_t e = pr.free_events.back();
+        pr.free_events.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// Folds the recorded launches into the per-class totals (synchronises).
+cudaError_t prof_flush(Profiler& pr) {
+    for (auto& r : pr.recs) {
+        cudaError_t e = cudaEventSynchronize(r.e1);
+        if (e != cudaSuccess) return e;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, r.e0, r.e1);
+        pr.ms[r.cls] += ms;
+        pr.bytes[r.cls] += r.bytes;
+        pr.launches[r.cls] += 1;
+        pr.free_events.push_back(r.e0);
+        pr.free_events.push_back(r.e1);
+    }
+    pr.recs.clear();
+    return cudaSuccess;
+}
+
+}  // namespace eecmg
+
+// Launch with optional profiling: an event pair around the launch and its
+// algorithmic byte count.
+#define LK(P, s, cls, nbytes, call)                                              \
+    do {                                                                         \
+        if ((P)->prof.on) {                                                      \
+            eecmg::Profiler::Rec rec_{(cls), (double)(nbytes), prof_event((P)->prof), \
+                                      prof_event((P)->prof)};                    \
+            cudaEventRecord(rec_.e0, (s));                                       \
+            CK(call);                                                            \
+            cudaEventRecord(rec_.e1, (s));                                       \
+            (P)->prof.recs.push_back(rec_);                                      \
+            if ((P)->prof.recs.size() > 8192) CK(prof_flush((P)->prof));         \
+        } else {                                                                 \
+            CK(call);                                                            \
+        }                                                                        \
+    } while (0)
+
 // ---------------------------------------------------------------------------
 // cascade enqueue
 // ---------------------------------------------------------------------------
@@ -155,11 +204,14 @@ eecmg_status solve_level_enqueue(eecmg_plan_s* P, int l, const float* g, float* 
     Scalars* sc = P->sc + l;
     const Taps* tH = P->dtaps + 2 * l;
     const Taps* tHT = P->dtaps + 2 * l + 1;
-    const int rt = L.rt, sepH = L.sepH, sepHT = L.sepHT;
+    const int rt = L.rt, sepH = L.sepH, sepHT = L.sepHT, prec = P->opt.precise_conv;
+    const bool mr2 = P->opt.smoother == EECMG_SMOOTHER_MR2;
+    float** V = P->vec;
 
     ConvArgs ra;
     ra.x = u;
-    ra.y = P->r;
+    ra.y = V[8];                      // r
+    ra.y2 = mr2 ? V[9] : nullptr;     // r_0 (kept for <w_j, r_0>)
     ra.e0 = g;
     ra.taps = tH;
     ra.sc = sc;
@@ -170,55 +222,61 @@ eecmg_status solve_level_enqueue(eecmg_plan_s* P, int l, const float* g, float* 
     ra.w = L.w;
     ra.mode = CM_RESID;
     ra.zero_input = zero_start ? 1 : 0;
-    CK(launch_conv(ra, rt, sepH, s));
+    LK(P, s, KC_CONV, 4.0 * n * (mr2 ? 4 : 3) - (zero_start ? 4.0 * n : 0.0), launch_conv(ra, rt, sepH, prec, s));
     if (m <= 0) return EECMG_OK;
 
-    if (P->opt.smoother == EECMG_SMOOTHER_MR2) {
+    if (mr2) {
+        MrVecs mv;
+        mv.v[0] = V[0];
+        mv.v[1] = V[1];
+        mv.aw[0] = V[2];
+        mv.aw[1] = V[3];
+        mv.d[0] = V[4];
+        mv.d[1] = V[5];
+        mv.hd[0] = V[6];
+        mv.hd[1] = V[7];
+        mv.u = u;
+        mv.r = V[8];
+        mv.r0 = V[9];
         ConvArgs c;
         c.taps = tH;
         c.sc = sc;
         c.partials = P->partials;
         c.h = L.h;
         c.w = L.w;
-        // p_1 = H r_0
-        c.x = P->r;
-        c.y = P->p[1];
-        c.mode = CM_MR_P1;
-        CK(launch_conv(c, rt, sepH, s));
-        // q_1 = H p_1, alpha_1
-        c.x = P->p[1];
-        c.y = P->q[1];
-        c.e0 = P->r;
-        c.mode = CM_MR_Q1;
-        CK(launch_conv(c, rt, sepH, s));
-        for (int k = 2; k <= m; ++k) {
-            const int cur = k & 1, prev = cur ^ 1;
-            c.x = P->q[prev];
-            c.y = P->z;
-            c.e0 = nullptr;
-            c.e1 = P->q[cur];
-            c.has_e1 = k >= 3;
+        c.x = V[9];  // v_1 = H r_0
+        c.y = mv.v[1];
+        c.mode = CM_MR_V1;
+        LK(P, s, KC_CONV, 8.0 * n, launch_conv(c, rt, sepH, prec, s));
+        for (int k = 1; k <= m; ++k) {
+            c.x = mv.v[k & 1];  // H w_k
+            c.y = mv.aw[k & 1];
             c.mode = CM_MR_A;
-            CK(launch_conv(c, rt, sepH, s));
-            CK(launch_mr_b(P->z, P->q[prev], P->q[cur], P->p[prev], P->p[cur], u, P->r, n, k >= 3,
-                           sc, P->partials, s));
+            LK(P, s, KC_CONV, 8.0 * n, launch_conv(c, rt, sepH, prec, s));
+            // step k-1 (k >= 2): reads v, Hw, u, r and 2/4 of the d/Hd history, writes d, Hd, u, r;
+            // Lanczos: reads Hw_k, v_k, r_0, writes v_{k+1}
+            const int j = k - 1;
+            const double step_vec = j >= 1 ? 4 + (j >= 2 ? 2 : 0) + (j >= 3 ? 2 : 0) + 4 : 0;
+            LK(P, s, KC_MR_B, 4.0 * n * (step_vec + 4), launch_mr_b(mv, k, n, sc, P->partials, s));
         }
-        CK(launch_step(u, P->p[m & 1], P->r, P->q[m & 1], n, 0, sc, P->partials, s));
+        LK(P, s, KC_MR_FINAL, 4.0 * n * (4 + (m >= 2 ? 2 : 0) + (m >= 3 ? 2 : 0) + 4),
+           launch_mr_final(mv, n, sc, P->partials, s));
     } else {
-        float* sv = P->z;
-        float* pv = P->p[0];
-        float* qv = P->q[0];
+        float* rv = V[8];
+        float* sv = V[0];
+        float* pv = V[1];
+        float* qv = V[2];
         ConvArgs c;
         c.sc = sc;
         c.partials = P->partials;
         c.h = L.h;
         c.w = L.w;
-        c.x = P->r;
+        c.x = rv;
         c.y = sv;
         c.y2 = pv;
         c.taps = tHT;
         c.mode = CM_CG_S0;
-        CK(launch_conv(c, rt, sepHT, s));
+        LK(P, s, KC_CONV, 12.0 * n, launch_conv(c, rt, sepHT, prec, s));
         for (int k = 1; k <= m; ++k) {
             ConvArgs q = c;
             q.x = pv;
@@ -226,14 +284,14 @@ eecmg_status solve_level_enqueue(eecmg_plan_s* P, int l, const float* g, float* 
             q.y2 = nullptr;
             q.taps = tH;
             q.mode = CM_CG_Q;
-            CK(launch_conv(q, rt, sepH, s));
-            CK(launch_step(u, pv, P->r, qv, n, 1, sc, P->partials, s));
+            LK(P, s, KC_CONV, 8.0 * n, launch_conv(q, rt, sepH, prec, s));
+            LK(P, s, KC_CG_STEP, 24.0 * n, launch_cg_step(u, pv, rv, qv, n, sc, P->partials, s));
             if (k < m) {
                 ConvArgs t = c;
                 t.y2 = nullptr;
                 t.mode = CM_CG_S;
-                CK(launch_conv(t, rt, sepHT, s));
-                CK(launch_cg_p(pv, sv, n, sc, s));
+                LK(P, s, KC_CONV, 8.0 * n, launch_conv(t, rt, sepHT, prec, s));
+                LK(P, s, KC_CG_P, 12.0 * n, launch_cg_p(pv, sv, n, sc, s));
             }
         }
     }
@@ -245,28 +303,34 @@ eecmg_status solve_level_enqueue(eecmg_plan_s* P, int l, const float* g, float* 
 eecmg_status prolong_enqueue(eecmg_plan_s* P, int l, cudaStream_t s) {
     LevelPlan& L = P->lv[l];
     LevelPlan& L1 = P->lv[l - 1];
-    float* up = P->z;  // prolonged, level l
+    float* up = P->vec[0];  // prolonged, level l
     if (P->opt.prolong == EECMG_PROLONG_EECMG) {
         LevelPlan& L2 = P->lv[l - 2];
-        float* ext = P->q[0];  // on the level-(l-1) grid
-        CK(launch_extrapolate(L1.u, L1.h, L1.w, L2.u, L2.h, L2.w, ext, s));
-        CK(launch_quadratic(ext, L1.h, L1.w, up, L.h, L.w, s));
+        float* ext = P->vec[2];  // on the level-(l-1) grid
+        LK(P, s, KC_PROLONG, 4.0 * (2.0 * L1.h * L1.w + (double)L2.h * L2.w),
+           launch_extrapolate(L1.u, L1.h, L1.w, L2.u, L2.h, L2.w, ext, s));
+        LK(P, s, KC_PROLONG, 4.0 * ((double)L1.h * L1.w + (double)L.h * L.w),
+           launch_quadratic(ext, L1.h, L1.w, up, L.h, L.w, s));
     } else if (P->opt.prolong == EECMG_PROLONG_IECMG_P) {
-        CK(launch_quadratic(L1.u, L1.h, L1.w, up, L.h, L.w, s));
+        LK(P, s, KC_PROLONG, 4.0 * ((double)L1.h * L1.w + (double)L.h * L.w),
+           launch_quadratic(L1.u, L1.h, L1.w, up, L.h, L.w, s));
     } else {
-        CK(launch_linear(L1.u, L1.h, L1.w, up, L.h, L.w, s));
+        LK(P, s, KC_PROLONG, 4.0 * ((double)L1.h * L1.w + (double)L.h * L.w),
+           launch_linear(L1.u, L1.h, L1.w, up, L.h, L.w, s));
     }
-    float* sm = P->p[0];
-    CK(launch_smooth(up, sm, L.h, L.w, (float)P->opt.s_scale, s));
+    float* sm = P->vec[1];
+    LK(P, s, KC_SMOOTH, 8.0 * L.h * L.w, launch_smooth(up, sm, L.h, L.w, (float)P->opt.s_scale, s));
     const int steps = P->opt.diffusion_steps;
     if (steps <= 0) {
-        CK(cudaMemcpyAsync(L.u, sm, sizeof(float) * L.h * L.w, cudaMemcpyDeviceToDevice, s));
+        LK(P, s, KC_COPY, 8.0 * L.h * L.w,
+           cudaMemcpyAsync(L.u, sm, sizeof(float) * L.h * L.w, cudaMemcpyDeviceToDevice, s));
         return EECMG_OK;
     }
     float* cur = sm;
     for (int d = 0; d < steps; ++d) {
         float* nxt = (d == steps - 1) ? L.u : (cur == sm ? up : sm);
-        CK(launch_denoise(cur, nxt, L.h, L.w, (float)P->tau, (float)P->kpm, s));
+        LK(P, s, KC_DENOISE, 8.0 * L.h * L.w,
+           launch_denoise(cur, nxt, L.h, L.w, (float)P->tau, (float)P->kpm, s));
         cur = nxt;
     }
     return EECMG_OK;
@@ -275,13 +339,15 @@ eecmg_status prolong_enqueue(eecmg_plan_s* P, int l, cudaStream_t s) {
 eecmg_status cascade_enqueue(eecmg_plan_s* P, cudaStream_t s) {
     const int L = P->L;
     for (int l = L - 1; l > 0; --l)
-        CK(launch_restrict(P->lv[l].g, P->lv[l].h, P->lv[l].w, P->lv[l - 1].g, P->lv[l - 1].h,
+        LK(P, s, KC_RESTRICT, 8.0 * P->lv[l - 1].h * P->lv[l - 1].w,
+           launch_restrict(P->lv[l].g, P->lv[l].h, P->lv[l].w, P->lv[l - 1].g, P->lv[l - 1].h,
                            P->lv[l - 1].w, s));
     const int nzero = P->opt.prolong == EECMG_PROLONG_EECMG ? 2 : 1;
     for (int l = 0; l < L; ++l) {
         const bool zero = l < nzero;
         if (zero) {
-            CK(cudaMemsetAsync(P->lv[l].u, 0, sizeof(float) * P->lv[l].h * P->lv[l].w, s));
+            LK(P, s, KC_COPY, 4.0 * P->lv[l].h * P->lv[l].w,
+               cudaMemsetAsync(P->lv[l].u, 0, sizeof(float) * P->lv[l].h * P->lv[l].w, s));
         } else {
             eecmg_status st = prolong_enqueue(P, l, s);
             if (st != EECMG_OK) return st;
@@ -293,7 +359,7 @@ eecmg_status cascade_enqueue(eecmg_plan_s* P, cudaStream_t s) {
 }
 
 eecmg_status run_cascade(eecmg_plan_s* P, cudaStream_t s) {
-    if (!P->opt.use_graph) return cascade_enqueue(P, s);
+    if (!P->opt.use_graph || P->prof.on) return cascade_enqueue(P, s);
     if (!P->gexec) {
         CK(cudaStreamBeginCapture(P->cap_stream, cudaStreamCaptureModeThreadLocal));
         eecmg_status st = cascade_enqueue(P, P->cap_stream);
@@ -340,6 +406,7 @@ eecmg_status eecmg_default_options(eecmg_options* o) {
     o->conv_tol = 1e-5;
     o->prolong = EECMG_PROLONG_EECMG;
     o->use_graph = 1;
+    o->precise_conv = 1;
     return EECMG_OK;
 }
 
@@ -439,7 +506,7 @@ eecmg_status eecmg_plan(int width, int height, int levels, const double* psf, in
         if (b > max_blocks) max_blocks = b;
     }
     (void)fine_n;
-    // workspace: g and u pyramids, six solver vectors, taps, scalars, partials
+    // workspace: g and u pyramids, solver vectors, taps, scalars, partials
     size_t off = 0;
     std::vector<size_t> g_off(levels), u_off(levels);
     for (int l = 0; l < levels; ++l) {
@@ -450,8 +517,8 @@ eecmg_status eecmg_plan(int width, int height, int levels, const double* psf, in
         u_off[l] = off;
         off = align_up(off + sizeof(float) * P->lv[l].h * P->lv[l].w, 256);
     }
-    size_t vec_off[6];
-    for (int i = 0; i < 6; ++i) {
+    size_t vec_off[eecmg_plan_s::NVEC];
+    for (int i = 0; i < eecmg_plan_s::NVEC; ++i) {
         vec_off[i] = off;
         off = align_up(off + sizeof(float) * max_n, 256);
     }
@@ -472,12 +539,7 @@ eecmg_status eecmg_plan(int width, int height, int levels, const double* psf, in
         P->lv[l].g = (float*)(P->ws + g_off[l]);
         P->lv[l].u = (float*)(P->ws + u_off[l]);
     }
-    P->r = (float*)(P->ws + vec_off[0]);
-    P->z = (float*)(P->ws + vec_off[1]);
-    P->p[0] = (float*)(P->ws + vec_off[2]);
-    P->p[1] = (float*)(P->ws + vec_off[3]);
-    P->q[0] = (float*)(P->ws + vec_off[4]);
-    P->q[1] = (float*)(P->ws + vec_off[5]);
+    for (int i = 0; i < eecmg_plan_s::NVEC; ++i) P->vec[i] = (float*)(P->ws + vec_off[i]);
     P->dtaps = (Taps*)(P->ws + taps_off);
     P->sc = (Scalars*)(P->ws + sc_off);
     P->partials = (double*)(P->ws + part_off);
@@ -503,6 +565,8 @@ eecmg_status eecmg_plan_destroy(eecmg_plan_t P) {
     cudaDeviceSynchronize();
     if (P->gexec) cudaGraphExecDestroy(P->gexec);
     if (P->cap_stream) cudaStreamDestroy(P->cap_stream);
+    prof_flush(P->prof);
+    for (cudaEvent_t e : P->prof.free_events) cudaEventDestroy(e);
     cudaFree(P->ws);
     delete P;
     return EECMG_OK;
@@ -581,7 +645,7 @@ eecmg_status eecmg_apply_H(eecmg_plan_t P, int level, const float* x, float* y, 
     a.w = L.w;
     a.taps = P->dtaps + 2 * level + (transpose ? 1 : 0);
     a.mode = CM_STORE;
-    CK(launch_conv(a, L.rt, transpose ? L.sepHT : L.sepH, s));
+    CK(launch_conv(a, L.rt, transpose ? L.sepHT : L.sepH, P->opt.precise_conv, s));
     return EECMG_OK;
 }
 
@@ -606,8 +670,8 @@ eecmg_status eecmg_prolong(eecmg_plan_t P, int level, const float* u1, const flo
     LevelPlan& L = P->lv[level];
     LevelPlan& L1 = P->lv[level - 1];
     LevelPlan& L2 = P->lv[level - 2];
-    CK(launch_extrapolate(u1, L1.h, L1.w, u2, L2.h, L2.w, P->q[0], s));
-    CK(launch_quadratic(P->q[0], L1.h, L1.w, out, L.h, L.w, s));
+    CK(launch_extrapolate(u1, L1.h, L1.w, u2, L2.h, L2.w, P->vec[2], s));
+    CK(launch_quadratic(P->vec[2], L1.h, L1.w, out, L.h, L.w, s));
     return EECMG_OK;
 }
 
@@ -650,6 +714,37 @@ eecmg_status eecmg_level_solve(eecmg_plan_t P, int level, const float* g, float*
     st = solve_level_enqueue(P, level, g, u, m, false, s);
     P->last_stream = s;
     return st;
+}
+
+eecmg_status eecmg_plan_profile(eecmg_plan_t P, int enable) {
+    if (!P) return set_error(EECMG_ERR_INVALID_ARG, "eecmg_plan_profile: NULL plan");
+    CK(prof_flush(P->prof));
+    P->prof.on = enable != 0;
+    for (int c = 0; c < KC_COUNT; ++c) {
+        P->prof.ms[c] = 0.0;
+        P->prof.bytes[c] = 0.0;
+        P->prof.launches[c] = 0;
+    }
+    return EECMG_OK;
+}
+
+eecmg_status eecmg_plan_profile_read(eecmg_plan_t P, eecmg_kernel_stat* out, int max, int* n) {
+    static const char* names[KC_COUNT] = {"conv", "mr_b", "mr_final", "cg_step", "cg_p",
+                                          "restrict", "prolong", "smooth", "denoise", "copy"};
+    if (!P || !n) return set_error(EECMG_ERR_INVALID_ARG, "eecmg_plan_profile_read: NULL argument");
+    CK(prof_flush(P->prof));
+    int k = 0;
+    for (int c = 0; c < KC_COUNT; ++c) {
+        if (out && k < max) {
+            std::snprintf(out[k].name, sizeof(out[k].name), "%s", names[c]);
+            out[k].launches = P->prof.launches[c];
+            out[k].ms = P->prof.ms[c];
+            out[k].bytes = P->prof.bytes[c];
+        }
+        ++k;
+    }
+    *n = k;
+    return EECMG_OK;
 }
 
 eecmg_status eecmg_restore_batched(const eecmg_plan_t* plans, const float* const* g, float* const* u,

@@ -18,6 +18,28 @@ struct LevelPlan {
     float* u = nullptr; // level solution (workspace)
 };
 
+// Kernel classes of the optional per-launch profiler.
+enum KernelClass : int {
+    KC_CONV = 0, KC_MR_B, KC_MR_FINAL, KC_CG_STEP, KC_CG_P, KC_RESTRICT, KC_PROLONG,
+    KC_SMOOTH, KC_DENOISE, KC_COPY, KC_COUNT
+};
+
+// Eager-mode profiler: an event pair around every launch of a restoration,
+// with the launch's algorithmic bytes (reads + writes the operator must do).
+struct Profiler {
+    bool on = false;
+    struct Rec {
+        int cls;
+        double bytes;
+        cudaEvent_t e0, e1;
+    };
+    std::vector<Rec> recs;
+    std::vector<cudaEvent_t> free_events;
+    double ms[KC_COUNT] = {};
+    double bytes[KC_COUNT] = {};
+    long long launches[KC_COUNT] = {};
+};
+
 eecmg_status set_error(eecmg_status st, const std::string& msg);
 int schedule_m(int L, int l);
 
@@ -36,13 +58,12 @@ struct eecmg_plan_s {
     eecmg::Taps* dtaps = nullptr;     // [2l] = H_l, [2l+1] = H_l^T
     eecmg::Scalars* sc = nullptr;     // one per level
     double* partials = nullptr;
-    float* r = nullptr;
-    float* z = nullptr;
-    float* p[2] = {nullptr, nullptr};
-    float* q[2] = {nullptr, nullptr};
+    static constexpr int NVEC = 10;
+    float* vec[NVEC] = {};              // solver vectors, each max level size
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t gexec = nullptr;
     cudaStream_t last_stream = nullptr;
+    eecmg::Profiler prof;
 };
 
 namespace eecmg {

@@ -50,7 +50,13 @@ class eecmg_options(ctypes.Structure):
         ("conv_tol", ctypes.c_double),
         ("prolong", ctypes.c_int),
         ("use_graph", ctypes.c_int),
+        ("precise_conv", ctypes.c_int),
     ]
+
+
+class eecmg_kernel_stat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 24), ("launches", ctypes.c_longlong),
+                ("ms", ctypes.c_double), ("bytes", ctypes.c_double)]
 
 
 _VP = ctypes.c_void_p
@@ -71,6 +77,8 @@ _SIGS = {
     "eecmg_restore_batched": [ctypes.POINTER(_VP), ctypes.POINTER(_VP), ctypes.POINTER(_VP), _I,
                               _VP],
     "eecmg_plan_stats": [_VP, _PI, _PD],
+    "eecmg_plan_profile": [_VP, _I],
+    "eecmg_plan_profile_read": [_VP, ctypes.POINTER(eecmg_kernel_stat), _I, _PI],
     "eecmg_apply_H": [_VP, _I, _VP, _VP, _I, _VP],
     "eecmg_restrict": [_VP, _I, _VP, _VP, _VP],
     "eecmg_prolong": [_VP, _I, _VP, _VP, _VP, _VP],
@@ -221,6 +229,19 @@ def eecmg_plan_stats(plan):
     res = (_D * L)()
     _call("eecmg_plan_stats", plan, it, res)
     return list(it), list(res)
+
+
+def eecmg_plan_profile(plan, enable=1):
+    _call("eecmg_plan_profile", plan, int(enable))
+
+
+def eecmg_plan_profile_read(plan):
+    """{class: {"launches", "ms", "bytes"}} accumulated since profiling was enabled."""
+    n = _I()
+    _call("eecmg_plan_profile_read", plan, None, 0, ctypes.byref(n))
+    arr = (eecmg_kernel_stat * n.value)()
+    _call("eecmg_plan_profile_read", plan, arr, n.value, ctypes.byref(n))
+    return {a.name.decode(): {"launches": a.launches, "ms": a.ms, "bytes": a.bytes} for a in arr}
 
 
 def eecmg_apply_H(plan, level, x, y, transpose=0, stream=None):

@@ -171,3 +171,52 @@ def test_convergence_stop_rule(orc, solver):
     tol = 0.5 * (fixed[5] + fixed[6]) / gn
     u, it, _ = getattr(orc, solver)(K, g, None, 11, conv_tol=tol)
     assert it == next(k for k, r in enumerate(fixed) if r <= tol * gn)
+
+
+def mr2_lanczos_givens(Hd, g, u0, m):
+    """MR-II by the Lanczos process on H started at H r0 and Givens QR of the
+    (k+1) x k tridiagonal least-squares problem with right-hand side <w_j, r0>."""
+    r0 = g - Hd @ u0
+    v = Hd @ r0
+    W = [v / np.linalg.norm(v)]
+    alphas, betas = [], []
+    u = u0.copy()
+    for k in range(m):
+        z = Hd @ W[k]
+        a = z @ W[k]
+        z = z - a * W[k] - (betas[-1] * W[k - 1] if k else 0.0)
+        b = np.linalg.norm(z)
+        alphas.append(a)
+        betas.append(b)
+        W.append(z / b)
+        T = np.zeros((k + 2, k + 1))
+        for j in range(k + 1):
+            T[j, j] = alphas[j]
+            T[j + 1, j] = betas[j]
+            if j:
+                T[j - 1, j] = betas[j - 1]
+        c = np.array([w @ r0 for w in W])
+        y, *_ = np.linalg.lstsq(T, c, rcond=None)
+        u = u0 + np.stack(W[:k + 1], axis=1) @ y
+    return u
+
+
+def test_mr2_recurrence_equals_lanczos_form(orc):
+    """Two formulations of MR-II give the same iterates (FP64, ill-conditioned H).
+
+    k stays at or below 15 on this 168-pixel grid: beyond that both FP64
+    formulations lose Lanczos orthogonality and part (1.5e-5 at k = 25).
+    """
+    from paper_2311_03010_gb300 import synth
+
+    rng = np.random.default_rng(18)
+    K = synth.gaussian_psf(1.5, 4)
+    h, w = 12, 14
+    Hd = dense_conv(K, h, w)
+    g = rng.uniform(0, 255, (h, w))
+    u0 = rng.uniform(0, 255, (h, w))
+    for m in (3, 10, 15):
+        exp = mr2_lanczos_givens(Hd, g.ravel(), u0.ravel(), m)
+        u, it, _ = orc.mr2(K, g, u0, m)
+        assert it == m
+        assert np.linalg.norm(u.ravel() - exp) <= 1e-10 * np.linalg.norm(exp), m
