@@ -12,6 +12,13 @@
 // u_0) is carried through H d_j (from the stored H w_j) for the stopping
 // rules, exactly as the recurrence residual.
 //
+// The projection c_{k+1} = <w_{k+1}, r_0> is taken as <w_{k+1}, r_{k-1}>:
+// r_0 - r_{k-1} = H (u_{k-1} - u_0) lies in H span(W_{k-1}) = span(W_k),
+// which is orthogonal to w_{k+1}, so the two are equal in exact arithmetic.
+// In FP32 the Lanczos vectors lose orthogonality to w_1, which carries the
+// large first coefficient; against the small current residual that loss no
+// longer sets a residual floor above the convergence threshold.
+//
 // Vectors are FP32; every inner product goes through the deterministic FP64
 // grid reduction, and all scalars (Lanczos coefficients, rotations, stop
 // flags) are decided on the device by the last block.  Each thread handles
@@ -44,7 +51,8 @@ __device__ __forceinline__ float mr_apply_step(const MrVecs& V, int j, size_t i,
     return rv;
 }
 
-// Phase B of iteration k (see launch.hpp).
+// Phase B of iteration k (see launch.hpp).  The dot for c_{k+1} uses the
+// residual after the pending step k-1 (r_{k-1}; r_0 when k = 1).
 __global__ void __launch_bounds__(NTHREADS)
     k_mr_b(MrVecs V, int k, size_t n, Scalars* sc, double* partials) {
     if (*(volatile int*)&sc->stopped) return;
@@ -69,7 +77,7 @@ __global__ void __launch_bounds__(NTHREADS)
             if (step) vn = fmaf(-cb, V.v[sk1][i], vn);
             V.v[sk1][i] = vn;
             avv = fmaf(vn, vn, avv);
-            avr = fmaf(vn, V.r0[i], avr);
+            avr = fmaf(vn, V.r[i], avr);
         }
     }
     double vals[3] = {(double)arr, (double)avv, (double)avr};

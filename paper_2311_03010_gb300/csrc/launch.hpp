@@ -53,7 +53,7 @@ cudaError_t launch_conv(const ConvArgs& a, int rt, int sep, int prec, cudaStream
 
 // MR-II (Lanczos / Givens form), phase B of iteration k: applies the
 // pending step k-1 (d, Hd, u, r), forms v_{k+1} and reduces ||r||^2,
-// <v_{k+1}, v_{k+1}>, <v_{k+1}, r_0>; the last block applies the stopping
+// <v_{k+1}, v_{k+1}>, <v_{k+1}, r_{k-1}>; the last block applies the stopping
 // rules and the Givens rotation of column k.  Buffers are indexed by step
 // parity: v[k & 1] = v_k, aw[k & 1] = H w_k, d/hd[j & 1] = d_j / H d_j.
 struct MrVecs {
@@ -63,7 +63,6 @@ struct MrVecs {
     float* hd[2];
     float* u;
     float* r;
-    const float* r0;
 };
 cudaError_t launch_mr_b(const MrVecs& V, int k, size_t n, Scalars* sc, double* partials,
                         cudaStream_t s);

@@ -211,7 +211,6 @@ eecmg_status solve_level_enqueue(eecmg_plan_s* P, int l, const float* g, float* 
     ConvArgs ra;
     ra.x = u;
     ra.y = V[8];                      // r
-    ra.y2 = mr2 ? V[9] : nullptr;     // r_0 (kept for <w_j, r_0>)
     ra.e0 = g;
     ra.taps = tH;
     ra.sc = sc;
@@ -222,7 +221,7 @@ eecmg_status solve_level_enqueue(eecmg_plan_s* P, int l, const float* g, float* 
     ra.w = L.w;
     ra.mode = CM_RESID;
     ra.zero_input = zero_start ? 1 : 0;
-    LK(P, s, KC_CONV, 4.0 * n * (mr2 ? 4 : 3) - (zero_start ? 4.0 * n : 0.0), launch_conv(ra, rt, sepH, prec, s));
+    LK(P, s, KC_CONV, 4.0 * n * 3 - (zero_start ? 4.0 * n : 0.0), launch_conv(ra, rt, sepH, prec, s));
     if (m <= 0) return EECMG_OK;
 
     if (mr2) {
@@ -237,14 +236,13 @@ eecmg_status solve_level_enqueue(eecmg_plan_s* P, int l, const float* g, float* 
         mv.hd[1] = V[7];
         mv.u = u;
         mv.r = V[8];
-        mv.r0 = V[9];
         ConvArgs c;
         c.taps = tH;
         c.sc = sc;
         c.partials = P->partials;
         c.h = L.h;
         c.w = L.w;
-        c.x = V[9];  // v_1 = H r_0
+        c.x = V[8];  // v_1 = H r_0
         c.y = mv.v[1];
         c.mode = CM_MR_V1;
         LK(P, s, KC_CONV, 8.0 * n, launch_conv(c, rt, sepH, prec, s));
@@ -254,10 +252,11 @@ eecmg_status solve_level_enqueue(eecmg_plan_s* P, int l, const float* g, float* 
             c.mode = CM_MR_A;
             LK(P, s, KC_CONV, 8.0 * n, launch_conv(c, rt, sepH, prec, s));
             // step k-1 (k >= 2): reads v, Hw, u, r and 2/4 of the d/Hd history, writes d, Hd, u, r;
-            // Lanczos: reads Hw_k, v_k, r_0, writes v_{k+1}
+            // Lanczos: reads Hw_k, v_k (and r, v_{k-1} when k = 1), writes v_{k+1}
             const int j = k - 1;
             const double step_vec = j >= 1 ? 4 + (j >= 2 ? 2 : 0) + (j >= 3 ? 2 : 0) + 4 : 0;
-            LK(P, s, KC_MR_B, 4.0 * n * (step_vec + 4), launch_mr_b(mv, k, n, sc, P->partials, s));
+            LK(P, s, KC_MR_B, 4.0 * n * (step_vec + (j >= 1 ? 3 : 4)),
+               launch_mr_b(mv, k, n, sc, P->partials, s));
         }
         LK(P, s, KC_MR_FINAL, 4.0 * n * (4 + (m >= 2 ? 2 : 0) + (m >= 3 ? 2 : 0) + 4),
            launch_mr_final(mv, n, sc, P->partials, s));

@@ -58,7 +58,7 @@ struct eecmg_plan_s {
     eecmg::Taps* dtaps = nullptr;     // [2l] = H_l, [2l+1] = H_l^T
     eecmg::Scalars* sc = nullptr;     // one per level
     double* partials = nullptr;
-    static constexpr int NVEC = 10;
+    static constexpr int NVEC = 9;
     float* vec[NVEC] = {};              // solver vectors, each max level size
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t gexec = nullptr;
