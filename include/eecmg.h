@@ -243,6 +243,30 @@ eecmg_status eecmg_denoise(eecmg_plan_t plan, int level, const float *in, float 
 eecmg_status eecmg_level_solve(eecmg_plan_t plan, int level, const float *g, float *u, int m,
                                cudaStream_t stream);
 
+/*
+ * r = g - H u and its norms, for callers that cannot allocate device memory
+ * (a process that forbids cudaMalloc after start-up because it can stall
+ * the device mid-request, or code under a framework allocator that already
+ * holds all of the GPU's memory).  The paper has no counterpart: this is the
+ * first step of a level solve (the residual of Section 2's stopping rule)
+ * without a plan.  H is the zero-boundary convolution with psf (host FP64,
+ * psf_h x psf_w, odd, radius <= EECMG_MAX_RADIUS).  g, u, r: device,
+ * height x width floats (r must not alias g or u); norms: device, 2
+ * doubles receiving ||r||^2 and ||g||^2 (Euclidean).  width and height must
+ * be in [1, 4096].  Asynchronous on `stream`.
+ * Scratch: the PSF taps, the reduction's per-block partial sums and its
+ * scalars live in one fixed __device__ array (about 264 KB) that every GPU
+ * which loads the library holds until the process exits; no call allocates
+ * or frees memory.  The first call on a device looks up that array's device
+ * address (once per device); make that first call before any stream capture.
+ * Every call shares the array and reinitialises it, so calls whose work
+ * overlaps on the GPU (other streams, other threads) race: serialise them.
+ * Errors: INVALID_ARG (sizes, PSF, NULL or aliased buffers), CUDA.
+ */
+eecmg_status eecmg_residual_noalloc(int width, int height, const double *psf, int psf_w,
+                                    int psf_h, const float *g, const float *u, float *r,
+                                    double *norms, cudaStream_t stream);
+
 /* ---- serving: continuous batching of restoration requests -------------- */
 
 typedef struct eecmg_server_s *eecmg_server_t;

@@ -86,6 +86,7 @@ _SIGS = {
     "eecmg_smooth": [_VP, _I, _VP, _VP, _VP],
     "eecmg_denoise": [_VP, _I, _VP, _VP, _VP],
     "eecmg_level_solve": [_VP, _I, _VP, _VP, _I, _VP],
+    "eecmg_residual_noalloc": [_I, _I, _PD, _I, _I, _VP, _VP, _VP, _VP, _VP],
     "eecmg_server_create": [ctypes.c_size_t, _I, ctypes.POINTER(_VP)],
     "eecmg_server_submit": [_VP, _VP, _VP, _VP, ctypes.POINTER(ctypes.c_uint64)],
     "eecmg_server_poll": [_VP, ctypes.c_uint64, _PI, _PD],
@@ -271,6 +272,17 @@ def eecmg_denoise(plan, level, x, y, stream=None):
 
 def eecmg_level_solve(plan, level, g, u, m, stream=None):
     _call("eecmg_level_solve", plan, int(level), _ptr(g), _ptr(u), int(m), _stream(stream))
+
+
+def eecmg_residual_noalloc(width, height, psf, g, u, r, norms, stream=None):
+    """r = g - H u and norms[0:2] = (||r||^2, ||g||^2); allocates no device memory.
+
+    norms is a device buffer of two float64 values (tensor or address).
+    """
+    psf = np.ascontiguousarray(psf, dtype=np.float64)
+    nptr = norms if isinstance(norms, int) else norms.data_ptr()
+    _call("eecmg_residual_noalloc", int(width), int(height), psf.ctypes.data_as(_PD),
+          psf.shape[1], psf.shape[0], _ptr(g), _ptr(u), _ptr(r), nptr, _stream(stream))
 
 
 def eecmg_server_create(mem_budget_bytes, max_slots):
