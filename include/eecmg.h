@@ -83,6 +83,8 @@ enum { EECMG_PROLONG_EECMG = 0, EECMG_PROLONG_IECMG_P = 1, EECMG_PROLONG_IECMG_L
  *   precise_conv = 1      compensated (error-free product + TwoSum) FP32
  *                         accumulation in the second pass of separable
  *                         convolutions; 0 = plain FMA accumulation.
+ *   persistent = 1        one cooperative launch per level solve (grid
+ *                         barriers inside); 0 = one launch per phase.
  */
 typedef struct {
     int smoother;
@@ -97,6 +99,7 @@ typedef struct {
     int prolong;
     int use_graph;
     int precise_conv;
+    int persistent;
 } eecmg_options;
 
 typedef struct eecmg_plan_s *eecmg_plan_t;

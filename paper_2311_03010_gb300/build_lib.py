@@ -63,7 +63,7 @@ def build(force: bool = False, verbose: bool = False, extra=None) -> str:
 
     todo = [cmd for (_, cmd, stale) in jobs if stale]
     if todo:
-        with cf.ThreadPoolExecutor(max_workers=min(8, len(todo))) as ex:
+        with cf.ThreadPoolExecutor(max_workers=max(1, min(os.cpu_count() or 8, len(todo)))) as ex:
             list(ex.map(run, todo))
     objs = [o for (o, _, _) in jobs]
     if force or todo or not os.path.exists(LIB) or os.path.getmtime(LIB) < max(

@@ -41,7 +41,7 @@ struct alignas(64) Scalars {
                           // 3 non-finite; 4 breakdown after deciding a last step
     int iters;            // iterations whose step has been decided
     unsigned int counter; // last-block arrival counter (reset by the last block)
-    int pad0;
+    int loops;            // iterations whose first phase ran (for byte accounting)
     // MR-II, Lanczos / Givens form
     double nrm, nrm_prev; // ||v_k||, ||v_{k-1}|| (w_k = v_k / ||v_k||)
     double alpha;         // alpha_k = <H w_k, w_k>

@@ -25,6 +25,7 @@
 // 8 elements strided by the block size, so loads and stores are coalesced.
 #include <math.h>
 
+#include "finish.cuh"
 #include "launch.hpp"
 
 namespace eecmg {
@@ -85,54 +86,7 @@ __global__ void __launch_bounds__(NTHREADS)
     double tot[3];
     grid_total<3>(partials, gridDim.x, &sc->counter, tot);
     if (threadIdx.x != 0) return;
-    if (step) {
-        const double rr = tot[0];
-        sc->rr = rr;
-        if (!(rr < 1.0e300)) {
-            sc->stopped = 3;
-            return;
-        }
-        if (rr <= sc->lim2) {  // stopping rule on ||r_{k-1}||, before iteration k
-            sc->stopped = 1;
-            return;
-        }
-    }
-    const double vv = tot[1];
-    if (!(vv < 1.0e300)) {
-        sc->stopped = 3;
-        return;
-    }
-    const double nrm_new = sqrt(vv);
-    const double c_new = vv > 0.0 ? tot[2] / nrm_new : 0.0;
-    // column k of T: ||v_k|| above the diagonal (0 for k = 1), alpha_k on it,
-    // ||v_{k+1}|| below; apply G_{k-2}, G_{k-1}, then the new rotation G_k
-    const double alpha = sc->alpha;
-    const double cpl = step ? sc->nrm : 0.0;
-    const double e = sc->sn2 * cpl;
-    const double t = sc->cs2 * cpl;
-    const double r1 = sc->cs1 * t + sc->sn1 * alpha;
-    const double a2 = -sc->sn1 * t + sc->cs1 * alpha;
-    const double rho = hypot(a2, nrm_new);
-    if (!(rho > 0.0) || !(rho < 1.0e300)) {
-        sc->stopped = rho > 0.0 ? 3 : 2;
-        return;
-    }
-    const double cs = a2 / rho, sn = nrm_new / rho;
-    const double phi = sc->phi;
-    sc->tau = cs * phi + sn * c_new;
-    sc->phi = -sn * phi + cs * c_new;
-    sc->dinv = 1.0 / rho;
-    sc->dw = 1.0 / (sc->nrm * rho);
-    sc->d1 = r1 / rho;
-    sc->d2 = e / rho;
-    sc->cs2 = sc->cs1;
-    sc->sn2 = sc->sn1;
-    sc->cs1 = cs;
-    sc->sn1 = sn;
-    sc->nrm_prev = sc->nrm;
-    sc->nrm = nrm_new;
-    sc->iters = k;
-    if (!(nrm_new > 0.0)) sc->stopped = 4;  // Krylov space exhausted: step k is the last
+    fin_mr_b(sc, k, tot[0], tot[1], tot[2]);
 }
 
 // Applies the step decided last (its index is sc->iters) and reduces ||r||^2.
@@ -159,8 +113,7 @@ __global__ void __launch_bounds__(NTHREADS)
     double tot[1];
     grid_total<1>(partials, gridDim.x, &sc->counter, tot);
     if (threadIdx.x != 0) return;
-    sc->rr = tot[0];
-    if (!(tot[0] < 1.0e300)) sc->stopped = 3;
+    fin_mr_final(sc, tot[0]);
 }
 
 // CGLS: u += alpha p, r -= alpha q, ||r||^2, then the stopping rule on the
@@ -187,9 +140,7 @@ __global__ void __launch_bounds__(NTHREADS)
     double tot[1];
     grid_total<1>(partials, gridDim.x, &sc->counter, tot);
     if (threadIdx.x != 0) return;
-    sc->rr = tot[0];
-    if (!(tot[0] < 1.0e300)) sc->stopped = 3;
-    else if (tot[0] <= sc->lim2) sc->stopped = 1;
+    fin_cg_step(sc, tot[0]);
 }
 
 // CGLS direction update p = s + beta p (beta decided by the H^T launch).

@@ -1,0 +1,365 @@
+// level_solve_impl.cuh -- persistent level smoothers C_l^m (Section 2): one
+// cooperative launch runs a whole level solve, MR-II (Lanczos / Givens form,
+// see krylov.cu) or CGLS.
+//
+// Every phase of an iteration is a grid-stride pass over the level's tiles
+// (convolution phases, 32 x 64 tiles with halo in shared memory) or pixels
+// (elementwise phases), ended by group_reduce: the deterministic FP64 sums
+// of the phase's inner products and its scalar update (finish.cuh), then a
+// bounded grid barrier.  Compared with one launch per phase this removes the
+// launch latency of every phase and, because the loop tests the stop flag,
+// the iterations that a stopping rule makes unnecessary are never launched.
+// Vectors written inside the launch are read back through L2 (ld.global.cg).
+#pragma once
+
+#include "conv_tile.cuh"
+#include "finish.cuh"
+#include "level_solve.hpp"
+#include "persistent.cuh"
+
+namespace eecmg {
+
+namespace ls_detail {
+
+__device__ __forceinline__ int volatile_stopped(const Scalars* sc) {
+    return *(volatile const int*)&sc->stopped;
+}
+
+__device__ __forceinline__ double vld(const double* p) { return *(volatile const double*)p; }
+
+// Applies MR-II step j at pixel i (coherent loads); returns the new r_i.
+__device__ __forceinline__ float mr_step_px(const LevelJob& J, int j, size_t i, float dw, float d1,
+                                            float d2, float dinv, float tau) {
+    const int sj = j & 1, sj1 = sj ^ 1;
+    float dj = dw * ldcg(J.v[sj] + i);
+    float hj = dinv * ldcg(J.aw[sj] + i);
+    if (j >= 2) {
+        dj = fmaf(-d1, ldcg(J.d[sj1] + i), dj);
+        hj = fmaf(-d1, ldcg(J.hd[sj1] + i), hj);
+    }
+    if (j >= 3) {
+        dj = fmaf(-d2, ldcg(J.d[sj] + i), dj);
+        hj = fmaf(-d2, ldcg(J.hd[sj] + i), hj);
+    }
+    J.d[sj][i] = dj;
+    J.hd[sj][i] = hj;
+    J.u[i] = fmaf(tau, dj, ldcg(J.u + i));
+    const float rv = fmaf(-tau, hj, ldcg(J.r + i));
+    J.r[i] = rv;
+    return rv;
+}
+
+// One convolution phase over the level: y = scale * (C (*) x) for every tile,
+// with epilogue E(idx, z, center) accumulating into acc0/acc1.
+template <int R, bool SEP, bool PREC, bool ZERO, class Epi>
+__device__ __forceinline__ void conv_phase(ConvSmem<R, SEP>& S, const float* x, int h, int w,
+                                           unsigned int nb, unsigned int bid, Epi&& epi) {
+    using SM = ConvSmem<R, SEP>;
+    const int tiles_x = (w + CONV_TW - 1) / CONV_TW, tiles_y = (h + CONV_TH - 1) / CONV_TH;
+    const int ntiles = tiles_x * tiles_y;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int t = (int)bid; t < ntiles; t += (int)nb) {
+        const int y0 = (t / tiles_x) * CONV_TH, x0 = (t % tiles_x) * CONV_TW;
+        if (!ZERO) {
+            conv_load<R, SEP, true>(S, x, h, w, y0, x0);
+            __syncthreads();
+            conv_compute<R, SEP, PREC>(S);
+            __syncthreads();
+        }
+#pragma unroll
+        for (int it = 0; it < CONV_TH / 8; ++it) {
+            const int r = warp + 8 * it, gy = y0 + r;
+#pragma unroll
+            for (int hf = 0; hf < 2; ++hf) {
+                const int c = lane + 32 * hf, gx = x0 + c;
+                if (gy < h && gx < w) {
+                    const size_t idx = (size_t)gy * w + gx;
+                    const float z = ZERO ? 0.f : S.out[r * SM::PO + c];
+                    const float ctr = ZERO ? 0.f : S.in[(r + R) * SM::IW + c + R];
+                    epi(idx, z, ctr);
+                }
+            }
+        }
+        __syncthreads();  // S is reused by the next tile
+    }
+}
+
+}  // namespace ls_detail
+
+using namespace ls_detail;
+
+template <int R, bool SEP, bool PREC>
+__global__ void __launch_bounds__(NTHREADS) k_level_mr2(LevelJob J) {
+    __shared__ ConvSmem<R, SEP> S;
+    const unsigned int nb = gridDim.x, bid = blockIdx.x;
+    const int h = J.h, w = J.w;
+    const size_t n = (size_t)h * w;
+    const size_t stride = (size_t)nb * NTHREADS;
+    Scalars* sc = J.sc;
+    conv_stage_taps<R, SEP>(S, J.taps);
+    __syncthreads();
+
+    // r_0 = g - H u_0, ||r_0||^2, ||g||^2, stopping limit
+    {
+        float a0 = 0.f, a1 = 0.f;
+        auto epi = [&](size_t idx, float z, float) {
+            const float gv = __ldg(J.g + idx);
+            const float rv = gv - z;
+            J.r[idx] = rv;
+            a0 = fmaf(rv, rv, a0);
+            a1 = fmaf(gv, gv, a1);
+        };
+        if (J.zero_start)
+            conv_phase<R, SEP, PREC, true>(S, J.u, h, w, nb, bid, epi);
+        else
+            conv_phase<R, SEP, PREC, false>(S, J.u, h, w, nb, bid, epi);
+        double v[2] = {(double)a0, (double)a1};
+        const double ct2 = J.conv_tol2, d2 = J.disc2;
+        if (!group_reduce<2>(v, J.partials, J.gs, nb, bid,
+                             [&](double* t) { fin_resid(sc, t[0], t[1], ct2, d2); }))
+            return;
+    }
+    if (J.m <= 0 || volatile_stopped(sc)) return;
+
+    // v_1 = H r_0, ||v_1||, <v_1, r_0>
+    {
+        float a0 = 0.f, a1 = 0.f;
+        float* v1 = J.v[1];
+        conv_phase<R, SEP, PREC, false>(S, J.r, h, w, nb, bid, [&](size_t idx, float z, float ctr) {
+            v1[idx] = z;
+            a0 = fmaf(z, z, a0);
+            a1 = fmaf(z, ctr, a1);
+        });
+        double v[2] = {(double)a0, (double)a1};
+        if (!group_reduce<2>(v, J.partials, J.gs, nb, bid,
+                             [&](double* t) { fin_mr_v1(sc, t[0], t[1]); }))
+            return;
+    }
+
+    for (int k = 1; k <= J.m; ++k) {
+        if (volatile_stopped(sc)) break;
+        const int sk = k & 1, sk1 = sk ^ 1;
+        // phase A: H w_k = H v_k / ||v_k||, alpha_k = <H w_k, w_k>
+        {
+            const float scale = (float)(1.0 / vld(&sc->nrm));
+            float a0 = 0.f;
+            float* aw = J.aw[sk];
+            conv_phase<R, SEP, PREC, false>(S, J.v[sk], h, w, nb, bid,
+                                            [&](size_t idx, float z, float ctr) {
+                                                const float hz = z * scale;
+                                                aw[idx] = hz;
+                                                a0 = fmaf(hz, ctr, a0);
+                                            });
+            double v[1] = {(double)a0};
+            if (!group_reduce<1>(v, J.partials, J.gs, nb, bid,
+                                 [&](double* t) { fin_mr_a(sc, t[0]); }))
+                return;
+        }
+        // phase B: pending step k-1, v_{k+1}, stopping rules, rotation of column k
+        {
+            const bool step = k >= 2;
+            const float dw = (float)vld(&sc->dw), d1 = (float)vld(&sc->d1);
+            const float d2 = (float)vld(&sc->d2), dinv = (float)vld(&sc->dinv);
+            const float tau = (float)vld(&sc->tau);
+            const double nrm = vld(&sc->nrm);
+            const float ca = (float)(vld(&sc->alpha) / nrm);
+            const float cb = step ? (float)(nrm / vld(&sc->nrm_prev)) : 0.f;
+            float arr = 0.f, avv = 0.f, avr = 0.f;
+            for (size_t i = (size_t)bid * NTHREADS + threadIdx.x; i < n; i += stride) {
+                float rv;
+                if (step) {
+                    rv = mr_step_px(J, k - 1, i, dw, d1, d2, dinv, tau);
+                    arr = fmaf(rv, rv, arr);
+                } else {
+                    rv = ldcg(J.r + i);
+                }
+                float vn = fmaf(-ca, ldcg(J.v[sk] + i), ldcg(J.aw[sk] + i));
+                if (step) vn = fmaf(-cb, ldcg(J.v[sk1] + i), vn);
+                J.v[sk1][i] = vn;
+                avv = fmaf(vn, vn, avv);
+                avr = fmaf(vn, rv, avr);
+            }
+            double v[3] = {(double)arr, (double)avv, (double)avr};
+            if (!group_reduce<3>(v, J.partials, J.gs, nb, bid,
+                                 [&](double* t) { fin_mr_b(sc, k, t[0], t[1], t[2]); }))
+                return;
+        }
+    }
+
+    // the step decided last (breakdown-with-step or the schedule's end)
+    const int st = volatile_stopped(sc);
+    const int j = *(volatile const int*)&sc->iters;
+    if ((st == 0 || st == 4) && j >= 1) {
+        const float dw = (float)vld(&sc->dw), d1 = (float)vld(&sc->d1);
+        const float d2 = (float)vld(&sc->d2), dinv = (float)vld(&sc->dinv);
+        const float tau = (float)vld(&sc->tau);
+        float arr = 0.f;
+        for (size_t i = (size_t)bid * NTHREADS + threadIdx.x; i < n; i += stride) {
+            const float rv = mr_step_px(J, j, i, dw, d1, d2, dinv, tau);
+            arr = fmaf(rv, rv, arr);
+        }
+        double v[1] = {(double)arr};
+        group_reduce<1>(v, J.partials, J.gs, nb, bid, [&](double* t) { fin_mr_final(sc, t[0]); });
+    }
+}
+
+template <int R, bool SEP, bool PREC>
+__global__ void __launch_bounds__(NTHREADS) k_level_cgls(LevelJob J) {
+    __shared__ ConvSmem<R, SEP> S;
+    const unsigned int nb = gridDim.x, bid = blockIdx.x;
+    const int h = J.h, w = J.w;
+    const size_t n = (size_t)h * w;
+    const size_t stride = (size_t)nb * NTHREADS;
+    Scalars* sc = J.sc;
+    float* rv_ = J.r;
+    float* sv = J.v[0];  // s
+    float* pv = J.v[1];  // p
+    float* qv = J.aw[0]; // q
+    conv_stage_taps<R, SEP>(S, J.taps);
+    __syncthreads();
+    {
+        float a0 = 0.f, a1 = 0.f;
+        auto epi = [&](size_t idx, float z, float) {
+            const float gv = __ldg(J.g + idx);
+            const float rv = gv - z;
+            rv_[idx] = rv;
+            a0 = fmaf(rv, rv, a0);
+            a1 = fmaf(gv, gv, a1);
+        };
+        if (J.zero_start)
+            conv_phase<R, SEP, PREC, true>(S, J.u, h, w, nb, bid, epi);
+        else
+            conv_phase<R, SEP, PREC, false>(S, J.u, h, w, nb, bid, epi);
+        double v[2] = {(double)a0, (double)a1};
+        const double ct2 = J.conv_tol2, d2 = J.disc2;
+        if (!group_reduce<2>(v, J.partials, J.gs, nb, bid,
+                             [&](double* t) { fin_resid(sc, t[0], t[1], ct2, d2); }))
+            return;
+    }
+    if (J.m <= 0 || volatile_stopped(sc)) return;
+    __syncthreads();
+    conv_stage_taps<R, SEP>(S, J.tapsT);  // s = H^T r, p = s
+    __syncthreads();
+    {
+        float a0 = 0.f;
+        conv_phase<R, SEP, PREC, false>(S, rv_, h, w, nb, bid, [&](size_t idx, float z, float) {
+            sv[idx] = z;
+            pv[idx] = z;
+            a0 = fmaf(z, z, a0);
+        });
+        double v[1] = {(double)a0};
+        if (!group_reduce<1>(v, J.partials, J.gs, nb, bid, [&](double* t) { fin_cg_s0(sc, t[0]); }))
+            return;
+    }
+    for (int k = 1; k <= J.m; ++k) {
+        if (volatile_stopped(sc)) break;
+        __syncthreads();
+        conv_stage_taps<R, SEP>(S, J.taps);  // q = H p, alpha
+        __syncthreads();
+        {
+            float a0 = 0.f;
+            conv_phase<R, SEP, PREC, false>(S, pv, h, w, nb, bid, [&](size_t idx, float z, float) {
+                qv[idx] = z;
+                a0 = fmaf(z, z, a0);
+            });
+            double v[1] = {(double)a0};
+            if (!group_reduce<1>(v, J.partials, J.gs, nb, bid,
+                                 [&](double* t) { fin_cg_q(sc, t[0]); }))
+                return;
+        }
+        if (volatile_stopped(sc)) break;
+        {  // u += alpha p, r -= alpha q, stopping rule
+            const float a = (float)vld(&sc->cg_alpha);
+            float arr = 0.f;
+            for (size_t i = (size_t)bid * NTHREADS + threadIdx.x; i < n; i += stride) {
+                J.u[i] = fmaf(a, ldcg(pv + i), ldcg(J.u + i));
+                const float r = fmaf(-a, ldcg(qv + i), ldcg(rv_ + i));
+                rv_[i] = r;
+                arr = fmaf(r, r, arr);
+            }
+            double v[1] = {(double)arr};
+            if (!group_reduce<1>(v, J.partials, J.gs, nb, bid,
+                                 [&](double* t) { fin_cg_step(sc, t[0]); }))
+                return;
+        }
+        if (k == J.m || volatile_stopped(sc)) break;
+        __syncthreads();
+        conv_stage_taps<R, SEP>(S, J.tapsT);  // s = H^T r, beta
+        __syncthreads();
+        {
+            float a0 = 0.f;
+            conv_phase<R, SEP, PREC, false>(S, rv_, h, w, nb, bid, [&](size_t idx, float z, float) {
+                sv[idx] = z;
+                a0 = fmaf(z, z, a0);
+            });
+            double v[1] = {(double)a0};
+            if (!group_reduce<1>(v, J.partials, J.gs, nb, bid,
+                                 [&](double* t) { fin_cg_s(sc, t[0]); }))
+                return;
+        }
+        if (volatile_stopped(sc)) break;
+        {  // p = s + beta p
+            const float b = (float)vld(&sc->beta);
+            for (size_t i = (size_t)bid * NTHREADS + threadIdx.x; i < n; i += stride)
+                pv[i] = fmaf(b, ldcg(pv + i), ldcg(sv + i));
+            double v[1] = {0.0};
+            if (!group_reduce<1>(v, J.partials, J.gs, nb, bid, [&](double*) {})) return;
+        }
+    }
+}
+
+template <class K>
+inline cudaError_t coop_launch(K kernel, const LevelJob& J, int blocks, cudaStream_t s) {
+    LevelJob arg = J;
+    void* params[] = {&arg};
+    return cudaLaunchCooperativeKernel((const void*)kernel, dim3(blocks), dim3(NTHREADS), params, 0, s);
+}
+
+template <class K>
+inline int coresident_blocks(K kernel) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, NTHREADS, 0);
+    return per_sm * sms;
+}
+
+template <class K>
+inline cudaError_t launch_capped(K kern, int& cap, const LevelJob& J, int want, cudaStream_t s,
+                                 int* used) {
+    if (cap < 0) cap = coresident_blocks(kern);
+    int blocks = want < cap ? want : cap;
+    if (blocks < 1) blocks = 1;
+    if (used) *used = blocks;
+    return coop_launch(kern, J, blocks, s);
+}
+
+// Launches one instantiation with min(want, co-resident capacity) blocks.
+template <int R, bool SEP, bool PREC, bool CGLS>
+cudaError_t launch_level_t(const LevelJob& J, int want, cudaStream_t s, int* used) {
+    static int cap = -1;  // per instantiation; the library runs on one GPU model
+    if constexpr (CGLS)
+        return launch_capped(k_level_cgls<R, SEP, PREC>, cap, J, want, s, used);
+    else
+        return launch_capped(k_level_mr2<R, SEP, PREC>, cap, J, want, s, used);
+}
+
+template <int R, bool CGLS>
+cudaError_t launch_level_r(const LevelJob& J, int sep, int prec, int want, cudaStream_t s,
+                           int* used) {
+    if (sep && prec) return launch_level_t<R, true, true, CGLS>(J, want, s, used);
+    if (sep) return launch_level_t<R, true, false, CGLS>(J, want, s, used);
+    return launch_level_t<R, false, false, CGLS>(J, want, s, used);
+}
+
+// Per translation unit: one solver, a range of radii.
+cudaError_t launch_level_mr2_lo(const LevelJob& J, int rt, int sep, int prec, int want,
+                                cudaStream_t s, int* used);
+cudaError_t launch_level_mr2_hi(const LevelJob& J, int rt, int sep, int prec, int want,
+                                cudaStream_t s, int* used);
+cudaError_t launch_level_cgls_lo(const LevelJob& J, int rt, int sep, int prec, int want,
+                                 cudaStream_t s, int* used);
+cudaError_t launch_level_cgls_hi(const LevelJob& J, int rt, int sep, int prec, int want,
+                                 cudaStream_t s, int* used);
+
+}  // namespace eecmg

@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "launch.hpp"
+#include "level_solve.hpp"
 #include "plan.hpp"
 
 using namespace eecmg;
@@ -155,15 +156,51 @@ cudaEvent_t prof_event(Profiler& pr) {
     return e;
 }
 
+// Algorithmic bytes of a persistent level solve, from the iterations it ran
+// (each operand read or written once per phase, FP32).
+double level_solve_bytes(const eecmg_plan_s* P, int l, const Scalars& sc, bool zero_start) {
+    const double n = (double)P->lv[l].h * P->lv[l].w;
+    double b = (zero_start ? 8.0 : 12.0) * n;  // r = g - H u
+    const int K = sc.loops;
+    if (P->opt.smoother == EECMG_SMOOTHER_MR2) {
+        if (K > 0 || sc.iters > 0) b += 8.0 * n;  // v_1 = H r_0
+        for (int k = 1; k <= K; ++k) {
+            b += 8.0 * n;  // H w_k
+            if (k == 1) {
+                b += 16.0 * n;
+            } else {
+                const int j = k - 1;
+                b += 4.0 * n * (4 + (j >= 2 ? 2 : 0) + (j >= 3 ? 2 : 0) + 4 + 3);
+            }
+        }
+        const int j = sc.iters;
+        if ((sc.stopped == 0 || sc.stopped == 4) && j >= 1)
+            b += 4.0 * n * (4 + (j >= 2 ? 2 : 0) + (j >= 3 ? 2 : 0) + 4);
+    } else {
+        if (K > 0 || sc.iters > 0) b += 12.0 * n;  // s = H^T r, p = s
+        b += (8.0 + 24.0) * n * K;                 // q = H p; u, r update
+        if (K > 1) b += (8.0 + 12.0) * n * (K - 1);  // s = H^T r; p = s + beta p
+    }
+    return b;
+}
+
 // Folds the recorded launches into the per-class totals (synchronises).
-cudaError_t prof_flush(Profiler& pr) {
+cudaError_t prof_flush(eecmg_plan_s* P) {
+    Profiler& pr = P->prof;
     for (auto& r : pr.recs) {
         cudaError_t e = cudaEventSynchronize(r.e1);
         if (e != cudaSuccess) return e;
         float ms = 0.f;
         cudaEventElapsedTime(&ms, r.e0, r.e1);
+        double bytes = r.bytes;
+        if (r.level >= 0) {
+            Scalars sc;
+            e = cudaMemcpy(&sc, P->sc + r.level, sizeof(Scalars), cudaMemcpyDeviceToHost);
+            if (e != cudaSuccess) return e;
+            bytes = level_solve_bytes(P, r.level, sc, r.bytes != 0.0);
+        }
         pr.ms[r.cls] += ms;
-        pr.bytes[r.cls] += r.bytes;
+        pr.bytes[r.cls] += bytes;
         pr.launches[r.cls] += 1;
         pr.free_events.push_back(r.e0);
         pr.free_events.push_back(r.e1);
@@ -185,7 +222,7 @@ cudaError_t prof_flush(Profiler& pr) {
             CK(call);                                                            \
             cudaEventRecord(rec_.e1, (s));                                       \
             (P)->prof.recs.push_back(rec_);                                      \
-            if ((P)->prof.recs.size() > 8192) CK(prof_flush((P)->prof));         \
+            if ((P)->prof.recs.size() > 8192) CK(prof_flush(P));         \
         } else {                                                                 \
             CK(call);                                                            \
         }                                                                        \
@@ -207,6 +244,43 @@ eecmg_status solve_level_enqueue(eecmg_plan_s* P, int l, const float* g, float* 
     const int rt = L.rt, sepH = L.sepH, sepHT = L.sepHT, prec = P->opt.precise_conv;
     const bool mr2 = P->opt.smoother == EECMG_SMOOTHER_MR2;
     float** V = P->vec;
+
+    if (P->opt.persistent) {
+        LevelJob J;
+        J.g = g;
+        J.u = u;
+        for (int i = 0; i < 2; ++i) {
+            J.v[i] = V[0 + i];
+            J.aw[i] = V[2 + i];
+            J.d[i] = V[4 + i];
+            J.hd[i] = V[6 + i];
+        }
+        J.r = V[8];
+        J.taps = tH;
+        J.tapsT = tHT;
+        J.sc = sc;
+        J.partials = P->partials;
+        J.gs = P->gsync + l;
+        J.conv_tol2 = P->conv_tol2;
+        J.disc2 = L.disc2;
+        J.h = L.h;
+        J.w = L.w;
+        J.m = m;
+        J.zero_start = zero_start ? 1 : 0;
+        int used = 0;
+        if (P->prof.on) {
+            // bytes field flags a zero start; the count itself is taken after the run
+            Profiler::Rec rec{KC_LEVEL, zero_start ? 1.0 : 0.0, prof_event(P->prof),
+                              prof_event(P->prof), l};
+            cudaEventRecord(rec.e0, s);
+            CK(launch_level_solve(J, rt, mr2 ? sepH : sepH, prec, mr2 ? 0 : 1, s, &used));
+            cudaEventRecord(rec.e1, s);
+            P->prof.recs.push_back(rec);
+        } else {
+            CK(launch_level_solve(J, rt, mr2 ? sepH : sepH, prec, mr2 ? 0 : 1, s, &used));
+        }
+        return EECMG_OK;
+    }
 
     ConvArgs ra;
     ra.x = u;
@@ -406,6 +480,7 @@ eecmg_status eecmg_default_options(eecmg_options* o) {
     o->prolong = EECMG_PROLONG_EECMG;
     o->use_graph = 1;
     o->precise_conv = 1;
+    o->persistent = 1;
     return EECMG_OK;
 }
 
@@ -502,6 +577,8 @@ eecmg_status eecmg_plan(int width, int height, int levels, const double* psf, in
         const size_t n = (size_t)P->lv[l].h * P->lv[l].w;
         size_t b = conv_blocks(P->lv[l].h, P->lv[l].w);
         if (ew_blocks(n) > b) b = ew_blocks(n);
+        const size_t pb = (n + 4 * NTHREADS - 1) / (4 * NTHREADS);  // persistent grid bound
+        if (pb > b) b = pb;
         if (b > max_blocks) max_blocks = b;
     }
     (void)fine_n;
@@ -525,6 +602,8 @@ eecmg_status eecmg_plan(int width, int height, int levels, const double* psf, in
     off = align_up(off + sizeof(Taps) * 2 * levels, 256);
     const size_t sc_off = off;
     off = align_up(off + sizeof(Scalars) * levels, 256);
+    const size_t gs_off = off;
+    off = align_up(off + sizeof(GroupSync) * levels, 256);
     const size_t part_off = off;
     off = align_up(off + sizeof(double) * NPART * max_blocks, 256);
     P->ws_bytes = off;
@@ -541,6 +620,7 @@ eecmg_status eecmg_plan(int width, int height, int levels, const double* psf, in
     for (int i = 0; i < eecmg_plan_s::NVEC; ++i) P->vec[i] = (float*)(P->ws + vec_off[i]);
     P->dtaps = (Taps*)(P->ws + taps_off);
     P->sc = (Scalars*)(P->ws + sc_off);
+    P->gsync = (GroupSync*)(P->ws + gs_off);
     P->partials = (double*)(P->ws + part_off);
     P->max_blocks = max_blocks;
     auto cleanup = [&](cudaError_t err, const char* what) {
@@ -564,7 +644,7 @@ eecmg_status eecmg_plan_destroy(eecmg_plan_t P) {
     cudaDeviceSynchronize();
     if (P->gexec) cudaGraphExecDestroy(P->gexec);
     if (P->cap_stream) cudaStreamDestroy(P->cap_stream);
-    prof_flush(P->prof);
+    prof_flush(P);
     for (cudaEvent_t e : P->prof.free_events) cudaEventDestroy(e);
     cudaFree(P->ws);
     delete P;
@@ -717,7 +797,7 @@ eecmg_status eecmg_level_solve(eecmg_plan_t P, int level, const float* g, float*
 
 eecmg_status eecmg_plan_profile(eecmg_plan_t P, int enable) {
     if (!P) return set_error(EECMG_ERR_INVALID_ARG, "eecmg_plan_profile: NULL plan");
-    CK(prof_flush(P->prof));
+    CK(prof_flush(P));
     P->prof.on = enable != 0;
     for (int c = 0; c < KC_COUNT; ++c) {
         P->prof.ms[c] = 0.0;
@@ -729,9 +809,10 @@ eecmg_status eecmg_plan_profile(eecmg_plan_t P, int enable) {
 
 eecmg_status eecmg_plan_profile_read(eecmg_plan_t P, eecmg_kernel_stat* out, int max, int* n) {
     static const char* names[KC_COUNT] = {"conv", "mr_b", "mr_final", "cg_step", "cg_p",
-                                          "restrict", "prolong", "smooth", "denoise", "copy"};
+                                          "restrict", "prolong", "smooth", "denoise", "copy",
+                                          "level_solve"};
     if (!P || !n) return set_error(EECMG_ERR_INVALID_ARG, "eecmg_plan_profile_read: NULL argument");
-    CK(prof_flush(P->prof));
+    CK(prof_flush(P));
     int k = 0;
     for (int c = 0; c < KC_COUNT; ++c) {
         if (out && k < max) {

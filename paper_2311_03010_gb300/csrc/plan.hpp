@@ -5,6 +5,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "persistent.cuh"
 
 namespace eecmg {
 
@@ -21,7 +22,7 @@ struct LevelPlan {
 // Kernel classes of the optional per-launch profiler.
 enum KernelClass : int {
     KC_CONV = 0, KC_MR_B, KC_MR_FINAL, KC_CG_STEP, KC_CG_P, KC_RESTRICT, KC_PROLONG,
-    KC_SMOOTH, KC_DENOISE, KC_COPY, KC_COUNT
+    KC_SMOOTH, KC_DENOISE, KC_COPY, KC_LEVEL, KC_COUNT
 };
 
 // Eager-mode profiler: an event pair around every launch of a restoration,
@@ -32,6 +33,7 @@ struct Profiler {
         int cls;
         double bytes;
         cudaEvent_t e0, e1;
+        int level = -1;   // persistent level solve: bytes counted from the iterations run
     };
     std::vector<Rec> recs;
     std::vector<cudaEvent_t> free_events;
@@ -57,6 +59,7 @@ struct eecmg_plan_s {
     size_t max_blocks = 0;
     eecmg::Taps* dtaps = nullptr;     // [2l] = H_l, [2l+1] = H_l^T
     eecmg::Scalars* sc = nullptr;     // one per level
+    eecmg::GroupSync* gsync = nullptr; // one per level (persistent solves)
     double* partials = nullptr;
     static constexpr int NVEC = 9;
     float* vec[NVEC] = {};              // solver vectors, each max level size

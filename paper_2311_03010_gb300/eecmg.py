@@ -51,6 +51,7 @@ class eecmg_options(ctypes.Structure):
         ("prolong", ctypes.c_int),
         ("use_graph", ctypes.c_int),
         ("precise_conv", ctypes.c_int),
+        ("persistent", ctypes.c_int),
     ]
 
 

@@ -42,7 +42,7 @@ def test_version_and_defaults(lib):
     o = lib.eecmg_default_options()
     assert (o.smoother, o.coarse_op, o.storage, o.stop) == (0, 0, 0, 0)
     assert (o.c, o.delta, o.diffusion_steps, o.s_scale) == (1.1, 0.0, 1, 1.0)
-    assert o.conv_tol == 1e-5 and o.prolong == 0 and o.use_graph == 1 and o.precise_conv == 1
+    assert o.conv_tol == 1e-5 and o.prolong == 0 and o.use_graph == 1 and o.precise_conv == 1 and o.persistent == 1
 
 
 @pytest.mark.parametrize("args,status", [

@@ -31,10 +31,11 @@ def gpu():
     return require_gpu()
 
 
+@pytest.mark.parametrize("persistent", [1, 0])
 @pytest.mark.parametrize("smoother", ["mr2", "cgls"])
 @pytest.mark.parametrize("psfname", ["gauss", "motion"])
 @pytest.mark.parametrize("shape", [(33, 65), (128, 128), (1, 1), (2, 3)])
-def test_level_solve(gpu, orc, smoother, psfname, shape):
+def test_level_solve(gpu, orc, smoother, psfname, shape, persistent):
     torch, E = gpu
     from paper_2311_03010_gb300 import synth
 
@@ -44,7 +45,7 @@ def test_level_solve(gpu, orc, smoother, psfname, shape):
     u_true = synth.synthetic_image(h, w, 61) if h * w > 16 else rng.uniform(0, 255, shape)
     g = (orc.apply_H(psf, u_true) + rng.normal(0, 1.0, shape)).astype(np.float32)
     u0 = rng.uniform(0, 255, shape).astype(np.float32)
-    plan = E.Plan(w, h, 1, psf, smoother=smoother)
+    plan = E.Plan(w, h, 1, psf, smoother=smoother, persistent=persistent)
     for m in ((1, 2) if h * w < 16 else (1, 2, 5, 12)):
         ud = dev(torch, u0)
         E.eecmg_level_solve(plan.handle, 0, dev(torch, g), ud, m)
@@ -116,12 +117,14 @@ def check_borderline_stops(orc, g64, L, psf, it, rit, sched, okw):
     assert abs(r_k / lim - 1.0) <= 0.05, (first, r_k, lim)
 
 
+@pytest.mark.parametrize("persistent", [1, 0])
 @pytest.mark.parametrize("name", ["cfg1", "cfg2_1pct", "cfg2_5pct", "rect_motion", "odd_gauss"])
 @pytest.mark.parametrize("smoother", ["mr2", "cgls"])
-def test_cascade_matches_oracle(gpu, orc, name, smoother):
+def test_cascade_matches_oracle(gpu, orc, name, smoother, persistent):
     torch, E = gpu
     p, L = _cascade_case(name)
-    it, rit, err, dpsnr, _ = check_cascade(torch, E, orc, p, L, smoother=smoother)
+    it, rit, err, dpsnr, _ = check_cascade(torch, E, orc, p, L, smoother=smoother,
+                                           persistent=persistent)
     assert it == rit
     assert err <= FP32_REL, err
     assert dpsnr <= FP32_DPSNR, dpsnr
@@ -164,7 +167,7 @@ def test_graph_eager_deterministic(gpu):
     gd = dev(torch, p.g)
     outs = []
     for use_graph in (1, 0):
-        plan = E.Plan(w, h, L, p.psf, use_graph=use_graph)
+        plan = E.Plan(w, h, L, p.psf, use_graph=use_graph, persistent=1)
         for _ in range(2):
             ud = torch.empty_like(gd)
             plan.restore(gd, ud)
