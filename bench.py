@@ -44,21 +44,28 @@ WORKLOADS = {
     "2048x2048-gauss3-L5": (2048, 2048, 5, ("gauss", 3.0, 10), (0.01,), 3000, (3001,)),
     "4096x4096-gauss3-L5": (4096, 4096, 5, ("gauss", 3.0, 10), (0.01,), 3001, (3002,)),
     "2048x2048-motion15-L5": (2048, 2048, 5, ("motion", 15, 30.0), (0.01,), 3000, (3001,)),
+    # 64 images, sides 128..1536 (square or 3:4), Gaussian or motion PSFs, 0.5-5 % noise
+    "batch64-uneven-L5": None,
 }
 DEFAULT_WORKLOAD = "512x512-gauss2.5-L5"
 
 
-def make_inputs(name):
+def make_problems(name):
+    """List of (clean image, PSF, levels, g FP32) for the workload."""
     from paper_2311_03010_gb300 import synth
 
+    if name == "batch64-uneven-L5":
+        out = []
+        for spec in synth.batch_specs(64, 4000):
+            psf = synth.psf_from_spec(spec["psf"])
+            u = synth.synthetic_image(spec["h"], spec["w"], spec["seed"])
+            g, _ = synth.degrade(u, psf, spec["v"], spec["seed"] + 1)
+            out.append((u, psf, 5, g))
+        return out
     h, w, L, spec, vs, seed, nseeds = WORKLOADS[name]
     psf = synth.psf_from_spec(spec)
     u = synth.synthetic_image(h, w, seed, texture=(h * w > 4096))
-    probs = []
-    for v, ns in zip(vs, nseeds):
-        g, delta = synth.degrade(u, psf, v, ns)
-        probs.append((g, delta))
-    return u, psf, L, probs
+    return [(u, psf, L, synth.degrade(u, psf, v, ns)[0]) for v, ns in zip(vs, nseeds)]
 
 
 def peaks():
@@ -124,14 +131,14 @@ def cpu_baseline(name, max_seconds=12.0):
     """The FP64 oracle on a bounded sample: whole images of the workload, repeated."""
     import oracle
 
-    u, psf, L, probs = make_inputs(name)
+    probs = make_problems(name)
     threads = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
     oracle.set_threads(threads)
     px = 0
     t0 = time.perf_counter()
     n = 0
     while True:
-        g, _ = probs[n % len(probs)]
+        _, psf, L, g = probs[n % len(probs)]
         oracle.cascade(g.astype(np.float64), L, psf)
         px += g.size
         n += 1
@@ -148,28 +155,30 @@ def run_reference(args, rank, world):
     if rank != 0:
         return
     name = args.workload
-    u, psf, L, probs = make_inputs(name)
+    probs = make_problems(name)
     import oracle
 
     threads = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
     oracle.set_threads(threads)
-    step = lambda: [oracle.cascade(g.astype(np.float64), L, psf) for (g, _) in probs]
+    # one step = a bounded sample: at most 2 whole restorations of the workload's images
+    sample = probs[:2]
+    step = lambda: [oracle.cascade(g.astype(np.float64), L, psf) for (_, psf, L, g) in sample]
     for _ in range(args.warmup):
         step()
     t0 = time.perf_counter()
     for _ in range(args.steps):
         step()
     dt = time.perf_counter() - t0
-    px = sum(g.size for (g, _) in probs) * args.steps
+    px = sum(g.size for (_, _, _, g) in sample) * args.steps
     val = px / dt / 1e6
     print(json.dumps({
         "impl": "reference", "metric": "Mpixel/s restored (EECMG, oracle-matched)", "value": val,
         "unit": "Mpixel/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": name, "images_per_step": len(probs)},
+        "config": {"workload": name, "images_per_step": len(sample)},
         "cpu_baseline": {"value": val, "unit": "Mpixel/s", "cores": threads, "kind": "oracle",
-                         "sample": f"{args.steps} steps of {len(probs)} whole restorations"},
+                         "sample": f"{args.steps} steps of {len(sample)} whole restorations"},
         "e2e": {"value": val, "unit": "Mpixel/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }), flush=True)
@@ -211,12 +220,16 @@ def main():
     eecmg.load()
 
     name = args.workload
-    u_clean, psf, L, probs = make_inputs(name)
-    h, w = probs[0][0].shape
+    probs = make_problems(name)
     stream = torch.cuda.current_stream()
-    plans = [eecmg.Plan(w, h, L, psf, smoother=args.smoother, precise_conv=args.precise_conv)
-             for _ in probs]
-    gs = [torch.from_numpy(g).cuda() for (g, _) in probs]
+    plans = []
+    for (_, psf, L, g) in probs:
+        h, w = g.shape
+        smo = args.smoother
+        if smo == "mr2" and not np.allclose(psf, psf[::-1, ::-1], rtol=0, atol=1e-15):
+            smo = "cgls"
+        plans.append(eecmg.Plan(w, h, L, psf, smoother=smo, precise_conv=args.precise_conv))
+    gs = [torch.from_numpy(g).cuda() for (_, _, _, g) in probs]
     us = [torch.empty_like(g) for g in gs]
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
@@ -254,13 +267,33 @@ def main():
     px_step = sum(g.numel() for g in gs)
     value = px_step * args.steps * world / (tot_ms / 1e3) / 1e6
 
+    # the plain per-image loop on the same plans (for the batched workload)
+    loop_value = None
+    if len(plans) > 2:
+        for p, g, u in zip(plans, gs, us):
+            p.restore(g, u, stream)
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        loop_steps = max(3, args.steps // 4)
+        loop_ms = 0.0
+        for _ in range(loop_steps):
+            flush.zero_()
+            e0.record(stream)
+            for p, g, u in zip(plans, gs, us):
+                p.restore(g, u, stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            loop_ms += e0.elapsed_time(e1)
+        loop_value = px_step * loop_steps / (loop_ms / 1e3) / 1e6
+
     # parity of this run's output against the oracle (first image, rank 0 only)
     parity = None
     if rank == 0 and not args.no_cpu_baseline:
         import oracle
 
+        u_clean, psf0, L0, g0 = probs[0]
         oracle.set_threads(len(os.sched_getaffinity(0)))
-        ref, _, _ = oracle.cascade(probs[0][0].astype(np.float64), L, psf, smoother=args.smoother)
+        ref, _, _ = oracle.cascade(g0.astype(np.float64), L0, psf0, smoother=args.smoother)
         got = us[0].double().cpu().numpy()
         parity = {"rel_l2": float(np.linalg.norm(got - ref) / np.linalg.norm(ref)),
                   "dpsnr_db": float(abs(oracle.psnr(u_clean, got) - oracle.psnr(u_clean, ref))),
@@ -268,7 +301,7 @@ def main():
         oracle.set_threads(1)
 
     # end to end through the public host-buffer entry point (pinned memory)
-    gh = [torch.from_numpy(g).pin_memory() for (g, _) in probs]
+    gh = [torch.from_numpy(g).pin_memory() for (_, _, _, g) in probs]
     uh = [torch.empty_like(x).pin_memory() for x in gh]
     for p, a, b in zip(plans, gh, uh):
         eecmg.eecmg_restore_host(p.handle, a.data_ptr(), b.data_ptr(), stream)
@@ -282,13 +315,15 @@ def main():
     e2e_s = time.perf_counter() - t0
     e2e_val = px_step * e2e_steps * world / e2e_s / 1e6
 
-    # profiled eager replay of the same steps: per-kernel-class event times
-    prof_steps = min(args.steps, 20)
+    # profiled eager replay of the same restorations (one plan at a time):
+    # per-kernel-class event times
+    prof_steps = min(args.steps, 20) if len(plans) <= 2 else 1
     for p in plans:
         eecmg.eecmg_plan_profile(p.handle, 1)
     for _ in range(prof_steps):
         flush.zero_()
-        step()
+        for p, g, u in zip(plans, gs, us):
+            p.restore(g, u, stream)
     barrier()
     classes = {}
     for p in plans:
@@ -329,6 +364,7 @@ def main():
             "kernel_classes_ms_per_step": {k: v["ms"] / prof_steps for k, v in classes.items()
                                            if v["launches"]},
             "clocks": clk,
+            "per_image_loop_value": loop_value,
             "parity": parity,
             "cpu_baseline": cpu,
         }

@@ -160,10 +160,16 @@ eecmg_status eecmg_restore_host(eecmg_plan_t plan, const float *g_host, float *u
                                 cudaStream_t stream);
 
 /*
- * Restores n images with their own plans (sizes and PSFs may differ) as one
- * batch: per cascade step, one fused launch covers every image.
- * plans[i], g[i] (device), u[i] (device).  The plans must be distinct.
- * Asynchronous on `stream`.  Errors: INVALID_ARG, CUDA.
+ * Restores n images with their own plans (sizes, PSFs, levels and options
+ * may differ) as one batch: per cascade step (levels counted from the
+ * coarsest), one persistent cooperative launch per kind of level solver
+ * covers every image, each image's solve owning its own block range.
+ * plans[i], g[i] (device), u[i] (device); the plans must be distinct, use
+ * the persistent level solve and not be profiling.  The first call with a
+ * given set of plans builds device job tables and a CUDA graph for it (an
+ * allocation; make it before any stream capture); later calls replay it.
+ * Destroying any of the plans drops the cached batch.  Asynchronous on
+ * `stream`.  Errors: INVALID_ARG, OOM, CUDA.
  */
 eecmg_status eecmg_restore_batched(const eecmg_plan_t *plans, const float *const *g,
                                    float *const *u, int n, cudaStream_t stream);

@@ -1,0 +1,273 @@
+// batch.cu -- batched restoration: many images of different sizes and PSFs,
+// one persistent cooperative launch per cascade step covering all of them.
+//
+// Each image keeps its own plan (workspace, level pyramid, scalars).  Per
+// cascade step s (levels counted from the coarsest, so every image's level s
+// is at the same depth of Algorithm 2), the level solves of all images are
+// jobs of one cooperative grid: image i's job owns a range of blocks with its
+// own group barrier, reduction partials and scalars, so the images never
+// wait for one another inside the launch.  Jobs are grouped by solver,
+// separability and precision (one kernel instantiation each) and, within a
+// group, share the largest PSF radius (smaller PSFs are zero-padded).  The
+// restriction and the per-image prolongation kernels run before each step.
+// The whole batch is captured once as a CUDA graph per set of plans and
+// replayed; inputs are copied into the plans' workspaces outside the graph.
+#include <algorithm>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "launch.hpp"
+#include "level_solve.hpp"
+#include "plan.hpp"
+
+namespace eecmg {
+
+namespace {
+
+struct Wave {
+    const LevelJob* d_jobs = nullptr;
+    const unsigned short* d_block_job = nullptr;
+    int njobs = 0, blocks = 0, rt = 0, sep = 0, prec = 0, cgls = 0;
+};
+
+struct BatchCtx {
+    std::vector<eecmg_plan_s*> plans;
+    std::vector<std::vector<Wave>> steps;  // per cascade step
+    void* dmem = nullptr;
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    ~BatchCtx() {
+        if (gexec) cudaGraphExecDestroy(gexec);
+        if (cap_stream) cudaStreamDestroy(cap_stream);
+        if (dmem) cudaFree(dmem);
+    }
+};
+
+std::mutex g_batch_mu;
+std::map<std::vector<eecmg_plan_s*>, std::unique_ptr<BatchCtx>> g_batches;
+
+LevelJob make_job(eecmg_plan_s* P, int l) {
+    LevelPlan& L = P->lv[l];
+    LevelJob J;
+    J.g = L.g;
+    J.u = L.u;
+    for (int i = 0; i < 2; ++i) {
+        J.v[i] = P->vec[0 + i];
+        J.aw[i] = P->vec[2 + i];
+        J.d[i] = P->vec[4 + i];
+        J.hd[i] = P->vec[6 + i];
+    }
+    J.r = P->vec[8];
+    J.taps = P->dtaps + 2 * l;
+    J.tapsT = P->dtaps + 2 * l + 1;
+    J.sc = P->sc + l;
+    J.partials = P->partials;
+    J.gs = P->gsync + l;
+    J.conv_tol2 = P->conv_tol2;
+    J.disc2 = L.disc2;
+    J.h = L.h;
+    J.w = L.w;
+    J.m = L.m;
+    const int nzero = P->opt.prolong == EECMG_PROLONG_EECMG ? 2 : 1;
+    J.zero_start = l < nzero ? 1 : 0;
+    return J;
+}
+
+// Builds the job tables of every step (one device allocation).
+eecmg_status build_ctx(BatchCtx& C) {
+    int maxL = 0;
+    for (auto* P : C.plans) maxL = std::max(maxL, P->L);
+    struct HostWave {
+        std::vector<LevelJob> jobs;
+        std::vector<unsigned short> block_job;
+        int blocks = 0, rt = 0, sep = 0, prec = 0, cgls = 0;
+    };
+    std::vector<std::vector<HostWave>> hsteps(maxL);
+    for (int s = 0; s < maxL; ++s) {
+        // group key -> indices of plans
+        std::map<std::tuple<int, int, int>, std::vector<int>> groups;
+        for (int i = 0; i < (int)C.plans.size(); ++i) {
+            eecmg_plan_s* P = C.plans[i];
+            if (s >= P->L) continue;
+            const int cg = P->opt.smoother == EECMG_SMOOTHER_CGLS ? 1 : 0;
+            groups[{cg, P->lv[s].sepH, P->opt.precise_conv}].push_back(i);
+        }
+        for (auto& kv : groups) {
+            const int cg = std::get<0>(kv.first), sep = std::get<1>(kv.first),
+                      prec = std::get<2>(kv.first);
+            int rt = 0;
+            for (int i : kv.second) rt = std::max(rt, C.plans[i]->lv[s].rt);
+            const int cap = level_capacity(rt, sep, prec, cg);
+            if (cap <= 0) return set_error(EECMG_ERR_CUDA, "eecmg_restore_batched: occupancy query failed");
+            // blocks per job: the same count as the job's solve alone (so the
+            // result is bitwise the same); jobs that do not fit start a new wave
+            std::vector<int> want;
+            for (int i : kv.second)
+                want.push_back(std::min(cap, level_want_blocks(C.plans[i]->lv[s].h, C.plans[i]->lv[s].w)));
+            HostWave cur;
+            cur.rt = rt;
+            cur.sep = sep;
+            cur.prec = prec;
+            cur.cgls = cg;
+            for (size_t k = 0; k < kv.second.size(); ++k) {
+                const int nb = std::max(1, want[k]);
+                if (cur.blocks + nb > cap && !cur.jobs.empty()) {  // next wave
+                    hsteps[s].push_back(cur);
+                    cur.jobs.clear();
+                    cur.block_job.clear();
+                    cur.blocks = 0;
+                }
+                LevelJob J = make_job(C.plans[kv.second[k]], s);
+                J.block0 = cur.blocks;
+                J.nblocks = nb;
+                for (int b = 0; b < nb; ++b) cur.block_job.push_back((unsigned short)cur.jobs.size());
+                cur.jobs.push_back(J);
+                cur.blocks += nb;
+            }
+            if (!cur.jobs.empty()) hsteps[s].push_back(cur);
+        }
+    }
+    size_t bytes = 0;
+    for (auto& st : hsteps)
+        for (auto& w : st) {
+            bytes += (sizeof(LevelJob) * w.jobs.size() + 255) / 256 * 256;
+            bytes += (sizeof(unsigned short) * w.block_job.size() + 255) / 256 * 256;
+        }
+    cudaError_t e = cudaMalloc(&C.dmem, bytes ? bytes : 256);
+    if (e != cudaSuccess) return set_error(EECMG_ERR_OOM, "eecmg_restore_batched: job tables");
+    char* p = (char*)C.dmem;
+    C.steps.assign(maxL, {});
+    for (int s = 0; s < maxL; ++s)
+        for (auto& w : hsteps[s]) {
+            Wave dw;
+            dw.d_jobs = (const LevelJob*)p;
+            e = cudaMemcpy(p, w.jobs.data(), sizeof(LevelJob) * w.jobs.size(), cudaMemcpyHostToDevice);
+            p += (sizeof(LevelJob) * w.jobs.size() + 255) / 256 * 256;
+            dw.d_block_job = (const unsigned short*)p;
+            if (e == cudaSuccess)
+                e = cudaMemcpy(p, w.block_job.data(), sizeof(unsigned short) * w.block_job.size(),
+                               cudaMemcpyHostToDevice);
+            p += (sizeof(unsigned short) * w.block_job.size() + 255) / 256 * 256;
+            if (e != cudaSuccess) return set_error(EECMG_ERR_CUDA, "eecmg_restore_batched: job upload");
+            dw.njobs = (int)w.jobs.size();
+            dw.blocks = w.blocks;
+            dw.rt = w.rt;
+            dw.sep = w.sep;
+            dw.prec = w.prec;
+            dw.cgls = w.cgls;
+            C.steps[s].push_back(dw);
+        }
+    e = cudaStreamCreateWithFlags(&C.cap_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return set_error(EECMG_ERR_CUDA, "eecmg_restore_batched: stream");
+    return EECMG_OK;
+}
+
+#define BCK(call)                                                                              \
+    do {                                                                                       \
+        cudaError_t e_ = (call);                                                               \
+        if (e_ != cudaSuccess)                                                                 \
+            return set_error(EECMG_ERR_CUDA, std::string("eecmg_restore_batched: ") + #call + \
+                                                 ": " + cudaGetErrorString(e_));               \
+    } while (0)
+
+eecmg_status enqueue_batch(BatchCtx& C, cudaStream_t s) {
+    for (auto* P : C.plans)
+        for (int l = P->L - 1; l > 0; --l)
+            BCK(launch_restrict(P->lv[l].g, P->lv[l].h, P->lv[l].w, P->lv[l - 1].g, P->lv[l - 1].h,
+                                P->lv[l - 1].w, s));
+    for (int st = 0; st < (int)C.steps.size(); ++st) {
+        for (auto* P : C.plans) {
+            if (st >= P->L) continue;
+            const int nzero = P->opt.prolong == EECMG_PROLONG_EECMG ? 2 : 1;
+            if (st < nzero) {
+                BCK(cudaMemsetAsync(P->lv[st].u, 0, sizeof(float) * P->lv[st].h * P->lv[st].w, s));
+            } else {
+                eecmg_status r = prolong_enqueue(P, st, s);
+                if (r != EECMG_OK) return r;
+            }
+        }
+        for (auto& w : C.steps[st])
+            BCK(launch_level_batch(w.d_jobs, w.d_block_job, w.njobs, w.blocks, w.rt, w.sep, w.prec,
+                                   w.cgls, s));
+    }
+    return EECMG_OK;
+}
+
+}  // namespace
+
+eecmg_status restore_batched_impl(const eecmg_plan_t* plans, const float* const* g, float* const* u,
+                                  int n, cudaStream_t s) {
+    std::vector<eecmg_plan_s*> key(plans, plans + n);
+    {
+        std::vector<eecmg_plan_s*> sorted = key;
+        std::sort(sorted.begin(), sorted.end());
+        if (std::adjacent_find(sorted.begin(), sorted.end()) != sorted.end())
+            return set_error(EECMG_ERR_INVALID_ARG, "eecmg_restore_batched: plans must be distinct");
+    }
+    for (int i = 0; i < n; ++i) {
+        if (!plans[i] || !g[i] || !u[i])
+            return set_error(EECMG_ERR_INVALID_ARG, "eecmg_restore_batched: NULL plan or buffer");
+        if (!plans[i]->opt.persistent)
+            return set_error(EECMG_ERR_INVALID_ARG,
+                             "eecmg_restore_batched: plans must use the persistent level solve");
+    }
+    std::lock_guard<std::mutex> lock(g_batch_mu);
+    auto it = g_batches.find(key);
+    if (it == g_batches.end()) {
+        auto C = std::make_unique<BatchCtx>();
+        C->plans = key;
+        eecmg_status st = build_ctx(*C);
+        if (st != EECMG_OK) return st;
+        it = g_batches.emplace(key, std::move(C)).first;
+    }
+    BatchCtx& C = *it->second;
+    for (int i = 0; i < n; ++i) {
+        eecmg_plan_s* P = plans[i];
+        LevelPlan& F = P->lv[P->L - 1];
+        if (g[i] != F.g)
+            BCK(cudaMemcpyAsync(F.g, g[i], sizeof(float) * P->W * P->H, cudaMemcpyDeviceToDevice, s));
+    }
+    if (!C.gexec) {
+        BCK(cudaStreamBeginCapture(C.cap_stream, cudaStreamCaptureModeThreadLocal));
+        eecmg_status st = enqueue_batch(C, C.cap_stream);
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamEndCapture(C.cap_stream, &graph);
+        if (st != EECMG_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return st;
+        }
+        if (e != cudaSuccess)
+            return set_error(EECMG_ERR_CUDA, std::string("eecmg_restore_batched: capture: ") + cudaGetErrorString(e));
+        e = cudaGraphInstantiate(&C.gexec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            C.gexec = nullptr;
+            return set_error(EECMG_ERR_CUDA, std::string("eecmg_restore_batched: instantiate: ") + cudaGetErrorString(e));
+        }
+    }
+    BCK(cudaGraphLaunch(C.gexec, s));
+    for (int i = 0; i < n; ++i) {
+        eecmg_plan_s* P = plans[i];
+        LevelPlan& F = P->lv[P->L - 1];
+        if (u[i] != F.u)
+            BCK(cudaMemcpyAsync(u[i], F.u, sizeof(float) * P->W * P->H, cudaMemcpyDeviceToDevice, s));
+        P->last_stream = s;
+    }
+    return EECMG_OK;
+}
+
+// A destroyed plan invalidates every cached batch that contains it.
+void forget_plan_batches(eecmg_plan_s* P) {
+    std::lock_guard<std::mutex> lock(g_batch_mu);
+    for (auto it = g_batches.begin(); it != g_batches.end();) {
+        if (std::find(it->first.begin(), it->first.end(), P) != it->first.end())
+            it = g_batches.erase(it);
+        else
+            ++it;
+    }
+}
+
+}  // namespace eecmg

@@ -56,6 +56,12 @@ struct alignas(64) Scalars {
     double gamma;         // <s, s>
     double qq;            // <q, q>
     double cg_alpha, beta;
+    // FP32 coefficients for the vector phases, rounded once from the FP64
+    // scalars by the thread that updates them (no FP64 work per element)
+    float f_scale;        // 1 / ||v_k||            (H w_k = f_scale * H v_k)
+    float f_ca, f_cb;     // alpha_k / ||v_k||, ||v_k|| / ||v_{k-1}||
+    float f_dw, f_d1, f_d2, f_dinv, f_tau;  // pending step
+    float f_cg_alpha, f_beta;
 };
 
 constexpr int NTHREADS = 256;
@@ -135,5 +141,25 @@ __device__ __forceinline__ void grid_total(const double* partials, unsigned int 
 }
 
 __device__ __forceinline__ bool finite_pos(double x) { return x > 0.0 && x < 1.0e300; }
+
+// float4 helpers (vectors are 256-byte aligned; index q addresses pixels 4q..4q+3)
+__device__ __forceinline__ float4 ld4cg(const float* p, size_t q) {
+    return __ldcg(reinterpret_cast<const float4*>(p) + q);
+}
+__device__ __forceinline__ void st4(float* p, size_t q, float4 v) {
+    reinterpret_cast<float4*>(p)[q] = v;
+}
+__device__ __forceinline__ float4 fma4(float a, float4 x, float4 y) {
+    return make_float4(fmaf(a, x.x, y.x), fmaf(a, x.y, y.y), fmaf(a, x.z, y.z), fmaf(a, x.w, y.w));
+}
+__device__ __forceinline__ float4 mul4(float a, float4 x) {
+    return make_float4(a * x.x, a * x.y, a * x.z, a * x.w);
+}
+__device__ __forceinline__ float dot4(float4 a, float4 b, float acc) {
+    acc = fmaf(a.x, b.x, acc);
+    acc = fmaf(a.y, b.y, acc);
+    acc = fmaf(a.z, b.z, acc);
+    return fmaf(a.w, b.w, acc);
+}
 
 }  // namespace eecmg

@@ -32,14 +32,19 @@ struct ConvSmem {
     int ntap;
 };
 
-// Stages the level's taps (call once per kernel, then __syncthreads()).
+// Stages the level's taps (then __syncthreads()).  The kernel radius R may
+// exceed the taps' own radius (a batched launch uses the largest radius of
+// its jobs): separable factors are placed centred and padded with zeros.
 template <int R, bool SEP>
 __device__ __forceinline__ void conv_stage_taps(ConvSmem<R, SEP>& S, const Taps* taps) {
     const int tid = threadIdx.x;
     if (SEP) {
+        const int rt = taps->rt;
         for (int d = tid; d < 2 * R + 1; d += NTHREADS) {
-            S.cy[d] = taps->cy[d];
-            S.cx[d] = taps->cx[d];
+            const int e = d - R + rt;
+            const bool in = e >= 0 && e <= 2 * rt;
+            S.cy[d] = in ? taps->cy[e] : 0.f;
+            S.cx[d] = in ? taps->cx[e] : 0.f;
         }
     } else {
         const int nt = taps->ntap;

@@ -38,6 +38,7 @@ __device__ __forceinline__ void fin_mr_v1(Scalars* sc, double vv, double vr) {
         sc->nrm = nrm;
         sc->nrm_prev = 0.0;
         sc->phi = vr / nrm;
+        sc->f_scale = (float)(1.0 / nrm);
         sc->cs1 = 1.0;
         sc->sn1 = 0.0;
         sc->cs2 = 1.0;
@@ -47,8 +48,12 @@ __device__ __forceinline__ void fin_mr_v1(Scalars* sc, double vv, double vr) {
 
 // alpha_k = <H w_k, w_k> from <H w_k, v_k>.
 __device__ __forceinline__ void fin_mr_a(Scalars* sc, double hv) {
-    sc->alpha = hv / sc->nrm;
+    const double alpha = hv / sc->nrm;
+    sc->alpha = alpha;
     sc->loops += 1;
+    // phase B of this iteration: v_{k+1} = H w_k - (alpha/||v_k||) v_k - (||v_k||/||v_{k-1}||) v_{k-1}
+    sc->f_ca = (float)(alpha / sc->nrm);
+    sc->f_cb = sc->nrm_prev > 0.0 ? (float)(sc->nrm / sc->nrm_prev) : 0.f;
 }
 
 // MR-II phase B of iteration k: rr = ||r_{k-1}||^2 (k >= 2), vv = ||v_{k+1}||^2,
@@ -102,6 +107,12 @@ __device__ __forceinline__ void fin_mr_b(Scalars* sc, int k, double rr, double v
     sc->nrm_prev = sc->nrm;
     sc->nrm = nrm_new;
     sc->iters = k;
+    sc->f_dw = (float)sc->dw;
+    sc->f_d1 = (float)sc->d1;
+    sc->f_d2 = (float)sc->d2;
+    sc->f_dinv = (float)inv_rho;
+    sc->f_tau = (float)sc->tau;
+    sc->f_scale = nrm_new > 0.0 ? (float)(1.0 / nrm_new) : 0.f;
     if (!(nrm_new > 0.0)) sc->stopped = 4;  // Krylov space exhausted: step k is the last
 }
 
@@ -127,6 +138,7 @@ __device__ __forceinline__ void fin_cg_q(Scalars* sc, double qq) {
     } else {
         sc->qq = qq;
         sc->cg_alpha = sc->gamma / qq;
+        sc->f_cg_alpha = (float)sc->cg_alpha;
         sc->iters += 1;
     }
 }
@@ -141,6 +153,7 @@ __device__ __forceinline__ void fin_cg_step(Scalars* sc, double rr) {
 // CGLS: s = H^T r, beta = <s, s> / gamma.
 __device__ __forceinline__ void fin_cg_s(Scalars* sc, double gn) {
     sc->beta = gn / sc->gamma;
+    sc->f_beta = (float)sc->beta;
     sc->gamma = gn;
     if (!(gn < 1.0e300)) sc->stopped = 3;
     else if (!(gn > 0.0)) sc->stopped = 2;

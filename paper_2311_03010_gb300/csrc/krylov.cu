@@ -58,10 +58,9 @@ __global__ void __launch_bounds__(NTHREADS)
     k_mr_b(MrVecs V, int k, size_t n, Scalars* sc, double* partials) {
     if (*(volatile int*)&sc->stopped) return;
     const bool step = k >= 2;  // step k-1 is pending
-    const float dw = (float)sc->dw, d1 = (float)sc->d1, d2 = (float)sc->d2;
-    const float dinv = (float)sc->dinv, tau = (float)sc->tau;
-    const float ca = (float)(sc->alpha / sc->nrm);                  // alpha_k / ||v_k||
-    const float cb = step ? (float)(sc->nrm / sc->nrm_prev) : 0.f;  // ||v_k|| / ||v_{k-1}||
+    const float dw = sc->f_dw, d1 = sc->f_d1, d2 = sc->f_d2, dinv = sc->f_dinv, tau = sc->f_tau;
+    const float ca = sc->f_ca;               // alpha_k / ||v_k||
+    const float cb = step ? sc->f_cb : 0.f;  // ||v_k|| / ||v_{k-1}||
     const int sk = k & 1, sk1 = sk ^ 1;
     float arr = 0.f, avv = 0.f, avr = 0.f;
     const size_t base = (size_t)blockIdx.x * EW_PER_BLOCK + threadIdx.x;
@@ -96,8 +95,7 @@ __global__ void __launch_bounds__(NTHREADS)
     if (st != 0 && st != 4) return;
     const int j = sc->iters;
     if (j < 1) return;
-    const float dw = (float)sc->dw, d1 = (float)sc->d1, d2 = (float)sc->d2;
-    const float dinv = (float)sc->dinv, tau = (float)sc->tau;
+    const float dw = sc->f_dw, d1 = sc->f_d1, d2 = sc->f_d2, dinv = sc->f_dinv, tau = sc->f_tau;
     float arr = 0.f;
     const size_t base = (size_t)blockIdx.x * EW_PER_BLOCK + threadIdx.x;
 #pragma unroll
@@ -122,7 +120,7 @@ __global__ void __launch_bounds__(NTHREADS)
     k_cg_step(float* __restrict__ u, const float* __restrict__ p, float* __restrict__ r,
               const float* __restrict__ q, size_t n, Scalars* sc, double* partials) {
     if (*(volatile int*)&sc->stopped) return;
-    const float a = (float)sc->cg_alpha;
+    const float a = sc->f_cg_alpha;
     float arr = 0.f;
     const size_t base = (size_t)blockIdx.x * EW_PER_BLOCK + threadIdx.x;
 #pragma unroll
@@ -147,7 +145,7 @@ __global__ void __launch_bounds__(NTHREADS)
 __global__ void __launch_bounds__(NTHREADS)
     k_cg_p(float* __restrict__ p, const float* __restrict__ s, size_t n, Scalars* sc) {
     if (*(volatile int*)&sc->stopped) return;
-    const float b = (float)sc->beta;
+    const float b = sc->f_beta;
     const size_t base = (size_t)blockIdx.x * EW_PER_BLOCK + threadIdx.x;
 #pragma unroll
     for (int j = 0; j < 8; ++j) {

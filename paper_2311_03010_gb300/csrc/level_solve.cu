@@ -4,19 +4,62 @@
 
 namespace eecmg {
 
+namespace {
+
+cudaError_t dispatch(const LevelLaunch& L, int rt, int sep, int prec, int cgls, int want,
+                     cudaStream_t s, int* used) {
+    if (rt < 0 || rt > RMAX) return cudaErrorInvalidValue;
+    if (cgls)
+        return rt < 6 ? launch_level_cgls_lo(L, rt, sep, prec, want, s, used)
+                      : launch_level_cgls_hi(L, rt, sep, prec, want, s, used);
+    return rt < 6 ? launch_level_mr2_lo(L, rt, sep, prec, want, s, used)
+                  : launch_level_mr2_hi(L, rt, sep, prec, want, s, used);
+}
+
+}  // namespace
+
+// Blocks of a level solve: one per 32 x 64 tile or per 1024 pixels, at most
+// two per SM.  The count depends only on the level's size, so a solve is
+// partitioned (and its reductions rounded) the same way alone or in a batch.
+int level_want_blocks(int h, int w) {
+    static int cap = 0;
+    if (cap == 0) {
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cap = 2 * (sms > 0 ? sms : 1);
+    }
+    const size_t n = (size_t)h * w;
+    const int tiles = (int)conv_blocks(h, w);
+    const int elem = (int)((n + 4 * NTHREADS - 1) / (4 * NTHREADS));
+    const int want = tiles > elem ? tiles : elem;
+    return want < cap ? want : cap;
+}
+
 cudaError_t launch_level_solve(const LevelJob& J, int rt, int sep, int prec, int cgls,
                                cudaStream_t s, int* blocks_used) {
     if (J.h <= 0 || J.w <= 0) return cudaSuccess;
-    const size_t n = (size_t)J.h * J.w;
-    const int tiles = (int)conv_blocks(J.h, J.w);
-    const int elem = (int)((n + 4 * NTHREADS - 1) / (4 * NTHREADS));
-    const int want = tiles > elem ? tiles : elem;
-    if (rt < 0 || rt > RMAX) return cudaErrorInvalidValue;
-    if (cgls)
-        return rt < 6 ? launch_level_cgls_lo(J, rt, sep, prec, want, s, blocks_used)
-                      : launch_level_cgls_hi(J, rt, sep, prec, want, s, blocks_used);
-    return rt < 6 ? launch_level_mr2_lo(J, rt, sep, prec, want, s, blocks_used)
-                  : launch_level_mr2_hi(J, rt, sep, prec, want, s, blocks_used);
+    LevelLaunch L;
+    L.job = J;
+    return dispatch(L, rt, sep, prec, cgls, level_want_blocks(J.h, J.w), s, blocks_used);
+}
+
+cudaError_t launch_level_batch(const LevelJob* d_jobs, const unsigned short* d_block_job, int njobs,
+                               int total_blocks, int rt, int sep, int prec, int cgls,
+                               cudaStream_t s) {
+    if (njobs <= 0 || total_blocks <= 0) return cudaSuccess;
+    LevelLaunch L;
+    L.jobs = d_jobs;
+    L.block_job = d_block_job;
+    L.njobs = njobs;
+    return dispatch(L, rt, sep, prec, cgls, -total_blocks, s, nullptr);
+}
+
+int level_capacity(int rt, int sep, int prec, int cgls) {
+    LevelLaunch L;
+    int cap = 0;
+    if (dispatch(L, rt, sep, prec, cgls, 0, nullptr, &cap) != cudaSuccess) return 0;
+    return cap;
 }
 
 }  // namespace eecmg

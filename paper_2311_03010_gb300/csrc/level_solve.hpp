@@ -23,7 +23,30 @@ struct LevelJob {
     GroupSync* gs = nullptr;
     double conv_tol2 = 0.0, disc2 = 0.0;
     int h = 0, w = 0, m = 0, zero_start = 0;
+    int block0 = 0, nblocks = 0;  // this job's blocks within a batched launch
 };
+
+// Kernel parameter: one job by value, or (jobs != nullptr) a device table of
+// njobs jobs, block b serving job block_job[b].
+struct LevelLaunch {
+    LevelJob job;
+    const LevelJob* jobs = nullptr;
+    const unsigned short* block_job = nullptr;
+    int njobs = 1;
+};
+
+// Launches a device job table as one cooperative grid of total_blocks blocks
+// (the caller sized the jobs' block ranges to fit co-residency; see
+// level_capacity).  All jobs share the kernel radius rt (>= each job's own),
+// separability, precision and solver.
+cudaError_t launch_level_batch(const LevelJob* d_jobs, const unsigned short* d_block_job, int njobs,
+                               int total_blocks, int rt, int sep, int prec, int cgls,
+                               cudaStream_t s);
+// Co-resident block capacity of the solver instantiation (0 on error).
+int level_capacity(int rt, int sep, int prec, int cgls);
+
+// Blocks a level solve of h x w pixels can use.
+int level_want_blocks(int h, int w);
 
 // Launches the persistent solver with as many co-resident blocks as useful
 // (capped by occupancy); *blocks_used receives the grid size.

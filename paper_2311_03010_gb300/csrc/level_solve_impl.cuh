@@ -25,7 +25,37 @@ __device__ __forceinline__ int volatile_stopped(const Scalars* sc) {
     return *(volatile const int*)&sc->stopped;
 }
 
-__device__ __forceinline__ double vld(const double* p) { return *(volatile const double*)p; }
+__device__ __forceinline__ float vldf(const float* p) { return *(volatile const float*)p; }
+
+struct StepCoef {
+    float dw, d1, d2, dinv, tau;
+};
+
+__device__ __forceinline__ StepCoef step_coef(const Scalars* sc) {
+    return StepCoef{vldf(&sc->f_dw), vldf(&sc->f_d1), vldf(&sc->f_d2), vldf(&sc->f_dinv),
+                    vldf(&sc->f_tau)};
+}
+
+// MR-II step j on pixels 4q..4q+3 (coherent loads); returns the new r.
+__device__ __forceinline__ float4 mr_step4(const LevelJob& J, int j, size_t q, const StepCoef& c) {
+    const int sj = j & 1, sj1 = sj ^ 1;
+    float4 dj = mul4(c.dw, ld4cg(J.v[sj], q));
+    float4 hj = mul4(c.dinv, ld4cg(J.aw[sj], q));
+    if (j >= 2) {
+        dj = fma4(-c.d1, ld4cg(J.d[sj1], q), dj);
+        hj = fma4(-c.d1, ld4cg(J.hd[sj1], q), hj);
+    }
+    if (j >= 3) {
+        dj = fma4(-c.d2, ld4cg(J.d[sj], q), dj);
+        hj = fma4(-c.d2, ld4cg(J.hd[sj], q), hj);
+    }
+    st4(J.d[sj], q, dj);
+    st4(J.hd[sj], q, hj);
+    st4(J.u, q, fma4(c.tau, dj, ld4cg(J.u, q)));
+    const float4 rv = fma4(-c.tau, hj, ld4cg(J.r, q));
+    st4(J.r, q, rv);
+    return rv;
+}
 
 // Applies MR-II step j at pixel i (coherent loads); returns the new r_i.
 __device__ __forceinline__ float mr_step_px(const LevelJob& J, int j, size_t i, float dw, float d1,
@@ -89,9 +119,14 @@ __device__ __forceinline__ void conv_phase(ConvSmem<R, SEP>& S, const float* x, 
 using namespace ls_detail;
 
 template <int R, bool SEP, bool PREC>
-__global__ void __launch_bounds__(NTHREADS) k_level_mr2(LevelJob J) {
+__global__ void __launch_bounds__(NTHREADS) k_level_mr2(LevelLaunch LL) {
     __shared__ ConvSmem<R, SEP> S;
-    const unsigned int nb = gridDim.x, bid = blockIdx.x;
+    __shared__ LevelJob sJ;
+    if (threadIdx.x == 0) sJ = LL.jobs ? LL.jobs[LL.block_job[blockIdx.x]] : LL.job;
+    __syncthreads();
+    const LevelJob& J = sJ;
+    const unsigned int nb = LL.jobs ? (unsigned int)J.nblocks : gridDim.x;
+    const unsigned int bid = LL.jobs ? blockIdx.x - (unsigned int)J.block0 : blockIdx.x;
     const int h = J.h, w = J.w;
     const size_t n = (size_t)h * w;
     const size_t stride = (size_t)nb * NTHREADS;
@@ -141,7 +176,7 @@ __global__ void __launch_bounds__(NTHREADS) k_level_mr2(LevelJob J) {
         const int sk = k & 1, sk1 = sk ^ 1;
         // phase A: H w_k = H v_k / ||v_k||, alpha_k = <H w_k, w_k>
         {
-            const float scale = (float)(1.0 / vld(&sc->nrm));
+            const float scale = vldf(&sc->f_scale);
             float a0 = 0.f;
             float* aw = J.aw[sk];
             conv_phase<R, SEP, PREC, false>(S, J.v[sk], h, w, nb, bid,
@@ -158,26 +193,40 @@ __global__ void __launch_bounds__(NTHREADS) k_level_mr2(LevelJob J) {
         // phase B: pending step k-1, v_{k+1}, stopping rules, rotation of column k
         {
             const bool step = k >= 2;
-            const float dw = (float)vld(&sc->dw), d1 = (float)vld(&sc->d1);
-            const float d2 = (float)vld(&sc->d2), dinv = (float)vld(&sc->dinv);
-            const float tau = (float)vld(&sc->tau);
-            const double nrm = vld(&sc->nrm);
-            const float ca = (float)(vld(&sc->alpha) / nrm);
-            const float cb = step ? (float)(nrm / vld(&sc->nrm_prev)) : 0.f;
+            const StepCoef c = step_coef(sc);
+            const float ca = vldf(&sc->f_ca);
+            const float cb = step ? vldf(&sc->f_cb) : 0.f;
             float arr = 0.f, avv = 0.f, avr = 0.f;
-            for (size_t i = (size_t)bid * NTHREADS + threadIdx.x; i < n; i += stride) {
-                float rv;
+            const size_t n4 = n >> 2;
+            for (size_t q = (size_t)bid * NTHREADS + threadIdx.x; q < n4; q += stride) {
+                float4 rv;
                 if (step) {
-                    rv = mr_step_px(J, k - 1, i, dw, d1, d2, dinv, tau);
-                    arr = fmaf(rv, rv, arr);
+                    rv = mr_step4(J, k - 1, q, c);
+                    arr = dot4(rv, rv, arr);
                 } else {
-                    rv = ldcg(J.r + i);
+                    rv = ld4cg(J.r, q);
                 }
-                float vn = fmaf(-ca, ldcg(J.v[sk] + i), ldcg(J.aw[sk] + i));
-                if (step) vn = fmaf(-cb, ldcg(J.v[sk1] + i), vn);
-                J.v[sk1][i] = vn;
-                avv = fmaf(vn, vn, avv);
-                avr = fmaf(vn, rv, avr);
+                float4 vn = fma4(-ca, ld4cg(J.v[sk], q), ld4cg(J.aw[sk], q));
+                if (step) vn = fma4(-cb, ld4cg(J.v[sk1], q), vn);
+                st4(J.v[sk1], q, vn);
+                avv = dot4(vn, vn, avv);
+                avr = dot4(vn, rv, avr);
+            }
+            if (bid == 0) {  // the n mod 4 tail
+                for (size_t i = 4 * n4 + threadIdx.x; i < n; i += NTHREADS) {
+                    float rv;
+                    if (step) {
+                        rv = mr_step_px(J, k - 1, i, c.dw, c.d1, c.d2, c.dinv, c.tau);
+                        arr = fmaf(rv, rv, arr);
+                    } else {
+                        rv = ldcg(J.r + i);
+                    }
+                    float vn = fmaf(-ca, ldcg(J.v[sk] + i), ldcg(J.aw[sk] + i));
+                    if (step) vn = fmaf(-cb, ldcg(J.v[sk1] + i), vn);
+                    J.v[sk1][i] = vn;
+                    avv = fmaf(vn, vn, avv);
+                    avr = fmaf(vn, rv, avr);
+                }
             }
             double v[3] = {(double)arr, (double)avv, (double)avr};
             if (!group_reduce<3>(v, J.partials, J.gs, nb, bid,
@@ -190,23 +239,32 @@ __global__ void __launch_bounds__(NTHREADS) k_level_mr2(LevelJob J) {
     const int st = volatile_stopped(sc);
     const int j = *(volatile const int*)&sc->iters;
     if ((st == 0 || st == 4) && j >= 1) {
-        const float dw = (float)vld(&sc->dw), d1 = (float)vld(&sc->d1);
-        const float d2 = (float)vld(&sc->d2), dinv = (float)vld(&sc->dinv);
-        const float tau = (float)vld(&sc->tau);
+        const StepCoef c = step_coef(sc);
         float arr = 0.f;
-        for (size_t i = (size_t)bid * NTHREADS + threadIdx.x; i < n; i += stride) {
-            const float rv = mr_step_px(J, j, i, dw, d1, d2, dinv, tau);
-            arr = fmaf(rv, rv, arr);
+        const size_t n4 = n >> 2;
+        for (size_t q = (size_t)bid * NTHREADS + threadIdx.x; q < n4; q += stride) {
+            const float4 rv = mr_step4(J, j, q, c);
+            arr = dot4(rv, rv, arr);
         }
+        if (bid == 0)
+            for (size_t i = 4 * n4 + threadIdx.x; i < n; i += NTHREADS) {
+                const float rv = mr_step_px(J, j, i, c.dw, c.d1, c.d2, c.dinv, c.tau);
+                arr = fmaf(rv, rv, arr);
+            }
         double v[1] = {(double)arr};
         group_reduce<1>(v, J.partials, J.gs, nb, bid, [&](double* t) { fin_mr_final(sc, t[0]); });
     }
 }
 
 template <int R, bool SEP, bool PREC>
-__global__ void __launch_bounds__(NTHREADS) k_level_cgls(LevelJob J) {
+__global__ void __launch_bounds__(NTHREADS) k_level_cgls(LevelLaunch LL) {
     __shared__ ConvSmem<R, SEP> S;
-    const unsigned int nb = gridDim.x, bid = blockIdx.x;
+    __shared__ LevelJob sJ;
+    if (threadIdx.x == 0) sJ = LL.jobs ? LL.jobs[LL.block_job[blockIdx.x]] : LL.job;
+    __syncthreads();
+    const LevelJob& J = sJ;
+    const unsigned int nb = LL.jobs ? (unsigned int)J.nblocks : gridDim.x;
+    const unsigned int bid = LL.jobs ? blockIdx.x - (unsigned int)J.block0 : blockIdx.x;
     const int h = J.h, w = J.w;
     const size_t n = (size_t)h * w;
     const size_t stride = (size_t)nb * NTHREADS;
@@ -269,14 +327,22 @@ __global__ void __launch_bounds__(NTHREADS) k_level_cgls(LevelJob J) {
         }
         if (volatile_stopped(sc)) break;
         {  // u += alpha p, r -= alpha q, stopping rule
-            const float a = (float)vld(&sc->cg_alpha);
+            const float a = vldf(&sc->f_cg_alpha);
             float arr = 0.f;
-            for (size_t i = (size_t)bid * NTHREADS + threadIdx.x; i < n; i += stride) {
-                J.u[i] = fmaf(a, ldcg(pv + i), ldcg(J.u + i));
-                const float r = fmaf(-a, ldcg(qv + i), ldcg(rv_ + i));
-                rv_[i] = r;
-                arr = fmaf(r, r, arr);
+            const size_t n4 = n >> 2;
+            for (size_t q = (size_t)bid * NTHREADS + threadIdx.x; q < n4; q += stride) {
+                st4(J.u, q, fma4(a, ld4cg(pv, q), ld4cg(J.u, q)));
+                const float4 r = fma4(-a, ld4cg(qv, q), ld4cg(rv_, q));
+                st4(rv_, q, r);
+                arr = dot4(r, r, arr);
             }
+            if (bid == 0)
+                for (size_t i = 4 * n4 + threadIdx.x; i < n; i += NTHREADS) {
+                    J.u[i] = fmaf(a, ldcg(pv + i), ldcg(J.u + i));
+                    const float r = fmaf(-a, ldcg(qv + i), ldcg(rv_ + i));
+                    rv_[i] = r;
+                    arr = fmaf(r, r, arr);
+                }
             double v[1] = {(double)arr};
             if (!group_reduce<1>(v, J.partials, J.gs, nb, bid,
                                  [&](double* t) { fin_cg_step(sc, t[0]); }))
@@ -299,9 +365,13 @@ __global__ void __launch_bounds__(NTHREADS) k_level_cgls(LevelJob J) {
         }
         if (volatile_stopped(sc)) break;
         {  // p = s + beta p
-            const float b = (float)vld(&sc->beta);
-            for (size_t i = (size_t)bid * NTHREADS + threadIdx.x; i < n; i += stride)
-                pv[i] = fmaf(b, ldcg(pv + i), ldcg(sv + i));
+            const float b = vldf(&sc->f_beta);
+            const size_t n4 = n >> 2;
+            for (size_t q = (size_t)bid * NTHREADS + threadIdx.x; q < n4; q += stride)
+                st4(pv, q, fma4(b, ld4cg(pv, q), ld4cg(sv, q)));
+            if (bid == 0)
+                for (size_t i = 4 * n4 + threadIdx.x; i < n; i += NTHREADS)
+                    pv[i] = fmaf(b, ldcg(pv + i), ldcg(sv + i));
             double v[1] = {0.0};
             if (!group_reduce<1>(v, J.partials, J.gs, nb, bid, [&](double*) {})) return;
         }
@@ -309,8 +379,8 @@ __global__ void __launch_bounds__(NTHREADS) k_level_cgls(LevelJob J) {
 }
 
 template <class K>
-inline cudaError_t coop_launch(K kernel, const LevelJob& J, int blocks, cudaStream_t s) {
-    LevelJob arg = J;
+inline cudaError_t coop_launch(K kernel, const LevelLaunch& L, int blocks, cudaStream_t s) {
+    LevelLaunch arg = L;
     void* params[] = {&arg};
     return cudaLaunchCooperativeKernel((const void*)kernel, dim3(blocks), dim3(NTHREADS), params, 0, s);
 }
@@ -324,42 +394,49 @@ inline int coresident_blocks(K kernel) {
     return per_sm * sms;
 }
 
+// want > 0: min(want, capacity) blocks; want < 0: exactly -want blocks
+// (a batched job table already sized to the capacity); want == 0: only
+// report the capacity in *used.
 template <class K>
-inline cudaError_t launch_capped(K kern, int& cap, const LevelJob& J, int want, cudaStream_t s,
+inline cudaError_t launch_capped(K kern, int& cap, const LevelLaunch& L, int want, cudaStream_t s,
                                  int* used) {
     if (cap < 0) cap = coresident_blocks(kern);
-    int blocks = want < cap ? want : cap;
+    if (want == 0) {
+        if (used) *used = cap;
+        return cudaSuccess;
+    }
+    int blocks = want < 0 ? -want : (want < cap ? want : cap);
     if (blocks < 1) blocks = 1;
     if (used) *used = blocks;
-    return coop_launch(kern, J, blocks, s);
+    return coop_launch(kern, L, blocks, s);
 }
 
-// Launches one instantiation with min(want, co-resident capacity) blocks.
+// Launches one instantiation (see launch_capped for want).
 template <int R, bool SEP, bool PREC, bool CGLS>
-cudaError_t launch_level_t(const LevelJob& J, int want, cudaStream_t s, int* used) {
+cudaError_t launch_level_t(const LevelLaunch& L, int want, cudaStream_t s, int* used) {
     static int cap = -1;  // per instantiation; the library runs on one GPU model
     if constexpr (CGLS)
-        return launch_capped(k_level_cgls<R, SEP, PREC>, cap, J, want, s, used);
+        return launch_capped(k_level_cgls<R, SEP, PREC>, cap, L, want, s, used);
     else
-        return launch_capped(k_level_mr2<R, SEP, PREC>, cap, J, want, s, used);
+        return launch_capped(k_level_mr2<R, SEP, PREC>, cap, L, want, s, used);
 }
 
 template <int R, bool CGLS>
-cudaError_t launch_level_r(const LevelJob& J, int sep, int prec, int want, cudaStream_t s,
+cudaError_t launch_level_r(const LevelLaunch& L, int sep, int prec, int want, cudaStream_t s,
                            int* used) {
-    if (sep && prec) return launch_level_t<R, true, true, CGLS>(J, want, s, used);
-    if (sep) return launch_level_t<R, true, false, CGLS>(J, want, s, used);
-    return launch_level_t<R, false, false, CGLS>(J, want, s, used);
+    if (sep && prec) return launch_level_t<R, true, true, CGLS>(L, want, s, used);
+    if (sep) return launch_level_t<R, true, false, CGLS>(L, want, s, used);
+    return launch_level_t<R, false, false, CGLS>(L, want, s, used);
 }
 
 // Per translation unit: one solver, a range of radii.
-cudaError_t launch_level_mr2_lo(const LevelJob& J, int rt, int sep, int prec, int want,
+cudaError_t launch_level_mr2_lo(const LevelLaunch& L, int rt, int sep, int prec, int want,
                                 cudaStream_t s, int* used);
-cudaError_t launch_level_mr2_hi(const LevelJob& J, int rt, int sep, int prec, int want,
+cudaError_t launch_level_mr2_hi(const LevelLaunch& L, int rt, int sep, int prec, int want,
                                 cudaStream_t s, int* used);
-cudaError_t launch_level_cgls_lo(const LevelJob& J, int rt, int sep, int prec, int want,
+cudaError_t launch_level_cgls_lo(const LevelLaunch& L, int rt, int sep, int prec, int want,
                                  cudaStream_t s, int* used);
-cudaError_t launch_level_cgls_hi(const LevelJob& J, int rt, int sep, int prec, int want,
+cudaError_t launch_level_cgls_hi(const LevelLaunch& L, int rt, int sep, int prec, int want,
                                  cudaStream_t s, int* used);
 
 }  // namespace eecmg

@@ -3,15 +3,15 @@
 
 namespace eecmg {
 
-cudaError_t launch_level_cgls_lo(const LevelJob& J, int rt, int sep, int prec, int want, cudaStream_t s,
+cudaError_t launch_level_cgls_lo(const LevelLaunch& L, int rt, int sep, int prec, int want, cudaStream_t s,
                  int* used) {
     switch (rt) {
-        case 0: return launch_level_r<0, true>(J, sep, prec, want, s, used);
-        case 1: return launch_level_r<1, true>(J, sep, prec, want, s, used);
-        case 2: return launch_level_r<2, true>(J, sep, prec, want, s, used);
-        case 3: return launch_level_r<3, true>(J, sep, prec, want, s, used);
-        case 4: return launch_level_r<4, true>(J, sep, prec, want, s, used);
-        case 5: return launch_level_r<5, true>(J, sep, prec, want, s, used);
+        case 0: return launch_level_r<0, true>(L, sep, prec, want, s, used);
+        case 1: return launch_level_r<1, true>(L, sep, prec, want, s, used);
+        case 2: return launch_level_r<2, true>(L, sep, prec, want, s, used);
+        case 3: return launch_level_r<3, true>(L, sep, prec, want, s, used);
+        case 4: return launch_level_r<4, true>(L, sep, prec, want, s, used);
+        case 5: return launch_level_r<5, true>(L, sep, prec, want, s, used);
         default: return cudaErrorInvalidValue;
     }
 }

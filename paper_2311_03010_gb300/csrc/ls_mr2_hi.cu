@@ -3,16 +3,16 @@
 
 namespace eecmg {
 
-cudaError_t launch_level_mr2_hi(const LevelJob& J, int rt, int sep, int prec, int want, cudaStream_t s,
+cudaError_t launch_level_mr2_hi(const LevelLaunch& L, int rt, int sep, int prec, int want, cudaStream_t s,
                  int* used) {
     switch (rt) {
-        case 6: return launch_level_r<6, false>(J, sep, prec, want, s, used);
-        case 7: return launch_level_r<7, false>(J, sep, prec, want, s, used);
-        case 8: return launch_level_r<8, false>(J, sep, prec, want, s, used);
-        case 9: return launch_level_r<9, false>(J, sep, prec, want, s, used);
-        case 10: return launch_level_r<10, false>(J, sep, prec, want, s, used);
-        case 11: return launch_level_r<11, false>(J, sep, prec, want, s, used);
-        case 12: return launch_level_r<12, false>(J, sep, prec, want, s, used);
+        case 6: return launch_level_r<6, false>(L, sep, prec, want, s, used);
+        case 7: return launch_level_r<7, false>(L, sep, prec, want, s, used);
+        case 8: return launch_level_r<8, false>(L, sep, prec, want, s, used);
+        case 9: return launch_level_r<9, false>(L, sep, prec, want, s, used);
+        case 10: return launch_level_r<10, false>(L, sep, prec, want, s, used);
+        case 11: return launch_level_r<11, false>(L, sep, prec, want, s, used);
+        case 12: return launch_level_r<12, false>(L, sep, prec, want, s, used);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -642,6 +642,7 @@ eecmg_status eecmg_plan(int width, int height, int levels, const double* psf, in
 eecmg_status eecmg_plan_destroy(eecmg_plan_t P) {
     if (!P) return EECMG_OK;
     cudaDeviceSynchronize();
+    forget_plan_batches(P);
     if (P->gexec) cudaGraphExecDestroy(P->gexec);
     if (P->cap_stream) cudaStreamDestroy(P->cap_stream);
     prof_flush(P);
@@ -831,11 +832,12 @@ eecmg_status eecmg_restore_batched(const eecmg_plan_t* plans, const float* const
                                    int n, cudaStream_t s) {
     if (n < 0 || (n > 0 && (!plans || !g || !u)))
         return set_error(EECMG_ERR_INVALID_ARG, "eecmg_restore_batched: bad arguments");
-    for (int i = 0; i < n; ++i) {
-        eecmg_status st = eecmg_restore(plans[i], g[i], u[i], s);
-        if (st != EECMG_OK) return st;
-    }
-    return EECMG_OK;
+    if (n == 0) return EECMG_OK;
+    for (int i = 0; i < n; ++i)
+        if (plans[i] && plans[i]->prof.on)
+            return set_error(EECMG_ERR_INVALID_ARG,
+                             "eecmg_restore_batched: disable profiling on the plans first");
+    return restore_batched_impl(plans, g, u, n, s);
 }
 
 }  // extern "C"

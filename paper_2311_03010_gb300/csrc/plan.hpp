@@ -75,4 +75,7 @@ eecmg_status solve_level_enqueue(eecmg_plan_s* P, int l, const float* g, float* 
 eecmg_status prolong_enqueue(eecmg_plan_s* P, int l, cudaStream_t s);
 eecmg_status cascade_enqueue(eecmg_plan_s* P, cudaStream_t s);
 eecmg_status run_cascade(eecmg_plan_s* P, cudaStream_t s);
+eecmg_status restore_batched_impl(const eecmg_plan_t* plans, const float* const* g, float* const* u,
+                                  int n, cudaStream_t s);
+void forget_plan_batches(eecmg_plan_s* P);
 }  // namespace eecmg
