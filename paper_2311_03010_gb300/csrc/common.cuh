@@ -44,6 +44,7 @@ struct alignas(64) Scalars {
     int loops;            // iterations whose first phase ran (for byte accounting)
     // MR-II, Lanczos / Givens form
     double nrm, nrm_prev; // ||v_k||, ||v_{k-1}|| (w_k = v_k / ||v_k||)
+    double inv_nrm, inv_nrm_prev;  // their reciprocals
     double alpha;         // alpha_k = <H w_k, w_k>
     double cs1, sn1;      // rotation G_{k-1}
     double cs2, sn2;      // rotation G_{k-2}
@@ -69,11 +70,47 @@ constexpr int NPART = 4;  // partial sums per block
 
 // ---------------------------------------------------------------------------
 // Deterministic reductions.  Each thread sums a few products in FP32 (a
-// handful of terms, so no FP64 work per element), the block reduces in FP64
-// with warp shuffles in a fixed order, and block b writes partials[b*NPART+j].
-// The last block to arrive (atomic counter) sums all block partials in a
-// fixed order, so the result does not depend on block scheduling.
+// handful of terms).  The warp and block trees add those partials in
+// double-float (an FP32 pair kept exact by TwoSum, ~48-bit significand), so
+// the tree runs on the FP32 pipes instead of the narrow FP64 pipe; each
+// block's total is then one FP64 value, block b writing partials[b*NPART+j].
+// The grid total is summed in a fixed order, so the result does not depend
+// on block scheduling.
 // ---------------------------------------------------------------------------
+
+struct DF {
+    float hi, lo;
+};
+
+// Error-free sum of two floats (Knuth's TwoSum).
+__device__ __forceinline__ DF two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bp = __fsub_rn(s, a);
+    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bp)), __fsub_rn(b, bp));
+    return DF{s, e};
+}
+
+__device__ __forceinline__ DF df_add(DF a, DF b) {
+    DF s = two_sum(a.hi, b.hi);
+    const float lo = __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo));
+    return two_sum(s.hi, lo);
+}
+
+__device__ __forceinline__ DF df_from_double(double x) {
+    const float hi = (float)x;
+    return DF{hi, (float)(x - (double)hi)};
+}
+
+__device__ __forceinline__ DF warp_sum_df(DF v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        DF w;
+        w.hi = __shfl_xor_sync(0xffffffffu, v.hi, o);
+        w.lo = __shfl_xor_sync(0xffffffffu, v.lo, o);
+        v = df_add(v, w);
+    }
+    return v;
+}
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -84,20 +121,20 @@ __device__ __forceinline__ double warp_sum(double v) {
 // Block-wide sum of NV values per thread; result valid in thread 0.
 template <int NV>
 __device__ __forceinline__ void block_sum(const double (&v)[NV], double (&out)[NV]) {
-    __shared__ double red[NV][NTHREADS / 32];
+    __shared__ DF red[NV][NTHREADS / 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int j = 0; j < NV; ++j) {
-        double s = warp_sum(v[j]);
+        const DF s = warp_sum_df(df_from_double(v[j]));
         if (lane == 0) red[j][warp] = s;
     }
     __syncthreads();
     if (warp == 0) {
 #pragma unroll
         for (int j = 0; j < NV; ++j) {
-            double s = lane < NTHREADS / 32 ? red[j][lane] : 0.0;
-            s = warp_sum(s);
-            out[j] = s;
+            DF s = lane < NTHREADS / 32 ? red[j][lane] : DF{0.f, 0.f};
+            s = warp_sum_df(s);
+            out[j] = (double)s.hi + (double)s.lo;
         }
     }
     __syncthreads();

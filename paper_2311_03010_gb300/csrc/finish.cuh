@@ -34,11 +34,13 @@ __device__ __forceinline__ void fin_mr_v1(Scalars* sc, double vv, double vr) {
     } else if (!(vv > 0.0)) {
         sc->stopped = 2;  // H r_0 = 0: no step
     } else {
-        const double nrm = sqrt(vv);
-        sc->nrm = nrm;
+        const double inv = rsqrt(vv);
+        sc->nrm = vv * inv;
+        sc->inv_nrm = inv;
         sc->nrm_prev = 0.0;
-        sc->phi = vr / nrm;
-        sc->f_scale = (float)(1.0 / nrm);
+        sc->inv_nrm_prev = 0.0;
+        sc->phi = vr * inv;
+        sc->f_scale = (float)inv;
         sc->cs1 = 1.0;
         sc->sn1 = 0.0;
         sc->cs2 = 1.0;
@@ -48,12 +50,13 @@ __device__ __forceinline__ void fin_mr_v1(Scalars* sc, double vv, double vr) {
 
 // alpha_k = <H w_k, w_k> from <H w_k, v_k>.
 __device__ __forceinline__ void fin_mr_a(Scalars* sc, double hv) {
-    const double alpha = hv / sc->nrm;
+    const double inv = sc->inv_nrm;
+    const double alpha = hv * inv;
     sc->alpha = alpha;
     sc->loops += 1;
     // phase B of this iteration: v_{k+1} = H w_k - (alpha/||v_k||) v_k - (||v_k||/||v_{k-1}||) v_{k-1}
-    sc->f_ca = (float)(alpha / sc->nrm);
-    sc->f_cb = sc->nrm_prev > 0.0 ? (float)(sc->nrm / sc->nrm_prev) : 0.f;
+    sc->f_ca = (float)(alpha * inv);
+    sc->f_cb = (float)(sc->nrm * sc->inv_nrm_prev);
 }
 
 // MR-II phase B of iteration k: rr = ||r_{k-1}||^2 (k >= 2), vv = ||v_{k+1}||^2,
@@ -78,26 +81,27 @@ __device__ __forceinline__ void fin_mr_b(Scalars* sc, int k, double rr, double v
         sc->stopped = 3;
         return;
     }
-    const double nrm_new = sqrt(vv);
-    const double c_new = vv > 0.0 ? vr / nrm_new : 0.0;
+    const double inv_new = vv > 0.0 ? rsqrt(vv) : 0.0;
+    const double nrm_new = vv * inv_new;
+    const double c_new = vr * inv_new;
     const double alpha = sc->alpha;
     const double cpl = step ? sc->nrm : 0.0;
     const double e = sc->sn2 * cpl;
     const double t = sc->cs2 * cpl;
     const double r1 = sc->cs1 * t + sc->sn1 * alpha;
     const double a2 = -sc->sn1 * t + sc->cs1 * alpha;
-    const double rho = hypot(a2, nrm_new);
-    if (!(rho > 0.0) || !(rho < 1.0e300)) {
-        sc->stopped = rho > 0.0 ? 3 : 2;
+    const double rho2 = a2 * a2 + vv;  // rho = hypot(a2, ||v_{k+1}||)
+    if (!(rho2 > 0.0) || !(rho2 < 1.0e300)) {
+        sc->stopped = rho2 > 0.0 ? 3 : 2;
         return;
     }
-    const double inv_rho = 1.0 / rho;
+    const double inv_rho = rsqrt(rho2);
     const double cs = a2 * inv_rho, sn = nrm_new * inv_rho;
     const double phi = sc->phi;
     sc->tau = cs * phi + sn * c_new;
     sc->phi = -sn * phi + cs * c_new;
     sc->dinv = inv_rho;
-    sc->dw = inv_rho / sc->nrm;
+    sc->dw = inv_rho * sc->inv_nrm;
     sc->d1 = r1 * inv_rho;
     sc->d2 = e * inv_rho;
     sc->cs2 = sc->cs1;
@@ -105,14 +109,16 @@ __device__ __forceinline__ void fin_mr_b(Scalars* sc, int k, double rr, double v
     sc->cs1 = cs;
     sc->sn1 = sn;
     sc->nrm_prev = sc->nrm;
+    sc->inv_nrm_prev = sc->inv_nrm;
     sc->nrm = nrm_new;
+    sc->inv_nrm = inv_new;
     sc->iters = k;
     sc->f_dw = (float)sc->dw;
     sc->f_d1 = (float)sc->d1;
     sc->f_d2 = (float)sc->d2;
     sc->f_dinv = (float)inv_rho;
     sc->f_tau = (float)sc->tau;
-    sc->f_scale = nrm_new > 0.0 ? (float)(1.0 / nrm_new) : 0.f;
+    sc->f_scale = (float)inv_new;
     if (!(nrm_new > 0.0)) sc->stopped = 4;  // Krylov space exhausted: step k is the last
 }
 

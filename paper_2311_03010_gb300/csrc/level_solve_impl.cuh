@@ -19,6 +19,26 @@
 
 namespace eecmg {
 
+#ifdef EECMG_TRACE
+// Phase timestamps of block 0 (tracing builds only): pairs (tag, %globaltimer ns).
+extern __device__ unsigned long long g_eecmg_trace[1 << 16];
+extern __device__ unsigned int g_eecmg_trace_n;
+__device__ __forceinline__ void trace_mark(unsigned int bid, unsigned int tag) {
+    if (bid == 0 && threadIdx.x == 0) {
+        unsigned long long t;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+        const unsigned int i = atomicAdd(&g_eecmg_trace_n, 2u);
+        if (i + 1 < (1u << 16)) {
+            g_eecmg_trace[i] = tag;
+            g_eecmg_trace[i + 1] = t;
+        }
+    }
+}
+#define TRACE(bid, tag) trace_mark((bid), (tag))
+#else
+#define TRACE(bid, tag) ((void)0)
+#endif
+
 namespace ls_detail {
 
 __device__ __forceinline__ int volatile_stopped(const Scalars* sc) {
@@ -175,6 +195,7 @@ __global__ void __launch_bounds__(NTHREADS) k_level_mr2(LevelLaunch LL) {
         if (volatile_stopped(sc)) break;
         const int sk = k & 1, sk1 = sk ^ 1;
         // phase A: H w_k = H v_k / ||v_k||, alpha_k = <H w_k, w_k>
+        TRACE(bid, 10);
         {
             const float scale = vldf(&sc->f_scale);
             float a0 = 0.f;
@@ -186,10 +207,12 @@ __global__ void __launch_bounds__(NTHREADS) k_level_mr2(LevelLaunch LL) {
                                                 a0 = fmaf(hz, ctr, a0);
                                             });
             double v[1] = {(double)a0};
+            TRACE(bid, 11);
             if (!group_reduce<1>(v, J.partials, J.gs, nb, bid,
                                  [&](double* t) { fin_mr_a(sc, t[0]); }))
                 return;
         }
+        TRACE(bid, 12);
         // phase B: pending step k-1, v_{k+1}, stopping rules, rotation of column k
         {
             const bool step = k >= 2;
@@ -229,10 +252,12 @@ __global__ void __launch_bounds__(NTHREADS) k_level_mr2(LevelLaunch LL) {
                 }
             }
             double v[3] = {(double)arr, (double)avv, (double)avr};
+            TRACE(bid, 13);
             if (!group_reduce<3>(v, J.partials, J.gs, nb, bid,
                                  [&](double* t) { fin_mr_b(sc, k, t[0], t[1], t[2]); }))
                 return;
         }
+        TRACE(bid, 14);
     }
 
     // the step decided last (breakdown-with-step or the schedule's end)
