@@ -193,6 +193,7 @@ def main():
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--smoother", default="mr2", choices=["mr2", "cgls"])
     ap.add_argument("--precise-conv", type=int, default=1)
+    ap.add_argument("--storage", default="fp32", choices=["fp32", "bf16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
 
@@ -228,7 +229,8 @@ def main():
         smo = args.smoother
         if smo == "mr2" and not np.allclose(psf, psf[::-1, ::-1], rtol=0, atol=1e-15):
             smo = "cgls"
-        plans.append(eecmg.Plan(w, h, L, psf, smoother=smo, precise_conv=args.precise_conv))
+        plans.append(eecmg.Plan(w, h, L, psf, smoother=smo, precise_conv=args.precise_conv,
+                                storage=args.storage))
     gs = [torch.from_numpy(g).cuda() for (_, _, _, g) in probs]
     us = [torch.empty_like(g) for g in gs]
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
@@ -351,6 +353,7 @@ def main():
             "data": "synthetic",
             "config": {"workload": name, "images_per_step": len(gs), "levels": L,
                        "smoother": args.smoother, "precise_conv": args.precise_conv,
+                       "storage": args.storage,
                        "parallelism": f"replicas x{world}", "l2": "flushed between steps"},
             "e2e": {"value": e2e_val, "unit": "Mpixel/s",
                     "h2d_bytes_per_step": int(sum(g.numel() * 4 for g in gs)),

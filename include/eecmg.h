@@ -67,8 +67,11 @@ enum { EECMG_PROLONG_EECMG = 0, EECMG_PROLONG_IECMG_P = 1, EECMG_PROLONG_IECMG_L
  *                         adjoint under the RMS inner product of Eq. 10;
  *                         GALERKIN_RENORM rescales each coarse PSF to the
  *                         fine PSF's sum.
- *   storage = FP32        BF16 stores the streamed Krylov vectors in bf16
- *                         (FP32 arithmetic, FP64 scalars).
+ *   storage = FP32        BF16 stores the streamed Krylov direction vectors
+ *                         (MR-II: d and H d; CGLS: s, p, q) as bf16, rounded
+ *                         to nearest even; Lanczos vectors, u and r stay FP32,
+ *                         arithmetic is FP32 and scalars FP64.  Needs
+ *                         persistent = 1 (else EECMG_ERR_UNSUPPORTED).
  *   stop = FIXED          exactly m_l iterations (Section 2 note), unless
  *                         DISCREPANCY: stop when ||r||_RMS <= c * delta.
  *   c = 1.1, delta = 0    discrepancy constant and noise level ||e||_RMS.

@@ -7,7 +7,8 @@
 // jobs of one cooperative grid: image i's job owns a range of blocks with its
 // own group barrier, reduction partials and scalars, so the images never
 // wait for one another inside the launch.  Jobs are grouped by solver,
-// separability and precision (one kernel instantiation each) and, within a
+// separability, precision and storage type (one kernel instantiation each)
+// and, within a
 // group, share the largest PSF radius (smaller PSFs are zero-padded).  The
 // restriction and the per-image prolongation kernels run before each step.
 // The whole batch is captured once as a CUDA graph per set of plans and
@@ -30,7 +31,7 @@ namespace {
 struct Wave {
     const LevelJob* d_jobs = nullptr;
     const unsigned short* d_block_job = nullptr;
-    int njobs = 0, blocks = 0, rt = 0, sep = 0, prec = 0, cgls = 0;
+    int njobs = 0, blocks = 0, rt = 0, sep = 0, prec = 0, cgls = 0, bf16 = 0;
 };
 
 struct BatchCtx {
@@ -83,24 +84,25 @@ eecmg_status build_ctx(BatchCtx& C) {
     struct HostWave {
         std::vector<LevelJob> jobs;
         std::vector<unsigned short> block_job;
-        int blocks = 0, rt = 0, sep = 0, prec = 0, cgls = 0;
+        int blocks = 0, rt = 0, sep = 0, prec = 0, cgls = 0, bf16 = 0;
     };
     std::vector<std::vector<HostWave>> hsteps(maxL);
     for (int s = 0; s < maxL; ++s) {
         // group key -> indices of plans
-        std::map<std::tuple<int, int, int>, std::vector<int>> groups;
+        std::map<std::tuple<int, int, int, int>, std::vector<int>> groups;
         for (int i = 0; i < (int)C.plans.size(); ++i) {
             eecmg_plan_s* P = C.plans[i];
             if (s >= P->L) continue;
             const int cg = P->opt.smoother == EECMG_SMOOTHER_CGLS ? 1 : 0;
-            groups[{cg, P->lv[s].sepH, P->opt.precise_conv}].push_back(i);
+            const int bf = P->opt.storage == EECMG_STORAGE_BF16 ? 1 : 0;
+            groups[{cg, P->lv[s].sepH, P->opt.precise_conv, bf}].push_back(i);
         }
         for (auto& kv : groups) {
             const int cg = std::get<0>(kv.first), sep = std::get<1>(kv.first),
-                      prec = std::get<2>(kv.first);
+                      prec = std::get<2>(kv.first), bf = std::get<3>(kv.first);
             int rt = 0;
             for (int i : kv.second) rt = std::max(rt, C.plans[i]->lv[s].rt);
-            const int cap = level_capacity(rt, sep, prec, cg);
+            const int cap = level_capacity(rt, sep, prec, cg, bf);
             if (cap <= 0) return set_error(EECMG_ERR_CUDA, "eecmg_restore_batched: occupancy query failed");
             // blocks per job: the same count as the job's solve alone (so the
             // result is bitwise the same); jobs that do not fit start a new wave
@@ -112,6 +114,7 @@ eecmg_status build_ctx(BatchCtx& C) {
             cur.sep = sep;
             cur.prec = prec;
             cur.cgls = cg;
+            cur.bf16 = bf;
             for (size_t k = 0; k < kv.second.size(); ++k) {
                 const int nb = std::max(1, want[k]);
                 if (cur.blocks + nb > cap && !cur.jobs.empty()) {  // next wave
@@ -158,6 +161,7 @@ eecmg_status build_ctx(BatchCtx& C) {
             dw.sep = w.sep;
             dw.prec = w.prec;
             dw.cgls = w.cgls;
+            dw.bf16 = w.bf16;
             C.steps[s].push_back(dw);
         }
     e = cudaStreamCreateWithFlags(&C.cap_stream, cudaStreamNonBlocking);
@@ -191,7 +195,7 @@ eecmg_status enqueue_batch(BatchCtx& C, cudaStream_t s) {
         }
         for (auto& w : C.steps[st])
             BCK(launch_level_batch(w.d_jobs, w.d_block_job, w.njobs, w.blocks, w.rt, w.sep, w.prec,
-                                   w.cgls, s));
+                                   w.cgls, w.bf16, s));
     }
     return EECMG_OK;
 }

@@ -7,6 +7,7 @@
 // with C = K.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -192,6 +193,49 @@ __device__ __forceinline__ float4 fma4(float a, float4 x, float4 y) {
 __device__ __forceinline__ float4 mul4(float a, float4 x) {
     return make_float4(a * x.x, a * x.y, a * x.z, a * x.w);
 }
+// Coherent (L2) element and float4 access to a vector stored as T (FP32, or
+// BF16 for the streamed vectors of the BF16-storage variant).  BF16 values
+// are rounded to nearest even on store and widened exactly on load.
+template <typename T>
+struct VecIO;
+template <>
+struct VecIO<float> {
+    static __device__ __forceinline__ float ld(const float* p, size_t i) { return __ldcg(p + i); }
+    static __device__ __forceinline__ void st(float* p, size_t i, float v) { p[i] = v; }
+    static __device__ __forceinline__ float4 ld4(const float* p, size_t q) {
+        return __ldcg(reinterpret_cast<const float4*>(p) + q);
+    }
+    static __device__ __forceinline__ void st4(float* p, size_t q, float4 v) {
+        reinterpret_cast<float4*>(p)[q] = v;
+    }
+};
+template <>
+struct VecIO<__nv_bfloat16> {
+    static __device__ __forceinline__ float widen(unsigned int bits16) {
+        return __uint_as_float(bits16 << 16);
+    }
+    static __device__ __forceinline__ unsigned int narrow(float v) {
+        return (unsigned int)__bfloat16_as_ushort(__float2bfloat16_rn(v));
+    }
+    static __device__ __forceinline__ float ld(const __nv_bfloat16* p, size_t i) {
+        return widen(__ldcg(reinterpret_cast<const unsigned short*>(p) + i));
+    }
+    static __device__ __forceinline__ void st(__nv_bfloat16* p, size_t i, float v) {
+        p[i] = __float2bfloat16_rn(v);
+    }
+    static __device__ __forceinline__ float4 ld4(const __nv_bfloat16* p, size_t q) {
+        const uint2 w = __ldcg(reinterpret_cast<const uint2*>(p) + q);
+        return make_float4(widen(w.x & 0xffffu), widen(w.x >> 16), widen(w.y & 0xffffu),
+                           widen(w.y >> 16));
+    }
+    static __device__ __forceinline__ void st4(__nv_bfloat16* p, size_t q, float4 v) {
+        uint2 w;
+        w.x = narrow(v.x) | (narrow(v.y) << 16);
+        w.y = narrow(v.z) | (narrow(v.w) << 16);
+        reinterpret_cast<uint2*>(p)[q] = w;
+    }
+};
+
 __device__ __forceinline__ float dot4(float4 a, float4 b, float acc) {
     acc = fmaf(a.x, b.x, acc);
     acc = fmaf(a.y, b.y, acc);

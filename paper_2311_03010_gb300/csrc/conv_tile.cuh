@@ -59,8 +59,8 @@ __device__ __forceinline__ void conv_stage_taps(ConvSmem<R, SEP>& S, const Taps*
 // Loads the tile at (y0, x0) with halo.  COHERENT loads go through L2 only
 // (ld.global.cg): required when x was written earlier in the same launch by
 // other blocks.
-template <int R, bool SEP, bool COHERENT>
-__device__ __forceinline__ void conv_load(ConvSmem<R, SEP>& S, const float* __restrict__ x, int h,
+template <int R, bool SEP, bool COHERENT, typename TIN = float>
+__device__ __forceinline__ void conv_load(ConvSmem<R, SEP>& S, const TIN* __restrict__ x, int h,
                                           int w, int y0, int x0) {
     constexpr int IH = ConvSmem<R, SEP>::IH, IW = ConvSmem<R, SEP>::IW;
     constexpr int NTOT = IH * IW;
@@ -74,8 +74,11 @@ __device__ __forceinline__ void conv_load(ConvSmem<R, SEP>& S, const float* __re
         const int gy = y0 - R + r, gx = x0 - R + c;
         float v = 0.f;
         if (i < NTOT && gy >= 0 && gy < h && gx >= 0 && gx < w) {
-            const float* p = x + (size_t)gy * w + gx;
-            v = COHERENT ? __ldcg(p) : __ldg(p);
+            const size_t idx = (size_t)gy * w + gx;
+            if constexpr (sizeof(TIN) == 4)
+                v = COHERENT ? __ldcg((const float*)x + idx) : __ldg((const float*)x + idx);
+            else
+                v = VecIO<TIN>::ld(x, idx);
         }
         vals[k] = v;
     }

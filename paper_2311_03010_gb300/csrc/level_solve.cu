@@ -11,14 +11,22 @@ __device__ unsigned int g_eecmg_trace_n;
 
 namespace {
 
-cudaError_t dispatch(const LevelLaunch& L, int rt, int sep, int prec, int cgls, int want,
+cudaError_t dispatch(const LevelLaunch& L, int rt, int sep, int prec, int cgls, int bf16, int want,
                      cudaStream_t s, int* used) {
     if (rt < 0 || rt > RMAX) return cudaErrorInvalidValue;
-    if (cgls)
-        return rt < 6 ? launch_level_cgls_lo(L, rt, sep, prec, want, s, used)
-                      : launch_level_cgls_hi(L, rt, sep, prec, want, s, used);
-    return rt < 6 ? launch_level_mr2_lo(L, rt, sep, prec, want, s, used)
-                  : launch_level_mr2_hi(L, rt, sep, prec, want, s, used);
+    const bool lo = rt < 6;
+    if (cgls) {
+        if (bf16)
+            return lo ? launch_level_cgls_bf16_lo(L, rt, sep, prec, want, s, used)
+                      : launch_level_cgls_bf16_hi(L, rt, sep, prec, want, s, used);
+        return lo ? launch_level_cgls_f32_lo(L, rt, sep, prec, want, s, used)
+                  : launch_level_cgls_f32_hi(L, rt, sep, prec, want, s, used);
+    }
+    if (bf16)
+        return lo ? launch_level_mr2_bf16_lo(L, rt, sep, prec, want, s, used)
+                  : launch_level_mr2_bf16_hi(L, rt, sep, prec, want, s, used);
+    return lo ? launch_level_mr2_f32_lo(L, rt, sep, prec, want, s, used)
+              : launch_level_mr2_f32_hi(L, rt, sep, prec, want, s, used);
 }
 
 }  // namespace
@@ -41,29 +49,29 @@ int level_want_blocks(int h, int w) {
     return want < cap ? want : cap;
 }
 
-cudaError_t launch_level_solve(const LevelJob& J, int rt, int sep, int prec, int cgls,
+cudaError_t launch_level_solve(const LevelJob& J, int rt, int sep, int prec, int cgls, int bf16,
                                cudaStream_t s, int* blocks_used) {
     if (J.h <= 0 || J.w <= 0) return cudaSuccess;
     LevelLaunch L;
     L.job = J;
-    return dispatch(L, rt, sep, prec, cgls, level_want_blocks(J.h, J.w), s, blocks_used);
+    return dispatch(L, rt, sep, prec, cgls, bf16, level_want_blocks(J.h, J.w), s, blocks_used);
 }
 
 cudaError_t launch_level_batch(const LevelJob* d_jobs, const unsigned short* d_block_job, int njobs,
-                               int total_blocks, int rt, int sep, int prec, int cgls,
+                               int total_blocks, int rt, int sep, int prec, int cgls, int bf16,
                                cudaStream_t s) {
     if (njobs <= 0 || total_blocks <= 0) return cudaSuccess;
     LevelLaunch L;
     L.jobs = d_jobs;
     L.block_job = d_block_job;
     L.njobs = njobs;
-    return dispatch(L, rt, sep, prec, cgls, -total_blocks, s, nullptr);
+    return dispatch(L, rt, sep, prec, cgls, bf16, -total_blocks, s, nullptr);
 }
 
-int level_capacity(int rt, int sep, int prec, int cgls) {
+int level_capacity(int rt, int sep, int prec, int cgls, int bf16) {
     LevelLaunch L;
     int cap = 0;
-    if (dispatch(L, rt, sep, prec, cgls, 0, nullptr, &cap) != cudaSuccess) return 0;
+    if (dispatch(L, rt, sep, prec, cgls, bf16, 0, nullptr, &cap) != cudaSuccess) return 0;
     return cap;
 }
 

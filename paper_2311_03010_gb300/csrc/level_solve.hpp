@@ -40,17 +40,18 @@ struct LevelLaunch {
 // level_capacity).  All jobs share the kernel radius rt (>= each job's own),
 // separability, precision and solver.
 cudaError_t launch_level_batch(const LevelJob* d_jobs, const unsigned short* d_block_job, int njobs,
-                               int total_blocks, int rt, int sep, int prec, int cgls,
+                               int total_blocks, int rt, int sep, int prec, int cgls, int bf16,
                                cudaStream_t s);
 // Co-resident block capacity of the solver instantiation (0 on error).
-int level_capacity(int rt, int sep, int prec, int cgls);
+int level_capacity(int rt, int sep, int prec, int cgls, int bf16);
 
 // Blocks a level solve of h x w pixels can use.
 int level_want_blocks(int h, int w);
 
 // Launches the persistent solver with as many co-resident blocks as useful
 // (capped by occupancy); *blocks_used receives the grid size.
-cudaError_t launch_level_solve(const LevelJob& J, int rt, int sep, int prec, int cgls,
+// bf16: the streamed Krylov direction vectors are stored as BF16.
+cudaError_t launch_level_solve(const LevelJob& J, int rt, int sep, int prec, int cgls, int bf16,
                                cudaStream_t s, int* blocks_used);
 
 }  // namespace eecmg

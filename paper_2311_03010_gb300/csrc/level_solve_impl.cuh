@@ -56,21 +56,27 @@ __device__ __forceinline__ StepCoef step_coef(const Scalars* sc) {
                     vldf(&sc->f_tau)};
 }
 
-// MR-II step j on pixels 4q..4q+3 (coherent loads); returns the new r.
+// MR-II step j on pixels 4q..4q+3 (coherent loads); returns the new r.  The
+// direction history d, H d is stored as HT (FP32, or BF16 in the BF16-storage
+// variant); arithmetic is FP32.
+template <typename HT>
 __device__ __forceinline__ float4 mr_step4(const LevelJob& J, int j, size_t q, const StepCoef& c) {
+    using IO = VecIO<HT>;
     const int sj = j & 1, sj1 = sj ^ 1;
+    HT* dd[2] = {reinterpret_cast<HT*>(J.d[0]), reinterpret_cast<HT*>(J.d[1])};
+    HT* hh[2] = {reinterpret_cast<HT*>(J.hd[0]), reinterpret_cast<HT*>(J.hd[1])};
     float4 dj = mul4(c.dw, ld4cg(J.v[sj], q));
     float4 hj = mul4(c.dinv, ld4cg(J.aw[sj], q));
     if (j >= 2) {
-        dj = fma4(-c.d1, ld4cg(J.d[sj1], q), dj);
-        hj = fma4(-c.d1, ld4cg(J.hd[sj1], q), hj);
+        dj = fma4(-c.d1, IO::ld4(dd[sj1], q), dj);
+        hj = fma4(-c.d1, IO::ld4(hh[sj1], q), hj);
     }
     if (j >= 3) {
-        dj = fma4(-c.d2, ld4cg(J.d[sj], q), dj);
-        hj = fma4(-c.d2, ld4cg(J.hd[sj], q), hj);
+        dj = fma4(-c.d2, IO::ld4(dd[sj], q), dj);
+        hj = fma4(-c.d2, IO::ld4(hh[sj], q), hj);
     }
-    st4(J.d[sj], q, dj);
-    st4(J.hd[sj], q, hj);
+    IO::st4(dd[sj], q, dj);
+    IO::st4(hh[sj], q, hj);
     st4(J.u, q, fma4(c.tau, dj, ld4cg(J.u, q)));
     const float4 rv = fma4(-c.tau, hj, ld4cg(J.r, q));
     st4(J.r, q, rv);
@@ -78,21 +84,25 @@ __device__ __forceinline__ float4 mr_step4(const LevelJob& J, int j, size_t q, c
 }
 
 // Applies MR-II step j at pixel i (coherent loads); returns the new r_i.
+template <typename HT>
 __device__ __forceinline__ float mr_step_px(const LevelJob& J, int j, size_t i, float dw, float d1,
                                             float d2, float dinv, float tau) {
+    using IO = VecIO<HT>;
     const int sj = j & 1, sj1 = sj ^ 1;
+    HT* dd[2] = {reinterpret_cast<HT*>(J.d[0]), reinterpret_cast<HT*>(J.d[1])};
+    HT* hh[2] = {reinterpret_cast<HT*>(J.hd[0]), reinterpret_cast<HT*>(J.hd[1])};
     float dj = dw * ldcg(J.v[sj] + i);
     float hj = dinv * ldcg(J.aw[sj] + i);
     if (j >= 2) {
-        dj = fmaf(-d1, ldcg(J.d[sj1] + i), dj);
-        hj = fmaf(-d1, ldcg(J.hd[sj1] + i), hj);
+        dj = fmaf(-d1, IO::ld(dd[sj1], i), dj);
+        hj = fmaf(-d1, IO::ld(hh[sj1], i), hj);
     }
     if (j >= 3) {
-        dj = fmaf(-d2, ldcg(J.d[sj] + i), dj);
-        hj = fmaf(-d2, ldcg(J.hd[sj] + i), hj);
+        dj = fmaf(-d2, IO::ld(dd[sj], i), dj);
+        hj = fmaf(-d2, IO::ld(hh[sj], i), hj);
     }
-    J.d[sj][i] = dj;
-    J.hd[sj][i] = hj;
+    IO::st(dd[sj], i, dj);
+    IO::st(hh[sj], i, hj);
     J.u[i] = fmaf(tau, dj, ldcg(J.u + i));
     const float rv = fmaf(-tau, hj, ldcg(J.r + i));
     J.r[i] = rv;
@@ -101,8 +111,8 @@ __device__ __forceinline__ float mr_step_px(const LevelJob& J, int j, size_t i, 
 
 // One convolution phase over the level: y = scale * (C (*) x) for every tile,
 // with epilogue E(idx, z, center) accumulating into acc0/acc1.
-template <int R, bool SEP, bool PREC, bool ZERO, class Epi>
-__device__ __forceinline__ void conv_phase(ConvSmem<R, SEP>& S, const float* x, int h, int w,
+template <int R, bool SEP, bool PREC, bool ZERO, typename TIN = float, class Epi>
+__device__ __forceinline__ void conv_phase(ConvSmem<R, SEP>& S, const TIN* x, int h, int w,
                                            unsigned int nb, unsigned int bid, Epi&& epi) {
     using SM = ConvSmem<R, SEP>;
     const int tiles_x = (w + CONV_TW - 1) / CONV_TW, tiles_y = (h + CONV_TH - 1) / CONV_TH;
@@ -111,7 +121,7 @@ __device__ __forceinline__ void conv_phase(ConvSmem<R, SEP>& S, const float* x, 
     for (int t = (int)bid; t < ntiles; t += (int)nb) {
         const int y0 = (t / tiles_x) * CONV_TH, x0 = (t % tiles_x) * CONV_TW;
         if (!ZERO) {
-            conv_load<R, SEP, true>(S, x, h, w, y0, x0);
+            conv_load<R, SEP, true, TIN>(S, x, h, w, y0, x0);
             __syncthreads();
             conv_compute<R, SEP, PREC>(S);
             __syncthreads();
@@ -138,7 +148,7 @@ __device__ __forceinline__ void conv_phase(ConvSmem<R, SEP>& S, const float* x, 
 
 using namespace ls_detail;
 
-template <int R, bool SEP, bool PREC>
+template <int R, bool SEP, bool PREC, typename HT>
 __global__ void __launch_bounds__(NTHREADS) k_level_mr2(LevelLaunch LL) {
     __shared__ ConvSmem<R, SEP> S;
     __shared__ LevelJob sJ;
@@ -224,7 +234,7 @@ __global__ void __launch_bounds__(NTHREADS) k_level_mr2(LevelLaunch LL) {
             for (size_t q = (size_t)bid * NTHREADS + threadIdx.x; q < n4; q += stride) {
                 float4 rv;
                 if (step) {
-                    rv = mr_step4(J, k - 1, q, c);
+                    rv = mr_step4<HT>(J, k - 1, q, c);
                     arr = dot4(rv, rv, arr);
                 } else {
                     rv = ld4cg(J.r, q);
@@ -239,7 +249,7 @@ __global__ void __launch_bounds__(NTHREADS) k_level_mr2(LevelLaunch LL) {
                 for (size_t i = 4 * n4 + threadIdx.x; i < n; i += NTHREADS) {
                     float rv;
                     if (step) {
-                        rv = mr_step_px(J, k - 1, i, c.dw, c.d1, c.d2, c.dinv, c.tau);
+                        rv = mr_step_px<HT>(J, k - 1, i, c.dw, c.d1, c.d2, c.dinv, c.tau);
                         arr = fmaf(rv, rv, arr);
                     } else {
                         rv = ldcg(J.r + i);
@@ -268,12 +278,12 @@ __global__ void __launch_bounds__(NTHREADS) k_level_mr2(LevelLaunch LL) {
         float arr = 0.f;
         const size_t n4 = n >> 2;
         for (size_t q = (size_t)bid * NTHREADS + threadIdx.x; q < n4; q += stride) {
-            const float4 rv = mr_step4(J, j, q, c);
+            const float4 rv = mr_step4<HT>(J, j, q, c);
             arr = dot4(rv, rv, arr);
         }
         if (bid == 0)
             for (size_t i = 4 * n4 + threadIdx.x; i < n; i += NTHREADS) {
-                const float rv = mr_step_px(J, j, i, c.dw, c.d1, c.d2, c.dinv, c.tau);
+                const float rv = mr_step_px<HT>(J, j, i, c.dw, c.d1, c.d2, c.dinv, c.tau);
                 arr = fmaf(rv, rv, arr);
             }
         double v[1] = {(double)arr};
@@ -281,8 +291,9 @@ __global__ void __launch_bounds__(NTHREADS) k_level_mr2(LevelLaunch LL) {
     }
 }
 
-template <int R, bool SEP, bool PREC>
+template <int R, bool SEP, bool PREC, typename HT>
 __global__ void __launch_bounds__(NTHREADS) k_level_cgls(LevelLaunch LL) {
+    using IO = VecIO<HT>;  // s, p, q stored as HT; u, r FP32
     __shared__ ConvSmem<R, SEP> S;
     __shared__ LevelJob sJ;
     if (threadIdx.x == 0) sJ = LL.jobs ? LL.jobs[LL.block_job[blockIdx.x]] : LL.job;
@@ -295,9 +306,9 @@ __global__ void __launch_bounds__(NTHREADS) k_level_cgls(LevelLaunch LL) {
     const size_t stride = (size_t)nb * NTHREADS;
     Scalars* sc = J.sc;
     float* rv_ = J.r;
-    float* sv = J.v[0];  // s
-    float* pv = J.v[1];  // p
-    float* qv = J.aw[0]; // q
+    HT* sv = reinterpret_cast<HT*>(J.v[0]);   // s
+    HT* pv = reinterpret_cast<HT*>(J.v[1]);   // p
+    HT* qv = reinterpret_cast<HT*>(J.aw[0]);  // q
     conv_stage_taps<R, SEP>(S, J.taps);
     __syncthreads();
     {
@@ -326,8 +337,8 @@ __global__ void __launch_bounds__(NTHREADS) k_level_cgls(LevelLaunch LL) {
     {
         float a0 = 0.f;
         conv_phase<R, SEP, PREC, false>(S, rv_, h, w, nb, bid, [&](size_t idx, float z, float) {
-            sv[idx] = z;
-            pv[idx] = z;
+            IO::st(sv, idx, z);
+            IO::st(pv, idx, z);
             a0 = fmaf(z, z, a0);
         });
         double v[1] = {(double)a0};
@@ -341,9 +352,10 @@ __global__ void __launch_bounds__(NTHREADS) k_level_cgls(LevelLaunch LL) {
         __syncthreads();
         {
             float a0 = 0.f;
-            conv_phase<R, SEP, PREC, false>(S, pv, h, w, nb, bid, [&](size_t idx, float z, float) {
-                qv[idx] = z;
-                a0 = fmaf(z, z, a0);
+            conv_phase<R, SEP, PREC, false, HT>(S, pv, h, w, nb, bid, [&](size_t idx, float z, float) {
+                IO::st(qv, idx, z);
+                const float zq = IO::ld(qv, idx);  // the stored value enters <q, q>
+                a0 = fmaf(zq, zq, a0);
             });
             double v[1] = {(double)a0};
             if (!group_reduce<1>(v, J.partials, J.gs, nb, bid,
@@ -356,15 +368,15 @@ __global__ void __launch_bounds__(NTHREADS) k_level_cgls(LevelLaunch LL) {
             float arr = 0.f;
             const size_t n4 = n >> 2;
             for (size_t q = (size_t)bid * NTHREADS + threadIdx.x; q < n4; q += stride) {
-                st4(J.u, q, fma4(a, ld4cg(pv, q), ld4cg(J.u, q)));
-                const float4 r = fma4(-a, ld4cg(qv, q), ld4cg(rv_, q));
+                st4(J.u, q, fma4(a, IO::ld4(pv, q), ld4cg(J.u, q)));
+                const float4 r = fma4(-a, IO::ld4(qv, q), ld4cg(rv_, q));
                 st4(rv_, q, r);
                 arr = dot4(r, r, arr);
             }
             if (bid == 0)
                 for (size_t i = 4 * n4 + threadIdx.x; i < n; i += NTHREADS) {
-                    J.u[i] = fmaf(a, ldcg(pv + i), ldcg(J.u + i));
-                    const float r = fmaf(-a, ldcg(qv + i), ldcg(rv_ + i));
+                    J.u[i] = fmaf(a, IO::ld(pv, i), ldcg(J.u + i));
+                    const float r = fmaf(-a, IO::ld(qv, i), ldcg(rv_ + i));
                     rv_[i] = r;
                     arr = fmaf(r, r, arr);
                 }
@@ -380,7 +392,7 @@ __global__ void __launch_bounds__(NTHREADS) k_level_cgls(LevelLaunch LL) {
         {
             float a0 = 0.f;
             conv_phase<R, SEP, PREC, false>(S, rv_, h, w, nb, bid, [&](size_t idx, float z, float) {
-                sv[idx] = z;
+                IO::st(sv, idx, z);
                 a0 = fmaf(z, z, a0);
             });
             double v[1] = {(double)a0};
@@ -393,10 +405,10 @@ __global__ void __launch_bounds__(NTHREADS) k_level_cgls(LevelLaunch LL) {
             const float b = vldf(&sc->f_beta);
             const size_t n4 = n >> 2;
             for (size_t q = (size_t)bid * NTHREADS + threadIdx.x; q < n4; q += stride)
-                st4(pv, q, fma4(b, ld4cg(pv, q), ld4cg(sv, q)));
+                IO::st4(pv, q, fma4(b, IO::ld4(pv, q), IO::ld4(sv, q)));
             if (bid == 0)
                 for (size_t i = 4 * n4 + threadIdx.x; i < n; i += NTHREADS)
-                    pv[i] = fmaf(b, ldcg(pv + i), ldcg(sv + i));
+                    IO::st(pv, i, fmaf(b, IO::ld(pv, i), IO::ld(sv, i)));
             double v[1] = {0.0};
             if (!group_reduce<1>(v, J.partials, J.gs, nb, bid, [&](double*) {})) return;
         }
@@ -437,31 +449,36 @@ inline cudaError_t launch_capped(K kern, int& cap, const LevelLaunch& L, int wan
 }
 
 // Launches one instantiation (see launch_capped for want).
-template <int R, bool SEP, bool PREC, bool CGLS>
+template <int R, bool SEP, bool PREC, bool CGLS, typename HT>
 cudaError_t launch_level_t(const LevelLaunch& L, int want, cudaStream_t s, int* used) {
     static int cap = -1;  // per instantiation; the library runs on one GPU model
     if constexpr (CGLS)
-        return launch_capped(k_level_cgls<R, SEP, PREC>, cap, L, want, s, used);
+        return launch_capped(k_level_cgls<R, SEP, PREC, HT>, cap, L, want, s, used);
     else
-        return launch_capped(k_level_mr2<R, SEP, PREC>, cap, L, want, s, used);
+        return launch_capped(k_level_mr2<R, SEP, PREC, HT>, cap, L, want, s, used);
 }
 
-template <int R, bool CGLS>
+template <int R, bool CGLS, typename HT>
 cudaError_t launch_level_r(const LevelLaunch& L, int sep, int prec, int want, cudaStream_t s,
                            int* used) {
-    if (sep && prec) return launch_level_t<R, true, true, CGLS>(L, want, s, used);
-    if (sep) return launch_level_t<R, true, false, CGLS>(L, want, s, used);
-    return launch_level_t<R, false, false, CGLS>(L, want, s, used);
+    if (sep && prec) return launch_level_t<R, true, true, CGLS, HT>(L, want, s, used);
+    if (sep) return launch_level_t<R, true, false, CGLS, HT>(L, want, s, used);
+    return launch_level_t<R, false, false, CGLS, HT>(L, want, s, used);
 }
 
-// Per translation unit: one solver, a range of radii.
-cudaError_t launch_level_mr2_lo(const LevelLaunch& L, int rt, int sep, int prec, int want,
-                                cudaStream_t s, int* used);
-cudaError_t launch_level_mr2_hi(const LevelLaunch& L, int rt, int sep, int prec, int want,
-                                cudaStream_t s, int* used);
-cudaError_t launch_level_cgls_lo(const LevelLaunch& L, int rt, int sep, int prec, int want,
-                                 cudaStream_t s, int* used);
-cudaError_t launch_level_cgls_hi(const LevelLaunch& L, int rt, int sep, int prec, int want,
-                                 cudaStream_t s, int* used);
+// Per translation unit: one solver, one storage type, a range of radii
+// (names: launch_level_<solver>_<storage>_<lo|hi>).
+#define EECMG_LS_DECL(name)                                                               \
+    cudaError_t name(const LevelLaunch& L, int rt, int sep, int prec, int want, cudaStream_t s, \
+                     int* used);
+EECMG_LS_DECL(launch_level_mr2_f32_lo)
+EECMG_LS_DECL(launch_level_mr2_f32_hi)
+EECMG_LS_DECL(launch_level_mr2_bf16_lo)
+EECMG_LS_DECL(launch_level_mr2_bf16_hi)
+EECMG_LS_DECL(launch_level_cgls_f32_lo)
+EECMG_LS_DECL(launch_level_cgls_f32_hi)
+EECMG_LS_DECL(launch_level_cgls_bf16_lo)
+EECMG_LS_DECL(launch_level_cgls_bf16_hi)
+#undef EECMG_LS_DECL
 
 }  // namespace eecmg

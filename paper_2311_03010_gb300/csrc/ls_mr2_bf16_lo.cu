@@ -1,0 +1,19 @@
+// Instantiations of the persistent level solver: MR-II, BF16 storage, radii 0..5.
+#include "level_solve_impl.cuh"
+
+namespace eecmg {
+
+cudaError_t launch_level_mr2_bf16_lo(const LevelLaunch& L, int rt, int sep, int prec, int want, cudaStream_t s,
+                 int* used) {
+    switch (rt) {
+        case 0: return launch_level_r<0, false, __nv_bfloat16>(L, sep, prec, want, s, used);
+        case 1: return launch_level_r<1, false, __nv_bfloat16>(L, sep, prec, want, s, used);
+        case 2: return launch_level_r<2, false, __nv_bfloat16>(L, sep, prec, want, s, used);
+        case 3: return launch_level_r<3, false, __nv_bfloat16>(L, sep, prec, want, s, used);
+        case 4: return launch_level_r<4, false, __nv_bfloat16>(L, sep, prec, want, s, used);
+        case 5: return launch_level_r<5, false, __nv_bfloat16>(L, sep, prec, want, s, used);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace eecmg

@@ -160,6 +160,9 @@ cudaEvent_t prof_event(Profiler& pr) {
 // (each operand read or written once per phase, FP32).
 double level_solve_bytes(const eecmg_plan_s* P, int l, const Scalars& sc, bool zero_start) {
     const double n = (double)P->lv[l].h * P->lv[l].w;
+    // bytes per element of the streamed direction vectors (MR-II d, H d;
+    // CGLS s, p, q): 2 in the BF16-storage variant
+    const double e = P->opt.storage == EECMG_STORAGE_BF16 ? 2.0 : 4.0;
     double b = (zero_start ? 8.0 : 12.0) * n;  // r = g - H u
     const int K = sc.loops;
     if (P->opt.smoother == EECMG_SMOOTHER_MR2) {
@@ -170,16 +173,16 @@ double level_solve_bytes(const eecmg_plan_s* P, int l, const Scalars& sc, bool z
                 b += 16.0 * n;
             } else {
                 const int j = k - 1;
-                b += 4.0 * n * (4 + (j >= 2 ? 2 : 0) + (j >= 3 ? 2 : 0) + 4 + 3);
+                b += n * (4.0 * 9 + e * (2 + (j >= 2 ? 2 : 0) + (j >= 3 ? 2 : 0)));
             }
         }
         const int j = sc.iters;
         if ((sc.stopped == 0 || sc.stopped == 4) && j >= 1)
-            b += 4.0 * n * (4 + (j >= 2 ? 2 : 0) + (j >= 3 ? 2 : 0) + 4);
+            b += n * (4.0 * 6 + e * (2 + (j >= 2 ? 2 : 0) + (j >= 3 ? 2 : 0)));
     } else {
-        if (K > 0 || sc.iters > 0) b += 12.0 * n;  // s = H^T r, p = s
-        b += (8.0 + 24.0) * n * K;                 // q = H p; u, r update
-        if (K > 1) b += (8.0 + 12.0) * n * (K - 1);  // s = H^T r; p = s + beta p
+        if (K > 0 || sc.iters > 0) b += (4.0 + 2 * e) * n;  // s = H^T r, p = s
+        b += (2 * e + 16.0 + 2 * e) * n * K;              // q = H p; u, r update
+        if (K > 1) b += (4.0 + e + 3 * e) * n * (K - 1);  // s = H^T r; p = s + beta p
     }
     return b;
 }
@@ -243,6 +246,7 @@ eecmg_status solve_level_enqueue(eecmg_plan_s* P, int l, const float* g, float* 
     const Taps* tHT = P->dtaps + 2 * l + 1;
     const int rt = L.rt, sepH = L.sepH, sepHT = L.sepHT, prec = P->opt.precise_conv;
     const bool mr2 = P->opt.smoother == EECMG_SMOOTHER_MR2;
+    const int bf16 = P->opt.storage == EECMG_STORAGE_BF16 ? 1 : 0;
     float** V = P->vec;
 
     if (P->opt.persistent) {
@@ -273,11 +277,11 @@ eecmg_status solve_level_enqueue(eecmg_plan_s* P, int l, const float* g, float* 
             Profiler::Rec rec{KC_LEVEL, zero_start ? 1.0 : 0.0, prof_event(P->prof),
                               prof_event(P->prof), l};
             cudaEventRecord(rec.e0, s);
-            CK(launch_level_solve(J, rt, mr2 ? sepH : sepH, prec, mr2 ? 0 : 1, s, &used));
+            CK(launch_level_solve(J, rt, sepH, prec, mr2 ? 0 : 1, bf16, s, &used));
             cudaEventRecord(rec.e1, s);
             P->prof.recs.push_back(rec);
         } else {
-            CK(launch_level_solve(J, rt, mr2 ? sepH : sepH, prec, mr2 ? 0 : 1, s, &used));
+            CK(launch_level_solve(J, rt, sepH, prec, mr2 ? 0 : 1, bf16, s, &used));
         }
         return EECMG_OK;
     }
@@ -507,8 +511,9 @@ eecmg_status eecmg_plan(int width, int height, int levels, const double* psf, in
         return set_error(EECMG_ERR_INVALID_ARG, "eecmg_plan: invalid option value");
     if (o.stop == EECMG_STOP_DISCREPANCY && (!(o.c > 0.0) || !(o.delta >= 0.0)))
         return set_error(EECMG_ERR_INVALID_ARG, "eecmg_plan: discrepancy rule needs c > 0, delta >= 0");
-    if (o.storage != EECMG_STORAGE_FP32)
-        return set_error(EECMG_ERR_UNSUPPORTED, "eecmg_plan: BF16 storage is not available in this build");
+    if (o.storage == EECMG_STORAGE_BF16 && !o.persistent)
+        return set_error(EECMG_ERR_UNSUPPORTED,
+                         "eecmg_plan: BF16 storage needs the persistent level solve (persistent = 1)");
     double sum = 0.0;
     for (int i = 0; i < psf_w * psf_h; ++i) {
         if (!std::isfinite(psf[i])) return set_error(EECMG_ERR_INVALID_ARG, "eecmg_plan: PSF has non-finite entries");

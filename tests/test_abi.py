@@ -52,14 +52,12 @@ def test_version_and_defaults(lib):
     (dict(alpha=0.3), 1), (dict(alpha=-0.1), 1), (dict(k=0.0), 1),
     (dict(iters=[1, -1, 2]), 1),
     (dict(psf=np.tri(5)), 2),            # MR-II needs a centrosymmetric PSF
-    (dict(storage="bf16"), 2),
+    (dict(storage="bf16", persistent=0), 2),  # BF16 storage needs the persistent solve
 ])
 def test_plan_validation_without_gpu(lib, args, status):
     kw = dict(width=64, height=64, levels=3, psf=np.ones((3, 3)) / 9, alpha=0.2, k=10.0)
     kw.update(args)
-    opts = {}
-    if "storage" in kw:
-        opts["storage"] = kw.pop("storage")
+    opts = {k: kw.pop(k) for k in ("storage", "persistent") if k in kw}
     with pytest.raises(lib.EecmgError) as ei:
         lib.eecmg_plan(kw["width"], kw["height"], kw["levels"], kw["psf"], kw["alpha"], kw["k"],
                        kw.get("iters"), **opts)
