@@ -67,11 +67,13 @@ enum { EECMG_PROLONG_EECMG = 0, EECMG_PROLONG_IECMG_P = 1, EECMG_PROLONG_IECMG_L
  *                         adjoint under the RMS inner product of Eq. 10;
  *                         GALERKIN_RENORM rescales each coarse PSF to the
  *                         fine PSF's sum.
- *   storage = FP32        BF16 stores the streamed Krylov direction vectors
- *                         (MR-II: d and H d; CGLS: s, p, q) as bf16, rounded
- *                         to nearest even; Lanczos vectors, u and r stay FP32,
- *                         arithmetic is FP32 and scalars FP64.  Needs
- *                         persistent = 1 (else EECMG_ERR_UNSUPPORTED).
+ *   storage = FP32        BF16 stores the Krylov search directions (MR-II: the
+ *                         d history; CGLS: s and p) as bf16, rounded to
+ *                         nearest even.  Lanczos vectors, H d, q = H p, u and
+ *                         r stay FP32, arithmetic is FP32 and scalars FP64,
+ *                         so residuals and stopping decisions follow the
+ *                         stored directions exactly.  Needs persistent = 1
+ *                         (else EECMG_ERR_UNSUPPORTED).
  *   stop = FIXED          exactly m_l iterations (Section 2 note), unless
  *                         DISCREPANCY: stop when ||r||_RMS <= c * delta.
  *   c = 1.1, delta = 0    discrepancy constant and noise level ||e||_RMS.
@@ -88,6 +90,11 @@ enum { EECMG_PROLONG_EECMG = 0, EECMG_PROLONG_IECMG_P = 1, EECMG_PROLONG_IECMG_L
  *                         convolutions; 0 = plain FMA accumulation.
  *   persistent = 1        one cooperative launch per level solve (grid
  *                         barriers inside); 0 = one launch per phase.
+ *   workspace = 1         allocate the plan's device workspace; 0 = the plan
+ *                         is a description only (no device memory), usable
+ *                         with eecmg_server_submit and eecmg_plan_info; every
+ *                         entry point that runs kernels on it returns
+ *                         EECMG_ERR_INVALID_ARG.
  */
 typedef struct {
     int smoother;
@@ -103,6 +110,7 @@ typedef struct {
     int use_graph;
     int precise_conv;
     int persistent;
+    int workspace;
 } eecmg_options;
 
 typedef struct eecmg_plan_s *eecmg_plan_t;

@@ -18,37 +18,13 @@
 #include <memory>
 #include <mutex>
 #include <string>
+#include <tuple>
 #include <vector>
 
+#include "batch.hpp"
 #include "launch.hpp"
-#include "level_solve.hpp"
-#include "plan.hpp"
 
 namespace eecmg {
-
-namespace {
-
-struct Wave {
-    const LevelJob* d_jobs = nullptr;
-    const unsigned short* d_block_job = nullptr;
-    int njobs = 0, blocks = 0, rt = 0, sep = 0, prec = 0, cgls = 0, bf16 = 0;
-};
-
-struct BatchCtx {
-    std::vector<eecmg_plan_s*> plans;
-    std::vector<std::vector<Wave>> steps;  // per cascade step
-    void* dmem = nullptr;
-    cudaStream_t cap_stream = nullptr;
-    cudaGraphExec_t gexec = nullptr;
-    ~BatchCtx() {
-        if (gexec) cudaGraphExecDestroy(gexec);
-        if (cap_stream) cudaStreamDestroy(cap_stream);
-        if (dmem) cudaFree(dmem);
-    }
-};
-
-std::mutex g_batch_mu;
-std::map<std::vector<eecmg_plan_s*>, std::unique_ptr<BatchCtx>> g_batches;
 
 LevelJob make_job(eecmg_plan_s* P, int l) {
     LevelPlan& L = P->lv[l];
@@ -77,61 +53,87 @@ LevelJob make_job(eecmg_plan_s* P, int l) {
     return J;
 }
 
+eecmg_status plan_waves(const std::vector<std::pair<eecmg_plan_s*, int>>& items,
+                        std::vector<HostWave>& waves) {
+    waves.clear();
+    // instantiation key -> indices of items
+    std::map<std::tuple<int, int, int, int>, std::vector<int>> groups;
+    for (int i = 0; i < (int)items.size(); ++i) {
+        eecmg_plan_s* P = items[i].first;
+        const int l = items[i].second;
+        const int cg = P->opt.smoother == EECMG_SMOOTHER_CGLS ? 1 : 0;
+        const int bf = P->opt.storage == EECMG_STORAGE_BF16 ? 1 : 0;
+        groups[{cg, P->lv[l].sepH, P->opt.precise_conv, bf}].push_back(i);
+    }
+    for (auto& kv : groups) {
+        const int cg = std::get<0>(kv.first), sep = std::get<1>(kv.first),
+                  prec = std::get<2>(kv.first), bf = std::get<3>(kv.first);
+        int rt = 0;
+        for (int i : kv.second) rt = std::max(rt, items[i].first->lv[items[i].second].rt);
+        const int cap = level_capacity(rt, sep, prec, cg, bf);
+        if (cap <= 0) return set_error(EECMG_ERR_CUDA, "batched level solve: occupancy query failed");
+        HostWave cur;
+        cur.rt = rt;
+        cur.sep = sep;
+        cur.prec = prec;
+        cur.cgls = cg;
+        cur.bf16 = bf;
+        for (int i : kv.second) {
+            const LevelPlan& Lp = items[i].first->lv[items[i].second];
+            const int nb = std::max(1, std::min(cap, level_want_blocks(Lp.h, Lp.w)));
+            if (cur.blocks + nb > cap && !cur.jobs.empty()) {  // next wave
+                waves.push_back(cur);
+                cur.jobs.clear();
+                cur.block_job.clear();
+                cur.blocks = 0;
+            }
+            LevelJob J = make_job(items[i].first, items[i].second);
+            J.block0 = cur.blocks;
+            J.nblocks = nb;
+            for (int b = 0; b < nb; ++b) cur.block_job.push_back((unsigned short)cur.jobs.size());
+            cur.jobs.push_back(J);
+            cur.blocks += nb;
+        }
+        if (!cur.jobs.empty()) waves.push_back(cur);
+    }
+    return EECMG_OK;
+}
+
+namespace {
+
+struct Wave {
+    const LevelJob* d_jobs = nullptr;
+    const unsigned short* d_block_job = nullptr;
+    int njobs = 0, blocks = 0, rt = 0, sep = 0, prec = 0, cgls = 0, bf16 = 0;
+};
+
+struct BatchCtx {
+    std::vector<eecmg_plan_s*> plans;
+    std::vector<std::vector<Wave>> steps;  // per cascade step
+    void* dmem = nullptr;
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    ~BatchCtx() {
+        if (gexec) cudaGraphExecDestroy(gexec);
+        if (cap_stream) cudaStreamDestroy(cap_stream);
+        if (dmem) cudaFree(dmem);
+    }
+};
+
+std::mutex g_batch_mu;
+std::map<std::vector<eecmg_plan_s*>, std::unique_ptr<BatchCtx>> g_batches;
+
 // Builds the job tables of every step (one device allocation).
 eecmg_status build_ctx(BatchCtx& C) {
     int maxL = 0;
     for (auto* P : C.plans) maxL = std::max(maxL, P->L);
-    struct HostWave {
-        std::vector<LevelJob> jobs;
-        std::vector<unsigned short> block_job;
-        int blocks = 0, rt = 0, sep = 0, prec = 0, cgls = 0, bf16 = 0;
-    };
     std::vector<std::vector<HostWave>> hsteps(maxL);
     for (int s = 0; s < maxL; ++s) {
-        // group key -> indices of plans
-        std::map<std::tuple<int, int, int, int>, std::vector<int>> groups;
-        for (int i = 0; i < (int)C.plans.size(); ++i) {
-            eecmg_plan_s* P = C.plans[i];
-            if (s >= P->L) continue;
-            const int cg = P->opt.smoother == EECMG_SMOOTHER_CGLS ? 1 : 0;
-            const int bf = P->opt.storage == EECMG_STORAGE_BF16 ? 1 : 0;
-            groups[{cg, P->lv[s].sepH, P->opt.precise_conv, bf}].push_back(i);
-        }
-        for (auto& kv : groups) {
-            const int cg = std::get<0>(kv.first), sep = std::get<1>(kv.first),
-                      prec = std::get<2>(kv.first), bf = std::get<3>(kv.first);
-            int rt = 0;
-            for (int i : kv.second) rt = std::max(rt, C.plans[i]->lv[s].rt);
-            const int cap = level_capacity(rt, sep, prec, cg, bf);
-            if (cap <= 0) return set_error(EECMG_ERR_CUDA, "eecmg_restore_batched: occupancy query failed");
-            // blocks per job: the same count as the job's solve alone (so the
-            // result is bitwise the same); jobs that do not fit start a new wave
-            std::vector<int> want;
-            for (int i : kv.second)
-                want.push_back(std::min(cap, level_want_blocks(C.plans[i]->lv[s].h, C.plans[i]->lv[s].w)));
-            HostWave cur;
-            cur.rt = rt;
-            cur.sep = sep;
-            cur.prec = prec;
-            cur.cgls = cg;
-            cur.bf16 = bf;
-            for (size_t k = 0; k < kv.second.size(); ++k) {
-                const int nb = std::max(1, want[k]);
-                if (cur.blocks + nb > cap && !cur.jobs.empty()) {  // next wave
-                    hsteps[s].push_back(cur);
-                    cur.jobs.clear();
-                    cur.block_job.clear();
-                    cur.blocks = 0;
-                }
-                LevelJob J = make_job(C.plans[kv.second[k]], s);
-                J.block0 = cur.blocks;
-                J.nblocks = nb;
-                for (int b = 0; b < nb; ++b) cur.block_job.push_back((unsigned short)cur.jobs.size());
-                cur.jobs.push_back(J);
-                cur.blocks += nb;
-            }
-            if (!cur.jobs.empty()) hsteps[s].push_back(cur);
-        }
+        std::vector<std::pair<eecmg_plan_s*, int>> items;
+        for (auto* P : C.plans)
+            if (s < P->L) items.push_back({P, s});
+        eecmg_status st = plan_waves(items, hsteps[s]);
+        if (st != EECMG_OK) return st;
     }
     size_t bytes = 0;
     for (auto& st : hsteps)

@@ -1,0 +1,33 @@
+// batch.hpp -- grouping of many level solves into persistent cooperative
+// launches (shared by the batched restoration and the server).
+#pragma once
+
+#include <utility>
+#include <vector>
+
+#include "level_solve.hpp"
+#include "plan.hpp"
+
+namespace eecmg {
+
+// One cooperative launch: a table of jobs, block b of the grid serving job
+// block_job[b].  All jobs share the kernel instantiation (solver,
+// separability, precision, storage) and the radius rt (the largest of them).
+struct HostWave {
+    std::vector<LevelJob> jobs;
+    std::vector<unsigned short> block_job;
+    int blocks = 0, rt = 0, sep = 0, prec = 0, cgls = 0, bf16 = 0;
+};
+
+// The level-l solve of plan P as a job (buffers from P's workspace).
+LevelJob make_job(eecmg_plan_s* P, int l);
+
+// Groups the level solves items[i] = (plan, level) into waves.  Every job
+// gets the block count of the same solve launched alone, so each result is
+// bitwise that of the plan's own restoration; jobs that do not fit the
+// co-resident capacity of their instantiation start a new wave.  Groups come
+// out in a fixed order (by instantiation key, then item order).
+eecmg_status plan_waves(const std::vector<std::pair<eecmg_plan_s*, int>>& items,
+                        std::vector<HostWave>& waves);
+
+}  // namespace eecmg

@@ -57,26 +57,26 @@ __device__ __forceinline__ StepCoef step_coef(const Scalars* sc) {
 }
 
 // MR-II step j on pixels 4q..4q+3 (coherent loads); returns the new r.  The
-// direction history d, H d is stored as HT (FP32, or BF16 in the BF16-storage
-// variant); arithmetic is FP32.
+// direction history d is stored as HT (FP32, or BF16 in the BF16-storage
+// variant); H d stays FP32, so the residual recurrence, every scalar and the
+// stopping decisions are those of the FP32 path and only u sees the rounding.
 template <typename HT>
 __device__ __forceinline__ float4 mr_step4(const LevelJob& J, int j, size_t q, const StepCoef& c) {
     using IO = VecIO<HT>;
     const int sj = j & 1, sj1 = sj ^ 1;
     HT* dd[2] = {reinterpret_cast<HT*>(J.d[0]), reinterpret_cast<HT*>(J.d[1])};
-    HT* hh[2] = {reinterpret_cast<HT*>(J.hd[0]), reinterpret_cast<HT*>(J.hd[1])};
     float4 dj = mul4(c.dw, ld4cg(J.v[sj], q));
     float4 hj = mul4(c.dinv, ld4cg(J.aw[sj], q));
     if (j >= 2) {
         dj = fma4(-c.d1, IO::ld4(dd[sj1], q), dj);
-        hj = fma4(-c.d1, IO::ld4(hh[sj1], q), hj);
+        hj = fma4(-c.d1, ld4cg(J.hd[sj1], q), hj);
     }
     if (j >= 3) {
         dj = fma4(-c.d2, IO::ld4(dd[sj], q), dj);
-        hj = fma4(-c.d2, IO::ld4(hh[sj], q), hj);
+        hj = fma4(-c.d2, ld4cg(J.hd[sj], q), hj);
     }
     IO::st4(dd[sj], q, dj);
-    IO::st4(hh[sj], q, hj);
+    st4(J.hd[sj], q, hj);
     st4(J.u, q, fma4(c.tau, dj, ld4cg(J.u, q)));
     const float4 rv = fma4(-c.tau, hj, ld4cg(J.r, q));
     st4(J.r, q, rv);
@@ -90,19 +90,18 @@ __device__ __forceinline__ float mr_step_px(const LevelJob& J, int j, size_t i, 
     using IO = VecIO<HT>;
     const int sj = j & 1, sj1 = sj ^ 1;
     HT* dd[2] = {reinterpret_cast<HT*>(J.d[0]), reinterpret_cast<HT*>(J.d[1])};
-    HT* hh[2] = {reinterpret_cast<HT*>(J.hd[0]), reinterpret_cast<HT*>(J.hd[1])};
     float dj = dw * ldcg(J.v[sj] + i);
     float hj = dinv * ldcg(J.aw[sj] + i);
     if (j >= 2) {
         dj = fmaf(-d1, IO::ld(dd[sj1], i), dj);
-        hj = fmaf(-d1, IO::ld(hh[sj1], i), hj);
+        hj = fmaf(-d1, ldcg(J.hd[sj1] + i), hj);
     }
     if (j >= 3) {
         dj = fmaf(-d2, IO::ld(dd[sj], i), dj);
-        hj = fmaf(-d2, IO::ld(hh[sj], i), hj);
+        hj = fmaf(-d2, ldcg(J.hd[sj] + i), hj);
     }
     IO::st(dd[sj], i, dj);
-    IO::st(hh[sj], i, hj);
+    J.hd[sj][i] = hj;
     J.u[i] = fmaf(tau, dj, ldcg(J.u + i));
     const float rv = fmaf(-tau, hj, ldcg(J.r + i));
     J.r[i] = rv;
@@ -293,7 +292,9 @@ __global__ void __launch_bounds__(NTHREADS) k_level_mr2(LevelLaunch LL) {
 
 template <int R, bool SEP, bool PREC, typename HT>
 __global__ void __launch_bounds__(NTHREADS) k_level_cgls(LevelLaunch LL) {
-    using IO = VecIO<HT>;  // s, p, q stored as HT; u, r FP32
+    // s and p are stored as HT; q = H p stays FP32 (computed from the stored
+    // p), so u and the residual recurrence see the same direction
+    using IO = VecIO<HT>;
     __shared__ ConvSmem<R, SEP> S;
     __shared__ LevelJob sJ;
     if (threadIdx.x == 0) sJ = LL.jobs ? LL.jobs[LL.block_job[blockIdx.x]] : LL.job;
@@ -308,7 +309,7 @@ __global__ void __launch_bounds__(NTHREADS) k_level_cgls(LevelLaunch LL) {
     float* rv_ = J.r;
     HT* sv = reinterpret_cast<HT*>(J.v[0]);   // s
     HT* pv = reinterpret_cast<HT*>(J.v[1]);   // p
-    HT* qv = reinterpret_cast<HT*>(J.aw[0]);  // q
+    float* qv = J.aw[0];                      // q
     conv_stage_taps<R, SEP>(S, J.taps);
     __syncthreads();
     {
@@ -353,9 +354,8 @@ __global__ void __launch_bounds__(NTHREADS) k_level_cgls(LevelLaunch LL) {
         {
             float a0 = 0.f;
             conv_phase<R, SEP, PREC, false, HT>(S, pv, h, w, nb, bid, [&](size_t idx, float z, float) {
-                IO::st(qv, idx, z);
-                const float zq = IO::ld(qv, idx);  // the stored value enters <q, q>
-                a0 = fmaf(zq, zq, a0);
+                qv[idx] = z;
+                a0 = fmaf(z, z, a0);
             });
             double v[1] = {(double)a0};
             if (!group_reduce<1>(v, J.partials, J.gs, nb, bid,
@@ -369,14 +369,14 @@ __global__ void __launch_bounds__(NTHREADS) k_level_cgls(LevelLaunch LL) {
             const size_t n4 = n >> 2;
             for (size_t q = (size_t)bid * NTHREADS + threadIdx.x; q < n4; q += stride) {
                 st4(J.u, q, fma4(a, IO::ld4(pv, q), ld4cg(J.u, q)));
-                const float4 r = fma4(-a, IO::ld4(qv, q), ld4cg(rv_, q));
+                const float4 r = fma4(-a, ld4cg(qv, q), ld4cg(rv_, q));
                 st4(rv_, q, r);
                 arr = dot4(r, r, arr);
             }
             if (bid == 0)
                 for (size_t i = 4 * n4 + threadIdx.x; i < n; i += NTHREADS) {
                     J.u[i] = fmaf(a, IO::ld(pv, i), ldcg(J.u + i));
-                    const float r = fmaf(-a, IO::ld(qv, i), ldcg(rv_ + i));
+                    const float r = fmaf(-a, ldcg(qv + i), ldcg(rv_ + i));
                     rv_[i] = r;
                     arr = fmaf(r, r, arr);
                 }

@@ -27,6 +27,11 @@ eecmg_status set_error(eecmg_status st, const std::string& msg) {
     return st;
 }
 
+static eecmg_status no_ws(const char* who) {
+    return set_error(EECMG_ERR_INVALID_ARG,
+                     std::string(who) + ": the plan is a description only (workspace = 0)");
+}
+
 // Economy schedule m_l (Section 2) in exact integer arithmetic, l = 1..L:
 //   l > L/2:  m_l = ceil((L - L/2)^2 4^(L-l)) = ceil(L^2 4^(L-l) / 4)
 //   l <= L/2: m_l = ceil((L - 1.5 l) 4^(l-1)) = ceil((2L - 3l) 4^(l-1) / 2)
@@ -160,8 +165,8 @@ cudaEvent_t prof_event(Profiler& pr) {
 // (each operand read or written once per phase, FP32).
 double level_solve_bytes(const eecmg_plan_s* P, int l, const Scalars& sc, bool zero_start) {
     const double n = (double)P->lv[l].h * P->lv[l].w;
-    // bytes per element of the streamed direction vectors (MR-II d, H d;
-    // CGLS s, p, q): 2 in the BF16-storage variant
+    // bytes per element of the BF16-able direction vectors (MR-II d; CGLS s,
+    // p): 2 in the BF16-storage variant
     const double e = P->opt.storage == EECMG_STORAGE_BF16 ? 2.0 : 4.0;
     double b = (zero_start ? 8.0 : 12.0) * n;  // r = g - H u
     const int K = sc.loops;
@@ -173,15 +178,15 @@ double level_solve_bytes(const eecmg_plan_s* P, int l, const Scalars& sc, bool z
                 b += 16.0 * n;
             } else {
                 const int j = k - 1;
-                b += n * (4.0 * 9 + e * (2 + (j >= 2 ? 2 : 0) + (j >= 3 ? 2 : 0)));
+                b += n * (4.0 * 9 + (4.0 + e) * (1 + (j >= 2 ? 1 : 0) + (j >= 3 ? 1 : 0)));
             }
         }
         const int j = sc.iters;
         if ((sc.stopped == 0 || sc.stopped == 4) && j >= 1)
-            b += n * (4.0 * 6 + e * (2 + (j >= 2 ? 2 : 0) + (j >= 3 ? 2 : 0)));
+            b += n * (4.0 * 6 + (4.0 + e) * (1 + (j >= 2 ? 1 : 0) + (j >= 3 ? 1 : 0)));
     } else {
         if (K > 0 || sc.iters > 0) b += (4.0 + 2 * e) * n;  // s = H^T r, p = s
-        b += (2 * e + 16.0 + 2 * e) * n * K;              // q = H p; u, r update
+        b += (e + 4.0 + e + 4.0 + 16.0) * n * K;          // q = H p; u, r update
         if (K > 1) b += (4.0 + e + 3 * e) * n * (K - 1);  // s = H^T r; p = s + beta p
     }
     return b;
@@ -236,6 +241,20 @@ cudaError_t prof_flush(eecmg_plan_s* P) {
 // ---------------------------------------------------------------------------
 
 namespace eecmg {
+
+void bind_workspace(eecmg_plan_s* P, char* ws) {
+    const PlanLayout& Y = P->layout;
+    P->ws = ws;
+    for (int l = 0; l < P->L; ++l) {
+        P->lv[l].g = (float*)(ws + Y.g_off[l]);
+        P->lv[l].u = (float*)(ws + Y.u_off[l]);
+    }
+    for (int i = 0; i < eecmg_plan_s::NVEC; ++i) P->vec[i] = (float*)(ws + Y.vec_off[i]);
+    P->dtaps = (Taps*)(ws + Y.taps_off);
+    P->sc = (Scalars*)(ws + Y.sc_off);
+    P->gsync = (GroupSync*)(ws + Y.gs_off);
+    P->partials = (double*)(ws + Y.part_off);
+}
 
 eecmg_status solve_level_enqueue(eecmg_plan_s* P, int l, const float* g, float* u, int m,
                                  bool zero_start, cudaStream_t s) {
@@ -485,6 +504,7 @@ eecmg_status eecmg_default_options(eecmg_options* o) {
     o->use_graph = 1;
     o->precise_conv = 1;
     o->persistent = 1;
+    o->workspace = 1;
     return EECMG_OK;
 }
 
@@ -588,46 +608,46 @@ eecmg_status eecmg_plan(int width, int height, int levels, const double* psf, in
     }
     (void)fine_n;
     // workspace: g and u pyramids, solver vectors, taps, scalars, partials
+    PlanLayout& Y = P->layout;
     size_t off = 0;
-    std::vector<size_t> g_off(levels), u_off(levels);
+    Y.g_off.resize(levels);
+    Y.u_off.resize(levels);
     for (int l = 0; l < levels; ++l) {
-        g_off[l] = off;
+        Y.g_off[l] = off;
         off = align_up(off + sizeof(float) * P->lv[l].h * P->lv[l].w, 256);
     }
     for (int l = 0; l < levels; ++l) {
-        u_off[l] = off;
+        Y.u_off[l] = off;
         off = align_up(off + sizeof(float) * P->lv[l].h * P->lv[l].w, 256);
     }
-    size_t vec_off[eecmg_plan_s::NVEC];
     for (int i = 0; i < eecmg_plan_s::NVEC; ++i) {
-        vec_off[i] = off;
+        Y.vec_off[i] = off;
         off = align_up(off + sizeof(float) * max_n, 256);
     }
-    const size_t taps_off = off;
+    Y.taps_off = off;
     off = align_up(off + sizeof(Taps) * 2 * levels, 256);
-    const size_t sc_off = off;
+    Y.sc_off = off;
     off = align_up(off + sizeof(Scalars) * levels, 256);
-    const size_t gs_off = off;
+    Y.gs_off = off;
     off = align_up(off + sizeof(GroupSync) * levels, 256);
-    const size_t part_off = off;
+    Y.part_off = off;
     off = align_up(off + sizeof(double) * NPART * max_blocks, 256);
+    Y.bytes = off;
     P->ws_bytes = off;
+    P->max_blocks = max_blocks;
+    P->htaps = htaps;
+    if (!o.workspace) {  // a description only (serving requests)
+        *out = P;
+        return EECMG_OK;
+    }
     cudaError_t e = cudaMalloc((void**)&P->ws, off);
     if (e != cudaSuccess) {
         delete P;
         cudaGetLastError();
         return set_error(EECMG_ERR_OOM, std::string("eecmg_plan: workspace allocation failed: ") + cudaGetErrorString(e));
     }
-    for (int l = 0; l < levels; ++l) {
-        P->lv[l].g = (float*)(P->ws + g_off[l]);
-        P->lv[l].u = (float*)(P->ws + u_off[l]);
-    }
-    for (int i = 0; i < eecmg_plan_s::NVEC; ++i) P->vec[i] = (float*)(P->ws + vec_off[i]);
-    P->dtaps = (Taps*)(P->ws + taps_off);
-    P->sc = (Scalars*)(P->ws + sc_off);
-    P->gsync = (GroupSync*)(P->ws + gs_off);
-    P->partials = (double*)(P->ws + part_off);
-    P->max_blocks = max_blocks;
+    P->owns_ws = true;
+    bind_workspace(P, P->ws);
     auto cleanup = [&](cudaError_t err, const char* what) {
         cudaFree(P->ws);
         if (P->cap_stream) cudaStreamDestroy(P->cap_stream);
@@ -652,7 +672,7 @@ eecmg_status eecmg_plan_destroy(eecmg_plan_t P) {
     if (P->cap_stream) cudaStreamDestroy(P->cap_stream);
     prof_flush(P);
     for (cudaEvent_t e : P->prof.free_events) cudaEventDestroy(e);
-    cudaFree(P->ws);
+    if (P->owns_ws) cudaFree(P->ws);
     delete P;
     return EECMG_OK;
 }
@@ -672,6 +692,7 @@ eecmg_status eecmg_plan_info(eecmg_plan_t P, int* levels, int* level_w, int* lev
 
 eecmg_status eecmg_restore(eecmg_plan_t P, const float* g, float* u, cudaStream_t s) {
     if (!P || !g || !u) return set_error(EECMG_ERR_INVALID_ARG, "eecmg_restore: NULL argument");
+    if (!P->ws) return no_ws("eecmg_restore");
     const size_t bytes = sizeof(float) * P->W * P->H;
     LevelPlan& F = P->lv[P->L - 1];
     if (g != F.g) CK(cudaMemcpyAsync(F.g, g, bytes, cudaMemcpyDeviceToDevice, s));
@@ -684,6 +705,7 @@ eecmg_status eecmg_restore(eecmg_plan_t P, const float* g, float* u, cudaStream_
 
 eecmg_status eecmg_restore_host(eecmg_plan_t P, const float* g, float* u, cudaStream_t s) {
     if (!P || !g || !u) return set_error(EECMG_ERR_INVALID_ARG, "eecmg_restore_host: NULL argument");
+    if (!P->ws) return no_ws("eecmg_restore_host");
     const size_t bytes = sizeof(float) * P->W * P->H;
     LevelPlan& F = P->lv[P->L - 1];
     CK(cudaMemcpyAsync(F.g, g, bytes, cudaMemcpyHostToDevice, s));
@@ -697,6 +719,7 @@ eecmg_status eecmg_restore_host(eecmg_plan_t P, const float* g, float* u, cudaSt
 
 eecmg_status eecmg_plan_stats(eecmg_plan_t P, int* iters_done, double* res_rms) {
     if (!P) return set_error(EECMG_ERR_INVALID_ARG, "eecmg_plan_stats: NULL plan");
+    if (!P->ws) return no_ws("eecmg_plan_stats");
     CK(cudaStreamSynchronize(P->last_stream));
     CK(cudaStreamSynchronize(P->cap_stream));
     std::vector<Scalars> h(P->L);
@@ -713,6 +736,7 @@ eecmg_status eecmg_plan_stats(eecmg_plan_t P, int* iters_done, double* res_rms) 
 
 static eecmg_status check_level(eecmg_plan_t P, int level, const char* who) {
     if (!P) return set_error(EECMG_ERR_INVALID_ARG, std::string(who) + ": NULL plan");
+    if (!P->ws) return no_ws(who);
     if (level < 0 || level >= P->L) return set_error(EECMG_ERR_INVALID_ARG, std::string(who) + ": level out of range");
     return EECMG_OK;
 }
@@ -803,6 +827,7 @@ eecmg_status eecmg_level_solve(eecmg_plan_t P, int level, const float* g, float*
 
 eecmg_status eecmg_plan_profile(eecmg_plan_t P, int enable) {
     if (!P) return set_error(EECMG_ERR_INVALID_ARG, "eecmg_plan_profile: NULL plan");
+    if (!P->ws) return no_ws("eecmg_plan_profile");
     CK(prof_flush(P));
     P->prof.on = enable != 0;
     for (int c = 0; c < KC_COUNT; ++c) {
@@ -838,6 +863,8 @@ eecmg_status eecmg_restore_batched(const eecmg_plan_t* plans, const float* const
     if (n < 0 || (n > 0 && (!plans || !g || !u)))
         return set_error(EECMG_ERR_INVALID_ARG, "eecmg_restore_batched: bad arguments");
     if (n == 0) return EECMG_OK;
+    for (int i = 0; i < n; ++i)
+        if (plans[i] && !plans[i]->ws) return no_ws("eecmg_restore_batched");
     for (int i = 0; i < n; ++i)
         if (plans[i] && plans[i]->prof.on)
             return set_error(EECMG_ERR_INVALID_ARG,

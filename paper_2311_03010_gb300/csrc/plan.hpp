@@ -47,6 +47,15 @@ int schedule_m(int L, int l);
 
 }  // namespace eecmg
 
+// Byte offsets of a plan's workspace regions (the layout is fixed by the
+// plan's description; a workspace can be bound anywhere 256-byte aligned).
+struct PlanLayout {
+    std::vector<size_t> g_off, u_off;  // per level
+    size_t vec_off[9] = {};
+    size_t taps_off = 0, sc_off = 0, gs_off = 0, part_off = 0;
+    size_t bytes = 0;                  // total
+};
+
 struct eecmg_plan_s {
     int W = 0, H = 0, L = 0;
     double tau = 0.2, kpm = 10.0;
@@ -54,6 +63,9 @@ struct eecmg_plan_s {
     eecmg_options opt{};
     int device = 0;
     std::vector<eecmg::LevelPlan> lv;
+    std::vector<eecmg::Taps> htaps;     // host copy of the level taps
+    PlanLayout layout;
+    bool owns_ws = false;
     char* ws = nullptr;
     size_t ws_bytes = 0;
     size_t max_blocks = 0;
@@ -70,6 +82,8 @@ struct eecmg_plan_s {
 };
 
 namespace eecmg {
+// Points the plan's level and solver buffers into ws (P->layout.bytes long).
+void bind_workspace(eecmg_plan_s* P, char* ws);
 eecmg_status solve_level_enqueue(eecmg_plan_s* P, int l, const float* g, float* u, int m,
                                  bool zero_start, cudaStream_t s);
 eecmg_status prolong_enqueue(eecmg_plan_s* P, int l, cudaStream_t s);

@@ -1,23 +1,524 @@
 // server.cu -- continuous-batching restoration server (C ABI).
-#include "plan.hpp"
+//
+// Requests are admitted first come, first served while their workspace fits
+// in the server's device arena (one allocation of mem_budget_bytes made at
+// creation, carved first-fit) and at most max_slots are active.  An admitted
+// request gets its plan's workspace layout inside the arena: data and
+// solution pyramids, solver vectors, taps, scalars and barrier state stay
+// resident on the device until it completes.
+//
+// A scheduler thread advances every active request together.  One tick runs
+// one cascade step (Algorithm 2) of each active request: for a request just
+// admitted, the copy of its data and the restriction of the data pyramid;
+// then per request the prolongation to its current level (or the zero
+// start); then the level solves of all of them as jobs of persistent
+// cooperative launches (one per kernel instantiation, see batch.hpp).
+// Requests admitted at different times therefore share launches while they
+// sit at different levels.  Each job keeps the block count of the same solve
+// launched alone, so a served result is bitwise the result of eecmg_restore
+// on the request's plan.  Two ticks may be in flight; a request completes
+// with the tick that ran its finest level, and its latency runs from
+// submission to that tick's end event on the device clock.
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "batch.hpp"
+#include "launch.hpp"
 
 using namespace eecmg;
 
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+constexpr int RING = 2;              // ticks in flight
+constexpr size_t QUEUE_CAP = 65536;  // queued (not yet admitted) requests
+constexpr int MAX_LEVELS = 30;
+
+size_t round256(size_t b) { return (b + 255) / 256 * 256; }
+
+// First-fit allocator over [0, cap): free ranges by offset, coalesced on
+// release.
+class Arena {
+public:
+    void reset(size_t cap) {
+        free_.clear();
+        if (cap) free_[0] = cap;
+        used_ = 0;
+    }
+    bool alloc(size_t bytes, size_t* off) {
+        bytes = round256(bytes);
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            if (it->second < bytes) continue;
+            *off = it->first;
+            const size_t rest = it->second - bytes, start = it->first + bytes;
+            free_.erase(it);
+            if (rest) free_[start] = rest;
+            used_ += bytes;
+            return true;
+        }
+        return false;
+    }
+    void release(size_t off, size_t bytes) {
+        bytes = round256(bytes);
+        used_ -= bytes;
+        auto it = free_.emplace(off, bytes).first;
+        auto nx = std::next(it);
+        if (nx != free_.end() && it->first + it->second == nx->first) {
+            it->second += nx->second;
+            free_.erase(nx);
+        }
+        if (it != free_.begin()) {
+            auto pv = std::prev(it);
+            if (pv->first + pv->second == it->first) {
+                pv->second += it->second;
+                free_.erase(it);
+            }
+        }
+    }
+    size_t used() const { return used_; }
+
+private:
+    std::map<size_t, size_t> free_;
+    size_t used_ = 0;
+};
+
+struct Request {
+    uint64_t ticket = 0;
+    const eecmg_plan_s* tmpl = nullptr;
+    const float* g = nullptr;
+    float* u = nullptr;
+    Clock::time_point t_submit;
+    eecmg_plan_s slot;  // the request's resident state (workspace in the arena)
+    size_t off = 0, bytes = 0;
+    int sidx = -1;      // status area
+    int step = 0;       // next cascade step
+};
+
+struct Result {
+    int done = 0;
+    eecmg_status st = EECMG_OK;
+    double latency_ms = 0.0;
+};
+
+}  // namespace
+
+struct eecmg_server_s {
+    int device = 0, nsm = 0, max_slots = 0;
+    size_t budget = 0;
+    char* arena_mem = nullptr;
+    Arena arena;
+    cudaStream_t stream = nullptr;
+    // job tables of the ticks in flight
+    size_t ring_bytes = 0;
+    char* d_ring = nullptr;  // RING x ring_bytes, device
+    char* h_ring = nullptr;  // RING x ring_bytes, pinned host
+    cudaEvent_t ev[RING] = {};
+    bool busy[RING] = {};
+    std::vector<Request*> fin[RING];
+    // per-slot status areas (pinned): every level's Scalars, then GroupSync
+    char* h_stat = nullptr;
+    size_t stat_stride = 0;
+    std::vector<int> free_sidx;
+    cudaEvent_t base_ev = nullptr;
+    Clock::time_point base_host;
+    // shared state (mu)
+    std::mutex mu;
+    std::condition_variable cv, cv_done;
+    std::deque<Request*> queue;
+    std::vector<Request*> active;
+    std::unordered_map<uint64_t, Result> results;
+    uint64_t next_ticket = 1;
+    size_t outstanding = 0;
+    bool stop = false;
+    eecmg_status fatal = EECMG_OK;
+    std::string fatal_msg;
+    std::thread th;
+    uint64_t tick = 0;  // scheduler thread only
+};
+
+namespace {
+
+#define SCK(call)                                                                          \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess)                                                             \
+            return set_error(EECMG_ERR_CUDA, std::string("eecmg_server: ") + #call + ": " + \
+                                                 cudaGetErrorString(e_));                  \
+    } while (0)
+
+// Gives the request its plan's layout at ws (host-side only).
+void bind_slot(Request* r, char* ws) {
+    eecmg_plan_s& S = r->slot;
+    const eecmg_plan_s& T = *r->tmpl;
+    S.W = T.W;
+    S.H = T.H;
+    S.L = T.L;
+    S.tau = T.tau;
+    S.kpm = T.kpm;
+    S.conv_tol2 = T.conv_tol2;
+    S.opt = T.opt;
+    S.device = T.device;
+    S.lv = T.lv;
+    S.layout = T.layout;
+    S.ws_bytes = T.ws_bytes;
+    S.max_blocks = T.max_blocks;
+    S.owns_ws = false;
+    bind_workspace(&S, ws);
+}
+
+char* stat_area(eecmg_server_s* S, int sidx) { return S->h_stat + (size_t)sidx * S->stat_stride; }
+
+// Enqueues tick k's work on the server stream; `finishing` receives the
+// requests whose finest level ran in it.
+eecmg_status enqueue_tick(eecmg_server_s* S, const std::vector<Request*>& admitted, int k,
+                          std::vector<Request*>& finishing) {
+    cudaStream_t s = S->stream;
+    for (Request* r : admitted) {
+        eecmg_plan_s& P = r->slot;
+        const PlanLayout& Y = P.layout;
+        // scalars, barrier state and partials start at zero, as in a new plan
+        SCK(cudaMemsetAsync(P.ws + Y.sc_off, 0, Y.bytes - Y.sc_off, s));
+        SCK(cudaMemcpyAsync(P.dtaps, r->tmpl->htaps.data(), sizeof(Taps) * 2 * P.L,
+                            cudaMemcpyHostToDevice, s));
+        LevelPlan& F = P.lv[P.L - 1];
+        SCK(cudaMemcpyAsync(F.g, r->g, sizeof(float) * F.h * F.w, cudaMemcpyDeviceToDevice, s));
+        for (int l = P.L - 1; l > 0; --l)
+            SCK(launch_restrict(P.lv[l].g, P.lv[l].h, P.lv[l].w, P.lv[l - 1].g, P.lv[l - 1].h,
+                                P.lv[l - 1].w, s));
+    }
+    std::vector<std::pair<eecmg_plan_s*, int>> items;
+    items.reserve(S->active.size());
+    for (Request* r : S->active) {
+        eecmg_plan_s& P = r->slot;
+        const int st = r->step;
+        const int nzero = P.opt.prolong == EECMG_PROLONG_EECMG ? 2 : 1;
+        if (st < nzero) {
+            SCK(cudaMemsetAsync(P.lv[st].u, 0, sizeof(float) * P.lv[st].h * P.lv[st].w, s));
+        } else {
+            eecmg_status e = prolong_enqueue(&P, st, s);
+            if (e != EECMG_OK) return e;
+        }
+        items.push_back({&P, st});
+    }
+    std::vector<HostWave> waves;
+    eecmg_status e = plan_waves(items, waves);
+    if (e != EECMG_OK) return e;
+    char* h = S->h_ring + (size_t)k * S->ring_bytes;
+    char* d = S->d_ring + (size_t)k * S->ring_bytes;
+    size_t off = 0;
+    std::vector<size_t> jo(waves.size()), bo(waves.size());
+    for (size_t w = 0; w < waves.size(); ++w) {
+        const size_t jb = sizeof(LevelJob) * waves[w].jobs.size();
+        const size_t bb = sizeof(unsigned short) * waves[w].block_job.size();
+        if (off + round256(jb) + round256(bb) > S->ring_bytes)
+            return set_error(EECMG_ERR_INVALID_ARG, "eecmg_server: job table overflow");
+        jo[w] = off;
+        std::memcpy(h + off, waves[w].jobs.data(), jb);
+        off += round256(jb);
+        bo[w] = off;
+        std::memcpy(h + off, waves[w].block_job.data(), bb);
+        off += round256(bb);
+    }
+    if (off) SCK(cudaMemcpyAsync(d, h, off, cudaMemcpyHostToDevice, s));
+    for (size_t w = 0; w < waves.size(); ++w) {
+        const HostWave& W = waves[w];
+        SCK(launch_level_batch((const LevelJob*)(d + jo[w]), (const unsigned short*)(d + bo[w]),
+                               (int)W.jobs.size(), W.blocks, W.rt, W.sep, W.prec, W.cgls, W.bf16, s));
+    }
+    for (Request* r : S->active) {
+        eecmg_plan_s& P = r->slot;
+        if (r->step != P.L - 1) continue;
+        LevelPlan& F = P.lv[P.L - 1];
+        SCK(cudaMemcpyAsync(r->u, F.u, sizeof(float) * F.h * F.w, cudaMemcpyDeviceToDevice, s));
+        char* a = stat_area(S, r->sidx);
+        SCK(cudaMemcpyAsync(a, P.sc, sizeof(Scalars) * P.L, cudaMemcpyDeviceToHost, s));
+        SCK(cudaMemcpyAsync(a + sizeof(Scalars) * MAX_LEVELS, P.gsync, sizeof(GroupSync) * P.L,
+                            cudaMemcpyDeviceToHost, s));
+        finishing.push_back(r);
+    }
+    SCK(cudaEventRecord(S->ev[k], s));
+    return EECMG_OK;
+}
+
+// The request's status from its copied scalars and barrier state.
+eecmg_status request_status(eecmg_server_s* S, const Request* r) {
+    const char* a = stat_area(S, r->sidx);
+    const Scalars* sc = (const Scalars*)a;
+    const GroupSync* gs = (const GroupSync*)(a + sizeof(Scalars) * MAX_LEVELS);
+    for (int l = 0; l < r->slot.L; ++l)
+        if (gs[l].err) return EECMG_ERR_TIMEOUT;
+    for (int l = 0; l < r->slot.L; ++l)
+        if (sc[l].stopped == 3) return EECMG_ERR_NUMERIC;
+    return EECMG_OK;
+}
+
+// Waits for tick slot k and completes the requests that finished in it.
+void complete(eecmg_server_s* S, int k) {
+    cudaError_t e = cudaEventSynchronize(S->ev[k]);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, S->base_ev, S->ev[k]);
+    const Clock::time_point t_done =
+        S->base_host + std::chrono::duration_cast<Clock::duration>(std::chrono::duration<double, std::milli>(ms));
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        for (Request* r : S->fin[k]) {
+            Result& res = S->results[r->ticket];
+            res.done = 1;
+            res.st = e == cudaSuccess ? request_status(S, r) : EECMG_ERR_CUDA;
+            res.latency_ms = std::chrono::duration<double, std::milli>(t_done - r->t_submit).count();
+            S->arena.release(r->off, r->bytes);
+            S->free_sidx.push_back(r->sidx);
+            --S->outstanding;
+            delete r;
+        }
+    }
+    S->fin[k].clear();
+    S->busy[k] = false;
+    S->cv_done.notify_all();
+}
+
+bool any_busy(const eecmg_server_s* S) {
+    for (int k = 0; k < RING; ++k)
+        if (S->busy[k]) return true;
+    return false;
+}
+
+void complete_oldest(eecmg_server_s* S) {
+    for (int i = 0; i < RING; ++i) {
+        const int k = (int)((S->tick + i) % RING);
+        if (S->busy[k]) {
+            complete(S, k);
+            return;
+        }
+    }
+}
+
+// A CUDA error on the server stream: every request in the server fails.
+void fail_all(eecmg_server_s* S, eecmg_status st) {
+    cudaStreamSynchronize(S->stream);
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->fatal = st;
+    S->fatal_msg = eecmg_last_error();
+    auto fail = [&](Request* r) {
+        Result& res = S->results[r->ticket];
+        res.done = 1;
+        res.st = st;
+        if (r->sidx >= 0) {
+            S->arena.release(r->off, r->bytes);
+            S->free_sidx.push_back(r->sidx);
+        }
+        --S->outstanding;
+        delete r;
+    };
+    for (int k = 0; k < RING; ++k) {
+        for (Request* r : S->fin[k]) fail(r);
+        S->fin[k].clear();
+        S->busy[k] = false;
+    }
+    for (Request* r : S->active) fail(r);
+    S->active.clear();
+    for (Request* r : S->queue) fail(r);
+    S->queue.clear();
+    S->cv_done.notify_all();
+}
+
+void scheduler(eecmg_server_s* S) {
+    cudaSetDevice(S->device);
+    for (;;) {
+        std::vector<Request*> admitted;
+        {
+            std::unique_lock<std::mutex> lk(S->mu);
+            S->cv.wait(lk, [&] {
+                return S->stop || !S->queue.empty() || !S->active.empty() || any_busy(S);
+            });
+            if (S->queue.empty() && S->active.empty() && !any_busy(S)) {
+                if (S->stop) break;
+                continue;
+            }
+            while (!S->queue.empty() && (int)S->active.size() < S->max_slots) {
+                Request* r = S->queue.front();
+                size_t off = 0;
+                if (!S->arena.alloc(r->bytes, &off)) break;  // first come, first served
+                S->queue.pop_front();
+                r->off = off;
+                r->sidx = S->free_sidx.back();
+                S->free_sidx.pop_back();
+                bind_slot(r, S->arena_mem + off);
+                S->active.push_back(r);
+                admitted.push_back(r);
+            }
+        }
+        if (admitted.empty() && S->active.empty()) {
+            // memory is held by requests finishing in flight: wait for them
+            complete_oldest(S);
+            continue;
+        }
+        const int k = (int)(S->tick % RING);
+        if (S->busy[k]) complete(S, k);
+        std::vector<Request*> finishing;
+        eecmg_status st = enqueue_tick(S, admitted, k, finishing);
+        if (st != EECMG_OK) {
+            fail_all(S, st);
+            continue;
+        }
+        S->busy[k] = true;
+        S->fin[k] = finishing;
+        {
+            std::lock_guard<std::mutex> lk(S->mu);
+            auto done = [&](Request* r) {
+                return std::find(finishing.begin(), finishing.end(), r) != finishing.end();
+            };
+            S->active.erase(std::remove_if(S->active.begin(), S->active.end(), done), S->active.end());
+        }
+        for (Request* r : S->active) ++r->step;
+        ++S->tick;
+    }
+}
+
+void free_server(eecmg_server_s* S) {
+    if (S->stream) cudaStreamSynchronize(S->stream);
+    for (int k = 0; k < RING; ++k)
+        if (S->ev[k]) cudaEventDestroy(S->ev[k]);
+    if (S->base_ev) cudaEventDestroy(S->base_ev);
+    if (S->stream) cudaStreamDestroy(S->stream);
+    if (S->d_ring) cudaFree(S->d_ring);
+    if (S->h_ring) cudaFreeHost(S->h_ring);
+    if (S->h_stat) cudaFreeHost(S->h_stat);
+    if (S->arena_mem) cudaFree(S->arena_mem);
+    delete S;
+}
+
+}  // namespace
+
 extern "C" {
 
-eecmg_status eecmg_server_create(size_t, int, eecmg_server_t* out) {
-    if (out) *out = nullptr;
-    return set_error(EECMG_ERR_UNSUPPORTED, "eecmg_server_create: server not available in this build");
+eecmg_status eecmg_server_create(size_t mem_budget_bytes, int max_slots, eecmg_server_t* out) {
+    if (!out) return set_error(EECMG_ERR_INVALID_ARG, "eecmg_server_create: out is NULL");
+    *out = nullptr;
+    if (mem_budget_bytes == 0 || max_slots < 1 || max_slots > 4096)
+        return set_error(EECMG_ERR_INVALID_ARG,
+                         "eecmg_server_create: need mem_budget_bytes > 0 and 1 <= max_slots <= 4096");
+    auto* S = new (std::nothrow) eecmg_server_s();
+    if (!S) return set_error(EECMG_ERR_OOM, "eecmg_server_create: host allocation failed");
+    S->budget = round256(mem_budget_bytes);
+    S->max_slots = max_slots;
+    auto fail = [&](eecmg_status st, const std::string& msg) {
+        cudaGetLastError();
+        free_server(S);
+        return set_error(st, "eecmg_server_create: " + msg);
+    };
+    cudaError_t e = cudaGetDevice(&S->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&S->nsm, cudaDevAttrMultiProcessorCount, S->device);
+    if (e != cudaSuccess) return fail(EECMG_ERR_CUDA, cudaGetErrorString(e));
+    e = cudaMalloc((void**)&S->arena_mem, S->budget);
+    if (e != cudaSuccess) {
+        S->arena_mem = nullptr;
+        return fail(EECMG_ERR_OOM, std::string("arena: ") + cudaGetErrorString(e));
+    }
+    S->arena.reset(S->budget);
+    // one job per active request per tick; at most 2 x SMs blocks per job
+    S->ring_bytes = (size_t)max_slots * (round256(sizeof(LevelJob)) + 512 +
+                                         round256(sizeof(unsigned short) * 2 * (size_t)S->nsm)) + 1024;
+    S->stat_stride = round256((sizeof(Scalars) + sizeof(GroupSync)) * MAX_LEVELS);
+    e = cudaStreamCreateWithFlags(&S->stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&S->d_ring, RING * S->ring_bytes);
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&S->h_ring, RING * S->ring_bytes);
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&S->h_stat, S->stat_stride * max_slots);
+    for (int k = 0; k < RING && e == cudaSuccess; ++k) e = cudaEventCreate(&S->ev[k]);
+    if (e == cudaSuccess) e = cudaEventCreate(&S->base_ev);
+    if (e == cudaSuccess) e = cudaEventRecord(S->base_ev, S->stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(S->base_ev);
+    if (e != cudaSuccess) return fail(EECMG_ERR_CUDA, cudaGetErrorString(e));
+    S->base_host = Clock::now();
+    for (int i = max_slots - 1; i >= 0; --i) S->free_sidx.push_back(i);
+    try {
+        S->th = std::thread(scheduler, S);
+    } catch (...) {
+        return fail(EECMG_ERR_OOM, "scheduler thread");
+    }
+    *out = S;
+    return EECMG_OK;
 }
-eecmg_status eecmg_server_submit(eecmg_server_t, eecmg_plan_t, const float*, float*, uint64_t*) {
-    return set_error(EECMG_ERR_UNSUPPORTED, "eecmg_server_submit: server not available in this build");
+
+eecmg_status eecmg_server_submit(eecmg_server_t S, eecmg_plan_t P, const float* g, float* u,
+                                 uint64_t* ticket) {
+    if (!S || !P || !g || !u || !ticket)
+        return set_error(EECMG_ERR_INVALID_ARG, "eecmg_server_submit: NULL argument");
+    *ticket = 0;
+    if (P->L > MAX_LEVELS || !P->opt.persistent || P->device != S->device)
+        return set_error(EECMG_ERR_INVALID_ARG,
+                         "eecmg_server_submit: the plan must use the persistent level solve, at most "
+                         "30 levels, on the server's device");
+    if (round256(P->ws_bytes) > S->budget)
+        return set_error(EECMG_ERR_OOM, "eecmg_server_submit: the request alone exceeds the memory budget");
+    auto* r = new (std::nothrow) Request();
+    if (!r) return set_error(EECMG_ERR_OOM, "eecmg_server_submit: host allocation failed");
+    r->tmpl = P;
+    r->g = g;
+    r->u = u;
+    r->bytes = P->ws_bytes;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        if (S->fatal != EECMG_OK) {
+            delete r;
+            return set_error(S->fatal, "eecmg_server_submit: server failed earlier: " + S->fatal_msg);
+        }
+        if (S->queue.size() >= QUEUE_CAP) {
+            delete r;
+            return set_error(EECMG_ERR_BUSY, "eecmg_server_submit: queue full");
+        }
+        r->ticket = S->next_ticket++;
+        r->t_submit = Clock::now();
+        S->results[r->ticket] = Result();
+        S->queue.push_back(r);
+        ++S->outstanding;
+        *ticket = r->ticket;
+    }
+    S->cv.notify_one();
+    return EECMG_OK;
 }
-eecmg_status eecmg_server_poll(eecmg_server_t, uint64_t, int*, double*) {
-    return set_error(EECMG_ERR_UNSUPPORTED, "eecmg_server_poll: server not available in this build");
+
+eecmg_status eecmg_server_poll(eecmg_server_t S, uint64_t ticket, int* done, double* latency_ms) {
+    if (!S || !done) return set_error(EECMG_ERR_INVALID_ARG, "eecmg_server_poll: NULL argument");
+    std::lock_guard<std::mutex> lk(S->mu);
+    auto it = S->results.find(ticket);
+    if (it == S->results.end()) return set_error(EECMG_ERR_INVALID_ARG, "eecmg_server_poll: unknown ticket");
+    *done = it->second.done;
+    if (latency_ms) *latency_ms = it->second.done ? it->second.latency_ms : 0.0;
+    if (it->second.done && it->second.st != EECMG_OK)
+        return set_error(it->second.st, "eecmg_server_poll: the request failed");
+    return EECMG_OK;
 }
-eecmg_status eecmg_server_drain(eecmg_server_t) {
-    return set_error(EECMG_ERR_UNSUPPORTED, "eecmg_server_drain: server not available in this build");
+
+eecmg_status eecmg_server_drain(eecmg_server_t S) {
+    if (!S) return set_error(EECMG_ERR_INVALID_ARG, "eecmg_server_drain: NULL server");
+    std::unique_lock<std::mutex> lk(S->mu);
+    S->cv_done.wait(lk, [&] { return S->outstanding == 0; });
+    if (S->fatal != EECMG_OK) return set_error(S->fatal, "eecmg_server_drain: " + S->fatal_msg);
+    return EECMG_OK;
 }
-eecmg_status eecmg_server_destroy(eecmg_server_t) { return EECMG_OK; }
+
+eecmg_status eecmg_server_destroy(eecmg_server_t S) {
+    if (!S) return EECMG_OK;
+    {
+        std::unique_lock<std::mutex> lk(S->mu);
+        S->cv_done.wait(lk, [&] { return S->outstanding == 0; });
+        S->stop = true;
+    }
+    S->cv.notify_all();
+    if (S->th.joinable()) S->th.join();
+    free_server(S);
+    return EECMG_OK;
+}
 
 }  // extern "C"

@@ -52,6 +52,7 @@ class eecmg_options(ctypes.Structure):
         ("use_graph", ctypes.c_int),
         ("precise_conv", ctypes.c_int),
         ("persistent", ctypes.c_int),
+        ("workspace", ctypes.c_int),
     ]
 
 
@@ -339,3 +340,30 @@ class Plan:
 
     def stats(self):
         return eecmg_plan_stats(self.handle)
+
+
+class Server:
+    """Owning wrapper of an eecmg_server_t (drained and destroyed on close)."""
+
+    def __init__(self, mem_budget_bytes, max_slots):
+        self.handle = eecmg_server_create(mem_budget_bytes, max_slots)
+
+    def submit(self, plan, g, u):
+        return eecmg_server_submit(self.handle, plan.handle if isinstance(plan, Plan) else plan, g, u)
+
+    def poll(self, ticket):
+        return eecmg_server_poll(self.handle, ticket)
+
+    def drain(self):
+        eecmg_server_drain(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            eecmg_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

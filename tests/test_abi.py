@@ -43,6 +43,7 @@ def test_version_and_defaults(lib):
     assert (o.smoother, o.coarse_op, o.storage, o.stop) == (0, 0, 0, 0)
     assert (o.c, o.delta, o.diffusion_steps, o.s_scale) == (1.1, 0.0, 1, 1.0)
     assert o.conv_tol == 1e-5 and o.prolong == 0 and o.use_graph == 1 and o.precise_conv == 1 and o.persistent == 1
+    assert o.workspace == 1
 
 
 @pytest.mark.parametrize("args,status", [
@@ -71,3 +72,14 @@ def test_null_handles_rejected(lib):
         with pytest.raises(lib.EecmgError) as ei:
             fn(*args)
         assert ei.value.status == 1
+
+
+def test_server_arguments_checked_before_any_device_call(lib):
+    for fn, args in [(lib.eecmg_server_create, (0, 4)), (lib.eecmg_server_create, (1 << 20, 0)),
+                     (lib.eecmg_server_create, (1 << 20, 5000)),
+                     (lib.eecmg_server_submit, (None, None, 1, 1)),
+                     (lib.eecmg_server_poll, (None, 1)), (lib.eecmg_server_drain, (None,))]:
+        with pytest.raises(lib.EecmgError) as ei:
+            fn(*args)
+        assert ei.value.status == 1
+    lib.eecmg_server_destroy(None)  # NULL is a no-op
