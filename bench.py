@@ -151,6 +151,111 @@ def cpu_baseline(name, max_seconds=12.0):
             "seconds": dt}
 
 
+def _percentiles(xs):
+    xs = np.asarray(xs, dtype=np.float64)
+    return {"p50_ms": float(np.percentile(xs, 50)), "p99_ms": float(np.percentile(xs, 99)),
+            "mean_ms": float(xs.mean()), "max_ms": float(xs.max())}
+
+
+def serving_leg(torch, eecmg, stream, storage, n_req=400, rate=200.0, seed=5000,
+                budget=64 << 30, slots=64):
+    """Serving form: a Poisson stream of restore requests (sizes 256^2..4096^2
+    log-uniform, Gaussian or motion PSF each, 1-5 % noise, 5 levels, MR-II)
+    through the continuous-batching server, and the same trace through the
+    plain per-image loop (eecmg_restore per request, FIFO on one stream, its
+    CUDA graph captured beforehand).  Open loop: requests are submitted at
+    their arrival times; latency = arrival -> result ready (device clock).
+    Saturated: the whole trace submitted at once, Mpixel/s = capacity.
+
+    Inputs: crops of one synthetic image, blurred on the device by zero-padded
+    2-D correlation with each request's (symmetric) PSF, plus seeded Gaussian
+    noise with ||e|| = v ||u||.
+    """
+    from paper_2311_03010_gb300 import synth
+
+    tr = synth.arrival_trace(n_req, rate, seed)
+    smax = max(max(r["h"], r["w"]) for r in tr)
+    u_clean = torch.from_numpy(synth.synthetic_image(smax, smax, seed).astype(np.float32)).cuda()
+    gen = torch.Generator(device="cuda")
+    reqs = []
+    for r in tr:
+        psf = synth.psf_from_spec(r["psf"])
+        h, w = r["h"], r["w"]
+        x = u_clean[:h, :w].reshape(1, 1, h, w)
+        k = torch.from_numpy(np.ascontiguousarray(psf[::-1, ::-1]).astype(np.float32)).cuda()
+        hu = torch.nn.functional.conv2d(x, k.reshape(1, 1, *psf.shape),
+                                        padding=(psf.shape[0] // 2, psf.shape[1] // 2))[0, 0]
+        gen.manual_seed(r["seed"])
+        e = torch.randn(h, w, generator=gen, device="cuda")
+        g = (hu + e * (r["v"] * x.norm() / e.norm())).contiguous()
+        reqs.append({"t": r["t"], "g": g, "u": torch.empty_like(g), "psf": psf, "h": h, "w": w})
+    px = sum(r["h"] * r["w"] for r in reqs)
+    torch.cuda.synchronize()
+
+    def replay(submit, finish, open_loop):
+        t0 = time.perf_counter()
+        subs = []
+        for r in reqs:
+            if open_loop:
+                delay = t0 + r["t"] - time.perf_counter()
+                if delay > 0:
+                    time.sleep(delay)
+            subs.append((time.perf_counter(), submit(r)))
+        lat = finish(subs)
+        return time.perf_counter() - t0, lat
+
+    out = {"requests": n_req, "rate_per_s": rate, "storage": storage, "levels": 5,
+           "pixels": px, "sizes": "256^2..4096^2 log-uniform", "budget_bytes": budget,
+           "max_slots": slots}
+    # --- continuous-batching server
+    descs = [eecmg.Plan(r["w"], r["h"], 5, r["psf"], storage=storage, workspace=0) for r in reqs]
+    srv = eecmg.Server(budget, slots)
+    for i in range(min(8, n_req)):  # warm-up (occupancy queries, first launches)
+        srv.submit(descs[i], reqs[i]["g"], reqs[i]["u"])
+    srv.drain()
+    idx = {id(r): i for i, r in enumerate(reqs)}
+
+    def srv_submit(r):
+        return srv.submit(descs[idx[id(r)]], r["g"], r["u"])
+
+    def srv_finish(subs):
+        srv.drain()
+        return [srv.poll(t)[1] for (_, t) in subs]
+
+    for mode in ("open", "saturated"):
+        dt, lat = replay(srv_submit, srv_finish, mode == "open")
+        out[f"server_{mode}"] = dict(_percentiles(lat), mpix_s=px / dt / 1e6, seconds=dt)
+    srv.close()
+    for d in descs:
+        d.close()
+    # --- plain per-image loop
+    plans = [eecmg.Plan(r["w"], r["h"], 5, r["psf"], storage=storage) for r in reqs]
+    for p, r in zip(plans, reqs):
+        p.restore(r["g"], r["u"], stream)  # captures each plan's graph
+    torch.cuda.synchronize()
+    base = torch.cuda.Event(enable_timing=True)
+    base.record(stream)
+    base.synchronize()
+    base_host = time.perf_counter()
+
+    def loop_submit(r):
+        plans[idx[id(r)]].restore(r["g"], r["u"], stream)
+        ev = torch.cuda.Event(enable_timing=True)
+        ev.record(stream)
+        return ev
+
+    def loop_finish(subs):
+        torch.cuda.synchronize()
+        return [(base_host + base.elapsed_time(ev) / 1e3 - t_sub) * 1e3 for (t_sub, ev) in subs]
+
+    for mode in ("open", "saturated"):
+        dt, lat = replay(loop_submit, loop_finish, mode == "open")
+        out[f"plain_loop_{mode}"] = dict(_percentiles(lat), mpix_s=px / dt / 1e6, seconds=dt)
+    for p in plans:
+        p.close()
+    return out
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -195,6 +300,7 @@ def main():
     ap.add_argument("--precise-conv", type=int, default=1)
     ap.add_argument("--storage", default="fp32", choices=["fp32", "bf16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -344,6 +450,10 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(name)
 
+    serving = None
+    if not args.no_serving:
+        serving = serving_leg(torch, eecmg, stream, args.storage)
+
     if rank == 0:
         out = {
             "metric": "Mpixel/s restored (EECMG, oracle-matched)",
@@ -368,6 +478,7 @@ def main():
                                            if v["launches"]},
             "clocks": clk,
             "per_image_loop_value": loop_value,
+            "serving": serving,
             "parity": parity,
             "cpu_baseline": cpu,
         }

@@ -14,6 +14,7 @@
 // The whole batch is captured once as a CUDA graph per set of plans and
 // replayed; inputs are copied into the plans' workspaces outside the graph.
 #include <algorithm>
+#include <cstdint>
 #include <map>
 #include <memory>
 #include <mutex>
@@ -56,21 +57,24 @@ LevelJob make_job(eecmg_plan_s* P, int l) {
 eecmg_status plan_waves(const std::vector<std::pair<eecmg_plan_s*, int>>& items,
                         std::vector<HostWave>& waves) {
     waves.clear();
-    // instantiation key -> indices of items
-    std::map<std::tuple<int, int, int, int>, std::vector<int>> groups;
+    // (cluster size, instantiation) -> indices of items
+    std::map<std::tuple<int, int, int, int, int>, std::vector<int>> groups;
     for (int i = 0; i < (int)items.size(); ++i) {
         eecmg_plan_s* P = items[i].first;
         const int l = items[i].second;
         const int cg = P->opt.smoother == EECMG_SMOOTHER_CGLS ? 1 : 0;
         const int bf = P->opt.storage == EECMG_STORAGE_BF16 ? 1 : 0;
-        groups[{cg, P->lv[l].sepH, P->opt.precise_conv, bf}].push_back(i);
+        const int cl = level_shape(P->lv[l].h, P->lv[l].w).cluster;
+        groups[{cl, cg, P->lv[l].sepH, P->opt.precise_conv, bf}].push_back(i);
     }
     for (auto& kv : groups) {
-        const int cg = std::get<0>(kv.first), sep = std::get<1>(kv.first),
-                  prec = std::get<2>(kv.first), bf = std::get<3>(kv.first);
+        const int cl = std::get<0>(kv.first), cg = std::get<1>(kv.first),
+                  sep = std::get<2>(kv.first), prec = std::get<3>(kv.first),
+                  bf = std::get<4>(kv.first);
         int rt = 0;
         for (int i : kv.second) rt = std::max(rt, items[i].first->lv[items[i].second].rt);
-        const int cap = level_capacity(rt, sep, prec, cg, bf);
+        // clusters are independent: one launch holds them all
+        const int cap = cl > 0 ? INT32_MAX : level_capacity(rt, sep, prec, cg, bf);
         if (cap <= 0) return set_error(EECMG_ERR_CUDA, "batched level solve: occupancy query failed");
         HostWave cur;
         cur.rt = rt;
@@ -78,10 +82,11 @@ eecmg_status plan_waves(const std::vector<std::pair<eecmg_plan_s*, int>>& items,
         cur.prec = prec;
         cur.cgls = cg;
         cur.bf16 = bf;
+        cur.cluster = cl;
         for (int i : kv.second) {
             const LevelPlan& Lp = items[i].first->lv[items[i].second];
-            const int nb = std::max(1, std::min(cap, level_want_blocks(Lp.h, Lp.w)));
-            if (cur.blocks + nb > cap && !cur.jobs.empty()) {  // next wave
+            const int nb = cl > 0 ? cl : std::max(1, std::min(cap, level_shape(Lp.h, Lp.w).blocks));
+            if ((long long)cur.blocks + nb > cap && !cur.jobs.empty()) {  // next wave
                 waves.push_back(cur);
                 cur.jobs.clear();
                 cur.block_job.clear();
@@ -104,7 +109,7 @@ namespace {
 struct Wave {
     const LevelJob* d_jobs = nullptr;
     const unsigned short* d_block_job = nullptr;
-    int njobs = 0, blocks = 0, rt = 0, sep = 0, prec = 0, cgls = 0, bf16 = 0;
+    int njobs = 0, blocks = 0, rt = 0, sep = 0, prec = 0, cgls = 0, bf16 = 0, cluster = 0;
 };
 
 struct BatchCtx {
@@ -164,6 +169,7 @@ eecmg_status build_ctx(BatchCtx& C) {
             dw.prec = w.prec;
             dw.cgls = w.cgls;
             dw.bf16 = w.bf16;
+            dw.cluster = w.cluster;
             C.steps[s].push_back(dw);
         }
     e = cudaStreamCreateWithFlags(&C.cap_stream, cudaStreamNonBlocking);
@@ -197,7 +203,7 @@ eecmg_status enqueue_batch(BatchCtx& C, cudaStream_t s) {
         }
         for (auto& w : C.steps[st])
             BCK(launch_level_batch(w.d_jobs, w.d_block_job, w.njobs, w.blocks, w.rt, w.sep, w.prec,
-                                   w.cgls, w.bf16, s));
+                                   w.cgls, w.bf16, w.cluster, s));
     }
     return EECMG_OK;
 }

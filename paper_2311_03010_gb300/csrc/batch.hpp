@@ -17,16 +17,18 @@ struct HostWave {
     std::vector<LevelJob> jobs;
     std::vector<unsigned short> block_job;
     int blocks = 0, rt = 0, sep = 0, prec = 0, cgls = 0, bf16 = 0;
+    int cluster = 0;  // > 0: one cluster of this many blocks per job
 };
 
 // The level-l solve of plan P as a job (buffers from P's workspace).
 LevelJob make_job(eecmg_plan_s* P, int l);
 
 // Groups the level solves items[i] = (plan, level) into waves.  Every job
-// gets the block count of the same solve launched alone, so each result is
-// bitwise that of the plan's own restoration; jobs that do not fit the
+// gets the partition of the same solve launched alone (level_shape), so each
+// result is bitwise that of the plan's own restoration.  Cluster-mode jobs of
+// one instantiation share one launch; cooperative jobs that do not fit the
 // co-resident capacity of their instantiation start a new wave.  Groups come
-// out in a fixed order (by instantiation key, then item order).
+// out in a fixed order (by cluster size and instantiation, then item order).
 eecmg_status plan_waves(const std::vector<std::pair<eecmg_plan_s*, int>>& items,
                         std::vector<HostWave>& waves);
 

@@ -1,5 +1,7 @@
 // level_solve.cu -- dispatch of the persistent level solve (kernels in
 // level_solve_impl.cuh, instantiated in the ls_*.cu translation units).
+#include <cstdlib>
+
 #include "level_solve_impl.cuh"
 
 namespace eecmg {
@@ -11,22 +13,52 @@ __device__ unsigned int g_eecmg_trace_n;
 
 namespace {
 
-cudaError_t dispatch(const LevelLaunch& L, int rt, int sep, int prec, int cgls, int bf16, int want,
-                     cudaStream_t s, int* used) {
+cudaError_t dispatch(const LevelLaunch& L, int rt, int sep, int prec, int cgls, int bf16, int op,
+                     int blocks, cudaStream_t s, int* out) {
     if (rt < 0 || rt > RMAX) return cudaErrorInvalidValue;
     const bool lo = rt < 6;
     if (cgls) {
         if (bf16)
-            return lo ? launch_level_cgls_bf16_lo(L, rt, sep, prec, want, s, used)
-                      : launch_level_cgls_bf16_hi(L, rt, sep, prec, want, s, used);
-        return lo ? launch_level_cgls_f32_lo(L, rt, sep, prec, want, s, used)
-                  : launch_level_cgls_f32_hi(L, rt, sep, prec, want, s, used);
+            return lo ? launch_level_cgls_bf16_lo(L, rt, sep, prec, op, blocks, s, out)
+                      : launch_level_cgls_bf16_hi(L, rt, sep, prec, op, blocks, s, out);
+        return lo ? launch_level_cgls_f32_lo(L, rt, sep, prec, op, blocks, s, out)
+                  : launch_level_cgls_f32_hi(L, rt, sep, prec, op, blocks, s, out);
     }
     if (bf16)
-        return lo ? launch_level_mr2_bf16_lo(L, rt, sep, prec, want, s, used)
-                  : launch_level_mr2_bf16_hi(L, rt, sep, prec, want, s, used);
-    return lo ? launch_level_mr2_f32_lo(L, rt, sep, prec, want, s, used)
-              : launch_level_mr2_f32_hi(L, rt, sep, prec, want, s, used);
+        return lo ? launch_level_mr2_bf16_lo(L, rt, sep, prec, op, blocks, s, out)
+                  : launch_level_mr2_bf16_hi(L, rt, sep, prec, op, blocks, s, out);
+    return lo ? launch_level_mr2_f32_lo(L, rt, sep, prec, op, blocks, s, out)
+              : launch_level_mr2_f32_hi(L, rt, sep, prec, op, blocks, s, out);
+}
+
+// Largest cluster every instantiation can run as (queried on the kernels
+// with the most shared memory: the largest radius, non-separable).
+int cluster_limit() {
+    static int lim = -1;
+    if (lim < 0) {
+        LevelLaunch L;
+        int m = CLUSTER_MAX;
+        for (int cgls = 0; cgls < 2; ++cgls)
+            for (int bf16 = 0; bf16 < 2; ++bf16) {
+                int c = 0;
+                if (dispatch(L, RMAX, 0, 0, cgls, bf16, LS_CLUSTER_MAX, 0, nullptr, &c) != cudaSuccess) c = 0;
+                m = c < m ? c : m;
+            }
+        lim = m;
+    }
+    return lim;
+}
+
+// Levels of at most this many pixels run in cluster mode (EECMG_CLUSTER_MAX_PX
+// overrides; 0 turns cluster mode off).
+size_t cluster_max_px() {
+    static long long v = -1;
+    if (v < 0) {
+        const char* e = std::getenv("EECMG_CLUSTER_MAX_PX");
+        v = e ? std::atoll(e) : 262144;
+        if (v < 0) v = 0;
+    }
+    return (size_t)v;
 }
 
 }  // namespace
@@ -49,29 +81,57 @@ int level_want_blocks(int h, int w) {
     return want < cap ? want : cap;
 }
 
+LevelShape level_shape(int h, int w) {
+    LevelShape sh;
+    const int want = level_want_blocks(h, w);
+    const size_t n = (size_t)h * w;
+    const int lim = n <= cluster_max_px() ? cluster_limit() : 0;
+    if (lim >= 1) {
+        sh.cluster = want < lim ? want : lim;
+        sh.blocks = sh.cluster;
+    } else {
+        sh.blocks = want;
+    }
+    return sh;
+}
+
 cudaError_t launch_level_solve(const LevelJob& J, int rt, int sep, int prec, int cgls, int bf16,
                                cudaStream_t s, int* blocks_used) {
     if (J.h <= 0 || J.w <= 0) return cudaSuccess;
     LevelLaunch L;
     L.job = J;
-    return dispatch(L, rt, sep, prec, cgls, bf16, level_want_blocks(J.h, J.w), s, blocks_used);
+    const LevelShape sh = level_shape(J.h, J.w);
+    if (sh.cluster > 0) {
+        L.cluster = sh.cluster;
+        if (blocks_used) *blocks_used = sh.blocks;
+        return dispatch(L, rt, sep, prec, cgls, bf16, LS_CLUSTER, sh.blocks, s, nullptr);
+    }
+    int cap = 0;
+    cudaError_t e = dispatch(L, rt, sep, prec, cgls, bf16, LS_CAPACITY, 0, nullptr, &cap);
+    if (e != cudaSuccess) return e;
+    int blocks = sh.blocks < cap ? sh.blocks : cap;
+    if (blocks < 1) blocks = 1;
+    if (blocks_used) *blocks_used = blocks;
+    return dispatch(L, rt, sep, prec, cgls, bf16, LS_COOP, blocks, s, nullptr);
 }
 
 cudaError_t launch_level_batch(const LevelJob* d_jobs, const unsigned short* d_block_job, int njobs,
                                int total_blocks, int rt, int sep, int prec, int cgls, int bf16,
-                               cudaStream_t s) {
+                               int cluster, cudaStream_t s) {
     if (njobs <= 0 || total_blocks <= 0) return cudaSuccess;
     LevelLaunch L;
     L.jobs = d_jobs;
     L.block_job = d_block_job;
     L.njobs = njobs;
-    return dispatch(L, rt, sep, prec, cgls, bf16, -total_blocks, s, nullptr);
+    L.cluster = cluster;
+    return dispatch(L, rt, sep, prec, cgls, bf16, cluster > 0 ? LS_CLUSTER : LS_COOP, total_blocks, s,
+                    nullptr);
 }
 
 int level_capacity(int rt, int sep, int prec, int cgls, int bf16) {
     LevelLaunch L;
     int cap = 0;
-    if (dispatch(L, rt, sep, prec, cgls, bf16, 0, nullptr, &cap) != cudaSuccess) return 0;
+    if (dispatch(L, rt, sep, prec, cgls, bf16, LS_CAPACITY, 0, nullptr, &cap) != cudaSuccess) return 0;
     return cap;
 }
 

@@ -27,21 +27,37 @@ struct LevelJob {
 };
 
 // Kernel parameter: one job by value, or (jobs != nullptr) a device table of
-// njobs jobs, block b serving job block_job[b].
+// njobs jobs, block b serving job block_job[b].  cluster > 0: every job runs
+// on one thread-block cluster of that many blocks (cluster mode); 0: the
+// jobs' blocks form one cooperative grid.
 struct LevelLaunch {
     LevelJob job;
     const LevelJob* jobs = nullptr;
     const unsigned short* block_job = nullptr;
     int njobs = 1;
+    int cluster = 0;
 };
 
-// Launches a device job table as one cooperative grid of total_blocks blocks
-// (the caller sized the jobs' block ranges to fit co-residency; see
-// level_capacity).  All jobs share the kernel radius rt (>= each job's own),
-// separability, precision and solver.
+enum LevelOp { LS_COOP = 0, LS_CLUSTER = 1, LS_CAPACITY = 2, LS_CLUSTER_MAX = 3 };
+
+// How a level solve of h x w pixels is partitioned: one cluster of `cluster`
+// blocks (small levels), or a cooperative grid of `blocks` blocks.  Depends
+// only on the level size and the device, so a solve is partitioned (and its
+// sums rounded) the same way alone, batched or served.
+struct LevelShape {
+    int cluster = 0;
+    int blocks = 0;
+};
+LevelShape level_shape(int h, int w);
+
+// Launches a device job table: one cooperative grid of total_blocks blocks
+// (cluster == 0; the caller sized the jobs' block ranges to fit
+// co-residency, see level_capacity), or clusters of `cluster` blocks, one per
+// job.  All jobs share the kernel radius rt (>= each job's own),
+// separability, precision, solver and storage.
 cudaError_t launch_level_batch(const LevelJob* d_jobs, const unsigned short* d_block_job, int njobs,
                                int total_blocks, int rt, int sep, int prec, int cgls, int bf16,
-                               cudaStream_t s);
+                               int cluster, cudaStream_t s);
 // Co-resident block capacity of the solver instantiation (0 on error).
 int level_capacity(int rt, int sep, int prec, int cgls, int bf16);
 

@@ -148,18 +148,11 @@ __device__ __forceinline__ void conv_phase(ConvSmem<R, SEP>& S, const TIN* x, in
 using namespace ls_detail;
 
 template <int R, bool SEP, bool PREC, typename HT>
-__global__ void __launch_bounds__(NTHREADS) k_level_mr2(LevelLaunch LL) {
-    __shared__ ConvSmem<R, SEP> S;
-    __shared__ LevelJob sJ;
-    if (threadIdx.x == 0) sJ = LL.jobs ? LL.jobs[LL.block_job[blockIdx.x]] : LL.job;
-    __syncthreads();
-    const LevelJob& J = sJ;
-    const unsigned int nb = LL.jobs ? (unsigned int)J.nblocks : gridDim.x;
-    const unsigned int bid = LL.jobs ? blockIdx.x - (unsigned int)J.block0 : blockIdx.x;
+__device__ __forceinline__ void mr2_body(ConvSmem<R, SEP>& S, const LevelJob& J, Scalars* sc,
+                                         unsigned int nb, unsigned int bid, LevelSync& sy) {
     const int h = J.h, w = J.w;
     const size_t n = (size_t)h * w;
     const size_t stride = (size_t)nb * NTHREADS;
-    Scalars* sc = J.sc;
     conv_stage_taps<R, SEP>(S, J.taps);
     __syncthreads();
 
@@ -179,8 +172,7 @@ __global__ void __launch_bounds__(NTHREADS) k_level_mr2(LevelLaunch LL) {
             conv_phase<R, SEP, PREC, false>(S, J.u, h, w, nb, bid, epi);
         double v[2] = {(double)a0, (double)a1};
         const double ct2 = J.conv_tol2, d2 = J.disc2;
-        if (!group_reduce<2>(v, J.partials, J.gs, nb, bid,
-                             [&](double* t) { fin_resid(sc, t[0], t[1], ct2, d2); }))
+        if (!sy.reduce<2>(v, [&](double* t) { fin_resid(sc, t[0], t[1], ct2, d2); }))
             return;
     }
     if (J.m <= 0 || volatile_stopped(sc)) return;
@@ -195,8 +187,7 @@ __global__ void __launch_bounds__(NTHREADS) k_level_mr2(LevelLaunch LL) {
             a1 = fmaf(z, ctr, a1);
         });
         double v[2] = {(double)a0, (double)a1};
-        if (!group_reduce<2>(v, J.partials, J.gs, nb, bid,
-                             [&](double* t) { fin_mr_v1(sc, t[0], t[1]); }))
+        if (!sy.reduce<2>(v, [&](double* t) { fin_mr_v1(sc, t[0], t[1]); }))
             return;
     }
 
@@ -217,8 +208,7 @@ __global__ void __launch_bounds__(NTHREADS) k_level_mr2(LevelLaunch LL) {
                                             });
             double v[1] = {(double)a0};
             TRACE(bid, 11);
-            if (!group_reduce<1>(v, J.partials, J.gs, nb, bid,
-                                 [&](double* t) { fin_mr_a(sc, t[0]); }))
+            if (!sy.reduce<1>(v, [&](double* t) { fin_mr_a(sc, t[0]); }))
                 return;
         }
         TRACE(bid, 12);
@@ -262,8 +252,7 @@ __global__ void __launch_bounds__(NTHREADS) k_level_mr2(LevelLaunch LL) {
             }
             double v[3] = {(double)arr, (double)avv, (double)avr};
             TRACE(bid, 13);
-            if (!group_reduce<3>(v, J.partials, J.gs, nb, bid,
-                                 [&](double* t) { fin_mr_b(sc, k, t[0], t[1], t[2]); }))
+            if (!sy.reduce<3>(v, [&](double* t) { fin_mr_b(sc, k, t[0], t[1], t[2]); }))
                 return;
         }
         TRACE(bid, 14);
@@ -286,26 +275,19 @@ __global__ void __launch_bounds__(NTHREADS) k_level_mr2(LevelLaunch LL) {
                 arr = fmaf(rv, rv, arr);
             }
         double v[1] = {(double)arr};
-        group_reduce<1>(v, J.partials, J.gs, nb, bid, [&](double* t) { fin_mr_final(sc, t[0]); });
+        sy.reduce<1>(v, [&](double* t) { fin_mr_final(sc, t[0]); });
     }
 }
 
 template <int R, bool SEP, bool PREC, typename HT>
-__global__ void __launch_bounds__(NTHREADS) k_level_cgls(LevelLaunch LL) {
+__device__ __forceinline__ void cgls_body(ConvSmem<R, SEP>& S, const LevelJob& J, Scalars* sc,
+                                          unsigned int nb, unsigned int bid, LevelSync& sy) {
     // s and p are stored as HT; q = H p stays FP32 (computed from the stored
     // p), so u and the residual recurrence see the same direction
     using IO = VecIO<HT>;
-    __shared__ ConvSmem<R, SEP> S;
-    __shared__ LevelJob sJ;
-    if (threadIdx.x == 0) sJ = LL.jobs ? LL.jobs[LL.block_job[blockIdx.x]] : LL.job;
-    __syncthreads();
-    const LevelJob& J = sJ;
-    const unsigned int nb = LL.jobs ? (unsigned int)J.nblocks : gridDim.x;
-    const unsigned int bid = LL.jobs ? blockIdx.x - (unsigned int)J.block0 : blockIdx.x;
     const int h = J.h, w = J.w;
     const size_t n = (size_t)h * w;
     const size_t stride = (size_t)nb * NTHREADS;
-    Scalars* sc = J.sc;
     float* rv_ = J.r;
     HT* sv = reinterpret_cast<HT*>(J.v[0]);   // s
     HT* pv = reinterpret_cast<HT*>(J.v[1]);   // p
@@ -327,8 +309,7 @@ __global__ void __launch_bounds__(NTHREADS) k_level_cgls(LevelLaunch LL) {
             conv_phase<R, SEP, PREC, false>(S, J.u, h, w, nb, bid, epi);
         double v[2] = {(double)a0, (double)a1};
         const double ct2 = J.conv_tol2, d2 = J.disc2;
-        if (!group_reduce<2>(v, J.partials, J.gs, nb, bid,
-                             [&](double* t) { fin_resid(sc, t[0], t[1], ct2, d2); }))
+        if (!sy.reduce<2>(v, [&](double* t) { fin_resid(sc, t[0], t[1], ct2, d2); }))
             return;
     }
     if (J.m <= 0 || volatile_stopped(sc)) return;
@@ -343,7 +324,7 @@ __global__ void __launch_bounds__(NTHREADS) k_level_cgls(LevelLaunch LL) {
             a0 = fmaf(z, z, a0);
         });
         double v[1] = {(double)a0};
-        if (!group_reduce<1>(v, J.partials, J.gs, nb, bid, [&](double* t) { fin_cg_s0(sc, t[0]); }))
+        if (!sy.reduce<1>(v, [&](double* t) { fin_cg_s0(sc, t[0]); }))
             return;
     }
     for (int k = 1; k <= J.m; ++k) {
@@ -358,8 +339,7 @@ __global__ void __launch_bounds__(NTHREADS) k_level_cgls(LevelLaunch LL) {
                 a0 = fmaf(z, z, a0);
             });
             double v[1] = {(double)a0};
-            if (!group_reduce<1>(v, J.partials, J.gs, nb, bid,
-                                 [&](double* t) { fin_cg_q(sc, t[0]); }))
+            if (!sy.reduce<1>(v, [&](double* t) { fin_cg_q(sc, t[0]); }))
                 return;
         }
         if (volatile_stopped(sc)) break;
@@ -381,8 +361,7 @@ __global__ void __launch_bounds__(NTHREADS) k_level_cgls(LevelLaunch LL) {
                     arr = fmaf(r, r, arr);
                 }
             double v[1] = {(double)arr};
-            if (!group_reduce<1>(v, J.partials, J.gs, nb, bid,
-                                 [&](double* t) { fin_cg_step(sc, t[0]); }))
+            if (!sy.reduce<1>(v, [&](double* t) { fin_cg_step(sc, t[0]); }))
                 return;
         }
         if (k == J.m || volatile_stopped(sc)) break;
@@ -396,8 +375,7 @@ __global__ void __launch_bounds__(NTHREADS) k_level_cgls(LevelLaunch LL) {
                 a0 = fmaf(z, z, a0);
             });
             double v[1] = {(double)a0};
-            if (!group_reduce<1>(v, J.partials, J.gs, nb, bid,
-                                 [&](double* t) { fin_cg_s(sc, t[0]); }))
+            if (!sy.reduce<1>(v, [&](double* t) { fin_cg_s(sc, t[0]); }))
                 return;
         }
         if (volatile_stopped(sc)) break;
@@ -410,9 +388,45 @@ __global__ void __launch_bounds__(NTHREADS) k_level_cgls(LevelLaunch LL) {
                 for (size_t i = 4 * n4 + threadIdx.x; i < n; i += NTHREADS)
                     IO::st(pv, i, fmaf(b, IO::ld(pv, i), IO::ld(sv, i)));
             double v[1] = {0.0};
-            if (!group_reduce<1>(v, J.partials, J.gs, nb, bid, [&](double*) {})) return;
+            if (!sy.reduce<1>(v, [&](double*) {})) return;
         }
     }
+}
+
+// One level solve per job: a cooperative grid (LL.cluster == 0; the job's
+// blocks meet at bounded grid barriers) or one thread-block cluster of
+// LL.cluster blocks per job (reductions through distributed shared memory).
+template <int R, bool SEP, bool PREC, typename HT, bool CGLS>
+__device__ __forceinline__ void level_kernel(const LevelLaunch& LL) {
+    __shared__ ConvSmem<R, SEP> S;
+    __shared__ LevelJob sJ;
+    __shared__ ClusterState CS;
+    if (threadIdx.x == 0) sJ = LL.jobs ? LL.jobs[LL.block_job[blockIdx.x]] : LL.job;
+    __syncthreads();
+    const LevelJob& J = sJ;
+    const unsigned int nb = LL.jobs ? (unsigned int)J.nblocks : gridDim.x;
+    const unsigned int bid = LL.jobs ? blockIdx.x - (unsigned int)J.block0 : blockIdx.x;
+    const bool cl = LL.cluster > 0;
+    TRACE(bid, 1);
+    if (cl) cluster_begin(CS, J.sc, nb);
+    LevelSync sy{J.partials, J.gs, nb, bid, cl ? &CS : nullptr, 0u};
+    Scalars* sc = cl ? &CS.sc : J.sc;
+    if constexpr (CGLS)
+        cgls_body<R, SEP, PREC, HT>(S, J, sc, nb, bid, sy);
+    else
+        mr2_body<R, SEP, PREC, HT>(S, J, sc, nb, bid, sy);
+    if (cl) cluster_end(CS, J.sc, bid);
+    TRACE(bid, 2);
+}
+
+template <int R, bool SEP, bool PREC, typename HT>
+__global__ void __launch_bounds__(NTHREADS) k_level_mr2(LevelLaunch LL) {
+    level_kernel<R, SEP, PREC, HT, false>(LL);
+}
+
+template <int R, bool SEP, bool PREC, typename HT>
+__global__ void __launch_bounds__(NTHREADS) k_level_cgls(LevelLaunch LL) {
+    level_kernel<R, SEP, PREC, HT, true>(LL);
 }
 
 template <class K>
@@ -420,6 +434,23 @@ inline cudaError_t coop_launch(K kernel, const LevelLaunch& L, int blocks, cudaS
     LevelLaunch arg = L;
     void* params[] = {&arg};
     return cudaLaunchCooperativeKernel((const void*)kernel, dim3(blocks), dim3(NTHREADS), params, 0, s);
+}
+
+template <class K>
+inline cudaError_t cluster_launch(K kernel, const LevelLaunch& L, int blocks, cudaStream_t s) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(blocks);
+    cfg.blockDim = dim3(NTHREADS);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = (unsigned int)L.cluster;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, L);
 }
 
 template <class K>
@@ -431,46 +462,72 @@ inline int coresident_blocks(K kernel) {
     return per_sm * sms;
 }
 
-// want > 0: min(want, capacity) blocks; want < 0: exactly -want blocks
-// (a batched job table already sized to the capacity); want == 0: only
-// report the capacity in *used.
+// Largest cluster (<= CLUSTER_MAX) the kernel can run as; 0 if none.
 template <class K>
-inline cudaError_t launch_capped(K kern, int& cap, const LevelLaunch& L, int want, cudaStream_t s,
-                                 int* used) {
-    if (cap < 0) cap = coresident_blocks(kern);
-    if (want == 0) {
-        if (used) *used = cap;
-        return cudaSuccess;
+inline int max_cluster(K kernel) {
+    if (cudaFuncSetAttribute(kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
     }
-    int blocks = want < 0 ? -want : (want < cap ? want : cap);
-    if (blocks < 1) blocks = 1;
-    if (used) *used = blocks;
-    return coop_launch(kern, L, blocks, s);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(CLUSTER_MAX);
+    cfg.blockDim = dim3(NTHREADS);
+    int c = 0;
+    if (cudaOccupancyMaxPotentialClusterSize(&c, kernel, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return c < CLUSTER_MAX ? c : CLUSTER_MAX;
 }
 
-// Launches one instantiation (see launch_capped for want).
+// One instantiation: op selects a cooperative launch of `blocks` blocks, a
+// cluster launch of `blocks` blocks in clusters of L.cluster, or a query
+// (*out = co-resident capacity, or the largest usable cluster).
+template <class K>
+inline cudaError_t level_op(K kern, int& cap, int& cmax, const LevelLaunch& L, int op, int blocks,
+                            cudaStream_t s, int* out) {
+    switch (op) {
+        case LS_CAPACITY:
+            if (cap < 0) cap = coresident_blocks(kern);
+            if (out) *out = cap;
+            return cudaSuccess;
+        case LS_CLUSTER_MAX:
+            if (cmax < 0) cmax = max_cluster(kern);
+            if (out) *out = cmax;
+            return cudaSuccess;
+        case LS_COOP:
+            return coop_launch(kern, L, blocks, s);
+        case LS_CLUSTER:
+            if (cmax < 0) cmax = max_cluster(kern);
+            if (L.cluster < 1 || L.cluster > cmax || blocks % L.cluster) return cudaErrorInvalidValue;
+            return cluster_launch(kern, L, blocks, s);
+        default:
+            return cudaErrorInvalidValue;
+    }
+}
+
 template <int R, bool SEP, bool PREC, bool CGLS, typename HT>
-cudaError_t launch_level_t(const LevelLaunch& L, int want, cudaStream_t s, int* used) {
-    static int cap = -1;  // per instantiation; the library runs on one GPU model
+cudaError_t launch_level_t(const LevelLaunch& L, int op, int blocks, cudaStream_t s, int* out) {
+    static int cap = -1, cmax = -1;  // per instantiation; the library runs on one GPU model
     if constexpr (CGLS)
-        return launch_capped(k_level_cgls<R, SEP, PREC, HT>, cap, L, want, s, used);
+        return level_op(k_level_cgls<R, SEP, PREC, HT>, cap, cmax, L, op, blocks, s, out);
     else
-        return launch_capped(k_level_mr2<R, SEP, PREC, HT>, cap, L, want, s, used);
+        return level_op(k_level_mr2<R, SEP, PREC, HT>, cap, cmax, L, op, blocks, s, out);
 }
 
 template <int R, bool CGLS, typename HT>
-cudaError_t launch_level_r(const LevelLaunch& L, int sep, int prec, int want, cudaStream_t s,
-                           int* used) {
-    if (sep && prec) return launch_level_t<R, true, true, CGLS, HT>(L, want, s, used);
-    if (sep) return launch_level_t<R, true, false, CGLS, HT>(L, want, s, used);
-    return launch_level_t<R, false, false, CGLS, HT>(L, want, s, used);
+cudaError_t launch_level_r(const LevelLaunch& L, int sep, int prec, int op, int blocks,
+                           cudaStream_t s, int* out) {
+    if (sep && prec) return launch_level_t<R, true, true, CGLS, HT>(L, op, blocks, s, out);
+    if (sep) return launch_level_t<R, true, false, CGLS, HT>(L, op, blocks, s, out);
+    return launch_level_t<R, false, false, CGLS, HT>(L, op, blocks, s, out);
 }
 
 // Per translation unit: one solver, one storage type, a range of radii
 // (names: launch_level_<solver>_<storage>_<lo|hi>).
-#define EECMG_LS_DECL(name)                                                               \
-    cudaError_t name(const LevelLaunch& L, int rt, int sep, int prec, int want, cudaStream_t s, \
-                     int* used);
+#define EECMG_LS_DECL(name)                                                                \
+    cudaError_t name(const LevelLaunch& L, int rt, int sep, int prec, int op, int blocks,      \
+                     cudaStream_t s, int* out);
 EECMG_LS_DECL(launch_level_mr2_f32_lo)
 EECMG_LS_DECL(launch_level_mr2_f32_hi)
 EECMG_LS_DECL(launch_level_mr2_bf16_lo)

@@ -3,15 +3,15 @@
 
 namespace eecmg {
 
-cudaError_t launch_level_mr2_bf16_lo(const LevelLaunch& L, int rt, int sep, int prec, int want, cudaStream_t s,
-                 int* used) {
+cudaError_t launch_level_mr2_bf16_lo(const LevelLaunch& L, int rt, int sep, int prec, int op,
+                                     int blocks, cudaStream_t s, int* out) {
     switch (rt) {
-        case 0: return launch_level_r<0, false, __nv_bfloat16>(L, sep, prec, want, s, used);
-        case 1: return launch_level_r<1, false, __nv_bfloat16>(L, sep, prec, want, s, used);
-        case 2: return launch_level_r<2, false, __nv_bfloat16>(L, sep, prec, want, s, used);
-        case 3: return launch_level_r<3, false, __nv_bfloat16>(L, sep, prec, want, s, used);
-        case 4: return launch_level_r<4, false, __nv_bfloat16>(L, sep, prec, want, s, used);
-        case 5: return launch_level_r<5, false, __nv_bfloat16>(L, sep, prec, want, s, used);
+        case 0: return launch_level_r<0, false, __nv_bfloat16>(L, sep, prec, op, blocks, s, out);
+        case 1: return launch_level_r<1, false, __nv_bfloat16>(L, sep, prec, op, blocks, s, out);
+        case 2: return launch_level_r<2, false, __nv_bfloat16>(L, sep, prec, op, blocks, s, out);
+        case 3: return launch_level_r<3, false, __nv_bfloat16>(L, sep, prec, op, blocks, s, out);
+        case 4: return launch_level_r<4, false, __nv_bfloat16>(L, sep, prec, op, blocks, s, out);
+        case 5: return launch_level_r<5, false, __nv_bfloat16>(L, sep, prec, op, blocks, s, out);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -121,4 +121,139 @@ __device__ __forceinline__ bool group_reduce(const double (&v)[NV], double* part
     return s_ok != 0 && *(volatile int*)&gs->err == 0;
 }
 
+// ---------------------------------------------------------------------------
+// Cluster mode: a small level solve runs on one thread-block cluster (up to
+// CLUSTER_MAX blocks, one per SM of a GPC) instead of a cooperative grid.
+// A reduction then never leaves the GPC: every block writes its FP64 block
+// sums into a slot of every block's shared memory (distributed shared
+// memory) and arrives on each block's mbarrier; each block waits on its own
+// mbarrier (bounded), sums the slots in rank order and runs the scalar
+// update itself.  All blocks hold identical scalar state (the same sums in
+// the same order), so no broadcast is needed and one barrier ends a phase.
+// ---------------------------------------------------------------------------
+
+constexpr int CLUSTER_MAX = 16;
+
+struct ClusterState {
+    double slots[2][CLUSTER_MAX][NPART];  // [phase parity][source rank][value]
+    unsigned long long mbar;
+    int err;
+    Scalars sc;                           // this block's replica of the solve's scalars
+};
+
+__device__ __forceinline__ unsigned int smem_u32(const void* p) {
+    return (unsigned int)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ unsigned int cluster_map(unsigned int addr, unsigned int rank) {
+    unsigned int r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
+    return r;
+}
+
+__device__ __forceinline__ void cluster_sync_all() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;"
+                 ::: "memory");
+}
+
+__device__ __forceinline__ bool mbar_test_parity(unsigned int addr, unsigned int parity) {
+    unsigned int ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(addr), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Called by all threads of every block of the cluster at kernel start, after
+// the job is in shared memory: loads the scalar replica, initialises the
+// mbarrier for nb arrivals per phase and makes it visible cluster-wide.
+__device__ __forceinline__ void cluster_begin(ClusterState& cs, const Scalars* gsc, unsigned int nb) {
+    if (threadIdx.x == 0) {
+        cs.sc = *gsc;
+        cs.err = 0;
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&cs.mbar)), "r"(nb)
+                     : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    cluster_sync_all();
+}
+
+// Called by all threads at kernel end: block 0 writes the scalars back and no
+// block leaves while another may still write into its shared memory.
+__device__ __forceinline__ void cluster_end(ClusterState& cs, Scalars* gsc, unsigned int rank) {
+    __syncthreads();
+    if (rank == 0 && threadIdx.x == 0) *gsc = cs.sc;
+    cluster_sync_all();
+}
+
+template <int NV, class Finish>
+__device__ __forceinline__ bool cluster_reduce(const double (&v)[NV], ClusterState& cs,
+                                               unsigned int phase, unsigned int nb,
+                                               unsigned int rank, GroupSync* gs, Finish&& finish) {
+    double out[NV];
+    GTRACE(rank == 0 && threadIdx.x == 0, 40);
+    block_sum<NV>(v, out);  // warp 0 holds the sums; ends with __syncthreads()
+    GTRACE(rank == 0 && threadIdx.x == 0, 41);
+    const unsigned int par = phase & 1u;
+    if (threadIdx.x < 32) {
+#pragma unroll
+        for (int j = 0; j < NV; ++j) out[j] = __shfl_sync(0xffffffffu, out[j], 0);  // lane 0's bits
+        if (threadIdx.x < nb) {  // lane t delivers this block's sums to block t
+            const unsigned int t = threadIdx.x;
+#pragma unroll
+            for (int j = 0; j < NV; ++j) {
+                const unsigned int dst = cluster_map(smem_u32(&cs.slots[par][rank][j]), t);
+                asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(dst), "d"(out[j]) : "memory");
+            }
+            const unsigned int bar = cluster_map(smem_u32(&cs.mbar), t);
+            asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(bar)
+                         : "memory");
+        }
+    }
+    if (threadIdx.x == 0) {
+        const unsigned int bar = smem_u32(&cs.mbar);
+        const long long t0 = clock64();
+        while (!mbar_test_parity(bar, par)) {
+            if (clock64() - t0 > GROUP_WAIT_LIMIT_CYCLES) {
+                cs.err = 1;
+                atomicExch(&gs->err, 1);
+                break;
+            }
+        }
+        GTRACE(rank == 0, 42);
+        if (!cs.err) {
+            double tot[NV];
+#pragma unroll
+            for (int j = 0; j < NV; ++j) tot[j] = 0.0;
+            for (unsigned int q = 0; q < nb; ++q) {
+#pragma unroll
+                for (int j = 0; j < NV; ++j) tot[j] += cs.slots[par][q][j];
+            }
+            finish(tot);
+        }
+        GTRACE(rank == 0, 43);
+    }
+    __syncthreads();
+    return cs.err == 0;
+}
+
+// The reduction + barrier of one phase, in grid or cluster mode.
+struct LevelSync {
+    double* partials;
+    GroupSync* gs;
+    unsigned int nb, bid;
+    ClusterState* cs;  // nullptr: cooperative grid
+    unsigned int phase;
+    template <int NV, class Finish>
+    __device__ __forceinline__ bool reduce(const double (&v)[NV], Finish&& finish) {
+        if (cs) return cluster_reduce<NV>(v, *cs, phase++, nb, bid, gs, finish);
+        return group_reduce<NV>(v, partials, gs, nb, bid, finish);
+    }
+};
+
 }  // namespace eecmg

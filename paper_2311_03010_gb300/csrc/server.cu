@@ -233,7 +233,8 @@ eecmg_status enqueue_tick(eecmg_server_s* S, const std::vector<Request*>& admitt
     for (size_t w = 0; w < waves.size(); ++w) {
         const HostWave& W = waves[w];
         SCK(launch_level_batch((const LevelJob*)(d + jo[w]), (const unsigned short*)(d + bo[w]),
-                               (int)W.jobs.size(), W.blocks, W.rt, W.sep, W.prec, W.cgls, W.bf16, s));
+                               (int)W.jobs.size(), W.blocks, W.rt, W.sep, W.prec, W.cgls, W.bf16,
+                               W.cluster, s));
     }
     for (Request* r : S->active) {
         eecmg_plan_s& P = r->slot;
@@ -345,7 +346,9 @@ void scheduler(eecmg_server_s* S) {
                 if (S->stop) break;
                 continue;
             }
-            while (!S->queue.empty() && (int)S->active.size() < S->max_slots) {
+            // a slot (status area) stays taken until its request's tick completes
+            while (!S->queue.empty() && (int)S->active.size() < S->max_slots &&
+                   !S->free_sidx.empty()) {
                 Request* r = S->queue.front();
                 size_t off = 0;
                 if (!S->arena.alloc(r->bytes, &off)) break;  // first come, first served
