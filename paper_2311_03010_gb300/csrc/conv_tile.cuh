@@ -95,25 +95,27 @@ __device__ __forceinline__ void conv_compute(ConvSmem<R, SEP>& S) {
     constexpr int IW = ConvSmem<R, SEP>::IW, PT = ConvSmem<R, SEP>::PT, PO = ConvSmem<R, SEP>::PO;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (SEP) {
-        float cyr[2 * R + 1], cxr[2 * R + 1];
-#pragma unroll
-        for (int d = 0; d < 2 * R + 1; ++d) {
-            cyr[d] = S.cy[d];
-            cxr[d] = S.cx[d];
-        }
+        // Each thread slides a register window over 8 outputs; the taps are
+        // read from shared memory (a broadcast) once per tap, tap-outer, so the
+        // window and the 8 accumulators are all that live in registers.  Every
+        // output still sums its taps in increasing order.
         // vertical pass: tmp(r, c) = sum_d cy[d] in(r + d, c), r < TH, all IW columns
         for (int item = tid; item < 4 * IW; item += NTHREADS) {
             const int rg = item / IW, c = item - rg * IW;
             float v[8 + 2 * R];
 #pragma unroll
             for (int j = 0; j < 8 + 2 * R; ++j) v[j] = S.in[(rg * 8 + j) * IW + c];
+            float acc[8];
 #pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                float acc = 0.f;
+            for (int i = 0; i < 8; ++i) acc[i] = 0.f;
 #pragma unroll
-                for (int d = 0; d < 2 * R + 1; ++d) acc = fmaf(cyr[d], v[i + d], acc);
-                S.tmp[(rg * 8 + i) * PT + c] = acc;
+            for (int d = 0; d < 2 * R + 1; ++d) {
+                const float cd = S.cy[d];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) acc[i] = fmaf(cd, v[i + d], acc[i]);
             }
+#pragma unroll
+            for (int i = 0; i < 8; ++i) S.tmp[(rg * 8 + i) * PT + c] = acc[i];
         }
         __syncthreads();
         // horizontal pass: one row per lane, 8 consecutive columns per warp
@@ -121,28 +123,32 @@ __device__ __forceinline__ void conv_compute(ConvSmem<R, SEP>& S) {
         float v[8 + 2 * R];
 #pragma unroll
         for (int j = 0; j < 8 + 2 * R; ++j) v[j] = S.tmp[r * PT + cg * 8 + j];
+        float acc[8], lo[8];
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
-            float acc = 0.f;
-            if (PREC) {
-                float lo = 0.f;
-#pragma unroll
-                for (int d = 0; d < 2 * R + 1; ++d) {
-                    const float p = __fmul_rn(cxr[d], v[i + d]);
-                    const float pe = fmaf(cxr[d], v[i + d], -p);  // exact product error
-                    const float s = __fadd_rn(acc, p);
-                    const float bp = __fsub_rn(s, acc);
-                    const float se = __fadd_rn(__fsub_rn(acc, __fsub_rn(s, bp)), __fsub_rn(p, bp));
-                    acc = s;
-                    lo = __fadd_rn(lo, __fadd_rn(pe, se));
-                }
-                acc = __fadd_rn(acc, lo);
-            } else {
-#pragma unroll
-                for (int d = 0; d < 2 * R + 1; ++d) acc = fmaf(cxr[d], v[i + d], acc);
-            }
-            S.out[r * PO + cg * 8 + i] = acc;
+            acc[i] = 0.f;
+            lo[i] = 0.f;
         }
+#pragma unroll
+        for (int d = 0; d < 2 * R + 1; ++d) {
+            const float cd = S.cx[d];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                if (PREC) {
+                    const float p = __fmul_rn(cd, v[i + d]);
+                    const float pe = fmaf(cd, v[i + d], -p);  // exact product error
+                    const float sm = __fadd_rn(acc[i], p);
+                    const float bp = __fsub_rn(sm, acc[i]);
+                    const float se = __fadd_rn(__fsub_rn(acc[i], __fsub_rn(sm, bp)), __fsub_rn(p, bp));
+                    acc[i] = sm;
+                    lo[i] = __fadd_rn(lo[i], __fadd_rn(pe, se));
+                } else {
+                    acc[i] = fmaf(cd, v[i + d], acc[i]);
+                }
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < 8; ++i) S.out[r * PO + cg * 8 + i] = PREC ? __fadd_rn(acc[i], lo[i]) : acc[i];
     } else {
         const int c = tid & 63, rg = tid >> 6;
         float acc[8];

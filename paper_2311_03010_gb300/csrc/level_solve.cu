@@ -50,12 +50,14 @@ int cluster_limit() {
 }
 
 // Levels of at most this many pixels run in cluster mode (EECMG_CLUSTER_MAX_PX
-// overrides; 0 turns cluster mode off).
+// overrides; 0 turns cluster mode off).  Measured on GB300: 128^2 and below
+// gain from the in-GPC exchange; from 256^2 up a 16-SM cluster is
+// throughput-bound and the grid form is faster.
 size_t cluster_max_px() {
     static long long v = -1;
     if (v < 0) {
         const char* e = std::getenv("EECMG_CLUSTER_MAX_PX");
-        v = e ? std::atoll(e) : 262144;
+        v = e ? std::atoll(e) : 16384;
         if (v < 0) v = 0;
     }
     return (size_t)v;
@@ -63,8 +65,12 @@ size_t cluster_max_px() {
 
 }  // namespace
 
-// Blocks of a level solve: one per 32 x 64 tile or per 1024 pixels, at most
-// two per SM.  The count depends only on the level's size, so a solve is
+// Blocks of a level solve: one per 32 x 64 tile (2048 pixels; the larger of
+// the tile count and pixels / EECMG_PX_PER_BLOCK when that is set), at most
+// two per SM (EECMG_BLOCKS_PER_SM, 1..3, overrides; every instantiation fits
+// three per SM).  Measured on GB300: one block per tile beats one per 1024
+// pixels by 10-25 % on the 512^2 and batched cascades (cheaper barriers, no
+// idle blocks in the convolution phases).  The count depends only on the level's size, so a solve is
 // partitioned (and its reductions rounded) the same way alone or in a batch.
 int level_want_blocks(int h, int w) {
     static int cap = 0;
@@ -72,11 +78,20 @@ int level_want_blocks(int h, int w) {
         int dev = 0, sms = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cap = 2 * (sms > 0 ? sms : 1);
+        const char* e = std::getenv("EECMG_BLOCKS_PER_SM");  // tuning override
+        int per = e ? std::atoi(e) : 2;
+        per = per < 1 ? 1 : (per > 3 ? 3 : per);
+        cap = per * (sms > 0 ? sms : 1);
+    }
+    static size_t px_per_block = 0;
+    if (px_per_block == 0) {
+        const char* e = std::getenv("EECMG_PX_PER_BLOCK");  // tuning override
+        const long long v = e ? std::atoll(e) : 2048;
+        px_per_block = v < 1024 ? 1024 : (size_t)v;  // the plan sizes partials for >= 1024
     }
     const size_t n = (size_t)h * w;
     const int tiles = (int)conv_blocks(h, w);
-    const int elem = (int)((n + 4 * NTHREADS - 1) / (4 * NTHREADS));
+    const int elem = (int)((n + px_per_block - 1) / px_per_block);
     const int want = tiles > elem ? tiles : elem;
     return want < cap ? want : cap;
 }

@@ -6,8 +6,9 @@
 namespace eecmg {
 
 // One level solve.  MR-II uses v[2], aw[2], d[2], hd[2], r; CGLS uses
-// v[0] = s, v[1] = p, aw[0] = q, r.  The group's GroupSync must be zero at
-// the first launch (every barrier leaves it zero again).
+// v[0] = s, v[1] = p, aw[0] = q, r.  The job's GroupSync must be zero at
+// the first launch (every launch leaves it zero again); partials holds
+// 2 x NPART doubles per block.
 struct LevelJob {
     const float* g = nullptr;
     float* u = nullptr;

@@ -4,9 +4,9 @@
 //
 // Every phase of an iteration is a grid-stride pass over the level's tiles
 // (convolution phases, 32 x 64 tiles with halo in shared memory) or pixels
-// (elementwise phases), ended by group_reduce: the deterministic FP64 sums
-// of the phase's inner products and its scalar update (finish.cuh), then a
-// bounded grid barrier.  Compared with one launch per phase this removes the
+// (elementwise phases), ended by a reduction barrier (persistent.cuh): the
+// deterministic FP64 sums of the phase's inner products and its scalar
+// update (finish.cuh), run by every block on its own replica of the scalars.  Compared with one launch per phase this removes the
 // launch latency of every phase and, because the loop tests the stop flag,
 // the iterations that a stopping rule makes unnecessary are never launched.
 // Vectors written inside the launch are read back through L2 (ld.global.cg).
@@ -408,24 +408,35 @@ __device__ __forceinline__ void level_kernel(const LevelLaunch& LL) {
     const unsigned int bid = LL.jobs ? blockIdx.x - (unsigned int)J.block0 : blockIdx.x;
     const bool cl = LL.cluster > 0;
     TRACE(bid, 1);
-    if (cl) cluster_begin(CS, J.sc, nb);
-    LevelSync sy{J.partials, J.gs, nb, bid, cl ? &CS : nullptr, 0u};
-    Scalars* sc = cl ? &CS.sc : J.sc;
+    if (cl) {
+        cluster_begin(CS, J.sc, nb);
+    } else {
+        if (threadIdx.x == 0) CS.sc = *J.sc;
+        __syncthreads();
+    }
+    LevelSync sy{J.partials, J.gs, nb, bid, &CS, cl, 0u};
+    Scalars* sc = &CS.sc;  // this block's replica (identical in every block)
     if constexpr (CGLS)
         cgls_body<R, SEP, PREC, HT>(S, J, sc, nb, bid, sy);
     else
         mr2_body<R, SEP, PREC, HT>(S, J, sc, nb, bid, sy);
-    if (cl) cluster_end(CS, J.sc, bid);
+    if (cl) {
+        cluster_end(CS, J.sc, bid);
+    } else {
+        __syncthreads();
+        if (bid == 0 && threadIdx.x == 0) *J.sc = CS.sc;
+        grid_exit(J.gs, nb);
+    }
     TRACE(bid, 2);
 }
 
 template <int R, bool SEP, bool PREC, typename HT>
-__global__ void __launch_bounds__(NTHREADS) k_level_mr2(LevelLaunch LL) {
+__global__ void __launch_bounds__(NTHREADS, 3) k_level_mr2(LevelLaunch LL) {
     level_kernel<R, SEP, PREC, HT, false>(LL);
 }
 
 template <int R, bool SEP, bool PREC, typename HT>
-__global__ void __launch_bounds__(NTHREADS) k_level_cgls(LevelLaunch LL) {
+__global__ void __launch_bounds__(NTHREADS, 3) k_level_cgls(LevelLaunch LL) {
     level_kernel<R, SEP, PREC, HT, true>(LL);
 }
 

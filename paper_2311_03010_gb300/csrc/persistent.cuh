@@ -1,13 +1,17 @@
-// persistent.cuh -- group barrier with a fused deterministic reduction, for
+// persistent.cuh -- phase barriers with a fused deterministic reduction, for
 // the persistent (one launch per level solve) kernels.
 //
-// All blocks of a group are co-resident (cooperative launch).  At the end of
-// a phase every block publishes its FP64 block sums; the last block to
-// arrive sums all blocks' partials in a fixed order, runs the phase's scalar
-// update on one thread and releases the others by bumping a generation
-// counter.  Waits spin on that counter with a clock64 limit: a wait that
-// runs out sets the group's error flag and every block returns, so a kernel
-// can never hang the GPU; the host reports the flag as a timeout.
+// Grid mode: all blocks of a job are co-resident (cooperative launch).  At
+// the end of a phase every block writes its FP64 block sums into its slot of
+// the phase's partials (double-buffered by phase parity), then adds one to
+// the job's arrival counter with release semantics.  Every block waits until
+// the counter reaches (phase + 1) x blocks, then sums all blocks' partials in
+// a fixed order and runs the phase's scalar update on its own replica of the
+// scalars: all replicas stay identical, so no block has to broadcast.  The
+// wait spins on an acquire load with a clock64 limit: a wait that runs out
+// sets the job's error flag and every block returns, so a kernel can never
+// hang the GPU; the host reports the flag as a timeout.  The counter starts
+// at zero; the last block to leave the kernel resets it for the next launch.
 #pragma once
 
 #include "common.cuh"
@@ -35,9 +39,9 @@ __device__ __forceinline__ void trace_any(unsigned int tag) {
 #endif
 
 struct alignas(64) GroupSync {
-    unsigned int count;   // arrivals in the current phase
-    unsigned int gen;     // phase generation (bumped by the last arrival)
-    int err;              // 1 after a wait ran out
+    unsigned int count;   // arrivals in this launch (phases x blocks)
+    unsigned int exits;   // blocks that have left this launch
+    int err;              // 1 after a wait ran out (sticky)
     int pad[13];
 };
 
@@ -49,76 +53,79 @@ __device__ __forceinline__ T ldcg(const T* p) {
     return __ldcg(p);
 }
 
-// Every thread of every block in the group calls this with its block's NV
-// values in v (thread-local contributions; reduced here).  Returns false if
-// the group is in error (the caller returns).
-//
-// Memory ordering: each thread's phase writes are ordered before the
-// arrival by __syncthreads() and thread 0's GPU-scope fence (fences are
-// cumulative); waiters fence after seeing the new generation and then
-// release their block with __syncthreads().  Vectors written in the phase
-// are read afterwards through L2 (ld.global.cg).
+__device__ __forceinline__ void red_release_add(unsigned int* p, unsigned int v) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ unsigned int ld_acquire(const unsigned int* p) {
+    unsigned int v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Every thread of every block of the job calls this with its NV values in v
+// (thread-local contributions).  partials holds 2 x nb x NPART doubles.
+// Returns false if the job is in error (the caller returns).
 template <int NV, class Finish>
-__device__ __forceinline__ bool group_reduce(const double (&v)[NV], double* partials,
-                                             GroupSync* gs, unsigned int nb, unsigned int bid,
-                                             Finish&& finish) {
+__device__ __forceinline__ bool grid_reduce(const double (&v)[NV], double* partials, GroupSync* gs,
+                                            unsigned int nb, unsigned int bid, unsigned int phase,
+                                            Finish&& finish) {
     double out[NV];
     block_sum<NV>(v, out);  // ends with __syncthreads()
-    __shared__ int s_last, s_ok;
+    __shared__ int s_ok;
+    double* slot = partials + (size_t)(phase & 1u) * nb * NPART;
     GTRACE(bid == 0 && threadIdx.x == 0, 20);
     if (threadIdx.x == 0) {
 #pragma unroll
-        for (int j = 0; j < NV; ++j) partials[(size_t)bid * NPART + j] = out[j];
-        const unsigned int gen = *(volatile unsigned int*)&gs->gen;
-        __threadfence();
-        const unsigned int t = atomicAdd(&gs->count, 1u);
-        GTRACE(bid == 0, 21);
-        s_last = (t == nb - 1);
-        s_ok = 1;
-        if (!s_last) {
-            const long long t0 = clock64();
-            while (*(volatile unsigned int*)&gs->gen == gen) {
-                if (*(volatile int*)&gs->err) {
-                    s_ok = 0;
-                    break;
-                }
-                if (clock64() - t0 > GROUP_WAIT_LIMIT_CYCLES) {
-                    atomicExch(&gs->err, 1);
-                    s_ok = 0;
-                    break;
-                }
-                __nanosleep(32);
+        for (int j = 0; j < NV; ++j) slot[(size_t)bid * NPART + j] = out[j];
+        red_release_add(&gs->count, 1u);  // orders this block's phase writes before the arrival
+        const unsigned int target = (phase + 1u) * nb;
+        int ok = 1;
+        const long long t0 = clock64();
+        while (ld_acquire(&gs->count) < target) {
+            if (*(volatile int*)&gs->err) {
+                ok = 0;
+                break;
             }
-            GTRACE(bid == 0, 22);
+            if (clock64() - t0 > GROUP_WAIT_LIMIT_CYCLES) {
+                atomicExch(&gs->err, 1);
+                ok = 0;
+                break;
+            }
+            __nanosleep(20);
         }
-        __threadfence();
+        s_ok = ok;
+        GTRACE(bid == 0, 21);
     }
     __syncthreads();
-    if (s_last) {
-        // the last block sums the blocks' partials in a fixed order, runs the
-        // scalar update and releases the group
-        GTRACE(threadIdx.x == 0, 30);
-        double acc[NV];
+    if (!s_ok) return false;
+    // every block: the blocks' partials in a fixed order, then the update
+    double acc[NV];
 #pragma unroll
-        for (int j = 0; j < NV; ++j) acc[j] = 0.0;
-        for (unsigned int b = threadIdx.x; b < nb; b += NTHREADS) {
+    for (int j = 0; j < NV; ++j) acc[j] = 0.0;
+    for (unsigned int b = threadIdx.x; b < nb; b += NTHREADS) {
 #pragma unroll
-            for (int j = 0; j < NV; ++j) acc[j] += __ldcg(partials + (size_t)b * NPART + j);
-        }
-        double tot[NV];
-        block_sum<NV>(acc, tot);
-        GTRACE(threadIdx.x == 0, 31);
-        if (threadIdx.x == 0) {
-            finish(tot);
-            GTRACE(true, 32);
-            gs->count = 0u;
-            __threadfence();
-            atomicAdd(&gs->gen, 1u);
-            GTRACE(true, 33);
-        }
-        __syncthreads();
+        for (int j = 0; j < NV; ++j) acc[j] += __ldcg(slot + (size_t)b * NPART + j);
     }
-    return s_ok != 0 && *(volatile int*)&gs->err == 0;
+    double tot[NV];
+    block_sum<NV>(acc, tot);
+    if (threadIdx.x == 0) finish(tot);
+    GTRACE(bid == 0 && threadIdx.x == 0, 22);
+    __syncthreads();
+    return true;
+}
+
+// Called by all threads of every block at the end of a grid-mode solve.
+__device__ __forceinline__ void grid_exit(GroupSync* gs, unsigned int nb) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned int t = atomicAdd(&gs->exits, 1u);
+        if (t == nb - 1) {  // every block has passed its last wait
+            gs->count = 0u;
+            gs->exits = 0u;
+            __threadfence();
+        }
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -134,6 +141,8 @@ __device__ __forceinline__ bool group_reduce(const double (&v)[NV], double* part
 
 constexpr int CLUSTER_MAX = 16;
 
+// Per-block shared state of a level solve: the block's replica of the
+// solve's scalars (both modes) and, in cluster mode, the exchange slots.
 struct ClusterState {
     double slots[2][CLUSTER_MAX][NPART];  // [phase parity][source rank][value]
     unsigned long long mbar;
@@ -247,12 +256,13 @@ struct LevelSync {
     double* partials;
     GroupSync* gs;
     unsigned int nb, bid;
-    ClusterState* cs;  // nullptr: cooperative grid
+    ClusterState* cs;
+    bool cluster;
     unsigned int phase;
     template <int NV, class Finish>
     __device__ __forceinline__ bool reduce(const double (&v)[NV], Finish&& finish) {
-        if (cs) return cluster_reduce<NV>(v, *cs, phase++, nb, bid, gs, finish);
-        return group_reduce<NV>(v, partials, gs, nb, bid, finish);
+        if (cluster) return cluster_reduce<NV>(v, *cs, phase++, nb, bid, gs, finish);
+        return grid_reduce<NV>(v, partials, gs, nb, bid, phase++, finish);
     }
 };
 

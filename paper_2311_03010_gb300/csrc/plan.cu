@@ -631,7 +631,7 @@ eecmg_status eecmg_plan(int width, int height, int levels, const double* psf, in
     Y.gs_off = off;
     off = align_up(off + sizeof(GroupSync) * levels, 256);
     Y.part_off = off;
-    off = align_up(off + sizeof(double) * NPART * max_blocks, 256);
+    off = align_up(off + sizeof(double) * 2 * NPART * max_blocks, 256);  // double-buffered
     Y.bytes = off;
     P->ws_bytes = off;
     P->max_blocks = max_blocks;
