@@ -287,6 +287,19 @@ eecmg_status eecmg_residual_noalloc(int width, int height, const double *psf, in
                                     int psf_h, const float *g, const float *u, float *r,
                                     double *norms, cudaStream_t stream);
 
+/*
+ * Diagnostic of the failure path (no counterpart in the paper).  Every wait
+ * inside a level solve (grid barrier poll, cluster mbarrier wait) gives up
+ * after a clock limit, sets the job's error flag and returns, so a stuck
+ * solve surfaces as EECMG_ERR_TIMEOUT instead of a hung GPU.  This call runs
+ * one such barrier whose arrival count can never be reached (cluster = 0:
+ * the grid barrier; 1: the cluster mbarrier) with a limit of about 10 us on
+ * one block, then reads the flag.  Returns EECMG_ERR_TIMEOUT when the wait
+ * gave up as designed, EECMG_OK if it did not (a defect), CUDA/OOM on
+ * failures.  Synchronises the stream; allocates and frees a small scratch.
+ */
+eecmg_status eecmg_selftest_bounded_wait(int cluster, cudaStream_t stream);
+
 /* ---- serving: continuous batching of restoration requests -------------- */
 
 typedef struct eecmg_server_s *eecmg_server_t;

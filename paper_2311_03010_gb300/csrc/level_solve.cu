@@ -67,8 +67,8 @@ size_t cluster_max_px() {
 
 // Blocks of a level solve: one per 32 x 64 tile (2048 pixels; the larger of
 // the tile count and pixels / EECMG_PX_PER_BLOCK when that is set), at most
-// two per SM (EECMG_BLOCKS_PER_SM, 1..3, overrides; every instantiation fits
-// three per SM).  Measured on GB300: one block per tile beats one per 1024
+// two per SM (EECMG_BLOCKS_PER_SM, 1..3, overrides; the MR-II solvers fit two
+// per SM, CGLS three; a solve never exceeds its instantiation's capacity).  Measured on GB300: one block per tile beats one per 1024
 // pixels by 10-25 % on the 512^2 and batched cascades (cheaper barriers, no
 // idle blocks in the convolution phases).  The count depends only on the level's size, so a solve is
 // partitioned (and its reductions rounded) the same way alone or in a batch.

@@ -220,16 +220,51 @@ __device__ __forceinline__ void mr2_body(ConvSmem<R, SEP>& S, const LevelJob& J,
             const float cb = step ? vldf(&sc->f_cb) : 0.f;
             float arr = 0.f, avv = 0.f, avr = 0.f;
             const size_t n4 = n >> 2;
+            using IO = VecIO<HT>;
+            const int j = k - 1, sj = j & 1, sj1 = sj ^ 1;  // sj == sk1
+            HT* dd[2] = {reinterpret_cast<HT*>(J.d[0]), reinterpret_cast<HT*>(J.d[1])};
             for (size_t q = (size_t)bid * NTHREADS + threadIdx.x; q < n4; q += stride) {
-                float4 rv;
+                // every operand is loaded before the first store, so the pass
+                // costs one round trip to L2 (the stores alias none of the
+                // loads except the same elements, already read)
+                const float4 vk = ld4cg(J.v[sk], q), awk = ld4cg(J.aw[sk], q);
+                const float4 rr = ld4cg(J.r, q);
+                float4 vj = make_float4(0.f, 0.f, 0.f, 0.f), awj = vj, uu = vj;
+                float4 dA = vj, hA = vj, dB = vj, hB = vj;
                 if (step) {
-                    rv = mr_step4<HT>(J, k - 1, q, c);
-                    arr = dot4(rv, rv, arr);
-                } else {
-                    rv = ld4cg(J.r, q);
+                    vj = ld4cg(J.v[sj], q);
+                    awj = ld4cg(J.aw[sj], q);
+                    uu = ld4cg(J.u, q);
+                    if (j >= 2) {
+                        dA = IO::ld4(dd[sj1], q);
+                        hA = ld4cg(J.hd[sj1], q);
+                    }
+                    if (j >= 3) {
+                        dB = IO::ld4(dd[sj], q);
+                        hB = ld4cg(J.hd[sj], q);
+                    }
                 }
-                float4 vn = fma4(-ca, ld4cg(J.v[sk], q), ld4cg(J.aw[sk], q));
-                if (step) vn = fma4(-cb, ld4cg(J.v[sk1], q), vn);
+                float4 rv = rr;
+                if (step) {  // step j = k - 1 (same operation order as mr_step4)
+                    float4 dj = mul4(c.dw, vj);
+                    float4 hj = mul4(c.dinv, awj);
+                    if (j >= 2) {
+                        dj = fma4(-c.d1, dA, dj);
+                        hj = fma4(-c.d1, hA, hj);
+                    }
+                    if (j >= 3) {
+                        dj = fma4(-c.d2, dB, dj);
+                        hj = fma4(-c.d2, hB, hj);
+                    }
+                    IO::st4(dd[sj], q, dj);
+                    st4(J.hd[sj], q, hj);
+                    st4(J.u, q, fma4(c.tau, dj, uu));
+                    rv = fma4(-c.tau, hj, rr);
+                    st4(J.r, q, rv);
+                    arr = dot4(rv, rv, arr);
+                }
+                float4 vn = fma4(-ca, vk, awk);
+                if (step) vn = fma4(-cb, vj, vn);
                 st4(J.v[sk1], q, vn);
                 avv = dot4(vn, vn, avv);
                 avr = dot4(vn, rv, avr);
@@ -348,8 +383,10 @@ __device__ __forceinline__ void cgls_body(ConvSmem<R, SEP>& S, const LevelJob& J
             float arr = 0.f;
             const size_t n4 = n >> 2;
             for (size_t q = (size_t)bid * NTHREADS + threadIdx.x; q < n4; q += stride) {
-                st4(J.u, q, fma4(a, IO::ld4(pv, q), ld4cg(J.u, q)));
-                const float4 r = fma4(-a, ld4cg(qv, q), ld4cg(rv_, q));
+                const float4 pq = IO::ld4(pv, q), uq = ld4cg(J.u, q);  // all loads first
+                const float4 qq = ld4cg(qv, q), rq = ld4cg(rv_, q);
+                st4(J.u, q, fma4(a, pq, uq));
+                const float4 r = fma4(-a, qq, rq);
                 st4(rv_, q, r);
                 arr = dot4(r, r, arr);
             }
@@ -431,7 +468,7 @@ __device__ __forceinline__ void level_kernel(const LevelLaunch& LL) {
 }
 
 template <int R, bool SEP, bool PREC, typename HT>
-__global__ void __launch_bounds__(NTHREADS, 3) k_level_mr2(LevelLaunch LL) {
+__global__ void __launch_bounds__(NTHREADS, 2) k_level_mr2(LevelLaunch LL) {
     level_kernel<R, SEP, PREC, HT, false>(LL);
 }
 

@@ -69,7 +69,8 @@ __device__ __forceinline__ unsigned int ld_acquire(const unsigned int* p) {
 template <int NV, class Finish>
 __device__ __forceinline__ bool grid_reduce(const double (&v)[NV], double* partials, GroupSync* gs,
                                             unsigned int nb, unsigned int bid, unsigned int phase,
-                                            Finish&& finish) {
+                                            Finish&& finish,
+                                            long long limit = GROUP_WAIT_LIMIT_CYCLES) {
     double out[NV];
     block_sum<NV>(v, out);  // ends with __syncthreads()
     __shared__ int s_ok;
@@ -87,7 +88,7 @@ __device__ __forceinline__ bool grid_reduce(const double (&v)[NV], double* parti
                 ok = 0;
                 break;
             }
-            if (clock64() - t0 > GROUP_WAIT_LIMIT_CYCLES) {
+            if (clock64() - t0 > limit) {
                 atomicExch(&gs->err, 1);
                 ok = 0;
                 break;
@@ -203,7 +204,8 @@ __device__ __forceinline__ void cluster_end(ClusterState& cs, Scalars* gsc, unsi
 template <int NV, class Finish>
 __device__ __forceinline__ bool cluster_reduce(const double (&v)[NV], ClusterState& cs,
                                                unsigned int phase, unsigned int nb,
-                                               unsigned int rank, GroupSync* gs, Finish&& finish) {
+                                               unsigned int rank, GroupSync* gs, Finish&& finish,
+                                               long long limit = GROUP_WAIT_LIMIT_CYCLES) {
     double out[NV];
     GTRACE(rank == 0 && threadIdx.x == 0, 40);
     block_sum<NV>(v, out);  // warp 0 holds the sums; ends with __syncthreads()
@@ -228,7 +230,7 @@ __device__ __forceinline__ bool cluster_reduce(const double (&v)[NV], ClusterSta
         const unsigned int bar = smem_u32(&cs.mbar);
         const long long t0 = clock64();
         while (!mbar_test_parity(bar, par)) {
-            if (clock64() - t0 > GROUP_WAIT_LIMIT_CYCLES) {
+            if (clock64() - t0 > limit) {
                 cs.err = 1;
                 atomicExch(&gs->err, 1);
                 break;

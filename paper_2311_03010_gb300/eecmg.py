@@ -89,6 +89,7 @@ _SIGS = {
     "eecmg_denoise": [_VP, _I, _VP, _VP, _VP],
     "eecmg_level_solve": [_VP, _I, _VP, _VP, _I, _VP],
     "eecmg_residual_noalloc": [_I, _I, _PD, _I, _I, _VP, _VP, _VP, _VP, _VP],
+    "eecmg_selftest_bounded_wait": [_I, _VP],
     "eecmg_server_create": [ctypes.c_size_t, _I, ctypes.POINTER(_VP)],
     "eecmg_server_submit": [_VP, _VP, _VP, _VP, ctypes.POINTER(ctypes.c_uint64)],
     "eecmg_server_poll": [_VP, ctypes.c_uint64, _PI, _PD],
@@ -285,6 +286,12 @@ def eecmg_residual_noalloc(width, height, psf, g, u, r, norms, stream=None):
     nptr = norms if isinstance(norms, int) else norms.data_ptr()
     _call("eecmg_residual_noalloc", int(width), int(height), psf.ctypes.data_as(_PD),
           psf.shape[1], psf.shape[0], _ptr(g), _ptr(u), _ptr(r), nptr, _stream(stream))
+
+
+def eecmg_selftest_bounded_wait(cluster, stream=None):
+    """Returns the status code (EECMG_ERR_TIMEOUT = 6 is the designed outcome)."""
+    lib = load()
+    return lib.eecmg_selftest_bounded_wait(int(cluster), _stream(stream))
 
 
 def eecmg_server_create(mem_budget_bytes, max_slots):
