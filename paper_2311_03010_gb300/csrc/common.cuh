@@ -119,6 +119,34 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
+__device__ __forceinline__ double df_to_double(DF a) { return (double)a.hi + (double)a.lo; }
+
+// Block-wide double-float sum of NV values per thread, entirely on the FP32
+// pipes (GB300's FP64 pipe is narrow).  Every lane of warp 0 returns lane
+// 0's totals (the butterfly's lanes may differ in the last bit otherwise).
+// Ends with __syncthreads().
+template <int NV>
+__device__ __forceinline__ void block_sum_df(const DF (&v)[NV], DF (&out)[NV]) {
+    __shared__ DF red_df[NV][NTHREADS / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int j = 0; j < NV; ++j) {
+        const DF s = warp_sum_df(v[j]);
+        if (lane == 0) red_df[j][warp] = s;
+    }
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int j = 0; j < NV; ++j) {
+            DF s = lane < NTHREADS / 32 ? red_df[j][lane] : DF{0.f, 0.f};
+            s = warp_sum_df(s);
+            out[j].hi = __shfl_sync(0xffffffffu, s.hi, 0);
+            out[j].lo = __shfl_sync(0xffffffffu, s.lo, 0);
+        }
+    }
+    __syncthreads();
+}
+
 // Block-wide sum of NV values per thread; result valid in thread 0.
 template <int NV>
 __device__ __forceinline__ void block_sum(const double (&v)[NV], double (&out)[NV]) {

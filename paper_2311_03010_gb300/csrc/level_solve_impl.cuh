@@ -20,21 +20,7 @@
 namespace eecmg {
 
 #ifdef EECMG_TRACE
-// Phase timestamps of block 0 (tracing builds only): pairs (tag, %globaltimer ns).
-extern __device__ unsigned long long g_eecmg_trace[1 << 16];
-extern __device__ unsigned int g_eecmg_trace_n;
-__device__ __forceinline__ void trace_mark(unsigned int bid, unsigned int tag) {
-    if (bid == 0 && threadIdx.x == 0) {
-        unsigned long long t;
-        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-        const unsigned int i = atomicAdd(&g_eecmg_trace_n, 2u);
-        if (i + 1 < (1u << 16)) {
-            g_eecmg_trace[i] = tag;
-            g_eecmg_trace[i + 1] = t;
-        }
-    }
-}
-#define TRACE(bid, tag) trace_mark((bid), (tag))
+#define TRACE(bid, tag) GTRACE((bid) == 0 && threadIdx.x == 0, (tag))
 #else
 #define TRACE(bid, tag) ((void)0)
 #endif
@@ -170,7 +156,7 @@ __device__ __forceinline__ void mr2_body(ConvSmem<R, SEP>& S, const LevelJob& J,
             conv_phase<R, SEP, PREC, true>(S, J.u, h, w, nb, bid, epi);
         else
             conv_phase<R, SEP, PREC, false>(S, J.u, h, w, nb, bid, epi);
-        double v[2] = {(double)a0, (double)a1};
+        float v[2] = {a0, a1};
         const double ct2 = J.conv_tol2, d2 = J.disc2;
         if (!sy.reduce<2>(v, [&](double* t) { fin_resid(sc, t[0], t[1], ct2, d2); }))
             return;
@@ -186,7 +172,7 @@ __device__ __forceinline__ void mr2_body(ConvSmem<R, SEP>& S, const LevelJob& J,
             a0 = fmaf(z, z, a0);
             a1 = fmaf(z, ctr, a1);
         });
-        double v[2] = {(double)a0, (double)a1};
+        float v[2] = {a0, a1};
         if (!sy.reduce<2>(v, [&](double* t) { fin_mr_v1(sc, t[0], t[1]); }))
             return;
     }
@@ -206,7 +192,7 @@ __device__ __forceinline__ void mr2_body(ConvSmem<R, SEP>& S, const LevelJob& J,
                                                 aw[idx] = hz;
                                                 a0 = fmaf(hz, ctr, a0);
                                             });
-            double v[1] = {(double)a0};
+            float v[1] = {a0};
             TRACE(bid, 11);
             if (!sy.reduce<1>(v, [&](double* t) { fin_mr_a(sc, t[0]); }))
                 return;
@@ -285,7 +271,7 @@ __device__ __forceinline__ void mr2_body(ConvSmem<R, SEP>& S, const LevelJob& J,
                     avr = fmaf(vn, rv, avr);
                 }
             }
-            double v[3] = {(double)arr, (double)avv, (double)avr};
+            float v[3] = {arr, avv, avr};
             TRACE(bid, 13);
             if (!sy.reduce<3>(v, [&](double* t) { fin_mr_b(sc, k, t[0], t[1], t[2]); }))
                 return;
@@ -309,7 +295,7 @@ __device__ __forceinline__ void mr2_body(ConvSmem<R, SEP>& S, const LevelJob& J,
                 const float rv = mr_step_px<HT>(J, j, i, c.dw, c.d1, c.d2, c.dinv, c.tau);
                 arr = fmaf(rv, rv, arr);
             }
-        double v[1] = {(double)arr};
+        float v[1] = {arr};
         sy.reduce<1>(v, [&](double* t) { fin_mr_final(sc, t[0]); });
     }
 }
@@ -342,7 +328,7 @@ __device__ __forceinline__ void cgls_body(ConvSmem<R, SEP>& S, const LevelJob& J
             conv_phase<R, SEP, PREC, true>(S, J.u, h, w, nb, bid, epi);
         else
             conv_phase<R, SEP, PREC, false>(S, J.u, h, w, nb, bid, epi);
-        double v[2] = {(double)a0, (double)a1};
+        float v[2] = {a0, a1};
         const double ct2 = J.conv_tol2, d2 = J.disc2;
         if (!sy.reduce<2>(v, [&](double* t) { fin_resid(sc, t[0], t[1], ct2, d2); }))
             return;
@@ -358,7 +344,7 @@ __device__ __forceinline__ void cgls_body(ConvSmem<R, SEP>& S, const LevelJob& J
             IO::st(pv, idx, z);
             a0 = fmaf(z, z, a0);
         });
-        double v[1] = {(double)a0};
+        float v[1] = {a0};
         if (!sy.reduce<1>(v, [&](double* t) { fin_cg_s0(sc, t[0]); }))
             return;
     }
@@ -373,7 +359,7 @@ __device__ __forceinline__ void cgls_body(ConvSmem<R, SEP>& S, const LevelJob& J
                 qv[idx] = z;
                 a0 = fmaf(z, z, a0);
             });
-            double v[1] = {(double)a0};
+            float v[1] = {a0};
             if (!sy.reduce<1>(v, [&](double* t) { fin_cg_q(sc, t[0]); }))
                 return;
         }
@@ -397,7 +383,7 @@ __device__ __forceinline__ void cgls_body(ConvSmem<R, SEP>& S, const LevelJob& J
                     rv_[i] = r;
                     arr = fmaf(r, r, arr);
                 }
-            double v[1] = {(double)arr};
+            float v[1] = {arr};
             if (!sy.reduce<1>(v, [&](double* t) { fin_cg_step(sc, t[0]); }))
                 return;
         }
@@ -411,7 +397,7 @@ __device__ __forceinline__ void cgls_body(ConvSmem<R, SEP>& S, const LevelJob& J
                 IO::st(sv, idx, z);
                 a0 = fmaf(z, z, a0);
             });
-            double v[1] = {(double)a0};
+            float v[1] = {a0};
             if (!sy.reduce<1>(v, [&](double* t) { fin_cg_s(sc, t[0]); }))
                 return;
         }
@@ -424,7 +410,7 @@ __device__ __forceinline__ void cgls_body(ConvSmem<R, SEP>& S, const LevelJob& J
             if (bid == 0)
                 for (size_t i = 4 * n4 + threadIdx.x; i < n; i += NTHREADS)
                     IO::st(pv, i, fmaf(b, IO::ld(pv, i), IO::ld(sv, i)));
-            double v[1] = {0.0};
+            float v[1] = {0.f};
             if (!sy.reduce<1>(v, [&](double*) {})) return;
         }
     }
@@ -444,6 +430,10 @@ __device__ __forceinline__ void level_kernel(const LevelLaunch& LL) {
     const unsigned int nb = LL.jobs ? (unsigned int)J.nblocks : gridDim.x;
     const unsigned int bid = LL.jobs ? blockIdx.x - (unsigned int)J.block0 : blockIdx.x;
     const bool cl = LL.cluster > 0;
+#ifdef EECMG_TRACE
+    trace_reset();
+    __syncthreads();
+#endif
     TRACE(bid, 1);
     if (cl) {
         cluster_begin(CS, J.sc, nb);
@@ -465,6 +455,9 @@ __device__ __forceinline__ void level_kernel(const LevelLaunch& LL) {
         grid_exit(J.gs, nb);
     }
     TRACE(bid, 2);
+#ifdef EECMG_TRACE
+    trace_flush(bid == 0);
+#endif
 }
 
 template <int R, bool SEP, bool PREC, typename HT>

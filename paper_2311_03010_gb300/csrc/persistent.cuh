@@ -19,15 +19,37 @@
 namespace eecmg {
 
 #ifdef EECMG_TRACE
+// Tracing builds only: thread 0 of block 0 records (tag, clock64) pairs in
+// shared memory (no global traffic while the solve runs); trace_flush copies
+// them to g_eecmg_trace at kernel end.
 extern __device__ unsigned long long g_eecmg_trace[1 << 16];
 extern __device__ unsigned int g_eecmg_trace_n;
-__device__ __forceinline__ void trace_any(unsigned int tag) {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    const unsigned int i = atomicAdd(&g_eecmg_trace_n, 2u);
-    if (i + 1 < (1u << 16)) {
-        g_eecmg_trace[i] = tag;
-        g_eecmg_trace[i + 1] = t;
+struct TraceBuf {
+    unsigned long long e[2 * 384];
+    int n;
+};
+__device__ __forceinline__ TraceBuf& trace_buf() {
+    __shared__ TraceBuf b;
+    return b;
+}
+static __device__ __noinline__ void trace_any(unsigned int tag) {
+    TraceBuf& b = trace_buf();
+    const int i = b.n;
+    if (i < 384) {
+        b.e[2 * i] = tag;
+        b.e[2 * i + 1] = (unsigned long long)clock64();
+        b.n = i + 1;
+    }
+}
+__device__ __forceinline__ void trace_reset() {
+    if (threadIdx.x == 0) trace_buf().n = 0;
+}
+__device__ __forceinline__ void trace_flush(bool rec) {
+    if (rec && threadIdx.x == 0) {
+        TraceBuf& b = trace_buf();
+        const unsigned int base = atomicAdd(&g_eecmg_trace_n, 2u * (unsigned int)b.n);
+        for (int i = 0; i < 2 * b.n; ++i)
+            if (base + i < (1u << 16)) g_eecmg_trace[base + i] = b.e[i];
     }
 }
 #define GTRACE(cond, tag) \
@@ -63,22 +85,26 @@ __device__ __forceinline__ unsigned int ld_acquire(const unsigned int* p) {
     return v;
 }
 
-// Every thread of every block of the job calls this with its NV values in v
-// (thread-local contributions).  partials holds 2 x nb x NPART doubles.
-// Returns false if the job is in error (the caller returns).
+// Every thread of every block of the job calls this with its NV FP32 values
+// in v (thread-local contributions).  partials holds 2 x nb x NPART
+// double-float slots (8 bytes each).  All sums run in double-float on the FP32
+// pipes; only the job totals handed to finish are FP64.  Returns false if the
+// job is in error (the caller returns).
 template <int NV, class Finish>
-__device__ __forceinline__ bool grid_reduce(const double (&v)[NV], double* partials, GroupSync* gs,
+__device__ __forceinline__ bool grid_reduce(const float (&v)[NV], double* partials, GroupSync* gs,
                                             unsigned int nb, unsigned int bid, unsigned int phase,
                                             Finish&& finish,
                                             long long limit = GROUP_WAIT_LIMIT_CYCLES) {
-    double out[NV];
-    block_sum<NV>(v, out);  // ends with __syncthreads()
+    DF in[NV], out[NV];
+#pragma unroll
+    for (int j = 0; j < NV; ++j) in[j] = DF{v[j], 0.f};
+    block_sum_df<NV>(in, out);  // ends with __syncthreads()
     __shared__ int s_ok;
-    double* slot = partials + (size_t)(phase & 1u) * nb * NPART;
+    float2* slot = reinterpret_cast<float2*>(partials) + (size_t)(phase & 1u) * nb * NPART;
     GTRACE(bid == 0 && threadIdx.x == 0, 20);
     if (threadIdx.x == 0) {
 #pragma unroll
-        for (int j = 0; j < NV; ++j) slot[(size_t)bid * NPART + j] = out[j];
+        for (int j = 0; j < NV; ++j) slot[(size_t)bid * NPART + j] = make_float2(out[j].hi, out[j].lo);
         red_release_add(&gs->count, 1u);  // orders this block's phase writes before the arrival
         const unsigned int target = (phase + 1u) * nb;
         int ok = 1;
@@ -101,16 +127,24 @@ __device__ __forceinline__ bool grid_reduce(const double (&v)[NV], double* parti
     __syncthreads();
     if (!s_ok) return false;
     // every block: the blocks' partials in a fixed order, then the update
-    double acc[NV];
+    DF acc[NV];
 #pragma unroll
-    for (int j = 0; j < NV; ++j) acc[j] = 0.0;
+    for (int j = 0; j < NV; ++j) acc[j] = DF{0.f, 0.f};
     for (unsigned int b = threadIdx.x; b < nb; b += NTHREADS) {
 #pragma unroll
-        for (int j = 0; j < NV; ++j) acc[j] += __ldcg(slot + (size_t)b * NPART + j);
+        for (int j = 0; j < NV; ++j) {
+            const float2 p = __ldcg(slot + (size_t)b * NPART + j);
+            acc[j] = df_add(acc[j], DF{p.x, p.y});
+        }
     }
-    double tot[NV];
-    block_sum<NV>(acc, tot);
-    if (threadIdx.x == 0) finish(tot);
+    DF tot[NV];
+    block_sum_df<NV>(acc, tot);
+    if (threadIdx.x == 0) {
+        double t[NV];
+#pragma unroll
+        for (int j = 0; j < NV; ++j) t[j] = df_to_double(tot[j]);
+        finish(t);
+    }
     GTRACE(bid == 0 && threadIdx.x == 0, 22);
     __syncthreads();
     return true;
@@ -145,7 +179,7 @@ constexpr int CLUSTER_MAX = 16;
 // Per-block shared state of a level solve: the block's replica of the
 // solve's scalars (both modes) and, in cluster mode, the exchange slots.
 struct ClusterState {
-    double slots[2][CLUSTER_MAX][NPART];  // [phase parity][source rank][value]
+    double slots[2][CLUSTER_MAX][NPART];  // [phase parity][source rank][value], double-float pairs
     unsigned long long mbar;
     int err;
     Scalars sc;                           // this block's replica of the solve's scalars
@@ -202,29 +236,29 @@ __device__ __forceinline__ void cluster_end(ClusterState& cs, Scalars* gsc, unsi
 }
 
 template <int NV, class Finish>
-__device__ __forceinline__ bool cluster_reduce(const double (&v)[NV], ClusterState& cs,
+__device__ __forceinline__ bool cluster_reduce(const float (&v)[NV], ClusterState& cs,
                                                unsigned int phase, unsigned int nb,
                                                unsigned int rank, GroupSync* gs, Finish&& finish,
                                                long long limit = GROUP_WAIT_LIMIT_CYCLES) {
-    double out[NV];
+    DF in[NV], out[NV];
+#pragma unroll
+    for (int j = 0; j < NV; ++j) in[j] = DF{v[j], 0.f};
     GTRACE(rank == 0 && threadIdx.x == 0, 40);
-    block_sum<NV>(v, out);  // warp 0 holds the sums; ends with __syncthreads()
+    block_sum_df<NV>(in, out);  // warp 0 holds lane 0's sums; ends with __syncthreads()
     GTRACE(rank == 0 && threadIdx.x == 0, 41);
     const unsigned int par = phase & 1u;
-    if (threadIdx.x < 32) {
+    if (threadIdx.x < nb) {  // lane t delivers this block's sums to block t
+        const unsigned int t = threadIdx.x;
 #pragma unroll
-        for (int j = 0; j < NV; ++j) out[j] = __shfl_sync(0xffffffffu, out[j], 0);  // lane 0's bits
-        if (threadIdx.x < nb) {  // lane t delivers this block's sums to block t
-            const unsigned int t = threadIdx.x;
-#pragma unroll
-            for (int j = 0; j < NV; ++j) {
-                const unsigned int dst = cluster_map(smem_u32(&cs.slots[par][rank][j]), t);
-                asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(dst), "d"(out[j]) : "memory");
-            }
-            const unsigned int bar = cluster_map(smem_u32(&cs.mbar), t);
-            asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(bar)
+        for (int j = 0; j < NV; ++j) {
+            const unsigned int dst = cluster_map(smem_u32(&cs.slots[par][rank][j]), t);
+            asm volatile("st.shared::cluster.v2.f32 [%0], {%1, %2};" ::"r"(dst), "f"(out[j].hi),
+                         "f"(out[j].lo)
                          : "memory");
         }
+        const unsigned int bar = cluster_map(smem_u32(&cs.mbar), t);
+        asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(bar)
+                     : "memory");
     }
     if (threadIdx.x == 0) {
         const unsigned int bar = smem_u32(&cs.mbar);
@@ -238,13 +272,19 @@ __device__ __forceinline__ bool cluster_reduce(const double (&v)[NV], ClusterSta
         }
         GTRACE(rank == 0, 42);
         if (!cs.err) {
-            double tot[NV];
+            DF acc[NV];
 #pragma unroll
-            for (int j = 0; j < NV; ++j) tot[j] = 0.0;
+            for (int j = 0; j < NV; ++j) acc[j] = DF{0.f, 0.f};
             for (unsigned int q = 0; q < nb; ++q) {
 #pragma unroll
-                for (int j = 0; j < NV; ++j) tot[j] += cs.slots[par][q][j];
+                for (int j = 0; j < NV; ++j) {
+                    const float2 p = *reinterpret_cast<const float2*>(&cs.slots[par][q][j]);
+                    acc[j] = df_add(acc[j], DF{p.x, p.y});
+                }
             }
+            double tot[NV];
+#pragma unroll
+            for (int j = 0; j < NV; ++j) tot[j] = df_to_double(acc[j]);
             finish(tot);
         }
         GTRACE(rank == 0, 43);
@@ -262,7 +302,7 @@ struct LevelSync {
     bool cluster;
     unsigned int phase;
     template <int NV, class Finish>
-    __device__ __forceinline__ bool reduce(const double (&v)[NV], Finish&& finish) {
+    __device__ __forceinline__ bool reduce(const float (&v)[NV], Finish&& finish) {
         if (cluster) return cluster_reduce<NV>(v, *cs, phase++, nb, bid, gs, finish);
         return grid_reduce<NV>(v, partials, gs, nb, bid, phase++, finish);
     }
