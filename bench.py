@@ -303,9 +303,9 @@ def main():
     ap.add_argument("--no-serving", action="store_true")
     args = ap.parse_args()
 
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    from paper_2311_03010_gb300 import replicas
+
+    rank, world, local = replicas.env()
 
     if args.impl == "reference":
         run_reference(args, rank, world)
@@ -316,14 +316,10 @@ def main():
     from paper_2311_03010_gb300 import build_lib, eecmg
 
     torch.cuda.set_device(local)
-    if world > 1:
-        import torch.distributed as dist
-
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    replicas.init(world, "nccl", torch.device("cuda", local))
     if rank == 0 or not os.path.exists(build_lib.LIB):
         build_lib.build()
-    if world > 1:
-        dist.barrier()
+    replicas.barrier(world)
     eecmg.load()
 
     name = args.workload
@@ -345,8 +341,7 @@ def main():
         eecmg.eecmg_restore_batched([p.handle for p in plans], gs, us, stream)
 
     def barrier():
-        if world > 1:
-            dist.barrier()
+        replicas.barrier(world)
         torch.cuda.synchronize()
 
     for _ in range(max(3, args.warmup)):
@@ -367,13 +362,9 @@ def main():
     barrier()
     clk = clocks.stop()
     step_ms = [a.elapsed_time(b) for (a, b) in ev]
-    tot_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([tot_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot_ms = float(t.item())
+    tot_ms = replicas.max_over_ranks(sum(step_ms), world, "cuda")
     px_step = sum(g.numel() for g in gs)
-    value = px_step * args.steps * world / (tot_ms / 1e3) / 1e6
+    value = replicas.aggregate_rate(px_step, args.steps, world, tot_ms) / 1e6
 
     # the plain per-image loop on the same plans (for the batched workload)
     loop_value = None
@@ -420,8 +411,8 @@ def main():
         for p, a, b in zip(plans, gh, uh):
             eecmg.eecmg_restore_host(p.handle, a.data_ptr(), b.data_ptr(), stream)
     barrier()
-    e2e_s = time.perf_counter() - t0
-    e2e_val = px_step * e2e_steps * world / e2e_s / 1e6
+    e2e_s = replicas.max_over_ranks(time.perf_counter() - t0, world, "cuda")
+    e2e_val = replicas.aggregate_rate(px_step, e2e_steps, world, e2e_s * 1e3) / 1e6
 
     # profiled eager replay of the same restorations (one plan at a time):
     # per-kernel-class event times
@@ -485,8 +476,7 @@ def main():
         print(json.dumps(out), flush=True)
     for p in plans:
         p.close()
-    if world > 1:
-        dist.destroy_process_group()
+    replicas.finalize(world)
 
 
 if __name__ == "__main__":
