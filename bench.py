@@ -301,6 +301,7 @@ def main():
     ap.add_argument("--storage", default="fp32", choices=["fp32", "bf16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
     args = ap.parse_args()
 
     from paper_2311_03010_gb300 import replicas
@@ -325,15 +326,27 @@ def main():
     name = args.workload
     probs = make_problems(name)
     stream = torch.cuda.current_stream()
-    plans = []
-    for (_, psf, L, g) in probs:
-        h, w = g.shape
+    gs = [torch.from_numpy(g).cuda() for (_, _, _, g) in probs]
+
+    def plan_opts(psf):
         smo = args.smoother
         if smo == "mr2" and not np.allclose(psf, psf[::-1, ::-1], rtol=0, atol=1e-15):
             smo = "cgls"
-        plans.append(eecmg.Plan(w, h, L, psf, smoother=smo, precise_conv=args.precise_conv,
-                                storage=args.storage))
-    gs = [torch.from_numpy(g).cuda() for (_, _, _, g) in probs]
+        return dict(smoother=smo, precise_conv=args.precise_conv, storage=args.storage)
+
+    # partition of the level solves: autotuned on this workload (before any plan
+    # owns a workspace), untimed
+    tuning_src = "defaults"
+    if not args.no_autotune:
+        descs = [eecmg.Plan(g.shape[1], g.shape[0], L, psf, workspace=0, **plan_opts(psf))
+                 for (_, psf, L, g) in probs]
+        t0 = time.perf_counter()
+        eecmg.eecmg_autotune(descs, gs, reps=5, stream=stream)
+        tuning_src = f"autotuned on this workload in {time.perf_counter() - t0:.1f} s"
+        for d in descs:
+            d.close()
+    tuning = dict(eecmg.eecmg_get_tuning(), source=tuning_src)
+    plans = [eecmg.Plan(g.shape[1], g.shape[0], L, psf, **plan_opts(psf)) for (_, psf, L, g) in probs]
     us = [torch.empty_like(g) for g in gs]
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
@@ -452,9 +465,9 @@ def main():
             "warmup": args.warmup, "ms_per_step": tot_ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": name, "images_per_step": len(gs), "levels": L,
+            "config": {"workload": name, "images_per_step": len(gs), "levels": probs[0][2],
                        "smoother": args.smoother, "precise_conv": args.precise_conv,
-                       "storage": args.storage,
+                       "storage": args.storage, "tile": "32x64 + halo", "partition": tuning,
                        "parallelism": f"replicas x{world}", "l2": "flushed between steps"},
             "e2e": {"value": e2e_val, "unit": "Mpixel/s",
                     "h2d_bytes_per_step": int(sum(g.numel() * 4 for g in gs)),

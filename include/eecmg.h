@@ -287,6 +287,50 @@ eecmg_status eecmg_residual_noalloc(int width, int height, const double *psf, in
                                     int psf_h, const float *g, const float *u, float *r,
                                     double *norms, cudaStream_t stream);
 
+/* ---- partition of the level solves and its autotuner ------------------ */
+
+/*
+ * How the persistent level solves are split over the GPU (system design, no
+ * counterpart in the paper).  A level of at most cluster_max_px pixels runs
+ * on one thread-block cluster of up to 16 blocks that exchange their sums
+ * through distributed shared memory; larger levels run as a cooperative grid
+ * of max(32x64 tiles, pixels / px_per_block) blocks, at most blocks_per_sm
+ * per SM.  Process-wide.  Initial values: the GB300 optimum of measured
+ * sweeps (cluster_max_px 16384, px_per_block 2048, blocks_per_sm 2),
+ * overridable by the environment variables EECMG_CLUSTER_MAX_PX,
+ * EECMG_PX_PER_BLOCK, EECMG_BLOCKS_PER_SM read at first use.
+ */
+typedef struct {
+    long long cluster_max_px; /* >= 0; 0 = never cluster mode                 */
+    int px_per_block;         /* 1024 .. 4194304                              */
+    int blocks_per_sm;        /* 1 .. 3                                       */
+} eecmg_tuning;
+
+eecmg_status eecmg_get_tuning(eecmg_tuning *out);
+
+/*
+ * Sets the partition.  Every solve of a process must be partitioned the same
+ * way (that is what keeps batched and served results bitwise equal to a
+ * plan's own restoration), so this returns EECMG_ERR_BUSY while any plan
+ * owning a workspace or any server exists.  INVALID_ARG outside the ranges.
+ */
+eecmg_status eecmg_set_tuning(const eecmg_tuning *t);
+
+/*
+ * Autotuner: times one batched restoration (eecmg_restore_batched) of the n
+ * plans on the inputs g[i] (device, plan i's size) under candidate
+ * partitions -- a coordinate search over cluster_max_px in {0, 4096, 16384,
+ * 65536, 262144}, then px_per_block in {1024, 2048, 4096}, then
+ * blocks_per_sm in {1, 2, 3}, from the current setting -- with `reps` timed
+ * runs each (CUDA events on `stream`, after two warm-up runs), and keeps the
+ * fastest (also written to *best if non-NULL).  The plans are descriptions:
+ * the tuner restores private copies with their own workspaces and frees
+ * them.  Needs the same conditions as eecmg_set_tuning (BUSY otherwise: pass
+ * plans created with workspace = 0).  Synchronises the stream.
+ */
+eecmg_status eecmg_autotune(const eecmg_plan_t *plans, const float *const *g, int n, int reps,
+                            cudaStream_t stream, eecmg_tuning *best);
+
 /*
  * Diagnostic of the failure path (no counterpart in the paper).  Every wait
  * inside a level solve (grid barrier poll, cluster mbarrier wait) gives up

@@ -1,5 +1,6 @@
 // level_solve.cu -- dispatch of the persistent level solve (kernels in
 // level_solve_impl.cuh, instantiated in the ls_*.cu translation units).
+#include <atomic>
 #include <cstdlib>
 
 #include "level_solve_impl.cuh"
@@ -49,58 +50,91 @@ int cluster_limit() {
     return lim;
 }
 
-// Levels of at most this many pixels run in cluster mode (EECMG_CLUSTER_MAX_PX
-// overrides; 0 turns cluster mode off).  Measured on GB300: 128^2 and below
-// gain from the in-GPC exchange; from 256^2 up a 16-SM cluster is
-// throughput-bound and the grid form is faster.
-size_t cluster_max_px() {
-    static long long v = -1;
-    if (v < 0) {
-        const char* e = std::getenv("EECMG_CLUSTER_MAX_PX");
-        v = e ? std::atoll(e) : 16384;
-        if (v < 0) v = 0;
-    }
-    return (size_t)v;
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Partition parameters (eecmg_tuning).  Process-wide; the C ABI changes them
+// only while no plan with a workspace and no server exists, so every solve
+// of a process is partitioned the same way alone, batched or served.
+// Initial values: the GB300 optimum measured by sweeps, overridable through
+// EECMG_PX_PER_BLOCK, EECMG_CLUSTER_MAX_PX and EECMG_BLOCKS_PER_SM.
+// ---------------------------------------------------------------------------
+
+namespace {
+
+std::atomic<int> g_px_per_block{0}, g_blocks_per_sm{0};
+std::atomic<long long> g_cluster_max_px{-1};
+
+void tuning_init() {
+    if (g_px_per_block.load() > 0) return;
+    const char* a = std::getenv("EECMG_PX_PER_BLOCK");
+    const char* b = std::getenv("EECMG_CLUSTER_MAX_PX");
+    const char* c = std::getenv("EECMG_BLOCKS_PER_SM");
+    Tuning t;
+    if (a) t.px_per_block = std::atoi(a);
+    if (b) t.cluster_max_px = std::atoll(b);
+    if (c) t.blocks_per_sm = std::atoi(c);
+    set_tuning_raw(t);
 }
 
 }  // namespace
 
-// Blocks of a level solve: one per 32 x 64 tile (2048 pixels; the larger of
-// the tile count and pixels / EECMG_PX_PER_BLOCK when that is set), at most
-// two per SM (EECMG_BLOCKS_PER_SM, 1..3, overrides; the MR-II solvers fit two
-// per SM, CGLS three; a solve never exceeds its instantiation's capacity).  Measured on GB300: one block per tile beats one per 1024
-// pixels by 10-25 % on the 512^2 and batched cascades (cheaper barriers, no
-// idle blocks in the convolution phases).  The count depends only on the level's size, so a solve is
-// partitioned (and its reductions rounded) the same way alone or in a batch.
+bool tuning_valid(const Tuning& t) {
+    return t.px_per_block >= 1024 && t.px_per_block <= (1 << 22) && t.cluster_max_px >= 0 &&
+           t.blocks_per_sm >= 1 && t.blocks_per_sm <= 3;
+}
+
+void set_tuning_raw(const Tuning& t0) {
+    Tuning t = t0;
+    // the plan sizes its reduction partials for at least 1024 pixels per block
+    if (t.px_per_block < 1024) t.px_per_block = 1024;
+    if (t.cluster_max_px < 0) t.cluster_max_px = 0;
+    t.blocks_per_sm = t.blocks_per_sm < 1 ? 1 : (t.blocks_per_sm > 3 ? 3 : t.blocks_per_sm);
+    g_cluster_max_px.store(t.cluster_max_px);
+    g_blocks_per_sm.store(t.blocks_per_sm);
+    g_px_per_block.store(t.px_per_block);
+}
+
+Tuning get_tuning() {
+    tuning_init();
+    Tuning t;
+    t.px_per_block = g_px_per_block.load();
+    t.cluster_max_px = g_cluster_max_px.load();
+    t.blocks_per_sm = g_blocks_per_sm.load();
+    return t;
+}
+
+// Blocks of a grid-mode level solve: the larger of the 32 x 64 tile count and
+// pixels / px_per_block, at most blocks_per_sm per SM (the MR-II solvers fit
+// two per SM, CGLS three; a solve never exceeds its instantiation's
+// capacity).  Measured on GB300: one block per tile (px_per_block 2048) beats
+// one per 1024 pixels by 10-25 % on the 512^2 and batched cascades (cheaper
+// barriers, no idle blocks in the convolution phases).
 int level_want_blocks(int h, int w) {
-    static int cap = 0;
-    if (cap == 0) {
-        int dev = 0, sms = 0;
+    static int sms = 0;
+    if (sms == 0) {
+        int dev = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        const char* e = std::getenv("EECMG_BLOCKS_PER_SM");  // tuning override
-        int per = e ? std::atoi(e) : 2;
-        per = per < 1 ? 1 : (per > 3 ? 3 : per);
-        cap = per * (sms > 0 ? sms : 1);
+        if (sms < 1) sms = 1;
     }
-    static size_t px_per_block = 0;
-    if (px_per_block == 0) {
-        const char* e = std::getenv("EECMG_PX_PER_BLOCK");  // tuning override
-        const long long v = e ? std::atoll(e) : 2048;
-        px_per_block = v < 1024 ? 1024 : (size_t)v;  // the plan sizes partials for >= 1024
-    }
+    const Tuning t = get_tuning();
+    const int cap = t.blocks_per_sm * sms;
     const size_t n = (size_t)h * w;
     const int tiles = (int)conv_blocks(h, w);
-    const int elem = (int)((n + px_per_block - 1) / px_per_block);
+    const int elem = (int)((n + (size_t)t.px_per_block - 1) / (size_t)t.px_per_block);
     const int want = tiles > elem ? tiles : elem;
     return want < cap ? want : cap;
 }
 
+// Levels of at most cluster_max_px pixels run in cluster mode (0: never).
+// Measured on GB300: 128^2 and below gain from the in-GPC exchange; from
+// 256^2 up a 16-SM cluster is throughput-bound and the grid form is faster.
 LevelShape level_shape(int h, int w) {
     LevelShape sh;
     const int want = level_want_blocks(h, w);
     const size_t n = (size_t)h * w;
-    const int lim = n <= cluster_max_px() ? cluster_limit() : 0;
+    const int lim = n <= (size_t)get_tuning().cluster_max_px ? cluster_limit() : 0;
     if (lim >= 1) {
         sh.cluster = want < lim ? want : lim;
         sh.blocks = sh.cluster;

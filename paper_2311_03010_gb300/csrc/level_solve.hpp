@@ -51,6 +51,16 @@ struct LevelShape {
 };
 LevelShape level_shape(int h, int w);
 
+// Partition parameters of the level solves (process-wide).
+struct Tuning {
+    int px_per_block = 2048;           // grid mode: at least one block per this many pixels (>= 1024)
+    long long cluster_max_px = 16384;  // levels with at most this many pixels run in cluster mode
+    int blocks_per_sm = 2;             // grid mode: at most this many blocks per SM (1..3)
+};
+Tuning get_tuning();
+void set_tuning_raw(const Tuning& t);  // no liveness check (see eecmg_set_tuning)
+bool tuning_valid(const Tuning& t);
+
 // Launches a device job table: one cooperative grid of total_blocks blocks
 // (cluster == 0; the caller sized the jobs' block ranges to fit
 // co-residency, see level_capacity), or clusters of `cluster` blocks, one per

@@ -6,6 +6,7 @@
 // restoration enqueues Algorithm 2 on a stream without any host round trip
 // (all Krylov scalars are decided on the device) and is captured once as a
 // CUDA graph, then replayed.
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -479,6 +480,68 @@ eecmg_status run_cascade(eecmg_plan_s* P, cudaStream_t s) {
 
 }  // namespace eecmg
 
+namespace eecmg {
+
+std::atomic<int> g_live_owners{0};
+
+// Allocates, zeroes and fills the plan's device workspace (layout already
+// computed) and its capture stream.  On failure nothing is left allocated.
+eecmg_status plan_allocate(eecmg_plan_s* P, const char* who) {
+    const size_t off = P->layout.bytes;
+    cudaError_t e = cudaMalloc((void**)&P->ws, off);
+    if (e != cudaSuccess) {
+        P->ws = nullptr;
+        cudaGetLastError();
+        return set_error(EECMG_ERR_OOM, std::string(who) + ": workspace allocation failed: " +
+                                            cudaGetErrorString(e));
+    }
+    bind_workspace(P, P->ws);
+    e = cudaMemset(P->ws, 0, off);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(P->dtaps, P->htaps.data(), sizeof(Taps) * 2 * P->L, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&P->cap_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        cudaFree(P->ws);
+        P->ws = nullptr;
+        if (P->cap_stream) cudaStreamDestroy(P->cap_stream);
+        P->cap_stream = nullptr;
+        return set_error(EECMG_ERR_CUDA, std::string(who) + ": " + cudaGetErrorString(e));
+    }
+    P->owns_ws = true;
+    g_live_owners.fetch_add(1);
+    return EECMG_OK;
+}
+
+// A new plan with D's description and its own workspace.
+eecmg_status plan_materialize(const eecmg_plan_s* D, eecmg_plan_s** out) {
+    *out = nullptr;
+    auto* P = new (std::nothrow) eecmg_plan_s();
+    if (!P) return set_error(EECMG_ERR_OOM, "host allocation failed");
+    P->W = D->W;
+    P->H = D->H;
+    P->L = D->L;
+    P->tau = D->tau;
+    P->kpm = D->kpm;
+    P->conv_tol2 = D->conv_tol2;
+    P->opt = D->opt;
+    P->opt.workspace = 1;
+    P->device = D->device;
+    P->lv = D->lv;
+    P->htaps = D->htaps;
+    P->layout = D->layout;
+    P->ws_bytes = D->ws_bytes;
+    P->max_blocks = D->max_blocks;
+    eecmg_status st = plan_allocate(P, "plan_materialize");
+    if (st != EECMG_OK) {
+        delete P;
+        return st;
+    }
+    *out = P;
+    return EECMG_OK;
+}
+
+}  // namespace eecmg
+
 // ---------------------------------------------------------------------------
 // C ABI
 // ---------------------------------------------------------------------------
@@ -636,30 +699,13 @@ eecmg_status eecmg_plan(int width, int height, int levels, const double* psf, in
     P->ws_bytes = off;
     P->max_blocks = max_blocks;
     P->htaps = htaps;
-    if (!o.workspace) {  // a description only (serving requests)
-        *out = P;
-        return EECMG_OK;
+    if (o.workspace) {
+        eecmg_status st = plan_allocate(P, "eecmg_plan");
+        if (st != EECMG_OK) {
+            delete P;
+            return st;
+        }
     }
-    cudaError_t e = cudaMalloc((void**)&P->ws, off);
-    if (e != cudaSuccess) {
-        delete P;
-        cudaGetLastError();
-        return set_error(EECMG_ERR_OOM, std::string("eecmg_plan: workspace allocation failed: ") + cudaGetErrorString(e));
-    }
-    P->owns_ws = true;
-    bind_workspace(P, P->ws);
-    auto cleanup = [&](cudaError_t err, const char* what) {
-        cudaFree(P->ws);
-        if (P->cap_stream) cudaStreamDestroy(P->cap_stream);
-        delete P;
-        return set_error(EECMG_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(err));
-    };
-    e = cudaMemset(P->ws, 0, off);
-    if (e != cudaSuccess) return cleanup(e, "eecmg_plan: memset");
-    e = cudaMemcpy(P->dtaps, htaps.data(), sizeof(Taps) * 2 * levels, cudaMemcpyHostToDevice);
-    if (e != cudaSuccess) return cleanup(e, "eecmg_plan: taps upload");
-    e = cudaStreamCreateWithFlags(&P->cap_stream, cudaStreamNonBlocking);
-    if (e != cudaSuccess) return cleanup(e, "eecmg_plan: stream");
     *out = P;
     return EECMG_OK;
 }
@@ -672,7 +718,10 @@ eecmg_status eecmg_plan_destroy(eecmg_plan_t P) {
     if (P->cap_stream) cudaStreamDestroy(P->cap_stream);
     prof_flush(P);
     for (cudaEvent_t e : P->prof.free_events) cudaEventDestroy(e);
-    if (P->owns_ws) cudaFree(P->ws);
+    if (P->owns_ws) {
+        cudaFree(P->ws);
+        g_live_owners.fetch_sub(1);
+    }
     delete P;
     return EECMG_OK;
 }

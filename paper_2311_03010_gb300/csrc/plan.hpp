@@ -81,9 +81,16 @@ struct eecmg_plan_s {
     eecmg::Profiler prof;
 };
 
+#include <atomic>
+
 namespace eecmg {
 // Points the plan's level and solver buffers into ws (P->layout.bytes long).
 void bind_workspace(eecmg_plan_s* P, char* ws);
+// Plans owning a workspace plus live servers: the partition parameters may
+// change only while this is zero.
+extern std::atomic<int> g_live_owners;
+eecmg_status plan_allocate(eecmg_plan_s* P, const char* who);
+eecmg_status plan_materialize(const eecmg_plan_s* D, eecmg_plan_s** out);
 eecmg_status solve_level_enqueue(eecmg_plan_s* P, int l, const float* g, float* u, int m,
                                  bool zero_start, cudaStream_t s);
 eecmg_status prolong_enqueue(eecmg_plan_s* P, int l, cudaStream_t s);

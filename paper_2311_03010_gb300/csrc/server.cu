@@ -449,6 +449,7 @@ eecmg_status eecmg_server_create(size_t mem_budget_bytes, int max_slots, eecmg_s
     } catch (...) {
         return fail(EECMG_ERR_OOM, "scheduler thread");
     }
+    g_live_owners.fetch_add(1);  // the partition parameters stay fixed while it exists
     *out = S;
     return EECMG_OK;
 }
@@ -521,6 +522,7 @@ eecmg_status eecmg_server_destroy(eecmg_server_t S) {
     S->cv.notify_all();
     if (S->th.joinable()) S->th.join();
     free_server(S);
+    g_live_owners.fetch_sub(1);
     return EECMG_OK;
 }
 

@@ -56,6 +56,11 @@ class eecmg_options(ctypes.Structure):
     ]
 
 
+class eecmg_tuning(ctypes.Structure):
+    _fields_ = [("cluster_max_px", ctypes.c_longlong), ("px_per_block", ctypes.c_int),
+                ("blocks_per_sm", ctypes.c_int)]
+
+
 class eecmg_kernel_stat(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 24), ("launches", ctypes.c_longlong),
                 ("ms", ctypes.c_double), ("bytes", ctypes.c_double)]
@@ -90,6 +95,10 @@ _SIGS = {
     "eecmg_level_solve": [_VP, _I, _VP, _VP, _I, _VP],
     "eecmg_residual_noalloc": [_I, _I, _PD, _I, _I, _VP, _VP, _VP, _VP, _VP],
     "eecmg_selftest_bounded_wait": [_I, _VP],
+    "eecmg_get_tuning": [ctypes.POINTER(eecmg_tuning)],
+    "eecmg_set_tuning": [ctypes.POINTER(eecmg_tuning)],
+    "eecmg_autotune": [ctypes.POINTER(_VP), ctypes.POINTER(_VP), _I, _I, _VP,
+                       ctypes.POINTER(eecmg_tuning)],
     "eecmg_server_create": [ctypes.c_size_t, _I, ctypes.POINTER(_VP)],
     "eecmg_server_submit": [_VP, _VP, _VP, _VP, ctypes.POINTER(ctypes.c_uint64)],
     "eecmg_server_poll": [_VP, ctypes.c_uint64, _PI, _PD],
@@ -286,6 +295,32 @@ def eecmg_residual_noalloc(width, height, psf, g, u, r, norms, stream=None):
     nptr = norms if isinstance(norms, int) else norms.data_ptr()
     _call("eecmg_residual_noalloc", int(width), int(height), psf.ctypes.data_as(_PD),
           psf.shape[1], psf.shape[0], _ptr(g), _ptr(u), _ptr(r), nptr, _stream(stream))
+
+
+def _tuning_dict(t):
+    return {"cluster_max_px": t.cluster_max_px, "px_per_block": t.px_per_block,
+            "blocks_per_sm": t.blocks_per_sm}
+
+
+def eecmg_get_tuning():
+    t = eecmg_tuning()
+    _call("eecmg_get_tuning", ctypes.byref(t))
+    return _tuning_dict(t)
+
+
+def eecmg_set_tuning(cluster_max_px, px_per_block, blocks_per_sm):
+    t = eecmg_tuning(int(cluster_max_px), int(px_per_block), int(blocks_per_sm))
+    _call("eecmg_set_tuning", ctypes.byref(t))
+
+
+def eecmg_autotune(plans, g, reps=10, stream=None):
+    """plans: description-only plan handles (or Plan objects); g: their device inputs."""
+    n = len(plans)
+    hp = (_VP * n)(*[p.handle if isinstance(p, Plan) else p for p in plans])
+    hg = (_VP * n)(*[_ptr(x) for x in g])
+    t = eecmg_tuning()
+    _call("eecmg_autotune", hp, hg, n, int(reps), _stream(stream), ctypes.byref(t))
+    return _tuning_dict(t)
 
 
 def eecmg_selftest_bounded_wait(cluster, stream=None):
