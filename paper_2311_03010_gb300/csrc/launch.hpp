@@ -76,6 +76,27 @@ cudaError_t launch_cg_step(float* u, const float* p, float* r, const float* q, s
 cudaError_t launch_cg_p(float* p, const float* sv, size_t n, Scalars* sc, cudaStream_t s);
 
 // Level operators.
+// Batched per-level operations (one launch per kind for many images).
+enum OpKind : int {
+    OP_RESTRICT = 0, OP_EXTRAPOLATE, OP_QUADRATIC, OP_LINEAR, OP_SMOOTH, OP_DENOISE, OP_ZERO, OP_COPY,
+    OP_KINDS
+};
+// One image's operation: output grid h x w (restriction: the coarse grid,
+// w1 = fine width; Pi: the level-(l-1) grid, inputs h1 x w1 and h2 x w2;
+// P / L: input h1 x w1; S: p0 = scale; D: p0 = tau, p1 = 1 / k^2).  bx and
+// block0 place its blocks within the launch (filled by the host).
+struct OpItem {
+    const float* a = nullptr;
+    const float* b = nullptr;
+    float* out = nullptr;
+    int h = 0, w = 0, h1 = 0, w1 = 0, h2 = 0, w2 = 0;
+    float p0 = 0.f, p1 = 0.f;
+    int bx = 0, block0 = 0;
+};
+int op_blocks(int h, int w);   // blocks covering an h x w output
+int op_blocks_x(int w);        // of which along x
+cudaError_t launch_ops_batch(int op, const OpItem* d_items, int n, int total_blocks, cudaStream_t s);
+
 cudaError_t launch_restrict(const float* fine, int hf, int wf, float* coarse, int hc, int wc,
                             cudaStream_t s);
 cudaError_t launch_extrapolate(const float* u1, int h1, int w1, const float* u2, int h2, int w2,

@@ -14,10 +14,13 @@ inline dim3 grid2(int h, int w) { return dim3((w + BX - 1) / BX, (h + BY - 1) / 
 }  // namespace
 
 // g_l(a, b) = g_{l+1}(2a, 2b): the paper's 1-based 2k - 1, per dimension.
+__device__ __forceinline__ void px_restrict(const float* __restrict__ fine, int wf,
+                                            float* __restrict__ coarse, int hc, int wc, int a, int b) {
+    if (a < hc && b < wc) coarse[(size_t)a * wc + b] = fine[(size_t)(2 * a) * wf + 2 * b];
+}
 __global__ void k_restrict(const float* __restrict__ fine, int wf, float* __restrict__ coarse,
                            int hc, int wc) {
-    const int b = blockIdx.x * BX + threadIdx.x, a = blockIdx.y * BY + threadIdx.y;
-    if (a < hc && b < wc) coarse[(size_t)a * wc + b] = fine[(size_t)(2 * a) * wf + 2 * b];
+    px_restrict(fine, wf, coarse, hc, wc, blockIdx.y * BY + threadIdx.y, blockIdx.x * BX + threadIdx.x);
 }
 
 // Pi on the level-(l-1) grid: u1 + (1/4) * (bilinear interpolant of
@@ -25,10 +28,9 @@ __global__ void k_restrict(const float* __restrict__ fine, int wf, float* __rest
 // at edge midpoints and u1 + (sum of four d)/16 at cell centres; indices
 // past the last level-(l-2) node are clamped to it.  The differences of the
 // two near-equal iterates are taken in FP64.
-__global__ void k_extrapolate(const float* __restrict__ u1, int h1, int w1,
-                              const float* __restrict__ u2, int h2, int w2,
-                              float* __restrict__ out) {
-    const int b = blockIdx.x * BX + threadIdx.x, a = blockIdx.y * BY + threadIdx.y;
+__device__ __forceinline__ void px_extrapolate(const float* __restrict__ u1, int h1, int w1,
+                                               const float* __restrict__ u2, int h2, int w2,
+                                               float* __restrict__ out, int a, int b) {
     if (a >= h1 || b >= w1) return;
     const int A0 = a >> 1, B0 = b >> 1;
     const int A1 = (a & 1) ? min(A0 + 1, h2 - 1) : A0;
@@ -39,6 +41,12 @@ __global__ void k_extrapolate(const float* __restrict__ u1, int h1, int w1,
     const double dsum = d(A0, B0) + d(A0, B1) + d(A1, B0) + d(A1, B1);
     out[(size_t)a * w1 + b] = (float)((double)u1[(size_t)a * w1 + b] + 0.0625 * dsum);
 }
+__global__ void k_extrapolate(const float* __restrict__ u1, int h1, int w1,
+                              const float* __restrict__ u2, int h2, int w2,
+                              float* __restrict__ out) {
+    px_extrapolate(u1, h1, w1, u2, h2, w2, out, blockIdx.y * BY + threadIdx.y,
+                   blockIdx.x * BX + threadIdx.x);
+}
 
 // Three-point Lagrange weights at offsets 0, 1/4, 1/2, 3/4 of a level-(l-2)
 // cell spanned by the level-(l-1) triplet (2A, 2A+1, 2A+2).
@@ -46,9 +54,8 @@ __constant__ float c_qw[4][3] = {
     {1.f, 0.f, 0.f}, {0.375f, 0.75f, -0.125f}, {0.f, 1.f, 0.f}, {-0.125f, 0.75f, 0.375f}};
 
 // P: tensor-product quadratic interpolation of ut (h1 x w1) onto h x w.
-__global__ void k_quadratic(const float* __restrict__ ut, int h1, int w1, float* __restrict__ out,
-                            int h, int w) {
-    const int x = blockIdx.x * BX + threadIdx.x, y = blockIdx.y * BY + threadIdx.y;
+__device__ __forceinline__ void px_quadratic(const float* __restrict__ ut, int h1, int w1,
+                                             float* __restrict__ out, int h, int w, int y, int x) {
     if (y >= h || x >= w) return;
     const int A = y >> 2, ty = y & 3, B = x >> 2, tx = x & 3;
     float s = 0.f;
@@ -65,13 +72,16 @@ __global__ void k_quadratic(const float* __restrict__ ut, int h1, int w1, float*
     }
     out[(size_t)y * w + x] = s;
 }
+__global__ void k_quadratic(const float* __restrict__ ut, int h1, int w1, float* __restrict__ out,
+                            int h, int w) {
+    px_quadratic(ut, h1, w1, out, h, w, blockIdx.y * BY + threadIdx.y, blockIdx.x * BX + threadIdx.x);
+}
 
 // L of Eq. 15 in 0-based indices: copy at (2a, 2b); horizontal / vertical
 // averages at (2a, 2b+1) / (2a+1, 2b); the diagonal pair (a, b), (a+1, b+1)
 // at (2a+1, 2b+1).  Indices past the last coarse node are clamped.
-__global__ void k_linear(const float* __restrict__ uc, int hc, int wc, float* __restrict__ out,
-                         int h, int w) {
-    const int x = blockIdx.x * BX + threadIdx.x, y = blockIdx.y * BY + threadIdx.y;
+__device__ __forceinline__ void px_linear(const float* __restrict__ uc, int hc, int wc,
+                                          float* __restrict__ out, int h, int w, int y, int x) {
     if (y >= h || x >= w) return;
     const int a = y >> 1, b = x >> 1;
     const int a1 = min(a + 1, hc - 1), b1 = min(b + 1, wc - 1);
@@ -83,6 +93,10 @@ __global__ void k_linear(const float* __restrict__ uc, int hc, int wc, float* __
     else v = 0.5f * (u00 + uc[(size_t)a1 * wc + b1]);
     out[(size_t)y * w + x] = v;
 }
+__global__ void k_linear(const float* __restrict__ uc, int hc, int wc, float* __restrict__ out,
+                         int h, int w) {
+    px_linear(uc, hc, wc, out, h, w, blockIdx.y * BY + threadIdx.y, blockIdx.x * BX + threadIdx.x);
+}
 
 // S: weighted least-squares plane fit over the in-image 3 x 3 neighbourhood
 // with weights exp(-(scale * (u_c - u_nb))^2) (Eqs. 18-19), output the fitted
@@ -90,9 +104,8 @@ __global__ void k_linear(const float* __restrict__ uc, int hc, int wc, float* __
 // of the offsets and of v = u_nb - u_c, the 2 x 2 moment matrix C and the
 // cross vector c, slope = C^+ c (eigenvalues below 1e-6 W dropped) and
 // a0 = u_c + vb - slope . (sb, tb).
-__global__ void k_smooth(const float* __restrict__ in, float* __restrict__ out, int h, int w,
-                         float scale) {
-    const int j = blockIdx.x * BX + threadIdx.x, i = blockIdx.y * BY + threadIdx.y;
+__device__ __forceinline__ void px_smooth(const float* __restrict__ in, float* __restrict__ out,
+                                          int h, int w, float scale, int i, int j) {
     if (i >= h || j >= w) return;
     const float uc = in[(size_t)i * w + j];
     float ws[9], ss[9], ts[9], vs[9];
@@ -164,6 +177,10 @@ __global__ void k_smooth(const float* __restrict__ in, float* __restrict__ out, 
     }
     out[(size_t)i * w + j] = uc + vb - (gs * sb + gt * tb);
 }
+__global__ void k_smooth(const float* __restrict__ in, float* __restrict__ out, int h, int w,
+                         float scale) {
+    px_smooth(in, out, h, w, scale, blockIdx.y * BY + threadIdx.y, blockIdx.x * BX + threadIdx.x);
+}
 
 // D: u + tau * sum over in-image 4-neighbours of (c_nb + c_c)/2 (u_nb - u_c),
 // c = 1 / (1 + |grad u|^2 / k^2) with central differences (an out-of-image
@@ -179,9 +196,8 @@ __device__ __forceinline__ float pm_c(const float* __restrict__ u, int h, int w,
     return 1.f / (1.f + (gx * gx + gy * gy) * inv_k2);
 }
 
-__global__ void k_denoise(const float* __restrict__ in, float* __restrict__ out, int h, int w,
-                          float tau, float inv_k2) {
-    const int j = blockIdx.x * BX + threadIdx.x, i = blockIdx.y * BY + threadIdx.y;
+__device__ __forceinline__ void px_denoise(const float* __restrict__ in, float* __restrict__ out,
+                                           int h, int w, float tau, float inv_k2, int i, int j) {
     if (i >= h || j >= w) return;
     const float uc = in[(size_t)i * w + j];
     const float cc = pm_c(in, h, w, i, j, inv_k2);
@@ -191,6 +207,37 @@ __global__ void k_denoise(const float* __restrict__ in, float* __restrict__ out,
     if (j + 1 < w) f += 0.5f * (pm_c(in, h, w, i, j + 1, inv_k2) + cc) * (in[(size_t)i * w + j + 1] - uc);
     if (j > 0) f += 0.5f * (pm_c(in, h, w, i, j - 1, inv_k2) + cc) * (in[(size_t)i * w + j - 1] - uc);
     out[(size_t)i * w + j] = fmaf(tau, f, uc);
+}
+__global__ void k_denoise(const float* __restrict__ in, float* __restrict__ out, int h, int w,
+                          float tau, float inv_k2) {
+    px_denoise(in, out, h, w, tau, inv_k2, blockIdx.y * BY + threadIdx.y, blockIdx.x * BX + threadIdx.x);
+}
+
+// Many operations of one kind in one launch (the server's ticks): block b
+// serves the item whose block range holds b (binary search over block0),
+// with the same per-pixel code as the single launches above.
+template <int OP>
+__global__ void __launch_bounds__(BX* BY) k_ops_batch(const OpItem* __restrict__ items, int n) {
+    const int blk = (int)blockIdx.x;
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (items[mid].block0 <= blk) lo = mid;
+        else hi = mid - 1;
+    }
+    const OpItem& it = items[lo];
+    const int local = blk - it.block0;
+    const int by = local / it.bx, bx = local - by * it.bx;
+    const int x = bx * BX + threadIdx.x, y = by * BY + threadIdx.y;
+    if constexpr (OP == OP_RESTRICT) px_restrict(it.a, it.w1, it.out, it.h, it.w, y, x);
+    if constexpr (OP == OP_EXTRAPOLATE) px_extrapolate(it.a, it.h1, it.w1, it.b, it.h2, it.w2, it.out, y, x);
+    if constexpr (OP == OP_QUADRATIC) px_quadratic(it.a, it.h1, it.w1, it.out, it.h, it.w, y, x);
+    if constexpr (OP == OP_LINEAR) px_linear(it.a, it.h1, it.w1, it.out, it.h, it.w, y, x);
+    if constexpr (OP == OP_SMOOTH) px_smooth(it.a, it.out, it.h, it.w, it.p0, y, x);
+    if constexpr (OP == OP_DENOISE) px_denoise(it.a, it.out, it.h, it.w, it.p0, it.p1, y, x);
+    if constexpr (OP == OP_ZERO || OP == OP_COPY) {
+        if (y < it.h && x < it.w) it.out[(size_t)y * it.w + x] = OP == OP_ZERO ? 0.f : it.a[(size_t)y * it.w + x];
+    }
 }
 
 cudaError_t launch_restrict(const float* fine, int hf, int wf, float* coarse, int hc, int wc,
@@ -232,6 +279,31 @@ cudaError_t launch_denoise(const float* in, float* out, int h, int w, float tau,
                            cudaStream_t s) {
     if (h <= 0 || w <= 0) return cudaSuccess;
     k_denoise<<<grid2(h, w), dim3(BX, BY), 0, s>>>(in, out, h, w, tau, 1.f / (kpm * kpm));
+    return cudaGetLastError();
+}
+
+int op_blocks(int h, int w) {
+    if (h <= 0 || w <= 0) return 0;
+    const dim3 g = grid2(h, w);
+    return (int)(g.x * g.y);
+}
+
+int op_blocks_x(int w) { return (w + BX - 1) / BX; }
+
+cudaError_t launch_ops_batch(int op, const OpItem* d_items, int n, int total_blocks, cudaStream_t s) {
+    if (n <= 0 || total_blocks <= 0) return cudaSuccess;
+    const dim3 g((unsigned int)total_blocks), b(BX, BY);
+    switch (op) {
+        case OP_RESTRICT: k_ops_batch<OP_RESTRICT><<<g, b, 0, s>>>(d_items, n); break;
+        case OP_EXTRAPOLATE: k_ops_batch<OP_EXTRAPOLATE><<<g, b, 0, s>>>(d_items, n); break;
+        case OP_QUADRATIC: k_ops_batch<OP_QUADRATIC><<<g, b, 0, s>>>(d_items, n); break;
+        case OP_LINEAR: k_ops_batch<OP_LINEAR><<<g, b, 0, s>>>(d_items, n); break;
+        case OP_SMOOTH: k_ops_batch<OP_SMOOTH><<<g, b, 0, s>>>(d_items, n); break;
+        case OP_DENOISE: k_ops_batch<OP_DENOISE><<<g, b, 0, s>>>(d_items, n); break;
+        case OP_ZERO: k_ops_batch<OP_ZERO><<<g, b, 0, s>>>(d_items, n); break;
+        case OP_COPY: k_ops_batch<OP_COPY><<<g, b, 0, s>>>(d_items, n); break;
+        default: return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 

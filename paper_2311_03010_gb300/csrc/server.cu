@@ -178,74 +178,252 @@ void bind_slot(Request* r, char* ws) {
 
 char* stat_area(eecmg_server_s* S, int sidx) { return S->h_stat + (size_t)sidx * S->stat_stride; }
 
+// Operations of one kind launched together (one launch per group).
+struct OpGroup {
+    int op;
+    std::vector<OpItem> items;
+};
+
+// Appends an operation to group gi (a group holds one kind).
+void add_op(std::vector<OpGroup>& groups, size_t gi, int op, OpItem it) {
+    if (groups.size() <= gi) groups.resize(gi + 1, OpGroup{-1, {}});
+    groups[gi].op = op;
+    it.bx = op_blocks_x(it.w);
+    groups[gi].items.push_back(it);
+}
+
+// Grows the tick ring to hold `bytes` per slot (waits for the ticks in flight).
+eecmg_status ensure_ring(eecmg_server_s* S, size_t bytes) {
+    if (bytes <= S->ring_bytes) return EECMG_OK;
+    size_t nb = S->ring_bytes;
+    while (nb < bytes) nb *= 2;
+    SCK(cudaStreamSynchronize(S->stream));
+    char *d = nullptr, *h = nullptr;
+    SCK(cudaMalloc((void**)&d, RING * nb));
+    if (cudaMallocHost((void**)&h, RING * nb) != cudaSuccess) {
+        cudaFree(d);
+        return set_error(EECMG_ERR_OOM, "eecmg_server: tick ring");
+    }
+    cudaFree(S->d_ring);
+    cudaFreeHost(S->h_ring);
+    S->d_ring = d;
+    S->h_ring = h;
+    S->ring_bytes = nb;
+    return EECMG_OK;
+}
+
 // Enqueues tick k's work on the server stream; `finishing` receives the
-// requests whose finest level ran in it.
+// requests whose finest level ran in it.  Every per-level operation of the
+// tick is one batched launch per kind over all requests (k_ops_batch), then
+// the level solves are the persistent launches of plan_waves.
 eecmg_status enqueue_tick(eecmg_server_s* S, const std::vector<Request*>& admitted, int k,
                           std::vector<Request*>& finishing) {
     cudaStream_t s = S->stream;
+    // launch groups in execution order; a group holds one kind
+    constexpr int G_IN = 0, G_RESTRICT0 = 1;           // + depth (at most MAX_LEVELS - 1)
+    constexpr int G_ZERO = G_RESTRICT0 + MAX_LEVELS;   // zero starts and new scalars
+    constexpr int G_EXTRA = G_ZERO + 1, G_QUAD = G_EXTRA + 1, G_LIN = G_QUAD + 1;
+    constexpr int G_SMOOTH = G_LIN + 1, G_STEP0 = G_SMOOTH + 1;  // + diffusion step (D or copy)
+    std::vector<OpGroup> pre, post;  // before / after the level solves
+    pre.resize(G_STEP0, OpGroup{-1, {}});
+    pre[G_IN].op = OP_COPY;
+    for (int d = 0; d < MAX_LEVELS; ++d) pre[G_RESTRICT0 + d].op = OP_RESTRICT;
+    pre[G_ZERO].op = OP_ZERO;
+    pre[G_EXTRA].op = OP_EXTRAPOLATE;
+    pre[G_QUAD].op = OP_QUADRATIC;
+    pre[G_LIN].op = OP_LINEAR;
+    pre[G_SMOOTH].op = OP_SMOOTH;
     for (Request* r : admitted) {
         eecmg_plan_s& P = r->slot;
         const PlanLayout& Y = P.layout;
-        // scalars, barrier state and partials start at zero, as in a new plan
-        SCK(cudaMemsetAsync(P.ws + Y.sc_off, 0, Y.bytes - Y.sc_off, s));
         SCK(cudaMemcpyAsync(P.dtaps, r->tmpl->htaps.data(), sizeof(Taps) * 2 * P.L,
                             cudaMemcpyHostToDevice, s));
         LevelPlan& F = P.lv[P.L - 1];
-        SCK(cudaMemcpyAsync(F.g, r->g, sizeof(float) * F.h * F.w, cudaMemcpyDeviceToDevice, s));
-        for (int l = P.L - 1; l > 0; --l)
-            SCK(launch_restrict(P.lv[l].g, P.lv[l].h, P.lv[l].w, P.lv[l - 1].g, P.lv[l - 1].h,
-                                P.lv[l - 1].w, s));
+        OpItem in;
+        in.a = r->g;
+        in.out = F.g;
+        in.h = F.h;
+        in.w = F.w;
+        add_op(pre, G_IN, OP_COPY, in);
+        // scalars, barrier state and partials start at zero, as in a new plan
+        OpItem z;
+        z.out = (float*)(P.ws + Y.sc_off);
+        z.h = 1;
+        z.w = (int)((Y.bytes - Y.sc_off) / sizeof(float));
+        add_op(pre, G_ZERO, OP_ZERO, z);
+        for (int l = P.L - 1; l > 0; --l) {
+            OpItem rs;
+            rs.a = P.lv[l].g;
+            rs.w1 = P.lv[l].w;
+            rs.out = P.lv[l - 1].g;
+            rs.h = P.lv[l - 1].h;
+            rs.w = P.lv[l - 1].w;
+            add_op(pre, G_RESTRICT0 + (P.L - 1 - l), OP_RESTRICT, rs);
+        }
     }
     std::vector<std::pair<eecmg_plan_s*, int>> items;
     items.reserve(S->active.size());
     for (Request* r : S->active) {
         eecmg_plan_s& P = r->slot;
         const int st = r->step;
-        const int nzero = P.opt.prolong == EECMG_PROLONG_EECMG ? 2 : 1;
-        if (st < nzero) {
-            SCK(cudaMemsetAsync(P.lv[st].u, 0, sizeof(float) * P.lv[st].h * P.lv[st].w, s));
-        } else {
-            eecmg_status e = prolong_enqueue(&P, st, s);
-            if (e != EECMG_OK) return e;
-        }
         items.push_back({&P, st});
+        const int nzero = P.opt.prolong == EECMG_PROLONG_EECMG ? 2 : 1;
+        LevelPlan& L = P.lv[st];
+        if (st < nzero) {
+            OpItem z;
+            z.out = L.u;
+            z.h = L.h;
+            z.w = L.w;
+            add_op(pre, G_ZERO, OP_ZERO, z);
+            continue;
+        }
+        // the prolongation of prolong_enqueue (plan.cu), same buffers and order
+        LevelPlan& L1 = P.lv[st - 1];
+        float* up = P.vec[0];
+        float* sm = P.vec[1];
+        if (P.opt.prolong == EECMG_PROLONG_EECMG) {
+            LevelPlan& L2 = P.lv[st - 2];
+            float* ext = P.vec[2];
+            OpItem x;
+            x.a = L1.u;
+            x.b = L2.u;
+            x.out = ext;
+            x.h = L1.h;
+            x.w = L1.w;
+            x.h1 = L1.h;
+            x.w1 = L1.w;
+            x.h2 = L2.h;
+            x.w2 = L2.w;
+            add_op(pre, G_EXTRA, OP_EXTRAPOLATE, x);
+            OpItem q;
+            q.a = ext;
+            q.out = up;
+            q.h = L.h;
+            q.w = L.w;
+            q.h1 = L1.h;
+            q.w1 = L1.w;
+            add_op(pre, G_QUAD, OP_QUADRATIC, q);
+        } else {
+            OpItem q;
+            q.a = L1.u;
+            q.out = up;
+            q.h = L.h;
+            q.w = L.w;
+            q.h1 = L1.h;
+            q.w1 = L1.w;
+            add_op(pre, P.opt.prolong == EECMG_PROLONG_IECMG_P ? G_QUAD : G_LIN,
+                   P.opt.prolong == EECMG_PROLONG_IECMG_P ? OP_QUADRATIC : OP_LINEAR, q);
+        }
+        OpItem sms;
+        sms.a = up;
+        sms.out = sm;
+        sms.h = L.h;
+        sms.w = L.w;
+        sms.p0 = (float)P.opt.s_scale;
+        add_op(pre, G_SMOOTH, OP_SMOOTH, sms);
+        const int steps = P.opt.diffusion_steps;
+        if (steps <= 0) {
+            OpItem c;
+            c.a = sm;
+            c.out = L.u;
+            c.h = L.h;
+            c.w = L.w;
+            add_op(pre, G_STEP0, OP_COPY, c);
+            continue;
+        }
+        const float* cur = sm;
+        const float kpm = (float)P.kpm;
+        for (int dstep = 0; dstep < steps; ++dstep) {
+            float* nxt = (dstep == steps - 1) ? L.u : (cur == sm ? up : sm);
+            OpItem dn;
+            dn.a = cur;
+            dn.out = nxt;
+            dn.h = L.h;
+            dn.w = L.w;
+            dn.p0 = (float)P.tau;
+            dn.p1 = 1.f / (kpm * kpm);
+            // copies (no diffusion) and D steps never share a group: a D
+            // step goes to its own group after the copy group of step 0
+            add_op(pre, G_STEP0 + 1 + dstep, OP_DENOISE, dn);
+            cur = nxt;
+        }
+    }
+    for (Request* r : S->active) {
+        eecmg_plan_s& P = r->slot;
+        if (r->step != P.L - 1) continue;
+        LevelPlan& F = P.lv[P.L - 1];
+        OpItem c;
+        c.a = F.u;
+        c.out = r->u;
+        c.h = F.h;
+        c.w = F.w;
+        add_op(post, 0, OP_COPY, c);
+        finishing.push_back(r);
     }
     std::vector<HostWave> waves;
     eecmg_status e = plan_waves(items, waves);
     if (e != EECMG_OK) return e;
+    // pack job tables and op items into the tick's ring slot: one upload
+    size_t need = 0;
+    for (auto* gs : {&pre, &post})
+        for (auto& g : *gs) need += round256(sizeof(OpItem) * g.items.size());
+    for (auto& w : waves)
+        need += round256(sizeof(LevelJob) * w.jobs.size()) + round256(sizeof(unsigned short) * w.block_job.size());
+    e = ensure_ring(S, need);
+    if (e != EECMG_OK) return e;
     char* h = S->h_ring + (size_t)k * S->ring_bytes;
     char* d = S->d_ring + (size_t)k * S->ring_bytes;
     size_t off = 0;
+    auto put = [&](const void* src, size_t bytes, size_t* at) -> bool {
+        if (off + round256(bytes) > S->ring_bytes) return false;
+        *at = off;
+        if (bytes) std::memcpy(h + off, src, bytes);
+        off += round256(bytes);
+        return true;
+    };
+    struct Placed {
+        int op;
+        size_t at;
+        int n, blocks;
+    };
+    auto place_groups = [&](std::vector<OpGroup>& groups, std::vector<Placed>& out) -> bool {
+        for (auto& g : groups) {
+            if (g.items.empty() || g.op < 0) continue;
+            int blocks = 0;
+            for (auto& it : g.items) {
+                it.block0 = blocks;
+                blocks += op_blocks(it.h, it.w);
+            }
+            size_t at = 0;
+            if (!put(g.items.data(), sizeof(OpItem) * g.items.size(), &at)) return false;
+            out.push_back(Placed{g.op, at, (int)g.items.size(), blocks});
+        }
+        return true;
+    };
+    std::vector<Placed> pre_l, post_l;
     std::vector<size_t> jo(waves.size()), bo(waves.size());
-    for (size_t w = 0; w < waves.size(); ++w) {
-        const size_t jb = sizeof(LevelJob) * waves[w].jobs.size();
-        const size_t bb = sizeof(unsigned short) * waves[w].block_job.size();
-        if (off + round256(jb) + round256(bb) > S->ring_bytes)
-            return set_error(EECMG_ERR_INVALID_ARG, "eecmg_server: job table overflow");
-        jo[w] = off;
-        std::memcpy(h + off, waves[w].jobs.data(), jb);
-        off += round256(jb);
-        bo[w] = off;
-        std::memcpy(h + off, waves[w].block_job.data(), bb);
-        off += round256(bb);
-    }
+    bool fits = place_groups(pre, pre_l) && place_groups(post, post_l);
+    for (size_t w = 0; w < waves.size() && fits; ++w)
+        fits = put(waves[w].jobs.data(), sizeof(LevelJob) * waves[w].jobs.size(), &jo[w]) &&
+               put(waves[w].block_job.data(), sizeof(unsigned short) * waves[w].block_job.size(), &bo[w]);
+    if (!fits) return set_error(EECMG_ERR_INVALID_ARG, "eecmg_server: tick tables exceed the ring slot");
     if (off) SCK(cudaMemcpyAsync(d, h, off, cudaMemcpyHostToDevice, s));
+    for (const Placed& p : pre_l)
+        SCK(launch_ops_batch(p.op, (const OpItem*)(d + p.at), p.n, p.blocks, s));
     for (size_t w = 0; w < waves.size(); ++w) {
         const HostWave& W = waves[w];
         SCK(launch_level_batch((const LevelJob*)(d + jo[w]), (const unsigned short*)(d + bo[w]),
                                (int)W.jobs.size(), W.blocks, W.rt, W.sep, W.prec, W.cgls, W.bf16,
                                W.cluster, s));
     }
-    for (Request* r : S->active) {
+    for (const Placed& p : post_l)
+        SCK(launch_ops_batch(p.op, (const OpItem*)(d + p.at), p.n, p.blocks, s));
+    for (Request* r : finishing) {
         eecmg_plan_s& P = r->slot;
-        if (r->step != P.L - 1) continue;
-        LevelPlan& F = P.lv[P.L - 1];
-        SCK(cudaMemcpyAsync(r->u, F.u, sizeof(float) * F.h * F.w, cudaMemcpyDeviceToDevice, s));
         char* a = stat_area(S, r->sidx);
         SCK(cudaMemcpyAsync(a, P.sc, sizeof(Scalars) * P.L, cudaMemcpyDeviceToHost, s));
         SCK(cudaMemcpyAsync(a + sizeof(Scalars) * MAX_LEVELS, P.gsync, sizeof(GroupSync) * P.L,
                             cudaMemcpyDeviceToHost, s));
-        finishing.push_back(r);
     }
     SCK(cudaEventRecord(S->ev[k], s));
     return EECMG_OK;

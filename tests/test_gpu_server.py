@@ -147,6 +147,37 @@ def test_description_only_plans(gpu):
     desc.close()
 
 
+def test_served_options_equal_alone(gpu):
+    """Algorithm 1 prolongations and other diffusion step counts through the server's batched ops."""
+    torch, E = gpu
+    from paper_2311_03010_gb300 import synth
+
+    specs = [(96, 80, 4, synth.gaussian_psf(1.5, 4), 84, dict(prolong="iecmg_l", diffusion_steps=2)),
+             (70, 110, 4, synth.motion_psf(7, 45.0), 85, dict(prolong="iecmg_p", diffusion_steps=0)),
+             (128, 128, 5, synth.gaussian_psf(2.0, 6), 86, dict(diffusion_steps=3)),
+             (64, 96, 4, synth.gaussian_psf(1.0, 3), 87, dict(smoother="cgls", diffusion_steps=0))]
+    plans, gs, singles = [], [], []
+    for (h, w, L, psf, seed, opts) in specs:
+        p = synth.make_problem(h, w, seed, psf, 0.02)
+        pl = E.Plan(w, h, L, psf, **opts)
+        gd = dev(torch, p.g)
+        ud = torch.empty_like(gd)
+        pl.restore(gd, ud)
+        singles.append(host(ud))
+        plans.append(pl)
+        gs.append(gd)
+    srv = E.Server(1 << 30, 8)
+    outs = [torch.empty_like(g) for g in gs]
+    ts = [srv.submit(pl, g, o) for pl, g, o in zip(plans, gs, outs)]
+    srv.drain()
+    for t, o, s_ in zip(ts, outs, singles):
+        assert srv.poll(t)[0]
+        assert np.array_equal(host(o), s_)
+    srv.close()
+    for pl in plans:
+        pl.close()
+
+
 def test_server_argument_errors(gpu):
     torch, E = gpu
     from paper_2311_03010_gb300 import synth
