@@ -68,6 +68,36 @@ def make_problems(name):
     return [(u, psf, L, synth.degrade(u, psf, v, ns)[0]) for v, ns in zip(vs, nseeds)]
 
 
+LEVEL_SOLVE_SOURCES = ("common.cuh", "conv_tile.cuh", "finish.cuh", "persistent.cuh",
+                       "level_solve.hpp", "level_solve_impl.cuh", "level_solve.cu")
+
+
+def level_solve_source_hash():
+    import hashlib
+
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2311_03010_gb300", "csrc")
+    for f in LEVEL_SOLVE_SOURCES:
+        h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()
+
+
+def profiled_traffic(workload):
+    """DRAM bytes per level-solve launch from the committed ncu summary of this
+    workload, if it was taken on the current level-solve sources (else None)."""
+    path = os.path.join(ROOT, "profiles", f"level_solve_traffic_{workload}.txt")
+    if not os.path.exists(path):
+        return None, "no ncu capture of this workload"
+    kv = {}
+    for line in open(path):
+        if ":" in line:
+            k, v = line.split(":", 1)
+            kv[k.strip()] = v.strip()
+    if kv.get("level_solve_sources_sha256") != level_solve_source_hash():
+        return None, "ncu capture predates the current level-solve sources"
+    return float(kv["dram_bytes_per_launch"]), path.replace(ROOT + os.sep, "")
+
+
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -444,8 +474,9 @@ def main():
             for f in c:
                 c[f] += v[f]
         eecmg.eecmg_plan_profile(p.handle, 0)
-    launches_per_step = sum(c["launches"] for c in classes.values()) / prof_steps
+    launches_per_step = eecmg.eecmg_batch_info(plans)  # graph nodes of one timed step
     top = max(classes.items(), key=lambda kv: kv[1]["ms"])
+    traffic, traffic_src = profiled_traffic(name)
     peak, peak_kind = peaks()
     achieved = top[1]["bytes"] / (top[1]["ms"] / 1e3) / 1e9 if top[1]["ms"] > 0 else 0.0
     prof_total = sum(c["ms"] for c in classes.values())
@@ -472,9 +503,10 @@ def main():
             "e2e": {"value": e2e_val, "unit": "Mpixel/s",
                     "h2d_bytes_per_step": int(sum(g.numel() * 4 for g in gs)),
                     "d2h_bytes_per_step": int(sum(g.numel() * 4 for g in gs))},
-            "gpu_launches": int(round(launches_per_step * args.steps)),
+            "gpu_launches": int(launches_per_step * args.steps),
             "roofline": {"bound": "hbm", "kernel": top[0], "achieved": achieved, "peak": peak,
-                         "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                         "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+                         "traffic_source": traffic_src,
                          "peak_kind": peak_kind,
                          "share_of_step": top[1]["ms"] / prof_total if prof_total else None,
                          "method": f"event pairs per launch, eager replay of {prof_steps} steps"},

@@ -186,6 +186,13 @@ eecmg_status eecmg_restore_batched(const eecmg_plan_t *plans, const float *const
                                    float *const *u, int n, cudaStream_t stream);
 
 /*
+ * Kernel nodes of the CUDA graph that eecmg_restore_batched replays for
+ * exactly these plans in this order (after its first call; INVALID_ARG
+ * before): the library's kernel launches per batched restoration.
+ */
+eecmg_status eecmg_batch_info(const eecmg_plan_t *plans, int n, int *graph_nodes);
+
+/*
  * Per-level outcome of the most recent restoration with this plan:
  * iters_done[l] (iterations actually taken) and res_rms[l] (||g_l - H_l
  * u_l||_RMS as carried by the recurrence, Eq. 10).  Synchronises the plan's
@@ -323,7 +330,8 @@ eecmg_status eecmg_set_tuning(const eecmg_tuning *t);
  * 65536, 262144}, then px_per_block in {1024, 2048, 4096}, then
  * blocks_per_sm in {1, 2, 3}, from the current setting -- with `reps` timed
  * runs each (CUDA events on `stream`, after two warm-up runs), and keeps the
- * fastest (also written to *best if non-NULL).  The plans are descriptions:
+ * fastest (a candidate must beat the incumbent by 3 %; also written to *best
+ * if non-NULL).  The plans are descriptions:
  * the tuner restores private copies with their own workspaces and frees
  * them.  Needs the same conditions as eecmg_set_tuning (BUSY otherwise: pass
  * plans created with workspace = 0).  Synchronises the stream.

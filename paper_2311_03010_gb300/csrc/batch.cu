@@ -118,6 +118,7 @@ struct BatchCtx {
     void* dmem = nullptr;
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t gexec = nullptr;
+    size_t graph_nodes = 0;  // kernel nodes of one batched restoration
     ~BatchCtx() {
         if (gexec) cudaGraphExecDestroy(gexec);
         if (cap_stream) cudaStreamDestroy(cap_stream);
@@ -253,6 +254,17 @@ eecmg_status restore_batched_impl(const eecmg_plan_t* plans, const float* const*
         }
         if (e != cudaSuccess)
             return set_error(EECMG_ERR_CUDA, std::string("eecmg_restore_batched: capture: ") + cudaGetErrorString(e));
+        {  // count the kernel nodes: one device launch each per restoration
+            size_t nn = 0;
+            cudaGraphGetNodes(graph, nullptr, &nn);
+            std::vector<cudaGraphNode_t> nodes(nn);
+            if (nn) cudaGraphGetNodes(graph, nodes.data(), &nn);
+            C.graph_nodes = 0;
+            for (auto nd : nodes) {
+                cudaGraphNodeType t;
+                if (cudaGraphNodeGetType(nd, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++C.graph_nodes;
+            }
+        }
         e = cudaGraphInstantiate(&C.gexec, graph, 0);
         cudaGraphDestroy(graph);
         if (e != cudaSuccess) {
@@ -268,6 +280,16 @@ eecmg_status restore_batched_impl(const eecmg_plan_t* plans, const float* const*
             BCK(cudaMemcpyAsync(u[i], F.u, sizeof(float) * P->W * P->H, cudaMemcpyDeviceToDevice, s));
         P->last_stream = s;
     }
+    return EECMG_OK;
+}
+
+eecmg_status batch_graph_nodes(const eecmg_plan_t* plans, int n, int* nodes) {
+    std::vector<eecmg_plan_s*> key(plans, plans + n);
+    std::lock_guard<std::mutex> lock(g_batch_mu);
+    auto it = g_batches.find(key);
+    if (it == g_batches.end() || !it->second->gexec)
+        return set_error(EECMG_ERR_INVALID_ARG, "eecmg_batch_info: no batched restoration of these plans yet");
+    *nodes = (int)it->second->graph_nodes;
     return EECMG_OK;
 }
 

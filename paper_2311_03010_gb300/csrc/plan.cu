@@ -907,6 +907,11 @@ eecmg_status eecmg_plan_profile_read(eecmg_plan_t P, eecmg_kernel_stat* out, int
     return EECMG_OK;
 }
 
+eecmg_status eecmg_batch_info(const eecmg_plan_t* plans, int n, int* graph_nodes) {
+    if (!plans || n < 1 || !graph_nodes) return set_error(EECMG_ERR_INVALID_ARG, "eecmg_batch_info: bad arguments");
+    return batch_graph_nodes(plans, n, graph_nodes);
+}
+
 eecmg_status eecmg_restore_batched(const eecmg_plan_t* plans, const float* const* g, float* const* u,
                                    int n, cudaStream_t s) {
     if (n < 0 || (n > 0 && (!plans || !g || !u)))

@@ -99,4 +99,5 @@ eecmg_status run_cascade(eecmg_plan_s* P, cudaStream_t s);
 eecmg_status restore_batched_impl(const eecmg_plan_t* plans, const float* const* g, float* const* u,
                                   int n, cudaStream_t s);
 void forget_plan_batches(eecmg_plan_s* P);
+eecmg_status batch_graph_nodes(const eecmg_plan_t* plans, int n, int* nodes);
 }  // namespace eecmg

@@ -8,7 +8,7 @@
 // solve of the process is partitioned the same way alone, batched or served.
 // eecmg_autotune times candidate settings on the caller's own workload (one
 // batched restoration of the given plans) by coordinate search and keeps the
-// fastest.
+// fastest (a change must gain at least 3 %).
 #include <string>
 #include <vector>
 
@@ -149,7 +149,9 @@ eecmg_status eecmg_autotune(const eecmg_plan_t* plans, const float* const* g, in
                     continue;  // already timed
                 float ms = 0.f;
                 st = time_tuning(R, g, reps, s, t, &ms);
-                if (st == EECMG_OK && ms < best_ms) {
+                // a candidate must beat the incumbent by 3 %: timing noise does
+                // not move the partition between runs
+                if (st == EECMG_OK && ms < 0.97f * best_ms) {
                     best_ms = ms;
                     cur = t;
                 }

@@ -84,6 +84,7 @@ _SIGS = {
     "eecmg_restore_batched": [ctypes.POINTER(_VP), ctypes.POINTER(_VP), ctypes.POINTER(_VP), _I,
                               _VP],
     "eecmg_plan_stats": [_VP, _PI, _PD],
+    "eecmg_batch_info": [ctypes.POINTER(_VP), _I, _PI],
     "eecmg_plan_profile": [_VP, _I],
     "eecmg_plan_profile_read": [_VP, ctypes.POINTER(eecmg_kernel_stat), _I, _PI],
     "eecmg_apply_H": [_VP, _I, _VP, _VP, _I, _VP],
@@ -300,6 +301,15 @@ def eecmg_residual_noalloc(width, height, psf, g, u, r, norms, stream=None):
 def _tuning_dict(t):
     return {"cluster_max_px": t.cluster_max_px, "px_per_block": t.px_per_block,
             "blocks_per_sm": t.blocks_per_sm}
+
+
+def eecmg_batch_info(plans):
+    """Device launches (graph nodes) of one eecmg_restore_batched of these plans."""
+    n = len(plans)
+    hp = (_VP * n)(*[p.handle if isinstance(p, Plan) else p for p in plans])
+    k = _I()
+    _call("eecmg_batch_info", hp, n, ctypes.byref(k))
+    return k.value
 
 
 def eecmg_get_tuning():
