@@ -4,13 +4,14 @@
 // Each image keeps its own plan (workspace, level pyramid, scalars).  Per
 // cascade step s (levels counted from the coarsest, so every image's level s
 // is at the same depth of Algorithm 2), the level solves of all images are
-// jobs of one cooperative grid: image i's job owns a range of blocks with its
+// jobs of one persistent launch: image i's job owns a range of blocks with its
 // own group barrier, reduction partials and scalars, so the images never
 // wait for one another inside the launch.  Jobs are grouped by solver,
 // separability, precision and storage type (one kernel instantiation each)
 // and, within a
 // group, share the largest PSF radius (smaller PSFs are zero-padded).  The
-// restriction and the per-image prolongation kernels run before each step.
+// restriction and the prolongation chain run before each step as one launch
+// per kind of operation over all images (k_ops_batch).
 // The whole batch is captured once as a CUDA graph per set of plans and
 // replayed; inputs are copied into the plans' workspaces outside the graph.
 #include <algorithm>
@@ -104,6 +105,123 @@ eecmg_status plan_waves(const std::vector<std::pair<eecmg_plan_s*, int>>& items,
     return EECMG_OK;
 }
 
+void add_op(std::vector<OpGroup>& groups, size_t gi, int op, OpItem it) {
+    if (groups.size() <= gi) groups.resize(gi + 1);
+    groups[gi].op = op;
+    it.bx = op_blocks_x(it.w);
+    groups[gi].items.push_back(it);
+}
+
+int place_items(OpGroup& g) {
+    int blocks = 0;
+    for (auto& it : g.items) {
+        it.block0 = blocks;
+        blocks += op_blocks(it.h, it.w);
+    }
+    return blocks;
+}
+
+void restrict_ops(const std::vector<eecmg_plan_s*>& plans, std::vector<OpGroup>& groups) {
+    const size_t base = groups.size();
+    for (eecmg_plan_s* P : plans)
+        for (int l = P->L - 1; l > 0; --l) {
+            OpItem rs;
+            rs.a = P->lv[l].g;
+            rs.w1 = P->lv[l].w;
+            rs.out = P->lv[l - 1].g;
+            rs.h = P->lv[l - 1].h;
+            rs.w = P->lv[l - 1].w;
+            add_op(groups, base + (size_t)(P->L - 1 - l), OP_RESTRICT, rs);
+        }
+}
+
+void step_ops(const std::vector<std::pair<eecmg_plan_s*, int>>& items, std::vector<OpGroup>& groups) {
+    const size_t base = groups.size();
+    const size_t G_ZERO = base, G_EXTRA = base + 1, G_QUAD = base + 2, G_LIN = base + 3,
+                 G_SMOOTH = base + 4, G_STEP0 = base + 5;  // + diffusion step
+    for (auto& itm : items) {
+        eecmg_plan_s& P = *itm.first;
+        const int st = itm.second;
+        const int nzero = P.opt.prolong == EECMG_PROLONG_EECMG ? 2 : 1;
+        LevelPlan& L = P.lv[st];
+        if (st < nzero) {
+            OpItem z;
+            z.out = L.u;
+            z.h = L.h;
+            z.w = L.w;
+            add_op(groups, G_ZERO, OP_ZERO, z);
+            continue;
+        }
+        LevelPlan& L1 = P.lv[st - 1];
+        float* up = P.vec[0];
+        float* sm = P.vec[1];
+        if (P.opt.prolong == EECMG_PROLONG_EECMG) {
+            LevelPlan& L2 = P.lv[st - 2];
+            float* ext = P.vec[2];
+            OpItem x;
+            x.a = L1.u;
+            x.b = L2.u;
+            x.out = ext;
+            x.h = L1.h;
+            x.w = L1.w;
+            x.h1 = L1.h;
+            x.w1 = L1.w;
+            x.h2 = L2.h;
+            x.w2 = L2.w;
+            add_op(groups, G_EXTRA, OP_EXTRAPOLATE, x);
+            OpItem q;
+            q.a = ext;
+            q.out = up;
+            q.h = L.h;
+            q.w = L.w;
+            q.h1 = L1.h;
+            q.w1 = L1.w;
+            add_op(groups, G_QUAD, OP_QUADRATIC, q);
+        } else {
+            OpItem q;
+            q.a = L1.u;
+            q.out = up;
+            q.h = L.h;
+            q.w = L.w;
+            q.h1 = L1.h;
+            q.w1 = L1.w;
+            const bool quad = P.opt.prolong == EECMG_PROLONG_IECMG_P;
+            add_op(groups, quad ? G_QUAD : G_LIN, quad ? OP_QUADRATIC : OP_LINEAR, q);
+        }
+        OpItem sms;
+        sms.a = up;
+        sms.out = sm;
+        sms.h = L.h;
+        sms.w = L.w;
+        sms.p0 = (float)P.opt.s_scale;
+        add_op(groups, G_SMOOTH, OP_SMOOTH, sms);
+        const int steps = P.opt.diffusion_steps;
+        if (steps <= 0) {
+            OpItem c;
+            c.a = sm;
+            c.out = L.u;
+            c.h = L.h;
+            c.w = L.w;
+            add_op(groups, G_STEP0, OP_COPY, c);
+            continue;
+        }
+        const float* cur = sm;
+        const float kpm = (float)P.kpm;
+        for (int d = 0; d < steps; ++d) {
+            float* nxt = (d == steps - 1) ? L.u : (cur == sm ? up : sm);
+            OpItem dn;
+            dn.a = cur;
+            dn.out = nxt;
+            dn.h = L.h;
+            dn.w = L.w;
+            dn.p0 = (float)P.tau;
+            dn.p1 = 1.f / (kpm * kpm);
+            add_op(groups, G_STEP0 + 1 + (size_t)d, OP_DENOISE, dn);  // never in the copy group
+            cur = nxt;
+        }
+    }
+}
+
 namespace {
 
 struct Wave {
@@ -112,9 +230,17 @@ struct Wave {
     int njobs = 0, blocks = 0, rt = 0, sep = 0, prec = 0, cgls = 0, bf16 = 0, cluster = 0;
 };
 
+struct OpLaunch {
+    int op = -1;
+    const OpItem* d_items = nullptr;
+    int n = 0, blocks = 0;
+};
+
 struct BatchCtx {
     std::vector<eecmg_plan_s*> plans;
     std::vector<std::vector<Wave>> steps;  // per cascade step
+    std::vector<OpLaunch> restrict_ops;    // the data pyramids
+    std::vector<std::vector<OpLaunch>> step_ops;  // per cascade step, before its waves
     void* dmem = nullptr;
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t gexec = nullptr;
@@ -141,7 +267,24 @@ eecmg_status build_ctx(BatchCtx& C) {
         eecmg_status st = plan_waves(items, hsteps[s]);
         if (st != EECMG_OK) return st;
     }
+    // per-level operations: one launch per kind over all images
+    std::vector<OpGroup> rgroups;
+    restrict_ops(C.plans, rgroups);
+    std::vector<std::vector<OpGroup>> sgroups(maxL);
+    for (int s = 0; s < maxL; ++s) {
+        std::vector<std::pair<eecmg_plan_s*, int>> items;
+        for (auto* P : C.plans)
+            if (s < P->L) items.push_back({P, s});
+        step_ops(items, sgroups[s]);
+    }
     size_t bytes = 0;
+    auto group_bytes = [](std::vector<OpGroup>& gs) {
+        size_t b = 0;
+        for (auto& g : gs) b += (sizeof(OpItem) * g.items.size() + 255) / 256 * 256;
+        return b;
+    };
+    bytes += group_bytes(rgroups);
+    for (auto& gs : sgroups) bytes += group_bytes(gs);
     for (auto& st : hsteps)
         for (auto& w : st) {
             bytes += (sizeof(LevelJob) * w.jobs.size() + 255) / 256 * 256;
@@ -150,6 +293,26 @@ eecmg_status build_ctx(BatchCtx& C) {
     cudaError_t e = cudaMalloc(&C.dmem, bytes ? bytes : 256);
     if (e != cudaSuccess) return set_error(EECMG_ERR_OOM, "eecmg_restore_batched: job tables");
     char* p = (char*)C.dmem;
+    auto upload_groups = [&](std::vector<OpGroup>& gs, std::vector<OpLaunch>& out) -> cudaError_t {
+        for (auto& g : gs) {
+            if (g.items.empty() || g.op < 0) continue;
+            OpLaunch L;
+            L.op = g.op;
+            L.blocks = place_items(g);
+            L.n = (int)g.items.size();
+            L.d_items = (const OpItem*)p;
+            cudaError_t err = cudaMemcpy(p, g.items.data(), sizeof(OpItem) * g.items.size(),
+                                         cudaMemcpyHostToDevice);
+            if (err != cudaSuccess) return err;
+            p += (sizeof(OpItem) * g.items.size() + 255) / 256 * 256;
+            out.push_back(L);
+        }
+        return cudaSuccess;
+    };
+    e = upload_groups(rgroups, C.restrict_ops);
+    C.step_ops.assign(maxL, {});
+    for (int s = 0; s < maxL && e == cudaSuccess; ++s) e = upload_groups(sgroups[s], C.step_ops[s]);
+    if (e != cudaSuccess) return set_error(EECMG_ERR_CUDA, "eecmg_restore_batched: op upload");
     C.steps.assign(maxL, {});
     for (int s = 0; s < maxL; ++s)
         for (auto& w : hsteps[s]) {
@@ -187,21 +350,9 @@ eecmg_status build_ctx(BatchCtx& C) {
     } while (0)
 
 eecmg_status enqueue_batch(BatchCtx& C, cudaStream_t s) {
-    for (auto* P : C.plans)
-        for (int l = P->L - 1; l > 0; --l)
-            BCK(launch_restrict(P->lv[l].g, P->lv[l].h, P->lv[l].w, P->lv[l - 1].g, P->lv[l - 1].h,
-                                P->lv[l - 1].w, s));
+    for (const OpLaunch& L : C.restrict_ops) BCK(launch_ops_batch(L.op, L.d_items, L.n, L.blocks, s));
     for (int st = 0; st < (int)C.steps.size(); ++st) {
-        for (auto* P : C.plans) {
-            if (st >= P->L) continue;
-            const int nzero = P->opt.prolong == EECMG_PROLONG_EECMG ? 2 : 1;
-            if (st < nzero) {
-                BCK(cudaMemsetAsync(P->lv[st].u, 0, sizeof(float) * P->lv[st].h * P->lv[st].w, s));
-            } else {
-                eecmg_status r = prolong_enqueue(P, st, s);
-                if (r != EECMG_OK) return r;
-            }
-        }
+        for (const OpLaunch& L : C.step_ops[st]) BCK(launch_ops_batch(L.op, L.d_items, L.n, L.blocks, s));
         for (auto& w : C.steps[st])
             BCK(launch_level_batch(w.d_jobs, w.d_block_job, w.njobs, w.blocks, w.rt, w.sep, w.prec,
                                    w.cgls, w.bf16, w.cluster, s));

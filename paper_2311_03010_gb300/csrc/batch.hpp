@@ -5,6 +5,7 @@
 #include <utility>
 #include <vector>
 
+#include "launch.hpp"
 #include "level_solve.hpp"
 #include "plan.hpp"
 
@@ -31,5 +32,28 @@ LevelJob make_job(eecmg_plan_s* P, int l);
 // out in a fixed order (by cluster size and instantiation, then item order).
 eecmg_status plan_waves(const std::vector<std::pair<eecmg_plan_s*, int>>& items,
                         std::vector<HostWave>& waves);
+
+// Per-level operations of many images, one launch per group (a group holds
+// one kind of operation, k_ops_batch).
+struct OpGroup {
+    int op = -1;
+    std::vector<OpItem> items;
+};
+
+// Appends an operation to group gi.
+void add_op(std::vector<OpGroup>& groups, size_t gi, int op, OpItem it);
+
+// Restriction of the data pyramids of `plans` (each finest g in place):
+// groups appended in execution order, one per depth.
+void restrict_ops(const std::vector<eecmg_plan_s*>& plans, std::vector<OpGroup>& groups);
+
+// The start of cascade step items[i] = (plan, level) before its level solve:
+// the zero start (Algorithm 2's first levels) or the prolongation chain of
+// prolong_enqueue (Pi or not, P or L, S, the D steps), with the same buffers
+// and per-pixel code.  Groups appended in execution order.
+void step_ops(const std::vector<std::pair<eecmg_plan_s*, int>>& items, std::vector<OpGroup>& groups);
+
+// Sets each item's block0 within its group; returns the group's blocks.
+int place_items(OpGroup& g);
 
 }  // namespace eecmg

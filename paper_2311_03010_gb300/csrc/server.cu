@@ -178,20 +178,6 @@ void bind_slot(Request* r, char* ws) {
 
 char* stat_area(eecmg_server_s* S, int sidx) { return S->h_stat + (size_t)sidx * S->stat_stride; }
 
-// Operations of one kind launched together (one launch per group).
-struct OpGroup {
-    int op;
-    std::vector<OpItem> items;
-};
-
-// Appends an operation to group gi (a group holds one kind).
-void add_op(std::vector<OpGroup>& groups, size_t gi, int op, OpItem it) {
-    if (groups.size() <= gi) groups.resize(gi + 1, OpGroup{-1, {}});
-    groups[gi].op = op;
-    it.bx = op_blocks_x(it.w);
-    groups[gi].items.push_back(it);
-}
-
 // Grows the tick ring to hold `bytes` per slot (waits for the ticks in flight).
 eecmg_status ensure_ring(eecmg_server_s* S, size_t bytes) {
     if (bytes <= S->ring_bytes) return EECMG_OK;
@@ -219,23 +205,11 @@ eecmg_status ensure_ring(eecmg_server_s* S, size_t bytes) {
 eecmg_status enqueue_tick(eecmg_server_s* S, const std::vector<Request*>& admitted, int k,
                           std::vector<Request*>& finishing) {
     cudaStream_t s = S->stream;
-    // launch groups in execution order; a group holds one kind
-    constexpr int G_IN = 0, G_RESTRICT0 = 1;           // + depth (at most MAX_LEVELS - 1)
-    constexpr int G_ZERO = G_RESTRICT0 + MAX_LEVELS;   // zero starts and new scalars
-    constexpr int G_EXTRA = G_ZERO + 1, G_QUAD = G_EXTRA + 1, G_LIN = G_QUAD + 1;
-    constexpr int G_SMOOTH = G_LIN + 1, G_STEP0 = G_SMOOTH + 1;  // + diffusion step (D or copy)
-    std::vector<OpGroup> pre, post;  // before / after the level solves
-    pre.resize(G_STEP0, OpGroup{-1, {}});
-    pre[G_IN].op = OP_COPY;
-    for (int d = 0; d < MAX_LEVELS; ++d) pre[G_RESTRICT0 + d].op = OP_RESTRICT;
-    pre[G_ZERO].op = OP_ZERO;
-    pre[G_EXTRA].op = OP_EXTRAPOLATE;
-    pre[G_QUAD].op = OP_QUADRATIC;
-    pre[G_LIN].op = OP_LINEAR;
-    pre[G_SMOOTH].op = OP_SMOOTH;
+    std::vector<OpGroup> pre, post;  // launch groups before / after the level solves
+    // admissions: the data copied in, its pyramid restricted, scalars zeroed
+    std::vector<eecmg_plan_s*> adm;
     for (Request* r : admitted) {
         eecmg_plan_s& P = r->slot;
-        const PlanLayout& Y = P.layout;
         SCK(cudaMemcpyAsync(P.dtaps, r->tmpl->htaps.data(), sizeof(Taps) * 2 * P.L,
                             cudaMemcpyHostToDevice, s));
         LevelPlan& F = P.lv[P.L - 1];
@@ -244,110 +218,24 @@ eecmg_status enqueue_tick(eecmg_server_s* S, const std::vector<Request*>& admitt
         in.out = F.g;
         in.h = F.h;
         in.w = F.w;
-        add_op(pre, G_IN, OP_COPY, in);
-        // scalars, barrier state and partials start at zero, as in a new plan
+        add_op(pre, 0, OP_COPY, in);
+        adm.push_back(&P);
+    }
+    restrict_ops(adm, pre);
+    const size_t gz = pre.size();
+    for (eecmg_plan_s* P : adm) {  // scalars, barrier state and partials, as in a new plan
+        const PlanLayout& Y = P->layout;
         OpItem z;
-        z.out = (float*)(P.ws + Y.sc_off);
+        z.out = (float*)(P->ws + Y.sc_off);
         z.h = 1;
         z.w = (int)((Y.bytes - Y.sc_off) / sizeof(float));
-        add_op(pre, G_ZERO, OP_ZERO, z);
-        for (int l = P.L - 1; l > 0; --l) {
-            OpItem rs;
-            rs.a = P.lv[l].g;
-            rs.w1 = P.lv[l].w;
-            rs.out = P.lv[l - 1].g;
-            rs.h = P.lv[l - 1].h;
-            rs.w = P.lv[l - 1].w;
-            add_op(pre, G_RESTRICT0 + (P.L - 1 - l), OP_RESTRICT, rs);
-        }
+        add_op(pre, gz, OP_ZERO, z);
     }
+    // every active request: the start of its current cascade step
     std::vector<std::pair<eecmg_plan_s*, int>> items;
     items.reserve(S->active.size());
-    for (Request* r : S->active) {
-        eecmg_plan_s& P = r->slot;
-        const int st = r->step;
-        items.push_back({&P, st});
-        const int nzero = P.opt.prolong == EECMG_PROLONG_EECMG ? 2 : 1;
-        LevelPlan& L = P.lv[st];
-        if (st < nzero) {
-            OpItem z;
-            z.out = L.u;
-            z.h = L.h;
-            z.w = L.w;
-            add_op(pre, G_ZERO, OP_ZERO, z);
-            continue;
-        }
-        // the prolongation of prolong_enqueue (plan.cu), same buffers and order
-        LevelPlan& L1 = P.lv[st - 1];
-        float* up = P.vec[0];
-        float* sm = P.vec[1];
-        if (P.opt.prolong == EECMG_PROLONG_EECMG) {
-            LevelPlan& L2 = P.lv[st - 2];
-            float* ext = P.vec[2];
-            OpItem x;
-            x.a = L1.u;
-            x.b = L2.u;
-            x.out = ext;
-            x.h = L1.h;
-            x.w = L1.w;
-            x.h1 = L1.h;
-            x.w1 = L1.w;
-            x.h2 = L2.h;
-            x.w2 = L2.w;
-            add_op(pre, G_EXTRA, OP_EXTRAPOLATE, x);
-            OpItem q;
-            q.a = ext;
-            q.out = up;
-            q.h = L.h;
-            q.w = L.w;
-            q.h1 = L1.h;
-            q.w1 = L1.w;
-            add_op(pre, G_QUAD, OP_QUADRATIC, q);
-        } else {
-            OpItem q;
-            q.a = L1.u;
-            q.out = up;
-            q.h = L.h;
-            q.w = L.w;
-            q.h1 = L1.h;
-            q.w1 = L1.w;
-            add_op(pre, P.opt.prolong == EECMG_PROLONG_IECMG_P ? G_QUAD : G_LIN,
-                   P.opt.prolong == EECMG_PROLONG_IECMG_P ? OP_QUADRATIC : OP_LINEAR, q);
-        }
-        OpItem sms;
-        sms.a = up;
-        sms.out = sm;
-        sms.h = L.h;
-        sms.w = L.w;
-        sms.p0 = (float)P.opt.s_scale;
-        add_op(pre, G_SMOOTH, OP_SMOOTH, sms);
-        const int steps = P.opt.diffusion_steps;
-        if (steps <= 0) {
-            OpItem c;
-            c.a = sm;
-            c.out = L.u;
-            c.h = L.h;
-            c.w = L.w;
-            add_op(pre, G_STEP0, OP_COPY, c);
-            continue;
-        }
-        const float* cur = sm;
-        const float kpm = (float)P.kpm;
-        for (int dstep = 0; dstep < steps; ++dstep) {
-            float* nxt = (dstep == steps - 1) ? L.u : (cur == sm ? up : sm);
-            OpItem dn;
-            dn.a = cur;
-            dn.out = nxt;
-            dn.h = L.h;
-            dn.w = L.w;
-            dn.p0 = (float)P.tau;
-            dn.p1 = 1.f / (kpm * kpm);
-            // copies (no diffusion) and D steps never share a group: a D
-            // step goes to its own group after the copy group of step 0
-            add_op(pre, G_STEP0 + 1 + dstep, OP_DENOISE, dn);
-            cur = nxt;
-        }
-    }
+    for (Request* r : S->active) items.push_back({&r->slot, r->step});
+    step_ops(items, pre);
     for (Request* r : S->active) {
         eecmg_plan_s& P = r->slot;
         if (r->step != P.L - 1) continue;
@@ -389,11 +277,7 @@ eecmg_status enqueue_tick(eecmg_server_s* S, const std::vector<Request*>& admitt
     auto place_groups = [&](std::vector<OpGroup>& groups, std::vector<Placed>& out) -> bool {
         for (auto& g : groups) {
             if (g.items.empty() || g.op < 0) continue;
-            int blocks = 0;
-            for (auto& it : g.items) {
-                it.block0 = blocks;
-                blocks += op_blocks(it.h, it.w);
-            }
+            const int blocks = place_items(g);
             size_t at = 0;
             if (!put(g.items.data(), sizeof(OpItem) * g.items.size(), &at)) return false;
             out.push_back(Placed{g.op, at, (int)g.items.size(), blocks});
