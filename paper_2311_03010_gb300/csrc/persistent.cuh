@@ -127,23 +127,44 @@ __device__ __forceinline__ bool grid_reduce(const float (&v)[NV], double* partia
     __syncthreads();
     if (!s_ok) return false;
     // every block: the blocks' partials in a fixed order, then the update
-    DF acc[NV];
+    if (nb <= 32) {  // one warp: lane b holds block b's partial, a butterfly sums them
+        if (threadIdx.x < 32) {
+            DF acc[NV];
 #pragma unroll
-    for (int j = 0; j < NV; ++j) acc[j] = DF{0.f, 0.f};
-    for (unsigned int b = threadIdx.x; b < nb; b += NTHREADS) {
+            for (int j = 0; j < NV; ++j) {
+                acc[j] = DF{0.f, 0.f};
+                if (threadIdx.x < nb) {
+                    const float2 p = __ldcg(slot + (size_t)threadIdx.x * NPART + j);
+                    acc[j] = DF{p.x, p.y};
+                }
+                acc[j] = warp_sum_df(acc[j]);
+            }
+            if (threadIdx.x == 0) {
+                double t[NV];
 #pragma unroll
-        for (int j = 0; j < NV; ++j) {
-            const float2 p = __ldcg(slot + (size_t)b * NPART + j);
-            acc[j] = df_add(acc[j], DF{p.x, p.y});
+                for (int j = 0; j < NV; ++j) t[j] = df_to_double(acc[j]);
+                finish(t);
+            }
         }
-    }
-    DF tot[NV];
-    block_sum_df<NV>(acc, tot);
-    if (threadIdx.x == 0) {
-        double t[NV];
+    } else {
+        DF acc[NV];
 #pragma unroll
-        for (int j = 0; j < NV; ++j) t[j] = df_to_double(tot[j]);
-        finish(t);
+        for (int j = 0; j < NV; ++j) acc[j] = DF{0.f, 0.f};
+        for (unsigned int b = threadIdx.x; b < nb; b += NTHREADS) {
+#pragma unroll
+            for (int j = 0; j < NV; ++j) {
+                const float2 p = __ldcg(slot + (size_t)b * NPART + j);
+                acc[j] = df_add(acc[j], DF{p.x, p.y});
+            }
+        }
+        DF tot[NV];
+        block_sum_df<NV>(acc, tot);
+        if (threadIdx.x == 0) {
+            double t[NV];
+#pragma unroll
+            for (int j = 0; j < NV; ++j) t[j] = df_to_double(tot[j]);
+            finish(t);
+        }
     }
     GTRACE(bid == 0 && threadIdx.x == 0, 22);
     __syncthreads();
