@@ -178,6 +178,41 @@ def test_served_options_equal_alone(gpu):
         pl.close()
 
 
+def test_failed_request_is_isolated(gpu):
+    """A request whose data holds a NaN fails alone (EECMG_ERR_NUMERIC); the others complete."""
+    torch, E = gpu
+    from paper_2311_03010_gb300 import synth
+
+    reqs = []
+    for k, (h, w, seed) in enumerate([(64, 64, 88), (96, 72, 89), (80, 80, 90)]):
+        p = synth.make_problem(h, w, seed, synth.gaussian_psf(1.5, 4), 0.02)
+        pl = E.Plan(w, h, 4, p.psf)
+        gd = dev(torch, p.g)
+        ud = torch.empty_like(gd)
+        pl.restore(gd, ud)
+        reqs.append((pl, gd, host(ud)))
+    bad = reqs[1][1].clone()
+    bad[5, 7] = float("nan")
+    srv = E.Server(1 << 30, 4)
+    outs = [torch.empty_like(r[1]) for r in reqs]
+    ts = [srv.submit(reqs[0][0], reqs[0][1], outs[0]), srv.submit(reqs[1][0], bad, outs[1]),
+          srv.submit(reqs[2][0], reqs[2][1], outs[2])]
+    srv.drain()
+    with pytest.raises(E.EecmgError) as ei:
+        srv.poll(ts[1])
+    assert ei.value.status == 5  # EECMG_ERR_NUMERIC
+    for i in (0, 2):
+        assert srv.poll(ts[i])[0]
+        assert np.array_equal(host(outs[i]), reqs[i][2])
+    # the server keeps serving after the failure
+    t = srv.submit(reqs[0][0], reqs[0][1], outs[0])
+    srv.drain()
+    assert srv.poll(t)[0] and np.array_equal(host(outs[0]), reqs[0][2])
+    srv.close()
+    for r in reqs:
+        r[0].close()
+
+
 def test_server_argument_errors(gpu):
     torch, E = gpu
     from paper_2311_03010_gb300 import synth
