@@ -119,7 +119,7 @@ __device__ __forceinline__ void px_smooth(const float* __restrict__ in, float* _
             const bool inside = ii >= 0 && ii < h && jj >= 0 && jj < w;
             const float v = inside ? in[(size_t)ii * w + jj] - uc : 0.f;
             const float e = scale * v;
-            const float wt = inside ? expf(-e * e) : 0.f;
+            const float wt = inside ? __expf(-e * e) : 0.f;  // MUFU exp: ~2 ulp, ample for a weight
             ws[k] = wt;
             ss[k] = (float)s;
             ts[k] = (float)t;
@@ -130,9 +130,10 @@ __device__ __forceinline__ void px_smooth(const float* __restrict__ in, float* _
             vb = fmaf(wt, v, vb);
         }
     }
-    sb /= W;
-    tb /= W;
-    vb /= W;
+    const float inv_w = 1.f / W;  // W >= 1: the centre always has weight 1
+    sb *= inv_w;
+    tb *= inv_w;
+    vb *= inv_w;
     float css = 0.f, cst = 0.f, ctt = 0.f, csv = 0.f, ctv = 0.f;
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
