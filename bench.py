@@ -13,8 +13,8 @@ by a barrier and torch.cuda.synchronize().  With torchrun (N > 1) every rank
 restores its own batch (replicas; the method has no cross-image exchange)
 and the max time over ranks is used.
 
-Extra objects: ``e2e`` (same metric through eecmg_restore_host with pinned
-host buffers, copies inside the timed region), ``roofline`` (dominant kernel
+Extra objects: ``e2e`` (same metric through eecmg_restore_batched_host with
+pinned host buffers, copies inside the timed region), ``roofline`` (dominant kernel
 class: algorithmic bytes / event-timed duration from a profiled eager replay
 of the same steps, vs the measured HBM copy peak), ``cpu_baseline`` (the
 FP64 CPU oracle on a bounded sample of the workload), ``clocks`` and
@@ -442,17 +442,17 @@ def main():
                   "psnr_db": float(oracle.psnr(u_clean, got))}
         oracle.set_threads(1)
 
-    # end to end through the public host-buffer entry point (pinned memory)
+    # end to end through the public host-buffer entry point (pinned memory):
+    # the step's images copied in, restored as one batch, copied out, synchronised
     gh = [torch.from_numpy(g).pin_memory() for (_, _, _, g) in probs]
     uh = [torch.empty_like(x).pin_memory() for x in gh]
-    for p, a, b in zip(plans, gh, uh):
-        eecmg.eecmg_restore_host(p.handle, a.data_ptr(), b.data_ptr(), stream)
+    hp = [p.handle for p in plans]
+    eecmg.eecmg_restore_batched_host(hp, gh, uh, stream)
     barrier()
     e2e_steps = max(3, args.steps // 2)
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        for p, a, b in zip(plans, gh, uh):
-            eecmg.eecmg_restore_host(p.handle, a.data_ptr(), b.data_ptr(), stream)
+        eecmg.eecmg_restore_batched_host(hp, gh, uh, stream)
     barrier()
     e2e_s = replicas.max_over_ranks(time.perf_counter() - t0, world, "cuda")
     e2e_val = replicas.aggregate_rate(px_step, e2e_steps, world, e2e_s * 1e3) / 1e6

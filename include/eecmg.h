@@ -171,6 +171,15 @@ eecmg_status eecmg_restore_host(eecmg_plan_t plan, const float *g_host, float *u
                                 cudaStream_t stream);
 
 /*
+ * eecmg_restore_batched with HOST buffers: copies every g_host[i] into its
+ * plan's workspace, runs the batched restoration, copies every result to
+ * u_host[i] and synchronises `stream` once.  Pinned host memory makes the
+ * copies asynchronous.  Errors as eecmg_restore_batched.
+ */
+eecmg_status eecmg_restore_batched_host(const eecmg_plan_t *plans, const float *const *g_host,
+                                        float *const *u_host, int n, cudaStream_t stream);
+
+/*
  * Restores n images with their own plans (sizes, PSFs, levels and options
  * may differ) as one batch: per cascade step (levels counted from the
  * coarsest), one persistent cooperative launch per kind of level solver

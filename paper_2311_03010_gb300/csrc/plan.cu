@@ -907,6 +907,34 @@ eecmg_status eecmg_plan_profile_read(eecmg_plan_t P, eecmg_kernel_stat* out, int
     return EECMG_OK;
 }
 
+eecmg_status eecmg_restore_batched_host(const eecmg_plan_t* plans, const float* const* g,
+                                        float* const* u, int n, cudaStream_t s) {
+    if (n < 0 || (n > 0 && (!plans || !g || !u)))
+        return set_error(EECMG_ERR_INVALID_ARG, "eecmg_restore_batched_host: bad arguments");
+    if (n == 0) return EECMG_OK;
+    std::vector<const float*> gd(n);
+    std::vector<float*> ud(n);
+    for (int i = 0; i < n; ++i) {
+        if (!plans[i] || !g[i] || !u[i])
+            return set_error(EECMG_ERR_INVALID_ARG, "eecmg_restore_batched_host: NULL plan or buffer");
+        if (!plans[i]->ws) return no_ws("eecmg_restore_batched_host");
+        if (plans[i]->prof.on)
+            return set_error(EECMG_ERR_INVALID_ARG, "eecmg_restore_batched_host: disable profiling first");
+        LevelPlan& F = plans[i]->lv[plans[i]->L - 1];
+        CK(cudaMemcpyAsync(F.g, g[i], sizeof(float) * plans[i]->W * plans[i]->H, cudaMemcpyHostToDevice, s));
+        gd[i] = F.g;  // already in place: the batched call copies nothing more
+        ud[i] = F.u;
+    }
+    eecmg_status st = restore_batched_impl(plans, gd.data(), ud.data(), n, s);
+    if (st != EECMG_OK) return st;
+    for (int i = 0; i < n; ++i) {
+        LevelPlan& F = plans[i]->lv[plans[i]->L - 1];
+        CK(cudaMemcpyAsync(u[i], F.u, sizeof(float) * plans[i]->W * plans[i]->H, cudaMemcpyDeviceToHost, s));
+    }
+    CK(cudaStreamSynchronize(s));
+    return EECMG_OK;
+}
+
 eecmg_status eecmg_batch_info(const eecmg_plan_t* plans, int n, int* graph_nodes) {
     if (!plans || n < 1 || !graph_nodes) return set_error(EECMG_ERR_INVALID_ARG, "eecmg_batch_info: bad arguments");
     return batch_graph_nodes(plans, n, graph_nodes);

@@ -85,6 +85,8 @@ _SIGS = {
                               _VP],
     "eecmg_plan_stats": [_VP, _PI, _PD],
     "eecmg_batch_info": [ctypes.POINTER(_VP), _I, _PI],
+    "eecmg_restore_batched_host": [ctypes.POINTER(_VP), ctypes.POINTER(_VP), ctypes.POINTER(_VP), _I,
+                                   _VP],
     "eecmg_plan_profile": [_VP, _I],
     "eecmg_plan_profile_read": [_VP, ctypes.POINTER(eecmg_kernel_stat), _I, _PI],
     "eecmg_apply_H": [_VP, _I, _VP, _VP, _I, _VP],
@@ -301,6 +303,15 @@ def eecmg_residual_noalloc(width, height, psf, g, u, r, norms, stream=None):
 def _tuning_dict(t):
     return {"cluster_max_px": t.cluster_max_px, "px_per_block": t.px_per_block,
             "blocks_per_sm": t.blocks_per_sm}
+
+
+def eecmg_restore_batched_host(plans, g_host, u_host, stream=None):
+    """Host-buffer batched restoration (host pointers or numpy / pinned torch tensors)."""
+    n = len(plans)
+    hp = (_VP * n)(*[p.handle if isinstance(p, Plan) else p for p in plans])
+    hg = (_VP * n)(*[_ptr(x) for x in g_host])
+    hu = (_VP * n)(*[_ptr(x) for x in u_host])
+    _call("eecmg_restore_batched_host", hp, hg, hu, n, _stream(stream))
 
 
 def eecmg_batch_info(plans):

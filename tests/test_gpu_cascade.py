@@ -240,6 +240,28 @@ def test_batched_is_bitwise_the_single_result(gpu, orc):
         pl.close()
 
 
+def test_batched_host_entry_point_equals_device(gpu):
+    """eecmg_restore_batched_host (pinned host buffers, one sync) gives the device results."""
+    torch, E = gpu
+    cases = _batch_cases()[:4]
+    plans, gs, singles = [], [], []
+    for (p, L, smo) in cases:
+        h, w = p.g.shape
+        pl = E.Plan(w, h, L, p.psf, smoother=smo)
+        gd = dev(torch, p.g)
+        ud = torch.empty_like(gd)
+        pl.restore(gd, ud)
+        singles.append(host(ud))
+        plans.append(pl)
+        gs.append(torch.from_numpy(np.ascontiguousarray(p.g)).pin_memory())
+    us = [torch.empty_like(g).pin_memory() for g in gs]
+    E.eecmg_restore_batched_host([pl.handle for pl in plans], gs, us)
+    for s_, u in zip(singles, us):
+        assert np.array_equal(s_, u.numpy())
+    for pl in plans:
+        pl.close()
+
+
 def test_invalid_arguments_rejected(gpu):
     torch, E = gpu
     from paper_2311_03010_gb300 import synth
