@@ -155,28 +155,19 @@ void step_ops(const std::vector<std::pair<eecmg_plan_s*, int>>& items, std::vect
         LevelPlan& L1 = P.lv[st - 1];
         float* up = P.vec[0];
         float* sm = P.vec[1];
-        if (P.opt.prolong == EECMG_PROLONG_EECMG) {
+        if (P.opt.prolong == EECMG_PROLONG_EECMG) {  // fused P(Pi)
             LevelPlan& L2 = P.lv[st - 2];
-            float* ext = P.vec[2];
             OpItem x;
             x.a = L1.u;
             x.b = L2.u;
-            x.out = ext;
-            x.h = L1.h;
-            x.w = L1.w;
+            x.out = up;
+            x.h = L.h;
+            x.w = L.w;
             x.h1 = L1.h;
             x.w1 = L1.w;
             x.h2 = L2.h;
             x.w2 = L2.w;
-            add_op(groups, G_EXTRA, OP_EXTRAPOLATE, x);
-            OpItem q;
-            q.a = ext;
-            q.out = up;
-            q.h = L.h;
-            q.w = L.w;
-            q.h1 = L1.h;
-            q.w1 = L1.w;
-            add_op(groups, G_QUAD, OP_QUADRATIC, q);
+            add_op(groups, G_EXTRA, OP_PROLONG, x);
         } else {
             OpItem q;
             q.a = L1.u;

@@ -79,10 +79,11 @@ cudaError_t launch_cg_p(float* p, const float* sv, size_t n, Scalars* sc, cudaSt
 // Batched per-level operations (one launch per kind for many images).
 enum OpKind : int {
     OP_RESTRICT = 0, OP_EXTRAPOLATE, OP_QUADRATIC, OP_LINEAR, OP_SMOOTH, OP_DENOISE, OP_ZERO, OP_COPY,
-    OP_KINDS
+    OP_PROLONG, OP_KINDS
 };
 // One image's operation: output grid h x w (restriction: the coarse grid,
 // w1 = fine width; Pi: the level-(l-1) grid, inputs h1 x w1 and h2 x w2;
+// fused P(Pi): output h x w, inputs a = u_{l-1} (h1 x w1), b = u_{l-2} (h2 x w2);
 // P / L: input h1 x w1; S: p0 = scale; D: p0 = tau, p1 = 1 / k^2).  bx and
 // block0 place its blocks within the launch (filled by the host).
 struct OpItem {
@@ -101,6 +102,9 @@ cudaError_t launch_restrict(const float* fine, int hf, int wf, float* coarse, in
                             cudaStream_t s);
 cudaError_t launch_extrapolate(const float* u1, int h1, int w1, const float* u2, int h2, int w2,
                                float* out, cudaStream_t s);
+// The nonlinear prolongation P(Pi(u1, u2)) of Section 3.2 in one pass (out h x w).
+cudaError_t launch_prolong(const float* u1, int h1, int w1, const float* u2, int h2, int w2,
+                           float* out, int h, int w, cudaStream_t s);
 cudaError_t launch_quadratic(const float* ut, int h1, int w1, float* out, int h, int w,
                              cudaStream_t s);
 cudaError_t launch_linear(const float* uc, int hc, int wc, float* out, int h, int w,

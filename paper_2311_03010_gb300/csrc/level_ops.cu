@@ -28,10 +28,8 @@ __global__ void k_restrict(const float* __restrict__ fine, int wf, float* __rest
 // at edge midpoints and u1 + (sum of four d)/16 at cell centres; indices
 // past the last level-(l-2) node are clamped to it.  The differences of the
 // two near-equal iterates are taken in FP64.
-__device__ __forceinline__ void px_extrapolate(const float* __restrict__ u1, int h1, int w1,
-                                               const float* __restrict__ u2, int h2, int w2,
-                                               float* __restrict__ out, int a, int b) {
-    if (a >= h1 || b >= w1) return;
+__device__ __forceinline__ float pi_at(const float* __restrict__ u1, int w1,
+                                      const float* __restrict__ u2, int h2, int w2, int a, int b) {
     const int A0 = a >> 1, B0 = b >> 1;
     const int A1 = (a & 1) ? min(A0 + 1, h2 - 1) : A0;
     const int B1 = (b & 1) ? min(B0 + 1, w2 - 1) : B0;
@@ -39,7 +37,13 @@ __device__ __forceinline__ void px_extrapolate(const float* __restrict__ u1, int
         return (double)u1[(size_t)(2 * A) * w1 + 2 * B] - (double)u2[(size_t)A * w2 + B];
     };
     const double dsum = d(A0, B0) + d(A0, B1) + d(A1, B0) + d(A1, B1);
-    out[(size_t)a * w1 + b] = (float)((double)u1[(size_t)a * w1 + b] + 0.0625 * dsum);
+    return (float)((double)u1[(size_t)a * w1 + b] + 0.0625 * dsum);
+}
+__device__ __forceinline__ void px_extrapolate(const float* __restrict__ u1, int h1, int w1,
+                                               const float* __restrict__ u2, int h2, int w2,
+                                               float* __restrict__ out, int a, int b) {
+    if (a >= h1 || b >= w1) return;
+    out[(size_t)a * w1 + b] = pi_at(u1, w1, u2, h2, w2, a, b);
 }
 __global__ void k_extrapolate(const float* __restrict__ u1, int h1, int w1,
                               const float* __restrict__ u2, int h2, int w2,
@@ -75,6 +79,49 @@ __device__ __forceinline__ void px_quadratic(const float* __restrict__ ut, int h
 __global__ void k_quadratic(const float* __restrict__ ut, int h1, int w1, float* __restrict__ out,
                             int h, int w) {
     px_quadratic(ut, h1, w1, out, h, w, blockIdx.y * BY + threadIdx.y, blockIdx.x * BX + threadIdx.x);
+}
+
+// The nonlinear prolongation P(Pi(u1, u2)) of Section 3.2 fused for one
+// BY x BX block of fine pixels at (y0, x0): the level-(l-1) values of Pi that
+// the block's quadratic interpolation reads (a window of at most 7 x 19,
+// indices clamped as in P) are computed into shared memory first, with the
+// same arithmetic as k_extrapolate, then P reads them as k_quadratic reads
+// its input.  The result equals k_extrapolate followed by k_quadratic, without
+// the round trip of Pi's output through memory.  Called by every thread of
+// the block.
+constexpr int PI_ROWS = 2 * ((BY + 3) / 4) + 3, PI_COLS = 2 * ((BX + 3) / 4) + 3;
+__device__ __forceinline__ void tile_prolong(const float* __restrict__ u1, int h1, int w1,
+                                             const float* __restrict__ u2, int h2, int w2,
+                                             float* __restrict__ out, int h, int w, int y0, int x0) {
+    __shared__ float ext[PI_ROWS][PI_COLS];
+    const int r0 = 2 * (y0 >> 2), c0 = 2 * (x0 >> 2);
+    const int nr = 2 * (((y0 + BY - 1) >> 2) - (y0 >> 2)) + 3;
+    const int nc = 2 * (((x0 + BX - 1) >> 2) - (x0 >> 2)) + 3;
+    const int tid = threadIdx.y * BX + threadIdx.x;
+    for (int k = tid; k < nr * nc; k += BX * BY) {
+        const int rr = k / nc, cc = k - rr * nc;
+        ext[rr][cc] = pi_at(u1, w1, u2, h2, w2, min(r0 + rr, h1 - 1), min(c0 + cc, w1 - 1));
+    }
+    __syncthreads();
+    const int y = y0 + threadIdx.y, x = x0 + threadIdx.x;
+    if (y >= h || x >= w) return;
+    const int A = y >> 2, ty = y & 3, B = x >> 2, tx = x & 3;
+    float acc = 0.f;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        // staged row 2A + i - r0 holds level-(l-1) row min(2A + i, h1 - 1), as P reads
+        const float* er = ext[2 * A + i - r0];
+        float row = 0.f;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) row = fmaf(c_qw[tx][j], er[2 * B + j - c0], row);
+        acc = fmaf(c_qw[ty][i], row, acc);
+    }
+    out[(size_t)y * w + x] = acc;
+}
+__global__ void __launch_bounds__(BX* BY) k_prolong(const float* __restrict__ u1, int h1, int w1,
+                                                   const float* __restrict__ u2, int h2, int w2,
+                                                   float* __restrict__ out, int h, int w) {
+    tile_prolong(u1, h1, w1, u2, h2, w2, out, h, w, blockIdx.y * BY, blockIdx.x * BX);
 }
 
 // L of Eq. 15 in 0-based indices: copy at (2a, 2b); horizontal / vertical
@@ -236,6 +283,8 @@ __global__ void __launch_bounds__(BX* BY) k_ops_batch(const OpItem* __restrict__
     if constexpr (OP == OP_LINEAR) px_linear(it.a, it.h1, it.w1, it.out, it.h, it.w, y, x);
     if constexpr (OP == OP_SMOOTH) px_smooth(it.a, it.out, it.h, it.w, it.p0, y, x);
     if constexpr (OP == OP_DENOISE) px_denoise(it.a, it.out, it.h, it.w, it.p0, it.p1, y, x);
+    if constexpr (OP == OP_PROLONG)
+        tile_prolong(it.a, it.h1, it.w1, it.b, it.h2, it.w2, it.out, it.h, it.w, by * BY, bx * BX);
     if constexpr (OP == OP_ZERO || OP == OP_COPY) {
         if (y < it.h && x < it.w) it.out[(size_t)y * it.w + x] = OP == OP_ZERO ? 0.f : it.a[(size_t)y * it.w + x];
     }
@@ -253,6 +302,13 @@ cudaError_t launch_extrapolate(const float* u1, int h1, int w1, const float* u2,
                                float* out, cudaStream_t s) {
     if (h1 <= 0 || w1 <= 0) return cudaSuccess;
     k_extrapolate<<<grid2(h1, w1), dim3(BX, BY), 0, s>>>(u1, h1, w1, u2, h2, w2, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prolong(const float* u1, int h1, int w1, const float* u2, int h2, int w2,
+                           float* out, int h, int w, cudaStream_t s) {
+    if (h <= 0 || w <= 0) return cudaSuccess;
+    k_prolong<<<grid2(h, w), dim3(BX, BY), 0, s>>>(u1, h1, w1, u2, h2, w2, out, h, w);
     return cudaGetLastError();
 }
 
@@ -303,6 +359,7 @@ cudaError_t launch_ops_batch(int op, const OpItem* d_items, int n, int total_blo
         case OP_DENOISE: k_ops_batch<OP_DENOISE><<<g, b, 0, s>>>(d_items, n); break;
         case OP_ZERO: k_ops_batch<OP_ZERO><<<g, b, 0, s>>>(d_items, n); break;
         case OP_COPY: k_ops_batch<OP_COPY><<<g, b, 0, s>>>(d_items, n); break;
+        case OP_PROLONG: k_ops_batch<OP_PROLONG><<<g, b, 0, s>>>(d_items, n); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

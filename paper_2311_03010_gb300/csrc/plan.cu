@@ -401,13 +401,10 @@ eecmg_status prolong_enqueue(eecmg_plan_s* P, int l, cudaStream_t s) {
     LevelPlan& L = P->lv[l];
     LevelPlan& L1 = P->lv[l - 1];
     float* up = P->vec[0];  // prolonged, level l
-    if (P->opt.prolong == EECMG_PROLONG_EECMG) {
+    if (P->opt.prolong == EECMG_PROLONG_EECMG) {  // P(Pi(u_{l-1}, u_{l-2})), one fused pass
         LevelPlan& L2 = P->lv[l - 2];
-        float* ext = P->vec[2];  // on the level-(l-1) grid
-        LK(P, s, KC_PROLONG, 4.0 * (2.0 * L1.h * L1.w + (double)L2.h * L2.w),
-           launch_extrapolate(L1.u, L1.h, L1.w, L2.u, L2.h, L2.w, ext, s));
-        LK(P, s, KC_PROLONG, 4.0 * ((double)L1.h * L1.w + (double)L.h * L.w),
-           launch_quadratic(ext, L1.h, L1.w, up, L.h, L.w, s));
+        LK(P, s, KC_PROLONG, 4.0 * ((double)L1.h * L1.w + (double)L2.h * L2.w + (double)L.h * L.w),
+           launch_prolong(L1.u, L1.h, L1.w, L2.u, L2.h, L2.w, up, L.h, L.w, s));
     } else if (P->opt.prolong == EECMG_PROLONG_IECMG_P) {
         LK(P, s, KC_PROLONG, 4.0 * ((double)L1.h * L1.w + (double)L.h * L.w),
            launch_quadratic(L1.u, L1.h, L1.w, up, L.h, L.w, s));
@@ -828,8 +825,7 @@ eecmg_status eecmg_prolong(eecmg_plan_t P, int level, const float* u1, const flo
     LevelPlan& L = P->lv[level];
     LevelPlan& L1 = P->lv[level - 1];
     LevelPlan& L2 = P->lv[level - 2];
-    CK(launch_extrapolate(u1, L1.h, L1.w, u2, L2.h, L2.w, P->vec[2], s));
-    CK(launch_quadratic(P->vec[2], L1.h, L1.w, out, L.h, L.w, s));
+    CK(launch_prolong(u1, L1.h, L1.w, u2, L2.h, L2.w, out, L.h, L.w, s));
     return EECMG_OK;
 }
 
