@@ -151,10 +151,11 @@ __global__ void k_linear(const float* __restrict__ uc, int hc, int wc, float* __
 // of the offsets and of v = u_nb - u_c, the 2 x 2 moment matrix C and the
 // cross vector c, slope = C^+ c (eigenvalues below 1e-6 W dropped) and
 // a0 = u_c + vb - slope . (sb, tb).
-__device__ __forceinline__ void px_smooth(const float* __restrict__ in, float* __restrict__ out,
-                                          int h, int w, float scale, int i, int j) {
+template <class Rd>
+__device__ __forceinline__ void px_smooth_rd(Rd rd, float* __restrict__ out, int h, int w, float scale,
+                                             int i, int j) {
     if (i >= h || j >= w) return;
-    const float uc = in[(size_t)i * w + j];
+    const float uc = rd(i, j);
     float ws[9], ss[9], ts[9], vs[9];
     float W = 0.f, sb = 0.f, tb = 0.f, vb = 0.f;
 #pragma unroll
@@ -164,7 +165,7 @@ __device__ __forceinline__ void px_smooth(const float* __restrict__ in, float* _
             const int k = (s + 1) * 3 + (t + 1);
             const int ii = i + s, jj = j + t;
             const bool inside = ii >= 0 && ii < h && jj >= 0 && jj < w;
-            const float v = inside ? in[(size_t)ii * w + jj] - uc : 0.f;
+            const float v = inside ? rd(ii, jj) - uc : 0.f;
             const float e = scale * v;
             const float wt = inside ? __expf(-e * e) : 0.f;  // MUFU exp: ~2 ulp, ample for a weight
             ws[k] = wt;
@@ -225,40 +226,85 @@ __device__ __forceinline__ void px_smooth(const float* __restrict__ in, float* _
     }
     out[(size_t)i * w + j] = uc + vb - (gs * sb + gt * tb);
 }
-__global__ void k_smooth(const float* __restrict__ in, float* __restrict__ out, int h, int w,
-                         float scale) {
-    px_smooth(in, out, h, w, scale, blockIdx.y * BY + threadIdx.y, blockIdx.x * BX + threadIdx.x);
+// S for one BY x BX block at (y0, x0): the input with a 1-pixel halo is staged
+// in shared memory once (the 3 x 3 fits read it nine times); same arithmetic
+// as the per-pixel form px_smooth_rd.  Called by every thread of the block.
+__device__ __forceinline__ void tile_smooth(const float* __restrict__ in, float* __restrict__ out,
+                                            int h, int w, float scale, int y0, int x0) {
+    __shared__ float U[BY + 2][BX + 2];
+    const int tid = threadIdx.y * BX + threadIdx.x;
+    for (int k = tid; k < (BY + 2) * (BX + 2); k += BX * BY) {
+        const int r = k / (BX + 2), c = k - r * (BX + 2);
+        const int gy = y0 - 1 + r, gx = x0 - 1 + c;
+        U[r][c] = (gy >= 0 && gy < h && gx >= 0 && gx < w) ? in[(size_t)gy * w + gx] : 0.f;
+    }
+    __syncthreads();
+    px_smooth_rd([&](int a, int b) { return U[a - y0 + 1][b - x0 + 1]; }, out, h, w, scale,
+                 y0 + threadIdx.y, x0 + threadIdx.x);
+}
+
+__global__ void __launch_bounds__(BX* BY) k_smooth(const float* __restrict__ in, float* __restrict__ out,
+                                                  int h, int w, float scale) {
+    tile_smooth(in, out, h, w, scale, blockIdx.y * BY, blockIdx.x * BX);
 }
 
 // D: u + tau * sum over in-image 4-neighbours of (c_nb + c_c)/2 (u_nb - u_c),
 // c = 1 / (1 + |grad u|^2 / k^2) with central differences (an out-of-image
 // neighbour replaced by the centre value).
-__device__ __forceinline__ float pm_c(const float* __restrict__ u, int h, int w, int i, int j,
-                                      float inv_k2) {
-    const float uc = u[(size_t)i * w + j];
-    const float ue = (j + 1 < w) ? u[(size_t)i * w + j + 1] : uc;
-    const float uw = (j > 0) ? u[(size_t)i * w + j - 1] : uc;
-    const float us = (i + 1 < h) ? u[(size_t)(i + 1) * w + j] : uc;
-    const float un = (i > 0) ? u[(size_t)(i - 1) * w + j] : uc;
+template <class Rd>
+__device__ __forceinline__ float pm_c_rd(Rd u, int h, int w, int i, int j, float inv_k2) {
+    const float uc = u(i, j);
+    const float ue = (j + 1 < w) ? u(i, j + 1) : uc;
+    const float uw = (j > 0) ? u(i, j - 1) : uc;
+    const float us = (i + 1 < h) ? u(i + 1, j) : uc;
+    const float un = (i > 0) ? u(i - 1, j) : uc;
     const float gx = 0.5f * (ue - uw), gy = 0.5f * (us - un);
     return 1.f / (1.f + (gx * gx + gy * gy) * inv_k2);
 }
-
-__device__ __forceinline__ void px_denoise(const float* __restrict__ in, float* __restrict__ out,
-                                           int h, int w, float tau, float inv_k2, int i, int j) {
+// c at (i, j) from a reader Cd of precomputed c, u from Ud.
+template <class Ud, class Cd>
+__device__ __forceinline__ void px_denoise_rd(Ud in, Cd c, float* __restrict__ out, int h, int w,
+                                              float tau, int i, int j) {
     if (i >= h || j >= w) return;
-    const float uc = in[(size_t)i * w + j];
-    const float cc = pm_c(in, h, w, i, j, inv_k2);
+    const float uc = in(i, j);
+    const float cc = c(i, j);
     float f = 0.f;
-    if (i + 1 < h) f += 0.5f * (pm_c(in, h, w, i + 1, j, inv_k2) + cc) * (in[(size_t)(i + 1) * w + j] - uc);
-    if (i > 0) f += 0.5f * (pm_c(in, h, w, i - 1, j, inv_k2) + cc) * (in[(size_t)(i - 1) * w + j] - uc);
-    if (j + 1 < w) f += 0.5f * (pm_c(in, h, w, i, j + 1, inv_k2) + cc) * (in[(size_t)i * w + j + 1] - uc);
-    if (j > 0) f += 0.5f * (pm_c(in, h, w, i, j - 1, inv_k2) + cc) * (in[(size_t)i * w + j - 1] - uc);
+    if (i + 1 < h) f += 0.5f * (c(i + 1, j) + cc) * (in(i + 1, j) - uc);
+    if (i > 0) f += 0.5f * (c(i - 1, j) + cc) * (in(i - 1, j) - uc);
+    if (j + 1 < w) f += 0.5f * (c(i, j + 1) + cc) * (in(i, j + 1) - uc);
+    if (j > 0) f += 0.5f * (c(i, j - 1) + cc) * (in(i, j - 1) - uc);
     out[(size_t)i * w + j] = fmaf(tau, f, uc);
 }
-__global__ void k_denoise(const float* __restrict__ in, float* __restrict__ out, int h, int w,
-                          float tau, float inv_k2) {
-    px_denoise(in, out, h, w, tau, inv_k2, blockIdx.y * BY + threadIdx.y, blockIdx.x * BX + threadIdx.x);
+// D for one BY x BX block at (y0, x0): the input with a 2-pixel halo and the
+// diffusivities c with a 1-pixel halo are staged in shared memory (c computed
+// once per pixel instead of five times); same arithmetic as the per-pixel form.
+// Called by every thread of the block.
+__device__ __forceinline__ void tile_denoise(const float* __restrict__ in, float* __restrict__ out,
+                                             int h, int w, float tau, float inv_k2, int y0, int x0) {
+    __shared__ float U[BY + 4][BX + 4];
+    __shared__ float C[BY + 2][BX + 2];
+    const int tid = threadIdx.y * BX + threadIdx.x;
+    for (int k = tid; k < (BY + 4) * (BX + 4); k += BX * BY) {
+        const int r = k / (BX + 4), cc = k - r * (BX + 4);
+        const int gy = y0 - 2 + r, gx = x0 - 2 + cc;
+        U[r][cc] = (gy >= 0 && gy < h && gx >= 0 && gx < w) ? in[(size_t)gy * w + gx] : 0.f;
+    }
+    __syncthreads();
+    auto u = [&](int a, int b) { return U[a - y0 + 2][b - x0 + 2]; };
+    for (int k = tid; k < (BY + 2) * (BX + 2); k += BX * BY) {
+        const int r = k / (BX + 2), cc = k - r * (BX + 2);
+        const int gy = y0 - 1 + r, gx = x0 - 1 + cc;
+        // only in-image pixels are ever read back
+        C[r][cc] = (gy >= 0 && gy < h && gx >= 0 && gx < w) ? pm_c_rd(u, h, w, gy, gx, inv_k2) : 0.f;
+    }
+    __syncthreads();
+    px_denoise_rd(u, [&](int a, int b) { return C[a - y0 + 1][b - x0 + 1]; }, out, h, w, tau,
+                  y0 + threadIdx.y, x0 + threadIdx.x);
+}
+
+__global__ void __launch_bounds__(BX* BY) k_denoise(const float* __restrict__ in, float* __restrict__ out,
+                                                   int h, int w, float tau, float inv_k2) {
+    tile_denoise(in, out, h, w, tau, inv_k2, blockIdx.y * BY, blockIdx.x * BX);
 }
 
 // Many operations of one kind in one launch (the server's ticks): block b
@@ -281,8 +327,8 @@ __global__ void __launch_bounds__(BX* BY) k_ops_batch(const OpItem* __restrict__
     if constexpr (OP == OP_EXTRAPOLATE) px_extrapolate(it.a, it.h1, it.w1, it.b, it.h2, it.w2, it.out, y, x);
     if constexpr (OP == OP_QUADRATIC) px_quadratic(it.a, it.h1, it.w1, it.out, it.h, it.w, y, x);
     if constexpr (OP == OP_LINEAR) px_linear(it.a, it.h1, it.w1, it.out, it.h, it.w, y, x);
-    if constexpr (OP == OP_SMOOTH) px_smooth(it.a, it.out, it.h, it.w, it.p0, y, x);
-    if constexpr (OP == OP_DENOISE) px_denoise(it.a, it.out, it.h, it.w, it.p0, it.p1, y, x);
+    if constexpr (OP == OP_SMOOTH) tile_smooth(it.a, it.out, it.h, it.w, it.p0, by * BY, bx * BX);
+    if constexpr (OP == OP_DENOISE) tile_denoise(it.a, it.out, it.h, it.w, it.p0, it.p1, by * BY, bx * BX);
     if constexpr (OP == OP_PROLONG)
         tile_prolong(it.a, it.h1, it.w1, it.b, it.h2, it.w2, it.out, it.h, it.w, by * BY, bx * BX);
     if constexpr (OP == OP_ZERO || OP == OP_COPY) {
