@@ -293,3 +293,17 @@ def test_large_images_match_oracle(gpu, orc, size, psfname):
     assert it == rit
     assert err <= FP32_REL, err
     assert dpsnr <= FP32_DPSNR, dpsnr
+
+
+@pytest.mark.parametrize("psfname", ["gauss3", "motion15"])
+def test_large_images_cgls_match_oracle(gpu, orc, psfname):
+    """2048^2 with the CGLS smoother (the reading of the paper's CG), vs the FP64 oracle."""
+    torch, E = gpu
+    from paper_2311_03010_gb300 import synth
+
+    psf = synth.gaussian_psf(3.0, 10) if psfname == "gauss3" else synth.motion_psf(15, 30.0)
+    p = synth.make_problem(2048, 2048, 3000, psf, 0.01)
+    it, rit, err, dpsnr, _ = check_cascade(torch, E, orc, p, 5, smoother="cgls")
+    assert it == rit
+    assert err <= FP32_REL, err
+    assert dpsnr <= FP32_DPSNR, dpsnr
