@@ -376,8 +376,9 @@ eecmg_status eecmg_server_create(size_t mem_budget_bytes, int max_slots, eecmg_s
 
 /*
  * Queues one request.  plan: a plan describing the request (size, PSF,
- * options; shared and read-only, only its description is used); g_delta,
- * u_out: device buffers that stay valid until the request completes.
+ * options; shared and read-only, only its description is used; it may be a
+ * workspace = 0 plan and must stay alive until the request completes);
+ * g_delta, u_out: device buffers that stay valid until the request completes.
  * *ticket receives an id.  Errors: INVALID_ARG, BUSY (queue full),
  * OOM (the request alone exceeds the budget).
  */

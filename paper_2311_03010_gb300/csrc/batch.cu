@@ -245,6 +245,14 @@ struct BatchCtx {
 
 std::mutex g_batch_mu;
 std::map<std::vector<eecmg_plan_s*>, std::unique_ptr<BatchCtx>> g_batches;
+std::vector<std::vector<eecmg_plan_s*>> g_batch_lru;  // least recently used first
+constexpr size_t BATCH_CACHE_MAX = 64;                // cached plan sets (graph + job tables)
+
+void touch_batch(const std::vector<eecmg_plan_s*>& key) {
+    auto it = std::find(g_batch_lru.begin(), g_batch_lru.end(), key);
+    if (it != g_batch_lru.end()) g_batch_lru.erase(it);
+    g_batch_lru.push_back(key);
+}
 
 // Builds the job tables of every step (one device allocation).
 eecmg_status build_ctx(BatchCtx& C) {
@@ -372,12 +380,19 @@ eecmg_status restore_batched_impl(const eecmg_plan_t* plans, const float* const*
     std::lock_guard<std::mutex> lock(g_batch_mu);
     auto it = g_batches.find(key);
     if (it == g_batches.end()) {
+        if (g_batches.size() >= BATCH_CACHE_MAX && !g_batch_lru.empty()) {
+            // drop the least recently used plan set (cudaFree of its tables
+            // waits for work in flight)
+            g_batches.erase(g_batch_lru.front());
+            g_batch_lru.erase(g_batch_lru.begin());
+        }
         auto C = std::make_unique<BatchCtx>();
         C->plans = key;
         eecmg_status st = build_ctx(*C);
         if (st != EECMG_OK) return st;
         it = g_batches.emplace(key, std::move(C)).first;
     }
+    touch_batch(key);
     BatchCtx& C = *it->second;
     for (int i = 0; i < n; ++i) {
         eecmg_plan_s* P = plans[i];
@@ -439,10 +454,13 @@ eecmg_status batch_graph_nodes(const eecmg_plan_t* plans, int n, int* nodes) {
 void forget_plan_batches(eecmg_plan_s* P) {
     std::lock_guard<std::mutex> lock(g_batch_mu);
     for (auto it = g_batches.begin(); it != g_batches.end();) {
-        if (std::find(it->first.begin(), it->first.end(), P) != it->first.end())
+        if (std::find(it->first.begin(), it->first.end(), P) != it->first.end()) {
+            auto l = std::find(g_batch_lru.begin(), g_batch_lru.end(), it->first);
+            if (l != g_batch_lru.end()) g_batch_lru.erase(l);
             it = g_batches.erase(it);
-        else
+        } else {
             ++it;
+        }
     }
 }
 
