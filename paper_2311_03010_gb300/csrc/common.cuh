@@ -62,6 +62,9 @@ struct alignas(64) Scalars {
     // scalars by the thread that updates them (no FP64 work per element)
     float f_scale;        // 1 / ||v_k||            (H w_k = f_scale * H v_k)
     float f_ca, f_cb;     // alpha_k / ||v_k||, ||v_k|| / ||v_{k-1}||
+    float f_ca_lo, f_cb_lo;  // their FP32 rounding errors: v_{k+1} = H w - (ca + ca_lo) v - ...
+                             // cancels to ~1e-4 of H w on near-scalar levels, where a
+                             // single-float ca would stall the Lanczos recurrence
     float f_dw, f_d1, f_d2, f_dinv, f_tau;  // pending step
     float f_cg_alpha, f_beta;
 };

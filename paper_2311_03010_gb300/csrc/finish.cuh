@@ -55,8 +55,12 @@ __device__ __forceinline__ void fin_mr_a(Scalars* sc, double hv) {
     sc->alpha = alpha;
     sc->loops += 1;
     // phase B of this iteration: v_{k+1} = H w_k - (alpha/||v_k||) v_k - (||v_k||/||v_{k-1}||) v_{k-1}
-    sc->f_ca = (float)(alpha * inv);
-    sc->f_cb = (float)(sc->nrm * sc->inv_nrm_prev);
+    // double-float (hi + lo) coefficients for the Lanczos update of phase B
+    const double ca = alpha * inv, cb = sc->nrm * sc->inv_nrm_prev;
+    sc->f_ca = (float)ca;
+    sc->f_ca_lo = (float)(ca - (double)sc->f_ca);
+    sc->f_cb = (float)cb;
+    sc->f_cb_lo = (float)(cb - (double)sc->f_cb);
 }
 
 // MR-II phase B of iteration k: rr = ||r_{k-1}||^2 (k >= 2), vv = ||v_{k+1}||^2,

@@ -59,8 +59,9 @@ __global__ void __launch_bounds__(NTHREADS)
     if (*(volatile int*)&sc->stopped) return;
     const bool step = k >= 2;  // step k-1 is pending
     const float dw = sc->f_dw, d1 = sc->f_d1, d2 = sc->f_d2, dinv = sc->f_dinv, tau = sc->f_tau;
-    const float ca = sc->f_ca;               // alpha_k / ||v_k||
-    const float cb = step ? sc->f_cb : 0.f;  // ||v_k|| / ||v_{k-1}||
+    const float ca = sc->f_ca, ca_lo = sc->f_ca_lo;  // alpha_k / ||v_k||, double-float
+    const float cb = step ? sc->f_cb : 0.f;          // ||v_k|| / ||v_{k-1}||
+    const float cb_lo = step ? sc->f_cb_lo : 0.f;
     const int sk = k & 1, sk1 = sk ^ 1;
     float arr = 0.f, avv = 0.f, avr = 0.f;
     const size_t base = (size_t)blockIdx.x * EW_PER_BLOCK + threadIdx.x;
@@ -73,8 +74,12 @@ __global__ void __launch_bounds__(NTHREADS)
                 arr = fmaf(rv, rv, arr);
             }
             // v_{k+1} = H w_k - alpha_k w_k - ||v_k|| w_{k-1}
-            float vn = fmaf(-ca, V.v[sk][i], V.aw[sk][i]);
-            if (step) vn = fmaf(-cb, V.v[sk1][i], vn);
+            const float vk = V.v[sk][i];
+            float vn = fmaf(-ca_lo, vk, fmaf(-ca, vk, V.aw[sk][i]));
+            if (step) {
+                const float vk1 = V.v[sk1][i];
+                vn = fmaf(-cb_lo, vk1, fmaf(-cb, vk1, vn));
+            }
             V.v[sk1][i] = vn;
             avv = fmaf(vn, vn, avv);
             avr = fmaf(vn, V.r[i], avr);

@@ -202,8 +202,9 @@ __device__ __forceinline__ void mr2_body(ConvSmem<R, SEP>& S, const LevelJob& J,
         {
             const bool step = k >= 2;
             const StepCoef c = step_coef(sc);
-            const float ca = vldf(&sc->f_ca);
-            const float cb = step ? vldf(&sc->f_cb) : 0.f;
+            // Lanczos coefficients in double-float: the update below cancels
+            const float ca = vldf(&sc->f_ca), ca_lo = vldf(&sc->f_ca_lo);
+            const float cb = step ? vldf(&sc->f_cb) : 0.f, cb_lo = step ? vldf(&sc->f_cb_lo) : 0.f;
             float arr = 0.f, avv = 0.f, avr = 0.f;
             const size_t n4 = n >> 2;
             using IO = VecIO<HT>;
@@ -249,8 +250,8 @@ __device__ __forceinline__ void mr2_body(ConvSmem<R, SEP>& S, const LevelJob& J,
                     st4(J.r, q, rv);
                     arr = dot4(rv, rv, arr);
                 }
-                float4 vn = fma4(-ca, vk, awk);
-                if (step) vn = fma4(-cb, vj, vn);
+                float4 vn = fma4(-ca_lo, vk, fma4(-ca, vk, awk));
+                if (step) vn = fma4(-cb_lo, vj, fma4(-cb, vj, vn));
                 st4(J.v[sk1], q, vn);
                 avv = dot4(vn, vn, avv);
                 avr = dot4(vn, rv, avr);
@@ -264,8 +265,12 @@ __device__ __forceinline__ void mr2_body(ConvSmem<R, SEP>& S, const LevelJob& J,
                     } else {
                         rv = ldcg(J.r + i);
                     }
-                    float vn = fmaf(-ca, ldcg(J.v[sk] + i), ldcg(J.aw[sk] + i));
-                    if (step) vn = fmaf(-cb, ldcg(J.v[sk1] + i), vn);
+                    const float vki = ldcg(J.v[sk] + i);
+                    float vn = fmaf(-ca_lo, vki, fmaf(-ca, vki, ldcg(J.aw[sk] + i)));
+                    if (step) {
+                        const float vk1 = ldcg(J.v[sk1] + i);
+                        vn = fmaf(-cb_lo, vk1, fmaf(-cb, vk1, vn));
+                    }
                     J.v[sk1][i] = vn;
                     avv = fmaf(vn, vn, avv);
                     avr = fmaf(vn, rv, avr);

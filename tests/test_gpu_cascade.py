@@ -58,6 +58,57 @@ def test_level_solve(gpu, orc, smoother, psfname, shape, persistent):
     plan.close()
 
 
+def test_near_scalar_level_stops_like_oracle(gpu, orc):
+    """A level whose operator is nearly a multiple of the identity (a coarse level of a narrow
+    PSF): the Lanczos update cancels to ~1e-4 of H w, so single-float coefficients would stall
+    the FP32 recurrence above the convergence stop; the solve must stop where the oracle does."""
+    torch, E = gpu
+    from paper_2311_03010_gb300 import synth
+
+    psf = np.array([[0.0, 1e-3, 0.0], [1e-3, 2.2066, 1e-3], [0.0, 1e-3, 0.0]])
+    h, w = 14, 16
+    rng = np.random.default_rng(70)
+    g = (orc.apply_H(psf, synth.synthetic_image(h, w, 71)) + rng.normal(0, 1.0, (h, w))).astype(np.float32)
+    u0 = (g / 2.2 + rng.normal(0, 30.0, (h, w))).astype(np.float32)
+    plan = E.Plan(w, h, 1, psf)
+    ud = dev(torch, u0)
+    E.eecmg_level_solve(plan.handle, 0, dev(torch, g), ud, 100)
+    it, _ = plan.stats()
+    ref, k, _ = orc.mr2(psf, g.astype(np.float64), u0.astype(np.float64), 100, conv_tol=orc.CONV_TOL)
+    assert it[0] == k, (it, k)
+    assert rel_l2(host(ud), ref) <= FP32_REL
+    plan.close()
+
+
+def _random_problem(case):
+    """Seeded random restoration problem: size, levels, PSF family and width, noise, smoother."""
+    from paper_2311_03010_gb300 import synth
+
+    rng = np.random.default_rng(5000 + case)
+    h, w = int(rng.integers(17, 400)), int(rng.integers(17, 400))
+    L = int(rng.integers(3, 6))
+    while L > 3 and min((h + 2 ** (L - 1) - 1) // 2 ** (L - 1), (w + 2 ** (L - 1) - 1) // 2 ** (L - 1)) < 2:
+        L -= 1
+    if rng.uniform() < 0.5:
+        sig = float(rng.uniform(0.8, 3.5))
+        psf = synth.gaussian_psf(sig, int(np.ceil(3 * sig)))
+    else:
+        psf = synth.motion_psf(int(rng.integers(3, 16)), float(rng.uniform(0.0, 180.0)))
+    smo = "mr2" if rng.uniform() < 0.6 else "cgls"
+    return synth.make_problem(h, w, 7000 + case, psf, float(rng.uniform(0.005, 0.05))), L, smo
+
+
+@pytest.mark.parametrize("case", range(16))
+def test_random_problems_match_oracle(gpu, orc, case):
+    """Seeded random sizes (17..399 per side), levels, Gaussian or motion PSFs, noise and
+    smoothers: the FP32 cascade within 1e-4 / 0.01 dB of the FP64 oracle at its counts."""
+    torch, E = gpu
+    p, L, smo = _random_problem(case)
+    it, rit, err, dpsnr, _ = check_cascade(torch, E, orc, p, L, smoother=smo)
+    assert err <= FP32_REL, err
+    assert dpsnr <= FP32_DPSNR, dpsnr
+
+
 def _cascade_case(name):
     from paper_2311_03010_gb300 import synth
 
