@@ -6,8 +6,10 @@ image (shapes + gradient + texture band), Gaussian PSF sigma = 2.5 on 15 x
 MR-II, FP32.  One step restores both degraded images.  Metric: Mpixel/s of
 restored fine-grid pixels.
 
-Timing: W untimed warm-up steps, then K steps, each bracketed by CUDA
-events on the launching stream; between steps a 256 MiB buffer is written
+Timing: W untimed warm-up steps, then K steps (default: as many as make
+about 1.5 s of timed work), each bracketed by CUDA events on the launching
+stream; clocks are sampled every 50 ms and only samples stamped inside the
+timed region are reported; between steps a 256 MiB buffer is written
 to flush the 129 MB L2 (outside the events).  The timed region is bracketed
 by a barrier and torch.cuda.synchronize().  With torchrun (N > 1) every rank
 restores its own batch (replicas; the method has no cross-image exchange)
@@ -107,9 +109,10 @@ def peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    """nvidia-smi clocks and throttle reasons, sampled every 50 ms from before the
+    timed region to after it; only the samples stamped inside the region count."""
 
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -117,44 +120,81 @@ class ClockSampler:
         self.idx = device_index
         self.proc = None
         self.path = None
+        self.t_begin = self.t_end = None
 
     def start(self):
+        """Starts nvidia-smi and waits (at most 5 s) for its first sample."""
         fd, self.path = tempfile.mkstemp(suffix=".csv")
         os.close(fd)
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
+            return
+        t0 = time.time()
+        while time.time() - t0 < 5.0 and os.path.getsize(self.path) == 0:
+            time.sleep(0.02)
+
+    def begin(self):
+        self.t_begin = time.time()
+
+    def end(self):
+        self.t_end = time.time()
 
     def stop(self):
+        import datetime
+
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.1)  # one more sample after the region
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.proc.kill()
-        sm, smax, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        def stamp(text):
+            for fmt in ("%Y/%m/%d %H:%M:%S.%f", "%Y/%m/%d %H:%M:%S"):
+                try:
+                    return datetime.datetime.strptime(text, fmt).timestamp()
+                except ValueError:
+                    pass
+            return None
+
+        rows = []
         for line in open(self.path):
             parts = [p.strip() for p in line.split(",")]
-            if len(parts) < 9:
+            if len(parts) < 10:
                 continue
             try:
-                sm.append(float(parts[1]))
-                smax.append(float(parts[2]))
+                rows.append((stamp(parts[0]), float(parts[2]), float(parts[3]), parts[6:10]))
             except ValueError:
                 continue
-            for nm, val in zip(names, parts[5:9]):
+        os.unlink(self.path)
+        if any(r[0] is None for r in rows):
+            # unreadable time stamps: every sample, from just before to just after the region
+            inside, window = rows, "sampler run around the timed region"
+        else:
+            inside = [r for r in rows if self.t_begin is not None and self.t_begin <= r[0] <= self.t_end]
+            window = "timed region"
+        if not inside and rows and self.t_begin is not None:
+            # a region shorter than the sampling period: the sample nearest to its middle
+            mid = 0.5 * (self.t_begin + self.t_end)
+            inside = [min(rows, key=lambda r: abs(r[0] - mid))]
+            window = "nearest sample to a region shorter than the sampling period"
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in inside:
+            for nm, val in zip(names, r[3]):
                 if val.lower().startswith("active"):
                     reasons.add(nm)
-        os.unlink(self.path)
-        return {"sm_mhz": statistics.median(sm) if sm else None,
-                "sm_max_mhz": max(smax) if smax else None,
-                "samples": len(sm), "reasons": sorted(reasons)}
+        return {"sm_mhz": statistics.median(r[1] for r in inside) if inside else None,
+                "sm_max_mhz": max(r[2] for r in inside) if inside else None,
+                "samples": len(inside), "window": window,
+                "region_s": (self.t_end - self.t_begin) if self.t_begin is not None else None,
+                "reasons": sorted(reasons)}
 
 
 def cpu_baseline(name, max_seconds=12.0):
@@ -300,6 +340,8 @@ def run_reference(args, rank, world):
     step = lambda: [oracle.cascade(g.astype(np.float64), L, psf) for (_, psf, L, g) in sample]
     for _ in range(args.warmup):
         step()
+    if args.steps <= 0:
+        args.steps = 10
     t0 = time.perf_counter()
     for _ in range(args.steps):
         step()
@@ -322,7 +364,8 @@ def run_reference(args, rank, world):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--steps", type=int, default=0,
+                    help="timed steps (default: enough for about 1.5 s of timed work, 100..5000)")
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
@@ -390,6 +433,18 @@ def main():
     for _ in range(max(3, args.warmup)):
         step()
     barrier()
+    if args.steps <= 0:
+        # enough steps for about 1.5 s of timed work (same count on every rank)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(3):
+            flush.zero_()
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        per = e0.elapsed_time(e1) / 3.0
+        args.steps = int(replicas.max_over_ranks(min(5000, max(100, int(1500.0 / max(per, 1e-3)))),
+                                                 world, "cuda"))
 
     # timed region
     clocks = ClockSampler(local)
@@ -397,12 +452,14 @@ def main():
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
     barrier()
+    clocks.begin()
     for i in range(args.steps):
         flush.zero_()
         ev[i][0].record(stream)
         step()
         ev[i][1].record(stream)
     barrier()
+    clocks.end()
     clk = clocks.stop()
     step_ms = [a.elapsed_time(b) for (a, b) in ev]
     tot_ms = replicas.max_over_ranks(sum(step_ms), world, "cuda")
