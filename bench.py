@@ -436,13 +436,14 @@ def main():
     if args.steps <= 0:
         # enough steps for about 1.5 s of timed work (same count on every rank)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(3):
-            flush.zero_()
-            step()
-        e1.record(stream)
-        torch.cuda.synchronize()
-        per = e0.elapsed_time(e1) / 3.0
+        for _ in range(2):  # the second pass is the estimate
+            e0.record(stream)
+            for _ in range(5):
+                flush.zero_()
+                step()
+            e1.record(stream)
+            torch.cuda.synchronize()
+        per = e0.elapsed_time(e1) / 5.0
         args.steps = int(replicas.max_over_ranks(min(5000, max(100, int(1500.0 / max(per, 1e-3)))),
                                                  world, "cuda"))
 

@@ -33,7 +33,13 @@ struct Taps {
     float wt[TAPS_MAX];
 };
 
-// Per-solve device scalars (FP64).  One block per level of a plan.
+// A double-float value hi + lo (two floats, |lo| <= ulp(hi) / 2).
+struct DF {
+    float hi, lo;
+};
+
+// Per-solve device scalars: totals and stopping limits in FP64 for the host,
+// the Krylov recurrence scalars as double-float pairs.  One per level of a plan.
 struct alignas(64) Scalars {
     double rr;            // last ||r||^2
     double gg;            // ||g||^2
@@ -43,22 +49,23 @@ struct alignas(64) Scalars {
     int iters;            // iterations whose step has been decided
     unsigned int counter; // last-block arrival counter (reset by the last block)
     int loops;            // iterations whose first phase ran (for byte accounting)
-    // MR-II, Lanczos / Givens form
-    double nrm, nrm_prev; // ||v_k||, ||v_{k-1}|| (w_k = v_k / ||v_k||)
-    double inv_nrm, inv_nrm_prev;  // their reciprocals
-    double alpha;         // alpha_k = <H w_k, w_k>
-    double cs1, sn1;      // rotation G_{k-1}
-    double cs2, sn2;      // rotation G_{k-2}
-    double phi;           // pending entry of the rotated right-hand side
+    DF lim2d;             // lim2 as a double-float pair (the per-iteration tests)
+    // MR-II, Lanczos / Givens form (double-float scalars: see finish.cuh)
+    DF nrm, nrm_prev;     // ||v_k||, ||v_{k-1}|| (w_k = v_k / ||v_k||)
+    DF inv_nrm, inv_nrm_prev;  // their reciprocals
+    DF alpha;             // alpha_k = <H w_k, w_k>
+    DF cs1, sn1;          // rotation G_{k-1}
+    DF cs2, sn2;          // rotation G_{k-2}
+    DF phi;               // pending entry of the rotated right-hand side
     // pending step j: d_j = dw v_j - d1 d_{j-1} - d2 d_{j-2}  (= (w_j - r1 d_{j-1} -
     // e d_{j-2}) / rho), H d_j = dinv H w_j - d1 H d_{j-1} - d2 H d_{j-2},
     // u += tau d_j, r -= tau H d_j
-    double dw, d1, d2, dinv, tau;
+    DF dw, d1, d2, dinv, tau;
     // CGLS
-    double gamma;         // <s, s>
-    double qq;            // <q, q>
-    double cg_alpha, beta;
-    // FP32 coefficients for the vector phases, rounded once from the FP64
+    DF gamma;             // <s, s>
+    DF qq;                // <q, q>
+    DF cg_alpha, beta;
+    // FP32 coefficients for the vector phases, rounded once from the
     // scalars by the thread that updates them (no FP64 work per element)
     float f_scale;        // 1 / ||v_k||            (H w_k = f_scale * H v_k)
     float f_ca, f_cb;     // alpha_k / ||v_k||, ||v_k|| / ||v_{k-1}||
@@ -82,10 +89,6 @@ constexpr int NPART = 4;  // partial sums per block
 // on block scheduling.
 // ---------------------------------------------------------------------------
 
-struct DF {
-    float hi, lo;
-};
-
 // Error-free sum of two floats (Knuth's TwoSum).
 __device__ __forceinline__ DF two_sum(float a, float b) {
     const float s = __fadd_rn(a, b);
@@ -99,6 +102,81 @@ __device__ __forceinline__ DF df_add(DF a, DF b) {
     const float lo = __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo));
     return two_sum(s.hi, lo);
 }
+
+// ---------------------------------------------------------------------------
+// Double-float scalar arithmetic for the solvers' scalar updates (Dekker's
+// pair arithmetic: a value is hi + lo with |lo| <= ulp(hi) / 2, sums by
+// Knuth's TwoSum, products made exact by one FMA).  On GB300 a dependent FP64
+// FMA takes about 66 cycles and an FP64 reciprocal square root about 400;
+// these run on the FP32 pipes in 4-cycle steps and keep 44-48 significant
+// bits.  Every operation ends normalised, so hi is the value rounded to
+// float.
+// ---------------------------------------------------------------------------
+
+// a + b when |a| >= |b| (or a == 0).
+__device__ __forceinline__ DF fast_two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    return DF{s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+
+__device__ __forceinline__ DF two_prod(float a, float b) {
+    const float p = __fmul_rn(a, b);
+    return DF{p, fmaf(a, b, -p)};
+}
+
+__device__ __forceinline__ DF df_neg(DF a) { return DF{-a.hi, -a.lo}; }
+
+// Sum keeping the rounding errors of both parts (accurate under cancellation).
+__device__ __forceinline__ DF df_add2(DF a, DF b) {
+    DF s = two_sum(a.hi, b.hi);
+    const DF t = two_sum(a.lo, b.lo);
+    s = fast_two_sum(s.hi, __fadd_rn(s.lo, t.hi));
+    return fast_two_sum(s.hi, __fadd_rn(s.lo, t.lo));
+}
+
+__device__ __forceinline__ DF df_sub2(DF a, DF b) { return df_add2(a, df_neg(b)); }
+
+__device__ __forceinline__ DF df_mul(DF a, DF b) {
+    const DF p = two_prod(a.hi, b.hi);
+    return fast_two_sum(p.hi, fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, p.lo)));
+}
+
+__device__ __forceinline__ DF df_mulf(DF a, float b) {
+    const DF p = two_prod(a.hi, b);
+    return fast_two_sum(p.hi, fmaf(a.lo, b, p.lo));
+}
+
+// a / b: the float quotient corrected once by the remainder a - b q.
+__device__ __forceinline__ DF df_div(DF a, DF b) {
+    const float q1 = __fdiv_rn(a.hi, b.hi);
+    const DF r = df_sub2(a, df_mulf(b, q1));
+    return fast_two_sum(q1, __fdiv_rn(r.hi, b.hi));
+}
+
+// 1 / sqrt(x), x > 0: the FP32 estimate y refined by one Newton step
+// y (1 + e / 2), e = 1 - x y^2 formed in double-float (relative error about
+// 3 e^2 / 8, below 2^-44).  x is first scaled by 2^-80 or 2^80 when far from
+// 1 so that y^2 stays in range.
+__device__ __forceinline__ DF df_rsqrt(DF x) {
+    float sc = 1.f;
+    if (x.hi < 0x1p-60f) {
+        x = DF{x.hi * 0x1p80f, x.lo * 0x1p80f};
+        sc = 0x1p40f;
+    } else if (x.hi > 0x1p60f) {
+        x = DF{x.hi * 0x1p-80f, x.lo * 0x1p-80f};
+        sc = 0x1p-40f;
+    }
+    const float y = rsqrtf(x.hi);
+    const DF e = df_sub2(DF{1.f, 0.f}, df_mul(x, two_prod(y, y)));
+    const DF c = two_prod(y, 0.5f * e.hi);
+    const DF r = two_sum(y, c.hi);
+    const DF n = fast_two_sum(r.hi, __fadd_rn(r.lo, c.lo));
+    return DF{n.hi * sc, n.lo * sc};
+}
+
+// a <= b, a < b (normalised pairs compare by hi, then lo)
+__device__ __forceinline__ bool df_le(DF a, DF b) { return a.hi < b.hi || (a.hi == b.hi && a.lo <= b.lo); }
+__device__ __forceinline__ bool df_finite(DF a) { return isfinite(a.hi) && isfinite(a.lo); }
 
 __device__ __forceinline__ DF df_from_double(double x) {
     const float hi = (float)x;

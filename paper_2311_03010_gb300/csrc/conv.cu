@@ -104,12 +104,12 @@ __global__ void __launch_bounds__(NTHREADS) k_conv(ConvArgs a) {
     grid_total<2>(a.partials, nblocks, &sc->counter, tot);
     if (tid != 0) return;
     switch (mode) {
-        case CM_RESID: fin_resid(sc, tot[0], tot[1], a.conv_tol2, a.disc2); break;
-        case CM_MR_V1: fin_mr_v1(sc, tot[0], tot[1]); break;
-        case CM_MR_A: fin_mr_a(sc, tot[0]); break;
-        case CM_CG_S0: fin_cg_s0(sc, tot[0]); break;
-        case CM_CG_Q: fin_cg_q(sc, tot[0]); break;
-        case CM_CG_S: fin_cg_s(sc, tot[0]); break;
+        case CM_RESID: fin_resid(sc, df_from_double(tot[0]), df_from_double(tot[1]), a.conv_tol2, a.disc2); break;
+        case CM_MR_V1: fin_mr_v1(sc, df_from_double(tot[0]), df_from_double(tot[1])); break;
+        case CM_MR_A: fin_mr_a(sc, df_from_double(tot[0])); break;
+        case CM_CG_S0: fin_cg_s0(sc, df_from_double(tot[0])); break;
+        case CM_CG_Q: fin_cg_q(sc, df_from_double(tot[0])); break;
+        case CM_CG_S: fin_cg_s(sc, df_from_double(tot[0])); break;
         default: break;
     }
 }

@@ -1,6 +1,14 @@
-// finish.cuh -- the FP64 scalar updates that end each phase of a level solve
-// (run on one thread once the phase's inner products are reduced).  Shared
-// by the per-phase kernels and the persistent level kernels.
+// finish.cuh -- the scalar updates that end each phase of a level solve (run
+// on one thread once the phase's inner products are reduced).  Shared by the
+// per-phase kernels and the persistent level kernels.
+//
+// The inner products arrive as double-float totals and the recurrence scalars
+// are kept and updated as double-float pairs (44-48 significant bits, see
+// common.cuh): these updates sit on the critical path of every iteration, and
+// on GB300 the FP64 form of the MR-II rotation update took about 3000 cycles
+// (1.45 us) per iteration against a few hundred in pairs.  The stopping limit
+// is formed once per solve in FP64; totals the host reads (||r||^2, ||g||^2)
+// are also kept in FP64.
 //
 // stopped: 0 running; 1 a stopping rule fired; 2 breakdown, no further step;
 //          3 non-finite value; 4 breakdown after deciding a last step
@@ -13,54 +21,60 @@
 
 namespace eecmg {
 
+__device__ __forceinline__ DF df_one() { return DF{1.f, 0.f}; }
+__device__ __forceinline__ DF df_zero() { return DF{0.f, 0.f}; }
+
 // r = g - H u: ||r||^2, ||g||^2; the stopping limit and the test before
 // iteration 1 (Section 2 discrepancy rule and the convergence stop).
-__device__ __forceinline__ void fin_resid(Scalars* sc, double rr, double gg, double conv_tol2,
+__device__ __forceinline__ void fin_resid(Scalars* sc, DF rr2, DF gg2, double conv_tol2,
                                           double disc2) {
+    const double rr = df_to_double(rr2), gg = df_to_double(gg2);
     sc->rr = rr;
     sc->gg = gg;
     const double l1 = conv_tol2 * gg;
-    sc->lim2 = l1 > disc2 ? l1 : disc2;
+    const double lim2 = l1 > disc2 ? l1 : disc2;
+    sc->lim2 = lim2;
+    sc->lim2d = df_from_double(lim2);
     sc->iters = 0;
     sc->loops = 0;
     if (!(rr < 1.0e300)) sc->stopped = 3;
-    else sc->stopped = (rr <= sc->lim2) ? 1 : 0;
+    else sc->stopped = (rr <= lim2) ? 1 : 0;
 }
 
 // MR-II start: v_1 = H r_0, ||v_1||, phi_1 = <w_1, r_0>, identity rotations.
-__device__ __forceinline__ void fin_mr_v1(Scalars* sc, double vv, double vr) {
-    if (!(vv < 1.0e300)) {
+__device__ __forceinline__ void fin_mr_v1(Scalars* sc, DF vv, DF vr) {
+    if (!df_finite(vv)) {
         sc->stopped = 3;
-    } else if (!(vv > 0.0)) {
+    } else if (!(vv.hi > 0.f)) {
         sc->stopped = 2;  // H r_0 = 0: no step
     } else {
-        const double inv = rsqrt(vv);
-        sc->nrm = vv * inv;
+        const DF inv = df_rsqrt(vv);
+        sc->nrm = df_mul(vv, inv);
         sc->inv_nrm = inv;
-        sc->nrm_prev = 0.0;
-        sc->inv_nrm_prev = 0.0;
-        sc->phi = vr * inv;
-        sc->f_scale = (float)inv;
-        sc->cs1 = 1.0;
-        sc->sn1 = 0.0;
-        sc->cs2 = 1.0;
-        sc->sn2 = 0.0;
+        sc->nrm_prev = df_zero();
+        sc->inv_nrm_prev = df_zero();
+        sc->phi = df_mul(vr, inv);
+        sc->f_scale = inv.hi;
+        sc->cs1 = df_one();
+        sc->sn1 = df_zero();
+        sc->cs2 = df_one();
+        sc->sn2 = df_zero();
     }
 }
 
 // alpha_k = <H w_k, w_k> from <H w_k, v_k>.
-__device__ __forceinline__ void fin_mr_a(Scalars* sc, double hv) {
-    const double inv = sc->inv_nrm;
-    const double alpha = hv * inv;
+__device__ __forceinline__ void fin_mr_a(Scalars* sc, DF hv) {
+    const DF inv = sc->inv_nrm;
+    const DF alpha = df_mul(hv, inv);
     sc->alpha = alpha;
     sc->loops += 1;
-    // phase B of this iteration: v_{k+1} = H w_k - (alpha/||v_k||) v_k - (||v_k||/||v_{k-1}||) v_{k-1}
-    // double-float (hi + lo) coefficients for the Lanczos update of phase B
-    const double ca = alpha * inv, cb = sc->nrm * sc->inv_nrm_prev;
-    sc->f_ca = (float)ca;
-    sc->f_ca_lo = (float)(ca - (double)sc->f_ca);
-    sc->f_cb = (float)cb;
-    sc->f_cb_lo = (float)(cb - (double)sc->f_cb);
+    // phase B of this iteration: v_{k+1} = H w_k - (alpha/||v_k||) v_k - (||v_k||/||v_{k-1}||) v_{k-1},
+    // with both coefficients applied as (hi, lo) pairs
+    const DF ca = df_mul(alpha, inv), cb = df_mul(sc->nrm, sc->inv_nrm_prev);
+    sc->f_ca = ca.hi;
+    sc->f_ca_lo = ca.lo;
+    sc->f_cb = cb.hi;
+    sc->f_cb_lo = cb.lo;
 }
 
 // MR-II phase B of iteration k: rr = ||r_{k-1}||^2 (k >= 2), vv = ||v_{k+1}||^2,
@@ -68,46 +82,50 @@ __device__ __forceinline__ void fin_mr_a(Scalars* sc, double hv) {
 // column k of the tridiagonal T (||v_k|| above the diagonal, 0 for k = 1;
 // alpha_k on it; ||v_{k+1}|| below): apply G_{k-2}, G_{k-1}, form G_k, and
 // record the coefficients of step k.
-__device__ __forceinline__ void fin_mr_b(Scalars* sc, int k, double rr, double vv, double vr) {
+__device__ __forceinline__ void fin_mr_b(Scalars* sc, int k, DF rr, DF vv, DF vr) {
     const bool step = k >= 2;
     if (step) {
-        sc->rr = rr;
-        if (!(rr < 1.0e300)) {
+        sc->rr = df_to_double(rr);
+        if (!df_finite(rr)) {
             sc->stopped = 3;
             return;
         }
-        if (rr <= sc->lim2) {  // stopping rule on ||r_{k-1}||, before iteration k
+        if (df_le(rr, sc->lim2d)) {  // stopping rule on ||r_{k-1}||, before iteration k
             sc->stopped = 1;
             return;
         }
     }
-    if (!(vv < 1.0e300)) {
+    if (!df_finite(vv)) {
         sc->stopped = 3;
         return;
     }
-    const double inv_new = vv > 0.0 ? rsqrt(vv) : 0.0;
-    const double nrm_new = vv * inv_new;
-    const double c_new = vr * inv_new;
-    const double alpha = sc->alpha;
-    const double cpl = step ? sc->nrm : 0.0;
-    const double e = sc->sn2 * cpl;
-    const double t = sc->cs2 * cpl;
-    const double r1 = sc->cs1 * t + sc->sn1 * alpha;
-    const double a2 = -sc->sn1 * t + sc->cs1 * alpha;
-    const double rho2 = a2 * a2 + vv;  // rho = hypot(a2, ||v_{k+1}||)
-    if (!(rho2 > 0.0) || !(rho2 < 1.0e300)) {
-        sc->stopped = rho2 > 0.0 ? 3 : 2;
+    const DF inv_new = vv.hi > 0.f ? df_rsqrt(vv) : df_zero();
+    const DF nrm_new = df_mul(vv, inv_new);
+    const DF c_new = df_mul(vr, inv_new);
+    const DF alpha = sc->alpha;
+    const DF cpl = step ? sc->nrm : df_zero();
+    const DF e = df_mul(sc->sn2, cpl);
+    const DF t = df_mul(sc->cs2, cpl);
+    const DF r1 = df_add2(df_mul(sc->cs1, t), df_mul(sc->sn1, alpha));
+    const DF a2 = df_sub2(df_mul(sc->cs1, alpha), df_mul(sc->sn1, t));
+    const DF rho2 = df_add2(df_mul(a2, a2), vv);  // rho = hypot(a2, ||v_{k+1}||)
+    if (!(rho2.hi > 0.f) || !df_finite(rho2)) {
+        sc->stopped = rho2.hi > 0.f ? 3 : 2;
         return;
     }
-    const double inv_rho = rsqrt(rho2);
-    const double cs = a2 * inv_rho, sn = nrm_new * inv_rho;
-    const double phi = sc->phi;
-    sc->tau = cs * phi + sn * c_new;
-    sc->phi = -sn * phi + cs * c_new;
+    const DF inv_rho = df_rsqrt(rho2);
+    const DF cs = df_mul(a2, inv_rho), sn = df_mul(nrm_new, inv_rho);
+    const DF phi = sc->phi;
+    const DF tau = df_add2(df_mul(cs, phi), df_mul(sn, c_new));
+    sc->phi = df_sub2(df_mul(cs, c_new), df_mul(sn, phi));
+    sc->tau = tau;
     sc->dinv = inv_rho;
-    sc->dw = inv_rho * sc->inv_nrm;
-    sc->d1 = r1 * inv_rho;
-    sc->d2 = e * inv_rho;
+    const DF dw = df_mul(inv_rho, sc->inv_nrm);
+    const DF d1 = df_mul(r1, inv_rho);
+    const DF d2 = df_mul(e, inv_rho);
+    sc->dw = dw;
+    sc->d1 = d1;
+    sc->d2 = d2;
     sc->cs2 = sc->cs1;
     sc->sn2 = sc->sn1;
     sc->cs1 = cs;
@@ -117,56 +135,61 @@ __device__ __forceinline__ void fin_mr_b(Scalars* sc, int k, double rr, double v
     sc->nrm = nrm_new;
     sc->inv_nrm = inv_new;
     sc->iters = k;
-    sc->f_dw = (float)sc->dw;
-    sc->f_d1 = (float)sc->d1;
-    sc->f_d2 = (float)sc->d2;
-    sc->f_dinv = (float)inv_rho;
-    sc->f_tau = (float)sc->tau;
-    sc->f_scale = (float)inv_new;
-    if (!(nrm_new > 0.0)) sc->stopped = 4;  // Krylov space exhausted: step k is the last
+    sc->f_dw = dw.hi;
+    sc->f_d1 = d1.hi;
+    sc->f_d2 = d2.hi;
+    sc->f_dinv = inv_rho.hi;
+    sc->f_tau = tau.hi;
+    sc->f_scale = inv_new.hi;
+    if (!(nrm_new.hi > 0.f)) sc->stopped = 4;  // Krylov space exhausted: step k is the last
 }
 
-__device__ __forceinline__ void fin_mr_final(Scalars* sc, double rr) {
-    sc->rr = rr;
-    if (!(rr < 1.0e300)) sc->stopped = 3;
+__device__ __forceinline__ void fin_mr_final(Scalars* sc, DF rr) {
+    sc->rr = df_to_double(rr);
+    if (!df_finite(rr)) sc->stopped = 3;
 }
 
 // CGLS start: s = H^T r, gamma = <s, s>.
-__device__ __forceinline__ void fin_cg_s0(Scalars* sc, double gm) {
-    if (!(gm < 1.0e300)) sc->stopped = 3;
-    else if (!(gm > 0.0)) sc->stopped = 2;
+__device__ __forceinline__ void fin_cg_s0(Scalars* sc, DF gm) {
+    if (!df_finite(gm)) sc->stopped = 3;
+    else if (!(gm.hi > 0.f)) sc->stopped = 2;
     else sc->gamma = gm;
 }
 
 // CGLS: q = H p, alpha = gamma / <q, q>.
-__device__ __forceinline__ void fin_cg_q(Scalars* sc, double qq) {
+__device__ __forceinline__ void fin_cg_q(Scalars* sc, DF qq) {
     sc->loops += 1;
-    if (!(qq < 1.0e300)) {
+    if (!df_finite(qq)) {
         sc->stopped = 3;
-    } else if (!(qq > 0.0)) {
+    } else if (!(qq.hi > 0.f)) {
         sc->stopped = 2;
     } else {
         sc->qq = qq;
-        sc->cg_alpha = sc->gamma / qq;
-        sc->f_cg_alpha = (float)sc->cg_alpha;
+        const DF a = df_div(sc->gamma, qq);
+        sc->cg_alpha = a;
+        sc->f_cg_alpha = a.hi;
         sc->iters += 1;
     }
 }
 
 // CGLS: after u += alpha p, r -= alpha q: the stopping rule on the new residual.
-__device__ __forceinline__ void fin_cg_step(Scalars* sc, double rr) {
-    sc->rr = rr;
-    if (!(rr < 1.0e300)) sc->stopped = 3;
-    else if (rr <= sc->lim2) sc->stopped = 1;
+__device__ __forceinline__ void fin_cg_step(Scalars* sc, DF rr) {
+    sc->rr = df_to_double(rr);
+    if (!df_finite(rr)) sc->stopped = 3;
+    else if (df_le(rr, sc->lim2d)) sc->stopped = 1;
 }
 
 // CGLS: s = H^T r, beta = <s, s> / gamma.
-__device__ __forceinline__ void fin_cg_s(Scalars* sc, double gn) {
-    sc->beta = gn / sc->gamma;
-    sc->f_beta = (float)sc->beta;
+__device__ __forceinline__ void fin_cg_s(Scalars* sc, DF gn) {
+    if (!df_finite(gn)) {
+        sc->stopped = 3;
+        return;
+    }
+    const DF b = df_div(gn, sc->gamma);
+    sc->beta = b;
+    sc->f_beta = b.hi;
     sc->gamma = gn;
-    if (!(gn < 1.0e300)) sc->stopped = 3;
-    else if (!(gn > 0.0)) sc->stopped = 2;
+    if (!(gn.hi > 0.f)) sc->stopped = 2;
 }
 
 }  // namespace eecmg

@@ -90,7 +90,7 @@ __global__ void __launch_bounds__(NTHREADS)
     double tot[3];
     grid_total<3>(partials, gridDim.x, &sc->counter, tot);
     if (threadIdx.x != 0) return;
-    fin_mr_b(sc, k, tot[0], tot[1], tot[2]);
+    fin_mr_b(sc, k, df_from_double(tot[0]), df_from_double(tot[1]), df_from_double(tot[2]));
 }
 
 // Applies the step decided last (its index is sc->iters) and reduces ||r||^2.
@@ -116,7 +116,7 @@ __global__ void __launch_bounds__(NTHREADS)
     double tot[1];
     grid_total<1>(partials, gridDim.x, &sc->counter, tot);
     if (threadIdx.x != 0) return;
-    fin_mr_final(sc, tot[0]);
+    fin_mr_final(sc, df_from_double(tot[0]));
 }
 
 // CGLS: u += alpha p, r -= alpha q, ||r||^2, then the stopping rule on the
@@ -143,7 +143,7 @@ __global__ void __launch_bounds__(NTHREADS)
     double tot[1];
     grid_total<1>(partials, gridDim.x, &sc->counter, tot);
     if (threadIdx.x != 0) return;
-    fin_cg_step(sc, tot[0]);
+    fin_cg_step(sc, df_from_double(tot[0]));
 }
 
 // CGLS direction update p = s + beta p (beta decided by the H^T launch).

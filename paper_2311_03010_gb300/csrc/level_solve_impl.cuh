@@ -158,7 +158,7 @@ __device__ __forceinline__ void mr2_body(ConvSmem<R, SEP>& S, const LevelJob& J,
             conv_phase<R, SEP, PREC, false>(S, J.u, h, w, nb, bid, epi);
         float v[2] = {a0, a1};
         const double ct2 = J.conv_tol2, d2 = J.disc2;
-        if (!sy.reduce<2>(v, [&](double* t) { fin_resid(sc, t[0], t[1], ct2, d2); }))
+        if (!sy.reduce<2>(v, [&](DF* t) { fin_resid(sc, t[0], t[1], ct2, d2); }))
             return;
     }
     if (J.m <= 0 || volatile_stopped(sc)) return;
@@ -173,7 +173,7 @@ __device__ __forceinline__ void mr2_body(ConvSmem<R, SEP>& S, const LevelJob& J,
             a1 = fmaf(z, ctr, a1);
         });
         float v[2] = {a0, a1};
-        if (!sy.reduce<2>(v, [&](double* t) { fin_mr_v1(sc, t[0], t[1]); }))
+        if (!sy.reduce<2>(v, [&](DF* t) { fin_mr_v1(sc, t[0], t[1]); }))
             return;
     }
 
@@ -194,7 +194,7 @@ __device__ __forceinline__ void mr2_body(ConvSmem<R, SEP>& S, const LevelJob& J,
                                             });
             float v[1] = {a0};
             TRACE(bid, 11);
-            if (!sy.reduce<1>(v, [&](double* t) { fin_mr_a(sc, t[0]); }))
+            if (!sy.reduce<1>(v, [&](DF* t) { fin_mr_a(sc, t[0]); }))
                 return;
         }
         TRACE(bid, 12);
@@ -278,7 +278,7 @@ __device__ __forceinline__ void mr2_body(ConvSmem<R, SEP>& S, const LevelJob& J,
             }
             float v[3] = {arr, avv, avr};
             TRACE(bid, 13);
-            if (!sy.reduce<3>(v, [&](double* t) { fin_mr_b(sc, k, t[0], t[1], t[2]); }))
+            if (!sy.reduce<3>(v, [&](DF* t) { fin_mr_b(sc, k, t[0], t[1], t[2]); }))
                 return;
         }
         TRACE(bid, 14);
@@ -301,7 +301,7 @@ __device__ __forceinline__ void mr2_body(ConvSmem<R, SEP>& S, const LevelJob& J,
                 arr = fmaf(rv, rv, arr);
             }
         float v[1] = {arr};
-        sy.reduce<1>(v, [&](double* t) { fin_mr_final(sc, t[0]); });
+        sy.reduce<1>(v, [&](DF* t) { fin_mr_final(sc, t[0]); });
     }
 }
 
@@ -335,7 +335,7 @@ __device__ __forceinline__ void cgls_body(ConvSmem<R, SEP>& S, const LevelJob& J
             conv_phase<R, SEP, PREC, false>(S, J.u, h, w, nb, bid, epi);
         float v[2] = {a0, a1};
         const double ct2 = J.conv_tol2, d2 = J.disc2;
-        if (!sy.reduce<2>(v, [&](double* t) { fin_resid(sc, t[0], t[1], ct2, d2); }))
+        if (!sy.reduce<2>(v, [&](DF* t) { fin_resid(sc, t[0], t[1], ct2, d2); }))
             return;
     }
     if (J.m <= 0 || volatile_stopped(sc)) return;
@@ -350,7 +350,7 @@ __device__ __forceinline__ void cgls_body(ConvSmem<R, SEP>& S, const LevelJob& J
             a0 = fmaf(z, z, a0);
         });
         float v[1] = {a0};
-        if (!sy.reduce<1>(v, [&](double* t) { fin_cg_s0(sc, t[0]); }))
+        if (!sy.reduce<1>(v, [&](DF* t) { fin_cg_s0(sc, t[0]); }))
             return;
     }
     for (int k = 1; k <= J.m; ++k) {
@@ -365,7 +365,7 @@ __device__ __forceinline__ void cgls_body(ConvSmem<R, SEP>& S, const LevelJob& J
                 a0 = fmaf(z, z, a0);
             });
             float v[1] = {a0};
-            if (!sy.reduce<1>(v, [&](double* t) { fin_cg_q(sc, t[0]); }))
+            if (!sy.reduce<1>(v, [&](DF* t) { fin_cg_q(sc, t[0]); }))
                 return;
         }
         if (volatile_stopped(sc)) break;
@@ -389,7 +389,7 @@ __device__ __forceinline__ void cgls_body(ConvSmem<R, SEP>& S, const LevelJob& J
                     arr = fmaf(r, r, arr);
                 }
             float v[1] = {arr};
-            if (!sy.reduce<1>(v, [&](double* t) { fin_cg_step(sc, t[0]); }))
+            if (!sy.reduce<1>(v, [&](DF* t) { fin_cg_step(sc, t[0]); }))
                 return;
         }
         if (k == J.m || volatile_stopped(sc)) break;
@@ -403,7 +403,7 @@ __device__ __forceinline__ void cgls_body(ConvSmem<R, SEP>& S, const LevelJob& J
                 a0 = fmaf(z, z, a0);
             });
             float v[1] = {a0};
-            if (!sy.reduce<1>(v, [&](double* t) { fin_cg_s(sc, t[0]); }))
+            if (!sy.reduce<1>(v, [&](DF* t) { fin_cg_s(sc, t[0]); }))
                 return;
         }
         if (volatile_stopped(sc)) break;
@@ -416,7 +416,7 @@ __device__ __forceinline__ void cgls_body(ConvSmem<R, SEP>& S, const LevelJob& J
                 for (size_t i = 4 * n4 + threadIdx.x; i < n; i += NTHREADS)
                     IO::st(pv, i, fmaf(b, IO::ld(pv, i), IO::ld(sv, i)));
             float v[1] = {0.f};
-            if (!sy.reduce<1>(v, [&](double*) {})) return;
+            if (!sy.reduce<1>(v, [&](DF*) {})) return;
         }
     }
 }

@@ -88,7 +88,7 @@ __device__ __forceinline__ unsigned int ld_acquire(const unsigned int* p) {
 // Every thread of every block of the job calls this with its NV FP32 values
 // in v (thread-local contributions).  partials holds 2 x nb x NPART
 // double-float slots (8 bytes each).  All sums run in double-float on the FP32
-// pipes; only the job totals handed to finish are FP64.  Returns false if the
+// pipes, and finish receives the job totals as double-float pairs.  Returns false if the
 // job is in error (the caller returns).
 template <int NV, class Finish>
 __device__ __forceinline__ bool grid_reduce(const float (&v)[NV], double* partials, GroupSync* gs,
@@ -139,12 +139,7 @@ __device__ __forceinline__ bool grid_reduce(const float (&v)[NV], double* partia
                 }
                 acc[j] = warp_sum_df(acc[j]);
             }
-            if (threadIdx.x == 0) {
-                double t[NV];
-#pragma unroll
-                for (int j = 0; j < NV; ++j) t[j] = df_to_double(acc[j]);
-                finish(t);
-            }
+            if (threadIdx.x == 0) finish(acc);
         }
     } else {
         DF acc[NV];
@@ -159,12 +154,7 @@ __device__ __forceinline__ bool grid_reduce(const float (&v)[NV], double* partia
         }
         DF tot[NV];
         block_sum_df<NV>(acc, tot);
-        if (threadIdx.x == 0) {
-            double t[NV];
-#pragma unroll
-            for (int j = 0; j < NV; ++j) t[j] = df_to_double(tot[j]);
-            finish(t);
-        }
+        if (threadIdx.x == 0) finish(tot);
     }
     GTRACE(bid == 0 && threadIdx.x == 0, 22);
     __syncthreads();
@@ -303,10 +293,7 @@ __device__ __forceinline__ bool cluster_reduce(const float (&v)[NV], ClusterStat
                     acc[j] = df_add(acc[j], DF{p.x, p.y});
                 }
             }
-            double tot[NV];
-#pragma unroll
-            for (int j = 0; j < NV; ++j) tot[j] = df_to_double(acc[j]);
-            finish(tot);
+            finish(acc);
         }
         GTRACE(rank == 0, 43);
     }

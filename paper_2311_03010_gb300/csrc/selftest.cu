@@ -26,7 +26,7 @@ struct SelftestScratch {
 __global__ void __launch_bounds__(NTHREADS) k_wait_timeout_grid(SelftestScratch* x) {
     const float v[1] = {1.f};
     // one block, but the barrier waits for two arrivals
-    grid_reduce<1>(v, x->partials, &x->gs, 2u, 0u, 0u, [&](double*) {}, SELFTEST_LIMIT_CYCLES);
+    grid_reduce<1>(v, x->partials, &x->gs, 2u, 0u, 0u, [&](DF*) {}, SELFTEST_LIMIT_CYCLES);
 }
 
 __global__ void __launch_bounds__(NTHREADS) k_wait_timeout_cluster(SelftestScratch* x) {
@@ -34,7 +34,7 @@ __global__ void __launch_bounds__(NTHREADS) k_wait_timeout_cluster(SelftestScrat
     cluster_begin(CS, &x->sc, 2u);  // mbarrier expects two arrivals per phase
     const float v[1] = {1.f};
     // a cluster of one block delivers only to itself (nb = 1): one arrival
-    cluster_reduce<1>(v, CS, 0u, 1u, 0u, &x->gs, [&](double*) {}, SELFTEST_LIMIT_CYCLES);
+    cluster_reduce<1>(v, CS, 0u, 1u, 0u, &x->gs, [&](DF*) {}, SELFTEST_LIMIT_CYCLES);
     cluster_end(CS, &x->sc, 0u);
 }
 
