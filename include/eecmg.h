@@ -153,6 +153,18 @@ eecmg_status eecmg_plan_info(eecmg_plan_t plan, int *levels, int *level_w, int *
                              int *iters, size_t *workspace_bytes);
 
 /*
+ * How the persistent solve of level `level` (0 = coarsest) is partitioned
+ * (system design, no counterpart in the paper; see eecmg_tuning): *cluster
+ * receives the blocks per thread-block cluster (0: one cooperative grid),
+ * *blocks the blocks of the solve, *resident the 32x64 tiles each block
+ * keeps in shared memory (0: the vectors stream through L2).  Follows the
+ * current eecmg_tuning; NULL outputs are skipped.  INVALID_ARG for a NULL
+ * plan or a level outside 0 .. levels-1; CUDA if the device query fails.
+ */
+eecmg_status eecmg_level_partition(eecmg_plan_t plan, int level, int *cluster, int *blocks,
+                                   int *resident);
+
+/*
  * Restores one image (Algorithm 2, Step 1 - Step 3).  g_delta and u_out are
  * device buffers of height x width floats; they may alias.  Asynchronous on
  * `stream` (0 = legacy default stream).  Errors: INVALID_ARG (NULL
@@ -307,19 +319,25 @@ eecmg_status eecmg_residual_noalloc(int width, int height, const double *psf, in
 
 /*
  * How the persistent level solves are split over the GPU (system design, no
- * counterpart in the paper).  A level of at most cluster_max_px pixels runs
- * on one thread-block cluster of up to 16 blocks that exchange their sums
- * through distributed shared memory; larger levels run as a cooperative grid
+ * counterpart in the paper).  An MR-II level with FP32 storage, a kernel
+ * radius of at most 5 and at most resident_max_tiles 32x64 tiles runs on one
+ * thread-block cluster whose blocks keep all the solve's vectors in shared
+ * memory for the whole solve (one or two tiles per block, at most 16 blocks).
+ * Otherwise a level of at most cluster_max_px pixels runs on one cluster of
+ * up to 16 blocks that exchange their sums through distributed shared memory
+ * and stream the vectors through L2; larger levels run as a cooperative grid
  * of max(32x64 tiles, pixels / px_per_block) blocks, at most blocks_per_sm
  * per SM.  Process-wide.  Initial values: the GB300 optimum of measured
- * sweeps (cluster_max_px 16384, px_per_block 2048, blocks_per_sm 2),
- * overridable by the environment variables EECMG_CLUSTER_MAX_PX,
- * EECMG_PX_PER_BLOCK, EECMG_BLOCKS_PER_SM read at first use.
+ * sweeps (resident_max_tiles 32, cluster_max_px 16384, px_per_block 2048,
+ * blocks_per_sm 2), overridable by the environment variables
+ * EECMG_RESIDENT_MAX_TILES, EECMG_CLUSTER_MAX_PX, EECMG_PX_PER_BLOCK,
+ * EECMG_BLOCKS_PER_SM read at first use.
  */
 typedef struct {
     long long cluster_max_px; /* >= 0; 0 = never cluster mode                 */
     int px_per_block;         /* 1024 .. 4194304                              */
     int blocks_per_sm;        /* 1 .. 3                                       */
+    int resident_max_tiles;   /* 0 .. 32; 0 = never shared-memory resident     */
 } eecmg_tuning;
 
 eecmg_status eecmg_get_tuning(eecmg_tuning *out);
@@ -335,9 +353,10 @@ eecmg_status eecmg_set_tuning(const eecmg_tuning *t);
 /*
  * Autotuner: times one batched restoration (eecmg_restore_batched) of the n
  * plans on the inputs g[i] (device, plan i's size) under candidate
- * partitions -- a coordinate search over cluster_max_px in {0, 4096, 16384,
- * 65536, 262144}, then px_per_block in {1024, 2048, 4096}, then
- * blocks_per_sm in {1, 2, 3}, from the current setting -- with `reps` timed
+ * partitions -- a coordinate search over resident_max_tiles in {0, 16, 32},
+ * then cluster_max_px in {0, 4096, 16384, 65536, 262144}, then px_per_block
+ * in {1024, 2048, 4096}, then blocks_per_sm in {1, 2, 3}, from the current
+ * setting -- with `reps` timed
  * runs each (CUDA events on `stream`, after two warm-up runs), and keeps the
  * fastest (a candidate must beat the incumbent by 3 %; also written to *best
  * if non-NULL).  The plans are descriptions:

@@ -58,20 +58,20 @@ LevelJob make_job(eecmg_plan_s* P, int l) {
 eecmg_status plan_waves(const std::vector<std::pair<eecmg_plan_s*, int>>& items,
                         std::vector<HostWave>& waves) {
     waves.clear();
-    // (cluster size, instantiation) -> indices of items
-    std::map<std::tuple<int, int, int, int, int>, std::vector<int>> groups;
+    // (cluster size, resident tiles, instantiation) -> indices of items
+    std::map<std::tuple<int, int, int, int, int, int>, std::vector<int>> groups;
     for (int i = 0; i < (int)items.size(); ++i) {
         eecmg_plan_s* P = items[i].first;
         const int l = items[i].second;
         const int cg = P->opt.smoother == EECMG_SMOOTHER_CGLS ? 1 : 0;
         const int bf = P->opt.storage == EECMG_STORAGE_BF16 ? 1 : 0;
-        const int cl = level_shape(P->lv[l].h, P->lv[l].w).cluster;
-        groups[{cl, cg, P->lv[l].sepH, P->opt.precise_conv, bf}].push_back(i);
+        const LevelShape sh = level_shape(P->lv[l].h, P->lv[l].w, P->lv[l].rt, cg, bf);
+        groups[{sh.cluster, sh.resident, cg, P->lv[l].sepH, P->opt.precise_conv, bf}].push_back(i);
     }
     for (auto& kv : groups) {
-        const int cl = std::get<0>(kv.first), cg = std::get<1>(kv.first),
-                  sep = std::get<2>(kv.first), prec = std::get<3>(kv.first),
-                  bf = std::get<4>(kv.first);
+        const int cl = std::get<0>(kv.first), res = std::get<1>(kv.first), cg = std::get<2>(kv.first),
+                  sep = std::get<3>(kv.first), prec = std::get<4>(kv.first),
+                  bf = std::get<5>(kv.first);
         int rt = 0;
         for (int i : kv.second) rt = std::max(rt, items[i].first->lv[items[i].second].rt);
         // clusters are independent: one launch holds them all
@@ -84,9 +84,10 @@ eecmg_status plan_waves(const std::vector<std::pair<eecmg_plan_s*, int>>& items,
         cur.cgls = cg;
         cur.bf16 = bf;
         cur.cluster = cl;
+        cur.resident = res;
         for (int i : kv.second) {
             const LevelPlan& Lp = items[i].first->lv[items[i].second];
-            const int nb = cl > 0 ? cl : std::max(1, std::min(cap, level_shape(Lp.h, Lp.w).blocks));
+            const int nb = cl > 0 ? cl : std::max(1, std::min(cap, level_shape(Lp.h, Lp.w, Lp.rt, cg, bf).blocks));
             if ((long long)cur.blocks + nb > cap && !cur.jobs.empty()) {  // next wave
                 waves.push_back(cur);
                 cur.jobs.clear();
@@ -218,7 +219,7 @@ namespace {
 struct Wave {
     const LevelJob* d_jobs = nullptr;
     const unsigned short* d_block_job = nullptr;
-    int njobs = 0, blocks = 0, rt = 0, sep = 0, prec = 0, cgls = 0, bf16 = 0, cluster = 0;
+    int njobs = 0, blocks = 0, rt = 0, sep = 0, prec = 0, cgls = 0, bf16 = 0, cluster = 0, resident = 0;
 };
 
 struct OpLaunch {
@@ -333,6 +334,7 @@ eecmg_status build_ctx(BatchCtx& C) {
             dw.cgls = w.cgls;
             dw.bf16 = w.bf16;
             dw.cluster = w.cluster;
+            dw.resident = w.resident;
             C.steps[s].push_back(dw);
         }
     e = cudaStreamCreateWithFlags(&C.cap_stream, cudaStreamNonBlocking);
@@ -354,7 +356,7 @@ eecmg_status enqueue_batch(BatchCtx& C, cudaStream_t s) {
         for (const OpLaunch& L : C.step_ops[st]) BCK(launch_ops_batch(L.op, L.d_items, L.n, L.blocks, s));
         for (auto& w : C.steps[st])
             BCK(launch_level_batch(w.d_jobs, w.d_block_job, w.njobs, w.blocks, w.rt, w.sep, w.prec,
-                                   w.cgls, w.bf16, w.cluster, s));
+                                   w.cgls, w.bf16, w.cluster, w.resident, s));
     }
     return EECMG_OK;
 }

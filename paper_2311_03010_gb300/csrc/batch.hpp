@@ -19,6 +19,7 @@ struct HostWave {
     std::vector<unsigned short> block_job;
     int blocks = 0, rt = 0, sep = 0, prec = 0, cgls = 0, bf16 = 0;
     int cluster = 0;  // > 0: one cluster of this many blocks per job
+    int resident = 0; // > 0: the resident MR-II solver, this many tiles per block
 };
 
 // The level-l solve of plan P as a job (buffers from P's workspace).

@@ -194,6 +194,25 @@ __device__ __forceinline__ DF warp_sum_df(DF v) {
     return v;
 }
 
+// Butterfly sums over groups of W lanes (W a power of two <= 32) of NV values
+// at once: each level issues the shuffles of all values, then their adds, so
+// the NV dependency chains overlap.  Same additions, in the same order, as
+// NV separate warp_sum_df calls (zero lanes beyond W would add exact zeros).
+template <int NV, int W = 32>
+__device__ __forceinline__ void warp_sum_df_n(DF (&v)[NV]) {
+#pragma unroll
+    for (int o = W / 2; o > 0; o >>= 1) {
+        DF w[NV];
+#pragma unroll
+        for (int j = 0; j < NV; ++j) {
+            w[j].hi = __shfl_xor_sync(0xffffffffu, v[j].hi, o);
+            w[j].lo = __shfl_xor_sync(0xffffffffu, v[j].lo, o);
+        }
+#pragma unroll
+        for (int j = 0; j < NV; ++j) v[j] = df_add(v[j], w[j]);
+    }
+}
+
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -210,19 +229,24 @@ template <int NV>
 __device__ __forceinline__ void block_sum_df(const DF (&v)[NV], DF (&out)[NV]) {
     __shared__ DF red_df[NV][NTHREADS / 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    DF s[NV];
 #pragma unroll
-    for (int j = 0; j < NV; ++j) {
-        const DF s = warp_sum_df(v[j]);
-        if (lane == 0) red_df[j][warp] = s;
+    for (int j = 0; j < NV; ++j) s[j] = v[j];
+    warp_sum_df_n<NV>(s);
+    if (lane == 0) {
+#pragma unroll
+        for (int j = 0; j < NV; ++j) red_df[j][warp] = s[j];
     }
     __syncthreads();
     if (warp == 0) {
+        DF t[NV];
+#pragma unroll
+        for (int j = 0; j < NV; ++j) t[j] = lane < NTHREADS / 32 ? red_df[j][lane] : DF{0.f, 0.f};
+        warp_sum_df_n<NV, NTHREADS / 32>(t);
 #pragma unroll
         for (int j = 0; j < NV; ++j) {
-            DF s = lane < NTHREADS / 32 ? red_df[j][lane] : DF{0.f, 0.f};
-            s = warp_sum_df(s);
-            out[j].hi = __shfl_sync(0xffffffffu, s.hi, 0);
-            out[j].lo = __shfl_sync(0xffffffffu, s.lo, 0);
+            out[j].hi = __shfl_sync(0xffffffffu, t[j].hi, 0);
+            out[j].lo = __shfl_sync(0xffffffffu, t[j].lo, 0);
         }
     }
     __syncthreads();

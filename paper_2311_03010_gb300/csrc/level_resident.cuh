@@ -1,0 +1,365 @@
+// level_resident.cuh -- the MR-II level solve (Section 2, Lanczos / Givens
+// form) with the whole level held in shared memory: FP32 storage, one
+// thread-block cluster of C <= 16 blocks per solve.  Block b owns T (1 or 2)
+// consecutive 32 x 64 tiles of the level in row-major tile order and keeps
+// all ten solver vectors of its tiles (u, r, v_k, v_{k+1}, H w_k, H w_{k+1},
+// two directions d, two H d) in its shared memory, tile-major, for the whole
+// solve: T x 2048 x 10 floats.  A convolution phase stages each tile with its
+// halo from the blocks that own the halo pixels (distributed shared memory
+// loads after the phase barrier); elementwise phases read and write shared
+// memory only; the reductions are the in-cluster exchange of persistent.cuh.
+// Only u0 and g are read from global memory (start phase) and only u is
+// written back (end).  Entries of partial tiles outside the level are zero
+// at the start and stay zero (every update is a linear combination of zero
+// entries), so the elementwise phases run over whole tiles.
+//
+// Per pixel and per scalar this is the arithmetic of mr2_body; only the
+// partition of the inner products into block sums differs.
+#pragma once
+
+namespace eecmg {
+
+constexpr int RES_TMAX = 2;                 // tiles per block
+constexpr int RES_NVEC = 10;
+constexpr int RES_RMAX = 5;                 // instantiated radii 0..RES_RMAX
+constexpr int TILE_PX = CONV_TH * CONV_TW;  // 2048
+
+__host__ __device__ constexpr size_t res_smem_bytes(int T) {
+    return (size_t)T * TILE_PX * RES_NVEC * sizeof(float);
+}
+
+namespace res_detail {
+
+enum { VU = 0, VR = 1, VV = 2, VAW = 4, VD = 6, VHD = 8 };  // vector slots (VV + 0/1 etc.)
+
+struct ResCtx {
+    float* base;                        // this block's vectors: RES_NVEC x NL floats
+    int T, NL, bid, tiles_x, ntiles, h, w;
+    __device__ __forceinline__ float* vec(int k) const { return base + (size_t)k * NL; }
+};
+
+__device__ __forceinline__ unsigned int cluster_addr(unsigned int shared_addr, unsigned int rank) {
+    unsigned int r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(shared_addr), "r"(rank));
+    return r;
+}
+
+__device__ __forceinline__ float ld_cluster(unsigned int addr) {
+    float v;
+    asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(v) : "r"(addr) : "memory");
+    return v;
+}
+
+constexpr unsigned int RES_NONE = 0xffffffffu;
+
+// Stages vector k's window of tile t (halo R, zero outside the level) into
+// S.in.  nbr[3 (dy + 1) + dx + 1] receives the distributed-shared-memory
+// address of vector k of the tile (dy, dx) away from t in the block that owns
+// it (RES_NONE outside the tile grid); each window pixel then reads its own
+// tile's copy.  Padding entries of partial tiles are zero, so pixels beyond
+// the level inside existing tiles need no test.
+template <int R, bool SEP>
+__device__ __forceinline__ void conv_load_res(ConvSmem<R, SEP>& S, unsigned int (&nbr)[9], const ResCtx& X,
+                                              int k, int t) {
+    constexpr int IW = ConvSmem<R, SEP>::IW;
+    constexpr int NTOT = ConvSmem<R, SEP>::IH * IW;
+    constexpr int ITERS = (NTOT + NTHREADS - 1) / NTHREADS;
+    if (threadIdx.x < 9) {
+        const int dy = (int)threadIdx.x / 3 - 1, dx = (int)threadIdx.x % 3 - 1;
+        const int ty = t / X.tiles_x + dy, tx = t % X.tiles_x + dx;
+        const int tiles_y = X.ntiles / X.tiles_x;
+        unsigned int a = RES_NONE;
+        if (ty >= 0 && ty < tiles_y && tx >= 0 && tx < X.tiles_x) {
+            const int tn = ty * X.tiles_x + tx;
+            const int owner = tn / X.T;
+            const unsigned int local =
+                (unsigned int)__cvta_generic_to_shared(X.base + (size_t)k * X.NL + (size_t)(tn - owner * X.T) * TILE_PX);
+            a = cluster_addr(local, (unsigned int)owner);
+        }
+        nbr[threadIdx.x] = a;
+    }
+    __syncthreads();
+    float vals[ITERS];
+#pragma unroll
+    for (int it = 0; it < ITERS; ++it) {
+        const int i = threadIdx.x + it * NTHREADS;
+        float v = 0.f;
+        if (i < NTOT) {
+            const int ry = i / IW - R, rx = i % IW - R;
+            const int sy = ry < 0 ? 0 : (ry >= CONV_TH ? 2 : 1), sx = rx < 0 ? 0 : (rx >= CONV_TW ? 2 : 1);
+            const unsigned int a = nbr[3 * sy + sx];
+            if (a != RES_NONE)
+                v = ld_cluster(a + 4u * (unsigned int)((ry - (sy - 1) * CONV_TH) * CONV_TW + rx - (sx - 1) * CONV_TW));
+        }
+        vals[it] = v;
+    }
+#pragma unroll
+    for (int it = 0; it < ITERS; ++it) {
+        const int i = threadIdx.x + it * NTHREADS;
+        if (i < NTOT) S.in[i] = vals[it];
+    }
+}
+
+// One convolution phase over this block's tiles: the input is u0 in global
+// memory (GLOBAL) or vector k of the cluster (ZERO: an all-zero input, no
+// loads); the epilogue gets (local index, level index, (C (*) x)(p), x(p)).
+template <int R, bool SEP, bool PREC, bool ZERO, bool GLOBAL, class Epi>
+__device__ __forceinline__ void conv_phase_res(ConvSmem<R, SEP>& S, const ResCtx& X, int k,
+                                               const float* xg, Epi&& epi) {
+    using SM = ConvSmem<R, SEP>;
+    __shared__ unsigned int nbr[9];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int lt = 0; lt < X.T; ++lt) {
+        const int t = X.bid * X.T + lt;
+        if (t >= X.ntiles) break;
+        const int y0 = (t / X.tiles_x) * CONV_TH, x0 = (t % X.tiles_x) * CONV_TW;
+        if (!ZERO) {
+            if (GLOBAL)
+                conv_load<R, SEP, true, float>(S, xg, X.h, X.w, y0, x0);
+            else
+                conv_load_res<R, SEP>(S, nbr, X, k, t);
+            __syncthreads();
+            conv_compute<R, SEP, PREC>(S);
+            __syncthreads();
+        }
+#pragma unroll
+        for (int it = 0; it < CONV_TH / 8; ++it) {
+            const int r = warp + 8 * it, gy = y0 + r;
+#pragma unroll
+            for (int hf = 0; hf < 2; ++hf) {
+                const int c = lane + 32 * hf, gx = x0 + c;
+                if (gy < X.h && gx < X.w) {
+                    const float z = ZERO ? 0.f : S.out[r * SM::PO + c];
+                    const float ctr = ZERO ? 0.f : S.in[(r + R) * SM::IW + c + R];
+                    epi(lt * TILE_PX + r * CONV_TW + c, (size_t)gy * X.w + gx, z, ctr);
+                }
+            }
+        }
+        __syncthreads();  // S is reused by the next tile
+    }
+}
+
+__device__ __forceinline__ float4 lds4(const float* p, int q) {
+    return reinterpret_cast<const float4*>(p)[q];
+}
+__device__ __forceinline__ void sts4(float* p, int q, float4 v) { reinterpret_cast<float4*>(p)[q] = v; }
+
+// MR-II step j on local float4 q; returns the new r.
+__device__ __forceinline__ float4 res_step4(const ResCtx& X, int j, int q, const StepCoef& c) {
+    const int sj = j & 1, sj1 = sj ^ 1;
+    float4 dj = mul4(c.dw, lds4(X.vec(VV + sj), q));
+    float4 hj = mul4(c.dinv, lds4(X.vec(VAW + sj), q));
+    if (j >= 2) {
+        dj = fma4(-c.d1, lds4(X.vec(VD + sj1), q), dj);
+        hj = fma4(-c.d1, lds4(X.vec(VHD + sj1), q), hj);
+    }
+    if (j >= 3) {
+        dj = fma4(-c.d2, lds4(X.vec(VD + sj), q), dj);
+        hj = fma4(-c.d2, lds4(X.vec(VHD + sj), q), hj);
+    }
+    sts4(X.vec(VD + sj), q, dj);
+    sts4(X.vec(VHD + sj), q, hj);
+    sts4(X.vec(VU), q, fma4(c.tau, dj, lds4(X.vec(VU), q)));
+    const float4 rv = fma4(-c.tau, hj, lds4(X.vec(VR), q));
+    sts4(X.vec(VR), q, rv);
+    return rv;
+}
+
+template <int R, bool SEP, bool PREC>
+__device__ __forceinline__ void mr2_res_body(ConvSmem<R, SEP>& S, const LevelJob& J, Scalars* sc,
+                                             const ResCtx& X, LevelSync& sy) {
+    const int n4 = X.NL >> 2;
+    conv_stage_taps<R, SEP>(S, J.taps);
+    {  // every vector zero, then u0
+        float4* b4 = reinterpret_cast<float4*>(X.base);
+        for (int q = threadIdx.x; q < RES_NVEC * n4; q += NTHREADS) b4[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+        __syncthreads();
+        if (!J.zero_start) {
+            float* u = X.vec(VU);
+            for (int lt = 0; lt < X.T; ++lt) {
+                const int t = X.bid * X.T + lt;
+                if (t >= X.ntiles) break;
+                const int y0 = (t / X.tiles_x) * CONV_TH, x0 = (t % X.tiles_x) * CONV_TW;
+                for (int p = threadIdx.x; p < TILE_PX; p += NTHREADS) {
+                    const int gy = y0 + p / CONV_TW, gx = x0 + p % CONV_TW;
+                    if (gy < X.h && gx < X.w) u[lt * TILE_PX + p] = __ldcg(J.u + (size_t)gy * X.w + gx);
+                }
+            }
+        }
+        __syncthreads();
+    }
+
+    // r_0 = g - H u_0, ||r_0||^2, ||g||^2, stopping limit
+    {
+        float a0 = 0.f, a1 = 0.f;
+        float* rv_ = X.vec(VR);
+        auto epi = [&](int li, size_t gi, float z, float) {
+            const float gv = __ldg(J.g + gi);
+            const float rv = gv - z;
+            rv_[li] = rv;
+            a0 = fmaf(rv, rv, a0);
+            a1 = fmaf(gv, gv, a1);
+        };
+        if (J.zero_start)
+            conv_phase_res<R, SEP, PREC, true, true>(S, X, 0, J.u, epi);
+        else
+            conv_phase_res<R, SEP, PREC, false, true>(S, X, 0, J.u, epi);
+        float v[2] = {a0, a1};
+        const double ct2 = J.conv_tol2, d2 = J.disc2;
+        if (!sy.reduce<2>(v, [&](DF* t) { fin_resid(sc, t[0], t[1], ct2, d2); })) return;
+    }
+    if (J.m <= 0 || volatile_stopped(sc)) return;  // u is still u0 in global memory
+
+    // v_1 = H r_0, ||v_1||, <v_1, r_0>
+    {
+        float a0 = 0.f, a1 = 0.f;
+        float* v1 = X.vec(VV + 1);
+        conv_phase_res<R, SEP, PREC, false, false>(S, X, VR, nullptr,
+                                                   [&](int li, size_t, float z, float ctr) {
+                                                       v1[li] = z;
+                                                       a0 = fmaf(z, z, a0);
+                                                       a1 = fmaf(z, ctr, a1);
+                                                   });
+        float v[2] = {a0, a1};
+        if (!sy.reduce<2>(v, [&](DF* t) { fin_mr_v1(sc, t[0], t[1]); })) return;
+    }
+
+    for (int k = 1; k <= J.m; ++k) {
+        if (volatile_stopped(sc)) break;
+        const int sk = k & 1, sk1 = sk ^ 1;
+        // phase A: H w_k = H v_k / ||v_k||, alpha_k = <H w_k, w_k>
+        TRACE(X.bid, 10);
+        {
+            const float scale = vldf(&sc->f_scale);
+            float a0 = 0.f;
+            float* aw = X.vec(VAW + sk);
+            conv_phase_res<R, SEP, PREC, false, false>(S, X, VV + sk, nullptr,
+                                                       [&](int li, size_t, float z, float ctr) {
+                                                           const float hz = z * scale;
+                                                           aw[li] = hz;
+                                                           a0 = fmaf(hz, ctr, a0);
+                                                       });
+            float v[1] = {a0};
+            TRACE(X.bid, 11);
+            if (!sy.reduce<1>(v, [&](DF* t) { fin_mr_a(sc, t[0]); })) return;
+        }
+        TRACE(X.bid, 12);
+        // phase B: pending step k-1, v_{k+1}, stopping rules, rotation of column k
+        {
+            const bool step = k >= 2;
+            const StepCoef c = step_coef(sc);
+            const float ca = vldf(&sc->f_ca), ca_lo = vldf(&sc->f_ca_lo);
+            const float cb = step ? vldf(&sc->f_cb) : 0.f, cb_lo = step ? vldf(&sc->f_cb_lo) : 0.f;
+            float arr = 0.f, avv = 0.f, avr = 0.f;
+            const int j = k - 1, sj = j & 1, sj1 = sj ^ 1;  // sj == sk1
+            for (int q = threadIdx.x; q < n4; q += NTHREADS) {
+                const float4 vk = lds4(X.vec(VV + sk), q), awk = lds4(X.vec(VAW + sk), q);
+                const float4 rr = lds4(X.vec(VR), q);
+                float4 vj = make_float4(0.f, 0.f, 0.f, 0.f), awj = vj, uu = vj;
+                float4 dA = vj, hA = vj, dB = vj, hB = vj;
+                if (step) {
+                    vj = lds4(X.vec(VV + sj), q);
+                    awj = lds4(X.vec(VAW + sj), q);
+                    uu = lds4(X.vec(VU), q);
+                    if (j >= 2) {
+                        dA = lds4(X.vec(VD + sj1), q);
+                        hA = lds4(X.vec(VHD + sj1), q);
+                    }
+                    if (j >= 3) {
+                        dB = lds4(X.vec(VD + sj), q);
+                        hB = lds4(X.vec(VHD + sj), q);
+                    }
+                }
+                float4 rv = rr;
+                if (step) {  // step j = k - 1 (the operation order of mr_step4)
+                    float4 dj = mul4(c.dw, vj);
+                    float4 hj = mul4(c.dinv, awj);
+                    if (j >= 2) {
+                        dj = fma4(-c.d1, dA, dj);
+                        hj = fma4(-c.d1, hA, hj);
+                    }
+                    if (j >= 3) {
+                        dj = fma4(-c.d2, dB, dj);
+                        hj = fma4(-c.d2, hB, hj);
+                    }
+                    sts4(X.vec(VD + sj), q, dj);
+                    sts4(X.vec(VHD + sj), q, hj);
+                    sts4(X.vec(VU), q, fma4(c.tau, dj, uu));
+                    rv = fma4(-c.tau, hj, rr);
+                    sts4(X.vec(VR), q, rv);
+                    arr = dot4(rv, rv, arr);
+                }
+                float4 vn = fma4(-ca_lo, vk, fma4(-ca, vk, awk));
+                if (step) vn = fma4(-cb_lo, vj, fma4(-cb, vj, vn));
+                sts4(X.vec(VV + sk1), q, vn);
+                avv = dot4(vn, vn, avv);
+                avr = dot4(vn, rv, avr);
+            }
+            float v[3] = {arr, avv, avr};
+            TRACE(X.bid, 13);
+            if (!sy.reduce<3>(v, [&](DF* t) { fin_mr_b(sc, k, t[0], t[1], t[2]); })) return;
+        }
+        TRACE(X.bid, 14);
+    }
+
+    // the step decided last (breakdown-with-step or the schedule's end)
+    const int st = volatile_stopped(sc);
+    const int j = *(volatile const int*)&sc->iters;
+    if ((st == 0 || st == 4) && j >= 1) {
+        const StepCoef c = step_coef(sc);
+        float arr = 0.f;
+        for (int q = threadIdx.x; q < n4; q += NTHREADS) {
+            const float4 rv = res_step4(X, j, q, c);
+            arr = dot4(rv, rv, arr);
+        }
+        float v[1] = {arr};
+        if (!sy.reduce<1>(v, [&](DF* t) { fin_mr_final(sc, t[0]); })) return;
+    }
+    // u back to global memory
+    const float* u = X.vec(VU);
+    for (int lt = 0; lt < X.T; ++lt) {
+        const int t = X.bid * X.T + lt;
+        if (t >= X.ntiles) break;
+        const int y0 = (t / X.tiles_x) * CONV_TH, x0 = (t % X.tiles_x) * CONV_TW;
+        for (int p = threadIdx.x; p < TILE_PX; p += NTHREADS) {
+            const int gy = y0 + p / CONV_TW, gx = x0 + p % CONV_TW;
+            if (gy < X.h && gx < X.w) J.u[(size_t)gy * X.w + gx] = u[lt * TILE_PX + p];
+        }
+    }
+}
+
+}  // namespace res_detail
+
+// One resident MR-II solve per cluster of LL.cluster blocks, LL.resident
+// tiles per block; dynamic shared memory res_smem_bytes(LL.resident).
+template <int R, bool SEP, bool PREC>
+__global__ void __launch_bounds__(NTHREADS, 1) k_level_mr2_res(LevelLaunch LL) {
+    using namespace res_detail;
+#ifdef EECMG_TRACE
+    trace_reset();
+#endif
+    __shared__ ConvSmem<R, SEP> S;
+    __shared__ LevelJob sJ;
+    __shared__ ClusterState CS;
+    extern __shared__ float4 res_smem[];
+    if (threadIdx.x == 0) sJ = LL.jobs ? LL.jobs[LL.block_job[blockIdx.x]] : LL.job;
+    __syncthreads();
+    const LevelJob& J = sJ;
+    const unsigned int nb = LL.jobs ? (unsigned int)J.nblocks : gridDim.x;
+    const unsigned int bid = LL.jobs ? blockIdx.x - (unsigned int)J.block0 : blockIdx.x;
+    float* base = reinterpret_cast<float*>(res_smem);
+    cluster_begin(CS, J.sc, nb);  // ends with a cluster barrier (every block's mbarrier ready)
+    const int tiles_x = (J.w + CONV_TW - 1) / CONV_TW, tiles_y = (J.h + CONV_TH - 1) / CONV_TH;
+    const ResCtx X{base, LL.resident, LL.resident * TILE_PX, (int)bid, tiles_x,
+                   tiles_x * tiles_y, J.h, J.w};
+    LevelSync sy{nullptr, J.gs, nb, bid, &CS, true, 0u};
+    TRACE(bid, 1);
+    mr2_res_body<R, SEP, PREC>(S, J, &CS.sc, X, sy);
+    cluster_end(CS, J.sc, bid);
+    TRACE(bid, 2);
+#ifdef EECMG_TRACE
+    trace_flush(bid == 0);
+#endif
+}
+
+}  // namespace eecmg

@@ -50,6 +50,25 @@ int cluster_limit() {
     return lim;
 }
 
+// Largest cluster of the resident solver with T tiles per block on every
+// instantiation (queried on the ones with the most static shared memory).
+int resident_cluster_limit(int T) {
+    static int lim[RES_TMAX + 1] = {-1, -1, -1};
+    if (T < 1 || T > RES_TMAX) return 0;
+    if (lim[T] < 0) {
+        LevelLaunch L;
+        L.resident = T;
+        int m = CLUSTER_MAX;
+        for (int sep = 0; sep < 2; ++sep) {
+            int c = 0;
+            if (dispatch(L, RES_RMAX, sep, 1, 0, 0, LS_RESIDENT_MAX, 0, nullptr, &c) != cudaSuccess) c = 0;
+            m = c < m ? c : m;
+        }
+        lim[T] = m;
+    }
+    return lim[T];
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -62,7 +81,7 @@ int cluster_limit() {
 
 namespace {
 
-std::atomic<int> g_px_per_block{0}, g_blocks_per_sm{0};
+std::atomic<int> g_px_per_block{0}, g_blocks_per_sm{0}, g_resident_max_tiles{0};
 std::atomic<long long> g_cluster_max_px{-1};
 
 void tuning_init() {
@@ -70,10 +89,12 @@ void tuning_init() {
     const char* a = std::getenv("EECMG_PX_PER_BLOCK");
     const char* b = std::getenv("EECMG_CLUSTER_MAX_PX");
     const char* c = std::getenv("EECMG_BLOCKS_PER_SM");
+    const char* d = std::getenv("EECMG_RESIDENT_MAX_TILES");
     Tuning t;
     if (a) t.px_per_block = std::atoi(a);
     if (b) t.cluster_max_px = std::atoll(b);
     if (c) t.blocks_per_sm = std::atoi(c);
+    if (d) t.resident_max_tiles = std::atoi(d);
     set_tuning_raw(t);
 }
 
@@ -81,7 +102,8 @@ void tuning_init() {
 
 bool tuning_valid(const Tuning& t) {
     return t.px_per_block >= 1024 && t.px_per_block <= (1 << 22) && t.cluster_max_px >= 0 &&
-           t.blocks_per_sm >= 1 && t.blocks_per_sm <= 3;
+           t.blocks_per_sm >= 1 && t.blocks_per_sm <= 3 && t.resident_max_tiles >= 0 &&
+           t.resident_max_tiles <= CLUSTER_MAX * RES_TMAX;
 }
 
 void set_tuning_raw(const Tuning& t0) {
@@ -90,6 +112,9 @@ void set_tuning_raw(const Tuning& t0) {
     if (t.px_per_block < 1024) t.px_per_block = 1024;
     if (t.cluster_max_px < 0) t.cluster_max_px = 0;
     t.blocks_per_sm = t.blocks_per_sm < 1 ? 1 : (t.blocks_per_sm > 3 ? 3 : t.blocks_per_sm);
+    const int rmt = CLUSTER_MAX * RES_TMAX;
+    t.resident_max_tiles = t.resident_max_tiles < 0 ? 0 : (t.resident_max_tiles > rmt ? rmt : t.resident_max_tiles);
+    g_resident_max_tiles.store(t.resident_max_tiles);
     g_cluster_max_px.store(t.cluster_max_px);
     g_blocks_per_sm.store(t.blocks_per_sm);
     g_px_per_block.store(t.px_per_block);
@@ -101,6 +126,7 @@ Tuning get_tuning() {
     t.px_per_block = g_px_per_block.load();
     t.cluster_max_px = g_cluster_max_px.load();
     t.blocks_per_sm = g_blocks_per_sm.load();
+    t.resident_max_tiles = g_resident_max_tiles.load();
     return t;
 }
 
@@ -130,8 +156,21 @@ int level_want_blocks(int h, int w) {
 // Levels of at most cluster_max_px pixels run in cluster mode (0: never).
 // Measured on GB300: 128^2 and below gain from the in-GPC exchange; from
 // 256^2 up a 16-SM cluster is throughput-bound and the grid form is faster.
-LevelShape level_shape(int h, int w) {
+LevelShape level_shape(int h, int w, int rt, int cgls, int bf16) {
     LevelShape sh;
+    // MR-II, FP32: levels of at most resident_max_tiles tiles (<= 32) keep their
+    // vectors in the shared memory of one cluster, T = 1 or 2 tiles per block
+    const int tiles = (int)conv_blocks(h, w);
+    if (!cgls && !bf16 && rt >= 0 && rt <= RES_RMAX && tiles <= get_tuning().resident_max_tiles) {
+        const int T = (tiles + CLUSTER_MAX - 1) / CLUSTER_MAX;
+        const int C = (tiles + T - 1) / T;
+        if (T <= RES_TMAX && C <= resident_cluster_limit(T)) {
+            sh.cluster = C;
+            sh.blocks = C;
+            sh.resident = T;
+            return sh;
+        }
+    }
     const int want = level_want_blocks(h, w);
     const size_t n = (size_t)h * w;
     const int lim = n <= (size_t)get_tuning().cluster_max_px ? cluster_limit() : 0;
@@ -149,11 +188,13 @@ cudaError_t launch_level_solve(const LevelJob& J, int rt, int sep, int prec, int
     if (J.h <= 0 || J.w <= 0) return cudaSuccess;
     LevelLaunch L;
     L.job = J;
-    const LevelShape sh = level_shape(J.h, J.w);
+    const LevelShape sh = level_shape(J.h, J.w, rt, cgls, bf16);
     if (sh.cluster > 0) {
         L.cluster = sh.cluster;
+        L.resident = sh.resident;
         if (blocks_used) *blocks_used = sh.blocks;
-        return dispatch(L, rt, sep, prec, cgls, bf16, LS_CLUSTER, sh.blocks, s, nullptr);
+        return dispatch(L, rt, sep, prec, cgls, bf16, sh.resident > 0 ? LS_RESIDENT : LS_CLUSTER,
+                        sh.blocks, s, nullptr);
     }
     int cap = 0;
     cudaError_t e = dispatch(L, rt, sep, prec, cgls, bf16, LS_CAPACITY, 0, nullptr, &cap);
@@ -166,15 +207,16 @@ cudaError_t launch_level_solve(const LevelJob& J, int rt, int sep, int prec, int
 
 cudaError_t launch_level_batch(const LevelJob* d_jobs, const unsigned short* d_block_job, int njobs,
                                int total_blocks, int rt, int sep, int prec, int cgls, int bf16,
-                               int cluster, cudaStream_t s) {
+                               int cluster, int resident, cudaStream_t s) {
     if (njobs <= 0 || total_blocks <= 0) return cudaSuccess;
     LevelLaunch L;
     L.jobs = d_jobs;
     L.block_job = d_block_job;
     L.njobs = njobs;
     L.cluster = cluster;
-    return dispatch(L, rt, sep, prec, cgls, bf16, cluster > 0 ? LS_CLUSTER : LS_COOP, total_blocks, s,
-                    nullptr);
+    L.resident = resident;
+    const int op = resident > 0 ? LS_RESIDENT : (cluster > 0 ? LS_CLUSTER : LS_COOP);
+    return dispatch(L, rt, sep, prec, cgls, bf16, op, total_blocks, s, nullptr);
 }
 
 int level_capacity(int rt, int sep, int prec, int cgls, int bf16) {

@@ -37,25 +37,38 @@ struct LevelLaunch {
     const unsigned short* block_job = nullptr;
     int njobs = 1;
     int cluster = 0;
+    int resident = 0;  // > 0: shared-memory resident MR-II, this many tiles per block
 };
 
-enum LevelOp { LS_COOP = 0, LS_CLUSTER = 1, LS_CAPACITY = 2, LS_CLUSTER_MAX = 3 };
+enum LevelOp {
+    LS_COOP = 0,
+    LS_CLUSTER = 1,
+    LS_CAPACITY = 2,
+    LS_CLUSTER_MAX = 3,
+    LS_RESIDENT = 4,      // cluster launch of the resident solver (L.cluster, L.resident)
+    LS_RESIDENT_MAX = 5,  // largest cluster of the resident solver with L.resident tiles per block
+};
 
 // How a level solve of h x w pixels is partitioned: one cluster of `cluster`
-// blocks (small levels), or a cooperative grid of `blocks` blocks.  Depends
-// only on the level size and the device, so a solve is partitioned (and its
+// blocks (small levels; resident > 0: the shared-memory resident MR-II with
+// that many tiles per block), or a cooperative grid of `blocks` blocks.
+// Depends only on the level size, the kernel radius rt, the solver, the
+// storage type and the device, so a solve of a plan is partitioned (and its
 // sums rounded) the same way alone, batched or served.
 struct LevelShape {
     int cluster = 0;
     int blocks = 0;
+    int resident = 0;
 };
-LevelShape level_shape(int h, int w);
+LevelShape level_shape(int h, int w, int rt, int cgls, int bf16);
 
 // Partition parameters of the level solves (process-wide).
 struct Tuning {
     int px_per_block = 2048;           // grid mode: at least one block per this many pixels (>= 1024)
     long long cluster_max_px = 16384;  // levels with at most this many pixels run in cluster mode
     int blocks_per_sm = 2;             // grid mode: at most this many blocks per SM (1..3)
+    int resident_max_tiles = 32;       // MR-II FP32 levels of at most this many 32 x 64 tiles
+                                       // run shared-memory resident (0 = never, <= 32)
 };
 Tuning get_tuning();
 void set_tuning_raw(const Tuning& t);  // no liveness check (see eecmg_set_tuning)
@@ -64,11 +77,12 @@ bool tuning_valid(const Tuning& t);
 // Launches a device job table: one cooperative grid of total_blocks blocks
 // (cluster == 0; the caller sized the jobs' block ranges to fit
 // co-residency, see level_capacity), or clusters of `cluster` blocks, one per
-// job.  All jobs share the kernel radius rt (>= each job's own),
-// separability, precision, solver and storage.
+// job (resident > 0: the resident MR-II solver, that many tiles per block).
+// All jobs share the kernel radius rt (>= each job's own), separability,
+// precision, solver and storage.
 cudaError_t launch_level_batch(const LevelJob* d_jobs, const unsigned short* d_block_job, int njobs,
                                int total_blocks, int rt, int sep, int prec, int cgls, int bf16,
-                               int cluster, cudaStream_t s);
+                               int cluster, int resident, cudaStream_t s);
 // Co-resident block capacity of the solver instantiation (0 on error).
 int level_capacity(int rt, int sep, int prec, int cgls, int bf16);
 

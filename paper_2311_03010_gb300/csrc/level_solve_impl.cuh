@@ -12,6 +12,8 @@
 // Vectors written inside the launch are read back through L2 (ld.global.cg).
 #pragma once
 
+#include <type_traits>
+
 #include "conv_tile.cuh"
 #include "finish.cuh"
 #include "level_solve.hpp"
@@ -475,6 +477,12 @@ __global__ void __launch_bounds__(NTHREADS, 3) k_level_cgls(LevelLaunch LL) {
     level_kernel<R, SEP, PREC, HT, true>(LL);
 }
 
+}  // namespace eecmg
+
+#include "level_resident.cuh"
+
+namespace eecmg {
+
 template <class K>
 inline cudaError_t coop_launch(K kernel, const LevelLaunch& L, int blocks, cudaStream_t s) {
     LevelLaunch arg = L;
@@ -552,9 +560,67 @@ inline cudaError_t level_op(K kern, int& cap, int& cmax, const LevelLaunch& L, i
     }
 }
 
+// The resident solver of one instantiation: a cluster launch with
+// res_smem_bytes(L.resident) of dynamic shared memory, or the largest cluster
+// it can run as with that much (cached per tile count).
+template <class K>
+inline bool res_attrs(K kern) {
+    const bool ok = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)res_smem_bytes(RES_TMAX)) == cudaSuccess &&
+                    cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
+                        cudaSuccess;
+    if (!ok) cudaGetLastError();
+    return ok;
+}
+
+// attrs: res_attrs() of this kernel (set once per instantiation by the caller)
+template <class K>
+inline cudaError_t res_op(K kern, bool attrs, int (&cmax)[RES_TMAX + 1], const LevelLaunch& L, int op,
+                          int blocks, cudaStream_t s, int* out) {
+    const int T = L.resident;
+    if (T < 1 || T > RES_TMAX) return cudaErrorInvalidValue;
+    cudaLaunchConfig_t cfg = {};
+    cfg.blockDim = dim3(NTHREADS);
+    cfg.dynamicSmemBytes = res_smem_bytes(T);
+    cfg.stream = s;
+    if (op == LS_RESIDENT_MAX) {
+        if (cmax[T] < 0) {
+            int c = 0;
+            cfg.gridDim = dim3(CLUSTER_MAX);
+            if (!attrs || cudaOccupancyMaxPotentialClusterSize(&c, kern, &cfg) != cudaSuccess) {
+                cudaGetLastError();
+                c = 0;
+            }
+            cmax[T] = c < CLUSTER_MAX ? c : CLUSTER_MAX;
+        }
+        if (out) *out = cmax[T];
+        return cudaSuccess;
+    }
+    if (!attrs || L.cluster < 1 || L.cluster > CLUSTER_MAX || blocks % L.cluster) return cudaErrorInvalidValue;
+    cfg.gridDim = dim3(blocks);
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = (unsigned int)L.cluster;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, L);
+}
+
 template <int R, bool SEP, bool PREC, bool CGLS, typename HT>
 cudaError_t launch_level_t(const LevelLaunch& L, int op, int blocks, cudaStream_t s, int* out) {
     static int cap = -1, cmax = -1;  // per instantiation; the library runs on one GPU model
+    if (op == LS_RESIDENT || op == LS_RESIDENT_MAX) {
+        if constexpr (!CGLS && std::is_same<HT, float>::value && R <= RES_RMAX) {
+            static int rmax[RES_TMAX + 1] = {-1, -1, -1};
+            static const bool attrs = res_attrs(k_level_mr2_res<R, SEP, PREC>);  // per instantiation
+            return res_op(k_level_mr2_res<R, SEP, PREC>, attrs, rmax, L, op, blocks, s, out);
+        } else {
+            if (out) *out = 0;
+            return op == LS_RESIDENT_MAX ? cudaSuccess : cudaErrorInvalidValue;
+        }
+    }
     if constexpr (CGLS)
         return level_op(k_level_cgls<R, SEP, PREC, HT>, cap, cmax, L, op, blocks, s, out);
     else

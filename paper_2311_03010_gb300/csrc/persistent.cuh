@@ -137,8 +137,8 @@ __device__ __forceinline__ bool grid_reduce(const float (&v)[NV], double* partia
                     const float2 p = __ldcg(slot + (size_t)threadIdx.x * NPART + j);
                     acc[j] = DF{p.x, p.y};
                 }
-                acc[j] = warp_sum_df(acc[j]);
             }
+            warp_sum_df_n<NV>(acc);
             if (threadIdx.x == 0) finish(acc);
         }
     } else {

@@ -6,6 +6,7 @@
 // restoration enqueues Algorithm 2 on a stream without any host round trip
 // (all Krylov scalars are decided on the device) and is captured once as a
 // CUDA graph, then replayed.
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <cstdio>
@@ -733,6 +734,25 @@ eecmg_status eecmg_plan_info(eecmg_plan_t P, int* levels, int* level_w, int* lev
         if (iters) iters[l] = P->lv[l].m;
     }
     if (workspace_bytes) *workspace_bytes = P->ws_bytes;
+    return EECMG_OK;
+}
+
+eecmg_status eecmg_level_partition(eecmg_plan_t P, int level, int* cluster, int* blocks, int* resident) {
+    if (!P || level < 0 || level >= P->L)
+        return set_error(EECMG_ERR_INVALID_ARG, "eecmg_level_partition: NULL plan or level out of range");
+    const LevelPlan& L = P->lv[level];
+    const int cg = P->opt.smoother == EECMG_SMOOTHER_CGLS ? 1 : 0;
+    const int bf = P->opt.storage == EECMG_STORAGE_BF16 ? 1 : 0;
+    const LevelShape sh = level_shape(L.h, L.w, L.rt, cg, bf);
+    int nb = sh.blocks;
+    if (sh.cluster == 0) {
+        const int cap = level_capacity(L.rt, L.sepH, P->opt.precise_conv, cg, bf);
+        if (cap <= 0) return set_error(EECMG_ERR_CUDA, "eecmg_level_partition: occupancy query failed");
+        nb = std::max(1, std::min(nb, cap));
+    }
+    if (cluster) *cluster = sh.cluster;
+    if (blocks) *blocks = nb;
+    if (resident) *resident = sh.resident;
     return EECMG_OK;
 }
 

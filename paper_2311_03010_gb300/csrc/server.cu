@@ -298,7 +298,7 @@ eecmg_status enqueue_tick(eecmg_server_s* S, const std::vector<Request*>& admitt
         const HostWave& W = waves[w];
         SCK(launch_level_batch((const LevelJob*)(d + jo[w]), (const unsigned short*)(d + bo[w]),
                                (int)W.jobs.size(), W.blocks, W.rt, W.sep, W.prec, W.cgls, W.bf16,
-                               W.cluster, s));
+                               W.cluster, W.resident, s));
     }
     for (const Placed& p : post_l)
         SCK(launch_ops_batch(p.op, (const OpItem*)(d + p.at), p.n, p.blocks, s));

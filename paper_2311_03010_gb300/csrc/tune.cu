@@ -24,6 +24,7 @@ eecmg_tuning to_c(const Tuning& t) {
     c.cluster_max_px = t.cluster_max_px;
     c.px_per_block = t.px_per_block;
     c.blocks_per_sm = t.blocks_per_sm;
+    c.resident_max_tiles = t.resident_max_tiles;
     return c;
 }
 
@@ -32,6 +33,7 @@ Tuning from_c(const eecmg_tuning& c) {
     t.cluster_max_px = c.cluster_max_px;
     t.px_per_block = c.px_per_block;
     t.blocks_per_sm = c.blocks_per_sm;
+    t.resident_max_tiles = c.resident_max_tiles;
     return t;
 }
 
@@ -92,7 +94,7 @@ eecmg_status eecmg_set_tuning(const eecmg_tuning* t) {
     if (!tuning_valid(x))
         return set_error(EECMG_ERR_INVALID_ARG,
                          "eecmg_set_tuning: need 1024 <= px_per_block <= 4194304, cluster_max_px >= 0, "
-                         "1 <= blocks_per_sm <= 3");
+                         "1 <= blocks_per_sm <= 3, 0 <= resident_max_tiles <= 32");
     if (g_live_owners.load() > 0)
         return set_error(EECMG_ERR_BUSY,
                          "eecmg_set_tuning: destroy every plan with a workspace and every server first");
@@ -132,20 +134,23 @@ eecmg_status eecmg_autotune(const eecmg_plan_t* plans, const float* const* g, in
             st = set_error(EECMG_ERR_CUDA, "eecmg_autotune: events");
         float best_ms = 0.f;
         if (st == EECMG_OK) st = time_tuning(R, g, reps, s, cur, &best_ms);
-        // coordinate search: cluster threshold, then pixels per block, then blocks per SM
+        // coordinate search: resident threshold, cluster threshold, pixels per
+        // block, then blocks per SM
+        const int rmt[] = {0, 16, 32};
         const long long cmax[] = {0, 4096, 16384, 65536, 262144};
         const int ppb[] = {1024, 2048, 4096};
         const int bps[] = {1, 2, 3};
-        for (int axis = 0; axis < 3 && st == EECMG_OK; ++axis) {
-            const int nc = axis == 0 ? 5 : 3;
+        for (int axis = 0; axis < 4 && st == EECMG_OK; ++axis) {
+            const int nc = axis == 1 ? 5 : 3;  // rmt, ppb and bps have 3 candidates
             Tuning base = cur;
             for (int c = 0; c < nc && st == EECMG_OK; ++c) {
                 Tuning t = base;
-                if (axis == 0) t.cluster_max_px = cmax[c];
-                if (axis == 1) t.px_per_block = ppb[c];
-                if (axis == 2) t.blocks_per_sm = bps[c];
+                if (axis == 0) t.resident_max_tiles = rmt[c];
+                if (axis == 1) t.cluster_max_px = cmax[c];
+                if (axis == 2) t.px_per_block = ppb[c];
+                if (axis == 3) t.blocks_per_sm = bps[c];
                 if (t.cluster_max_px == base.cluster_max_px && t.px_per_block == base.px_per_block &&
-                    t.blocks_per_sm == base.blocks_per_sm)
+                    t.blocks_per_sm == base.blocks_per_sm && t.resident_max_tiles == base.resident_max_tiles)
                     continue;  // already timed
                 float ms = 0.f;
                 st = time_tuning(R, g, reps, s, t, &ms);

@@ -58,7 +58,7 @@ class eecmg_options(ctypes.Structure):
 
 class eecmg_tuning(ctypes.Structure):
     _fields_ = [("cluster_max_px", ctypes.c_longlong), ("px_per_block", ctypes.c_int),
-                ("blocks_per_sm", ctypes.c_int)]
+                ("blocks_per_sm", ctypes.c_int), ("resident_max_tiles", ctypes.c_int)]
 
 
 class eecmg_kernel_stat(ctypes.Structure):
@@ -87,6 +87,7 @@ _SIGS = {
     "eecmg_batch_info": [ctypes.POINTER(_VP), _I, _PI],
     "eecmg_restore_batched_host": [ctypes.POINTER(_VP), ctypes.POINTER(_VP), ctypes.POINTER(_VP), _I,
                                    _VP],
+    "eecmg_level_partition": [_VP, _I, _PI, _PI, _PI],
     "eecmg_plan_profile": [_VP, _I],
     "eecmg_plan_profile_read": [_VP, ctypes.POINTER(eecmg_kernel_stat), _I, _PI],
     "eecmg_apply_H": [_VP, _I, _VP, _VP, _I, _VP],
@@ -247,6 +248,13 @@ def eecmg_plan_stats(plan):
     return list(it), list(res)
 
 
+def eecmg_level_partition(plan, level):
+    """(cluster, blocks, resident) of the level's persistent solve."""
+    c, b, r = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _call("eecmg_level_partition", plan, int(level), ctypes.byref(c), ctypes.byref(b), ctypes.byref(r))
+    return c.value, b.value, r.value
+
+
 def eecmg_plan_profile(plan, enable=1):
     _call("eecmg_plan_profile", plan, int(enable))
 
@@ -302,7 +310,7 @@ def eecmg_residual_noalloc(width, height, psf, g, u, r, norms, stream=None):
 
 def _tuning_dict(t):
     return {"cluster_max_px": t.cluster_max_px, "px_per_block": t.px_per_block,
-            "blocks_per_sm": t.blocks_per_sm}
+            "blocks_per_sm": t.blocks_per_sm, "resident_max_tiles": t.resident_max_tiles}
 
 
 def eecmg_restore_batched_host(plans, g_host, u_host, stream=None):
@@ -329,8 +337,8 @@ def eecmg_get_tuning():
     return _tuning_dict(t)
 
 
-def eecmg_set_tuning(cluster_max_px, px_per_block, blocks_per_sm):
-    t = eecmg_tuning(int(cluster_max_px), int(px_per_block), int(blocks_per_sm))
+def eecmg_set_tuning(cluster_max_px, px_per_block, blocks_per_sm, resident_max_tiles=32):
+    t = eecmg_tuning(int(cluster_max_px), int(px_per_block), int(blocks_per_sm), int(resident_max_tiles))
     _call("eecmg_set_tuning", ctypes.byref(t))
 
 

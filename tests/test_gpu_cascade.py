@@ -58,6 +58,55 @@ def test_level_solve(gpu, orc, smoother, psfname, shape, persistent):
     plan.close()
 
 
+@pytest.mark.parametrize("resident", [32, 0])
+@pytest.mark.parametrize("psfname", ["gauss5", "motion7"])
+@pytest.mark.parametrize("shape", [(150, 250), (256, 256), (31, 700), (700, 20), (64, 64), (5, 5)])
+def test_resident_level_solve(gpu, orc, psfname, shape, resident):
+    """MR-II level solves with the level held in the shared memory of one cluster (one or two
+    32 x 64 tiles per block, partial tiles, wide and tall levels, radii 5 and 3) and, with
+    resident_max_tiles = 0, streamed through L2: both stop where the oracle's MR-II stops and
+    stay within the FP32 bar of it."""
+    import gc
+
+    torch, E = gpu
+    from paper_2311_03010_gb300 import synth
+
+    gc.collect()
+    before = E.eecmg_get_tuning()
+    E.eecmg_set_tuning(before["cluster_max_px"], before["px_per_block"], before["blocks_per_sm"],
+                       resident)
+    plan = None
+    try:
+        psf = synth.gaussian_psf(2.0, 5) if psfname == "gauss5" else synth.motion_psf(7, 60.0)
+        h, w = shape
+        rng = np.random.default_rng(80)
+        g = (orc.apply_H(psf, synth.synthetic_image(h, w, 81)) + rng.normal(0, 1.0, shape)).astype(np.float32)
+        u0 = rng.uniform(0, 255, shape).astype(np.float32)
+        plan = E.Plan(w, h, 1, psf)
+        cl, nb, res = E.eecmg_level_partition(plan.handle, 0)
+        tiles = ((h + 31) // 32) * ((w + 63) // 64)
+        if resident:
+            assert res == (1 if tiles <= 16 else 2) and cl == nb == -(-tiles // res), (cl, nb, res)
+        else:
+            assert res == 0
+        # a 5 x 5 level under an 11 x 11 PSF: past 3 iterations the FP64 iterate itself moves
+        # by 1e-4 under 1e-7 changes of g (it grows to 30x the data by iteration 12)
+        for m in ((1, 3) if h * w < 64 else (1, 3, 12)):
+            ud = dev(torch, u0)
+            E.eecmg_level_solve(plan.handle, 0, dev(torch, g), ud, m)
+            it, res = plan.stats()
+            ref, k, rres = orc.mr2(psf, g.astype(np.float64), u0.astype(np.float64), m,
+                                   conv_tol=orc.CONV_TOL)
+            assert it[0] == k, (m, it, k)
+            assert rel_l2(host(ud), ref) <= FP32_REL, (m, rel_l2(host(ud), ref))
+            assert res[0] == pytest.approx(rres, rel=1e-3, abs=1e-3)
+    finally:
+        if plan is not None:
+            plan.close()
+        gc.collect()
+        E.eecmg_set_tuning(**before)
+
+
 def test_near_scalar_level_stops_like_oracle(gpu, orc):
     """A level whose operator is nearly a multiple of the identity (a coarse level of a narrow
     PSF): the Lanczos update cancels to ~1e-4 of H w, so single-float coefficients would stall

@@ -49,9 +49,13 @@ def test_set_tuning_is_refused_while_a_plan_owns_a_workspace(gpu, restore_defaul
     with pytest.raises(E.EecmgError) as ei:
         E.eecmg_set_tuning(t["cluster_max_px"], 512, t["blocks_per_sm"])
     assert ei.value.status == EECMG_ERR_INVALID_ARG
+    with pytest.raises(E.EecmgError) as ei:
+        E.eecmg_set_tuning(t["cluster_max_px"], t["px_per_block"], t["blocks_per_sm"], 33)
+    assert ei.value.status == EECMG_ERR_INVALID_ARG
 
 
-@pytest.mark.parametrize("tuning", [(0, 1024, 2), (262144, 4096, 1), (65536, 2048, 3)])
+@pytest.mark.parametrize("tuning", [(0, 1024, 2, 0), (262144, 4096, 1, 8), (65536, 2048, 3, 32),
+                                    (16384, 2048, 2, 0)])
 def test_other_partitions_match_the_oracle_and_stay_bitwise_batched(gpu, orc, restore_default_tuning,
                                                                    tuning):
     torch, E = gpu
@@ -93,6 +97,7 @@ def test_autotune_picks_a_valid_partition(gpu, restore_default_tuning):
     assert best == E.eecmg_get_tuning()
     assert best["cluster_max_px"] in (0, 4096, 16384, 65536, 262144)
     assert best["px_per_block"] in (1024, 2048, 4096) and best["blocks_per_sm"] in (1, 2, 3)
+    assert best["resident_max_tiles"] in (0, 16, 32)
     # with a plan alive the tuner refuses
     full = E.Plan(64, 64, 3, synth.gaussian_psf(1.5, 4))
     with pytest.raises(E.EecmgError) as ei:
