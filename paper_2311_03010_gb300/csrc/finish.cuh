@@ -85,18 +85,20 @@ __device__ __forceinline__ void fin_mr_a(Scalars* sc, DF hv) {
 __device__ __forceinline__ void fin_mr_b(Scalars* sc, int k, DF rr, DF vv, DF vr) {
     const bool step = k >= 2;
     if (step) {
-        sc->rr = df_to_double(rr);
         if (!df_finite(rr)) {
             sc->stopped = 3;
+            sc->rr = df_to_double(rr);
             return;
         }
         if (df_le(rr, sc->lim2d)) {  // stopping rule on ||r_{k-1}||, before iteration k
             sc->stopped = 1;
+            sc->rr = df_to_double(rr);
             return;
         }
     }
     if (!df_finite(vv)) {
         sc->stopped = 3;
+        if (step) sc->rr = df_to_double(rr);
         return;
     }
     const DF inv_new = vv.hi > 0.f ? df_rsqrt(vv) : df_zero();
@@ -111,6 +113,7 @@ __device__ __forceinline__ void fin_mr_b(Scalars* sc, int k, DF rr, DF vv, DF vr
     const DF rho2 = df_add2(df_mul(a2, a2), vv);  // rho = hypot(a2, ||v_{k+1}||)
     if (!(rho2.hi > 0.f) || !df_finite(rho2)) {
         sc->stopped = rho2.hi > 0.f ? 3 : 2;
+        if (step) sc->rr = df_to_double(rr);
         return;
     }
     const DF inv_rho = df_rsqrt(rho2);
@@ -142,6 +145,8 @@ __device__ __forceinline__ void fin_mr_b(Scalars* sc, int k, DF rr, DF vv, DF vr
     sc->f_tau = tau.hi;
     sc->f_scale = inv_new.hi;
     if (!(nrm_new.hi > 0.f)) sc->stopped = 4;  // Krylov space exhausted: step k is the last
+    // the FP64 copy for the host last: its conversion is off the coefficients' path
+    if (step) sc->rr = df_to_double(rr);
 }
 
 __device__ __forceinline__ void fin_mr_final(Scalars* sc, DF rr) {
@@ -174,9 +179,9 @@ __device__ __forceinline__ void fin_cg_q(Scalars* sc, DF qq) {
 
 // CGLS: after u += alpha p, r -= alpha q: the stopping rule on the new residual.
 __device__ __forceinline__ void fin_cg_step(Scalars* sc, DF rr) {
-    sc->rr = df_to_double(rr);
     if (!df_finite(rr)) sc->stopped = 3;
     else if (df_le(rr, sc->lim2d)) sc->stopped = 1;
+    sc->rr = df_to_double(rr);
 }
 
 // CGLS: s = H^T r, beta = <s, s> / gamma.

@@ -50,6 +50,12 @@ __device__ __forceinline__ float ld_cluster(unsigned int addr) {
     return v;
 }
 
+__device__ __forceinline__ float ld_local(unsigned int addr) {
+    float v;
+    asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(addr) : "memory");
+    return v;
+}
+
 constexpr unsigned int RES_NONE = 0xffffffffu;
 
 // Stages vector k's window of tile t (halo R, zero outside the level) into
@@ -79,6 +85,9 @@ __device__ __forceinline__ void conv_load_res(ConvSmem<R, SEP>& S, unsigned int 
         nbr[threadIdx.x] = a;
     }
     __syncthreads();
+    // the tile itself is this block's (plain shared-memory loads when R = 0)
+    const unsigned int own = (unsigned int)__cvta_generic_to_shared(
+        X.base + (size_t)k * X.NL + (size_t)(t - X.bid * X.T) * TILE_PX);
     float vals[ITERS];
 #pragma unroll
     for (int it = 0; it < ITERS; ++it) {
@@ -87,9 +96,13 @@ __device__ __forceinline__ void conv_load_res(ConvSmem<R, SEP>& S, unsigned int 
         if (i < NTOT) {
             const int ry = i / IW - R, rx = i % IW - R;
             const int sy = ry < 0 ? 0 : (ry >= CONV_TH ? 2 : 1), sx = rx < 0 ? 0 : (rx >= CONV_TW ? 2 : 1);
-            const unsigned int a = nbr[3 * sy + sx];
-            if (a != RES_NONE)
-                v = ld_cluster(a + 4u * (unsigned int)((ry - (sy - 1) * CONV_TH) * CONV_TW + rx - (sx - 1) * CONV_TW));
+            const unsigned int off = 4u * (unsigned int)((ry - (sy - 1) * CONV_TH) * CONV_TW + rx - (sx - 1) * CONV_TW);
+            if constexpr (R == 0) {
+                v = ld_local(own + off);  // the window is the tile
+            } else {  // one load form for every pixel: no divergence at the window's edges
+                const unsigned int a = nbr[3 * sy + sx];
+                if (a != RES_NONE) v = ld_cluster(a + off);
+            }
         }
         vals[it] = v;
     }
