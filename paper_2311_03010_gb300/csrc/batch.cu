@@ -122,17 +122,22 @@ int place_items(OpGroup& g) {
     return blocks;
 }
 
+// Every coarse level straight from the finest, g_l(a, b) = g_{L-1}(2^j a, 2^j b)
+// with j = L-1-l (the restrictions compose; pure copies, so bitwise the
+// level-by-level chain): one launch for the whole pyramid of every plan.
 void restrict_ops(const std::vector<eecmg_plan_s*>& plans, std::vector<OpGroup>& groups) {
     const size_t base = groups.size();
     for (eecmg_plan_s* P : plans)
-        for (int l = P->L - 1; l > 0; --l) {
+        for (int l = P->L - 2; l >= 0; --l) {
+            const LevelPlan& F = P->lv[P->L - 1];
             OpItem rs;
-            rs.a = P->lv[l].g;
-            rs.w1 = P->lv[l].w;
-            rs.out = P->lv[l - 1].g;
-            rs.h = P->lv[l - 1].h;
-            rs.w = P->lv[l - 1].w;
-            add_op(groups, base + (size_t)(P->L - 1 - l), OP_RESTRICT, rs);
+            rs.a = F.g;
+            rs.w1 = F.w;
+            rs.h2 = 1 << (P->L - 1 - l);  // stride into the finest level
+            rs.out = P->lv[l].g;
+            rs.h = P->lv[l].h;
+            rs.w = P->lv[l].w;
+            add_op(groups, base, OP_RESTRICT, rs);
         }
 }
 

@@ -14,9 +14,11 @@ inline dim3 grid2(int h, int w) { return dim3((w + BX - 1) / BX, (h + BY - 1) / 
 }  // namespace
 
 // g_l(a, b) = g_{l+1}(2a, 2b): the paper's 1-based 2k - 1, per dimension.
+// step = 2^j restricts j levels at once: g_{l}(a, b) = g_{l+j}(2^j a, 2^j b).
 __device__ __forceinline__ void px_restrict(const float* __restrict__ fine, int wf,
-                                            float* __restrict__ coarse, int hc, int wc, int a, int b) {
-    if (a < hc && b < wc) coarse[(size_t)a * wc + b] = fine[(size_t)(2 * a) * wf + 2 * b];
+                                            float* __restrict__ coarse, int hc, int wc, int a, int b,
+                                            int step = 2) {
+    if (a < hc && b < wc) coarse[(size_t)a * wc + b] = fine[(size_t)(step * a) * wf + step * b];
 }
 __global__ void k_restrict(const float* __restrict__ fine, int wf, float* __restrict__ coarse,
                            int hc, int wc) {
@@ -323,7 +325,7 @@ __global__ void __launch_bounds__(BX* BY) k_ops_batch(const OpItem* __restrict__
     const int local = blk - it.block0;
     const int by = local / it.bx, bx = local - by * it.bx;
     const int x = bx * BX + threadIdx.x, y = by * BY + threadIdx.y;
-    if constexpr (OP == OP_RESTRICT) px_restrict(it.a, it.w1, it.out, it.h, it.w, y, x);
+    if constexpr (OP == OP_RESTRICT) px_restrict(it.a, it.w1, it.out, it.h, it.w, y, x, it.h2);
     if constexpr (OP == OP_EXTRAPOLATE) px_extrapolate(it.a, it.h1, it.w1, it.b, it.h2, it.w2, it.out, y, x);
     if constexpr (OP == OP_QUADRATIC) px_quadratic(it.a, it.h1, it.w1, it.out, it.h, it.w, y, x);
     if constexpr (OP == OP_LINEAR) px_linear(it.a, it.h1, it.w1, it.out, it.h, it.w, y, x);
@@ -335,6 +337,14 @@ __global__ void __launch_bounds__(BX* BY) k_ops_batch(const OpItem* __restrict__
         if (y < it.h && x < it.w) it.out[(size_t)y * it.w + x] = OP == OP_ZERO ? 0.f : it.a[(size_t)y * it.w + x];
     }
 }
+
+namespace {
+template <int OP>
+cudaError_t launch_op(const OpItem* d_items, int n, int total_blocks, cudaStream_t s) {
+    k_ops_batch<OP><<<dim3((unsigned int)total_blocks), dim3(BX, BY), 0, s>>>(d_items, n);
+    return cudaGetLastError();
+}
+}  // namespace
 
 cudaError_t launch_restrict(const float* fine, int hf, int wf, float* coarse, int hc, int wc,
                             cudaStream_t s) {
@@ -395,20 +405,18 @@ int op_blocks_x(int w) { return (w + BX - 1) / BX; }
 
 cudaError_t launch_ops_batch(int op, const OpItem* d_items, int n, int total_blocks, cudaStream_t s) {
     if (n <= 0 || total_blocks <= 0) return cudaSuccess;
-    const dim3 g((unsigned int)total_blocks), b(BX, BY);
     switch (op) {
-        case OP_RESTRICT: k_ops_batch<OP_RESTRICT><<<g, b, 0, s>>>(d_items, n); break;
-        case OP_EXTRAPOLATE: k_ops_batch<OP_EXTRAPOLATE><<<g, b, 0, s>>>(d_items, n); break;
-        case OP_QUADRATIC: k_ops_batch<OP_QUADRATIC><<<g, b, 0, s>>>(d_items, n); break;
-        case OP_LINEAR: k_ops_batch<OP_LINEAR><<<g, b, 0, s>>>(d_items, n); break;
-        case OP_SMOOTH: k_ops_batch<OP_SMOOTH><<<g, b, 0, s>>>(d_items, n); break;
-        case OP_DENOISE: k_ops_batch<OP_DENOISE><<<g, b, 0, s>>>(d_items, n); break;
-        case OP_ZERO: k_ops_batch<OP_ZERO><<<g, b, 0, s>>>(d_items, n); break;
-        case OP_COPY: k_ops_batch<OP_COPY><<<g, b, 0, s>>>(d_items, n); break;
-        case OP_PROLONG: k_ops_batch<OP_PROLONG><<<g, b, 0, s>>>(d_items, n); break;
+        case OP_RESTRICT: return launch_op<OP_RESTRICT>(d_items, n, total_blocks, s);
+        case OP_EXTRAPOLATE: return launch_op<OP_EXTRAPOLATE>(d_items, n, total_blocks, s);
+        case OP_QUADRATIC: return launch_op<OP_QUADRATIC>(d_items, n, total_blocks, s);
+        case OP_LINEAR: return launch_op<OP_LINEAR>(d_items, n, total_blocks, s);
+        case OP_SMOOTH: return launch_op<OP_SMOOTH>(d_items, n, total_blocks, s);
+        case OP_DENOISE: return launch_op<OP_DENOISE>(d_items, n, total_blocks, s);
+        case OP_ZERO: return launch_op<OP_ZERO>(d_items, n, total_blocks, s);
+        case OP_COPY: return launch_op<OP_COPY>(d_items, n, total_blocks, s);
+        case OP_PROLONG: return launch_op<OP_PROLONG>(d_items, n, total_blocks, s);
         default: return cudaErrorInvalidValue;
     }
-    return cudaGetLastError();
 }
 
 }  // namespace eecmg
