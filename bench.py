@@ -71,7 +71,7 @@ def make_problems(name):
 
 
 LEVEL_SOLVE_SOURCES = ("common.cuh", "conv_tile.cuh", "finish.cuh", "persistent.cuh",
-                       "level_solve.hpp", "level_solve_impl.cuh", "level_solve.cu")
+                       "level_solve.hpp", "level_solve_impl.cuh", "level_resident.cuh", "level_solve.cu")
 
 
 def level_solve_source_hash():
