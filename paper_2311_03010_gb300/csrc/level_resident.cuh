@@ -116,25 +116,117 @@ __device__ __forceinline__ void conv_load_res(ConvSmem<R, SEP>& S, unsigned int 
 // One convolution phase over this block's tiles: the input is u0 in global
 // memory (GLOBAL) or vector k of the cluster (ZERO: an all-zero input, no
 // loads); the epilogue gets (local index, level index, (C (*) x)(p), x(p)).
+// conv_compute on two staged tiles at once: every thread carries the outputs
+// of both tiles through the same loops (twice the independent chains while a
+// block holds one SM), with the operations of conv_compute per output.
+template <int R, bool SEP, bool PREC>
+__device__ __forceinline__ void conv_compute2(ConvSmem<R, SEP>& A, ConvSmem<R, SEP>& B) {
+    constexpr int IW = ConvSmem<R, SEP>::IW, PT = ConvSmem<R, SEP>::PT, PO = ConvSmem<R, SEP>::PO;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    ConvSmem<R, SEP>* S[2] = {&A, &B};
+    if (SEP) {
+        for (int item = tid; item < 4 * IW; item += NTHREADS) {
+            const int rg = item / IW, c = item - rg * IW;
+            float v[2][8 + 2 * R];
+#pragma unroll
+            for (int s = 0; s < 2; ++s)
+#pragma unroll
+                for (int j = 0; j < 8 + 2 * R; ++j) v[s][j] = S[s]->in[(rg * 8 + j) * IW + c];
+            float acc[2][8];
+#pragma unroll
+            for (int s = 0; s < 2; ++s)
+#pragma unroll
+                for (int i = 0; i < 8; ++i) acc[s][i] = 0.f;
+#pragma unroll
+            for (int d = 0; d < 2 * R + 1; ++d) {
+                const float cd = A.cy[d];
+#pragma unroll
+                for (int s = 0; s < 2; ++s)
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) acc[s][i] = fmaf(cd, v[s][i + d], acc[s][i]);
+            }
+#pragma unroll
+            for (int s = 0; s < 2; ++s)
+#pragma unroll
+                for (int i = 0; i < 8; ++i) S[s]->tmp[(rg * 8 + i) * PT + c] = acc[s][i];
+        }
+        __syncthreads();
+        const int r = lane, cg = warp;
+        float v[2][8 + 2 * R];
+#pragma unroll
+        for (int s = 0; s < 2; ++s)
+#pragma unroll
+            for (int j = 0; j < 8 + 2 * R; ++j) v[s][j] = S[s]->tmp[r * PT + cg * 8 + j];
+        float acc[2][8], lo[2][8], comp[2][8];
+#pragma unroll
+        for (int s = 0; s < 2; ++s)
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                acc[s][i] = 0.f;
+                lo[s][i] = 0.f;
+                comp[s][i] = 0.f;
+            }
+#pragma unroll
+        for (int d = 0; d < 2 * R + 1; ++d) {
+            const float cd = A.cx[d];
+#pragma unroll
+            for (int s = 0; s < 2; ++s)
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    if (PREC) {
+                        const float p = __fmul_rn(cd, v[s][i + d]);
+                        const float pe = fmaf(cd, v[s][i + d], -p);
+                        const float y = __fsub_rn(p, comp[s][i]);
+                        const float t = __fadd_rn(acc[s][i], y);
+                        comp[s][i] = __fsub_rn(__fsub_rn(t, acc[s][i]), y);
+                        acc[s][i] = t;
+                        lo[s][i] = __fadd_rn(lo[s][i], pe);
+                    } else {
+                        acc[s][i] = fmaf(cd, v[s][i + d], acc[s][i]);
+                    }
+                }
+        }
+#pragma unroll
+        for (int s = 0; s < 2; ++s)
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+                S[s]->out[r * PO + cg * 8 + i] =
+                    PREC ? __fadd_rn(acc[s][i], __fsub_rn(lo[s][i], comp[s][i])) : acc[s][i];
+    } else {
+        const int c = tid & 63, rg = tid >> 6;
+        float acc[2][8];
+#pragma unroll
+        for (int s = 0; s < 2; ++s)
+#pragma unroll
+            for (int i = 0; i < 8; ++i) acc[s][i] = 0.f;
+        const int nt = A.ntap;
+        for (int t = 0; t < nt; ++t) {
+            const float wt = A.wt[t];
+            const int off = A.off[t] + (rg * 8) * IW + c;
+#pragma unroll
+            for (int s = 0; s < 2; ++s)
+#pragma unroll
+                for (int i = 0; i < 8; ++i) acc[s][i] = fmaf(wt, S[s]->in[off + i * IW], acc[s][i]);
+        }
+#pragma unroll
+        for (int s = 0; s < 2; ++s)
+#pragma unroll
+            for (int i = 0; i < 8; ++i) S[s]->out[(rg * 8 + i) * PO + c] = acc[s][i];
+    }
+}
+
+// One convolution phase over this block's tiles: the input is u0 in global
+// memory (GLOBAL) or vector k of the cluster (ZERO: an all-zero input, no
+// loads); the epilogue gets (local index, level index, (C (*) x)(p), x(p)).
+// S[0] stages one tile at a time; with two tiles of the cluster's vector
+// both are staged (S[0], S[1]) and computed together.  Only S[0] holds taps.
 template <int R, bool SEP, bool PREC, bool ZERO, bool GLOBAL, class Epi>
-__device__ __forceinline__ void conv_phase_res(ConvSmem<R, SEP>& S, const ResCtx& X, int k,
+__device__ __forceinline__ void conv_phase_res(ConvSmem<R, SEP> (&S)[2], const ResCtx& X, int k,
                                                const float* xg, Epi&& epi) {
     using SM = ConvSmem<R, SEP>;
-    __shared__ unsigned int nbr[9];
+    __shared__ unsigned int nbr[2][9];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int lt = 0; lt < X.T; ++lt) {
-        const int t = X.bid * X.T + lt;
-        if (t >= X.ntiles) break;
-        const int y0 = (t / X.tiles_x) * CONV_TH, x0 = (t % X.tiles_x) * CONV_TW;
-        if (!ZERO) {
-            if (GLOBAL)
-                conv_load<R, SEP, true, float>(S, xg, X.h, X.w, y0, x0);
-            else
-                conv_load_res<R, SEP>(S, nbr, X, k, t);
-            __syncthreads();
-            conv_compute<R, SEP, PREC>(S);
-            __syncthreads();
-        }
+    auto epilogue = [&](const SM& T, int lt, int y0, int x0) {
 #pragma unroll
         for (int it = 0; it < CONV_TH / 8; ++it) {
             const int r = warp + 8 * it, gy = y0 + r;
@@ -142,13 +234,40 @@ __device__ __forceinline__ void conv_phase_res(ConvSmem<R, SEP>& S, const ResCtx
             for (int hf = 0; hf < 2; ++hf) {
                 const int c = lane + 32 * hf, gx = x0 + c;
                 if (gy < X.h && gx < X.w) {
-                    const float z = ZERO ? 0.f : S.out[r * SM::PO + c];
-                    const float ctr = ZERO ? 0.f : S.in[(r + R) * SM::IW + c + R];
+                    const float z = ZERO ? 0.f : T.out[r * SM::PO + c];
+                    const float ctr = ZERO ? 0.f : T.in[(r + R) * SM::IW + c + R];
                     epi(lt * TILE_PX + r * CONV_TW + c, (size_t)gy * X.w + gx, z, ctr);
                 }
             }
         }
-        __syncthreads();  // S is reused by the next tile
+    };
+    const int t0 = X.bid * X.T;
+    if (!ZERO && !GLOBAL && X.T == 2 && t0 + 1 < X.ntiles) {
+        conv_load_res<R, SEP>(S[0], nbr[0], X, k, t0);
+        conv_load_res<R, SEP>(S[1], nbr[1], X, k, t0 + 1);
+        __syncthreads();
+        conv_compute2<R, SEP, PREC>(S[0], S[1]);
+        __syncthreads();
+        for (int lt = 0; lt < 2; ++lt)
+            epilogue(S[lt], lt, ((t0 + lt) / X.tiles_x) * CONV_TH, ((t0 + lt) % X.tiles_x) * CONV_TW);
+        __syncthreads();
+        return;
+    }
+    for (int lt = 0; lt < X.T; ++lt) {
+        const int t = t0 + lt;
+        if (t >= X.ntiles) break;
+        const int y0 = (t / X.tiles_x) * CONV_TH, x0 = (t % X.tiles_x) * CONV_TW;
+        if (!ZERO) {
+            if (GLOBAL)
+                conv_load<R, SEP, true, float>(S[0], xg, X.h, X.w, y0, x0);
+            else
+                conv_load_res<R, SEP>(S[0], nbr[0], X, k, t);
+            __syncthreads();
+            conv_compute<R, SEP, PREC>(S[0]);
+            __syncthreads();
+        }
+        epilogue(S[0], lt, y0, x0);
+        __syncthreads();  // S[0] is reused by the next tile
     }
 }
 
@@ -179,10 +298,10 @@ __device__ __forceinline__ float4 res_step4(const ResCtx& X, int j, int q, const
 }
 
 template <int R, bool SEP, bool PREC>
-__device__ __forceinline__ void mr2_res_body(ConvSmem<R, SEP>& S, const LevelJob& J, Scalars* sc,
+__device__ __forceinline__ void mr2_res_body(ConvSmem<R, SEP> (&S)[2], const LevelJob& J, Scalars* sc,
                                              const ResCtx& X, LevelSync& sy) {
     const int n4 = X.NL >> 2;
-    conv_stage_taps<R, SEP>(S, J.taps);
+    conv_stage_taps<R, SEP>(S[0], J.taps);
     {  // every vector zero, then u0
         float4* b4 = reinterpret_cast<float4*>(X.base);
         for (int q = threadIdx.x; q < RES_NVEC * n4; q += NTHREADS) b4[q] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -351,7 +470,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_level_mr2_res(LevelLaunch LL) {
 #ifdef EECMG_TRACE
     trace_reset();
 #endif
-    __shared__ ConvSmem<R, SEP> S;
+    __shared__ ConvSmem<R, SEP> S[2];
     __shared__ LevelJob sJ;
     __shared__ ClusterState CS;
     extern __shared__ float4 res_smem[];
