@@ -180,8 +180,8 @@ __device__ __forceinline__ void grid_exit(GroupSync* gs, unsigned int nb) {
 // A reduction then never leaves the GPC: every block writes its FP64 block
 // sums into a slot of every block's shared memory (distributed shared
 // memory) and arrives on each block's mbarrier; each block waits on its own
-// mbarrier (bounded), sums the slots in rank order and runs the scalar
-// update itself.  All blocks hold identical scalar state (the same sums in
+// mbarrier (bounded), sums the slots in a fixed order (rank order up to 4
+// blocks, a butterfly beyond) and runs the scalar update itself.  All blocks hold identical scalar state (the same sums in
 // the same order), so no broadcast is needed and one barrier ends a phase.
 // ---------------------------------------------------------------------------
 
@@ -271,31 +271,51 @@ __device__ __forceinline__ bool cluster_reduce(const float (&v)[NV], ClusterStat
         asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(bar)
                      : "memory");
     }
-    if (threadIdx.x == 0) {
+    if (threadIdx.x < 32) {  // warp 0: every lane waits (bounded) and acquires, lane q reads block q's sums
         const unsigned int bar = smem_u32(&cs.mbar);
         const long long t0 = clock64();
+        bool ok = true;
         while (!mbar_test_parity(bar, par)) {
             if (clock64() - t0 > limit) {
-                cs.err = 1;
-                atomicExch(&gs->err, 1);
+                ok = false;
                 break;
             }
         }
-        GTRACE(rank == 0, 42);
-        if (!cs.err) {
+        ok = __all_sync(0xffffffffu, ok);
+        GTRACE(rank == 0 && threadIdx.x == 0, 42);
+        if (!ok) {
+            if (threadIdx.x == 0) {
+                cs.err = 1;
+                atomicExch(&gs->err, 1);
+            }
+        } else if (nb <= 4) {  // a few slots: lane 0 adds them in rank order
+            if (threadIdx.x == 0) {
+                DF acc[NV];
+#pragma unroll
+                for (int j = 0; j < NV; ++j) acc[j] = DF{0.f, 0.f};
+                for (unsigned int q = 0; q < nb; ++q) {
+#pragma unroll
+                    for (int j = 0; j < NV; ++j) {
+                        const float2 p = *reinterpret_cast<const float2*>(&cs.slots[par][q][j]);
+                        acc[j] = df_add(acc[j], DF{p.x, p.y});
+                    }
+                }
+                finish(acc);
+            }
+        } else {  // lane q holds block q's sums; a 16-lane butterfly adds them
             DF acc[NV];
 #pragma unroll
-            for (int j = 0; j < NV; ++j) acc[j] = DF{0.f, 0.f};
-            for (unsigned int q = 0; q < nb; ++q) {
-#pragma unroll
-                for (int j = 0; j < NV; ++j) {
-                    const float2 p = *reinterpret_cast<const float2*>(&cs.slots[par][q][j]);
-                    acc[j] = df_add(acc[j], DF{p.x, p.y});
+            for (int j = 0; j < NV; ++j) {
+                acc[j] = DF{0.f, 0.f};
+                if (threadIdx.x < nb) {
+                    const float2 p = *reinterpret_cast<const float2*>(&cs.slots[par][threadIdx.x][j]);
+                    acc[j] = DF{p.x, p.y};
                 }
             }
-            finish(acc);
+            warp_sum_df_n<NV, CLUSTER_MAX>(acc);  // lanes >= nb add zeros
+            if (threadIdx.x == 0) finish(acc);
         }
-        GTRACE(rank == 0, 43);
+        GTRACE(rank == 0 && threadIdx.x == 0, 43);
     }
     __syncthreads();
     return cs.err == 0;
