@@ -242,9 +242,18 @@ struct BatchCtx {
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t gexec = nullptr;
     size_t graph_nodes = 0;  // kernel nodes of one batched restoration
+    // Steps 0 and 1 (the two levels solved from zero, Algorithm 2) run as two
+    // branches of the graph when every job of both is a resident solve: such
+    // a solve touches only its own level's g, u, scalars and sync words.
+    bool fork01 = false;
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     ~BatchCtx() {
         if (gexec) cudaGraphExecDestroy(gexec);
         if (cap_stream) cudaStreamDestroy(cap_stream);
+        if (side) cudaStreamDestroy(side);
+        if (ev_fork) cudaEventDestroy(ev_fork);
+        if (ev_join) cudaEventDestroy(ev_join);
         if (dmem) cudaFree(dmem);
     }
 };
@@ -344,6 +353,20 @@ eecmg_status build_ctx(BatchCtx& C) {
         }
     e = cudaStreamCreateWithFlags(&C.cap_stream, cudaStreamNonBlocking);
     if (e != cudaSuccess) return set_error(EECMG_ERR_CUDA, "eecmg_restore_batched: stream");
+    C.fork01 = maxL >= 2;
+    for (auto* P : C.plans) {
+        const int cg = P->opt.smoother == EECMG_SMOOTHER_CGLS ? 1 : 0;
+        const int bf = P->opt.storage == EECMG_STORAGE_BF16 ? 1 : 0;
+        bool ok = P->L >= 2 && P->opt.prolong == EECMG_PROLONG_EECMG;
+        for (int l = 0; l < 2 && ok; ++l)
+            ok = level_shape(P->lv[l].h, P->lv[l].w, P->lv[l].rt, cg, bf).resident > 0;
+        C.fork01 = C.fork01 && ok;
+    }
+    if (C.fork01 &&
+        (cudaStreamCreateWithFlags(&C.side, cudaStreamNonBlocking) != cudaSuccess ||
+         cudaEventCreateWithFlags(&C.ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+         cudaEventCreateWithFlags(&C.ev_join, cudaEventDisableTiming) != cudaSuccess))
+        return set_error(EECMG_ERR_CUDA, "eecmg_restore_batched: side stream");
     return EECMG_OK;
 }
 
@@ -355,13 +378,30 @@ eecmg_status build_ctx(BatchCtx& C) {
                                                  ": " + cudaGetErrorString(e_));               \
     } while (0)
 
+eecmg_status enqueue_step(BatchCtx& C, int st, cudaStream_t s) {
+    for (const OpLaunch& L : C.step_ops[st]) BCK(launch_ops_batch(L.op, L.d_items, L.n, L.blocks, s));
+    for (auto& w : C.steps[st])
+        BCK(launch_level_batch(w.d_jobs, w.d_block_job, w.njobs, w.blocks, w.rt, w.sep, w.prec, w.cgls,
+                               w.bf16, w.cluster, w.resident, s));
+    return EECMG_OK;
+}
+
 eecmg_status enqueue_batch(BatchCtx& C, cudaStream_t s) {
     for (const OpLaunch& L : C.restrict_ops) BCK(launch_ops_batch(L.op, L.d_items, L.n, L.blocks, s));
-    for (int st = 0; st < (int)C.steps.size(); ++st) {
-        for (const OpLaunch& L : C.step_ops[st]) BCK(launch_ops_batch(L.op, L.d_items, L.n, L.blocks, s));
-        for (auto& w : C.steps[st])
-            BCK(launch_level_batch(w.d_jobs, w.d_block_job, w.njobs, w.blocks, w.rt, w.sep, w.prec,
-                                   w.cgls, w.bf16, w.cluster, w.resident, s));
+    int st = 0;
+    if (C.fork01) {  // step 0 on the side branch, step 1 on the main one
+        BCK(cudaEventRecord(C.ev_fork, s));
+        BCK(cudaStreamWaitEvent(C.side, C.ev_fork, 0));
+        eecmg_status e0 = enqueue_step(C, 0, C.side);
+        eecmg_status e1 = e0 == EECMG_OK ? enqueue_step(C, 1, s) : e0;
+        BCK(cudaEventRecord(C.ev_join, C.side));  // always join the branch back
+        BCK(cudaStreamWaitEvent(s, C.ev_join, 0));
+        if (e1 != EECMG_OK) return e1;
+        st = 2;
+    }
+    for (; st < (int)C.steps.size(); ++st) {
+        eecmg_status e = enqueue_step(C, st, s);
+        if (e != EECMG_OK) return e;
     }
     return EECMG_OK;
 }
