@@ -319,8 +319,8 @@ eecmg_status eecmg_residual_noalloc(int width, int height, const double *psf, in
 
 /*
  * How the persistent level solves are split over the GPU (system design, no
- * counterpart in the paper).  An MR-II level with FP32 storage, a kernel
- * radius of at most 5 and at most resident_max_tiles 32x64 tiles runs on one
+ * counterpart in the paper).  A level with FP32 storage (MR-II or CGLS), a
+ * kernel radius of at most 5 and at most resident_max_tiles 32x64 tiles runs on one
  * thread-block cluster whose blocks keep all the solve's vectors in shared
  * memory for the whole solve (one or two tiles per block, at most 16 blocks).
  * Otherwise a level of at most cluster_max_px pixels runs on one cluster of

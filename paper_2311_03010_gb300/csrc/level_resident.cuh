@@ -1,9 +1,9 @@
-// level_resident.cuh -- the MR-II level solve (Section 2, Lanczos / Givens
-// form) with the whole level held in shared memory: FP32 storage, one
+// level_resident.cuh -- the level solves (Section 2: MR-II in Lanczos / Givens
+// form, and CGLS) with the whole level held in shared memory: FP32 storage, one
 // thread-block cluster of C <= 16 blocks per solve.  Block b owns T (1 or 2)
 // consecutive 32 x 64 tiles of the level in row-major tile order and keeps
-// all ten solver vectors of its tiles (u, r, v_k, v_{k+1}, H w_k, H w_{k+1},
-// two directions d, two H d) in its shared memory, tile-major, for the whole
+// the solver vectors of its tiles (MR-II: u, r, v_k, v_{k+1}, H w_k, H w_{k+1},
+// two directions d, two H d; CGLS: u, r, s, p, q) in its shared memory, tile-major, for the whole
 // solve: T x 2048 x 10 floats.  A convolution phase stages each tile with its
 // halo from the blocks that own the halo pixels (distributed shared memory
 // loads after the phase barrier); elementwise phases read and write shared
@@ -13,8 +13,8 @@
 // at the start and stay zero (every update is a linear combination of zero
 // entries), so the elementwise phases run over whole tiles.
 //
-// Per pixel and per scalar this is the arithmetic of mr2_body; only the
-// partition of the inner products into block sums differs.
+// Per pixel and per scalar this is the arithmetic of mr2_body / cgls_body;
+// only the partition of the inner products into block sums differs.
 #pragma once
 
 namespace eecmg {
@@ -460,12 +460,137 @@ __device__ __forceinline__ void mr2_res_body(ConvSmem<R, SEP> (&S)[2], const Lev
     }
 }
 
+// CGLS (Section 2) on the resident vectors: the phases and per-pixel
+// arithmetic of cgls_body (u, r, s = H^T r, p, q = H p; s and p FP32).
+enum { CU = 0, CR = 1, CS_ = 2, CP = 3, CQ = 4 };
+
+template <int R, bool SEP, bool PREC>
+__device__ __forceinline__ void cgls_res_body(ConvSmem<R, SEP> (&S)[2], const LevelJob& J, Scalars* sc,
+                                              const ResCtx& X, LevelSync& sy) {
+    const int n4 = X.NL >> 2;
+    conv_stage_taps<R, SEP>(S[0], J.taps);
+    {  // every vector zero, then u0
+        float4* b4 = reinterpret_cast<float4*>(X.base);
+        for (int q = threadIdx.x; q < RES_NVEC * n4; q += NTHREADS) b4[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+        __syncthreads();
+        if (!J.zero_start) {
+            float* u = X.vec(CU);
+            for (int lt = 0; lt < X.T; ++lt) {
+                const int t = X.bid * X.T + lt;
+                if (t >= X.ntiles) break;
+                const int y0 = (t / X.tiles_x) * CONV_TH, x0 = (t % X.tiles_x) * CONV_TW;
+                for (int p = threadIdx.x; p < TILE_PX; p += NTHREADS) {
+                    const int gy = y0 + p / CONV_TW, gx = x0 + p % CONV_TW;
+                    if (gy < X.h && gx < X.w) u[lt * TILE_PX + p] = __ldcg(J.u + (size_t)gy * X.w + gx);
+                }
+            }
+        }
+        __syncthreads();
+    }
+    float* rv_ = X.vec(CR);
+    float* sv = X.vec(CS_);
+    float* pv = X.vec(CP);
+    float* qv = X.vec(CQ);
+    {  // r_0 = g - H u_0
+        float a0 = 0.f, a1 = 0.f;
+        auto epi = [&](int li, size_t gi, float z, float) {
+            const float gv = __ldg(J.g + gi);
+            const float rv = gv - z;
+            rv_[li] = rv;
+            a0 = fmaf(rv, rv, a0);
+            a1 = fmaf(gv, gv, a1);
+        };
+        if (J.zero_start)
+            conv_phase_res<R, SEP, PREC, true, true>(S, X, 0, J.u, epi);
+        else
+            conv_phase_res<R, SEP, PREC, false, true>(S, X, 0, J.u, epi);
+        float v[2] = {a0, a1};
+        const double ct2 = J.conv_tol2, d2 = J.disc2;
+        if (!sy.reduce<2>(v, [&](DF* t) { fin_resid(sc, t[0], t[1], ct2, d2); })) return;
+    }
+    if (J.m <= 0 || volatile_stopped(sc)) return;  // u is still u0 in global memory
+    conv_stage_taps<R, SEP>(S[0], J.tapsT);  // s = H^T r, p = s
+    __syncthreads();
+    {
+        float a0 = 0.f;
+        conv_phase_res<R, SEP, PREC, false, false>(S, X, CR, nullptr, [&](int li, size_t, float z, float) {
+            sv[li] = z;
+            pv[li] = z;
+            a0 = fmaf(z, z, a0);
+        });
+        float v[1] = {a0};
+        if (!sy.reduce<1>(v, [&](DF* t) { fin_cg_s0(sc, t[0]); })) return;
+    }
+    bool ok = true;
+    for (int k = 1; k <= J.m && ok; ++k) {
+        if (volatile_stopped(sc)) break;
+        __syncthreads();
+        conv_stage_taps<R, SEP>(S[0], J.taps);  // q = H p, alpha
+        __syncthreads();
+        {
+            float a0 = 0.f;
+            conv_phase_res<R, SEP, PREC, false, false>(S, X, CP, nullptr, [&](int li, size_t, float z, float) {
+                qv[li] = z;
+                a0 = fmaf(z, z, a0);
+            });
+            float v[1] = {a0};
+            if (!sy.reduce<1>(v, [&](DF* t) { fin_cg_q(sc, t[0]); })) return;
+        }
+        if (volatile_stopped(sc)) break;
+        {  // u += alpha p, r -= alpha q, stopping rule
+            const float a = vldf(&sc->f_cg_alpha);
+            float arr = 0.f;
+            for (int q = threadIdx.x; q < n4; q += NTHREADS) {
+                const float4 pq = lds4(pv, q), uq = lds4(X.vec(CU), q);
+                const float4 qq = lds4(qv, q), rq = lds4(rv_, q);
+                sts4(X.vec(CU), q, fma4(a, pq, uq));
+                const float4 r = fma4(-a, qq, rq);
+                sts4(rv_, q, r);
+                arr = dot4(r, r, arr);
+            }
+            float v[1] = {arr};
+            if (!sy.reduce<1>(v, [&](DF* t) { fin_cg_step(sc, t[0]); })) return;
+        }
+        if (k == J.m || volatile_stopped(sc)) break;
+        __syncthreads();
+        conv_stage_taps<R, SEP>(S[0], J.tapsT);  // s = H^T r, beta
+        __syncthreads();
+        {
+            float a0 = 0.f;
+            conv_phase_res<R, SEP, PREC, false, false>(S, X, CR, nullptr, [&](int li, size_t, float z, float) {
+                sv[li] = z;
+                a0 = fmaf(z, z, a0);
+            });
+            float v[1] = {a0};
+            if (!sy.reduce<1>(v, [&](DF* t) { fin_cg_s(sc, t[0]); })) return;
+        }
+        if (volatile_stopped(sc)) break;
+        {  // p = s + beta p; the reduction is the barrier before other blocks read p's halo
+            const float b = vldf(&sc->f_beta);
+            for (int q = threadIdx.x; q < n4; q += NTHREADS) sts4(pv, q, fma4(b, lds4(pv, q), lds4(sv, q)));
+            float v[1] = {0.f};
+            ok = sy.reduce<1>(v, [&](DF*) {});
+        }
+    }
+    if (!ok) return;
+    const float* u = X.vec(CU);  // u back to global memory
+    for (int lt = 0; lt < X.T; ++lt) {
+        const int t = X.bid * X.T + lt;
+        if (t >= X.ntiles) break;
+        const int y0 = (t / X.tiles_x) * CONV_TH, x0 = (t % X.tiles_x) * CONV_TW;
+        for (int p = threadIdx.x; p < TILE_PX; p += NTHREADS) {
+            const int gy = y0 + p / CONV_TW, gx = x0 + p % CONV_TW;
+            if (gy < X.h && gx < X.w) J.u[(size_t)gy * X.w + gx] = u[lt * TILE_PX + p];
+        }
+    }
+}
+
 }  // namespace res_detail
 
-// One resident MR-II solve per cluster of LL.cluster blocks, LL.resident
-// tiles per block; dynamic shared memory res_smem_bytes(LL.resident).
-template <int R, bool SEP, bool PREC>
-__global__ void __launch_bounds__(NTHREADS, 1) k_level_mr2_res(LevelLaunch LL) {
+// One resident solve (MR-II, or CGLS) per cluster of LL.cluster blocks,
+// LL.resident tiles per block; dynamic shared memory res_smem_bytes(LL.resident).
+template <int R, bool SEP, bool PREC, bool CGLS>
+__device__ __forceinline__ void level_res_kernel(const LevelLaunch& LL) {
     using namespace res_detail;
 #ifdef EECMG_TRACE
     trace_reset();
@@ -486,12 +611,25 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_level_mr2_res(LevelLaunch LL) {
                    tiles_x * tiles_y, J.h, J.w};
     LevelSync sy{nullptr, J.gs, nb, bid, &CS, true, 0u};
     TRACE(bid, 1);
-    mr2_res_body<R, SEP, PREC>(S, J, &CS.sc, X, sy);
+    if constexpr (CGLS)
+        cgls_res_body<R, SEP, PREC>(S, J, &CS.sc, X, sy);
+    else
+        mr2_res_body<R, SEP, PREC>(S, J, &CS.sc, X, sy);
     cluster_end(CS, J.sc, bid);
     TRACE(bid, 2);
 #ifdef EECMG_TRACE
     trace_flush(bid == 0);
 #endif
+}
+
+template <int R, bool SEP, bool PREC>
+__global__ void __launch_bounds__(NTHREADS, 1) k_level_mr2_res(LevelLaunch LL) {
+    level_res_kernel<R, SEP, PREC, false>(LL);
+}
+
+template <int R, bool SEP, bool PREC>
+__global__ void __launch_bounds__(NTHREADS, 1) k_level_cgls_res(LevelLaunch LL) {
+    level_res_kernel<R, SEP, PREC, true>(LL);
 }
 
 }  // namespace eecmg

@@ -59,11 +59,13 @@ int resident_cluster_limit(int T) {
         LevelLaunch L;
         L.resident = T;
         int m = CLUSTER_MAX;
-        for (int sep = 0; sep < 2; ++sep) {
-            int c = 0;
-            if (dispatch(L, RES_RMAX, sep, 1, 0, 0, LS_RESIDENT_MAX, 0, nullptr, &c) != cudaSuccess) c = 0;
-            m = c < m ? c : m;
-        }
+        for (int cgls = 0; cgls < 2; ++cgls)
+            for (int sep = 0; sep < 2; ++sep) {
+                int c = 0;
+                if (dispatch(L, RES_RMAX, sep, 1, cgls, 0, LS_RESIDENT_MAX, 0, nullptr, &c) != cudaSuccess)
+                    c = 0;
+                m = c < m ? c : m;
+            }
         lim[T] = m;
     }
     return lim[T];
@@ -158,10 +160,11 @@ int level_want_blocks(int h, int w) {
 // 256^2 up a 16-SM cluster is throughput-bound and the grid form is faster.
 LevelShape level_shape(int h, int w, int rt, int cgls, int bf16) {
     LevelShape sh;
-    // MR-II, FP32: levels of at most resident_max_tiles tiles (<= 32) keep their
+    // FP32 storage: levels of at most resident_max_tiles tiles (<= 32) keep their
     // vectors in the shared memory of one cluster, T = 1 or 2 tiles per block
+    (void)cgls;
     const int tiles = (int)conv_blocks(h, w);
-    if (!cgls && !bf16 && rt >= 0 && rt <= RES_RMAX && tiles <= get_tuning().resident_max_tiles) {
+    if (!bf16 && rt >= 0 && rt <= RES_RMAX && tiles <= get_tuning().resident_max_tiles) {
         const int T = (tiles + CLUSTER_MAX - 1) / CLUSTER_MAX;
         const int C = (tiles + T - 1) / T;
         if (T <= RES_TMAX && C <= resident_cluster_limit(T)) {

@@ -612,10 +612,15 @@ template <int R, bool SEP, bool PREC, bool CGLS, typename HT>
 cudaError_t launch_level_t(const LevelLaunch& L, int op, int blocks, cudaStream_t s, int* out) {
     static int cap = -1, cmax = -1;  // per instantiation; the library runs on one GPU model
     if (op == LS_RESIDENT || op == LS_RESIDENT_MAX) {
-        if constexpr (!CGLS && std::is_same<HT, float>::value && R <= RES_RMAX) {
+        if constexpr (std::is_same<HT, float>::value && R <= RES_RMAX) {
             static int rmax[RES_TMAX + 1] = {-1, -1, -1};
-            static const bool attrs = res_attrs(k_level_mr2_res<R, SEP, PREC>);  // per instantiation
-            return res_op(k_level_mr2_res<R, SEP, PREC>, attrs, rmax, L, op, blocks, s, out);
+            if constexpr (CGLS) {
+                static const bool attrs = res_attrs(k_level_cgls_res<R, SEP, PREC>);  // per instantiation
+                return res_op(k_level_cgls_res<R, SEP, PREC>, attrs, rmax, L, op, blocks, s, out);
+            } else {
+                static const bool attrs = res_attrs(k_level_mr2_res<R, SEP, PREC>);
+                return res_op(k_level_mr2_res<R, SEP, PREC>, attrs, rmax, L, op, blocks, s, out);
+            }
         } else {
             if (out) *out = 0;
             return op == LS_RESIDENT_MAX ? cudaSuccess : cudaErrorInvalidValue;

@@ -58,13 +58,14 @@ def test_level_solve(gpu, orc, smoother, psfname, shape, persistent):
     plan.close()
 
 
+@pytest.mark.parametrize("smoother", ["mr2", "cgls"])
 @pytest.mark.parametrize("resident", [32, 0])
 @pytest.mark.parametrize("psfname", ["gauss5", "motion7"])
 @pytest.mark.parametrize("shape", [(150, 250), (256, 256), (31, 700), (700, 20), (64, 64), (5, 5)])
-def test_resident_level_solve(gpu, orc, psfname, shape, resident):
-    """MR-II level solves with the level held in the shared memory of one cluster (one or two
-    32 x 64 tiles per block, partial tiles, wide and tall levels, radii 5 and 3) and, with
-    resident_max_tiles = 0, streamed through L2: both stop where the oracle's MR-II stops and
+def test_resident_level_solve(gpu, orc, psfname, shape, resident, smoother):
+    """Level solves (MR-II and CGLS) with the level held in the shared memory of one cluster (one
+    or two 32 x 64 tiles per block, partial tiles, wide and tall levels, radii 5 and 3) and, with
+    resident_max_tiles = 0, streamed through L2: both stop where the oracle's solver stops and
     stay within the FP32 bar of it."""
     import gc
 
@@ -82,7 +83,7 @@ def test_resident_level_solve(gpu, orc, psfname, shape, resident):
         rng = np.random.default_rng(80)
         g = (orc.apply_H(psf, synth.synthetic_image(h, w, 81)) + rng.normal(0, 1.0, shape)).astype(np.float32)
         u0 = rng.uniform(0, 255, shape).astype(np.float32)
-        plan = E.Plan(w, h, 1, psf)
+        plan = E.Plan(w, h, 1, psf, smoother=smoother)
         cl, nb, res = E.eecmg_level_partition(plan.handle, 0)
         tiles = ((h + 31) // 32) * ((w + 63) // 64)
         if resident:
@@ -95,8 +96,8 @@ def test_resident_level_solve(gpu, orc, psfname, shape, resident):
             ud = dev(torch, u0)
             E.eecmg_level_solve(plan.handle, 0, dev(torch, g), ud, m)
             it, res = plan.stats()
-            ref, k, rres = orc.mr2(psf, g.astype(np.float64), u0.astype(np.float64), m,
-                                   conv_tol=orc.CONV_TOL)
+            ref, k, rres = getattr(orc, smoother)(psf, g.astype(np.float64), u0.astype(np.float64), m,
+                                                  conv_tol=orc.CONV_TOL)
             assert it[0] == k, (m, it, k)
             assert rel_l2(host(ud), ref) <= FP32_REL, (m, rel_l2(host(ud), ref))
             assert res[0] == pytest.approx(rres, rel=1e-3, abs=1e-3)
