@@ -67,7 +67,7 @@ struct Tuning {
     int px_per_block = 2048;           // grid mode: at least one block per this many pixels (>= 1024)
     long long cluster_max_px = 16384;  // levels with at most this many pixels run in cluster mode
     int blocks_per_sm = 2;             // grid mode: at most this many blocks per SM (1..3)
-    int resident_max_tiles = 32;       // MR-II FP32 levels of at most this many 32 x 64 tiles
+    int resident_max_tiles = 32;       // FP32 levels of at most this many 32 x 64 tiles
                                        // run shared-memory resident (0 = never, <= 32)
 };
 Tuning get_tuning();

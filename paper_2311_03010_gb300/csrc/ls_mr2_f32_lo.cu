@@ -1,4 +1,5 @@
-// Instantiations of the persistent level solver: MR-II, FP32 storage, radii 0..5.
+// Instantiations of the persistent level solver: MR-II, FP32 storage, radii 0..5 (also the
+// shared-memory resident form).
 #include "level_solve_impl.cuh"
 
 namespace eecmg {
