@@ -191,7 +191,7 @@ constexpr int CLUSTER_MAX = 16;
 // solve's scalars (both modes) and, in cluster mode, the exchange slots.
 struct ClusterState {
     double slots[2][CLUSTER_MAX][NPART];  // [phase parity][source rank][value], double-float pairs
-    unsigned long long mbar;
+    unsigned long long mbar[2];  // phases alternate between the two barriers
     int err;
     Scalars sc;                           // this block's replica of the solve's scalars
 };
@@ -224,13 +224,15 @@ __device__ __forceinline__ bool mbar_test_parity(unsigned int addr, unsigned int
 }
 
 // Called by all threads of every block of the cluster at kernel start, after
-// the job is in shared memory: loads the scalar replica, initialises the
-// mbarrier for nb arrivals per phase and makes it visible cluster-wide.
+// the job is in shared memory: loads the scalar replica, initialises the two
+// mbarriers for nb arrivals per phase and makes them visible cluster-wide.
 __device__ __forceinline__ void cluster_begin(ClusterState& cs, const Scalars* gsc, unsigned int nb) {
     if (threadIdx.x == 0) {
         cs.sc = *gsc;
         cs.err = 0;
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&cs.mbar)), "r"(nb)
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&cs.mbar[0])), "r"(nb)
+                     : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&cs.mbar[1])), "r"(nb)
                      : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -257,7 +259,11 @@ __device__ __forceinline__ bool cluster_reduce(const float (&v)[NV], ClusterStat
     GTRACE(rank == 0 && threadIdx.x == 0, 40);
     block_sum_df<NV>(in, out);  // warp 0 holds lane 0's sums; ends with __syncthreads()
     GTRACE(rank == 0 && threadIdx.x == 0, 41);
-    const unsigned int par = phase & 1u;
+    // phase k uses slots[k & 1] and mbar[k & 1], whose own phase parity is (k >> 1) & 1.  A block
+    // arrives for phase k + 1 only after it has seen every block's phase-k arrival, and for phase
+    // k + 2 only after every block has arrived for k + 1, i.e. has finished waiting on phase k:
+    // so no arrival can land on a barrier that is still collecting an earlier phase.
+    const unsigned int par = phase & 1u, bpar = (phase >> 1) & 1u;
     if (threadIdx.x < nb) {  // lane t delivers this block's sums to block t
         const unsigned int t = threadIdx.x;
 #pragma unroll
@@ -267,15 +273,15 @@ __device__ __forceinline__ bool cluster_reduce(const float (&v)[NV], ClusterStat
                          "f"(out[j].lo)
                          : "memory");
         }
-        const unsigned int bar = cluster_map(smem_u32(&cs.mbar), t);
+        const unsigned int bar = cluster_map(smem_u32(&cs.mbar[par]), t);
         asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(bar)
                      : "memory");
     }
     if (threadIdx.x < 32) {  // warp 0: every lane waits (bounded) and acquires, lane q reads block q's sums
-        const unsigned int bar = smem_u32(&cs.mbar);
+        const unsigned int bar = smem_u32(&cs.mbar[par]);
         const long long t0 = clock64();
         bool ok = true;
-        while (!mbar_test_parity(bar, par)) {
+        while (!mbar_test_parity(bar, bpar)) {
             if (clock64() - t0 > limit) {
                 ok = false;
                 break;
