@@ -61,10 +61,11 @@ def test_level_solve(gpu, orc, smoother, psfname, shape, persistent):
 @pytest.mark.parametrize("smoother", ["mr2", "cgls"])
 @pytest.mark.parametrize("resident", [32, 0])
 @pytest.mark.parametrize("psfname", ["gauss5", "motion7"])
-@pytest.mark.parametrize("shape", [(150, 250), (256, 256), (31, 700), (700, 20), (64, 64), (5, 5)])
+@pytest.mark.parametrize("shape", [(150, 250), (256, 256), (160, 320), (31, 700), (700, 20), (64, 64), (5, 5)])
 def test_resident_level_solve(gpu, orc, psfname, shape, resident, smoother):
     """Level solves (MR-II and CGLS) with the level held in the shared memory of one cluster (one
-    or two 32 x 64 tiles per block, partial tiles, wide and tall levels, radii 5 and 3) and, with
+    or two 32 x 64 tiles per block, an odd tile count whose last block holds one tile, partial
+    tiles, wide and tall levels, radii 5 and 3) and, with
     resident_max_tiles = 0, streamed through L2: both stop where the oracle's solver stops and
     stay within the FP32 bar of it."""
     import gc
