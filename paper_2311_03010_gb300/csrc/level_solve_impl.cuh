@@ -5,7 +5,7 @@
 // Every phase of an iteration is a grid-stride pass over the level's tiles
 // (convolution phases, 32 x 64 tiles with halo in shared memory) or pixels
 // (elementwise phases), ended by a reduction barrier (persistent.cuh): the
-// deterministic FP64 sums of the phase's inner products and its scalar
+// deterministic double-float sums of the phase's inner products and its scalar
 // update (finish.cuh), run by every block on its own replica of the scalars.  Compared with one launch per phase this removes the
 // launch latency of every phase and, because the loop tests the stop flag,
 // the iterations that a stopping rule makes unnecessary are never launched.

@@ -2,7 +2,7 @@
 // the persistent (one launch per level solve) kernels.
 //
 // Grid mode: all blocks of a job are co-resident (cooperative launch).  At
-// the end of a phase every block writes its FP64 block sums into its slot of
+// the end of a phase every block writes its double-float block sums into its slot of
 // the phase's partials (double-buffered by phase parity), then adds one to
 // the job's arrival counter with release semantics.  Every block waits until
 // the counter reaches (phase + 1) x blocks, then sums all blocks' partials in
@@ -177,8 +177,8 @@ __device__ __forceinline__ void grid_exit(GroupSync* gs, unsigned int nb) {
 // ---------------------------------------------------------------------------
 // Cluster mode: a small level solve runs on one thread-block cluster (up to
 // CLUSTER_MAX blocks, one per SM of a GPC) instead of a cooperative grid.
-// A reduction then never leaves the GPC: every block writes its FP64 block
-// sums into a slot of every block's shared memory (distributed shared
+// A reduction then never leaves the GPC: every block writes its double-float
+// block sums into a slot of every block's shared memory (distributed shared
 // memory) and arrives on each block's mbarrier; each block waits on its own
 // mbarrier (bounded), sums the slots in a fixed order (rank order up to 4
 // blocks, a butterfly beyond) and runs the scalar update itself.  All blocks hold identical scalar state (the same sums in
