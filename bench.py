@@ -1,31 +1,41 @@
 """Throughput benchmark of GB300 EECMG restoration (one JSON line on rank 0).
 
-Default workload (512x512 precision/parity case): one synthetic 512 x 512
-image (shapes + gradient + texture band), Gaussian PSF sigma = 2.5 on 15 x
-15, two noise draws (1 % and 5 %), 5 levels with the economy schedule,
-MR-II, FP32.  One step restores both degraded images.  Metric: Mpixel/s of
-restored fine-grid pixels.
+Default workload (the precision-form case, the largest single-GPU one): one
+synthetic 4096 x 4096 image (shapes + gradient + texture band), Gaussian
+PSF sigma = 3 on 21 x 21, 1 % relative noise, 5 levels, MR-II, FP32, the
+economy schedule of Section 2 as the cap of the discrepancy stop
+(||g_l - H_l u||_RMS <= 1.1 delta, delta = ||e||_RMS of the data).  One step
+restores the image.  Metric: Mpixel/s of restored fine-grid pixels.
 
 Timing: W untimed warm-up steps, then K steps (default: as many as make
 about 1.5 s of timed work), each bracketed by CUDA events on the launching
-stream; clocks are sampled every 50 ms and only samples stamped inside the
-timed region are reported; between steps a 256 MiB buffer is written
-to flush the 129 MB L2 (outside the events).  The timed region is bracketed
-by a barrier and torch.cuda.synchronize().  With torchrun (N > 1) every rank
-restores its own batch (replicas; the method has no cross-image exchange)
-and the max time over ranks is used.
+stream; between steps a 256 MiB buffer is written to flush the 129 MB L2
+(outside the events).  Clocks are sampled every 50 ms and only samples
+stamped inside the timed region are reported.  The timed region is
+bracketed by a barrier and torch.cuda.synchronize().  With torchrun (N > 1)
+every rank restores its own images (replicas; the method has no exchange
+between images) and the max time over ranks is used.
 
-Extra objects: ``e2e`` (same metric through eecmg_restore_batched_host with
-pinned host buffers, copies inside the timed region), ``roofline`` (dominant kernel
-class: algorithmic bytes / event-timed duration from a profiled eager replay
-of the same steps, vs the measured HBM copy peak), ``cpu_baseline`` (the
-FP64 CPU oracle on a bounded sample of the workload), ``clocks`` and
-``gpu_launches``.
+Extra objects on the line: ``roofline`` (the dominant level-solve launch:
+algorithmic bytes over its duration, both measured inside the timed region
+by an event pair recorded in the replayed CUDA graph around that launch,
+against the measured HBM copy peak), ``parity`` (every image of the step
+against the FP64 oracle: rel-L2, |delta PSNR|, PSNR of the result and of
+the data), ``e2e`` (the same metric through eecmg_restore_batched_host with
+pinned host buffers, copies inside the timed region), ``cpu_baseline`` (the
+FP64 CPU oracle on a bounded sample of the workload), ``clocks``,
+``gpu_launches`` and, with the default workload, ``legs``: the 512 x 512
+two-noise case and the 64-image uneven batch (batched form against the
+plain per-image loop on the same plans), and ``serving``: a 2000-request
+Poisson trace through the continuous-batching server and through the plain
+per-image loop.
+
 ``--impl reference`` times the CPU oracle itself on the same workload.
 """
 from __future__ import annotations
 
 import argparse
+import collections
 import json
 import os
 import statistics
@@ -39,21 +49,27 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+METRIC = "Mpixel/s restored (EECMG, oracle-matched)"
+
 WORKLOADS = {
     # name: (h, w, levels, psf spec, noise levels, seed, noise seeds)
+    "4096x4096-gauss3-L5": (4096, 4096, 5, ("gauss", 3.0, 10), (0.01,), 3001, (3002,)),
     "512x512-gauss2.5-L5": (512, 512, 5, ("gauss", 2.5, 7), (0.01, 0.05), 2000, (2001, 2002)),
     "64x64-gauss1.5-L3": (64, 64, 3, ("gauss", 1.5, 4), (0.01,), 1000, (1001,)),
     "2048x2048-gauss3-L5": (2048, 2048, 5, ("gauss", 3.0, 10), (0.01,), 3000, (3001,)),
-    "4096x4096-gauss3-L5": (4096, 4096, 5, ("gauss", 3.0, 10), (0.01,), 3001, (3002,)),
     "2048x2048-motion15-L5": (2048, 2048, 5, ("motion", 15, 30.0), (0.01,), 3000, (3001,)),
     # 64 images, sides 128..1536 (square or 3:4), Gaussian or motion PSFs, 0.5-5 % noise
     "batch64-uneven-L5": None,
 }
-DEFAULT_WORKLOAD = "512x512-gauss2.5-L5"
+DEFAULT_WORKLOAD = "4096x4096-gauss3-L5"
+EXTRA_LEGS = ("512x512-gauss2.5-L5", "batch64-uneven-L5")
+
+# clean image (FP64), PSF, levels, degraded data (FP32), noise level ||e||_RMS
+Prob = collections.namedtuple("Prob", "u psf L g delta")
 
 
 def make_problems(name):
-    """List of (clean image, PSF, levels, g FP32) for the workload."""
+    """The workload's restoration problems (seeded, synthetic)."""
     from paper_2311_03010_gb300 import synth
 
     if name == "batch64-uneven-L5":
@@ -61,13 +77,17 @@ def make_problems(name):
         for spec in synth.batch_specs(64, 4000):
             psf = synth.psf_from_spec(spec["psf"])
             u = synth.synthetic_image(spec["h"], spec["w"], spec["seed"])
-            g, _ = synth.degrade(u, psf, spec["v"], spec["seed"] + 1)
-            out.append((u, psf, 5, g))
+            g, delta = synth.degrade(u, psf, spec["v"], spec["seed"] + 1)
+            out.append(Prob(u, psf, 5, g, delta))
         return out
     h, w, L, spec, vs, seed, nseeds = WORKLOADS[name]
     psf = synth.psf_from_spec(spec)
     u = synth.synthetic_image(h, w, seed, texture=(h * w > 4096))
-    return [(u, psf, L, synth.degrade(u, psf, v, ns)[0]) for v, ns in zip(vs, nseeds)]
+    out = []
+    for v, ns in zip(vs, nseeds):
+        g, delta = synth.degrade(u, psf, v, ns)
+        out.append(Prob(u, psf, L, g, delta))
+    return out
 
 
 LEVEL_SOLVE_SOURCES = ("common.cuh", "conv_tile.cuh", "finish.cuh", "persistent.cuh",
@@ -84,9 +104,10 @@ def level_solve_source_hash():
     return h.hexdigest()
 
 
-def profiled_traffic(workload):
-    """DRAM bytes per level-solve launch from the committed ncu summary of this
-    workload, if it was taken on the current level-solve sources (else None)."""
+def profiled_traffic(workload, step):
+    """DRAM bytes per launch of the workload's level solve at cascade step `step`
+    from the committed ncu summary, if it was taken on the current level-solve
+    sources (else None and the reason)."""
     path = os.path.join(ROOT, "profiles", f"level_solve_traffic_{workload}.txt")
     if not os.path.exists(path):
         return None, "no ncu capture of this workload"
@@ -97,6 +118,8 @@ def profiled_traffic(workload):
             kv[k.strip()] = v.strip()
     if kv.get("level_solve_sources_sha256") != level_solve_source_hash():
         return None, "ncu capture predates the current level-solve sources"
+    if kv.get("cascade_step") not in (None, str(step)):
+        return None, f"ncu capture is of cascade step {kv.get('cascade_step')}"
     return float(kv["dram_bytes_per_launch"]), path.replace(ROOT + os.sep, "")
 
 
@@ -155,6 +178,7 @@ class ClockSampler:
             self.proc.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.proc.kill()
+
         def stamp(text):
             for fmt in ("%Y/%m/%d %H:%M:%S.%f", "%Y/%m/%d %H:%M:%S"):
                 try:
@@ -197,28 +221,44 @@ class ClockSampler:
                 "reasons": sorted(reasons)}
 
 
-def cpu_baseline(name, max_seconds=12.0):
-    """The FP64 oracle on a bounded sample: whole images of the workload, repeated."""
-    import oracle
+def host_threads():
+    return len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
 
-    probs = make_problems(name)
-    threads = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
-    oracle.set_threads(threads)
-    px = 0
-    t0 = time.perf_counter()
-    n = 0
-    while True:
-        _, psf, L, g = probs[n % len(probs)]
-        oracle.cascade(g.astype(np.float64), L, psf)
-        px += g.size
-        n += 1
-        if time.perf_counter() - t0 > max_seconds or n >= 64:
-            break
-    dt = time.perf_counter() - t0
-    oracle.set_threads(1)
-    return {"value": px / dt / 1e6, "unit": "Mpixel/s", "cores": threads, "kind": "oracle",
-            "sample": f"{n} whole restorations of the {name} images (FP64 C oracle, OpenMP)",
-            "seconds": dt}
+
+def oracle_restore(oracle, p, smoother, **kw):
+    """The FP64 oracle's restoration of problem p under the bench's stopping rule."""
+    return oracle.cascade(p.g.astype(np.float64), p.L, p.psf, smoother=smoother, stop="discrepancy",
+                          c=1.1, delta=p.delta, **kw)
+
+
+def parity_of(oracle, probs, outs, iters, smoother):
+    """Every listed image against the FP64 oracle (with the oracle's own run timed).
+
+    Where the GPU stopped a level at a different count than the oracle (a residual
+    within rounding of the stopping limit), the oracle is also run at the GPU's
+    counts and that comparison is reported."""
+    images = []
+    t_oracle, px = 0.0, 0
+    for p, u, it in zip(probs, outs, iters):
+        t0 = time.perf_counter()
+        ref, rit, _ = oracle_restore(oracle, p, smoother)
+        t_oracle += time.perf_counter() - t0
+        px += p.g.size
+        at_counts = False
+        if list(it) != list(rit):
+            ref, _, _ = oracle.cascade(p.g.astype(np.float64), p.L, p.psf, smoother=smoother,
+                                       iters=list(it), stop="fixed", conv_tol=0.0)
+            at_counts = True
+        images.append({
+            "rel_l2": float(np.linalg.norm(u - ref) / np.linalg.norm(ref)),
+            "dpsnr_db": float(abs(oracle.psnr(p.u, u) - oracle.psnr(p.u, ref))),
+            "psnr_db": float(oracle.psnr(p.u, u)), "psnr_g_db": float(oracle.psnr(p.u, p.g)),
+            "iters": list(it), "oracle_iters": list(rit), "oracle_at_gpu_counts": at_counts})
+    out = {"rel_l2": max(x["rel_l2"] for x in images),
+           "dpsnr_db": max(x["dpsnr_db"] for x in images),
+           "restores_every_image": all(x["psnr_db"] > x["psnr_g_db"] for x in images),
+           "tolerance": {"rel_l2": 1e-4, "dpsnr_db": 0.01}, "images": images}
+    return out, t_oracle, px
 
 
 def _percentiles(xs):
@@ -227,19 +267,164 @@ def _percentiles(xs):
             "mean_ms": float(xs.mean()), "max_ms": float(xs.max())}
 
 
-def serving_leg(torch, eecmg, stream, storage, n_req=400, rate=200.0, seed=5000,
+class Leg:
+    """Plans, device buffers and the batched step of one workload."""
+
+    def __init__(self, torch, eecmg, stream, name, args, autotune):
+        self.torch, self.E, self.stream, self.name = torch, eecmg, stream, name
+        self.probs = make_problems(name)
+        self.gs = [torch.from_numpy(p.g).cuda() for p in self.probs]
+        self.smoother = args.smoother
+
+        def opts(p):
+            smo = args.smoother
+            if smo == "mr2" and not np.allclose(p.psf, p.psf[::-1, ::-1], rtol=0, atol=1e-15):
+                smo = "cgls"
+            return dict(smoother=smo, precise_conv=args.precise_conv, storage=args.storage,
+                        stop="discrepancy", c=1.1, delta=p.delta)
+
+        # partition of the level solves: autotuned on this workload (before any of its
+        # plans owns a workspace), untimed
+        src = "defaults"
+        if autotune:
+            descs = [eecmg.Plan(p.g.shape[1], p.g.shape[0], p.L, p.psf, workspace=0, **opts(p))
+                     for p in self.probs]
+            t0 = time.perf_counter()
+            eecmg.eecmg_autotune(descs, self.gs, reps=5, stream=stream)
+            src = f"autotuned on this workload in {time.perf_counter() - t0:.1f} s"
+            for d in descs:
+                d.close()
+        self.tuning = dict(eecmg.eecmg_get_tuning(), source=src)
+        self.plans = [eecmg.Plan(p.g.shape[1], p.g.shape[0], p.L, p.psf, **opts(p)) for p in self.probs]
+        self.handles = [p.handle for p in self.plans]
+        self.us = [torch.empty_like(g) for g in self.gs]
+        self.px = sum(g.numel() for g in self.gs)
+
+    def step(self):
+        self.E.eecmg_restore_batched(self.handles, self.gs, self.us, self.stream)
+
+    def outputs(self):
+        self.torch.cuda.synchronize()
+        return [u.double().cpu().numpy() for u in self.us]
+
+    def iters(self):
+        return [p.stats()[0] for p in self.plans]
+
+    def close(self):
+        for p in self.plans:
+            p.close()
+        self.plans = []
+
+
+def time_steps(torch, leg, steps, flush, hook=False):
+    """Device time (ms) of each of `steps` batched restorations, L2 flushed between
+    them; with `hook`, also the hooked level-solve launch(es) of each step."""
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    hk = []
+    for i in range(steps):
+        flush.zero_()
+        ev[i][0].record(leg.stream)
+        leg.step()
+        ev[i][1].record(leg.stream)
+        if hook:
+            hk.append(leg.E.eecmg_batch_step_time(leg.handles))
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for (a, b) in ev], hk
+
+
+def auto_steps(torch, leg, flush, world, target_ms=1500.0):
+    """Enough steps for about target_ms of timed work (the same count on every rank)."""
+    from paper_2311_03010_gb300 import replicas
+
+    per = 1.0
+    for _ in range(2):  # the second pass is the estimate
+        ms, _ = time_steps(torch, leg, 5, flush)
+        per = sum(ms) / 5.0
+    return int(replicas.max_over_ranks(min(5000, max(20, int(target_ms / max(per, 1e-3)))), world, "cuda"))
+
+
+def dominant_step(torch, leg, flush):
+    """The cascade step whose level-solve launches take longest (hook read over 3 replays)."""
+    E = leg.E
+    best = (-1.0, 0)
+    for s in range(max(p.L for p in leg.probs)):
+        E.eecmg_batch_time_step(leg.handles, s, 1)
+        leg.step()  # captures the graph with the hook
+        _, hk = time_steps(torch, leg, 3, flush, hook=True)
+        ms = min(h[0] for h in hk)
+        best = max(best, (ms, s))
+    return best[1]
+
+
+def extra_leg(torch, eecmg, stream, name, args, world, flush, oracle_ok):
+    """Batched Mpixel/s of another workload (and, for a batch of many images, the plain
+    per-image loop on the same plans), with its parity against the oracle."""
+    leg = Leg(torch, eecmg, stream, name, args, autotune=not args.no_autotune)
+    for _ in range(3):
+        leg.step()
+    torch.cuda.synchronize()
+    steps = auto_steps(torch, leg, flush, world, target_ms=600.0)
+    ms, _ = time_steps(torch, leg, steps, flush)
+    tot = sum(ms)
+    from paper_2311_03010_gb300 import replicas
+
+    tot = replicas.max_over_ranks(tot, world, "cuda")
+    out = {"value": replicas.aggregate_rate(leg.px, steps, world, tot) / 1e6, "unit": "Mpixel/s",
+           "steps": steps, "ms_per_step": tot / steps, "images_per_step": len(leg.gs),
+           "pixels_per_step": leg.px, "partition": leg.tuning,
+           "gpu_launches_per_step": eecmg.eecmg_batch_info(leg.handles)}
+    if len(leg.plans) > 2:
+        # the plain per-image loop on the same plans (each plan's own CUDA graph)
+        for p, g, u in zip(leg.plans, leg.gs, leg.us):
+            p.restore(g, u, stream)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        loop_steps = max(3, steps // 2)
+        loop_ms = 0.0
+        for _ in range(loop_steps):
+            flush.zero_()
+            e0.record(stream)
+            for p, g, u in zip(leg.plans, leg.gs, leg.us):
+                p.restore(g, u, stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            loop_ms += e0.elapsed_time(e1)
+        loop_ms = replicas.max_over_ranks(loop_ms, world, "cuda")
+        out["per_image_loop_value"] = replicas.aggregate_rate(leg.px, loop_steps, world, loop_ms) / 1e6
+        leg.step()
+    if oracle_ok:
+        import oracle
+
+        oracle.set_threads(host_threads())
+        k = min(len(leg.probs), 4)
+        par, _, _ = parity_of(oracle, leg.probs[:k], leg.outputs()[:k], leg.iters()[:k], leg.smoother)
+        par["images_checked"] = f"{k} of {len(leg.probs)}"
+        out["parity"] = par
+        oracle.set_threads(1)
+    leg.close()
+    return out
+
+
+def serving_leg(torch, eecmg, stream, storage, n_req=2000, rate=200.0, seed=5000, chunk=400,
                 budget=64 << 30, slots=64):
     """Serving form: a Poisson stream of restore requests (sizes 256^2..4096^2
-    log-uniform, Gaussian or motion PSF each, 1-5 % noise, 5 levels, MR-II)
-    through the continuous-batching server, and the same trace through the
-    plain per-image loop (eecmg_restore per request, FIFO on one stream, its
-    CUDA graph captured beforehand).  Open loop: requests are submitted at
-    their arrival times; latency = arrival -> result ready (device clock).
-    Saturated: the whole trace submitted at once, Mpixel/s = capacity.
+    log-uniform, Gaussian or motion PSF each, 1-5 % noise, 5 levels, MR-II, the
+    discrepancy stop with each request's noise level) through the
+    continuous-batching server, and the same trace through the plain per-image
+    loop (eecmg_restore per request, FIFO on one stream, its CUDA graph captured
+    beforehand).  Open loop: requests are submitted at their arrival times;
+    latency = arrival -> result ready (device clock).  Saturated: the requests
+    submitted at once, Mpixel/s = capacity.
+
+    The trace is replayed in consecutive chunks of `chunk` requests (each chunk's
+    arrivals relative to its first), so that the inputs and the plain loop's
+    plans of one chunk at a time are on the device; latencies and times are
+    pooled over the chunks.
 
     Inputs: crops of one synthetic image, blurred on the device by zero-padded
-    2-D correlation with each request's (symmetric) PSF, plus seeded Gaussian
-    noise with ||e|| = v ||u||.
+    2-D correlation with each request's (centrosymmetric) PSF, plus seeded
+    Gaussian noise with ||e|| = v ||u||.
     """
     from paper_2311_03010_gb300 import synth
 
@@ -247,22 +432,26 @@ def serving_leg(torch, eecmg, stream, storage, n_req=400, rate=200.0, seed=5000,
     smax = max(max(r["h"], r["w"]) for r in tr)
     u_clean = torch.from_numpy(synth.synthetic_image(smax, smax, seed).astype(np.float32)).cuda()
     gen = torch.Generator(device="cuda")
-    reqs = []
-    for r in tr:
-        psf = synth.psf_from_spec(r["psf"])
-        h, w = r["h"], r["w"]
-        x = u_clean[:h, :w].reshape(1, 1, h, w)
-        k = torch.from_numpy(np.ascontiguousarray(psf[::-1, ::-1]).astype(np.float32)).cuda()
-        hu = torch.nn.functional.conv2d(x, k.reshape(1, 1, *psf.shape),
-                                        padding=(psf.shape[0] // 2, psf.shape[1] // 2))[0, 0]
-        gen.manual_seed(r["seed"])
-        e = torch.randn(h, w, generator=gen, device="cuda")
-        g = (hu + e * (r["v"] * x.norm() / e.norm())).contiguous()
-        reqs.append({"t": r["t"], "g": g, "u": torch.empty_like(g), "psf": psf, "h": h, "w": w})
-    px = sum(r["h"] * r["w"] for r in reqs)
-    torch.cuda.synchronize()
 
-    def replay(submit, finish, open_loop):
+    def make_inputs(part):
+        reqs = []
+        for r in part:
+            psf = synth.psf_from_spec(r["psf"])
+            h, w = r["h"], r["w"]
+            x = u_clean[:h, :w].reshape(1, 1, h, w)
+            k = torch.from_numpy(np.ascontiguousarray(psf[::-1, ::-1]).astype(np.float32)).cuda()
+            hu = torch.nn.functional.conv2d(x, k.reshape(1, 1, *psf.shape),
+                                            padding=(psf.shape[0] // 2, psf.shape[1] // 2))[0, 0]
+            gen.manual_seed(r["seed"])
+            e = torch.randn(h, w, generator=gen, device="cuda")
+            scale = r["v"] * float(x.norm()) / float(e.norm())
+            g = (hu + e * scale).contiguous()
+            reqs.append({"t": r["t"] - part[0]["t"], "g": g, "u": torch.empty_like(g), "psf": psf,
+                         "h": h, "w": w, "delta": scale * float(e.norm()) / (h * w) ** 0.5})
+        torch.cuda.synchronize()
+        return reqs
+
+    def replay(reqs, submit, finish, open_loop):
         t0 = time.perf_counter()
         subs = []
         for r in reqs:
@@ -274,55 +463,68 @@ def serving_leg(torch, eecmg, stream, storage, n_req=400, rate=200.0, seed=5000,
         lat = finish(subs)
         return time.perf_counter() - t0, lat
 
+    px = sum(r["h"] * r["w"] for r in tr)
     out = {"requests": n_req, "rate_per_s": rate, "storage": storage, "levels": 5,
            "pixels": px, "sizes": "256^2..4096^2 log-uniform", "budget_bytes": budget,
-           "max_slots": slots}
-    # --- continuous-batching server
-    descs = [eecmg.Plan(r["w"], r["h"], 5, r["psf"], storage=storage, workspace=0) for r in reqs]
+           "max_slots": slots, "chunk": chunk, "stop": "discrepancy, c = 1.1, delta per request"}
+    acc = {f"{s}_{m}": {"lat": [], "s": 0.0} for s in ("server", "plain_loop") for m in ("open", "saturated")}
     srv = eecmg.Server(budget, slots)
-    for i in range(min(8, n_req)):  # warm-up (occupancy queries, first launches)
-        srv.submit(descs[i], reqs[i]["g"], reqs[i]["u"])
-    srv.drain()
-    idx = {id(r): i for i, r in enumerate(reqs)}
+    warm = True
+    for c0 in range(0, n_req, chunk):
+        reqs = make_inputs(tr[c0:c0 + chunk])
+        opt = lambda r: dict(storage=storage, delta=r["delta"])
+        # --- continuous-batching server
+        descs = [eecmg.Plan(r["w"], r["h"], 5, r["psf"], workspace=0, **opt(r)) for r in reqs]
+        if warm:  # first launches and occupancy queries
+            for i in range(min(8, len(reqs))):
+                srv.submit(descs[i], reqs[i]["g"], reqs[i]["u"])
+            srv.drain()
+            warm = False
+        idx = {id(r): i for i, r in enumerate(reqs)}
 
-    def srv_submit(r):
-        return srv.submit(descs[idx[id(r)]], r["g"], r["u"])
+        def srv_submit(r):
+            return srv.submit(descs[idx[id(r)]], r["g"], r["u"])
 
-    def srv_finish(subs):
-        srv.drain()
-        return [srv.poll(t)[1] for (_, t) in subs]
+        def srv_finish(subs):
+            srv.drain()
+            return [srv.poll(t)[1] for (_, t) in subs]
 
-    for mode in ("open", "saturated"):
-        dt, lat = replay(srv_submit, srv_finish, mode == "open")
-        out[f"server_{mode}"] = dict(_percentiles(lat), mpix_s=px / dt / 1e6, seconds=dt)
-    srv.close()
-    for d in descs:
-        d.close()
-    # --- plain per-image loop
-    plans = [eecmg.Plan(r["w"], r["h"], 5, r["psf"], storage=storage) for r in reqs]
-    for p, r in zip(plans, reqs):
-        p.restore(r["g"], r["u"], stream)  # captures each plan's graph
-    torch.cuda.synchronize()
-    base = torch.cuda.Event(enable_timing=True)
-    base.record(stream)
-    base.synchronize()
-    base_host = time.perf_counter()
-
-    def loop_submit(r):
-        plans[idx[id(r)]].restore(r["g"], r["u"], stream)
-        ev = torch.cuda.Event(enable_timing=True)
-        ev.record(stream)
-        return ev
-
-    def loop_finish(subs):
+        for mode in ("open", "saturated"):
+            dt, lat = replay(reqs, srv_submit, srv_finish, mode == "open")
+            acc[f"server_{mode}"]["lat"] += lat
+            acc[f"server_{mode}"]["s"] += dt
+        for d in descs:
+            d.close()
+        # --- plain per-image loop
+        plans = [eecmg.Plan(r["w"], r["h"], 5, r["psf"], **opt(r)) for r in reqs]
+        for p, r in zip(plans, reqs):
+            p.restore(r["g"], r["u"], stream)  # captures each plan's graph
         torch.cuda.synchronize()
-        return [(base_host + base.elapsed_time(ev) / 1e3 - t_sub) * 1e3 for (t_sub, ev) in subs]
+        base = torch.cuda.Event(enable_timing=True)
+        base.record(stream)
+        base.synchronize()
+        base_host = time.perf_counter()
 
-    for mode in ("open", "saturated"):
-        dt, lat = replay(loop_submit, loop_finish, mode == "open")
-        out[f"plain_loop_{mode}"] = dict(_percentiles(lat), mpix_s=px / dt / 1e6, seconds=dt)
-    for p in plans:
-        p.close()
+        def loop_submit(r):
+            plans[idx[id(r)]].restore(r["g"], r["u"], stream)
+            ev = torch.cuda.Event(enable_timing=True)
+            ev.record(stream)
+            return ev
+
+        def loop_finish(subs):
+            torch.cuda.synchronize()
+            return [(base_host + base.elapsed_time(ev) / 1e3 - t_sub) * 1e3 for (t_sub, ev) in subs]
+
+        for mode in ("open", "saturated"):
+            dt, lat = replay(reqs, loop_submit, loop_finish, mode == "open")
+            acc[f"plain_loop_{mode}"]["lat"] += lat
+            acc[f"plain_loop_{mode}"]["s"] += dt
+        for p in plans:
+            p.close()
+        del reqs
+    srv.close()
+    for k, v in acc.items():
+        out[k] = dict(_percentiles(v["lat"]), mpix_s=px / v["s"] / 1e6, seconds=v["s"])
     return out
 
 
@@ -333,11 +535,11 @@ def run_reference(args, rank, world):
     probs = make_problems(name)
     import oracle
 
-    threads = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    threads = host_threads()
     oracle.set_threads(threads)
     # one step = a bounded sample: at most 2 whole restorations of the workload's images
     sample = probs[:2]
-    step = lambda: [oracle.cascade(g.astype(np.float64), L, psf) for (_, psf, L, g) in sample]
+    step = lambda: [oracle_restore(oracle, p, args.smoother) for p in sample]
     for _ in range(args.warmup):
         step()
     if args.steps <= 0:
@@ -346,14 +548,15 @@ def run_reference(args, rank, world):
     for _ in range(args.steps):
         step()
     dt = time.perf_counter() - t0
-    px = sum(g.size for (_, _, _, g) in sample) * args.steps
+    px = sum(p.g.size for p in sample) * args.steps
     val = px / dt / 1e6
     print(json.dumps({
-        "impl": "reference", "metric": "Mpixel/s restored (EECMG, oracle-matched)", "value": val,
+        "impl": "reference", "metric": METRIC, "value": val,
         "unit": "Mpixel/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": name, "images_per_step": len(sample)},
+        "config": {"workload": name, "images_per_step": len(sample),
+                   "stop": "discrepancy, c = 1.1, delta = ||e||_RMS"},
         "cpu_baseline": {"value": val, "unit": "Mpixel/s", "cores": threads, "kind": "oracle",
                          "sample": f"{args.steps} steps of {len(sample)} whole restorations"},
         "e2e": {"value": val, "unit": "Mpixel/s", "h2d_bytes_per_step": 0,
@@ -365,16 +568,19 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=0,
-                    help="timed steps (default: enough for about 1.5 s of timed work, 100..5000)")
+                    help="timed steps (default: enough for about 1.5 s of timed work, 20..5000)")
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--smoother", default="mr2", choices=["mr2", "cgls"])
-    ap.add_argument("--precise-conv", type=int, default=1)
+    ap.add_argument("--precise-conv", type=int, default=-1,
+                    help="-1: per plan (compensated only where a level can run long), 0 or 1")
     ap.add_argument("--storage", default="fp32", choices=["fp32", "bf16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-legs", action="store_true", help="skip the 512^2 and batch64 legs")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--serving-requests", type=int, default=2000)
     args = ap.parse_args()
 
     from paper_2311_03010_gb300 import replicas
@@ -397,188 +603,134 @@ def main():
     eecmg.load()
 
     name = args.workload
-    probs = make_problems(name)
     stream = torch.cuda.current_stream()
-    gs = [torch.from_numpy(g).cuda() for (_, _, _, g) in probs]
-
-    def plan_opts(psf):
-        smo = args.smoother
-        if smo == "mr2" and not np.allclose(psf, psf[::-1, ::-1], rtol=0, atol=1e-15):
-            smo = "cgls"
-        return dict(smoother=smo, precise_conv=args.precise_conv, storage=args.storage)
-
-    # partition of the level solves: autotuned on this workload (before any plan
-    # owns a workspace), untimed
-    tuning_src = "defaults"
-    if not args.no_autotune:
-        descs = [eecmg.Plan(g.shape[1], g.shape[0], L, psf, workspace=0, **plan_opts(psf))
-                 for (_, psf, L, g) in probs]
-        t0 = time.perf_counter()
-        eecmg.eecmg_autotune(descs, gs, reps=5, stream=stream)
-        tuning_src = f"autotuned on this workload in {time.perf_counter() - t0:.1f} s"
-        for d in descs:
-            d.close()
-    tuning = dict(eecmg.eecmg_get_tuning(), source=tuning_src)
-    plans = [eecmg.Plan(g.shape[1], g.shape[0], L, psf, **plan_opts(psf)) for (_, psf, L, g) in probs]
-    us = [torch.empty_like(g) for g in gs]
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-
-    def step():
-        eecmg.eecmg_restore_batched([p.handle for p in plans], gs, us, stream)
+    leg = Leg(torch, eecmg, stream, name, args, autotune=not args.no_autotune)
 
     def barrier():
         replicas.barrier(world)
         torch.cuda.synchronize()
 
     for _ in range(max(3, args.warmup)):
-        step()
+        leg.step()
     barrier()
     if args.steps <= 0:
-        # enough steps for about 1.5 s of timed work (same count on every rank)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        for _ in range(2):  # the second pass is the estimate
-            e0.record(stream)
-            for _ in range(5):
-                flush.zero_()
-                step()
-            e1.record(stream)
-            torch.cuda.synchronize()
-        per = e0.elapsed_time(e1) / 5.0
-        args.steps = int(replicas.max_over_ranks(min(5000, max(100, int(1500.0 / max(per, 1e-3)))),
-                                                 world, "cuda"))
+        args.steps = auto_steps(torch, leg, flush, world)
+
+    # the dominant level-solve launch, hooked by an event pair inside the replayed graph
+    hook_step = dominant_step(torch, leg, flush)
+    eecmg.eecmg_batch_time_step(leg.handles, hook_step, 1)
+    leg.step()
+    barrier()
 
     # timed region
     clocks = ClockSampler(local)
     clocks.start()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(args.steps)]
     barrier()
     clocks.begin()
-    for i in range(args.steps):
-        flush.zero_()
-        ev[i][0].record(stream)
-        step()
-        ev[i][1].record(stream)
+    step_ms, hk = time_steps(torch, leg, args.steps, flush, hook=True)
     barrier()
     clocks.end()
     clk = clocks.stop()
-    step_ms = [a.elapsed_time(b) for (a, b) in ev]
     tot_ms = replicas.max_over_ranks(sum(step_ms), world, "cuda")
-    px_step = sum(g.numel() for g in gs)
-    value = replicas.aggregate_rate(px_step, args.steps, world, tot_ms) / 1e6
+    value = replicas.aggregate_rate(leg.px, args.steps, world, tot_ms) / 1e6
+    launches_per_step = eecmg.eecmg_batch_info(leg.handles)  # kernel nodes of one timed step
 
-    # the plain per-image loop on the same plans (for the batched workload)
-    loop_value = None
-    if len(plans) > 2:
-        for p, g, u in zip(plans, gs, us):
-            p.restore(g, u, stream)
-        barrier()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        loop_steps = max(3, args.steps // 4)
-        loop_ms = 0.0
-        for _ in range(loop_steps):
-            flush.zero_()
-            e0.record(stream)
-            for p, g, u in zip(plans, gs, us):
-                p.restore(g, u, stream)
-            e1.record(stream)
-            torch.cuda.synchronize()
-            loop_ms += e0.elapsed_time(e1)
-        loop_value = px_step * loop_steps / (loop_ms / 1e3) / 1e6
+    # roofline of the hooked launch(es), from the timed region itself
+    k_ms = sum(h[0] for h in hk)
+    k_launches = sum(h[1] for h in hk)
+    k_bytes = sum(h[2] for h in hk)
+    peak, peak_kind = peaks()
+    achieved = k_bytes / (k_ms / 1e3) / 1e9 if k_ms > 0 else 0.0
+    fp = leg.plans[0].info
+    traffic, traffic_src = profiled_traffic(name, hook_step)
+    roofline = {
+        "bound": "hbm", "kernel": f"level solve, cascade step {hook_step} "
+                                  f"({fp['h'][hook_step]}x{fp['w'][hook_step]})",
+        "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+        "traffic": traffic, "traffic_source": traffic_src, "peak_kind": peak_kind,
+        "launches": k_launches, "ms_per_launch": k_ms / max(k_launches, 1),
+        "bytes_per_launch": k_bytes / max(k_launches, 1),
+        "share_of_step": k_ms / sum(step_ms),
+        "method": "CUDA event pair recorded inside the replayed graph around the launch, "
+                  "every timed step; bytes from the iterations each solve ran"}
+    eecmg.eecmg_batch_time_step(leg.handles, hook_step, 0)
 
-    # parity of this run's output against the oracle (first image, rank 0 only)
-    parity = None
-    if rank == 0 and not args.no_cpu_baseline:
-        import oracle
-
-        u_clean, psf0, L0, g0 = probs[0]
-        oracle.set_threads(len(os.sched_getaffinity(0)))
-        ref, _, _ = oracle.cascade(g0.astype(np.float64), L0, psf0, smoother=args.smoother)
-        got = us[0].double().cpu().numpy()
-        parity = {"rel_l2": float(np.linalg.norm(got - ref) / np.linalg.norm(ref)),
-                  "dpsnr_db": float(abs(oracle.psnr(u_clean, got) - oracle.psnr(u_clean, ref))),
-                  "psnr_db": float(oracle.psnr(u_clean, got))}
-        oracle.set_threads(1)
+    outs, iters = leg.outputs(), leg.iters()
 
     # end to end through the public host-buffer entry point (pinned memory):
     # the step's images copied in, restored as one batch, copied out, synchronised
-    gh = [torch.from_numpy(g).pin_memory() for (_, _, _, g) in probs]
+    gh = [torch.from_numpy(p.g).pin_memory() for p in leg.probs]
     uh = [torch.empty_like(x).pin_memory() for x in gh]
-    hp = [p.handle for p in plans]
-    eecmg.eecmg_restore_batched_host(hp, gh, uh, stream)
+    eecmg.eecmg_restore_batched_host(leg.handles, gh, uh, stream)
     barrier()
     e2e_steps = max(3, args.steps // 2)
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        eecmg.eecmg_restore_batched_host(hp, gh, uh, stream)
+        eecmg.eecmg_restore_batched_host(leg.handles, gh, uh, stream)
     barrier()
     e2e_s = replicas.max_over_ranks(time.perf_counter() - t0, world, "cuda")
-    e2e_val = replicas.aggregate_rate(px_step, e2e_steps, world, e2e_s * 1e3) / 1e6
+    e2e_val = replicas.aggregate_rate(leg.px, e2e_steps, world, e2e_s * 1e3) / 1e6
+    config = {"workload": name, "images_per_step": len(leg.gs), "levels": leg.probs[0].L,
+              "smoother": args.smoother, "stop": "discrepancy, c = 1.1, delta = ||e||_RMS of the data, "
+              "economy schedule as the cap", "precise_conv": args.precise_conv,
+              "storage": args.storage, "tile": "32x64 + halo", "partition": leg.tuning,
+              "parallelism": f"replicas x{world}", "l2": "flushed between steps"}
+    leg.close()
 
-    # profiled eager replay of the same restorations (one plan at a time):
-    # per-kernel-class event times
-    prof_steps = min(args.steps, 20) if len(plans) <= 2 else 1
-    for p in plans:
-        eecmg.eecmg_plan_profile(p.handle, 1)
-    for _ in range(prof_steps):
-        flush.zero_()
-        for p, g, u in zip(plans, gs, us):
-            p.restore(g, u, stream)
-    barrier()
-    classes = {}
-    for p in plans:
-        for k, v in eecmg.eecmg_plan_profile_read(p.handle).items():
-            c = classes.setdefault(k, {"launches": 0, "ms": 0.0, "bytes": 0.0})
-            for f in c:
-                c[f] += v[f]
-        eecmg.eecmg_plan_profile(p.handle, 0)
-    launches_per_step = eecmg.eecmg_batch_info(plans)  # graph nodes of one timed step
-    top = max(classes.items(), key=lambda kv: kv[1]["ms"])
-    traffic, traffic_src = profiled_traffic(name)
-    peak, peak_kind = peaks()
-    achieved = top[1]["bytes"] / (top[1]["ms"] / 1e3) / 1e9 if top[1]["ms"] > 0 else 0.0
-    prof_total = sum(c["ms"] for c in classes.values())
+    # parity of this run's output against the oracle (every image, rank 0 only); the
+    # oracle's own run is also the CPU baseline's sample
+    parity = cpu = None
+    oracle_ok = rank == 0 and not args.no_cpu_baseline
+    if oracle_ok:
+        import oracle
 
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(name)
+        threads = host_threads()
+        oracle.set_threads(threads)
+        parity, t_or, px_or = parity_of(oracle, leg.probs, outs, iters, args.smoother)
+        n_or = len(leg.probs)
+        while t_or < 10.0 and world == 1:  # a bounded sample of about 10-30 s of CPU work
+            p = leg.probs[n_or % len(leg.probs)]
+            t0 = time.perf_counter()
+            oracle_restore(oracle, p, args.smoother)
+            t_or += time.perf_counter() - t0
+            px_or += p.g.size
+            n_or += 1
+        oracle.set_threads(1)
+        if world == 1:
+            cpu = {"value": px_or / t_or / 1e6, "unit": "Mpixel/s", "cores": threads, "kind": "oracle",
+                   "sample": f"{n_or} whole restorations of the {name} images "
+                             "(FP64 C oracle, OpenMP), the first also the parity reference",
+                   "seconds": t_or}
+
+    legs = None
+    if not args.no_legs and name == DEFAULT_WORKLOAD:
+        legs = {n: extra_leg(torch, eecmg, stream, n, args, world, flush, oracle_ok) for n in EXTRA_LEGS}
 
     serving = None
     if not args.no_serving:
-        serving = serving_leg(torch, eecmg, stream, args.storage)
+        serving = serving_leg(torch, eecmg, stream, args.storage, n_req=args.serving_requests)
 
     if rank == 0:
         out = {
-            "metric": "Mpixel/s restored (EECMG, oracle-matched)",
+            "metric": METRIC,
             "value": value, "unit": "Mpixel/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": tot_ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": name, "images_per_step": len(gs), "levels": probs[0][2],
-                       "smoother": args.smoother, "precise_conv": args.precise_conv,
-                       "storage": args.storage, "tile": "32x64 + halo", "partition": tuning,
-                       "parallelism": f"replicas x{world}", "l2": "flushed between steps"},
+            "config": config,
             "e2e": {"value": e2e_val, "unit": "Mpixel/s",
-                    "h2d_bytes_per_step": int(sum(g.numel() * 4 for g in gs)),
-                    "d2h_bytes_per_step": int(sum(g.numel() * 4 for g in gs))},
+                    "h2d_bytes_per_step": int(sum(g.numel() * 4 for g in leg.gs)),
+                    "d2h_bytes_per_step": int(sum(g.numel() * 4 for g in leg.gs))},
             "gpu_launches": int(launches_per_step * args.steps),
-            "roofline": {"bound": "hbm", "kernel": top[0], "achieved": achieved, "peak": peak,
-                         "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
-                         "traffic_source": traffic_src,
-                         "peak_kind": peak_kind,
-                         "share_of_step": top[1]["ms"] / prof_total if prof_total else None,
-                         "method": f"event pairs per launch, eager replay of {prof_steps} steps"},
-            "kernel_classes_ms_per_step": {k: v["ms"] / prof_steps for k, v in classes.items()
-                                           if v["launches"]},
+            "roofline": roofline,
             "clocks": clk,
-            "per_image_loop_value": loop_value,
-            "serving": serving,
             "parity": parity,
             "cpu_baseline": cpu,
+            "legs": legs,
+            "serving": serving,
         }
         print(json.dumps(out), flush=True)
-    for p in plans:
-        p.close()
     replicas.finalize(world)
 
 

@@ -74,9 +74,19 @@ enum { EECMG_PROLONG_EECMG = 0, EECMG_PROLONG_IECMG_P = 1, EECMG_PROLONG_IECMG_L
  *                         so residuals and stopping decisions follow the
  *                         stored directions exactly.  Needs persistent = 1
  *                         (else EECMG_ERR_UNSUPPORTED).
- *   stop = FIXED          exactly m_l iterations (Section 2 note), unless
- *                         DISCREPANCY: stop when ||r||_RMS <= c * delta.
- *   c = 1.1, delta = 0    discrepancy constant and noise level ||e||_RMS.
+ *   stop = DISCREPANCY    the stopping rule of Section 2 (after Eq. 10): a
+ *                         level stops before an iteration once
+ *                         ||g_l - H_l u||_RMS <= c * delta, and after at
+ *                         most m_l iterations (the economy schedule is the
+ *                         cap).  FIXED runs exactly m_l iterations (the note
+ *                         of Algorithm 2), which on noisy data iterates far
+ *                         past the noise level and amplifies it.
+ *   c = 1.1, delta = 0    discrepancy constant c > 1 and the noise level
+ *                         delta = ||e||_RMS of the data (the same on every
+ *                         level: the RMS norm does not depend on the grid
+ *                         size).  delta = 0 (noise-free data) leaves only
+ *                         the cap, i.e. the FIXED schedule: pass the data's
+ *                         noise level to get the rule.
  *   diffusion_steps = 1   explicit Perona-Malik steps per prolonged level.
  *   s_scale = 1           scale of the weight argument of Eq. 18.
  *   conv_tol = 1e-5       a level also stops once ||r|| <= conv_tol ||g_l||
@@ -85,9 +95,15 @@ enum { EECMG_PROLONG_EECMG = 0, EECMG_PROLONG_IECMG_P = 1, EECMG_PROLONG_IECMG_L
  *   prolong = EECMG       Algorithm 2; IECMG_P / IECMG_L run Algorithm 1
  *                         with quadratic / linear (Eq. 15) prolongation.
  *   use_graph = 1         capture the cascade as a CUDA graph per plan.
- *   precise_conv = 1      compensated (error-free product + TwoSum) FP32
+ *   precise_conv = -1     1: compensated (error-free product + Kahan) FP32
  *                         accumulation in the second pass of separable
- *                         convolutions; 0 = plain FMA accumulation.
+ *                         convolutions; 0: plain FMA accumulation; -1
+ *                         (auto): 1 where a level can run many iterations
+ *                         (stop = FIXED, or delta = 0), else 0.  Under the
+ *                         discrepancy rule a level stops within a few
+ *                         iterations and the plain pass stays within the
+ *                         FP32 bar of the FP64 result; over a long fixed
+ *                         schedule its rounding grows with the count.
  *   persistent = 1        one cooperative launch per level solve (grid
  *                         barriers inside); 0 = one launch per phase.
  *   workspace = 1         allocate the plan's device workspace; 0 = the plan
@@ -214,6 +230,31 @@ eecmg_status eecmg_restore_batched(const eecmg_plan_t *plans, const float *const
 eecmg_status eecmg_batch_info(const eecmg_plan_t *plans, int n, int *graph_nodes);
 
 /*
+ * Measurement hook (system design, no counterpart in the paper).  With
+ * enable = 1, the CUDA graph that eecmg_restore_batched replays for exactly
+ * these plans in this order also records a pair of CUDA events, as
+ * event-record nodes on the launch stream, immediately before the first and
+ * after the last level-solve launch of cascade step `step` (0 = every
+ * image's coarsest level).  enable = 0 removes them.  A change synchronises
+ * the device and drops the cached graph, which is captured again at the next
+ * eecmg_restore_batched (do not call it during a stream capture).  Errors:
+ * INVALID_ARG if these plans were never restored as a batch or step is out
+ * of range; CUDA.
+ */
+eecmg_status eecmg_batch_time_step(const eecmg_plan_t *plans, int n, int step, int enable);
+
+/*
+ * Reads the hook of the most recent replay: waits for its second event, then
+ * *ms receives the elapsed time between the two events, *launches the
+ * level-solve launches between them and *bytes their algorithmic bytes (each
+ * solver vector read or written once per phase, FP32 or BF16 as stored,
+ * counted from the iterations each solve actually ran).  NULL outputs are
+ * skipped.  INVALID_ARG without an enabled hook and a replay.
+ */
+eecmg_status eecmg_batch_step_time(const eecmg_plan_t *plans, int n, float *ms, int *launches,
+                                   double *bytes);
+
+/*
  * Per-level outcome of the most recent restoration with this plan:
  * iters_done[l] (iterations actually taken) and res_rms[l] (||g_l - H_l
  * u_l||_RMS as carried by the recurrence, Eq. 10).  Synchronises the plan's
@@ -273,6 +314,18 @@ eecmg_status eecmg_prolong(eecmg_plan_t plan, int level, const float *u1, const 
 eecmg_status eecmg_prolong_single(eecmg_plan_t plan, int level, const float *u1, float *out,
                                   int quadratic, cudaStream_t stream);
 
+/*
+ * The start of a prolonged level in Algorithm 2 (Step 2): out = D_l(S_l(P_l(
+ * Pi_l(u1, u2)))), the new extrapolation and quadratic interpolation of
+ * Section 3.2, the local smoothing of Section 3.3 and one Perona-Malik step of
+ * Section 4, as one pass (bitwise equal to eecmg_prolong, eecmg_smooth and
+ * eecmg_denoise in sequence).  level >= 2; u1, u2: device solutions of
+ * levels level-1 and level-2; out: device, level sizes, aliasing neither.
+ * UNSUPPORTED unless the plan has diffusion_steps = 1.  Asynchronous.
+ */
+eecmg_status eecmg_start_level(eecmg_plan_t plan, int level, const float *u1, const float *u2,
+                               float *out, cudaStream_t stream);
+
 /* Local smoothing S_l of Section 3.3 (Eqs. 18-19).  in != out.  Device. */
 eecmg_status eecmg_smooth(eecmg_plan_t plan, int level, const float *in, float *out,
                           cudaStream_t stream);
@@ -306,7 +359,11 @@ eecmg_status eecmg_level_solve(eecmg_plan_t plan, int level, const float *g, flo
  * scalars live in one fixed __device__ array (about 264 KB) that every GPU
  * which loads the library holds until the process exits; no call allocates
  * or frees memory.  The first call on a device looks up that array's device
- * address (once per device); make that first call before any stream capture.
+ * address (once per device); under lazy module loading (CUDA's default) that
+ * lookup is also what loads the library's device code and reserves the
+ * array, so the first call is a warm-up: make it at start-up, before any
+ * stream capture and before a framework allocator reserves the GPU's memory.
+ * Later calls allocate nothing.
  * Every call shares the array and reinitialises it, so calls whose work
  * overlaps on the GPU (other streams, other threads) race: serialise them.
  * Errors: INVALID_ARG (sizes, PSF, NULL or aliased buffers), CUDA.
@@ -380,6 +437,17 @@ eecmg_status eecmg_autotune(const eecmg_plan_t *plans, const float *const *g, in
  */
 eecmg_status eecmg_selftest_bounded_wait(int cluster, cudaStream_t stream);
 
+/*
+ * Diagnostic (no counterpart in the paper): the FP32 FMA rate of the current
+ * GPU, the compute half of the roofline of the convolution and stencil
+ * kernels.  One warm-up and `reps` timed launches (CUDA events on `stream`)
+ * of a kernel running independent fmaf chains on every SM at full
+ * occupancy; *tflops receives the best rate as 2 x FMAs per second / 1e12.
+ * Synchronises the stream; allocates and frees a 1 KB buffer.  Errors:
+ * INVALID_ARG (reps < 1, NULL output), OOM, CUDA.
+ */
+eecmg_status eecmg_probe_fp32_fma(int reps, cudaStream_t stream, double *tflops);
+
 /* ---- serving: continuous batching of restoration requests -------------- */
 
 typedef struct eecmg_server_s *eecmg_server_t;
@@ -398,8 +466,10 @@ eecmg_status eecmg_server_create(size_t mem_budget_bytes, int max_slots, eecmg_s
  * options; shared and read-only, only its description is used; it may be a
  * workspace = 0 plan and must stay alive until the request completes);
  * g_delta, u_out: device buffers that stay valid until the request completes.
- * *ticket receives an id.  Errors: INVALID_ARG, BUSY (queue full),
- * OOM (the request alone exceeds the budget).
+ * *ticket receives an id.  Errors: INVALID_ARG (also a plan with more than 30
+ * levels or more than 16 diffusion steps: the server's per-tick tables are
+ * sized for these at creation and nothing is allocated while serving), BUSY
+ * (queue full), OOM (the request alone exceeds the budget).
  */
 eecmg_status eecmg_server_submit(eecmg_server_t srv, eecmg_plan_t plan, const float *g_delta,
                                  float *u_out, uint64_t *ticket);

@@ -231,7 +231,7 @@ _PROLONG = {"eecmg": 0, "iecmg_p": 1, "iecmg_l": 2}
 
 def cascade(g, L: int, psf, tau: float = 0.2, k: float = 10.0, iters=None,
             smoother: str = "mr2", coarse_op: str = "rms", prolong: str = "eecmg",
-            stop: str = "fixed", c: float = 1.1, delta: float = 0.0,
+            stop: str = "discrepancy", c: float = 1.1, delta: float = 0.0,
             diffusion_steps: int = 1, s_scale: float = 1.0, conv_tol: float = CONV_TOL):
     """Algorithm 2 (or Algorithm 1) on data g; returns (u, iterations, ||r||_RMS per level)."""
     g, psf = _f64(g), _f64(psf)

@@ -109,7 +109,7 @@ eecmg_status plan_waves(const std::vector<std::pair<eecmg_plan_s*, int>>& items,
 void add_op(std::vector<OpGroup>& groups, size_t gi, int op, OpItem it) {
     if (groups.size() <= gi) groups.resize(gi + 1);
     groups[gi].op = op;
-    it.bx = op_blocks_x(it.w);
+    it.bx = op_blocks_x(op, it.w);
     groups[gi].items.push_back(it);
 }
 
@@ -117,7 +117,7 @@ int place_items(OpGroup& g) {
     int blocks = 0;
     for (auto& it : g.items) {
         it.block0 = blocks;
-        blocks += op_blocks(it.h, it.w);
+        blocks += op_blocks(g.op, it.h, it.w);
     }
     return blocks;
 }
@@ -143,8 +143,8 @@ void restrict_ops(const std::vector<eecmg_plan_s*>& plans, std::vector<OpGroup>&
 
 void step_ops(const std::vector<std::pair<eecmg_plan_s*, int>>& items, std::vector<OpGroup>& groups) {
     const size_t base = groups.size();
-    const size_t G_ZERO = base, G_EXTRA = base + 1, G_QUAD = base + 2, G_LIN = base + 3,
-                 G_SMOOTH = base + 4, G_STEP0 = base + 5;  // + diffusion step
+    const size_t G_ZERO = base, G_PSD = base + 1, G_EXTRA = base + 2, G_QUAD = base + 3,
+                 G_LIN = base + 4, G_SMOOTH = base + 5, G_STEP0 = base + 6;  // + diffusion step
     for (auto& itm : items) {
         eecmg_plan_s& P = *itm.first;
         const int st = itm.second;
@@ -161,6 +161,39 @@ void step_ops(const std::vector<std::pair<eecmg_plan_s*, int>>& items, std::vect
         LevelPlan& L1 = P.lv[st - 1];
         float* up = P.vec[0];
         float* sm = P.vec[1];
+        const int steps = P.opt.diffusion_steps;
+        const float kpm = (float)P.kpm;
+        if (P.opt.prolong == EECMG_PROLONG_EECMG && steps >= 1) {  // fused D(S(P(Pi))), then D steps 2..
+            LevelPlan& L2 = P.lv[st - 2];
+            OpItem x;
+            x.a = L1.u;
+            x.b = L2.u;
+            x.out = steps == 1 ? L.u : sm;
+            x.h = L.h;
+            x.w = L.w;
+            x.h1 = L1.h;
+            x.w1 = L1.w;
+            x.h2 = L2.h;
+            x.w2 = L2.w;
+            x.s0 = (float)P.opt.s_scale;
+            x.p0 = (float)P.tau;
+            x.p1 = 1.f / (kpm * kpm);
+            add_op(groups, G_PSD, OP_PSD, x);
+            const float* cur = x.out;
+            for (int d = 1; d < steps; ++d) {
+                float* nxt = (d == steps - 1) ? L.u : (cur == sm ? up : sm);
+                OpItem dn;
+                dn.a = cur;
+                dn.out = nxt;
+                dn.h = L.h;
+                dn.w = L.w;
+                dn.p0 = (float)P.tau;
+                dn.p1 = 1.f / (kpm * kpm);
+                add_op(groups, G_STEP0 + 1 + (size_t)d, OP_DENOISE, dn);
+                cur = nxt;
+            }
+            continue;
+        }
         if (P.opt.prolong == EECMG_PROLONG_EECMG) {  // fused P(Pi)
             LevelPlan& L2 = P.lv[st - 2];
             OpItem x;
@@ -192,7 +225,6 @@ void step_ops(const std::vector<std::pair<eecmg_plan_s*, int>>& items, std::vect
         sms.w = L.w;
         sms.p0 = (float)P.opt.s_scale;
         add_op(groups, G_SMOOTH, OP_SMOOTH, sms);
-        const int steps = P.opt.diffusion_steps;
         if (steps <= 0) {
             OpItem c;
             c.a = sm;
@@ -203,7 +235,6 @@ void step_ops(const std::vector<std::pair<eecmg_plan_s*, int>>& items, std::vect
             continue;
         }
         const float* cur = sm;
-        const float kpm = (float)P.kpm;
         for (int d = 0; d < steps; ++d) {
             float* nxt = (d == steps - 1) ? L.u : (cur == sm ? up : sm);
             OpItem dn;
@@ -248,12 +279,18 @@ struct BatchCtx {
     bool fork01 = false;
     cudaStream_t side = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    // Measurement hook: event-record nodes around the level-solve launches of
+    // cascade step timed_step (-1: none).
+    int timed_step = -1;
+    cudaEvent_t tev[2] = {nullptr, nullptr};
     ~BatchCtx() {
         if (gexec) cudaGraphExecDestroy(gexec);
         if (cap_stream) cudaStreamDestroy(cap_stream);
         if (side) cudaStreamDestroy(side);
         if (ev_fork) cudaEventDestroy(ev_fork);
         if (ev_join) cudaEventDestroy(ev_join);
+        for (cudaEvent_t e : tev)
+            if (e) cudaEventDestroy(e);
         if (dmem) cudaFree(dmem);
     }
 };
@@ -380,9 +417,12 @@ eecmg_status build_ctx(BatchCtx& C) {
 
 eecmg_status enqueue_step(BatchCtx& C, int st, cudaStream_t s) {
     for (const OpLaunch& L : C.step_ops[st]) BCK(launch_ops_batch(L.op, L.d_items, L.n, L.blocks, s));
+    const bool timed = st == C.timed_step && !C.steps[st].empty();
+    if (timed) BCK(cudaEventRecordWithFlags(C.tev[0], s, cudaEventRecordExternal));
     for (auto& w : C.steps[st])
         BCK(launch_level_batch(w.d_jobs, w.d_block_job, w.njobs, w.blocks, w.rt, w.sep, w.prec, w.cgls,
                                w.bf16, w.cluster, w.resident, s));
+    if (timed) BCK(cudaEventRecordWithFlags(C.tev[1], s, cudaEventRecordExternal));
     return EECMG_OK;
 }
 
@@ -494,6 +534,60 @@ eecmg_status batch_graph_nodes(const eecmg_plan_t* plans, int n, int* nodes) {
     if (it == g_batches.end() || !it->second->gexec)
         return set_error(EECMG_ERR_INVALID_ARG, "eecmg_batch_info: no batched restoration of these plans yet");
     *nodes = (int)it->second->graph_nodes;
+    return EECMG_OK;
+}
+
+eecmg_status batch_time_step(const eecmg_plan_t* plans, int n, int step, int enable) {
+    std::vector<eecmg_plan_s*> key(plans, plans + n);
+    std::lock_guard<std::mutex> lock(g_batch_mu);
+    auto it = g_batches.find(key);
+    if (it == g_batches.end())
+        return set_error(EECMG_ERR_INVALID_ARG,
+                         "eecmg_batch_time_step: no batched restoration of these plans yet");
+    BatchCtx& C = *it->second;
+    if (enable && (step < 0 || step >= (int)C.steps.size()))
+        return set_error(EECMG_ERR_INVALID_ARG, "eecmg_batch_time_step: step out of range");
+    const int want = enable ? step : -1;
+    if (want == C.timed_step) return EECMG_OK;
+    for (int i = 0; i < 2 && enable; ++i)
+        if (!C.tev[i]) BCK(cudaEventCreate(&C.tev[i]));
+    // the graph is captured again, with or without the event nodes, at the next replay
+    if (C.gexec) {
+        BCK(cudaDeviceSynchronize());
+        cudaGraphExecDestroy(C.gexec);
+        C.gexec = nullptr;
+    }
+    C.timed_step = want;
+    return EECMG_OK;
+}
+
+eecmg_status batch_step_time(const eecmg_plan_t* plans, int n, float* ms, int* launches,
+                             double* bytes) {
+    std::vector<eecmg_plan_s*> key(plans, plans + n);
+    std::lock_guard<std::mutex> lock(g_batch_mu);
+    auto it = g_batches.find(key);
+    if (it == g_batches.end() || it->second->timed_step < 0 || !it->second->gexec)
+        return set_error(EECMG_ERR_INVALID_ARG,
+                         "eecmg_batch_step_time: no timed replay (eecmg_batch_time_step, then "
+                         "eecmg_restore_batched)");
+    BatchCtx& C = *it->second;
+    const int st = C.timed_step;
+    BCK(cudaEventSynchronize(C.tev[1]));
+    float t = 0.f;
+    BCK(cudaEventElapsedTime(&t, C.tev[0], C.tev[1]));
+    if (ms) *ms = t;
+    if (launches) *launches = (int)C.steps[st].size();
+    if (bytes) {
+        double b = 0.0;
+        for (eecmg_plan_s* P : C.plans) {
+            if (st >= P->L) continue;
+            Scalars sc;
+            BCK(cudaMemcpy(&sc, P->sc + st, sizeof(Scalars), cudaMemcpyDeviceToHost));
+            const int nzero = P->opt.prolong == EECMG_PROLONG_EECMG ? 2 : 1;
+            b += level_solve_bytes(P, st, sc, st < nzero);
+        }
+        *bytes = b;
+    }
     return EECMG_OK;
 }
 

@@ -50,8 +50,9 @@ void restrict_ops(const std::vector<eecmg_plan_s*>& plans, std::vector<OpGroup>&
 
 // The start of cascade step items[i] = (plan, level) before its level solve:
 // the zero start (Algorithm 2's first levels) or the prolongation chain of
-// prolong_enqueue (Pi or not, P or L, S, the D steps), with the same buffers
-// and per-pixel code.  Groups appended in execution order.
+// prolong_enqueue (the fused D(S(P(Pi))) pass and any further D steps; or Pi
+// or not, P or L, S, the D steps), with the same buffers and per-pixel code.
+// Groups appended in execution order.
 void step_ops(const std::vector<std::pair<eecmg_plan_s*, int>>& items, std::vector<OpGroup>& groups);
 
 // Sets each item's block0 within its group; returns the group's blocks.

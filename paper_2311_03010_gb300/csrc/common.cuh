@@ -50,6 +50,11 @@ struct alignas(64) Scalars {
     unsigned int counter; // last-block arrival counter (reset by the last block)
     int loops;            // iterations whose first phase ran (for byte accounting)
     DF lim2d;             // lim2 as a double-float pair (the per-iteration tests)
+    // MR-II early check (see fin_mr_b): a step applied ahead of its iteration's phase B
+    DF lim2spec;          // threshold on the predicted ||r_k||^2 (-1: never predict)
+    int spec;             // 1: the next phase applies step `iters` and checks ||r||
+    int applied;          // the last step applied by such a check (0: none)
+    double bpp;           // algorithmic bytes per pixel of the phases run so far
     // MR-II, Lanczos / Givens form (double-float scalars: see finish.cuh)
     DF nrm, nrm_prev;     // ||v_k||, ||v_{k-1}|| (w_k = v_k / ||v_k||)
     DF inv_nrm, inv_nrm_prev;  // their reciprocals

@@ -37,6 +37,13 @@ __device__ __forceinline__ void fin_resid(Scalars* sc, DF rr2, DF gg2, double co
     sc->lim2d = df_from_double(lim2);
     sc->iters = 0;
     sc->loops = 0;
+    sc->spec = 0;
+    sc->applied = 0;
+    // MR-II predicts ||r_k|| (fin_mr_b) only where the discrepancy limit is the one that binds:
+    // there the residual stays within a small factor of ||r_0|| and the prediction is accurate
+    // to rounding; at a convergence limit far below ||r_0|| it would be all cancellation
+    sc->lim2spec = (disc2 > 0.0 && disc2 >= l1) ? df_from_double(lim2 * (1.0 + 1.0 / 64.0))
+                                                : DF{-1.f, 0.f};
     if (!(rr < 1.0e300)) sc->stopped = 3;
     else sc->stopped = (rr <= lim2) ? 1 : 0;
 }
@@ -84,6 +91,7 @@ __device__ __forceinline__ void fin_mr_a(Scalars* sc, DF hv) {
 // record the coefficients of step k.
 __device__ __forceinline__ void fin_mr_b(Scalars* sc, int k, DF rr, DF vv, DF vr) {
     const bool step = k >= 2;
+    sc->spec = 0;
     if (step) {
         if (!df_finite(rr)) {
             sc->stopped = 3;
@@ -145,8 +153,26 @@ __device__ __forceinline__ void fin_mr_b(Scalars* sc, int k, DF rr, DF vv, DF vr
     sc->f_tau = tau.hi;
     sc->f_scale = inv_new.hi;
     if (!(nrm_new.hi > 0.f)) sc->stopped = 4;  // Krylov space exhausted: step k is the last
+    // Step k moves tau_k out of the residual: ||r_k||^2 = ||r_{k-1}||^2 - tau_k^2 (the Givens
+    // rotation is orthogonal).  When this prediction is at or below the limit (with a margin),
+    // the kernel applies step k at once and checks ||r_k|| explicitly (fin_mr_check) instead of
+    // first spending the convolution of iteration k + 1, whose phase B would find the stop.
+    // The step and its check are the same arithmetic either way, so the prediction changes the
+    // work done, never the result.
+    const DF rprev = step ? rr : df_from_double(sc->rr);  // k = 1: ||r_0||^2
+    sc->spec = (sc->stopped == 0 && df_le(df_sub2(rprev, df_mul(tau, tau)), sc->lim2spec)) ? 1 : 0;
     // the FP64 copy for the host last: its conversion is off the coefficients' path
     if (step) sc->rr = df_to_double(rr);
+}
+
+// The early check of step k, applied by the phase just ended: ||r_k||^2 against the limit.
+// If it does not stop, phase B of iteration k + 1 skips the step it would otherwise apply.
+__device__ __forceinline__ void fin_mr_check(Scalars* sc, int k, DF rr) {
+    sc->applied = k;
+    sc->spec = 0;
+    sc->rr = df_to_double(rr);
+    if (!df_finite(rr)) sc->stopped = 3;
+    else if (df_le(rr, sc->lim2d)) sc->stopped = 1;
 }
 
 __device__ __forceinline__ void fin_mr_final(Scalars* sc, DF rr) {

@@ -79,23 +79,24 @@ cudaError_t launch_cg_p(float* p, const float* sv, size_t n, Scalars* sc, cudaSt
 // Batched per-level operations (one launch per kind for many images).
 enum OpKind : int {
     OP_RESTRICT = 0, OP_EXTRAPOLATE, OP_QUADRATIC, OP_LINEAR, OP_SMOOTH, OP_DENOISE, OP_ZERO, OP_COPY,
-    OP_PROLONG, OP_KINDS
+    OP_PROLONG, OP_PSD, OP_KINDS
 };
 // One image's operation: output grid h x w (restriction: the coarse grid,
 // w1 = fine width; Pi: the level-(l-1) grid, inputs h1 x w1 and h2 x w2;
 // fused P(Pi): output h x w, inputs a = u_{l-1} (h1 x w1), b = u_{l-2} (h2 x w2);
-// P / L: input h1 x w1; S: p0 = scale; D: p0 = tau, p1 = 1 / k^2).  bx and
+// P / L: input h1 x w1; S: p0 = scale; D: p0 = tau, p1 = 1 / k^2; fused D(S(P(Pi))):
+// the inputs of P(Pi), s0 = scale, p0 = tau, p1 = 1 / k^2).  bx and
 // block0 place its blocks within the launch (filled by the host).
 struct OpItem {
     const float* a = nullptr;
     const float* b = nullptr;
     float* out = nullptr;
     int h = 0, w = 0, h1 = 0, w1 = 0, h2 = 0, w2 = 0;
-    float p0 = 0.f, p1 = 0.f;
+    float p0 = 0.f, p1 = 0.f, s0 = 0.f;
     int bx = 0, block0 = 0;
 };
-int op_blocks(int h, int w);   // blocks covering an h x w output
-int op_blocks_x(int w);        // of which along x
+int op_blocks(int op, int h, int w);  // blocks of operation kind op covering an h x w output
+int op_blocks_x(int op, int w);       // of which along x
 cudaError_t launch_ops_batch(int op, const OpItem* d_items, int n, int total_blocks, cudaStream_t s);
 
 cudaError_t launch_restrict(const float* fine, int hf, int wf, float* coarse, int hc, int wc,
@@ -105,6 +106,10 @@ cudaError_t launch_extrapolate(const float* u1, int h1, int w1, const float* u2,
 // The nonlinear prolongation P(Pi(u1, u2)) of Section 3.2 in one pass (out h x w).
 cudaError_t launch_prolong(const float* u1, int h1, int w1, const float* u2, int h2, int w2,
                            float* out, int h, int w, cudaStream_t s);
+// D(S(P(Pi(u1, u2)))) in one pass (out h x w): the start of a prolonged level of Algorithm 2
+// with one Perona-Malik step.
+cudaError_t launch_psd(const float* u1, int h1, int w1, const float* u2, int h2, int w2, float* out,
+                       int h, int w, float scale, float tau, float kpm, cudaStream_t s);
 cudaError_t launch_quadratic(const float* ut, int h1, int w1, float* out, int h, int w,
                              cudaStream_t s);
 cudaError_t launch_linear(const float* uc, int hc, int wc, float* out, int h, int w,

@@ -29,17 +29,22 @@ __global__ void k_restrict(const float* __restrict__ fine, int wf, float* __rest
 // d = u1|coarse - u2), i.e. (5 u1 - u2)/4 at coarse nodes, u1 + (d_a + d_b)/8
 // at edge midpoints and u1 + (sum of four d)/16 at cell centres; indices
 // past the last level-(l-2) node are clamped to it.  The differences of the
-// two near-equal iterates are taken in FP64.
+// two near-equal iterates are taken exactly (TwoSum: each is a double-float
+// pair, as exact as an FP64 difference of two FP32 values) and summed in
+// double-float, all on the FP32 pipes: GB300's FP64 pipe is narrow, and an
+// FP64 form of this made the prolongation 20x slower than its memory traffic.
+// The result is the double-float value rounded once to FP32.
 __device__ __forceinline__ float pi_at(const float* __restrict__ u1, int w1,
                                       const float* __restrict__ u2, int h2, int w2, int a, int b) {
     const int A0 = a >> 1, B0 = b >> 1;
     const int A1 = (a & 1) ? min(A0 + 1, h2 - 1) : A0;
     const int B1 = (b & 1) ? min(B0 + 1, w2 - 1) : B0;
-    auto d = [&](int A, int B) -> double {
-        return (double)u1[(size_t)(2 * A) * w1 + 2 * B] - (double)u2[(size_t)A * w2 + B];
+    auto d = [&](int A, int B) -> DF {
+        return two_sum(u1[(size_t)(2 * A) * w1 + 2 * B], -u2[(size_t)A * w2 + B]);
     };
-    const double dsum = d(A0, B0) + d(A0, B1) + d(A1, B0) + d(A1, B1);
-    return (float)((double)u1[(size_t)a * w1 + b] + 0.0625 * dsum);
+    const DF dsum = df_add2(df_add2(d(A0, B0), d(A0, B1)), df_add2(d(A1, B0), d(A1, B1)));
+    const DF e = df_add2(DF{u1[(size_t)a * w1 + b], 0.f}, DF{0.0625f * dsum.hi, 0.0625f * dsum.lo});
+    return __fadd_rn(e.hi, e.lo);
 }
 __device__ __forceinline__ void px_extrapolate(const float* __restrict__ u1, int h1, int w1,
                                                const float* __restrict__ u2, int h2, int w2,
@@ -154,9 +159,7 @@ __global__ void k_linear(const float* __restrict__ uc, int hc, int wc, float* __
 // cross vector c, slope = C^+ c (eigenvalues below 1e-6 W dropped) and
 // a0 = u_c + vb - slope . (sb, tb).
 template <class Rd>
-__device__ __forceinline__ void px_smooth_rd(Rd rd, float* __restrict__ out, int h, int w, float scale,
-                                             int i, int j) {
-    if (i >= h || j >= w) return;
+__device__ __forceinline__ float smooth_value_rd(Rd rd, int h, int w, float scale, int i, int j) {
     const float uc = rd(i, j);
     float ws[9], ss[9], ts[9], vs[9];
     float W = 0.f, sb = 0.f, tb = 0.f, vb = 0.f;
@@ -226,7 +229,13 @@ __device__ __forceinline__ void px_smooth_rd(Rd rd, float* __restrict__ out, int
         gs = fmaf(c2, e2s, gs);
         gt = fmaf(c2, e2t, gt);
     }
-    out[(size_t)i * w + j] = uc + vb - (gs * sb + gt * tb);
+    return uc + vb - (gs * sb + gt * tb);
+}
+template <class Rd>
+__device__ __forceinline__ void px_smooth_rd(Rd rd, float* __restrict__ out, int h, int w, float scale,
+                                             int i, int j) {
+    if (i >= h || j >= w) return;
+    out[(size_t)i * w + j] = smooth_value_rd(rd, h, w, scale, i, j);
 }
 // S for one BY x BX block at (y0, x0): the input with a 1-pixel halo is staged
 // in shared memory once (the 3 x 3 fits read it nine times); same arithmetic
@@ -265,9 +274,7 @@ __device__ __forceinline__ float pm_c_rd(Rd u, int h, int w, int i, int j, float
 }
 // c at (i, j) from a reader Cd of precomputed c, u from Ud.
 template <class Ud, class Cd>
-__device__ __forceinline__ void px_denoise_rd(Ud in, Cd c, float* __restrict__ out, int h, int w,
-                                              float tau, int i, int j) {
-    if (i >= h || j >= w) return;
+__device__ __forceinline__ float denoise_value_rd(Ud in, Cd c, int h, int w, float tau, int i, int j) {
     const float uc = in(i, j);
     const float cc = c(i, j);
     float f = 0.f;
@@ -275,7 +282,13 @@ __device__ __forceinline__ void px_denoise_rd(Ud in, Cd c, float* __restrict__ o
     if (i > 0) f += 0.5f * (c(i - 1, j) + cc) * (in(i - 1, j) - uc);
     if (j + 1 < w) f += 0.5f * (c(i, j + 1) + cc) * (in(i, j + 1) - uc);
     if (j > 0) f += 0.5f * (c(i, j - 1) + cc) * (in(i, j - 1) - uc);
-    out[(size_t)i * w + j] = fmaf(tau, f, uc);
+    return fmaf(tau, f, uc);
+}
+template <class Ud, class Cd>
+__device__ __forceinline__ void px_denoise_rd(Ud in, Cd c, float* __restrict__ out, int h, int w,
+                                              float tau, int i, int j) {
+    if (i >= h || j >= w) return;
+    out[(size_t)i * w + j] = denoise_value_rd(in, c, h, w, tau, i, j);
 }
 // D for one BY x BX block at (y0, x0): the input with a 2-pixel halo and the
 // diffusivities c with a 1-pixel halo are staged in shared memory (c computed
@@ -309,6 +322,95 @@ __global__ void __launch_bounds__(BX* BY) k_denoise(const float* __restrict__ in
     tile_denoise(in, out, h, w, tau, inv_k2, blockIdx.y * BY, blockIdx.x * BX);
 }
 
+// The start of a prolonged level (Algorithm 2, Step 2) in one pass: D(S(P(Pi(u1, u2)))) for
+// one PSD_TH x PSD_TW block of fine pixels at (y0, x0).  D needs S's output with a 2-pixel halo
+// (its own 4 neighbours and their diffusivities), S needs P's with a 1-pixel halo beyond that,
+// and P the level-(l-1) window of Pi values its triplets read; each stage is computed for its
+// whole region into shared memory (pixels outside the image are never read), with the
+// per-pixel arithmetic of k_prolong, k_smooth and k_denoise, so the result equals those three
+// kernels in sequence bitwise, while the two intermediate images never leave the SM.  Halo
+// work: P on 1.30x, S on 1.20x, c on 1.10x the block's pixels.  Called by every thread of a
+// 256-thread block.
+constexpr int PSD_TH = 32, PSD_TW = 64;
+constexpr int PSD_PH = PSD_TH + 6, PSD_PW = PSD_TW + 6;  // P: 3-pixel halo
+constexpr int PSD_SH = PSD_TH + 4, PSD_SW = PSD_TW + 4;  // S: 2
+constexpr int PSD_CH = PSD_TH + 2, PSD_CW = PSD_TW + 2;  // c: 1
+// Pi window: n consecutive fine indices read level-(l-1) indices 2A .. 2A' + 2 with
+// A' - A <= (n + 2) / 4
+constexpr int PSD_XR = 2 * ((PSD_PH + 2) / 4) + 3, PSD_XC = 2 * ((PSD_PW + 2) / 4) + 3;
+struct PsdSmem {
+    float X[PSD_XR][PSD_XC];
+    float P[PSD_PH][PSD_PW];
+    float S[PSD_SH][PSD_SW];
+    float C[PSD_CH][PSD_CW];
+};
+__device__ __forceinline__ void tile_psd(PsdSmem& M, const float* __restrict__ u1, int h1, int w1,
+                                         const float* __restrict__ u2, int h2, int w2,
+                                         float* __restrict__ out, int h, int w, float scale, float tau,
+                                         float inv_k2, int y0, int x0) {
+    const int tid = threadIdx.y * BX + threadIdx.x;
+    constexpr int NT = BX * BY;
+    // fine region of P (clipped to the image) and its Pi window
+    const int py0 = max(y0 - 3, 0), px0 = max(x0 - 3, 0);
+    const int py1 = min(y0 + PSD_TH + 3, h), px1 = min(x0 + PSD_TW + 3, w);  // exclusive
+    const int r0 = 2 * (py0 >> 2), c0 = 2 * (px0 >> 2);
+    const int nr = 2 * (((py1 - 1) >> 2) - (py0 >> 2)) + 3;
+    const int nc = 2 * (((px1 - 1) >> 2) - (px0 >> 2)) + 3;
+    for (int k = tid; k < nr * nc; k += NT) {
+        const int rr = k / nc, cc = k - rr * nc;
+        M.X[rr][cc] = pi_at(u1, w1, u2, h2, w2, min(r0 + rr, h1 - 1), min(c0 + cc, w1 - 1));
+    }
+    __syncthreads();
+    // P on rows y0-3 .. y0+TH+2 and columns x0-3 .. x0+TW+2 (in-image part)
+    for (int k = tid; k < PSD_PH * PSD_PW; k += NT) {
+        const int rr = k / PSD_PW, cc = k - rr * PSD_PW;
+        const int y = y0 - 3 + rr, x = x0 - 3 + cc;
+        float acc = 0.f;
+        if (y >= 0 && y < h && x >= 0 && x < w) {
+            const int A = y >> 2, ty = y & 3, B = x >> 2, tx = x & 3;
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                // staged row 2A + i - r0 holds level-(l-1) row min(2A + i, h1 - 1), as P reads
+                const float* er = M.X[2 * A + i - r0];
+                float row = 0.f;
+#pragma unroll
+                for (int j = 0; j < 3; ++j) row = fmaf(c_qw[tx][j], er[2 * B + j - c0], row);
+                acc = fmaf(c_qw[ty][i], row, acc);
+            }
+        }
+        M.P[rr][cc] = acc;
+    }
+    __syncthreads();
+    auto pr = [&](int a, int b) { return M.P[a - y0 + 3][b - x0 + 3]; };
+    for (int k = tid; k < PSD_SH * PSD_SW; k += NT) {
+        const int rr = k / PSD_SW, cc = k - rr * PSD_SW;
+        const int y = y0 - 2 + rr, x = x0 - 2 + cc;
+        M.S[rr][cc] = (y >= 0 && y < h && x >= 0 && x < w) ? smooth_value_rd(pr, h, w, scale, y, x) : 0.f;
+    }
+    __syncthreads();
+    auto sr = [&](int a, int b) { return M.S[a - y0 + 2][b - x0 + 2]; };
+    for (int k = tid; k < PSD_CH * PSD_CW; k += NT) {
+        const int rr = k / PSD_CW, cc = k - rr * PSD_CW;
+        const int y = y0 - 1 + rr, x = x0 - 1 + cc;
+        M.C[rr][cc] = (y >= 0 && y < h && x >= 0 && x < w) ? pm_c_rd(sr, h, w, y, x, inv_k2) : 0.f;
+    }
+    __syncthreads();
+    auto cr = [&](int a, int b) { return M.C[a - y0 + 1][b - x0 + 1]; };
+    for (int k = tid; k < PSD_TH * PSD_TW; k += NT) {
+        const int rr = k / PSD_TW, cc = k - rr * PSD_TW;
+        px_denoise_rd(sr, cr, out, h, w, tau, y0 + rr, x0 + cc);
+    }
+}
+
+__global__ void __launch_bounds__(BX* BY) k_psd(const float* __restrict__ u1, int h1, int w1,
+                                               const float* __restrict__ u2, int h2, int w2,
+                                               float* __restrict__ out, int h, int w, float scale,
+                                               float tau, float inv_k2) {
+    __shared__ PsdSmem M;
+    tile_psd(M, u1, h1, w1, u2, h2, w2, out, h, w, scale, tau, inv_k2, blockIdx.y * PSD_TH,
+             blockIdx.x * PSD_TW);
+}
+
 // Many operations of one kind in one launch (the server's ticks): block b
 // serves the item whose block range holds b (binary search over block0),
 // with the same per-pixel code as the single launches above.
@@ -333,6 +435,12 @@ __global__ void __launch_bounds__(BX* BY) k_ops_batch(const OpItem* __restrict__
     if constexpr (OP == OP_DENOISE) tile_denoise(it.a, it.out, it.h, it.w, it.p0, it.p1, by * BY, bx * BX);
     if constexpr (OP == OP_PROLONG)
         tile_prolong(it.a, it.h1, it.w1, it.b, it.h2, it.w2, it.out, it.h, it.w, by * BY, bx * BX);
+    if constexpr (OP == OP_PSD) {
+        __shared__ PsdSmem M;
+        // this block's tile of the 32 x 64 grid (bx counts PSD_TW-wide tiles)
+        tile_psd(M, it.a, it.h1, it.w1, it.b, it.h2, it.w2, it.out, it.h, it.w, it.s0, it.p0, it.p1,
+                 by * PSD_TH, bx * PSD_TW);
+    }
     if constexpr (OP == OP_ZERO || OP == OP_COPY) {
         if (y < it.h && x < it.w) it.out[(size_t)y * it.w + x] = OP == OP_ZERO ? 0.f : it.a[(size_t)y * it.w + x];
     }
@@ -368,6 +476,14 @@ cudaError_t launch_prolong(const float* u1, int h1, int w1, const float* u2, int
     return cudaGetLastError();
 }
 
+cudaError_t launch_psd(const float* u1, int h1, int w1, const float* u2, int h2, int w2, float* out,
+                       int h, int w, float scale, float tau, float kpm, cudaStream_t s) {
+    if (h <= 0 || w <= 0) return cudaSuccess;
+    const dim3 grid((w + PSD_TW - 1) / PSD_TW, (h + PSD_TH - 1) / PSD_TH);
+    k_psd<<<grid, dim3(BX, BY), 0, s>>>(u1, h1, w1, u2, h2, w2, out, h, w, scale, tau, 1.f / (kpm * kpm));
+    return cudaGetLastError();
+}
+
 cudaError_t launch_quadratic(const float* ut, int h1, int w1, float* out, int h, int w,
                              cudaStream_t s) {
     if (h <= 0 || w <= 0) return cudaSuccess;
@@ -395,13 +511,14 @@ cudaError_t launch_denoise(const float* in, float* out, int h, int w, float tau,
     return cudaGetLastError();
 }
 
-int op_blocks(int h, int w) {
+int op_blocks(int op, int h, int w) {
     if (h <= 0 || w <= 0) return 0;
+    if (op == OP_PSD) return ((w + PSD_TW - 1) / PSD_TW) * ((h + PSD_TH - 1) / PSD_TH);
     const dim3 g = grid2(h, w);
     return (int)(g.x * g.y);
 }
 
-int op_blocks_x(int w) { return (w + BX - 1) / BX; }
+int op_blocks_x(int op, int w) { return op == OP_PSD ? (w + PSD_TW - 1) / PSD_TW : (w + BX - 1) / BX; }
 
 cudaError_t launch_ops_batch(int op, const OpItem* d_items, int n, int total_blocks, cudaStream_t s) {
     if (n <= 0 || total_blocks <= 0) return cudaSuccess;
@@ -415,6 +532,7 @@ cudaError_t launch_ops_batch(int op, const OpItem* d_items, int n, int total_blo
         case OP_ZERO: return launch_op<OP_ZERO>(d_items, n, total_blocks, s);
         case OP_COPY: return launch_op<OP_COPY>(d_items, n, total_blocks, s);
         case OP_PROLONG: return launch_op<OP_PROLONG>(d_items, n, total_blocks, s);
+        case OP_PSD: return launch_op<OP_PSD>(d_items, n, total_blocks, s);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -338,9 +338,16 @@ __device__ __forceinline__ void mr2_res_body(ConvSmem<R, SEP> (&S)[2], const Lev
             conv_phase_res<R, SEP, PREC, false, true>(S, X, 0, J.u, epi);
         float v[2] = {a0, a1};
         const double ct2 = J.conv_tol2, d2 = J.disc2;
-        if (!sy.reduce<2>(v, [&](DF* t) { fin_resid(sc, t[0], t[1], ct2, d2); })) return;
+        const double b0 = J.zero_start ? 8.0 : 12.0;
+        if (!sy.reduce<2>(v, [&](DF* t) {
+                fin_resid(sc, t[0], t[1], ct2, d2);
+                sc->bpp = b0;
+            }))
+            return;
     }
     if (J.m <= 0 || volatile_stopped(sc)) return;  // u is still u0 in global memory
+    // algorithmic bytes per pixel of the vector phases (as the streaming solver counts them)
+    auto hist = [](int j) { return 8.0 * ((j >= 2 ? 1 : 0) + (j >= 3 ? 1 : 0)); };
 
     // v_1 = H r_0, ||v_1||, <v_1, r_0>
     {
@@ -353,7 +360,11 @@ __device__ __forceinline__ void mr2_res_body(ConvSmem<R, SEP> (&S)[2], const Lev
                                                        a1 = fmaf(z, ctr, a1);
                                                    });
         float v[2] = {a0, a1};
-        if (!sy.reduce<2>(v, [&](DF* t) { fin_mr_v1(sc, t[0], t[1]); })) return;
+        if (!sy.reduce<2>(v, [&](DF* t) {
+                fin_mr_v1(sc, t[0], t[1]);
+                sc->bpp += 8.0;
+            }))
+            return;
     }
 
     for (int k = 1; k <= J.m; ++k) {
@@ -373,12 +384,18 @@ __device__ __forceinline__ void mr2_res_body(ConvSmem<R, SEP> (&S)[2], const Lev
                                                        });
             float v[1] = {a0};
             TRACE(X.bid, 11);
-            if (!sy.reduce<1>(v, [&](DF* t) { fin_mr_a(sc, t[0]); })) return;
+            if (!sy.reduce<1>(v, [&](DF* t) {
+                    fin_mr_a(sc, t[0]);
+                    sc->bpp += 8.0;
+                }))
+                return;
         }
         TRACE(X.bid, 12);
-        // phase B: pending step k-1, v_{k+1}, stopping rules, rotation of column k
+        // phase B: pending step k-1 (unless an early check applied it), v_{k+1}, stopping
+        // rules, rotation of column k
         {
             const bool step = k >= 2;
+            const bool apply = step && *(volatile const int*)&sc->applied != k - 1;
             const StepCoef c = step_coef(sc);
             const float ca = vldf(&sc->f_ca), ca_lo = vldf(&sc->f_ca_lo);
             const float cb = step ? vldf(&sc->f_cb) : 0.f, cb_lo = step ? vldf(&sc->f_cb_lo) : 0.f;
@@ -389,8 +406,8 @@ __device__ __forceinline__ void mr2_res_body(ConvSmem<R, SEP> (&S)[2], const Lev
                 const float4 rr = lds4(X.vec(VR), q);
                 float4 vj = make_float4(0.f, 0.f, 0.f, 0.f), awj = vj, uu = vj;
                 float4 dA = vj, hA = vj, dB = vj, hB = vj;
-                if (step) {
-                    vj = lds4(X.vec(VV + sj), q);
+                if (step) vj = lds4(X.vec(VV + sj), q);
+                if (apply) {
                     awj = lds4(X.vec(VAW + sj), q);
                     uu = lds4(X.vec(VU), q);
                     if (j >= 2) {
@@ -403,7 +420,7 @@ __device__ __forceinline__ void mr2_res_body(ConvSmem<R, SEP> (&S)[2], const Lev
                     }
                 }
                 float4 rv = rr;
-                if (step) {  // step j = k - 1 (the operation order of mr_step4)
+                if (apply) {  // step j = k - 1 (the operation order of mr_step4)
                     float4 dj = mul4(c.dw, vj);
                     float4 hj = mul4(c.dinv, awj);
                     if (j >= 2) {
@@ -419,8 +436,8 @@ __device__ __forceinline__ void mr2_res_body(ConvSmem<R, SEP> (&S)[2], const Lev
                     sts4(X.vec(VU), q, fma4(c.tau, dj, uu));
                     rv = fma4(-c.tau, hj, rr);
                     sts4(X.vec(VR), q, rv);
-                    arr = dot4(rv, rv, arr);
                 }
+                if (step) arr = dot4(rv, rv, arr);
                 float4 vn = fma4(-ca_lo, vk, fma4(-ca, vk, awk));
                 if (step) vn = fma4(-cb_lo, vj, fma4(-cb, vj, vn));
                 sts4(X.vec(VV + sk1), q, vn);
@@ -429,15 +446,38 @@ __device__ __forceinline__ void mr2_res_body(ConvSmem<R, SEP> (&S)[2], const Lev
             }
             float v[3] = {arr, avv, avr};
             TRACE(X.bid, 13);
-            if (!sy.reduce<3>(v, [&](DF* t) { fin_mr_b(sc, k, t[0], t[1], t[2]); })) return;
+            const double bb = k == 1 ? 16.0 : (apply ? 44.0 + hist(k - 1) : 20.0);
+            if (!sy.reduce<3>(v, [&](DF* t) {
+                    fin_mr_b(sc, k, t[0], t[1], t[2]);
+                    sc->bpp += bb;
+                }))
+                return;
         }
         TRACE(X.bid, 14);
+        // early check of step k (fin_mr_b predicted ||r_k|| at the limit): apply it now and
+        // test ||r_k||, so that a solve that stops here skips iteration k + 1's convolution
+        if (k < J.m && *(volatile const int*)&sc->spec && !volatile_stopped(sc)) {
+            const StepCoef c = step_coef(sc);
+            float arr = 0.f;
+            for (int q = threadIdx.x; q < n4; q += NTHREADS) {
+                const float4 rv = res_step4(X, k, q, c);
+                arr = dot4(rv, rv, arr);
+            }
+            float v[1] = {arr};
+            const double bc = 32.0 + hist(k);
+            if (!sy.reduce<1>(v, [&](DF* t) {
+                    fin_mr_check(sc, k, t[0]);
+                    sc->bpp += bc;
+                }))
+                return;
+        }
     }
 
-    // the step decided last (breakdown-with-step or the schedule's end)
+    // the step decided last (breakdown-with-step or the schedule's end), unless an early
+    // check applied it already
     const int st = volatile_stopped(sc);
     const int j = *(volatile const int*)&sc->iters;
-    if ((st == 0 || st == 4) && j >= 1) {
+    if ((st == 0 || st == 4) && j >= 1 && *(volatile const int*)&sc->applied != j) {
         const StepCoef c = step_coef(sc);
         float arr = 0.f;
         for (int q = threadIdx.x; q < n4; q += NTHREADS) {
@@ -445,7 +485,12 @@ __device__ __forceinline__ void mr2_res_body(ConvSmem<R, SEP> (&S)[2], const Lev
             arr = dot4(rv, rv, arr);
         }
         float v[1] = {arr};
-        if (!sy.reduce<1>(v, [&](DF* t) { fin_mr_final(sc, t[0]); })) return;
+        const double bf = 32.0 + hist(j);
+        if (!sy.reduce<1>(v, [&](DF* t) {
+                fin_mr_final(sc, t[0]);
+                sc->bpp += bf;
+            }))
+            return;
     }
     // u back to global memory
     const float* u = X.vec(VU);

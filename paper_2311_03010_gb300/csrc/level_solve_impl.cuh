@@ -160,10 +160,19 @@ __device__ __forceinline__ void mr2_body(ConvSmem<R, SEP>& S, const LevelJob& J,
             conv_phase<R, SEP, PREC, false>(S, J.u, h, w, nb, bid, epi);
         float v[2] = {a0, a1};
         const double ct2 = J.conv_tol2, d2 = J.disc2;
-        if (!sy.reduce<2>(v, [&](DF* t) { fin_resid(sc, t[0], t[1], ct2, d2); }))
+        const double b0 = J.zero_start ? 8.0 : 12.0;
+        if (!sy.reduce<2>(v, [&](DF* t) {
+                fin_resid(sc, t[0], t[1], ct2, d2);
+                sc->bpp = b0;
+            }))
             return;
     }
     if (J.m <= 0 || volatile_stopped(sc)) return;
+
+    // bytes per pixel of the vector phases (each operand read or written once;
+    // the d history is stored as HT)
+    constexpr double E = (double)sizeof(HT);
+    auto hist = [](int j) { return (4.0 + E) * ((j >= 2 ? 1 : 0) + (j >= 3 ? 1 : 0)); };
 
     // v_1 = H r_0, ||v_1||, <v_1, r_0>
     {
@@ -175,7 +184,10 @@ __device__ __forceinline__ void mr2_body(ConvSmem<R, SEP>& S, const LevelJob& J,
             a1 = fmaf(z, ctr, a1);
         });
         float v[2] = {a0, a1};
-        if (!sy.reduce<2>(v, [&](DF* t) { fin_mr_v1(sc, t[0], t[1]); }))
+        if (!sy.reduce<2>(v, [&](DF* t) {
+                fin_mr_v1(sc, t[0], t[1]);
+                sc->bpp += 8.0;
+            }))
             return;
     }
 
@@ -196,13 +208,18 @@ __device__ __forceinline__ void mr2_body(ConvSmem<R, SEP>& S, const LevelJob& J,
                                             });
             float v[1] = {a0};
             TRACE(bid, 11);
-            if (!sy.reduce<1>(v, [&](DF* t) { fin_mr_a(sc, t[0]); }))
+            if (!sy.reduce<1>(v, [&](DF* t) {
+                    fin_mr_a(sc, t[0]);
+                    sc->bpp += 8.0;
+                }))
                 return;
         }
         TRACE(bid, 12);
-        // phase B: pending step k-1, v_{k+1}, stopping rules, rotation of column k
+        // phase B: pending step k-1 (unless an early check applied it), v_{k+1}, stopping
+        // rules, rotation of column k
         {
             const bool step = k >= 2;
+            const bool apply = step && *(volatile const int*)&sc->applied != k - 1;
             const StepCoef c = step_coef(sc);
             // Lanczos coefficients in double-float: the update below cancels
             const float ca = vldf(&sc->f_ca), ca_lo = vldf(&sc->f_ca_lo);
@@ -220,8 +237,8 @@ __device__ __forceinline__ void mr2_body(ConvSmem<R, SEP>& S, const LevelJob& J,
                 const float4 rr = ld4cg(J.r, q);
                 float4 vj = make_float4(0.f, 0.f, 0.f, 0.f), awj = vj, uu = vj;
                 float4 dA = vj, hA = vj, dB = vj, hB = vj;
-                if (step) {
-                    vj = ld4cg(J.v[sj], q);
+                if (step) vj = ld4cg(J.v[sj], q);
+                if (apply) {
                     awj = ld4cg(J.aw[sj], q);
                     uu = ld4cg(J.u, q);
                     if (j >= 2) {
@@ -234,7 +251,7 @@ __device__ __forceinline__ void mr2_body(ConvSmem<R, SEP>& S, const LevelJob& J,
                     }
                 }
                 float4 rv = rr;
-                if (step) {  // step j = k - 1 (same operation order as mr_step4)
+                if (apply) {  // step j = k - 1 (same operation order as mr_step4)
                     float4 dj = mul4(c.dw, vj);
                     float4 hj = mul4(c.dinv, awj);
                     if (j >= 2) {
@@ -250,8 +267,8 @@ __device__ __forceinline__ void mr2_body(ConvSmem<R, SEP>& S, const LevelJob& J,
                     st4(J.u, q, fma4(c.tau, dj, uu));
                     rv = fma4(-c.tau, hj, rr);
                     st4(J.r, q, rv);
-                    arr = dot4(rv, rv, arr);
                 }
+                if (step) arr = dot4(rv, rv, arr);
                 float4 vn = fma4(-ca_lo, vk, fma4(-ca, vk, awk));
                 if (step) vn = fma4(-cb_lo, vj, fma4(-cb, vj, vn));
                 st4(J.v[sk1], q, vn);
@@ -260,13 +277,9 @@ __device__ __forceinline__ void mr2_body(ConvSmem<R, SEP>& S, const LevelJob& J,
             }
             if (bid == 0) {  // the n mod 4 tail
                 for (size_t i = 4 * n4 + threadIdx.x; i < n; i += NTHREADS) {
-                    float rv;
-                    if (step) {
-                        rv = mr_step_px<HT>(J, k - 1, i, c.dw, c.d1, c.d2, c.dinv, c.tau);
-                        arr = fmaf(rv, rv, arr);
-                    } else {
-                        rv = ldcg(J.r + i);
-                    }
+                    const float rv = apply ? mr_step_px<HT>(J, k - 1, i, c.dw, c.d1, c.d2, c.dinv, c.tau)
+                                           : ldcg(J.r + i);
+                    if (step) arr = fmaf(rv, rv, arr);
                     const float vki = ldcg(J.v[sk] + i);
                     float vn = fmaf(-ca_lo, vki, fmaf(-ca, vki, ldcg(J.aw[sk] + i)));
                     if (step) {
@@ -280,16 +293,44 @@ __device__ __forceinline__ void mr2_body(ConvSmem<R, SEP>& S, const LevelJob& J,
             }
             float v[3] = {arr, avv, avr};
             TRACE(bid, 13);
-            if (!sy.reduce<3>(v, [&](DF* t) { fin_mr_b(sc, k, t[0], t[1], t[2]); }))
+            const double bb = k == 1 ? 16.0 : (apply ? 40.0 + E + hist(k - 1) : 20.0);
+            if (!sy.reduce<3>(v, [&](DF* t) {
+                    fin_mr_b(sc, k, t[0], t[1], t[2]);
+                    sc->bpp += bb;
+                }))
                 return;
         }
         TRACE(bid, 14);
+        // early check of step k (fin_mr_b predicted ||r_k|| at the limit): apply it now and
+        // test ||r_k||, so that a solve that stops here skips iteration k + 1's convolution
+        if (k < J.m && *(volatile const int*)&sc->spec && !volatile_stopped(sc)) {
+            const StepCoef c = step_coef(sc);
+            float arr = 0.f;
+            const size_t n4 = n >> 2;
+            for (size_t q = (size_t)bid * NTHREADS + threadIdx.x; q < n4; q += stride) {
+                const float4 rv = mr_step4<HT>(J, k, q, c);
+                arr = dot4(rv, rv, arr);
+            }
+            if (bid == 0)
+                for (size_t i = 4 * n4 + threadIdx.x; i < n; i += NTHREADS) {
+                    const float rv = mr_step_px<HT>(J, k, i, c.dw, c.d1, c.d2, c.dinv, c.tau);
+                    arr = fmaf(rv, rv, arr);
+                }
+            float v[1] = {arr};
+            const double bc = 28.0 + E + hist(k);
+            if (!sy.reduce<1>(v, [&](DF* t) {
+                    fin_mr_check(sc, k, t[0]);
+                    sc->bpp += bc;
+                }))
+                return;
+        }
     }
 
-    // the step decided last (breakdown-with-step or the schedule's end)
+    // the step decided last (breakdown-with-step or the schedule's end), unless an early
+    // check applied it already
     const int st = volatile_stopped(sc);
     const int j = *(volatile const int*)&sc->iters;
-    if ((st == 0 || st == 4) && j >= 1) {
+    if ((st == 0 || st == 4) && j >= 1 && *(volatile const int*)&sc->applied != j) {
         const StepCoef c = step_coef(sc);
         float arr = 0.f;
         const size_t n4 = n >> 2;
@@ -303,7 +344,11 @@ __device__ __forceinline__ void mr2_body(ConvSmem<R, SEP>& S, const LevelJob& J,
                 arr = fmaf(rv, rv, arr);
             }
         float v[1] = {arr};
-        sy.reduce<1>(v, [&](DF* t) { fin_mr_final(sc, t[0]); });
+        const double bf = 28.0 + E + hist(j);
+        sy.reduce<1>(v, [&](DF* t) {
+            fin_mr_final(sc, t[0]);
+            sc->bpp += bf;
+        });
     }
 }
 

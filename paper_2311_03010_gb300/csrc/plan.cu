@@ -170,23 +170,12 @@ double level_solve_bytes(const eecmg_plan_s* P, int l, const Scalars& sc, bool z
     // bytes per element of the BF16-able direction vectors (MR-II d; CGLS s,
     // p): 2 in the BF16-storage variant
     const double e = P->opt.storage == EECMG_STORAGE_BF16 ? 2.0 : 4.0;
+    // MR-II: the solver adds each phase's bytes per pixel as it runs (the early
+    // checks of the discrepancy rule change which phases run)
+    if (P->opt.smoother == EECMG_SMOOTHER_MR2) return sc.bpp * n;
     double b = (zero_start ? 8.0 : 12.0) * n;  // r = g - H u
     const int K = sc.loops;
-    if (P->opt.smoother == EECMG_SMOOTHER_MR2) {
-        if (K > 0 || sc.iters > 0) b += 8.0 * n;  // v_1 = H r_0
-        for (int k = 1; k <= K; ++k) {
-            b += 8.0 * n;  // H w_k
-            if (k == 1) {
-                b += 16.0 * n;
-            } else {
-                const int j = k - 1;
-                b += n * (4.0 * 9 + (4.0 + e) * (1 + (j >= 2 ? 1 : 0) + (j >= 3 ? 1 : 0)));
-            }
-        }
-        const int j = sc.iters;
-        if ((sc.stopped == 0 || sc.stopped == 4) && j >= 1)
-            b += n * (4.0 * 6 + (4.0 + e) * (1 + (j >= 2 ? 1 : 0) + (j >= 3 ? 1 : 0)));
-    } else {
+    {
         if (K > 0 || sc.iters > 0) b += (4.0 + 2 * e) * n;  // s = H^T r, p = s
         b += (e + 4.0 + e + 4.0 + 16.0) * n * K;          // q = H p; u, r update
         if (K > 1) b += (4.0 + e + 3 * e) * n * (K - 1);  // s = H^T r; p = s + beta p
@@ -402,6 +391,24 @@ eecmg_status prolong_enqueue(eecmg_plan_s* P, int l, cudaStream_t s) {
     LevelPlan& L = P->lv[l];
     LevelPlan& L1 = P->lv[l - 1];
     float* up = P->vec[0];  // prolonged, level l
+    const int steps = P->opt.diffusion_steps;
+    if (P->opt.prolong == EECMG_PROLONG_EECMG && steps >= 1) {
+        // D(S(P(Pi(u_{l-1}, u_{l-2})))) in one pass, then the further D steps
+        LevelPlan& L2 = P->lv[l - 2];
+        float* sm = P->vec[1];
+        float* first = steps == 1 ? L.u : sm;
+        LK(P, s, KC_PROLONG, 4.0 * ((double)L1.h * L1.w + (double)L2.h * L2.w + (double)L.h * L.w),
+           launch_psd(L1.u, L1.h, L1.w, L2.u, L2.h, L2.w, first, L.h, L.w, (float)P->opt.s_scale,
+                      (float)P->tau, (float)P->kpm, s));
+        float* cur = first;
+        for (int d = 1; d < steps; ++d) {
+            float* nxt = (d == steps - 1) ? L.u : (cur == sm ? up : sm);
+            LK(P, s, KC_DENOISE, 8.0 * L.h * L.w,
+               launch_denoise(cur, nxt, L.h, L.w, (float)P->tau, (float)P->kpm, s));
+            cur = nxt;
+        }
+        return EECMG_OK;
+    }
     if (P->opt.prolong == EECMG_PROLONG_EECMG) {  // P(Pi(u_{l-1}, u_{l-2})), one fused pass
         LevelPlan& L2 = P->lv[l - 2];
         LK(P, s, KC_PROLONG, 4.0 * ((double)L1.h * L1.w + (double)L2.h * L2.w + (double)L.h * L.w),
@@ -415,7 +422,6 @@ eecmg_status prolong_enqueue(eecmg_plan_s* P, int l, cudaStream_t s) {
     }
     float* sm = P->vec[1];
     LK(P, s, KC_SMOOTH, 8.0 * L.h * L.w, launch_smooth(up, sm, L.h, L.w, (float)P->opt.s_scale, s));
-    const int steps = P->opt.diffusion_steps;
     if (steps <= 0) {
         LK(P, s, KC_COPY, 8.0 * L.h * L.w,
            cudaMemcpyAsync(L.u, sm, sizeof(float) * L.h * L.w, cudaMemcpyDeviceToDevice, s));
@@ -555,7 +561,7 @@ eecmg_status eecmg_default_options(eecmg_options* o) {
     o->smoother = EECMG_SMOOTHER_MR2;
     o->coarse_op = EECMG_COARSE_GALERKIN_RMS;
     o->storage = EECMG_STORAGE_FP32;
-    o->stop = EECMG_STOP_FIXED;
+    o->stop = EECMG_STOP_DISCREPANCY;
     o->c = 1.1;
     o->delta = 0.0;
     o->diffusion_steps = 1;
@@ -563,7 +569,7 @@ eecmg_status eecmg_default_options(eecmg_options* o) {
     o->conv_tol = 1e-5;
     o->prolong = EECMG_PROLONG_EECMG;
     o->use_graph = 1;
-    o->precise_conv = 1;
+    o->precise_conv = -1;
     o->persistent = 1;
     o->workspace = 1;
     return EECMG_OK;
@@ -588,10 +594,15 @@ eecmg_status eecmg_plan(int width, int height, int levels, const double* psf, in
     if (opt) o = *opt;
     if (o.smoother < 0 || o.smoother > 1 || o.coarse_op < 0 || o.coarse_op > 1 || o.storage < 0 ||
         o.storage > 1 || o.stop < 0 || o.stop > 1 || o.prolong < 0 || o.prolong > 2 ||
-        o.diffusion_steps < 0 || !(o.conv_tol >= 0.0) || !(o.s_scale >= 0.0))
+        o.diffusion_steps < 0 || !(o.conv_tol >= 0.0) || !(o.s_scale >= 0.0) ||
+        o.precise_conv < -1 || o.precise_conv > 1)
         return set_error(EECMG_ERR_INVALID_ARG, "eecmg_plan: invalid option value");
     if (o.stop == EECMG_STOP_DISCREPANCY && (!(o.c > 0.0) || !(o.delta >= 0.0)))
         return set_error(EECMG_ERR_INVALID_ARG, "eecmg_plan: discrepancy rule needs c > 0, delta >= 0");
+    // compensated convolution where a level can run many iterations (the fixed schedule, or
+    // no noise level): there FP32 rounding of the second pass grows with the count
+    if (o.precise_conv < 0)
+        o.precise_conv = (o.stop == EECMG_STOP_FIXED || !(o.delta > 0.0)) ? 1 : 0;
     if (o.storage == EECMG_STORAGE_BF16 && !o.persistent)
         return set_error(EECMG_ERR_UNSUPPORTED,
                          "eecmg_plan: BF16 storage needs the persistent level solve (persistent = 1)");
@@ -864,6 +875,23 @@ eecmg_status eecmg_prolong_single(eecmg_plan_t P, int level, const float* u1, fl
     return EECMG_OK;
 }
 
+eecmg_status eecmg_start_level(eecmg_plan_t P, int level, const float* u1, const float* u2, float* out,
+                               cudaStream_t s) {
+    eecmg_status st = check_level(P, level, "eecmg_start_level");
+    if (st != EECMG_OK) return st;
+    if (level < 2) return set_error(EECMG_ERR_INVALID_ARG, "eecmg_start_level: level must be >= 2");
+    if (!u1 || !u2 || !out || out == u1 || out == u2)
+        return set_error(EECMG_ERR_INVALID_ARG, "eecmg_start_level: NULL or aliased buffers");
+    if (P->opt.diffusion_steps != 1)
+        return set_error(EECMG_ERR_UNSUPPORTED, "eecmg_start_level: needs diffusion_steps = 1");
+    LevelPlan& L = P->lv[level];
+    LevelPlan& L1 = P->lv[level - 1];
+    LevelPlan& L2 = P->lv[level - 2];
+    CK(launch_psd(u1, L1.h, L1.w, u2, L2.h, L2.w, out, L.h, L.w, (float)P->opt.s_scale, (float)P->tau,
+                  (float)P->kpm, s));
+    return EECMG_OK;
+}
+
 eecmg_status eecmg_smooth(eecmg_plan_t P, int level, const float* in, float* out, cudaStream_t s) {
     eecmg_status st = check_level(P, level, "eecmg_smooth");
     if (st != EECMG_OK) return st;
@@ -954,6 +982,17 @@ eecmg_status eecmg_restore_batched_host(const eecmg_plan_t* plans, const float* 
 eecmg_status eecmg_batch_info(const eecmg_plan_t* plans, int n, int* graph_nodes) {
     if (!plans || n < 1 || !graph_nodes) return set_error(EECMG_ERR_INVALID_ARG, "eecmg_batch_info: bad arguments");
     return batch_graph_nodes(plans, n, graph_nodes);
+}
+
+eecmg_status eecmg_batch_time_step(const eecmg_plan_t* plans, int n, int step, int enable) {
+    if (!plans || n < 1) return set_error(EECMG_ERR_INVALID_ARG, "eecmg_batch_time_step: bad arguments");
+    return batch_time_step(plans, n, step, enable);
+}
+
+eecmg_status eecmg_batch_step_time(const eecmg_plan_t* plans, int n, float* ms, int* launches,
+                                   double* bytes) {
+    if (!plans || n < 1) return set_error(EECMG_ERR_INVALID_ARG, "eecmg_batch_step_time: bad arguments");
+    return batch_step_time(plans, n, ms, launches, bytes);
 }
 
 eecmg_status eecmg_restore_batched(const eecmg_plan_t* plans, const float* const* g, float* const* u,

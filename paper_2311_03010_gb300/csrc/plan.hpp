@@ -100,4 +100,9 @@ eecmg_status restore_batched_impl(const eecmg_plan_t* plans, const float* const*
                                   int n, cudaStream_t s);
 void forget_plan_batches(eecmg_plan_s* P);
 eecmg_status batch_graph_nodes(const eecmg_plan_t* plans, int n, int* nodes);
+eecmg_status batch_time_step(const eecmg_plan_t* plans, int n, int step, int enable);
+eecmg_status batch_step_time(const eecmg_plan_t* plans, int n, float* ms, int* launches,
+                             double* bytes);
+// Algorithmic bytes of a persistent level solve from the iterations it ran.
+double level_solve_bytes(const eecmg_plan_s* P, int l, const Scalars& sc, bool zero_start);
 }  // namespace eecmg

@@ -1,10 +1,12 @@
-// selftest.cu -- diagnostic: the bounded waits of the level-solve barriers.
+// selftest.cu -- diagnostics: the bounded waits of the level-solve barriers,
+// and a probe of the GPU's FP32 FMA rate (the compute half of the roofline).
 //
 // One block runs one reduction barrier whose arrival count can never be
 // reached (it claims to be one of two blocks, or expects two arrivals on its
 // cluster mbarrier while only itself delivers), with a wait limit of about
 // 10 microseconds.  The wait must give up, set the job's error flag and let
 // the block return; nothing faults or hangs, and the context stays usable.
+#include <algorithm>
 #include <string>
 
 #include "launch.hpp"
@@ -71,5 +73,69 @@ extern "C" eecmg_status eecmg_selftest_bounded_wait(int cluster, cudaStream_t s)
     if (e != cudaSuccess)
         return set_error(EECMG_ERR_CUDA, std::string("eecmg_selftest_bounded_wait: ") + cudaGetErrorString(e));
     if (err) return set_error(EECMG_ERR_TIMEOUT, "eecmg_selftest_bounded_wait: the wait gave up as designed");
+    return EECMG_OK;
+}
+
+namespace {
+
+// Independent fmaf chains: 8 per thread, 16 rounds per loop trip, so every
+// SM sub-partition always has FMAs ready to issue.  The chains stay bounded
+// (|x| -> b / (1 - a)); the store is only there to keep them alive.
+constexpr int PROBE_CHAINS = 8, PROBE_UNROLL = 16, PROBE_THREADS = 256;
+
+__global__ void __launch_bounds__(PROBE_THREADS) k_fma_probe(float* sink, int iters, float a, float b) {
+    float x[PROBE_CHAINS];
+#pragma unroll
+    for (int i = 0; i < PROBE_CHAINS; ++i) x[i] = 1e-3f * (float)threadIdx.x + (float)i;
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int u = 0; u < PROBE_UNROLL; ++u)
+#pragma unroll
+            for (int i = 0; i < PROBE_CHAINS; ++i) x[i] = fmaf(x[i], a, b);
+    }
+    float t = 0.f;
+#pragma unroll
+    for (int i = 0; i < PROBE_CHAINS; ++i) t += x[i];
+    if (t == -1.0f) sink[threadIdx.x] = t;  // never true for these inputs
+}
+
+}  // namespace
+
+extern "C" eecmg_status eecmg_probe_fp32_fma(int reps, cudaStream_t s, double* tflops) {
+    if (reps < 1 || !tflops) return set_error(EECMG_ERR_INVALID_ARG, "eecmg_probe_fp32_fma: bad arguments");
+    int dev = 0, nsm = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fma_probe, PROBE_THREADS, 0);
+    if (e != cudaSuccess || per_sm < 1)
+        return set_error(EECMG_ERR_CUDA, "eecmg_probe_fp32_fma: device query failed");
+    float* sink = nullptr;
+    e = cudaMalloc((void**)&sink, sizeof(float) * PROBE_THREADS);
+    if (e != cudaSuccess) return set_error(EECMG_ERR_OOM, "eecmg_probe_fp32_fma: scratch");
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    const int blocks = nsm * per_sm, iters = 4096;
+    const double fmas = (double)blocks * PROBE_THREADS * iters * PROBE_UNROLL * PROBE_CHAINS;
+    double best = 0.0;
+    for (int r = 0; r <= reps && e == cudaSuccess; ++r) {  // launch 0 warms up
+        e = cudaEventRecord(e0, s);
+        if (e == cudaSuccess) {
+            k_fma_probe<<<blocks, PROBE_THREADS, 0, s>>>(sink, iters, 0.9999999f, 1e-7f);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e == cudaSuccess && r > 0 && ms > 0.f) best = std::max(best, 2.0 * fmas / (ms * 1e-3) / 1e12);
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(sink);
+    if (e != cudaSuccess)
+        return set_error(EECMG_ERR_CUDA, std::string("eecmg_probe_fp32_fma: ") + cudaGetErrorString(e));
+    *tflops = best;
     return EECMG_OK;
 }

@@ -43,8 +43,26 @@ using Clock = std::chrono::steady_clock;
 constexpr int RING = 2;              // ticks in flight
 constexpr size_t QUEUE_CAP = 65536;  // queued (not yet admitted) requests
 constexpr int MAX_LEVELS = 30;
+constexpr int MAX_DIFFUSION = 16;    // Perona-Malik steps per level of a served request
 
 size_t round256(size_t b) { return (b + 255) / 256 * 256; }
+
+// Upper bound of one tick's job tables and operation items (enqueue_tick), so
+// that the tick ring is allocated once, at creation.  Every active request
+// adds at most MAX_LEVELS + 4 + MAX_DIFFUSION operation items (the copy of its
+// data, the restriction to each coarser level, the reset of its scalars, the
+// start of its cascade step: zero start or prolongation, smoothing, the
+// diffusion steps; the copy of its result) and one level-solve job of at most
+// max(16, 3 x SMs) blocks; there are at most 11 + MAX_DIFFUSION operation
+// groups and one wave per job, each table rounded up to 256 bytes.
+size_t tick_table_bound(int max_slots, int nsm) {
+    const size_t slots = (size_t)max_slots;
+    const size_t items = slots * (MAX_LEVELS + 4 + MAX_DIFFUSION);
+    const size_t groups = 11 + MAX_DIFFUSION;
+    const size_t job_blocks = std::max<size_t>(16, 3 * (size_t)nsm);
+    return items * sizeof(OpItem) + 256 * groups + slots * (sizeof(LevelJob) + 256) +
+           slots * (sizeof(unsigned short) * job_blocks + 256);
+}
 
 // First-fit allocator over [0, cap): free ranges by offset, coalesced on
 // release.
@@ -178,26 +196,6 @@ void bind_slot(Request* r, char* ws) {
 
 char* stat_area(eecmg_server_s* S, int sidx) { return S->h_stat + (size_t)sidx * S->stat_stride; }
 
-// Grows the tick ring to hold `bytes` per slot (waits for the ticks in flight).
-eecmg_status ensure_ring(eecmg_server_s* S, size_t bytes) {
-    if (bytes <= S->ring_bytes) return EECMG_OK;
-    size_t nb = S->ring_bytes;
-    while (nb < bytes) nb *= 2;
-    SCK(cudaStreamSynchronize(S->stream));
-    char *d = nullptr, *h = nullptr;
-    SCK(cudaMalloc((void**)&d, RING * nb));
-    if (cudaMallocHost((void**)&h, RING * nb) != cudaSuccess) {
-        cudaFree(d);
-        return set_error(EECMG_ERR_OOM, "eecmg_server: tick ring");
-    }
-    cudaFree(S->d_ring);
-    cudaFreeHost(S->h_ring);
-    S->d_ring = d;
-    S->h_ring = h;
-    S->ring_bytes = nb;
-    return EECMG_OK;
-}
-
 // Enqueues tick k's work on the server stream; `finishing` receives the
 // requests whose finest level ran in it.  Every per-level operation of the
 // tick is one batched launch per kind over all requests (k_ops_batch), then
@@ -257,8 +255,8 @@ eecmg_status enqueue_tick(eecmg_server_s* S, const std::vector<Request*>& admitt
         for (auto& g : *gs) need += round256(sizeof(OpItem) * g.items.size());
     for (auto& w : waves)
         need += round256(sizeof(LevelJob) * w.jobs.size()) + round256(sizeof(unsigned short) * w.block_job.size());
-    e = ensure_ring(S, need);
-    if (e != EECMG_OK) return e;
+    if (need > S->ring_bytes)
+        return set_error(EECMG_ERR_INVALID_ARG, "eecmg_server: tick tables exceed the ring slot");
     char* h = S->h_ring + (size_t)k * S->ring_bytes;
     char* d = S->d_ring + (size_t)k * S->ring_bytes;
     size_t off = 0;
@@ -491,9 +489,8 @@ eecmg_status eecmg_server_create(size_t mem_budget_bytes, int max_slots, eecmg_s
         return fail(EECMG_ERR_OOM, std::string("arena: ") + cudaGetErrorString(e));
     }
     S->arena.reset(S->budget);
-    // one job per active request per tick; at most 2 x SMs blocks per job
-    S->ring_bytes = (size_t)max_slots * (round256(sizeof(LevelJob)) + 512 +
-                                         round256(sizeof(unsigned short) * 2 * (size_t)S->nsm)) + 1024;
+    // sized once for the largest tick admission allows (no allocation while serving)
+    S->ring_bytes = round256(tick_table_bound(max_slots, S->nsm));
     S->stat_stride = round256((sizeof(Scalars) + sizeof(GroupSync)) * MAX_LEVELS);
     e = cudaStreamCreateWithFlags(&S->stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaMalloc((void**)&S->d_ring, RING * S->ring_bytes);
@@ -521,10 +518,11 @@ eecmg_status eecmg_server_submit(eecmg_server_t S, eecmg_plan_t P, const float* 
     if (!S || !P || !g || !u || !ticket)
         return set_error(EECMG_ERR_INVALID_ARG, "eecmg_server_submit: NULL argument");
     *ticket = 0;
-    if (P->L > MAX_LEVELS || !P->opt.persistent || P->device != S->device)
+    if (P->L > MAX_LEVELS || P->opt.diffusion_steps > MAX_DIFFUSION || !P->opt.persistent ||
+        P->device != S->device)
         return set_error(EECMG_ERR_INVALID_ARG,
                          "eecmg_server_submit: the plan must use the persistent level solve, at most "
-                         "30 levels, on the server's device");
+                         "30 levels and 16 diffusion steps, on the server's device");
     if (round256(P->ws_bytes) > S->budget)
         return set_error(EECMG_ERR_OOM, "eecmg_server_submit: the request alone exceeds the memory budget");
     auto* r = new (std::nothrow) Request();

@@ -84,6 +84,8 @@ _SIGS = {
     "eecmg_restore_batched": [ctypes.POINTER(_VP), ctypes.POINTER(_VP), ctypes.POINTER(_VP), _I,
                               _VP],
     "eecmg_plan_stats": [_VP, _PI, _PD],
+    "eecmg_batch_time_step": [ctypes.POINTER(_VP), _I, _I, _I],
+    "eecmg_batch_step_time": [ctypes.POINTER(_VP), _I, ctypes.POINTER(ctypes.c_float), _PI, _PD],
     "eecmg_batch_info": [ctypes.POINTER(_VP), _I, _PI],
     "eecmg_restore_batched_host": [ctypes.POINTER(_VP), ctypes.POINTER(_VP), ctypes.POINTER(_VP), _I,
                                    _VP],
@@ -94,11 +96,13 @@ _SIGS = {
     "eecmg_restrict": [_VP, _I, _VP, _VP, _VP],
     "eecmg_prolong": [_VP, _I, _VP, _VP, _VP, _VP],
     "eecmg_prolong_single": [_VP, _I, _VP, _VP, _I, _VP],
+    "eecmg_start_level": [_VP, _I, _VP, _VP, _VP, _VP],
     "eecmg_smooth": [_VP, _I, _VP, _VP, _VP],
     "eecmg_denoise": [_VP, _I, _VP, _VP, _VP],
     "eecmg_level_solve": [_VP, _I, _VP, _VP, _I, _VP],
     "eecmg_residual_noalloc": [_I, _I, _PD, _I, _I, _VP, _VP, _VP, _VP, _VP],
     "eecmg_selftest_bounded_wait": [_I, _VP],
+    "eecmg_probe_fp32_fma": [_I, _VP, _PD],
     "eecmg_get_tuning": [ctypes.POINTER(eecmg_tuning)],
     "eecmg_set_tuning": [ctypes.POINTER(eecmg_tuning)],
     "eecmg_autotune": [ctypes.POINTER(_VP), ctypes.POINTER(_VP), _I, _I, _VP,
@@ -285,6 +289,10 @@ def eecmg_prolong_single(plan, level, u1, out, quadratic=1, stream=None):
           _stream(stream))
 
 
+def eecmg_start_level(plan, level, u1, u2, out, stream=None):
+    _call("eecmg_start_level", plan, int(level), _ptr(u1), _ptr(u2), _ptr(out), _stream(stream))
+
+
 def eecmg_smooth(plan, level, x, y, stream=None):
     _call("eecmg_smooth", plan, int(level), _ptr(x), _ptr(y), _stream(stream))
 
@@ -303,7 +311,16 @@ def eecmg_residual_noalloc(width, height, psf, g, u, r, norms, stream=None):
     norms is a device buffer of two float64 values (tensor or address).
     """
     psf = np.ascontiguousarray(psf, dtype=np.float64)
-    nptr = norms if isinstance(norms, int) else norms.data_ptr()
+    if psf.ndim != 2 or psf.shape[0] % 2 != 1 or psf.shape[1] % 2 != 1:
+        raise ValueError("psf must be a 2-D array with odd sides")
+    if isinstance(norms, int):
+        nptr = norms
+    else:
+        if str(norms.dtype) != "torch.float64" or not norms.is_contiguous() or norms.numel() < 2:
+            raise ValueError("norms must be a contiguous float64 tensor of at least 2 elements")
+        if not norms.is_cuda:
+            raise ValueError("norms must be a device tensor")
+        nptr = norms.data_ptr()
     _call("eecmg_residual_noalloc", int(width), int(height), psf.ctypes.data_as(_PD),
           psf.shape[1], psf.shape[0], _ptr(g), _ptr(u), _ptr(r), nptr, _stream(stream))
 
@@ -331,6 +348,22 @@ def eecmg_batch_info(plans):
     return k.value
 
 
+def eecmg_batch_time_step(plans, step, enable=1):
+    """Event pair inside the batched graph of these plans around cascade step `step`'s solves."""
+    n = len(plans)
+    hp = (_VP * n)(*[p.handle if isinstance(p, Plan) else p for p in plans])
+    _call("eecmg_batch_time_step", hp, n, int(step), int(enable))
+
+
+def eecmg_batch_step_time(plans):
+    """(ms, level-solve launches, algorithmic bytes) of the hooked step in the last replay."""
+    n = len(plans)
+    hp = (_VP * n)(*[p.handle if isinstance(p, Plan) else p for p in plans])
+    ms, k, b = ctypes.c_float(), _I(), _D()
+    _call("eecmg_batch_step_time", hp, n, ctypes.byref(ms), ctypes.byref(k), ctypes.byref(b))
+    return ms.value, k.value, b.value
+
+
 def eecmg_get_tuning():
     t = eecmg_tuning()
     _call("eecmg_get_tuning", ctypes.byref(t))
@@ -356,6 +389,13 @@ def eecmg_selftest_bounded_wait(cluster, stream=None):
     """Returns the status code (EECMG_ERR_TIMEOUT = 6 is the designed outcome)."""
     lib = load()
     return lib.eecmg_selftest_bounded_wait(int(cluster), _stream(stream))
+
+
+def eecmg_probe_fp32_fma(reps=5, stream=None):
+    """Measured FP32 FMA rate of the current GPU in TFLOP/s (2 flops per FMA)."""
+    t = _D()
+    _call("eecmg_probe_fp32_fma", int(reps), _stream(stream), ctypes.byref(t))
+    return t.value
 
 
 def eecmg_server_create(mem_budget_bytes, max_slots):

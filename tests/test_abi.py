@@ -40,9 +40,10 @@ def test_every_declared_symbol_is_exported(lib):
 def test_version_and_defaults(lib):
     assert "sm_103a" in lib.eecmg_version()
     o = lib.eecmg_default_options()
-    assert (o.smoother, o.coarse_op, o.storage, o.stop) == (0, 0, 0, 0)
+    assert (o.smoother, o.coarse_op, o.storage, o.stop) == (0, 0, 0, 1)  # stop: discrepancy rule
     assert (o.c, o.delta, o.diffusion_steps, o.s_scale) == (1.1, 0.0, 1, 1.0)
-    assert o.conv_tol == 1e-5 and o.prolong == 0 and o.use_graph == 1 and o.precise_conv == 1 and o.persistent == 1
+    assert o.conv_tol == 1e-5 and o.prolong == 0 and o.use_graph == 1 and o.persistent == 1
+    assert o.precise_conv == -1  # resolved per plan: compensated where a level can run long
     assert o.workspace == 1
 
 

@@ -25,7 +25,8 @@ def test_reference_arm_prints_one_json_line():
     assert d["cpu_baseline"]["cores"] >= 1
     assert d["e2e"] == {"value": d["value"], "unit": "Mpixel/s", "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}
-    assert d["config"]["workload"] == "512x512-gauss2.5-L5"
+    assert d["config"]["workload"] == "4096x4096-gauss3-L5"
+    assert d["config"]["stop"].startswith("discrepancy")
 
 
 class _Proc:

@@ -6,11 +6,12 @@ tolerance the specification states for the FP32 path), with the same number
 of iterations on every level.
 
 Iteration counts are integers decided by floating point in one place: the
-convergence stop ||r|| <= conv_tol ||g_l||.  When the residual lands within
-rounding of that threshold the FP32 path and the FP64 oracle may stop one
-iteration apart.  Both are then valid; the test checks that the decision
+stopping limit, the larger of the convergence stop conv_tol ||g_l|| and the
+discrepancy limit c delta sqrt(N_l) of Section 2.  When the residual lands
+within rounding of that limit the FP32 path and the FP64 oracle may stop
+one iteration apart.  Both are then valid; the test checks that the decision
 was borderline (the oracle's residual at the earlier count is within 5 % of
-the threshold) and compares the output with the oracle run at the GPU's
+the limit) and compares the output with the oracle run at the GPU's
 counts.  Tiny grids (1 x 1, 2 x 3) are compared for 1 and 2 iterations
 only: a few more exhaust their Krylov space, where FP32 and FP64 iterates
 legitimately part.
@@ -149,27 +150,32 @@ def _random_problem(case):
     return synth.make_problem(h, w, 7000 + case, psf, float(rng.uniform(0.005, 0.05))), L, smo
 
 
+@pytest.mark.parametrize("stop", ["discrepancy", "fixed"])
 @pytest.mark.parametrize("case", range(24))
-def test_random_problems_match_oracle(gpu, orc, case):
+def test_random_problems_match_oracle(gpu, orc, case, stop):
     """Seeded random sizes (17..399 per side), levels (coarsest side >= 8 where L > 3),
     Gaussian or motion PSFs, noise and smoothers: the FP32 cascade within 1e-4 / 0.01 dB of
-    the FP64 oracle at its counts.
+    the FP64 oracle at its counts, under the discrepancy rule of Section 2 with the data's
+    noise level (the default) and under the fixed schedule.
 
-    Cases where the FP64 cascade itself diverges are skipped: there the fixed schedule runs a
-    coarse level far past the noise level (e.g. 100 iterations on a 47 x 64 level under a
-    15-pixel motion blur), the iterate grows to many times the data range, and it is the
-    rounding error of whichever arithmetic runs it, amplified; no FP32 result can track FP64
-    to 1e-4 there."""
+    Under the fixed schedule, cases where the FP64 cascade itself diverges are skipped: there
+    the schedule runs a coarse level far past the noise level (e.g. 100 iterations on a
+    47 x 64 level under a 15-pixel motion blur), the iterate grows to many times the data
+    range, and it is the rounding error of whichever arithmetic runs it, amplified; no FP32
+    result can track FP64 to 1e-4 there.  The discrepancy rule stops before that happens,
+    so no case is skipped under it."""
     torch, E = gpu
     p, L, smo = _random_problem(case)
-    orc.set_threads(oracle_threads())
-    ref, _, _ = orc.cascade(p.g.astype(np.float64), L, p.psf, smoother=smo)
-    orc.set_threads(1)
-    peak = float(np.abs(ref).max())
-    if peak > 4.0 * float(np.abs(p.g).max()):
-        pytest.skip(f"the FP64 cascade diverges (max |u| = {peak:.0f}, "
-                    f"PSNR {orc.psnr(p.u, ref):.1f} dB against {orc.psnr(p.u, p.g):.1f} dB for g)")
-    it, rit, err, dpsnr, _ = check_cascade(torch, E, orc, p, L, smoother=smo)
+    kw = dict(smoother=smo, stop=stop, delta=p.delta if stop == "discrepancy" else 0.0)
+    if stop == "fixed":
+        orc.set_threads(oracle_threads())
+        ref, _, _ = orc.cascade(p.g.astype(np.float64), L, p.psf, **kw)
+        orc.set_threads(1)
+        peak = float(np.abs(ref).max())
+        if peak > 4.0 * float(np.abs(p.g).max()):
+            pytest.skip(f"the FP64 cascade diverges (max |u| = {peak:.0f}, "
+                        f"PSNR {orc.psnr(p.u, ref):.1f} dB against {orc.psnr(p.u, p.g):.1f} dB for g)")
+    it, rit, err, dpsnr, _ = check_cascade(torch, E, orc, p, L, **kw)
     assert err <= FP32_REL, err
     assert dpsnr <= FP32_DPSNR, dpsnr
 
@@ -200,12 +206,13 @@ def check_cascade(torch, E, orc, p, L, **opts):
     it, res = plan.stats()
     u = host(ud)
     orc.set_threads(oracle_threads())
-    okw = {k: v for k, v in opts.items() if k in ("smoother", "coarse_op", "prolong")}
+    okw = {k: v for k, v in opts.items() if k in ("smoother", "coarse_op", "prolong", "stop", "c",
+                                                 "delta")}
     g64 = p.g.astype(np.float64)
     ref, rit, rres = orc.cascade(g64, L, p.psf, **okw)
     if it != rit:
         check_borderline_stops(orc, g64, L, p.psf, it, rit, sched, okw)
-        ref, rit2, _ = orc.cascade(g64, L, p.psf, iters=it, conv_tol=0.0, **okw)
+        ref, rit2, _ = orc.cascade(g64, L, p.psf, iters=it, conv_tol=0.0, **dict(okw, stop="fixed"))
         assert rit2 == it
     orc.set_threads(1)
     err = rel_l2(u, ref)
@@ -214,10 +221,19 @@ def check_cascade(torch, E, orc, p, L, **opts):
     return it, it, err, dpsnr, u
 
 
+def stop_limit(orc, g_l, okw):
+    """Euclidean residual limit of a level: the larger of the convergence stop and, under
+    the discrepancy rule (Section 2), c delta sqrt(N_l) (c delta in the RMS norm)."""
+    lim = orc.CONV_TOL * np.linalg.norm(g_l)
+    if okw.get("stop", "discrepancy") == "discrepancy" and okw.get("delta", 0.0) > 0.0:
+        lim = max(lim, okw.get("c", 1.1) * okw["delta"] * np.sqrt(g_l.size))
+    return lim
+
+
 def check_borderline_stops(orc, g64, L, psf, it, rit, sched, okw):
-    """Counts may differ only at a level stopped by the convergence rule, by at most 8,
-    with the oracle's residual within 5 % of the limit at every count in between (a
-    residual that hovers at the limit lets rounding pick any of those counts)."""
+    """Counts may differ only at a level stopped by a stopping rule, by at most 8, with
+    the oracle's residual within 5 % of the limit at every count in between (a residual
+    that hovers at the limit lets rounding pick any of those counts)."""
     hs, ws = orc.level_sizes(g64.shape[0], g64.shape[1], L)
     gl = [None] * L
     gl[-1] = g64
@@ -226,10 +242,11 @@ def check_borderline_stops(orc, g64, L, psf, it, rit, sched, okw):
     first = next(l for l in range(L) if it[l] != rit[l])
     a, b = sorted((it[first], rit[first]))
     assert a < sched[first] and b - a <= 8, (it, rit, sched)
-    lim = orc.CONV_TOL * np.linalg.norm(gl[first])
+    lim = stop_limit(orc, gl[first], okw)
+    fixed = dict(okw, stop="fixed")
     for k in range(a, b + (0 if b == sched[first] else 1)):
         counts = list(rit[:first]) + [k] + list(sched[first + 1:])
-        _, _, res = orc.cascade(g64, L, psf, iters=counts, conv_tol=0.0, **okw)
+        _, _, res = orc.cascade(g64, L, psf, iters=counts, conv_tol=0.0, **fixed)
         r_k = res[first] * np.sqrt(gl[first].size)
         assert abs(r_k / lim - 1.0) <= 0.05, (first, k, r_k, lim)
 
@@ -245,6 +262,80 @@ def test_cascade_matches_oracle(gpu, orc, name, smoother, persistent):
     assert it == rit
     assert err <= FP32_REL, err
     assert dpsnr <= FP32_DPSNR, dpsnr
+
+
+def _discrepancy_case(name):
+    from paper_2311_03010_gb300 import synth
+
+    if name.startswith("cfg1") or name.startswith("cfg2"):
+        return _cascade_case(name)
+    size, psfname, v = {"cfg3_2048_gauss3": (2048, "gauss3", 0.01),
+                        "cfg3_2048_motion15": (2048, "motion15", 0.01),
+                        "cfg3_2048_gauss3_5pct": (2048, "gauss3", 0.05),
+                        "cfg3_4096_gauss3": (4096, "gauss3", 0.01)}[name]
+    psf = synth.gaussian_psf(3.0, 10) if psfname == "gauss3" else synth.motion_psf(15, 30.0)
+    seed = 3000 if size == 2048 else 3001
+    return synth.make_problem(size, size, seed, psf, v), 5
+
+
+@pytest.mark.parametrize("smoother", ["mr2", "cgls"])
+@pytest.mark.parametrize("name", ["cfg1", "cfg2_1pct", "cfg2_5pct", "cfg3_2048_gauss3",
+                                  "cfg3_2048_motion15", "cfg3_2048_gauss3_5pct",
+                                  "cfg3_4096_gauss3"])
+def test_discrepancy_stop_matches_oracle(gpu, orc, name, smoother):
+    """The stopping rule of Section 2 (||g_l - H_l u||_RMS <= c delta before each iteration,
+    the economy schedule as the cap; the library's default) with the data's noise level
+    delta = ||e||_RMS: the FP32 cascade stops where the FP64 oracle stops (or on a borderline
+    residual, see check_borderline_stops) and is within 1e-4 / 0.01 dB of it, and the
+    restoration is better than the data it started from (PSNR(u) > PSNR(g)).  The library's
+    default precise_conv resolves to the plain convolution pass here."""
+    torch, E = gpu
+    p, L = _discrepancy_case(name)
+    it, rit, err, dpsnr, u = check_cascade(torch, E, orc, p, L, smoother=smoother,
+                                           stop="discrepancy", c=1.1, delta=p.delta)
+    assert err <= FP32_REL, err
+    assert dpsnr <= FP32_DPSNR, dpsnr
+    assert orc.psnr(p.u, u) > orc.psnr(p.u, p.g), (orc.psnr(p.u, u), orc.psnr(p.u, p.g))
+
+
+def test_precise_conv_auto_resolution(gpu):
+    """precise_conv = -1 (the default) is 0 under the discrepancy rule with a noise level and 1
+    under the fixed schedule (or delta = 0): bitwise the explicit settings."""
+    torch, E = gpu
+    p, L = _cascade_case("odd_gauss")
+    h, w = p.g.shape
+    gd = dev(torch, p.g)
+
+    def run(**kw):
+        plan = E.Plan(w, h, L, p.psf, **kw)
+        ud = torch.empty_like(gd)
+        plan.restore(gd, ud)
+        out = host(ud)
+        plan.close()
+        return out
+
+    assert np.array_equal(run(delta=p.delta), run(delta=p.delta, precise_conv=0))
+    assert np.array_equal(run(stop="fixed"), run(stop="fixed", precise_conv=1))
+    assert np.array_equal(run(), run(precise_conv=1))
+
+
+def test_discrepancy_stop_is_the_default(gpu, orc):
+    """Default options with delta set: the same counts and bits as stop = "discrepancy"."""
+    torch, E = gpu
+    p, L = _cascade_case("cfg2_1pct")
+    h, w = p.g.shape
+    gd = dev(torch, p.g)
+    outs = []
+    for kw in ({}, {"stop": "discrepancy"}):
+        plan = E.Plan(w, h, L, p.psf, delta=p.delta, **kw)
+        ud = torch.empty_like(gd)
+        plan.restore(gd, ud)
+        outs.append((plan.stats()[0], host(ud)))
+        plan.close()
+    assert outs[0][0] == outs[1][0] and np.array_equal(outs[0][1], outs[1][1])
+    desc = E.Plan(w, h, L, p.psf, workspace=0)
+    assert outs[0][0] != desc.info["iters"]  # stopped before the schedule's cap
+    desc.close()
 
 
 @pytest.mark.parametrize("prolong", ["iecmg_p", "iecmg_l"])

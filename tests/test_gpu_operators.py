@@ -208,3 +208,34 @@ def test_denoise_matches_oracle(gpu, orc):
             assert np.abs(got - ref).max() <= 1e-3
             assert rel_l2(got, ref) <= 1e-6
             plan.close()
+
+
+@pytest.mark.parametrize("shape", [(64, 64), (65, 65), (45, 70), (130, 200), (33, 700), (7, 6), (5, 5)])
+def test_start_level_is_the_operator_chain(gpu, orc, shape):
+    """The fused start of a prolonged level, D(S(P(Pi(u1, u2)))) in one pass over 32 x 64 tiles
+    with shared-memory halos, equals eecmg_prolong, eecmg_smooth and eecmg_denoise in sequence
+    bitwise (partial tiles, tiles narrower than the halo, one-tile images) and the FP64 oracle's
+    chain within the operators' FP32 bar."""
+    torch, E = gpu
+    from paper_2311_03010_gb300 import synth
+
+    h, w = shape
+    plan = E.Plan(w, h, 3, synth.gaussian_psf(1.0, 2))
+    hs, ws = orc.level_sizes(h, w, 3)
+    rng = np.random.default_rng(56)
+    u1 = synth.synthetic_image(hs[1], ws[1], 57).astype(np.float32)
+    u2 = (u1[::2, ::2] + rng.uniform(-3, 3, (hs[0], ws[0]))).astype(np.float32)
+    d1, d2 = dev(torch, u1), dev(torch, u2)
+    fused = torch.full((h, w), float("nan"), device="cuda")
+    E.eecmg_start_level(plan.handle, 2, d1, d2, fused)
+    p, s, d = (torch.empty(h, w, device="cuda") for _ in range(3))
+    E.eecmg_prolong(plan.handle, 2, d1, d2, p)
+    E.eecmg_smooth(plan.handle, 2, p, s)
+    E.eecmg_denoise(plan.handle, 2, s, d)
+    assert np.array_equal(host(fused), host(d))
+    ref = orc.denoise(orc.smooth(orc.quadratic(orc.extrapolate(u1.astype(np.float64),
+                                                               u2.astype(np.float64)), h, w), 1.0),
+                      0.2, 10.0)
+    assert np.abs(host(fused) - ref).max() <= 1e-3
+    assert rel_l2(host(fused), ref) <= 1e-6
+    plan.close()

@@ -7,6 +7,7 @@ fixed-order reductions give identical sums), and so lie within the FP32 bar
 of the FP64 oracle.  Admission by memory, slot limits, description-only
 plans and argument errors are covered too.
 """
+import gc
 import time
 
 import numpy as np
@@ -42,7 +43,7 @@ def _setup(torch, E):
     reqs = []
     for (h, w, L, psf, seed, smo, st) in _specs():
         p = synth.make_problem(h, w, seed, psf, 0.02)
-        plan = E.Plan(w, h, L, psf, smoother=smo, storage=st)
+        plan = E.Plan(w, h, L, psf, smoother=smo, storage=st, delta=p.delta)  # discrepancy stop
         gd = dev(torch, p.g)
         ud = torch.empty_like(gd)
         plan.restore(gd, ud)
@@ -90,7 +91,9 @@ def test_served_results_equal_alone(gpu, orc):
     srv.close()
     # and the served FP32 result of a mixed-size request matches the oracle
     p, L, smo = reqs[3][0], reqs[3][1], reqs[3][2]
-    ref, _, _ = orc.cascade(p.g.astype(np.float64), L, p.psf, smoother=smo)
+    ref, rit, _ = orc.cascade(p.g.astype(np.float64), L, p.psf, smoother=smo, stop="discrepancy",
+                              delta=p.delta)
+    assert reqs[3][3].stats()[0] == rit
     assert rel_l2(host(outs[3]), ref) <= 1e-4
     for r in reqs:
         r[3].close()
@@ -176,6 +179,56 @@ def test_served_options_equal_alone(gpu):
     srv.close()
     for pl in plans:
         pl.close()
+
+
+def test_device_memory_stays_flat_while_serving(gpu):
+    """After a warm-up, serving allocates no device memory: the arena and the per-tick tables
+    are sized when the server is created."""
+    torch, E = gpu
+    reqs = _setup(torch, E)
+    srv = E.Server(2 << 30, 4)
+    outs = [torch.empty_like(r[4]) for r in reqs * 4]
+    srv.drain()
+    for r, o in zip(reqs, outs):  # warm-up: every kind of request once
+        srv.submit(r[3], r[4], o)
+    srv.drain()
+    gc.collect()  # garbage of earlier tests must not be freed inside the measurement
+    torch.cuda.synchronize()
+    free0, alloc0 = torch.cuda.mem_get_info()[0], torch.cuda.memory_allocated()
+    for _ in range(3):  # more requests than slots: admission waits for slots and memory
+        ts = [srv.submit(r[3], r[4], o) for r, o in zip(reqs * 4, outs)]
+        srv.drain()
+        assert all(srv.poll(t)[0] for t in ts)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    assert torch.cuda.memory_allocated() == alloc0
+    for k, o in enumerate(outs):
+        assert np.array_equal(host(o), reqs[k % len(reqs)][5]), k
+    srv.close()
+    for r in reqs:
+        r[3].close()
+
+
+def test_server_rejects_requests_beyond_its_table_bounds(gpu):
+    """Plans with more diffusion steps than the server's per-tick tables allow are refused at
+    submission (the tables are never grown while serving)."""
+    torch, E = gpu
+    from paper_2311_03010_gb300 import synth
+
+    srv = E.Server(1 << 28, 2)
+    plan = E.Plan(32, 32, 3, synth.gaussian_psf(1.0, 2), diffusion_steps=17, workspace=0)
+    g = torch.zeros(32, 32, device="cuda")
+    with pytest.raises(E.EecmgError) as ei:
+        srv.submit(plan, g, torch.empty_like(g))
+    assert ei.value.status == 1
+    ok = E.Plan(32, 32, 3, synth.gaussian_psf(1.0, 2), diffusion_steps=16, workspace=0)
+    u = torch.empty_like(g)
+    t = srv.submit(ok, g, u)
+    srv.drain()
+    assert srv.poll(t)[0]
+    srv.close()
+    plan.close()
+    ok.close()
 
 
 def test_failed_request_is_isolated(gpu):

@@ -13,6 +13,8 @@ the operator tests, on two calls in a row with different inputs.
 This file is named to be collected last, so that a run stopping at the
 first failure has already run every other test.
 """
+import gc
+
 import numpy as np
 import pytest
 
@@ -48,6 +50,35 @@ def test_noalloc_residual_matches_plan_entry_points():
             assert np.sqrt(nrm[0] / (h * w)) == pytest.approx(res[0], rel=1e-5), call
             assert nrm[1] == pytest.approx(float(np.sum(g.astype(np.float64) ** 2)), rel=1e-6)
         plan.close()
+
+
+def test_noalloc_calls_after_the_warm_up_allocate_nothing():
+    """The first call (at start-up) reserves the fixed scratch array with the library's device
+    code; every later call leaves the device's free memory and torch's allocator untouched."""
+    torch, E = require_gpu()
+    from paper_2311_03010_gb300 import synth
+
+    h, w = 257, 333
+    psf = synth.gaussian_psf(1.5, 4)
+    rng = np.random.default_rng(91)
+    gd = dev(torch, rng.uniform(0, 255, (h, w)))
+    ud = dev(torch, rng.uniform(0, 255, (h, w)))
+    r = torch.empty_like(gd)
+    norms = torch.zeros(2, dtype=torch.float64, device="cuda")
+    E.eecmg_residual_noalloc(w, h, psf, gd, ud, r, norms)  # warm-up
+    first = torch.empty((h, w), dtype=torch.float32)  # host copies: no device allocation
+    again = torch.empty((h, w), dtype=torch.float32)
+    first.copy_(r)
+    gc.collect()  # garbage of earlier tests must not be freed inside the measurement
+    torch.cuda.synchronize()
+    free0, alloc0 = torch.cuda.mem_get_info()[0], torch.cuda.memory_allocated()
+    for _ in range(5):
+        r.fill_(float("nan"))
+        E.eecmg_residual_noalloc(w, h, psf, gd, ud, r, norms)
+        again.copy_(r)
+        assert torch.equal(again, first)
+    assert torch.cuda.mem_get_info()[0] == free0
+    assert torch.cuda.memory_allocated() == alloc0
 
 
 def test_noalloc_rejects_oversized_images():
