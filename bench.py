@@ -25,10 +25,12 @@ the data), ``e2e`` (the same metric through eecmg_restore_batched_host with
 pinned host buffers, copies inside the timed region), ``cpu_baseline`` (the
 FP64 CPU oracle on a bounded sample of the workload), ``clocks``,
 ``gpu_launches`` and, with the default workload, ``legs``: the 512 x 512
-two-noise case and the 64-image uneven batch (batched form against the
-plain per-image loop on the same plans), and ``serving``: a 2000-request
+two-noise case, the 64-image uneven batch (batched form against the plain
+per-image loop on the same plans), the default workload with each
+level's start fused into its solve (fuse_start = 1) and with BF16 storage of
+the Krylov vectors, and ``serving``: a 2000-request
 Poisson trace through the continuous-batching server and through the plain
-per-image loop.
+per-image loop (and its first 400 requests with the other storage type).
 
 ``--impl reference`` times the CPU oracle itself on the same workload.
 """
@@ -62,7 +64,11 @@ WORKLOADS = {
     "batch64-uneven-L5": None,
 }
 DEFAULT_WORKLOAD = "4096x4096-gauss3-L5"
-EXTRA_LEGS = ("512x512-gauss2.5-L5", "batch64-uneven-L5")
+# extra legs of the default run: (key, workload, plan options beyond the bench's)
+EXTRA_LEGS = (("512x512-gauss2.5-L5", "512x512-gauss2.5-L5", {}),
+              ("batch64-uneven-L5", "batch64-uneven-L5", {}),
+              ("4096x4096-gauss3-L5 fuse_start=1", "4096x4096-gauss3-L5", {"fuse_start": 1}),
+              ("4096x4096-gauss3-L5 storage=bf16", "4096x4096-gauss3-L5", {"storage": "bf16"}))
 
 # clean image (FP64), PSF, levels, degraded data (FP32), noise level ||e||_RMS
 Prob = collections.namedtuple("Prob", "u psf L g delta")
@@ -90,7 +96,7 @@ def make_problems(name):
     return out
 
 
-LEVEL_SOLVE_SOURCES = ("common.cuh", "conv_tile.cuh", "finish.cuh", "persistent.cuh",
+LEVEL_SOLVE_SOURCES = ("common.cuh", "launch.hpp", "conv_tile.cuh", "finish.cuh", "persistent.cuh", "level_ops.cuh",
                        "level_solve.hpp", "level_solve_impl.cuh", "level_resident.cuh", "level_solve.cu")
 
 
@@ -270,7 +276,7 @@ def _percentiles(xs):
 class Leg:
     """Plans, device buffers and the batched step of one workload."""
 
-    def __init__(self, torch, eecmg, stream, name, args, autotune):
+    def __init__(self, torch, eecmg, stream, name, args, autotune, extra=None):
         self.torch, self.E, self.stream, self.name = torch, eecmg, stream, name
         self.probs = make_problems(name)
         self.gs = [torch.from_numpy(p.g).cuda() for p in self.probs]
@@ -280,8 +286,10 @@ class Leg:
             smo = args.smoother
             if smo == "mr2" and not np.allclose(p.psf, p.psf[::-1, ::-1], rtol=0, atol=1e-15):
                 smo = "cgls"
-            return dict(smoother=smo, precise_conv=args.precise_conv, storage=args.storage,
-                        stop="discrepancy", c=1.1, delta=p.delta)
+            o = dict(smoother=smo, precise_conv=args.precise_conv, storage=args.storage,
+                     stop="discrepancy", c=1.1, delta=p.delta)
+            o.update(extra or {})
+            return o
 
         # partition of the level solves: autotuned on this workload (before any of its
         # plans owns a workspace), untimed
@@ -357,10 +365,10 @@ def dominant_step(torch, leg, flush):
     return best[1]
 
 
-def extra_leg(torch, eecmg, stream, name, args, world, flush, oracle_ok):
-    """Batched Mpixel/s of another workload (and, for a batch of many images, the plain
-    per-image loop on the same plans), with its parity against the oracle."""
-    leg = Leg(torch, eecmg, stream, name, args, autotune=not args.no_autotune)
+def extra_leg(torch, eecmg, stream, name, args, world, flush, oracle_ok, extra=None):
+    """Batched Mpixel/s of another workload or plan option (and, for a batch of many images,
+    the plain per-image loop on the same plans), with its parity against the oracle."""
+    leg = Leg(torch, eecmg, stream, name, args, autotune=not args.no_autotune, extra=extra)
     for _ in range(3):
         leg.step()
     torch.cuda.synchronize()
@@ -372,7 +380,7 @@ def extra_leg(torch, eecmg, stream, name, args, world, flush, oracle_ok):
     tot = replicas.max_over_ranks(tot, world, "cuda")
     out = {"value": replicas.aggregate_rate(leg.px, steps, world, tot) / 1e6, "unit": "Mpixel/s",
            "steps": steps, "ms_per_step": tot / steps, "images_per_step": len(leg.gs),
-           "pixels_per_step": leg.px, "partition": leg.tuning,
+           "pixels_per_step": leg.px, "partition": leg.tuning, "plan_options": extra or {},
            "gpu_launches_per_step": eecmg.eecmg_batch_info(leg.handles)}
     if len(leg.plans) > 2:
         # the plain per-image loop on the same plans (each plan's own CUDA graph)
@@ -400,6 +408,8 @@ def extra_leg(torch, eecmg, stream, name, args, world, flush, oracle_ok):
         k = min(len(leg.probs), 4)
         par, _, _ = parity_of(oracle, leg.probs[:k], leg.outputs()[:k], leg.iters()[:k], leg.smoother)
         par["images_checked"] = f"{k} of {len(leg.probs)}"
+        if (extra or {}).get("storage", args.storage) == "bf16":
+            par["tolerance"] = {"rel_l2": 5e-3, "dpsnr_db": 0.05}
         out["parity"] = par
         oracle.set_threads(1)
     leg.close()
@@ -578,7 +588,7 @@ def main():
     ap.add_argument("--storage", default="fp32", choices=["fp32", "bf16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
-    ap.add_argument("--no-legs", action="store_true", help="skip the 512^2 and batch64 legs")
+    ap.add_argument("--no-legs", action="store_true", help="skip the extra legs (512^2, batch64, fused start)")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=2000)
     args = ap.parse_args()
@@ -705,11 +715,15 @@ def main():
 
     legs = None
     if not args.no_legs and name == DEFAULT_WORKLOAD:
-        legs = {n: extra_leg(torch, eecmg, stream, n, args, world, flush, oracle_ok) for n in EXTRA_LEGS}
+        legs = {key: extra_leg(torch, eecmg, stream, wl, args, world, flush, oracle_ok, extra)
+                for (key, wl, extra) in EXTRA_LEGS}
 
     serving = None
     if not args.no_serving:
         serving = serving_leg(torch, eecmg, stream, args.storage, n_req=args.serving_requests)
+        # the other storage type on the first chunk of the same trace
+        other = "bf16" if args.storage == "fp32" else "fp32"
+        serving[f"variant_{other}"] = serving_leg(torch, eecmg, stream, other, n_req=400)
 
     if rank == 0:
         out = {

@@ -111,6 +111,16 @@ enum { EECMG_PROLONG_EECMG = 0, EECMG_PROLONG_IECMG_P = 1, EECMG_PROLONG_IECMG_L
  *                         with eecmg_server_submit and eecmg_plan_info; every
  *                         entry point that runs kernels on it returns
  *                         EECMG_ERR_INVALID_ARG.
+ *   fuse_start = 0        1: every prolonged level's persistent solve runs
+ *                         the level's start D(S(P(Pi))) itself as its first
+ *                         phase, so a restoration is one launch per cascade
+ *                         step (Algorithm 2 with diffusion_steps = 1; the
+ *                         same arithmetic, bitwise the same result).  0: the
+ *                         start is its own launch at full occupancy, which
+ *                         is faster on GB300 (the start is compute-bound and
+ *                         a solve runs two blocks per SM).  The two coarsest
+ *                         levels write their zero start inside their solve
+ *                         either way.
  */
 typedef struct {
     int smoother;
@@ -127,6 +137,7 @@ typedef struct {
     int precise_conv;
     int persistent;
     int workspace;
+    int fuse_start;
 } eecmg_options;
 
 typedef struct eecmg_plan_s *eecmg_plan_t;

@@ -52,6 +52,7 @@ LevelJob make_job(eecmg_plan_s* P, int l) {
     J.m = L.m;
     const int nzero = P->opt.prolong == EECMG_PROLONG_EECMG ? 2 : 1;
     J.zero_start = l < nzero ? 1 : 0;
+    set_level_start(P, l, J);
     return J;
 }
 
@@ -143,21 +144,15 @@ void restrict_ops(const std::vector<eecmg_plan_s*>& plans, std::vector<OpGroup>&
 
 void step_ops(const std::vector<std::pair<eecmg_plan_s*, int>>& items, std::vector<OpGroup>& groups) {
     const size_t base = groups.size();
-    const size_t G_ZERO = base, G_PSD = base + 1, G_EXTRA = base + 2, G_QUAD = base + 3,
-                 G_LIN = base + 4, G_SMOOTH = base + 5, G_STEP0 = base + 6;  // + diffusion step
+    const size_t G_PSD = base, G_EXTRA = base + 1, G_QUAD = base + 2, G_LIN = base + 3,
+                 G_SMOOTH = base + 4, G_STEP0 = base + 5;  // + diffusion step
     for (auto& itm : items) {
         eecmg_plan_s& P = *itm.first;
         const int st = itm.second;
         const int nzero = P.opt.prolong == EECMG_PROLONG_EECMG ? 2 : 1;
         LevelPlan& L = P.lv[st];
-        if (st < nzero) {
-            OpItem z;
-            z.out = L.u;
-            z.h = L.h;
-            z.w = L.w;
-            add_op(groups, G_ZERO, OP_ZERO, z);
-            continue;
-        }
+        // the persistent solve writes its zero start, or runs the fused start, itself
+        if (st < nzero || level_fused_start(&P, st)) continue;
         LevelPlan& L1 = P.lv[st - 1];
         float* up = P.vec[0];
         float* sm = P.vec[1];

@@ -56,37 +56,116 @@ __device__ __forceinline__ void conv_stage_taps(ConvSmem<R, SEP>& S, const Taps*
     }
 }
 
-// Loads the tile at (y0, x0) with halo.  COHERENT loads go through L2 only
+// Per-thread share of a tile with halo, held in registers between its global
+// loads and its shared-memory stores.  Rows are fetched as 16-byte chunks (4
+// FP32 or 8 BF16 values) starting PADX (the halo rounded up to a chunk) left
+// of the tile, so that every chunk is aligned whenever the row pitch is: an
+// element costs a fraction of an address computation and bounds test.
+template <int R, bool SEP, typename TIN = float>
+struct ConvRegs {
+    static constexpr int EPC = 16 / (int)sizeof(TIN);       // elements per chunk
+    static constexpr int PADX = (R + EPC - 1) / EPC * EPC;
+    static constexpr int XOFF = PADX - R;                   // loaded columns left of the halo
+    static constexpr int CPR = (CONV_TW + 2 * PADX) / EPC;  // chunks per row
+    static constexpr int IH = ConvSmem<R, SEP>::IH;
+    static constexpr int NC = IH * CPR;
+    static constexpr int ITERS = (NC + NTHREADS - 1) / NTHREADS;
+    uint4 q[ITERS];
+};
+
+__device__ __forceinline__ float chunk_elem(const uint4& c, int e, float) {
+    const unsigned int b = e == 0 ? c.x : (e == 1 ? c.y : (e == 2 ? c.z : c.w));
+    return __uint_as_float(b);
+}
+__device__ __forceinline__ float chunk_elem(const uint4& c, int e, __nv_bfloat16) {
+    const unsigned int b = (e >> 1) == 0 ? c.x : ((e >> 1) == 1 ? c.y : ((e >> 1) == 2 ? c.z : c.w));
+    return __uint_as_float((e & 1) ? (b & 0xffff0000u) : (b << 16));
+}
+// The raw bits of element i of x (an FP32 or BF16 vector), through L2 or the read-only path.
+template <bool COHERENT>
+__device__ __forceinline__ unsigned int elem_bits(const float* x, size_t i) {
+    const unsigned int* p = reinterpret_cast<const unsigned int*>(x) + i;
+    return COHERENT ? __ldcg(p) : __ldg(p);
+}
+template <bool COHERENT>
+__device__ __forceinline__ unsigned int elem_bits(const __nv_bfloat16* x, size_t i) {
+    const unsigned short* p = reinterpret_cast<const unsigned short*>(x) + i;
+    return (unsigned int)(COHERENT ? __ldcg(p) : __ldg(p));
+}
+
+// Issues the global loads of the tile at (y0, x0) with halo into registers
+// (zero outside the image).  COHERENT loads go through L2 only
 // (ld.global.cg): required when x was written earlier in the same launch by
-// other blocks.
+// other blocks.  Aligned 16-byte loads when x is 16-byte aligned and w a
+// multiple of the chunk; element loads otherwise (same values).
+template <int R, bool SEP, bool COHERENT, typename TIN = float>
+__device__ __forceinline__ void conv_fetch(ConvRegs<R, SEP, TIN>& V, const TIN* __restrict__ x, int h,
+                                           int w, int y0, int x0) {
+    using CR = ConvRegs<R, SEP, TIN>;
+    constexpr int EPC = CR::EPC;
+    const int tid = threadIdx.x;
+    const bool vec = (w % EPC) == 0 && (reinterpret_cast<uintptr_t>(x) & 15) == 0;
+#pragma unroll
+    for (int k = 0; k < CR::ITERS; ++k) {
+        const int i = tid + k * NTHREADS;
+        const int r = i / CR::CPR, c = i - r * CR::CPR;
+        const int gy = y0 - R + r, gx = x0 - CR::PADX + EPC * c;
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
+        if (i < CR::NC && gy >= 0 && gy < h) {
+            const size_t row = (size_t)gy * w;
+            if (vec) {
+                if (gx >= 0 && gx < w) {
+                    const uint4* p = reinterpret_cast<const uint4*>(x + row + gx);
+                    v = COHERENT ? __ldcg(p) : __ldg(p);
+                }
+            } else {
+                unsigned int b[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+                for (int e = 0; e < EPC; ++e) {
+                    const int gxe = gx + e;
+                    if (gxe >= 0 && gxe < w)
+                        b[e * (int)sizeof(TIN) / 4] |= elem_bits<COHERENT>(x, row + gxe)
+                                                       << (8 * ((e * (int)sizeof(TIN)) & 3));
+                }
+                v = make_uint4(b[0], b[1], b[2], b[3]);
+            }
+        }
+        V.q[k] = v;
+    }
+}
+
+// Stores a fetched tile into S.in as FP32 (the caller synchronises before reading it).
+template <int R, bool SEP, typename TIN = float>
+__device__ __forceinline__ void conv_put(ConvSmem<R, SEP>& S, const ConvRegs<R, SEP, TIN>& V) {
+    using CR = ConvRegs<R, SEP, TIN>;
+    constexpr int IW = ConvSmem<R, SEP>::IW, EPC = CR::EPC;
+    const int tid = threadIdx.x;
+#pragma unroll
+    for (int k = 0; k < CR::ITERS; ++k) {
+        const int i = tid + k * NTHREADS;
+        if (i < CR::NC) {
+            const int r = i / CR::CPR, c = i - r * CR::CPR;
+            const int lc = EPC * c - CR::XOFF;  // tile column of the chunk's first element
+            float* dst = S.in + r * IW + lc;
+            if (lc >= 0 && lc + EPC - 1 < IW) {
+#pragma unroll
+                for (int e = 0; e < EPC; ++e) dst[e] = chunk_elem(V.q[k], e, TIN());
+            } else {
+#pragma unroll
+                for (int e = 0; e < EPC; ++e)
+                    if (lc + e >= 0 && lc + e < IW) dst[e] = chunk_elem(V.q[k], e, TIN());
+            }
+        }
+    }
+}
+
+// Loads the tile at (y0, x0) with halo into S.in.
 template <int R, bool SEP, bool COHERENT, typename TIN = float>
 __device__ __forceinline__ void conv_load(ConvSmem<R, SEP>& S, const TIN* __restrict__ x, int h,
                                           int w, int y0, int x0) {
-    constexpr int IH = ConvSmem<R, SEP>::IH, IW = ConvSmem<R, SEP>::IW;
-    constexpr int NTOT = IH * IW;
-    constexpr int ITERS = (NTOT + NTHREADS - 1) / NTHREADS;
-    const int tid = threadIdx.x;
-    float vals[ITERS];
-#pragma unroll
-    for (int k = 0; k < ITERS; ++k) {
-        const int i = tid + k * NTHREADS;
-        const int r = i / IW, c = i - r * IW;
-        const int gy = y0 - R + r, gx = x0 - R + c;
-        float v = 0.f;
-        if (i < NTOT && gy >= 0 && gy < h && gx >= 0 && gx < w) {
-            const size_t idx = (size_t)gy * w + gx;
-            if constexpr (sizeof(TIN) == 4)
-                v = COHERENT ? __ldcg((const float*)x + idx) : __ldg((const float*)x + idx);
-            else
-                v = VecIO<TIN>::ld(x, idx);
-        }
-        vals[k] = v;
-    }
-#pragma unroll
-    for (int k = 0; k < ITERS; ++k) {
-        const int i = tid + k * NTHREADS;
-        if (i < NTOT) S.in[i] = vals[k];
-    }
+    ConvRegs<R, SEP, TIN> V;
+    conv_fetch<R, SEP, COHERENT, TIN>(V, x, h, w, y0, x0);
+    conv_put<R, SEP, TIN>(S, V);
 }
 
 // Computes S.out from S.in (the caller synchronises before and after).

@@ -5,6 +5,7 @@
 // Each runs once per level per restoration; they are simple stencils with
 // 32 x 8 thread blocks over the output image.
 #include "launch.hpp"
+#include "level_ops.cuh"
 
 namespace eecmg {
 
@@ -25,27 +26,6 @@ __global__ void k_restrict(const float* __restrict__ fine, int wf, float* __rest
     px_restrict(fine, wf, coarse, hc, wc, blockIdx.y * BY + threadIdx.y, blockIdx.x * BX + threadIdx.x);
 }
 
-// Pi on the level-(l-1) grid: u1 + (1/4) * (bilinear interpolant of
-// d = u1|coarse - u2), i.e. (5 u1 - u2)/4 at coarse nodes, u1 + (d_a + d_b)/8
-// at edge midpoints and u1 + (sum of four d)/16 at cell centres; indices
-// past the last level-(l-2) node are clamped to it.  The differences of the
-// two near-equal iterates are taken exactly (TwoSum: each is a double-float
-// pair, as exact as an FP64 difference of two FP32 values) and summed in
-// double-float, all on the FP32 pipes: GB300's FP64 pipe is narrow, and an
-// FP64 form of this made the prolongation 20x slower than its memory traffic.
-// The result is the double-float value rounded once to FP32.
-__device__ __forceinline__ float pi_at(const float* __restrict__ u1, int w1,
-                                      const float* __restrict__ u2, int h2, int w2, int a, int b) {
-    const int A0 = a >> 1, B0 = b >> 1;
-    const int A1 = (a & 1) ? min(A0 + 1, h2 - 1) : A0;
-    const int B1 = (b & 1) ? min(B0 + 1, w2 - 1) : B0;
-    auto d = [&](int A, int B) -> DF {
-        return two_sum(u1[(size_t)(2 * A) * w1 + 2 * B], -u2[(size_t)A * w2 + B]);
-    };
-    const DF dsum = df_add2(df_add2(d(A0, B0), d(A0, B1)), df_add2(d(A1, B0), d(A1, B1)));
-    const DF e = df_add2(DF{u1[(size_t)a * w1 + b], 0.f}, DF{0.0625f * dsum.hi, 0.0625f * dsum.lo});
-    return __fadd_rn(e.hi, e.lo);
-}
 __device__ __forceinline__ void px_extrapolate(const float* __restrict__ u1, int h1, int w1,
                                                const float* __restrict__ u2, int h2, int w2,
                                                float* __restrict__ out, int a, int b) {
@@ -58,11 +38,6 @@ __global__ void k_extrapolate(const float* __restrict__ u1, int h1, int w1,
     px_extrapolate(u1, h1, w1, u2, h2, w2, out, blockIdx.y * BY + threadIdx.y,
                    blockIdx.x * BX + threadIdx.x);
 }
-
-// Three-point Lagrange weights at offsets 0, 1/4, 1/2, 3/4 of a level-(l-2)
-// cell spanned by the level-(l-1) triplet (2A, 2A+1, 2A+2).
-__constant__ float c_qw[4][3] = {
-    {1.f, 0.f, 0.f}, {0.375f, 0.75f, -0.125f}, {0.f, 1.f, 0.f}, {-0.125f, 0.75f, 0.375f}};
 
 // P: tensor-product quadratic interpolation of ut (h1 x w1) onto h x w.
 __device__ __forceinline__ void px_quadratic(const float* __restrict__ ut, int h1, int w1,
@@ -152,85 +127,6 @@ __global__ void k_linear(const float* __restrict__ uc, int hc, int wc, float* __
     px_linear(uc, hc, wc, out, h, w, blockIdx.y * BY + threadIdx.y, blockIdx.x * BX + threadIdx.x);
 }
 
-// S: weighted least-squares plane fit over the in-image 3 x 3 neighbourhood
-// with weights exp(-(scale * (u_c - u_nb))^2) (Eqs. 18-19), output the fitted
-// constant.  Solved in centred form: with W, the weighted means (sb, tb, vb)
-// of the offsets and of v = u_nb - u_c, the 2 x 2 moment matrix C and the
-// cross vector c, slope = C^+ c (eigenvalues below 1e-6 W dropped) and
-// a0 = u_c + vb - slope . (sb, tb).
-template <class Rd>
-__device__ __forceinline__ float smooth_value_rd(Rd rd, int h, int w, float scale, int i, int j) {
-    const float uc = rd(i, j);
-    float ws[9], ss[9], ts[9], vs[9];
-    float W = 0.f, sb = 0.f, tb = 0.f, vb = 0.f;
-#pragma unroll
-    for (int s = -1; s <= 1; ++s) {
-#pragma unroll
-        for (int t = -1; t <= 1; ++t) {
-            const int k = (s + 1) * 3 + (t + 1);
-            const int ii = i + s, jj = j + t;
-            const bool inside = ii >= 0 && ii < h && jj >= 0 && jj < w;
-            const float v = inside ? rd(ii, jj) - uc : 0.f;
-            const float e = scale * v;
-            const float wt = inside ? __expf(-e * e) : 0.f;  // MUFU exp: ~2 ulp, ample for a weight
-            ws[k] = wt;
-            ss[k] = (float)s;
-            ts[k] = (float)t;
-            vs[k] = v;
-            W += wt;
-            sb = fmaf(wt, (float)s, sb);
-            tb = fmaf(wt, (float)t, tb);
-            vb = fmaf(wt, v, vb);
-        }
-    }
-    const float inv_w = 1.f / W;  // W >= 1: the centre always has weight 1
-    sb *= inv_w;
-    tb *= inv_w;
-    vb *= inv_w;
-    float css = 0.f, cst = 0.f, ctt = 0.f, csv = 0.f, ctv = 0.f;
-#pragma unroll
-    for (int k = 0; k < 9; ++k) {
-        const float ds = ss[k] - sb, dt = ts[k] - tb, dv = vs[k] - vb;
-        const float wd = ws[k];
-        css = fmaf(wd * ds, ds, css);
-        cst = fmaf(wd * ds, dt, cst);
-        ctt = fmaf(wd * dt, dt, ctt);
-        csv = fmaf(wd * ds, dv, csv);
-        ctv = fmaf(wd * dt, dv, ctv);
-    }
-    const float tr = 0.5f * (css + ctt), df = 0.5f * (css - ctt);
-    const float rad = sqrtf(df * df + cst * cst);
-    const float l1 = tr + rad;
-    // small eigenvalue from the determinant: no cancellation
-    const float l2 = l1 > 0.f ? (css * ctt - cst * cst) / l1 : 0.f;
-    const float thr = 1e-6f * W;
-    float e1s = 1.f, e1t = 0.f;
-    if (rad > 0.f) {
-        const float a0 = css - l2, c0 = ctt - l2;
-        if (fabsf(a0) >= fabsf(c0)) {
-            const float nn = rsqrtf(a0 * a0 + cst * cst);
-            e1s = a0 * nn;
-            e1t = cst * nn;
-        } else {
-            const float nn = rsqrtf(cst * cst + c0 * c0);
-            e1s = cst * nn;
-            e1t = c0 * nn;
-        }
-    }
-    const float e2s = -e1t, e2t = e1s;
-    float gs = 0.f, gt = 0.f;
-    if (l1 > thr) {
-        const float c1 = (e1s * csv + e1t * ctv) / l1;
-        gs = fmaf(c1, e1s, gs);
-        gt = fmaf(c1, e1t, gt);
-    }
-    if (l2 > thr) {
-        const float c2 = (e2s * csv + e2t * ctv) / l2;
-        gs = fmaf(c2, e2s, gs);
-        gt = fmaf(c2, e2t, gt);
-    }
-    return uc + vb - (gs * sb + gt * tb);
-}
 template <class Rd>
 __device__ __forceinline__ void px_smooth_rd(Rd rd, float* __restrict__ out, int h, int w, float scale,
                                              int i, int j) {
@@ -259,31 +155,6 @@ __global__ void __launch_bounds__(BX* BY) k_smooth(const float* __restrict__ in,
     tile_smooth(in, out, h, w, scale, blockIdx.y * BY, blockIdx.x * BX);
 }
 
-// D: u + tau * sum over in-image 4-neighbours of (c_nb + c_c)/2 (u_nb - u_c),
-// c = 1 / (1 + |grad u|^2 / k^2) with central differences (an out-of-image
-// neighbour replaced by the centre value).
-template <class Rd>
-__device__ __forceinline__ float pm_c_rd(Rd u, int h, int w, int i, int j, float inv_k2) {
-    const float uc = u(i, j);
-    const float ue = (j + 1 < w) ? u(i, j + 1) : uc;
-    const float uw = (j > 0) ? u(i, j - 1) : uc;
-    const float us = (i + 1 < h) ? u(i + 1, j) : uc;
-    const float un = (i > 0) ? u(i - 1, j) : uc;
-    const float gx = 0.5f * (ue - uw), gy = 0.5f * (us - un);
-    return 1.f / (1.f + (gx * gx + gy * gy) * inv_k2);
-}
-// c at (i, j) from a reader Cd of precomputed c, u from Ud.
-template <class Ud, class Cd>
-__device__ __forceinline__ float denoise_value_rd(Ud in, Cd c, int h, int w, float tau, int i, int j) {
-    const float uc = in(i, j);
-    const float cc = c(i, j);
-    float f = 0.f;
-    if (i + 1 < h) f += 0.5f * (c(i + 1, j) + cc) * (in(i + 1, j) - uc);
-    if (i > 0) f += 0.5f * (c(i - 1, j) + cc) * (in(i - 1, j) - uc);
-    if (j + 1 < w) f += 0.5f * (c(i, j + 1) + cc) * (in(i, j + 1) - uc);
-    if (j > 0) f += 0.5f * (c(i, j - 1) + cc) * (in(i, j - 1) - uc);
-    return fmaf(tau, f, uc);
-}
 template <class Ud, class Cd>
 __device__ __forceinline__ void px_denoise_rd(Ud in, Cd c, float* __restrict__ out, int h, int w,
                                               float tau, int i, int j) {
@@ -322,93 +193,14 @@ __global__ void __launch_bounds__(BX* BY) k_denoise(const float* __restrict__ in
     tile_denoise(in, out, h, w, tau, inv_k2, blockIdx.y * BY, blockIdx.x * BX);
 }
 
-// The start of a prolonged level (Algorithm 2, Step 2) in one pass: D(S(P(Pi(u1, u2)))) for
-// one PSD_TH x PSD_TW block of fine pixels at (y0, x0).  D needs S's output with a 2-pixel halo
-// (its own 4 neighbours and their diffusivities), S needs P's with a 1-pixel halo beyond that,
-// and P the level-(l-1) window of Pi values its triplets read; each stage is computed for its
-// whole region into shared memory (pixels outside the image are never read), with the
-// per-pixel arithmetic of k_prolong, k_smooth and k_denoise, so the result equals those three
-// kernels in sequence bitwise, while the two intermediate images never leave the SM.  Halo
-// work: P on 1.30x, S on 1.20x, c on 1.10x the block's pixels.  Called by every thread of a
-// 256-thread block.
-constexpr int PSD_TH = 32, PSD_TW = 64;
-constexpr int PSD_PH = PSD_TH + 6, PSD_PW = PSD_TW + 6;  // P: 3-pixel halo
-constexpr int PSD_SH = PSD_TH + 4, PSD_SW = PSD_TW + 4;  // S: 2
-constexpr int PSD_CH = PSD_TH + 2, PSD_CW = PSD_TW + 2;  // c: 1
-// Pi window: n consecutive fine indices read level-(l-1) indices 2A .. 2A' + 2 with
-// A' - A <= (n + 2) / 4
-constexpr int PSD_XR = 2 * ((PSD_PH + 2) / 4) + 3, PSD_XC = 2 * ((PSD_PW + 2) / 4) + 3;
-struct PsdSmem {
-    float X[PSD_XR][PSD_XC];
-    float P[PSD_PH][PSD_PW];
-    float S[PSD_SH][PSD_SW];
-    float C[PSD_CH][PSD_CW];
-};
-__device__ __forceinline__ void tile_psd(PsdSmem& M, const float* __restrict__ u1, int h1, int w1,
-                                         const float* __restrict__ u2, int h2, int w2,
-                                         float* __restrict__ out, int h, int w, float scale, float tau,
-                                         float inv_k2, int y0, int x0) {
-    const int tid = threadIdx.y * BX + threadIdx.x;
-    constexpr int NT = BX * BY;
-    // fine region of P (clipped to the image) and its Pi window
-    const int py0 = max(y0 - 3, 0), px0 = max(x0 - 3, 0);
-    const int py1 = min(y0 + PSD_TH + 3, h), px1 = min(x0 + PSD_TW + 3, w);  // exclusive
-    const int r0 = 2 * (py0 >> 2), c0 = 2 * (px0 >> 2);
-    const int nr = 2 * (((py1 - 1) >> 2) - (py0 >> 2)) + 3;
-    const int nc = 2 * (((px1 - 1) >> 2) - (px0 >> 2)) + 3;
-    for (int k = tid; k < nr * nc; k += NT) {
-        const int rr = k / nc, cc = k - rr * nc;
-        M.X[rr][cc] = pi_at(u1, w1, u2, h2, w2, min(r0 + rr, h1 - 1), min(c0 + cc, w1 - 1));
-    }
-    __syncthreads();
-    // P on rows y0-3 .. y0+TH+2 and columns x0-3 .. x0+TW+2 (in-image part)
-    for (int k = tid; k < PSD_PH * PSD_PW; k += NT) {
-        const int rr = k / PSD_PW, cc = k - rr * PSD_PW;
-        const int y = y0 - 3 + rr, x = x0 - 3 + cc;
-        float acc = 0.f;
-        if (y >= 0 && y < h && x >= 0 && x < w) {
-            const int A = y >> 2, ty = y & 3, B = x >> 2, tx = x & 3;
-#pragma unroll
-            for (int i = 0; i < 3; ++i) {
-                // staged row 2A + i - r0 holds level-(l-1) row min(2A + i, h1 - 1), as P reads
-                const float* er = M.X[2 * A + i - r0];
-                float row = 0.f;
-#pragma unroll
-                for (int j = 0; j < 3; ++j) row = fmaf(c_qw[tx][j], er[2 * B + j - c0], row);
-                acc = fmaf(c_qw[ty][i], row, acc);
-            }
-        }
-        M.P[rr][cc] = acc;
-    }
-    __syncthreads();
-    auto pr = [&](int a, int b) { return M.P[a - y0 + 3][b - x0 + 3]; };
-    for (int k = tid; k < PSD_SH * PSD_SW; k += NT) {
-        const int rr = k / PSD_SW, cc = k - rr * PSD_SW;
-        const int y = y0 - 2 + rr, x = x0 - 2 + cc;
-        M.S[rr][cc] = (y >= 0 && y < h && x >= 0 && x < w) ? smooth_value_rd(pr, h, w, scale, y, x) : 0.f;
-    }
-    __syncthreads();
-    auto sr = [&](int a, int b) { return M.S[a - y0 + 2][b - x0 + 2]; };
-    for (int k = tid; k < PSD_CH * PSD_CW; k += NT) {
-        const int rr = k / PSD_CW, cc = k - rr * PSD_CW;
-        const int y = y0 - 1 + rr, x = x0 - 1 + cc;
-        M.C[rr][cc] = (y >= 0 && y < h && x >= 0 && x < w) ? pm_c_rd(sr, h, w, y, x, inv_k2) : 0.f;
-    }
-    __syncthreads();
-    auto cr = [&](int a, int b) { return M.C[a - y0 + 1][b - x0 + 1]; };
-    for (int k = tid; k < PSD_TH * PSD_TW; k += NT) {
-        const int rr = k / PSD_TW, cc = k - rr * PSD_TW;
-        px_denoise_rd(sr, cr, out, h, w, tau, y0 + rr, x0 + cc);
-    }
-}
-
 __global__ void __launch_bounds__(BX* BY) k_psd(const float* __restrict__ u1, int h1, int w1,
                                                const float* __restrict__ u2, int h2, int w2,
                                                float* __restrict__ out, int h, int w, float scale,
                                                float tau, float inv_k2) {
     __shared__ PsdSmem M;
-    tile_psd(M, u1, h1, w1, u2, h2, w2, out, h, w, scale, tau, inv_k2, blockIdx.y * PSD_TH,
-             blockIdx.x * PSD_TW);
+    const int y0 = blockIdx.y * PSD_TH, x0 = blockIdx.x * PSD_TW;
+    tile_psd(M, u1, h1, w1, u2, h2, w2, h, w, scale, tau, inv_k2, y0, x0,
+             [&](int rr, int cc, float v) { out[(size_t)(y0 + rr) * w + x0 + cc] = v; });
 }
 
 // Many operations of one kind in one launch (the server's ticks): block b
@@ -438,8 +230,11 @@ __global__ void __launch_bounds__(BX* BY) k_ops_batch(const OpItem* __restrict__
     if constexpr (OP == OP_PSD) {
         __shared__ PsdSmem M;
         // this block's tile of the 32 x 64 grid (bx counts PSD_TW-wide tiles)
-        tile_psd(M, it.a, it.h1, it.w1, it.b, it.h2, it.w2, it.out, it.h, it.w, it.s0, it.p0, it.p1,
-                 by * PSD_TH, bx * PSD_TW);
+        const int y0 = by * PSD_TH, x0 = bx * PSD_TW;
+        float* out = it.out;
+        const int w = it.w;
+        tile_psd(M, it.a, it.h1, it.w1, it.b, it.h2, it.w2, it.h, it.w, it.s0, it.p0, it.p1, y0, x0,
+                 [&](int rr, int cc, float v) { out[(size_t)(y0 + rr) * w + x0 + cc] = v; });
     }
     if constexpr (OP == OP_ZERO || OP == OP_COPY) {
         if (y < it.h && x < it.w) it.out[(size_t)y * it.w + x] = OP == OP_ZERO ? 0.f : it.a[(size_t)y * it.w + x];

@@ -297,16 +297,38 @@ __device__ __forceinline__ float4 res_step4(const ResCtx& X, int j, int q, const
     return rv;
 }
 
+// Phase 0 of a resident solve that starts its own level (J.start): D(S(P(Pi))) of each of the
+// block's tiles into its resident u and into u in global memory (the r_0 phase stages its
+// halo windows from there), then a cluster barrier.  Returns false if the job is in error.
+__device__ __forceinline__ bool res_start_phase(PsdSmem& M, const LevelJob& J, const ResCtx& X,
+                                                float* ures, LevelSync& sy) {
+    for (int lt = 0; lt < X.T; ++lt) {
+        const int t = X.bid * X.T + lt;
+        if (t >= X.ntiles) break;
+        const int y0 = (t / X.tiles_x) * CONV_TH, x0 = (t % X.tiles_x) * CONV_TW;
+        float* ul = ures + lt * TILE_PX;
+        tile_psd(M, J.s_u1, J.s_h1, J.s_w1, J.s_u2, J.s_h2, J.s_w2, X.h, X.w, J.s_scale, J.s_tau,
+                 J.s_ik2, y0, x0, [&](int rr, int cc, float v) {
+                     ul[rr * CONV_TW + cc] = v;
+                     J.u[(size_t)(y0 + rr) * X.w + x0 + cc] = v;
+                 });
+        __syncthreads();
+    }
+    float v[1] = {0.f};
+    return sy.reduce<1>(v, [&](DF*) {});
+}
+
 template <int R, bool SEP, bool PREC>
-__device__ __forceinline__ void mr2_res_body(ConvSmem<R, SEP> (&S)[2], const LevelJob& J, Scalars* sc,
+__device__ __forceinline__ void mr2_res_body(ConvSmem<R, SEP> (&S)[2], PsdSmem& M, const LevelJob& J, Scalars* sc,
                                              const ResCtx& X, LevelSync& sy) {
     const int n4 = X.NL >> 2;
-    conv_stage_taps<R, SEP>(S[0], J.taps);
-    {  // every vector zero, then u0
+    {  // every vector zero, then u0 (or the level's start, phase 0)
         float4* b4 = reinterpret_cast<float4*>(X.base);
         for (int q = threadIdx.x; q < RES_NVEC * n4; q += NTHREADS) b4[q] = make_float4(0.f, 0.f, 0.f, 0.f);
         __syncthreads();
-        if (!J.zero_start) {
+        if (J.start) {
+            if (!res_start_phase(M, J, X, X.vec(VU), sy)) return;
+        } else if (!J.zero_start) {
             float* u = X.vec(VU);
             for (int lt = 0; lt < X.T; ++lt) {
                 const int t = X.bid * X.T + lt;
@@ -320,15 +342,19 @@ __device__ __forceinline__ void mr2_res_body(ConvSmem<R, SEP> (&S)[2], const Lev
         }
         __syncthreads();
     }
+    conv_stage_taps<R, SEP>(S[0], J.taps);  // after phase 0, whose tile shares this memory
+    __syncthreads();
 
     // r_0 = g - H u_0, ||r_0||^2, ||g||^2, stopping limit
     {
         float a0 = 0.f, a1 = 0.f;
         float* rv_ = X.vec(VR);
+        const bool zs = J.zero_start != 0;
         auto epi = [&](int li, size_t gi, float z, float) {
             const float gv = __ldg(J.g + gi);
             const float rv = gv - z;
             rv_[li] = rv;
+            if (zs) J.u[gi] = 0.f;  // the zero start, in global memory for an early return
             a0 = fmaf(rv, rv, a0);
             a1 = fmaf(gv, gv, a1);
         };
@@ -338,14 +364,14 @@ __device__ __forceinline__ void mr2_res_body(ConvSmem<R, SEP> (&S)[2], const Lev
             conv_phase_res<R, SEP, PREC, false, true>(S, X, 0, J.u, epi);
         float v[2] = {a0, a1};
         const double ct2 = J.conv_tol2, d2 = J.disc2;
-        const double b0 = J.zero_start ? 8.0 : 12.0;
+        const double b0 = (J.zero_start ? 8.0 : 12.0) + ls_detail::start_bytes(J);
         if (!sy.reduce<2>(v, [&](DF* t) {
                 fin_resid(sc, t[0], t[1], ct2, d2);
                 sc->bpp = b0;
             }))
             return;
     }
-    if (J.m <= 0 || volatile_stopped(sc)) return;  // u is still u0 in global memory
+    if (J.m <= 0 || volatile_stopped(sc)) return;  // u in global memory holds the start
     // algorithmic bytes per pixel of the vector phases (as the streaming solver counts them)
     auto hist = [](int j) { return 8.0 * ((j >= 2 ? 1 : 0) + (j >= 3 ? 1 : 0)); };
 
@@ -371,7 +397,6 @@ __device__ __forceinline__ void mr2_res_body(ConvSmem<R, SEP> (&S)[2], const Lev
         if (volatile_stopped(sc)) break;
         const int sk = k & 1, sk1 = sk ^ 1;
         // phase A: H w_k = H v_k / ||v_k||, alpha_k = <H w_k, w_k>
-        TRACE(X.bid, 10);
         {
             const float scale = vldf(&sc->f_scale);
             float a0 = 0.f;
@@ -383,14 +408,12 @@ __device__ __forceinline__ void mr2_res_body(ConvSmem<R, SEP> (&S)[2], const Lev
                                                            a0 = fmaf(hz, ctr, a0);
                                                        });
             float v[1] = {a0};
-            TRACE(X.bid, 11);
             if (!sy.reduce<1>(v, [&](DF* t) {
                     fin_mr_a(sc, t[0]);
                     sc->bpp += 8.0;
                 }))
                 return;
         }
-        TRACE(X.bid, 12);
         // phase B: pending step k-1 (unless an early check applied it), v_{k+1}, stopping
         // rules, rotation of column k
         {
@@ -445,7 +468,6 @@ __device__ __forceinline__ void mr2_res_body(ConvSmem<R, SEP> (&S)[2], const Lev
                 avr = dot4(vn, rv, avr);
             }
             float v[3] = {arr, avv, avr};
-            TRACE(X.bid, 13);
             const double bb = k == 1 ? 16.0 : (apply ? 44.0 + hist(k - 1) : 20.0);
             if (!sy.reduce<3>(v, [&](DF* t) {
                     fin_mr_b(sc, k, t[0], t[1], t[2]);
@@ -453,7 +475,6 @@ __device__ __forceinline__ void mr2_res_body(ConvSmem<R, SEP> (&S)[2], const Lev
                 }))
                 return;
         }
-        TRACE(X.bid, 14);
         // early check of step k (fin_mr_b predicted ||r_k|| at the limit): apply it now and
         // test ||r_k||, so that a solve that stops here skips iteration k + 1's convolution
         if (k < J.m && *(volatile const int*)&sc->spec && !volatile_stopped(sc)) {
@@ -510,15 +531,16 @@ __device__ __forceinline__ void mr2_res_body(ConvSmem<R, SEP> (&S)[2], const Lev
 enum { CU = 0, CR = 1, CS_ = 2, CP = 3, CQ = 4 };
 
 template <int R, bool SEP, bool PREC>
-__device__ __forceinline__ void cgls_res_body(ConvSmem<R, SEP> (&S)[2], const LevelJob& J, Scalars* sc,
+__device__ __forceinline__ void cgls_res_body(ConvSmem<R, SEP> (&S)[2], PsdSmem& M, const LevelJob& J, Scalars* sc,
                                               const ResCtx& X, LevelSync& sy) {
     const int n4 = X.NL >> 2;
-    conv_stage_taps<R, SEP>(S[0], J.taps);
-    {  // every vector zero, then u0
+    {  // every vector zero, then u0 (or the level's start, phase 0)
         float4* b4 = reinterpret_cast<float4*>(X.base);
         for (int q = threadIdx.x; q < RES_NVEC * n4; q += NTHREADS) b4[q] = make_float4(0.f, 0.f, 0.f, 0.f);
         __syncthreads();
-        if (!J.zero_start) {
+        if (J.start) {
+            if (!res_start_phase(M, J, X, X.vec(CU), sy)) return;
+        } else if (!J.zero_start) {
             float* u = X.vec(CU);
             for (int lt = 0; lt < X.T; ++lt) {
                 const int t = X.bid * X.T + lt;
@@ -532,16 +554,20 @@ __device__ __forceinline__ void cgls_res_body(ConvSmem<R, SEP> (&S)[2], const Le
         }
         __syncthreads();
     }
+    conv_stage_taps<R, SEP>(S[0], J.taps);  // after phase 0, whose tile shares this memory
+    __syncthreads();
     float* rv_ = X.vec(CR);
     float* sv = X.vec(CS_);
     float* pv = X.vec(CP);
     float* qv = X.vec(CQ);
     {  // r_0 = g - H u_0
         float a0 = 0.f, a1 = 0.f;
+        const bool zs = J.zero_start != 0;
         auto epi = [&](int li, size_t gi, float z, float) {
             const float gv = __ldg(J.g + gi);
             const float rv = gv - z;
             rv_[li] = rv;
+            if (zs) J.u[gi] = 0.f;  // the zero start, in global memory for an early return
             a0 = fmaf(rv, rv, a0);
             a1 = fmaf(gv, gv, a1);
         };
@@ -551,9 +577,14 @@ __device__ __forceinline__ void cgls_res_body(ConvSmem<R, SEP> (&S)[2], const Le
             conv_phase_res<R, SEP, PREC, false, true>(S, X, 0, J.u, epi);
         float v[2] = {a0, a1};
         const double ct2 = J.conv_tol2, d2 = J.disc2;
-        if (!sy.reduce<2>(v, [&](DF* t) { fin_resid(sc, t[0], t[1], ct2, d2); })) return;
+        const double sb = ls_detail::start_bytes(J);  // the host counts the CGLS phases themselves
+        if (!sy.reduce<2>(v, [&](DF* t) {
+                fin_resid(sc, t[0], t[1], ct2, d2);
+                sc->bpp = sb;
+            }))
+            return;
     }
-    if (J.m <= 0 || volatile_stopped(sc)) return;  // u is still u0 in global memory
+    if (J.m <= 0 || volatile_stopped(sc)) return;  // u in global memory holds the start
     conv_stage_taps<R, SEP>(S[0], J.tapsT);  // s = H^T r, p = s
     __syncthreads();
     {
@@ -637,10 +668,11 @@ __device__ __forceinline__ void cgls_res_body(ConvSmem<R, SEP> (&S)[2], const Le
 template <int R, bool SEP, bool PREC, bool CGLS>
 __device__ __forceinline__ void level_res_kernel(const LevelLaunch& LL) {
     using namespace res_detail;
-#ifdef EECMG_TRACE
-    trace_reset();
-#endif
-    __shared__ ConvSmem<R, SEP> S[2];
+    __shared__ union {
+        ConvSmem<R, SEP> conv[2];
+        PsdSmem psd;  // phase 0: the level's start
+    } U;
+    ConvSmem<R, SEP>(&S)[2] = U.conv;
     __shared__ LevelJob sJ;
     __shared__ ClusterState CS;
     extern __shared__ float4 res_smem[];
@@ -655,16 +687,11 @@ __device__ __forceinline__ void level_res_kernel(const LevelLaunch& LL) {
     const ResCtx X{base, LL.resident, LL.resident * TILE_PX, (int)bid, tiles_x,
                    tiles_x * tiles_y, J.h, J.w};
     LevelSync sy{nullptr, J.gs, nb, bid, &CS, true, 0u};
-    TRACE(bid, 1);
     if constexpr (CGLS)
-        cgls_res_body<R, SEP, PREC>(S, J, &CS.sc, X, sy);
+        cgls_res_body<R, SEP, PREC>(S, U.psd, J, &CS.sc, X, sy);
     else
-        mr2_res_body<R, SEP, PREC>(S, J, &CS.sc, X, sy);
+        mr2_res_body<R, SEP, PREC>(S, U.psd, J, &CS.sc, X, sy);
     cluster_end(CS, J.sc, bid);
-    TRACE(bid, 2);
-#ifdef EECMG_TRACE
-    trace_flush(bid == 0);
-#endif
 }
 
 template <int R, bool SEP, bool PREC>

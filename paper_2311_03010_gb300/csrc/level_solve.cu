@@ -7,11 +7,6 @@
 
 namespace eecmg {
 
-#ifdef EECMG_TRACE
-__device__ unsigned long long g_eecmg_trace[1 << 16];
-__device__ unsigned int g_eecmg_trace_n;
-#endif
-
 namespace {
 
 cudaError_t dispatch(const LevelLaunch& L, int rt, int sep, int prec, int cgls, int bf16, int op,
@@ -231,17 +226,3 @@ int level_capacity(int rt, int sep, int prec, int cgls, int bf16) {
 
 }  // namespace eecmg
 
-#ifdef EECMG_TRACE
-// Tracing builds only: copies the phase timestamps out and resets them.
-extern "C" int eecmg_trace_dump(unsigned long long* out, int max) {
-    unsigned int n = 0;
-    cudaDeviceSynchronize();
-    cudaMemcpyFromSymbol(&n, eecmg::g_eecmg_trace_n, sizeof(n));
-    if (n > (1u << 16)) n = 1u << 16;
-    if ((int)n > max) n = (unsigned int)max;
-    cudaMemcpyFromSymbol(out, eecmg::g_eecmg_trace, sizeof(unsigned long long) * n);
-    const unsigned int z = 0;
-    cudaMemcpyToSymbol(eecmg::g_eecmg_trace_n, &z, sizeof(z));
-    return (int)n;
-}
-#endif

@@ -25,6 +25,15 @@ struct LevelJob {
     double conv_tol2 = 0.0, disc2 = 0.0;
     int h = 0, w = 0, m = 0, zero_start = 0;
     int block0 = 0, nblocks = 0;  // this job's blocks within a batched launch
+    // The start of the level, run by the solve as its first phase (Algorithm 2,
+    // Step 2): start = 1 writes u = D(S(P(Pi(s_u1, s_u2)))) (one Perona-Malik
+    // step) before r_0 is formed; 0 leaves u as given.  With zero_start the r_0
+    // phase also writes the zero start into u.
+    int start = 0;
+    const float* s_u1 = nullptr;  // level-1 solution, s_h1 x s_w1
+    const float* s_u2 = nullptr;  // level-2 solution, s_h2 x s_w2
+    int s_h1 = 0, s_w1 = 0, s_h2 = 0, s_w2 = 0;
+    float s_scale = 1.f, s_tau = 0.f, s_ik2 = 0.f;  // S weight scale, D step and 1 / k^2
 };
 
 // Kernel parameter: one job by value, or (jobs != nullptr) a device table of

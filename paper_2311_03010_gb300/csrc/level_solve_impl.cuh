@@ -16,16 +16,12 @@
 
 #include "conv_tile.cuh"
 #include "finish.cuh"
+#include "level_ops.cuh"
 #include "level_solve.hpp"
 #include "persistent.cuh"
 
 namespace eecmg {
 
-#ifdef EECMG_TRACE
-#define TRACE(bid, tag) GTRACE((bid) == 0 && threadIdx.x == 0, (tag))
-#else
-#define TRACE(bid, tag) ((void)0)
-#endif
 
 namespace ls_detail {
 
@@ -44,27 +40,48 @@ __device__ __forceinline__ StepCoef step_coef(const Scalars* sc) {
                     vldf(&sc->f_tau)};
 }
 
-// MR-II step j on pixels 4q..4q+3 (coherent loads); returns the new r.  The
-// direction history d is stored as HT (FP32, or BF16 in the BF16-storage
-// variant); H d stays FP32, so the residual recurrence, every scalar and the
-// stopping decisions are those of the FP32 path and only u sees the rounding.
+// The MR-II vectors of a solve: the directions d as HT (FP32, or BF16 in the
+// BF16-storage variant); the Lanczos vectors v, their images H w, the images
+// H d, u, r and g stay FP32.  Neither v nor the images can be rounded: the
+// Lanczos update v_{k+1} = H w_k - alpha v_k - beta v_{k-1} cancels to a small
+// fraction of H w on smooth operators, so a rounding of v_k or H w_k there is
+// amplified in v_{k+1}, and H d carries the residual recurrence.
 template <typename HT>
-__device__ __forceinline__ float4 mr_step4(const LevelJob& J, int j, size_t q, const StepCoef& c) {
+struct MrVec {
+    float* v[2];
+    float* aw[2];
+    HT* d[2];
+    float* hd[2];
+    __device__ __forceinline__ explicit MrVec(const LevelJob& J) {
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            v[i] = J.v[i];
+            aw[i] = J.aw[i];
+            d[i] = reinterpret_cast<HT*>(J.d[i]);
+            hd[i] = J.hd[i];
+        }
+    }
+};
+
+// MR-II step j on pixels 4q..4q+3 (coherent loads); returns the new r.  d_j is
+// stored as HT; u and r are updated with its unrounded value.
+template <typename HT>
+__device__ __forceinline__ float4 mr_step4(const LevelJob& J, const MrVec<HT>& M, int j, size_t q,
+                                           const StepCoef& c) {
     using IO = VecIO<HT>;
     const int sj = j & 1, sj1 = sj ^ 1;
-    HT* dd[2] = {reinterpret_cast<HT*>(J.d[0]), reinterpret_cast<HT*>(J.d[1])};
-    float4 dj = mul4(c.dw, ld4cg(J.v[sj], q));
-    float4 hj = mul4(c.dinv, ld4cg(J.aw[sj], q));
+    float4 dj = mul4(c.dw, ld4cg(M.v[sj], q));
+    float4 hj = mul4(c.dinv, ld4cg(M.aw[sj], q));
     if (j >= 2) {
-        dj = fma4(-c.d1, IO::ld4(dd[sj1], q), dj);
-        hj = fma4(-c.d1, ld4cg(J.hd[sj1], q), hj);
+        dj = fma4(-c.d1, IO::ld4(M.d[sj1], q), dj);
+        hj = fma4(-c.d1, ld4cg(M.hd[sj1], q), hj);
     }
     if (j >= 3) {
-        dj = fma4(-c.d2, IO::ld4(dd[sj], q), dj);
-        hj = fma4(-c.d2, ld4cg(J.hd[sj], q), hj);
+        dj = fma4(-c.d2, IO::ld4(M.d[sj], q), dj);
+        hj = fma4(-c.d2, ld4cg(M.hd[sj], q), hj);
     }
-    IO::st4(dd[sj], q, dj);
-    st4(J.hd[sj], q, hj);
+    IO::st4(M.d[sj], q, dj);
+    st4(M.hd[sj], q, hj);
     st4(J.u, q, fma4(c.tau, dj, ld4cg(J.u, q)));
     const float4 rv = fma4(-c.tau, hj, ld4cg(J.r, q));
     st4(J.r, q, rv);
@@ -73,23 +90,22 @@ __device__ __forceinline__ float4 mr_step4(const LevelJob& J, int j, size_t q, c
 
 // Applies MR-II step j at pixel i (coherent loads); returns the new r_i.
 template <typename HT>
-__device__ __forceinline__ float mr_step_px(const LevelJob& J, int j, size_t i, float dw, float d1,
-                                            float d2, float dinv, float tau) {
+__device__ __forceinline__ float mr_step_px(const LevelJob& J, const MrVec<HT>& M, int j, size_t i,
+                                            float dw, float d1, float d2, float dinv, float tau) {
     using IO = VecIO<HT>;
     const int sj = j & 1, sj1 = sj ^ 1;
-    HT* dd[2] = {reinterpret_cast<HT*>(J.d[0]), reinterpret_cast<HT*>(J.d[1])};
-    float dj = dw * ldcg(J.v[sj] + i);
-    float hj = dinv * ldcg(J.aw[sj] + i);
+    float dj = dw * ldcg(M.v[sj] + i);
+    float hj = dinv * ldcg(M.aw[sj] + i);
     if (j >= 2) {
-        dj = fmaf(-d1, IO::ld(dd[sj1], i), dj);
-        hj = fmaf(-d1, ldcg(J.hd[sj1] + i), hj);
+        dj = fmaf(-d1, IO::ld(M.d[sj1], i), dj);
+        hj = fmaf(-d1, ldcg(M.hd[sj1] + i), hj);
     }
     if (j >= 3) {
-        dj = fmaf(-d2, IO::ld(dd[sj], i), dj);
-        hj = fmaf(-d2, ldcg(J.hd[sj] + i), hj);
+        dj = fmaf(-d2, IO::ld(M.d[sj], i), dj);
+        hj = fmaf(-d2, ldcg(M.hd[sj] + i), hj);
     }
-    IO::st(dd[sj], i, dj);
-    J.hd[sj][i] = hj;
+    IO::st(M.d[sj], i, dj);
+    M.hd[sj][i] = hj;
     J.u[i] = fmaf(tau, dj, ldcg(J.u + i));
     const float rv = fmaf(-tau, hj, ldcg(J.r + i));
     J.r[i] = rv;
@@ -105,11 +121,20 @@ __device__ __forceinline__ void conv_phase(ConvSmem<R, SEP>& S, const TIN* x, in
     const int tiles_x = (w + CONV_TW - 1) / CONV_TW, tiles_y = (h + CONV_TH - 1) / CONV_TH;
     const int ntiles = tiles_x * tiles_y;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // software pipeline: the loads of the block's next tile are issued before the
+    // current tile is convolved, so their latency overlaps the compute and the epilogue
+    ConvRegs<R, SEP, TIN> V;
+    if (!ZERO && (int)bid < ntiles)
+        conv_fetch<R, SEP, true, TIN>(V, x, h, w, ((int)bid / tiles_x) * CONV_TH,
+                                      ((int)bid % tiles_x) * CONV_TW);
     for (int t = (int)bid; t < ntiles; t += (int)nb) {
         const int y0 = (t / tiles_x) * CONV_TH, x0 = (t % tiles_x) * CONV_TW;
         if (!ZERO) {
-            conv_load<R, SEP, true, TIN>(S, x, h, w, y0, x0);
+            conv_put<R, SEP, TIN>(S, V);
             __syncthreads();
+            const int tn = t + (int)nb;
+            if (tn < ntiles)
+                conv_fetch<R, SEP, true, TIN>(V, x, h, w, (tn / tiles_x) * CONV_TH, (tn % tiles_x) * CONV_TW);
             conv_compute<R, SEP, PREC>(S);
             __syncthreads();
         }
@@ -131,36 +156,67 @@ __device__ __forceinline__ void conv_phase(ConvSmem<R, SEP>& S, const TIN* x, in
     }
 }
 
+// Phase 0 of a solve that starts its own level (J.start): u = D(S(P(Pi(u1, u2)))) over the
+// level's 32 x 64 tiles, then a barrier (the r_0 phase reads u with its halo).  Returns false
+// if the job is in error.
+__device__ __forceinline__ bool start_phase(PsdSmem& M, const LevelJob& J, unsigned int nb,
+                                            unsigned int bid, LevelSync& sy) {
+    const int h = J.h, w = J.w;
+    const int tiles_x = (w + PSD_TW - 1) / PSD_TW, ntiles = tiles_x * ((h + PSD_TH - 1) / PSD_TH);
+    float* u = J.u;
+    for (int t = (int)bid; t < ntiles; t += (int)nb) {
+        const int y0 = (t / tiles_x) * PSD_TH, x0 = (t % tiles_x) * PSD_TW;
+        tile_psd(M, J.s_u1, J.s_h1, J.s_w1, J.s_u2, J.s_h2, J.s_w2, h, w, J.s_scale, J.s_tau, J.s_ik2,
+                 y0, x0, [&](int rr, int cc, float v) { u[(size_t)(y0 + rr) * w + x0 + cc] = v; });
+        __syncthreads();
+    }
+    float v[1] = {0.f};
+    return sy.reduce<1>(v, [&](DF*) {});
+}
+
+// Algorithmic bytes per pixel of the level's start: the zero start written into u, or the
+// fused start reading both coarser solutions and writing u.
+__device__ __forceinline__ double start_bytes(const LevelJob& J) {
+    if (J.start)
+        return 4.0 + 4.0 * ((double)J.s_h1 * J.s_w1 + (double)J.s_h2 * J.s_w2) / ((double)J.h * J.w);
+    return J.zero_start ? 4.0 : 0.0;
+}
+
 }  // namespace ls_detail
 
 using namespace ls_detail;
 
 template <int R, bool SEP, bool PREC, typename HT>
-__device__ __forceinline__ void mr2_body(ConvSmem<R, SEP>& S, const LevelJob& J, Scalars* sc,
+__device__ __forceinline__ void mr2_body(ConvSmem<R, SEP>& S, PsdSmem& M, const LevelJob& J, Scalars* sc,
                                          unsigned int nb, unsigned int bid, LevelSync& sy) {
     const int h = J.h, w = J.w;
     const size_t n = (size_t)h * w;
     const size_t stride = (size_t)nb * NTHREADS;
+    using IO = VecIO<HT>;
+    const MrVec<HT> K(J);
+    if (J.start && !start_phase(M, J, nb, bid, sy)) return;
     conv_stage_taps<R, SEP>(S, J.taps);
     __syncthreads();
 
-    // r_0 = g - H u_0, ||r_0||^2, ||g||^2, stopping limit
+    // r_0 = g - H u_0, ||r_0||^2, ||g||^2, stopping limit (a zero start is written into u here)
     {
         float a0 = 0.f, a1 = 0.f;
+        const bool zs = J.zero_start != 0;
         auto epi = [&](size_t idx, float z, float) {
             const float gv = __ldg(J.g + idx);
             const float rv = gv - z;
             J.r[idx] = rv;
+            if (zs) J.u[idx] = 0.f;
             a0 = fmaf(rv, rv, a0);
             a1 = fmaf(gv, gv, a1);
         };
-        if (J.zero_start)
+        if (zs)
             conv_phase<R, SEP, PREC, true>(S, J.u, h, w, nb, bid, epi);
         else
             conv_phase<R, SEP, PREC, false>(S, J.u, h, w, nb, bid, epi);
         float v[2] = {a0, a1};
         const double ct2 = J.conv_tol2, d2 = J.disc2;
-        const double b0 = J.zero_start ? 8.0 : 12.0;
+        const double b0 = (J.zero_start ? 8.0 : 12.0) + start_bytes(J);
         if (!sy.reduce<2>(v, [&](DF* t) {
                 fin_resid(sc, t[0], t[1], ct2, d2);
                 sc->bpp = b0;
@@ -170,14 +226,14 @@ __device__ __forceinline__ void mr2_body(ConvSmem<R, SEP>& S, const LevelJob& J,
     if (J.m <= 0 || volatile_stopped(sc)) return;
 
     // bytes per pixel of the vector phases (each operand read or written once;
-    // the d history is stored as HT)
+    // d stored as HT, everything else FP32)
     constexpr double E = (double)sizeof(HT);
     auto hist = [](int j) { return (4.0 + E) * ((j >= 2 ? 1 : 0) + (j >= 3 ? 1 : 0)); };
 
     // v_1 = H r_0, ||v_1||, <v_1, r_0>
     {
         float a0 = 0.f, a1 = 0.f;
-        float* v1 = J.v[1];
+        float* v1 = K.v[1];
         conv_phase<R, SEP, PREC, false>(S, J.r, h, w, nb, bid, [&](size_t idx, float z, float ctr) {
             v1[idx] = z;
             a0 = fmaf(z, z, a0);
@@ -195,26 +251,23 @@ __device__ __forceinline__ void mr2_body(ConvSmem<R, SEP>& S, const LevelJob& J,
         if (volatile_stopped(sc)) break;
         const int sk = k & 1, sk1 = sk ^ 1;
         // phase A: H w_k = H v_k / ||v_k||, alpha_k = <H w_k, w_k>
-        TRACE(bid, 10);
         {
             const float scale = vldf(&sc->f_scale);
             float a0 = 0.f;
-            float* aw = J.aw[sk];
-            conv_phase<R, SEP, PREC, false>(S, J.v[sk], h, w, nb, bid,
-                                            [&](size_t idx, float z, float ctr) {
-                                                const float hz = z * scale;
-                                                aw[idx] = hz;
-                                                a0 = fmaf(hz, ctr, a0);
-                                            });
+            float* aw = K.aw[sk];
+            conv_phase<R, SEP, PREC, false>(S, K.v[sk], h, w, nb, bid,
+                                                [&](size_t idx, float z, float ctr) {
+                                                    const float hz = z * scale;
+                                                    aw[idx] = hz;
+                                                    a0 = fmaf(hz, ctr, a0);
+                                                });
             float v[1] = {a0};
-            TRACE(bid, 11);
             if (!sy.reduce<1>(v, [&](DF* t) {
                     fin_mr_a(sc, t[0]);
                     sc->bpp += 8.0;
                 }))
                 return;
         }
-        TRACE(bid, 12);
         // phase B: pending step k-1 (unless an early check applied it), v_{k+1}, stopping
         // rules, rotation of column k
         {
@@ -226,28 +279,26 @@ __device__ __forceinline__ void mr2_body(ConvSmem<R, SEP>& S, const LevelJob& J,
             const float cb = step ? vldf(&sc->f_cb) : 0.f, cb_lo = step ? vldf(&sc->f_cb_lo) : 0.f;
             float arr = 0.f, avv = 0.f, avr = 0.f;
             const size_t n4 = n >> 2;
-            using IO = VecIO<HT>;
             const int j = k - 1, sj = j & 1, sj1 = sj ^ 1;  // sj == sk1
-            HT* dd[2] = {reinterpret_cast<HT*>(J.d[0]), reinterpret_cast<HT*>(J.d[1])};
             for (size_t q = (size_t)bid * NTHREADS + threadIdx.x; q < n4; q += stride) {
                 // every operand is loaded before the first store, so the pass
                 // costs one round trip to L2 (the stores alias none of the
                 // loads except the same elements, already read)
-                const float4 vk = ld4cg(J.v[sk], q), awk = ld4cg(J.aw[sk], q);
+                const float4 vk = ld4cg(K.v[sk], q), awk = ld4cg(K.aw[sk], q);
                 const float4 rr = ld4cg(J.r, q);
                 float4 vj = make_float4(0.f, 0.f, 0.f, 0.f), awj = vj, uu = vj;
                 float4 dA = vj, hA = vj, dB = vj, hB = vj;
-                if (step) vj = ld4cg(J.v[sj], q);
+                if (step) vj = ld4cg(K.v[sj], q);
                 if (apply) {
-                    awj = ld4cg(J.aw[sj], q);
+                    awj = ld4cg(K.aw[sj], q);
                     uu = ld4cg(J.u, q);
                     if (j >= 2) {
-                        dA = IO::ld4(dd[sj1], q);
-                        hA = ld4cg(J.hd[sj1], q);
+                        dA = IO::ld4(K.d[sj1], q);
+                        hA = ld4cg(K.hd[sj1], q);
                     }
                     if (j >= 3) {
-                        dB = IO::ld4(dd[sj], q);
-                        hB = ld4cg(J.hd[sj], q);
+                        dB = IO::ld4(K.d[sj], q);
+                        hB = ld4cg(K.hd[sj], q);
                     }
                 }
                 float4 rv = rr;
@@ -262,8 +313,8 @@ __device__ __forceinline__ void mr2_body(ConvSmem<R, SEP>& S, const LevelJob& J,
                         dj = fma4(-c.d2, dB, dj);
                         hj = fma4(-c.d2, hB, hj);
                     }
-                    IO::st4(dd[sj], q, dj);
-                    st4(J.hd[sj], q, hj);
+                    IO::st4(K.d[sj], q, dj);
+                    st4(K.hd[sj], q, hj);
                     st4(J.u, q, fma4(c.tau, dj, uu));
                     rv = fma4(-c.tau, hj, rr);
                     st4(J.r, q, rv);
@@ -271,28 +322,27 @@ __device__ __forceinline__ void mr2_body(ConvSmem<R, SEP>& S, const LevelJob& J,
                 if (step) arr = dot4(rv, rv, arr);
                 float4 vn = fma4(-ca_lo, vk, fma4(-ca, vk, awk));
                 if (step) vn = fma4(-cb_lo, vj, fma4(-cb, vj, vn));
-                st4(J.v[sk1], q, vn);
+                st4(K.v[sk1], q, vn);
                 avv = dot4(vn, vn, avv);
                 avr = dot4(vn, rv, avr);
             }
             if (bid == 0) {  // the n mod 4 tail
                 for (size_t i = 4 * n4 + threadIdx.x; i < n; i += NTHREADS) {
-                    const float rv = apply ? mr_step_px<HT>(J, k - 1, i, c.dw, c.d1, c.d2, c.dinv, c.tau)
+                    const float rv = apply ? mr_step_px<HT>(J, K, k - 1, i, c.dw, c.d1, c.d2, c.dinv, c.tau)
                                            : ldcg(J.r + i);
                     if (step) arr = fmaf(rv, rv, arr);
-                    const float vki = ldcg(J.v[sk] + i);
-                    float vn = fmaf(-ca_lo, vki, fmaf(-ca, vki, ldcg(J.aw[sk] + i)));
+                    const float vki = ldcg(K.v[sk] + i);
+                    float vn = fmaf(-ca_lo, vki, fmaf(-ca, vki, ldcg(K.aw[sk] + i)));
                     if (step) {
-                        const float vk1 = ldcg(J.v[sk1] + i);
+                        const float vk1 = ldcg(K.v[sk1] + i);
                         vn = fmaf(-cb_lo, vk1, fmaf(-cb, vk1, vn));
                     }
-                    J.v[sk1][i] = vn;
+                    K.v[sk1][i] = vn;
                     avv = fmaf(vn, vn, avv);
                     avr = fmaf(vn, rv, avr);
                 }
             }
             float v[3] = {arr, avv, avr};
-            TRACE(bid, 13);
             const double bb = k == 1 ? 16.0 : (apply ? 40.0 + E + hist(k - 1) : 20.0);
             if (!sy.reduce<3>(v, [&](DF* t) {
                     fin_mr_b(sc, k, t[0], t[1], t[2]);
@@ -300,7 +350,6 @@ __device__ __forceinline__ void mr2_body(ConvSmem<R, SEP>& S, const LevelJob& J,
                 }))
                 return;
         }
-        TRACE(bid, 14);
         // early check of step k (fin_mr_b predicted ||r_k|| at the limit): apply it now and
         // test ||r_k||, so that a solve that stops here skips iteration k + 1's convolution
         if (k < J.m && *(volatile const int*)&sc->spec && !volatile_stopped(sc)) {
@@ -308,12 +357,12 @@ __device__ __forceinline__ void mr2_body(ConvSmem<R, SEP>& S, const LevelJob& J,
             float arr = 0.f;
             const size_t n4 = n >> 2;
             for (size_t q = (size_t)bid * NTHREADS + threadIdx.x; q < n4; q += stride) {
-                const float4 rv = mr_step4<HT>(J, k, q, c);
+                const float4 rv = mr_step4<HT>(J, K, k, q, c);
                 arr = dot4(rv, rv, arr);
             }
             if (bid == 0)
                 for (size_t i = 4 * n4 + threadIdx.x; i < n; i += NTHREADS) {
-                    const float rv = mr_step_px<HT>(J, k, i, c.dw, c.d1, c.d2, c.dinv, c.tau);
+                    const float rv = mr_step_px<HT>(J, K, k, i, c.dw, c.d1, c.d2, c.dinv, c.tau);
                     arr = fmaf(rv, rv, arr);
                 }
             float v[1] = {arr};
@@ -335,12 +384,12 @@ __device__ __forceinline__ void mr2_body(ConvSmem<R, SEP>& S, const LevelJob& J,
         float arr = 0.f;
         const size_t n4 = n >> 2;
         for (size_t q = (size_t)bid * NTHREADS + threadIdx.x; q < n4; q += stride) {
-            const float4 rv = mr_step4<HT>(J, j, q, c);
+            const float4 rv = mr_step4<HT>(J, K, j, q, c);
             arr = dot4(rv, rv, arr);
         }
         if (bid == 0)
             for (size_t i = 4 * n4 + threadIdx.x; i < n; i += NTHREADS) {
-                const float rv = mr_step_px<HT>(J, j, i, c.dw, c.d1, c.d2, c.dinv, c.tau);
+                const float rv = mr_step_px<HT>(J, K, j, i, c.dw, c.d1, c.d2, c.dinv, c.tau);
                 arr = fmaf(rv, rv, arr);
             }
         float v[1] = {arr};
@@ -353,7 +402,7 @@ __device__ __forceinline__ void mr2_body(ConvSmem<R, SEP>& S, const LevelJob& J,
 }
 
 template <int R, bool SEP, bool PREC, typename HT>
-__device__ __forceinline__ void cgls_body(ConvSmem<R, SEP>& S, const LevelJob& J, Scalars* sc,
+__device__ __forceinline__ void cgls_body(ConvSmem<R, SEP>& S, PsdSmem& M, const LevelJob& J, Scalars* sc,
                                           unsigned int nb, unsigned int bid, LevelSync& sy) {
     // s and p are stored as HT; q = H p stays FP32 (computed from the stored
     // p), so u and the residual recurrence see the same direction
@@ -365,24 +414,31 @@ __device__ __forceinline__ void cgls_body(ConvSmem<R, SEP>& S, const LevelJob& J
     HT* sv = reinterpret_cast<HT*>(J.v[0]);   // s
     HT* pv = reinterpret_cast<HT*>(J.v[1]);   // p
     float* qv = J.aw[0];                      // q
+    if (J.start && !start_phase(M, J, nb, bid, sy)) return;
     conv_stage_taps<R, SEP>(S, J.taps);
     __syncthreads();
     {
         float a0 = 0.f, a1 = 0.f;
+        const bool zs = J.zero_start != 0;
         auto epi = [&](size_t idx, float z, float) {
             const float gv = __ldg(J.g + idx);
             const float rv = gv - z;
             rv_[idx] = rv;
+            if (zs) J.u[idx] = 0.f;
             a0 = fmaf(rv, rv, a0);
             a1 = fmaf(gv, gv, a1);
         };
-        if (J.zero_start)
+        if (zs)
             conv_phase<R, SEP, PREC, true>(S, J.u, h, w, nb, bid, epi);
         else
             conv_phase<R, SEP, PREC, false>(S, J.u, h, w, nb, bid, epi);
         float v[2] = {a0, a1};
         const double ct2 = J.conv_tol2, d2 = J.disc2;
-        if (!sy.reduce<2>(v, [&](DF* t) { fin_resid(sc, t[0], t[1], ct2, d2); }))
+        const double sb = start_bytes(J);  // the host counts the CGLS phases themselves
+        if (!sy.reduce<2>(v, [&](DF* t) {
+                fin_resid(sc, t[0], t[1], ct2, d2);
+                sc->bpp = sb;
+            }))
             return;
     }
     if (J.m <= 0 || volatile_stopped(sc)) return;
@@ -471,9 +527,18 @@ __device__ __forceinline__ void cgls_body(ConvSmem<R, SEP>& S, const LevelJob& J
 // One level solve per job: a cooperative grid (LL.cluster == 0; the job's
 // blocks meet at bounded grid barriers) or one thread-block cluster of
 // LL.cluster blocks per job (reductions through distributed shared memory).
+// Shared memory of a streaming solve: the convolution tile of every phase, or
+// the level-start tile of phase 0.
+template <int R, bool SEP>
+union LevelSmem {
+    ConvSmem<R, SEP> conv;
+    PsdSmem psd;
+};
+
 template <int R, bool SEP, bool PREC, typename HT, bool CGLS>
 __device__ __forceinline__ void level_kernel(const LevelLaunch& LL) {
-    __shared__ ConvSmem<R, SEP> S;
+    __shared__ LevelSmem<R, SEP> U;
+    ConvSmem<R, SEP>& S = U.conv;
     __shared__ LevelJob sJ;
     __shared__ ClusterState CS;
     if (threadIdx.x == 0) sJ = LL.jobs ? LL.jobs[LL.block_job[blockIdx.x]] : LL.job;
@@ -482,11 +547,6 @@ __device__ __forceinline__ void level_kernel(const LevelLaunch& LL) {
     const unsigned int nb = LL.jobs ? (unsigned int)J.nblocks : gridDim.x;
     const unsigned int bid = LL.jobs ? blockIdx.x - (unsigned int)J.block0 : blockIdx.x;
     const bool cl = LL.cluster > 0;
-#ifdef EECMG_TRACE
-    trace_reset();
-    __syncthreads();
-#endif
-    TRACE(bid, 1);
     if (cl) {
         cluster_begin(CS, J.sc, nb);
     } else {
@@ -496,9 +556,9 @@ __device__ __forceinline__ void level_kernel(const LevelLaunch& LL) {
     LevelSync sy{J.partials, J.gs, nb, bid, &CS, cl, 0u};
     Scalars* sc = &CS.sc;  // this block's replica (identical in every block)
     if constexpr (CGLS)
-        cgls_body<R, SEP, PREC, HT>(S, J, sc, nb, bid, sy);
+        cgls_body<R, SEP, PREC, HT>(S, U.psd, J, sc, nb, bid, sy);
     else
-        mr2_body<R, SEP, PREC, HT>(S, J, sc, nb, bid, sy);
+        mr2_body<R, SEP, PREC, HT>(S, U.psd, J, sc, nb, bid, sy);
     if (cl) {
         cluster_end(CS, J.sc, bid);
     } else {
@@ -506,10 +566,6 @@ __device__ __forceinline__ void level_kernel(const LevelLaunch& LL) {
         if (bid == 0 && threadIdx.x == 0) *J.sc = CS.sc;
         grid_exit(J.gs, nb);
     }
-    TRACE(bid, 2);
-#ifdef EECMG_TRACE
-    trace_flush(bid == 0);
-#endif
 }
 
 template <int R, bool SEP, bool PREC, typename HT>

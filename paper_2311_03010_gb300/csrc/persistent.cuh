@@ -18,47 +18,6 @@
 
 namespace eecmg {
 
-#ifdef EECMG_TRACE
-// Tracing builds only: thread 0 of block 0 records (tag, clock64) pairs in
-// shared memory (no global traffic while the solve runs); trace_flush copies
-// them to g_eecmg_trace at kernel end.
-extern __device__ unsigned long long g_eecmg_trace[1 << 16];
-extern __device__ unsigned int g_eecmg_trace_n;
-struct TraceBuf {
-    unsigned long long e[2 * 384];
-    int n;
-};
-__device__ __forceinline__ TraceBuf& trace_buf() {
-    __shared__ TraceBuf b;
-    return b;
-}
-static __device__ __noinline__ void trace_any(unsigned int tag) {
-    TraceBuf& b = trace_buf();
-    const int i = b.n;
-    if (i < 384) {
-        b.e[2 * i] = tag;
-        b.e[2 * i + 1] = (unsigned long long)clock64();
-        b.n = i + 1;
-    }
-}
-__device__ __forceinline__ void trace_reset() {
-    if (threadIdx.x == 0) trace_buf().n = 0;
-}
-__device__ __forceinline__ void trace_flush(bool rec) {
-    if (rec && threadIdx.x == 0) {
-        TraceBuf& b = trace_buf();
-        const unsigned int base = atomicAdd(&g_eecmg_trace_n, 2u * (unsigned int)b.n);
-        for (int i = 0; i < 2 * b.n; ++i)
-            if (base + i < (1u << 16)) g_eecmg_trace[base + i] = b.e[i];
-    }
-}
-#define GTRACE(cond, tag) \
-    do {                  \
-        if (cond) trace_any(tag); \
-    } while (0)
-#else
-#define GTRACE(cond, tag) ((void)0)
-#endif
 
 struct alignas(64) GroupSync {
     unsigned int count;   // arrivals in this launch (phases x blocks)
@@ -101,7 +60,6 @@ __device__ __forceinline__ bool grid_reduce(const float (&v)[NV], double* partia
     block_sum_df<NV>(in, out);  // ends with __syncthreads()
     __shared__ int s_ok;
     float2* slot = reinterpret_cast<float2*>(partials) + (size_t)(phase & 1u) * nb * NPART;
-    GTRACE(bid == 0 && threadIdx.x == 0, 20);
     if (threadIdx.x == 0) {
 #pragma unroll
         for (int j = 0; j < NV; ++j) slot[(size_t)bid * NPART + j] = make_float2(out[j].hi, out[j].lo);
@@ -122,7 +80,6 @@ __device__ __forceinline__ bool grid_reduce(const float (&v)[NV], double* partia
             __nanosleep(20);
         }
         s_ok = ok;
-        GTRACE(bid == 0, 21);
     }
     __syncthreads();
     if (!s_ok) return false;
@@ -156,7 +113,6 @@ __device__ __forceinline__ bool grid_reduce(const float (&v)[NV], double* partia
         block_sum_df<NV>(acc, tot);
         if (threadIdx.x == 0) finish(tot);
     }
-    GTRACE(bid == 0 && threadIdx.x == 0, 22);
     __syncthreads();
     return true;
 }
@@ -256,9 +212,7 @@ __device__ __forceinline__ bool cluster_reduce(const float (&v)[NV], ClusterStat
     DF in[NV], out[NV];
 #pragma unroll
     for (int j = 0; j < NV; ++j) in[j] = DF{v[j], 0.f};
-    GTRACE(rank == 0 && threadIdx.x == 0, 40);
     block_sum_df<NV>(in, out);  // warp 0 holds lane 0's sums; ends with __syncthreads()
-    GTRACE(rank == 0 && threadIdx.x == 0, 41);
     // phase k uses slots[k & 1] and mbar[k & 1], whose own phase parity is (k >> 1) & 1.  A block
     // arrives for phase k + 1 only after it has seen every block's phase-k arrival, and for phase
     // k + 2 only after every block has arrived for k + 1, i.e. has finished waiting on phase k:
@@ -288,7 +242,6 @@ __device__ __forceinline__ bool cluster_reduce(const float (&v)[NV], ClusterStat
             }
         }
         ok = __all_sync(0xffffffffu, ok);
-        GTRACE(rank == 0 && threadIdx.x == 0, 42);
         if (!ok) {
             if (threadIdx.x == 0) {
                 cs.err = 1;
@@ -321,7 +274,6 @@ __device__ __forceinline__ bool cluster_reduce(const float (&v)[NV], ClusterStat
             warp_sum_df_n<NV, CLUSTER_MAX>(acc);  // lanes >= nb add zeros
             if (threadIdx.x == 0) finish(acc);
         }
-        GTRACE(rank == 0 && threadIdx.x == 0, 43);
     }
     __syncthreads();
     return cs.err == 0;

@@ -173,7 +173,8 @@ double level_solve_bytes(const eecmg_plan_s* P, int l, const Scalars& sc, bool z
     // MR-II: the solver adds each phase's bytes per pixel as it runs (the early
     // checks of the discrepancy rule change which phases run)
     if (P->opt.smoother == EECMG_SMOOTHER_MR2) return sc.bpp * n;
-    double b = (zero_start ? 8.0 : 12.0) * n;  // r = g - H u
+    // CGLS: the solver records the bytes of the level's start (if it ran one) in bpp
+    double b = (zero_start ? 8.0 : 12.0) * n + sc.bpp * n;  // start; r = g - H u
     const int K = sc.loops;
     {
         if (K > 0 || sc.iters > 0) b += (4.0 + 2 * e) * n;  // s = H^T r, p = s
@@ -247,8 +248,30 @@ void bind_workspace(eecmg_plan_s* P, char* ws) {
     P->partials = (double*)(ws + Y.part_off);
 }
 
+bool level_fused_start(const eecmg_plan_s* P, int l) {
+    return P->opt.fuse_start && P->opt.persistent && P->opt.prolong == EECMG_PROLONG_EECMG &&
+           P->opt.diffusion_steps == 1 && l >= 2;
+}
+
+void set_level_start(const eecmg_plan_s* P, int l, LevelJob& J) {
+    if (!level_fused_start(P, l)) return;
+    const LevelPlan& L1 = P->lv[l - 1];
+    const LevelPlan& L2 = P->lv[l - 2];
+    J.start = 1;
+    J.s_u1 = L1.u;
+    J.s_u2 = L2.u;
+    J.s_h1 = L1.h;
+    J.s_w1 = L1.w;
+    J.s_h2 = L2.h;
+    J.s_w2 = L2.w;
+    J.s_scale = (float)P->opt.s_scale;
+    J.s_tau = (float)P->tau;
+    const float kpm = (float)P->kpm;
+    J.s_ik2 = 1.f / (kpm * kpm);
+}
+
 eecmg_status solve_level_enqueue(eecmg_plan_s* P, int l, const float* g, float* u, int m,
-                                 bool zero_start, cudaStream_t s) {
+                                 bool zero_start, cudaStream_t s, bool own_start) {
     LevelPlan& L = P->lv[l];
     const size_t n = (size_t)L.h * L.w;
     Scalars* sc = P->sc + l;
@@ -281,6 +304,7 @@ eecmg_status solve_level_enqueue(eecmg_plan_s* P, int l, const float* g, float* 
         J.w = L.w;
         J.m = m;
         J.zero_start = zero_start ? 1 : 0;
+        if (own_start) set_level_start(P, l, J);
         int used = 0;
         if (P->prof.on) {
             // bytes field flags a zero start; the count itself is taken after the run
@@ -446,14 +470,17 @@ eecmg_status cascade_enqueue(eecmg_plan_s* P, cudaStream_t s) {
     const int nzero = P->opt.prolong == EECMG_PROLONG_EECMG ? 2 : 1;
     for (int l = 0; l < L; ++l) {
         const bool zero = l < nzero;
+        // a persistent solve writes its zero start, or runs the fused start of its level,
+        // itself (one launch per cascade step)
         if (zero) {
-            LK(P, s, KC_COPY, 4.0 * P->lv[l].h * P->lv[l].w,
-               cudaMemsetAsync(P->lv[l].u, 0, sizeof(float) * P->lv[l].h * P->lv[l].w, s));
-        } else {
+            if (!P->opt.persistent)
+                LK(P, s, KC_COPY, 4.0 * P->lv[l].h * P->lv[l].w,
+                   cudaMemsetAsync(P->lv[l].u, 0, sizeof(float) * P->lv[l].h * P->lv[l].w, s));
+        } else if (!level_fused_start(P, l)) {
             eecmg_status st = prolong_enqueue(P, l, s);
             if (st != EECMG_OK) return st;
         }
-        eecmg_status st = solve_level_enqueue(P, l, P->lv[l].g, P->lv[l].u, P->lv[l].m, zero, s);
+        eecmg_status st = solve_level_enqueue(P, l, P->lv[l].g, P->lv[l].u, P->lv[l].m, zero, s, true);
         if (st != EECMG_OK) return st;
     }
     return EECMG_OK;
@@ -572,6 +599,7 @@ eecmg_status eecmg_default_options(eecmg_options* o) {
     o->precise_conv = -1;
     o->persistent = 1;
     o->workspace = 1;
+    o->fuse_start = 0;
     return EECMG_OK;
 }
 
@@ -595,7 +623,7 @@ eecmg_status eecmg_plan(int width, int height, int levels, const double* psf, in
     if (o.smoother < 0 || o.smoother > 1 || o.coarse_op < 0 || o.coarse_op > 1 || o.storage < 0 ||
         o.storage > 1 || o.stop < 0 || o.stop > 1 || o.prolong < 0 || o.prolong > 2 ||
         o.diffusion_steps < 0 || !(o.conv_tol >= 0.0) || !(o.s_scale >= 0.0) ||
-        o.precise_conv < -1 || o.precise_conv > 1)
+        o.precise_conv < -1 || o.precise_conv > 1 || o.fuse_start < 0 || o.fuse_start > 1)
         return set_error(EECMG_ERR_INVALID_ARG, "eecmg_plan: invalid option value");
     if (o.stop == EECMG_STOP_DISCREPANCY && (!(o.c > 0.0) || !(o.delta >= 0.0)))
         return set_error(EECMG_ERR_INVALID_ARG, "eecmg_plan: discrepancy rule needs c > 0, delta >= 0");

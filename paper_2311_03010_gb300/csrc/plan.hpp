@@ -5,6 +5,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "level_solve.hpp"
 #include "persistent.cuh"
 
 namespace eecmg {
@@ -92,7 +93,14 @@ extern std::atomic<int> g_live_owners;
 eecmg_status plan_allocate(eecmg_plan_s* P, const char* who);
 eecmg_status plan_materialize(const eecmg_plan_s* D, eecmg_plan_s** out);
 eecmg_status solve_level_enqueue(eecmg_plan_s* P, int l, const float* g, float* u, int m,
-                                 bool zero_start, cudaStream_t s);
+                                 bool zero_start, cudaStream_t s, bool own_start = false);
+// Whether the persistent solve of level l starts the level itself (Algorithm 2,
+// Step 2: the fused D(S(P(Pi))) of a plan with fuse_start and one Perona-Malik
+// step, l >= 2); the two coarsest levels write their zero start themselves in
+// any case.
+bool level_fused_start(const eecmg_plan_s* P, int l);
+// Fills the start fields of level l's job (zero start or fused start).
+void set_level_start(const eecmg_plan_s* P, int l, LevelJob& J);
 eecmg_status prolong_enqueue(eecmg_plan_s* P, int l, cudaStream_t s);
 eecmg_status cascade_enqueue(eecmg_plan_s* P, cudaStream_t s);
 eecmg_status run_cascade(eecmg_plan_s* P, cudaStream_t s);

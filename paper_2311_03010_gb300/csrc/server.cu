@@ -8,11 +8,13 @@
 // resident on the device until it completes.
 //
 // A scheduler thread advances every active request together.  One tick runs
-// one cascade step (Algorithm 2) of each active request: for a request just
-// admitted, the copy of its data and the restriction of the data pyramid;
-// then per request the prolongation to its current level (or the zero
-// start); then the level solves of all of them as jobs of persistent
-// cooperative launches (one per kernel instantiation, see batch.hpp).
+// at least one cascade step (Algorithm 2) of each active request: for a
+// request just admitted, the copy of its data and the restriction of the data
+// pyramid; then per request the start of its current level (the prolongation
+// chain, or the zero start); then the level solves of all of them as jobs of
+// persistent cooperative launches (one per kernel instantiation, see
+// batch.hpp).  Requests whose next level is small go on to it in further
+// rounds of the same tick (at most MAX_ROUNDS steps per tick).
 // Requests admitted at different times therefore share launches while they
 // sit at different levels.  Each job keeps the block count of the same solve
 // launched alone, so a served result is bitwise the result of eecmg_restore
@@ -44,24 +46,37 @@ constexpr int RING = 2;              // ticks in flight
 constexpr size_t QUEUE_CAP = 65536;  // queued (not yet admitted) requests
 constexpr int MAX_LEVELS = 30;
 constexpr int MAX_DIFFUSION = 16;    // Perona-Malik steps per level of a served request
+// A tick runs up to MAX_ROUNDS rounds: round 0 advances every active request by
+// one cascade step; a request takes part in the next round while its next
+// level has at most SMALL_LEVEL_PX pixels.  The coarse steps of a request are
+// short on the GPU (a level is a quarter of the next) and a tick's host work
+// is not: with one step per tick the GPU idled between the ticks of a lone
+// request (GB300: +38 us on a 256^2 request, +176 us on a 4096^2 one against
+// the plain loop).  Levels above 1024^2 still get a tick each, so requests
+// admitted meanwhile join at the next tick.
+constexpr int MAX_ROUNDS = 5;
+constexpr long long SMALL_LEVEL_PX = 1LL << 20;
 
 size_t round256(size_t b) { return (b + 255) / 256 * 256; }
 
 // Upper bound of one tick's job tables and operation items (enqueue_tick), so
 // that the tick ring is allocated once, at creation.  Every active request
-// adds at most MAX_LEVELS + 4 + MAX_DIFFUSION operation items (the copy of its
-// data, the restriction to each coarser level, the reset of its scalars, the
-// start of its cascade step: zero start or prolongation, smoothing, the
-// diffusion steps; the copy of its result) and one level-solve job of at most
-// max(16, 3 x SMs) blocks; there are at most 11 + MAX_DIFFUSION operation
-// groups and one wave per job, each table rounded up to 256 bytes.
+// adds at most MAX_LEVELS + 1 admission items (the copy of its data, the
+// restriction to each coarser level, the reset of its scalars), per round at
+// most 3 + MAX_DIFFUSION items (the start of its cascade step: zero start, or
+// the fused prolongation chain or prolongation, smoothing and the diffusion
+// steps) and one level-solve job of at most max(16, 3 x SMs) blocks, and one
+// item for the copy of its result; there are at most 4 + MAX_ROUNDS x (7 +
+// MAX_DIFFUSION) operation groups and one wave per job, each table rounded up
+// to 256 bytes.
 size_t tick_table_bound(int max_slots, int nsm) {
     const size_t slots = (size_t)max_slots;
-    const size_t items = slots * (MAX_LEVELS + 4 + MAX_DIFFUSION);
-    const size_t groups = 11 + MAX_DIFFUSION;
+    const size_t items = slots * (MAX_LEVELS + 2 + (size_t)MAX_ROUNDS * (3 + MAX_DIFFUSION));
+    const size_t groups = 4 + (size_t)MAX_ROUNDS * (7 + MAX_DIFFUSION);
+    const size_t jobs = slots * MAX_ROUNDS;
     const size_t job_blocks = std::max<size_t>(16, 3 * (size_t)nsm);
-    return items * sizeof(OpItem) + 256 * groups + slots * (sizeof(LevelJob) + 256) +
-           slots * (sizeof(unsigned short) * job_blocks + 256);
+    return items * sizeof(OpItem) + 256 * groups + jobs * (sizeof(LevelJob) + 256) +
+           jobs * (sizeof(unsigned short) * job_blocks + 256);
 }
 
 // First-fit allocator over [0, cap): free ranges by offset, coalesced on
@@ -103,8 +118,6 @@ public:
             }
         }
     }
-    size_t used() const { return used_; }
-
 private:
     std::map<size_t, size_t> free_;
     size_t used_ = 0;
@@ -196,14 +209,16 @@ void bind_slot(Request* r, char* ws) {
 
 char* stat_area(eecmg_server_s* S, int sidx) { return S->h_stat + (size_t)sidx * S->stat_stride; }
 
-// Enqueues tick k's work on the server stream; `finishing` receives the
-// requests whose finest level ran in it.  Every per-level operation of the
-// tick is one batched launch per kind over all requests (k_ops_batch), then
-// the level solves are the persistent launches of plan_waves.
+// Enqueues tick k's work on the server stream: the admissions, then up to
+// MAX_ROUNDS rounds of cascade steps, each round one batched launch per kind
+// of per-level operation (k_ops_batch) followed by the level solves of that
+// round as the persistent launches of plan_waves.  `finishing` receives the
+// requests whose finest level ran in it; every other active request's step
+// advances by the rounds it took part in (when the tick is committed).
 eecmg_status enqueue_tick(eecmg_server_s* S, const std::vector<Request*>& admitted, int k,
-                          std::vector<Request*>& finishing) {
+                          std::vector<Request*>& finishing, std::vector<int>& advance) {
     cudaStream_t s = S->stream;
-    std::vector<OpGroup> pre, post;  // launch groups before / after the level solves
+    std::vector<OpGroup> pre, post;  // launch groups before the rounds / after them
     // admissions: the data copied in, its pyramid restricted, scalars zeroed
     std::vector<eecmg_plan_s*> adm;
     for (Request* r : admitted) {
@@ -229,32 +244,54 @@ eecmg_status enqueue_tick(eecmg_server_s* S, const std::vector<Request*>& admitt
         z.w = (int)((Y.bytes - Y.sc_off) / sizeof(float));
         add_op(pre, gz, OP_ZERO, z);
     }
-    // every active request: the start of its current cascade step
-    std::vector<std::pair<eecmg_plan_s*, int>> items;
-    items.reserve(S->active.size());
-    for (Request* r : S->active) items.push_back({&r->slot, r->step});
-    step_ops(items, pre);
-    for (Request* r : S->active) {
-        eecmg_plan_s& P = r->slot;
-        if (r->step != P.L - 1) continue;
-        LevelPlan& F = P.lv[P.L - 1];
-        OpItem c;
-        c.a = F.u;
-        c.out = r->u;
-        c.h = F.h;
-        c.w = F.w;
-        add_op(post, 0, OP_COPY, c);
-        finishing.push_back(r);
+    // the rounds: every active request in round 0, then those whose next level is small
+    std::vector<std::vector<OpGroup>> rops;
+    std::vector<std::vector<HostWave>> rwaves;
+    advance.assign(S->active.size(), 0);
+    std::vector<int> cur(S->active.size());
+    for (size_t i = 0; i < cur.size(); ++i) cur[(size_t)i] = (int)i;
+    for (int round = 0; round < MAX_ROUNDS && !cur.empty(); ++round) {
+        std::vector<std::pair<eecmg_plan_s*, int>> items;
+        items.reserve(cur.size());
+        for (int i : cur) items.push_back({&S->active[i]->slot, S->active[i]->step + round});
+        rops.emplace_back();
+        step_ops(items, rops.back());
+        rwaves.emplace_back();
+        eecmg_status e = plan_waves(items, rwaves.back());
+        if (e != EECMG_OK) return e;
+        std::vector<int> next;
+        for (int i : cur) {
+            Request* r = S->active[i];
+            eecmg_plan_s& P = r->slot;
+            const int st = r->step + round;
+            advance[i] += 1;
+            if (st == P.L - 1) {
+                LevelPlan& F = P.lv[P.L - 1];
+                OpItem c;
+                c.a = F.u;
+                c.out = r->u;
+                c.h = F.h;
+                c.w = F.w;
+                add_op(post, 0, OP_COPY, c);
+                finishing.push_back(r);
+            } else if ((long long)P.lv[st + 1].h * P.lv[st + 1].w <= SMALL_LEVEL_PX) {
+                next.push_back(i);
+            }
+        }
+        cur.swap(next);
     }
-    std::vector<HostWave> waves;
-    eecmg_status e = plan_waves(items, waves);
-    if (e != EECMG_OK) return e;
     // pack job tables and op items into the tick's ring slot: one upload
     size_t need = 0;
-    for (auto* gs : {&pre, &post})
-        for (auto& g : *gs) need += round256(sizeof(OpItem) * g.items.size());
-    for (auto& w : waves)
-        need += round256(sizeof(LevelJob) * w.jobs.size()) + round256(sizeof(unsigned short) * w.block_job.size());
+    auto groups_need = [&](const std::vector<OpGroup>& gs) {
+        for (auto& g : gs) need += round256(sizeof(OpItem) * g.items.size());
+    };
+    groups_need(pre);
+    groups_need(post);
+    for (auto& ro : rops) groups_need(ro);
+    for (auto& ws : rwaves)
+        for (auto& w : ws)
+            need += round256(sizeof(LevelJob) * w.jobs.size()) +
+                    round256(sizeof(unsigned short) * w.block_job.size());
     if (need > S->ring_bytes)
         return set_error(EECMG_ERR_INVALID_ARG, "eecmg_server: tick tables exceed the ring slot");
     char* h = S->h_ring + (size_t)k * S->ring_bytes;
@@ -283,20 +320,33 @@ eecmg_status enqueue_tick(eecmg_server_s* S, const std::vector<Request*>& admitt
         return true;
     };
     std::vector<Placed> pre_l, post_l;
-    std::vector<size_t> jo(waves.size()), bo(waves.size());
+    std::vector<std::vector<Placed>> rops_l(rops.size());
+    std::vector<std::vector<size_t>> jo(rwaves.size()), bo(rwaves.size());
     bool fits = place_groups(pre, pre_l) && place_groups(post, post_l);
-    for (size_t w = 0; w < waves.size() && fits; ++w)
-        fits = put(waves[w].jobs.data(), sizeof(LevelJob) * waves[w].jobs.size(), &jo[w]) &&
-               put(waves[w].block_job.data(), sizeof(unsigned short) * waves[w].block_job.size(), &bo[w]);
+    for (size_t r = 0; r < rops.size() && fits; ++r) fits = place_groups(rops[r], rops_l[r]);
+    for (size_t r = 0; r < rwaves.size() && fits; ++r) {
+        const auto& waves = rwaves[r];
+        jo[r].resize(waves.size());
+        bo[r].resize(waves.size());
+        for (size_t w = 0; w < waves.size() && fits; ++w)
+            fits = put(waves[w].jobs.data(), sizeof(LevelJob) * waves[w].jobs.size(), &jo[r][w]) &&
+                   put(waves[w].block_job.data(), sizeof(unsigned short) * waves[w].block_job.size(),
+                       &bo[r][w]);
+    }
     if (!fits) return set_error(EECMG_ERR_INVALID_ARG, "eecmg_server: tick tables exceed the ring slot");
     if (off) SCK(cudaMemcpyAsync(d, h, off, cudaMemcpyHostToDevice, s));
     for (const Placed& p : pre_l)
         SCK(launch_ops_batch(p.op, (const OpItem*)(d + p.at), p.n, p.blocks, s));
-    for (size_t w = 0; w < waves.size(); ++w) {
-        const HostWave& W = waves[w];
-        SCK(launch_level_batch((const LevelJob*)(d + jo[w]), (const unsigned short*)(d + bo[w]),
-                               (int)W.jobs.size(), W.blocks, W.rt, W.sep, W.prec, W.cgls, W.bf16,
-                               W.cluster, W.resident, s));
+    for (size_t r = 0; r < rops.size(); ++r) {
+        for (const Placed& p : rops_l[r])
+            SCK(launch_ops_batch(p.op, (const OpItem*)(d + p.at), p.n, p.blocks, s));
+        const auto& waves = rwaves[r];
+        for (size_t w = 0; w < waves.size(); ++w) {
+            const HostWave& W = waves[w];
+            SCK(launch_level_batch((const LevelJob*)(d + jo[r][w]), (const unsigned short*)(d + bo[r][w]),
+                                   (int)W.jobs.size(), W.blocks, W.rt, W.sep, W.prec, W.cgls, W.bf16,
+                                   W.cluster, W.resident, s));
+        }
     }
     for (const Placed& p : post_l)
         SCK(launch_ops_batch(p.op, (const OpItem*)(d + p.at), p.n, p.blocks, s));
@@ -429,13 +479,16 @@ void scheduler(eecmg_server_s* S) {
         const int k = (int)(S->tick % RING);
         if (S->busy[k]) complete(S, k);
         std::vector<Request*> finishing;
-        eecmg_status st = enqueue_tick(S, admitted, k, finishing);
+        std::vector<int> advance;
+        eecmg_status st = enqueue_tick(S, admitted, k, finishing, advance);
         if (st != EECMG_OK) {
             fail_all(S, st);
             continue;
         }
         S->busy[k] = true;
         S->fin[k] = finishing;
+        // advance[i] belongs to S->active[i] as enqueued (only this thread changes active)
+        for (size_t i = 0; i < advance.size(); ++i) S->active[i]->step += advance[i];
         {
             std::lock_guard<std::mutex> lk(S->mu);
             auto done = [&](Request* r) {
@@ -443,7 +496,6 @@ void scheduler(eecmg_server_s* S) {
             };
             S->active.erase(std::remove_if(S->active.begin(), S->active.end(), done), S->active.end());
         }
-        for (Request* r : S->active) ++r->step;
         ++S->tick;
     }
 }

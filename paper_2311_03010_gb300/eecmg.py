@@ -53,6 +53,7 @@ class eecmg_options(ctypes.Structure):
         ("precise_conv", ctypes.c_int),
         ("persistent", ctypes.c_int),
         ("workspace", ctypes.c_int),
+        ("fuse_start", ctypes.c_int),
     ]
 
 

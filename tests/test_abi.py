@@ -44,7 +44,7 @@ def test_version_and_defaults(lib):
     assert (o.c, o.delta, o.diffusion_steps, o.s_scale) == (1.1, 0.0, 1, 1.0)
     assert o.conv_tol == 1e-5 and o.prolong == 0 and o.use_graph == 1 and o.persistent == 1
     assert o.precise_conv == -1  # resolved per plan: compensated where a level can run long
-    assert o.workspace == 1
+    assert o.workspace == 1 and o.fuse_start == 0
 
 
 @pytest.mark.parametrize("args,status", [

@@ -319,6 +319,36 @@ def test_precise_conv_auto_resolution(gpu):
     assert np.array_equal(run(), run(precise_conv=1))
 
 
+def test_fused_level_start_is_bitwise_the_separate_start(gpu):
+    """fuse_start = 1 (each prolonged level's solve runs D(S(P(Pi))) as its first phase: one
+    launch per cascade step) gives bitwise the restoration of the separate start, alone and
+    batched, MR-II and CGLS, on levels of every solver form (resident, cluster, grid)."""
+    torch, E = gpu
+    cases = _batch_cases()
+    outs = {}
+    for fuse in (0, 1):
+        plans, gs, us = [], [], []
+        for (p, L, smo) in cases:
+            h, w = p.g.shape
+            pl = E.Plan(w, h, L, p.psf, smoother=smo, delta=p.delta, fuse_start=fuse)
+            gd = dev(torch, p.g)
+            ud = torch.empty_like(gd)
+            pl.restore(gd, ud)
+            plans.append(pl)
+            gs.append(gd)
+            us.append(host(ud))
+        bu = [torch.empty_like(g) for g in gs]
+        E.eecmg_restore_batched([pl.handle for pl in plans], gs, bu)
+        outs[fuse] = (us, [host(u) for u in bu], E.eecmg_batch_info(plans))
+        for pl in plans:
+            pl.close()
+    for k in range(len(cases)):
+        assert np.array_equal(outs[0][0][k], outs[1][0][k]), k
+        assert np.array_equal(outs[0][1][k], outs[1][1][k]), k
+        assert np.array_equal(outs[1][0][k], outs[1][1][k]), k
+    assert outs[1][2] < outs[0][2]  # fewer launches per batched restoration
+
+
 def test_discrepancy_stop_is_the_default(gpu, orc):
     """Default options with delta set: the same counts and bits as stop = "discrepancy"."""
     torch, E = gpu
