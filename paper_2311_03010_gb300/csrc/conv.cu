@@ -70,12 +70,12 @@ __global__ void __launch_bounds__(NTHREADS) k_conv(ConvArgs a) {
                     case CM_MR_V1: {  // v_1 = H r_0, with <v, v>, <v, r_0>
                         y[idx] = z;
                         acc0 = fmaf(z, z, acc0);
-                        acc1 = fmaf(z, S.in[(r + R) * IW + c + R], acc1);
+                        acc1 = fmaf(z, S.in[SM::at(r + R, c + R)], acc1);
                     } break;
                     case CM_MR_A: {   // H w_k = H v_k / ||v_k||, with <H w_k, v_k>
                         const float hz = z * scale;
                         y[idx] = hz;
-                        acc0 = fmaf(hz, S.in[(r + R) * IW + c + R], acc0);
+                        acc0 = fmaf(hz, S.in[SM::at(r + R, c + R)], acc0);
                     } break;
                     case CM_CG_S0: {
                         y[idx] = z;

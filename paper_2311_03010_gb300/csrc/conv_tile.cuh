@@ -5,11 +5,12 @@
 // The input tile plus a halo of R pixels is staged in shared memory (zero
 // outside the image: the block-Toeplitz boundary of Eq. 7).  Separable PSFs
 // run a vertical then a horizontal pass, each thread sliding a register
-// window over 8 outputs; other PSFs run over their non-zero taps.  PREC
+// window over its outputs; other PSFs run over their non-zero taps.  PREC
 // selects a compensated horizontal pass: each product is split exactly into
 // p + pe with an FMA, the p are summed with Kahan compensation and the pe in
-// a separate accumulator (7 FP32 operations per tap instead of 1).  The result lands in S.out (row r, column c at r * PO + c) and the
-// staged input stays in S.in (pixel (r, c) of the tile at (r + R) * IW + c + R).
+// a separate accumulator (7 FP32 operations per tap instead of 1).  The result
+// lands in S.out (row r, column c at r * PO + c) and the staged input stays in
+// S.in (pixel (r, c) of the tile at S.at(r + R, c + R)).
 #pragma once
 
 #include "launch.hpp"
@@ -20,16 +21,29 @@ template <int R, bool SEP>
 struct ConvSmem {
     static constexpr int TH = CONV_TH, TW = CONV_TW;
     static constexpr int IH = TH + 2 * R, IW = TW + 2 * R;
+    // Input rows start 16-byte aligned and hold the window from column -X0:
+    // the halo rounded up to whole 4-float chunks, so that a row of the
+    // window arrives as aligned 16-byte chunks (one shared store each).
+    static constexpr int PADX = (R + 3) / 4 * 4;
+    static constexpr int X0 = PADX - R;
+    static constexpr int IP = TW + 2 * PADX;
     static constexpr int PT = TW + 2 * R + 1;  // odd pitch: conflict-free column walks
     static constexpr int PO = TW + 1;
     static constexpr int NT = SEP ? 1 : (2 * R + 1) * (2 * R + 1);
-    float in[IH * IW];
+    // Vertical pass of the separable form: VG groups of VR consecutive rows
+    // per window column, one group per thread, every thread busy in one
+    // round (the last group starts at TH - VR and overlaps the one before).
+    static constexpr int VG = 3 * IW <= NTHREADS ? 3 : 2;
+    static constexpr int VR = (TH + VG - 1) / VG;
+    alignas(16) float in[IH * IP];
     float tmp[SEP ? TH * PT : 1];
     float out[TH * PO];
     float cy[2 * R + 1], cx[2 * R + 1];
     int off[NT];
     float wt[NT];
     int ntap;
+    // index in `in` of window pixel (r, c), r in [0, IH), c in [0, IW)
+    static __device__ __forceinline__ int at(int r, int c) { return r * IP + X0 + c; }
 };
 
 // Stages the level's taps (then __syncthreads()).  The kernel radius R may
@@ -50,7 +64,8 @@ __device__ __forceinline__ void conv_stage_taps(ConvSmem<R, SEP>& S, const Taps*
         const int nt = taps->ntap;
         if (tid == 0) S.ntap = nt;
         for (int t = tid; t < nt; t += NTHREADS) {
-            S.off[t] = (taps->dy[t] + R) * ConvSmem<R, SEP>::IW + (taps->dx[t] + R);
+            // offset of tap (dy, dx) from window pixel (r, c) to (r + dy + R, c + dx + R)
+            S.off[t] = (taps->dy[t] + R) * ConvSmem<R, SEP>::IP + (taps->dx[t] + R);
             S.wt[t] = taps->wt[t];
         }
     }
@@ -135,25 +150,37 @@ __device__ __forceinline__ void conv_fetch(ConvRegs<R, SEP, TIN>& V, const TIN* 
 }
 
 // Stores a fetched tile into S.in as FP32 (the caller synchronises before reading it).
+// FP32 chunks land whole (their columns line up with the rows of S.in); BF16
+// chunks are widened element by element, the parts outside the window dropped.
 template <int R, bool SEP, typename TIN = float>
 __device__ __forceinline__ void conv_put(ConvSmem<R, SEP>& S, const ConvRegs<R, SEP, TIN>& V) {
     using CR = ConvRegs<R, SEP, TIN>;
-    constexpr int IW = ConvSmem<R, SEP>::IW, EPC = CR::EPC;
+    using SM = ConvSmem<R, SEP>;
+    constexpr int IW = SM::IW, EPC = CR::EPC;
     const int tid = threadIdx.x;
+    if constexpr (EPC == 4) {
+        static_assert(CR::PADX == SM::PADX && CR::CPR * 4 == SM::IP, "FP32 chunks must tile the rows of S.in");
 #pragma unroll
-    for (int k = 0; k < CR::ITERS; ++k) {
-        const int i = tid + k * NTHREADS;
-        if (i < CR::NC) {
-            const int r = i / CR::CPR, c = i - r * CR::CPR;
-            const int lc = EPC * c - CR::XOFF;  // tile column of the chunk's first element
-            float* dst = S.in + r * IW + lc;
-            if (lc >= 0 && lc + EPC - 1 < IW) {
+        for (int k = 0; k < CR::ITERS; ++k) {
+            const int i = tid + k * NTHREADS;
+            if (i < CR::NC) reinterpret_cast<uint4*>(S.in)[i] = V.q[k];
+        }
+    } else {
 #pragma unroll
-                for (int e = 0; e < EPC; ++e) dst[e] = chunk_elem(V.q[k], e, TIN());
-            } else {
+        for (int k = 0; k < CR::ITERS; ++k) {
+            const int i = tid + k * NTHREADS;
+            if (i < CR::NC) {
+                const int r = i / CR::CPR, c = i - r * CR::CPR;
+                const int lc = EPC * c - CR::XOFF;  // window column of the chunk's first element
+                float* dst = S.in + SM::at(r, lc);
+                if (lc >= 0 && lc + EPC - 1 < IW) {
 #pragma unroll
-                for (int e = 0; e < EPC; ++e)
-                    if (lc + e >= 0 && lc + e < IW) dst[e] = chunk_elem(V.q[k], e, TIN());
+                    for (int e = 0; e < EPC; ++e) dst[e] = chunk_elem(V.q[k], e, TIN());
+                } else {
+#pragma unroll
+                    for (int e = 0; e < EPC; ++e)
+                        if (lc + e >= 0 && lc + e < IW) dst[e] = chunk_elem(V.q[k], e, TIN());
+                }
             }
         }
     }
@@ -171,30 +198,35 @@ __device__ __forceinline__ void conv_load(ConvSmem<R, SEP>& S, const TIN* __rest
 // Computes S.out from S.in (the caller synchronises before and after).
 template <int R, bool SEP, bool PREC>
 __device__ __forceinline__ void conv_compute(ConvSmem<R, SEP>& S) {
-    constexpr int IW = ConvSmem<R, SEP>::IW, PT = ConvSmem<R, SEP>::PT, PO = ConvSmem<R, SEP>::PO;
+    using SM = ConvSmem<R, SEP>;
+    constexpr int IW = SM::IW, PT = SM::PT, PO = SM::PO, VR = SM::VR, VG = SM::VG;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (SEP) {
-        // Each thread slides a register window over 8 outputs; the taps are
+        // Each thread slides a register window over its outputs; the taps are
         // read from shared memory (a broadcast) once per tap, tap-outer, so the
-        // window and the 8 accumulators are all that live in registers.  Every
+        // window and the accumulators are all that live in registers.  Every
         // output still sums its taps in increasing order.
-        // vertical pass: tmp(r, c) = sum_d cy[d] in(r + d, c), r < TH, all IW columns
-        for (int item = tid; item < 4 * IW; item += NTHREADS) {
-            const int rg = item / IW, c = item - rg * IW;
-            float v[8 + 2 * R];
+        // vertical pass: tmp(r, c) = sum_d cy[d] in(r + d, c), r < TH, all IW columns;
+        // thread (g, c) takes rows r0 .. r0 + VR - 1 of column c
+        const int g = tid / IW, c = tid - g * IW;
+        if (g < VG) {
+            const int r0 = g == VG - 1 ? CONV_TH - VR : g * VR;
+            float v[VR + 2 * R];
 #pragma unroll
-            for (int j = 0; j < 8 + 2 * R; ++j) v[j] = S.in[(rg * 8 + j) * IW + c];
-            float acc[8];
+            for (int j = 0; j < VR + 2 * R; ++j) v[j] = S.in[SM::at(r0 + j, c)];
+            float acc[VR];
 #pragma unroll
-            for (int i = 0; i < 8; ++i) acc[i] = 0.f;
+            for (int i = 0; i < VR; ++i) acc[i] = 0.f;
 #pragma unroll
             for (int d = 0; d < 2 * R + 1; ++d) {
                 const float cd = S.cy[d];
 #pragma unroll
-                for (int i = 0; i < 8; ++i) acc[i] = fmaf(cd, v[i + d], acc[i]);
+                for (int i = 0; i < VR; ++i) acc[i] = fmaf(cd, v[i + d], acc[i]);
             }
+            // rows the group before already wrote are skipped
 #pragma unroll
-            for (int i = 0; i < 8; ++i) S.tmp[(rg * 8 + i) * PT + c] = acc[i];
+            for (int i = 0; i < VR; ++i)
+                if (g < VG - 1 || i >= VG * VR - CONV_TH) S.tmp[(r0 + i) * PT + c] = acc[i];
         }
         __syncthreads();
         // horizontal pass: one row per lane, 8 consecutive columns per warp
@@ -238,12 +270,12 @@ __device__ __forceinline__ void conv_compute(ConvSmem<R, SEP>& S) {
 #pragma unroll
         for (int i = 0; i < 8; ++i) acc[i] = 0.f;
         const int nt = S.ntap;
-        const float* base = S.in + (rg * 8) * IW + c;
+        const float* base = S.in + SM::at(rg * 8, c);
         for (int t = 0; t < nt; ++t) {
             const float wt = S.wt[t];
             const float* p = base + S.off[t];
 #pragma unroll
-            for (int i = 0; i < 8; ++i) acc[i] = fmaf(wt, p[i * IW], acc[i]);
+            for (int i = 0; i < 8; ++i) acc[i] = fmaf(wt, p[i * SM::IP], acc[i]);
         }
 #pragma unroll
         for (int i = 0; i < 8; ++i) S.out[(rg * 8 + i) * PO + c] = acc[i];

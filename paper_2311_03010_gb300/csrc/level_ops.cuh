@@ -57,9 +57,11 @@ __device__ __forceinline__ float smooth_value_rd(Rd rd, int h, int w, float scal
             const int k = (s + 1) * 3 + (t + 1);
             const int ii = i + s, jj = j + t;
             const bool inside = !EDGE || (ii >= 0 && ii < h && jj >= 0 && jj < w);
-            const float v = inside ? rd(ii, jj) - uc : 0.f;
+            // the centre term is v = 0, weight exp(0) = 1 exactly (as the exponential gives it)
+            const bool ctr = s == 0 && t == 0;
+            const float v = ctr ? 0.f : (inside ? rd(ii, jj) - uc : 0.f);
             const float e = scale * v;
-            const float wt = inside ? __expf(-e * e) : 0.f;  // MUFU exp: ~2 ulp, ample for a weight
+            const float wt = ctr ? 1.f : (inside ? __expf(-e * e) : 0.f);  // MUFU exp: ~2 ulp, ample for a weight
             ws[k] = wt;
             ss[k] = (float)s;
             ts[k] = (float)t;

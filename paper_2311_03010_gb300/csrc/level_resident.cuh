@@ -109,7 +109,7 @@ __device__ __forceinline__ void conv_load_res(ConvSmem<R, SEP>& S, unsigned int 
 #pragma unroll
     for (int it = 0; it < ITERS; ++it) {
         const int i = threadIdx.x + it * NTHREADS;
-        if (i < NTOT) S.in[i] = vals[it];
+        if (i < NTOT) S.in[ConvSmem<R, SEP>::at(i / IW, i % IW)] = vals[it];
     }
 }
 
@@ -121,34 +121,38 @@ __device__ __forceinline__ void conv_load_res(ConvSmem<R, SEP>& S, unsigned int 
 // block holds one SM), with the operations of conv_compute per output.
 template <int R, bool SEP, bool PREC>
 __device__ __forceinline__ void conv_compute2(ConvSmem<R, SEP>& A, ConvSmem<R, SEP>& B) {
-    constexpr int IW = ConvSmem<R, SEP>::IW, PT = ConvSmem<R, SEP>::PT, PO = ConvSmem<R, SEP>::PO;
+    using SM = ConvSmem<R, SEP>;
+    constexpr int IW = SM::IW, PT = SM::PT, PO = SM::PO, VR = SM::VR, VG = SM::VG;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     ConvSmem<R, SEP>* S[2] = {&A, &B};
     if (SEP) {
-        for (int item = tid; item < 4 * IW; item += NTHREADS) {
-            const int rg = item / IW, c = item - rg * IW;
-            float v[2][8 + 2 * R];
+        // vertical pass: thread (g, c) takes rows r0 .. r0 + VR - 1 of column c of both tiles
+        const int g = tid / IW, c = tid - g * IW;
+        if (g < VG) {
+            const int r0 = g == VG - 1 ? CONV_TH - VR : g * VR;
+            float v[2][VR + 2 * R];
 #pragma unroll
             for (int s = 0; s < 2; ++s)
 #pragma unroll
-                for (int j = 0; j < 8 + 2 * R; ++j) v[s][j] = S[s]->in[(rg * 8 + j) * IW + c];
-            float acc[2][8];
+                for (int j = 0; j < VR + 2 * R; ++j) v[s][j] = S[s]->in[SM::at(r0 + j, c)];
+            float acc[2][VR];
 #pragma unroll
             for (int s = 0; s < 2; ++s)
 #pragma unroll
-                for (int i = 0; i < 8; ++i) acc[s][i] = 0.f;
+                for (int i = 0; i < VR; ++i) acc[s][i] = 0.f;
 #pragma unroll
             for (int d = 0; d < 2 * R + 1; ++d) {
                 const float cd = A.cy[d];
 #pragma unroll
                 for (int s = 0; s < 2; ++s)
 #pragma unroll
-                    for (int i = 0; i < 8; ++i) acc[s][i] = fmaf(cd, v[s][i + d], acc[s][i]);
+                    for (int i = 0; i < VR; ++i) acc[s][i] = fmaf(cd, v[s][i + d], acc[s][i]);
             }
 #pragma unroll
             for (int s = 0; s < 2; ++s)
 #pragma unroll
-                for (int i = 0; i < 8; ++i) S[s]->tmp[(rg * 8 + i) * PT + c] = acc[s][i];
+                for (int i = 0; i < VR; ++i)
+                    if (g < VG - 1 || i >= VG * VR - CONV_TH) S[s]->tmp[(r0 + i) * PT + c] = acc[s][i];
         }
         __syncthreads();
         const int r = lane, cg = warp;
@@ -202,11 +206,11 @@ __device__ __forceinline__ void conv_compute2(ConvSmem<R, SEP>& A, ConvSmem<R, S
         const int nt = A.ntap;
         for (int t = 0; t < nt; ++t) {
             const float wt = A.wt[t];
-            const int off = A.off[t] + (rg * 8) * IW + c;
+            const int off = A.off[t] + ConvSmem<R, SEP>::at(rg * 8, c);
 #pragma unroll
             for (int s = 0; s < 2; ++s)
 #pragma unroll
-                for (int i = 0; i < 8; ++i) acc[s][i] = fmaf(wt, S[s]->in[off + i * IW], acc[s][i]);
+                for (int i = 0; i < 8; ++i) acc[s][i] = fmaf(wt, S[s]->in[off + i * ConvSmem<R, SEP>::IP], acc[s][i]);
         }
 #pragma unroll
         for (int s = 0; s < 2; ++s)
@@ -235,7 +239,7 @@ __device__ __forceinline__ void conv_phase_res(ConvSmem<R, SEP> (&S)[2], const R
                 const int c = lane + 32 * hf, gx = x0 + c;
                 if (gy < X.h && gx < X.w) {
                     const float z = ZERO ? 0.f : T.out[r * SM::PO + c];
-                    const float ctr = ZERO ? 0.f : T.in[(r + R) * SM::IW + c + R];
+                    const float ctr = ZERO ? 0.f : T.in[SM::at(r + R, c + R)];
                     epi(lt * TILE_PX + r * CONV_TW + c, (size_t)gy * X.w + gx, z, ctr);
                 }
             }

@@ -147,7 +147,7 @@ __device__ __forceinline__ void conv_phase(ConvSmem<R, SEP>& S, const TIN* x, in
                 if (gy < h && gx < w) {
                     const size_t idx = (size_t)gy * w + gx;
                     const float z = ZERO ? 0.f : S.out[r * SM::PO + c];
-                    const float ctr = ZERO ? 0.f : S.in[(r + R) * SM::IW + c + R];
+                    const float ctr = ZERO ? 0.f : S.in[SM::at(r + R, c + R)];
                     epi(idx, z, ctr);
                 }
             }
