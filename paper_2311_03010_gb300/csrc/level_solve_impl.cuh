@@ -64,59 +64,88 @@ struct MrVec {
 };
 
 // MR-II step j on pixels 4q..4q+3 (coherent loads); returns the new r.  d_j is
-// stored as HT; u and r are updated with its unrounded value.
+// stored as HT; u and r are updated with its unrounded value.  Every operand
+// is loaded before the first store (the stores may alias nothing the compiler
+// can see, so a load after a store would wait for it): one round trip to L2.
 template <typename HT>
 __device__ __forceinline__ float4 mr_step4(const LevelJob& J, const MrVec<HT>& M, int j, size_t q,
                                            const StepCoef& c) {
     using IO = VecIO<HT>;
     const int sj = j & 1, sj1 = sj ^ 1;
-    float4 dj = mul4(c.dw, ld4cg(M.v[sj], q));
-    float4 hj = mul4(c.dinv, ld4cg(M.aw[sj], q));
+    const float4 vj = ld4cg(M.v[sj], q), awj = ld4cg(M.aw[sj], q);
+    const float4 uu = ld4cg(J.u, q), rr = ld4cg(J.r, q);
+    float4 dA = vj, hA = vj, dB = vj, hB = vj;
     if (j >= 2) {
-        dj = fma4(-c.d1, IO::ld4(M.d[sj1], q), dj);
-        hj = fma4(-c.d1, ld4cg(M.hd[sj1], q), hj);
+        dA = IO::ld4(M.d[sj1], q);
+        hA = ld4cg(M.hd[sj1], q);
     }
     if (j >= 3) {
-        dj = fma4(-c.d2, IO::ld4(M.d[sj], q), dj);
-        hj = fma4(-c.d2, ld4cg(M.hd[sj], q), hj);
+        dB = IO::ld4(M.d[sj], q);
+        hB = ld4cg(M.hd[sj], q);
+    }
+    float4 dj = mul4(c.dw, vj);
+    float4 hj = mul4(c.dinv, awj);
+    if (j >= 2) {
+        dj = fma4(-c.d1, dA, dj);
+        hj = fma4(-c.d1, hA, hj);
+    }
+    if (j >= 3) {
+        dj = fma4(-c.d2, dB, dj);
+        hj = fma4(-c.d2, hB, hj);
     }
     IO::st4(M.d[sj], q, dj);
     st4(M.hd[sj], q, hj);
-    st4(J.u, q, fma4(c.tau, dj, ld4cg(J.u, q)));
-    const float4 rv = fma4(-c.tau, hj, ld4cg(J.r, q));
+    st4(J.u, q, fma4(c.tau, dj, uu));
+    const float4 rv = fma4(-c.tau, hj, rr);
     st4(J.r, q, rv);
     return rv;
 }
 
-// Applies MR-II step j at pixel i (coherent loads); returns the new r_i.
+// Applies MR-II step j at pixel i (coherent loads, all before the stores);
+// returns the new r_i.
 template <typename HT>
 __device__ __forceinline__ float mr_step_px(const LevelJob& J, const MrVec<HT>& M, int j, size_t i,
                                             float dw, float d1, float d2, float dinv, float tau) {
     using IO = VecIO<HT>;
     const int sj = j & 1, sj1 = sj ^ 1;
-    float dj = dw * ldcg(M.v[sj] + i);
-    float hj = dinv * ldcg(M.aw[sj] + i);
+    const float vj = ldcg(M.v[sj] + i), awj = ldcg(M.aw[sj] + i);
+    const float uu = ldcg(J.u + i), rr = ldcg(J.r + i);
+    float dA = 0.f, hA = 0.f, dB = 0.f, hB = 0.f;
     if (j >= 2) {
-        dj = fmaf(-d1, IO::ld(M.d[sj1], i), dj);
-        hj = fmaf(-d1, ldcg(M.hd[sj1] + i), hj);
+        dA = IO::ld(M.d[sj1], i);
+        hA = ldcg(M.hd[sj1] + i);
     }
     if (j >= 3) {
-        dj = fmaf(-d2, IO::ld(M.d[sj], i), dj);
-        hj = fmaf(-d2, ldcg(M.hd[sj] + i), hj);
+        dB = IO::ld(M.d[sj], i);
+        hB = ldcg(M.hd[sj] + i);
+    }
+    float dj = dw * vj;
+    float hj = dinv * awj;
+    if (j >= 2) {
+        dj = fmaf(-d1, dA, dj);
+        hj = fmaf(-d1, hA, hj);
+    }
+    if (j >= 3) {
+        dj = fmaf(-d2, dB, dj);
+        hj = fmaf(-d2, hB, hj);
     }
     IO::st(M.d[sj], i, dj);
     M.hd[sj][i] = hj;
-    J.u[i] = fmaf(tau, dj, ldcg(J.u + i));
-    const float rv = fmaf(-tau, hj, ldcg(J.r + i));
+    J.u[i] = fmaf(tau, dj, uu);
+    const float rv = fmaf(-tau, hj, rr);
     J.r[i] = rv;
     return rv;
 }
 
 // One convolution phase over the level: y = scale * (C (*) x) for every tile,
-// with epilogue E(idx, z, center) accumulating into acc0/acc1.
+// with epilogue E(idx, z, center, pre) accumulating into acc0/acc1.  pre is
+// the value of the read-only vector `pre` at the pixel (0 if pre is null): its
+// loads are issued before the tile is convolved, so their latency overlaps
+// the compute (loaded inside the epilogue, each would wait behind the
+// epilogue's stores, which the compiler cannot tell apart from it).
 template <int R, bool SEP, bool PREC, bool ZERO, typename TIN = float, class Epi>
 __device__ __forceinline__ void conv_phase(ConvSmem<R, SEP>& S, const TIN* x, int h, int w,
-                                           unsigned int nb, unsigned int bid, Epi&& epi) {
+                                           unsigned int nb, unsigned int bid, const float* pre, Epi&& epi) {
     using SM = ConvSmem<R, SEP>;
     const int tiles_x = (w + CONV_TW - 1) / CONV_TW, tiles_y = (h + CONV_TH - 1) / CONV_TH;
     const int ntiles = tiles_x * tiles_y;
@@ -135,6 +164,16 @@ __device__ __forceinline__ void conv_phase(ConvSmem<R, SEP>& S, const TIN* x, in
             const int tn = t + (int)nb;
             if (tn < ntiles)
                 conv_fetch<R, SEP, true, TIN>(V, x, h, w, (tn / tiles_x) * CONV_TH, (tn % tiles_x) * CONV_TW);
+        }
+        float pv[CONV_TH / 8][2];
+#pragma unroll
+        for (int it = 0; it < CONV_TH / 8; ++it)
+#pragma unroll
+            for (int hf = 0; hf < 2; ++hf) {
+                const int gy = y0 + warp + 8 * it, gx = x0 + lane + 32 * hf;
+                pv[it][hf] = (pre && gy < h && gx < w) ? __ldg(pre + (size_t)gy * w + gx) : 0.f;
+            }
+        if (!ZERO) {
             conv_compute<R, SEP, PREC>(S);
             __syncthreads();
         }
@@ -148,7 +187,7 @@ __device__ __forceinline__ void conv_phase(ConvSmem<R, SEP>& S, const TIN* x, in
                     const size_t idx = (size_t)gy * w + gx;
                     const float z = ZERO ? 0.f : S.out[r * SM::PO + c];
                     const float ctr = ZERO ? 0.f : S.in[SM::at(r + R, c + R)];
-                    epi(idx, z, ctr);
+                    epi(idx, z, ctr, pv[it][hf]);
                 }
             }
         }
@@ -202,8 +241,7 @@ __device__ __forceinline__ void mr2_body(ConvSmem<R, SEP>& S, PsdSmem& M, const 
     {
         float a0 = 0.f, a1 = 0.f;
         const bool zs = J.zero_start != 0;
-        auto epi = [&](size_t idx, float z, float) {
-            const float gv = __ldg(J.g + idx);
+        auto epi = [&](size_t idx, float z, float, float gv) {
             const float rv = gv - z;
             J.r[idx] = rv;
             if (zs) J.u[idx] = 0.f;
@@ -211,9 +249,9 @@ __device__ __forceinline__ void mr2_body(ConvSmem<R, SEP>& S, PsdSmem& M, const 
             a1 = fmaf(gv, gv, a1);
         };
         if (zs)
-            conv_phase<R, SEP, PREC, true>(S, J.u, h, w, nb, bid, epi);
+            conv_phase<R, SEP, PREC, true>(S, J.u, h, w, nb, bid, J.g, epi);
         else
-            conv_phase<R, SEP, PREC, false>(S, J.u, h, w, nb, bid, epi);
+            conv_phase<R, SEP, PREC, false>(S, J.u, h, w, nb, bid, J.g, epi);
         float v[2] = {a0, a1};
         const double ct2 = J.conv_tol2, d2 = J.disc2;
         const double b0 = (J.zero_start ? 8.0 : 12.0) + start_bytes(J);
@@ -234,7 +272,7 @@ __device__ __forceinline__ void mr2_body(ConvSmem<R, SEP>& S, PsdSmem& M, const 
     {
         float a0 = 0.f, a1 = 0.f;
         float* v1 = K.v[1];
-        conv_phase<R, SEP, PREC, false>(S, J.r, h, w, nb, bid, [&](size_t idx, float z, float ctr) {
+        conv_phase<R, SEP, PREC, false>(S, J.r, h, w, nb, bid, nullptr, [&](size_t idx, float z, float ctr, float) {
             v1[idx] = z;
             a0 = fmaf(z, z, a0);
             a1 = fmaf(z, ctr, a1);
@@ -255,12 +293,12 @@ __device__ __forceinline__ void mr2_body(ConvSmem<R, SEP>& S, PsdSmem& M, const 
             const float scale = vldf(&sc->f_scale);
             float a0 = 0.f;
             float* aw = K.aw[sk];
-            conv_phase<R, SEP, PREC, false>(S, K.v[sk], h, w, nb, bid,
-                                                [&](size_t idx, float z, float ctr) {
-                                                    const float hz = z * scale;
-                                                    aw[idx] = hz;
-                                                    a0 = fmaf(hz, ctr, a0);
-                                                });
+            conv_phase<R, SEP, PREC, false>(S, K.v[sk], h, w, nb, bid, nullptr,
+                                            [&](size_t idx, float z, float ctr, float) {
+                                                const float hz = z * scale;
+                                                aw[idx] = hz;
+                                                a0 = fmaf(hz, ctr, a0);
+                                            });
             float v[1] = {a0};
             if (!sy.reduce<1>(v, [&](DF* t) {
                     fin_mr_a(sc, t[0]);
@@ -420,8 +458,7 @@ __device__ __forceinline__ void cgls_body(ConvSmem<R, SEP>& S, PsdSmem& M, const
     {
         float a0 = 0.f, a1 = 0.f;
         const bool zs = J.zero_start != 0;
-        auto epi = [&](size_t idx, float z, float) {
-            const float gv = __ldg(J.g + idx);
+        auto epi = [&](size_t idx, float z, float, float gv) {
             const float rv = gv - z;
             rv_[idx] = rv;
             if (zs) J.u[idx] = 0.f;
@@ -429,9 +466,9 @@ __device__ __forceinline__ void cgls_body(ConvSmem<R, SEP>& S, PsdSmem& M, const
             a1 = fmaf(gv, gv, a1);
         };
         if (zs)
-            conv_phase<R, SEP, PREC, true>(S, J.u, h, w, nb, bid, epi);
+            conv_phase<R, SEP, PREC, true>(S, J.u, h, w, nb, bid, J.g, epi);
         else
-            conv_phase<R, SEP, PREC, false>(S, J.u, h, w, nb, bid, epi);
+            conv_phase<R, SEP, PREC, false>(S, J.u, h, w, nb, bid, J.g, epi);
         float v[2] = {a0, a1};
         const double ct2 = J.conv_tol2, d2 = J.disc2;
         const double sb = start_bytes(J);  // the host counts the CGLS phases themselves
@@ -447,7 +484,7 @@ __device__ __forceinline__ void cgls_body(ConvSmem<R, SEP>& S, PsdSmem& M, const
     __syncthreads();
     {
         float a0 = 0.f;
-        conv_phase<R, SEP, PREC, false>(S, rv_, h, w, nb, bid, [&](size_t idx, float z, float) {
+        conv_phase<R, SEP, PREC, false>(S, rv_, h, w, nb, bid, nullptr, [&](size_t idx, float z, float, float) {
             IO::st(sv, idx, z);
             IO::st(pv, idx, z);
             a0 = fmaf(z, z, a0);
@@ -463,7 +500,7 @@ __device__ __forceinline__ void cgls_body(ConvSmem<R, SEP>& S, PsdSmem& M, const
         __syncthreads();
         {
             float a0 = 0.f;
-            conv_phase<R, SEP, PREC, false, HT>(S, pv, h, w, nb, bid, [&](size_t idx, float z, float) {
+            conv_phase<R, SEP, PREC, false, HT>(S, pv, h, w, nb, bid, nullptr, [&](size_t idx, float z, float, float) {
                 qv[idx] = z;
                 a0 = fmaf(z, z, a0);
             });
@@ -501,7 +538,7 @@ __device__ __forceinline__ void cgls_body(ConvSmem<R, SEP>& S, PsdSmem& M, const
         __syncthreads();
         {
             float a0 = 0.f;
-            conv_phase<R, SEP, PREC, false>(S, rv_, h, w, nb, bid, [&](size_t idx, float z, float) {
+            conv_phase<R, SEP, PREC, false>(S, rv_, h, w, nb, bid, nullptr, [&](size_t idx, float z, float, float) {
                 IO::st(sv, idx, z);
                 a0 = fmaf(z, z, a0);
             });
