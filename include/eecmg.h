@@ -121,6 +121,15 @@ enum { EECMG_PROLONG_EECMG = 0, EECMG_PROLONG_IECMG_P = 1, EECMG_PROLONG_IECMG_L
  *                         a solve runs two blocks per SM).  The two coarsest
  *                         levels write their zero start inside their solve
  *                         either way.
+ *   early_check = 1       MR-II's early stop check under the discrepancy
+ *                         rule (Section 2): when the rotation predicts
+ *                         ||r_k|| within 1/64 of the limit, the solve updates
+ *                         u with step k and tests the explicit ||r_k|| before
+ *                         spending iteration k + 1's convolution; if the test
+ *                         fails, the next iteration completes the step.  The
+ *                         iterate and every decision are the same as without
+ *                         the check.  0: no early check; 2: a check before
+ *                         every step (the same result; for tests).
  */
 typedef struct {
     int smoother;
@@ -138,6 +147,7 @@ typedef struct {
     int persistent;
     int workspace;
     int fuse_start;
+    int early_check;
 } eecmg_options;
 
 typedef struct eecmg_plan_s *eecmg_plan_t;
@@ -217,6 +227,18 @@ eecmg_status eecmg_restore_host(eecmg_plan_t plan, const float *g_host, float *u
  */
 eecmg_status eecmg_restore_batched_host(const eecmg_plan_t *plans, const float *const *g_host,
                                         float *const *u_host, int n, cudaStream_t stream);
+
+/*
+ * eecmg_restore_batched_host without the final synchronisation: the copies
+ * in, the batched restoration and the copies out are queued on `stream` and
+ * the call returns.  The host buffers must stay valid (and the plans unused
+ * elsewhere) until the stream has passed this point; with pinned host memory
+ * the copies run asynchronously, so a caller that alternates two sets of
+ * plans on two streams overlaps one batch's copies with the other's
+ * restoration.  Errors as eecmg_restore_batched.
+ */
+eecmg_status eecmg_restore_batched_host_async(const eecmg_plan_t *plans, const float *const *g_host,
+                                              float *const *u_host, int n, cudaStream_t stream);
 
 /*
  * Restores n images with their own plans (sizes, PSFs, levels and options

@@ -47,6 +47,7 @@ LevelJob make_job(eecmg_plan_s* P, int l) {
     J.gs = P->gsync + l;
     J.conv_tol2 = P->conv_tol2;
     J.disc2 = L.disc2;
+    J.early = P->opt.early_check;
     J.h = L.h;
     J.w = L.w;
     J.m = L.m;

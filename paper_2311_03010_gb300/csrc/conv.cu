@@ -24,7 +24,7 @@ template <int R, bool SEP, bool PREC>
 __global__ void __launch_bounds__(NTHREADS) k_conv(ConvArgs a) {
     using SM = ConvSmem<R, SEP>;
     __shared__ SM S;
-    constexpr int IW = SM::IW, PO = SM::PO, TH = SM::TH;
+    constexpr int PO = SM::PO, TH = SM::TH;
 
     const int mode = a.mode;
     if (a.sc != nullptr && mode != CM_RESID) {

@@ -27,8 +27,13 @@ struct ConvSmem {
     static constexpr int PADX = (R + 3) / 4 * 4;
     static constexpr int X0 = PADX - R;
     static constexpr int IP = TW + 2 * PADX;
-    static constexpr int PT = TW + 2 * R + 1;  // odd pitch: conflict-free column walks
+    // tmp pitch: the window rounded up to whole 16-byte vectors (rows are read as
+    // 16-byte vectors), an odd number of them, so the 8 rows of a quarter warp's
+    // 16-byte loads fall on distinct banks
+    static constexpr int PT0 = (IW + 3) / 4 * 4;
+    static constexpr int PT = (PT0 / 4) % 2 == 1 ? PT0 : PT0 + 4;
     static constexpr int PO = TW + 1;
+    static constexpr int NTAP4 = (2 * R + 1 + 3) / 4 * 4;  // taps padded to whole float4
     static constexpr int NT = SEP ? 1 : (2 * R + 1) * (2 * R + 1);
     // Vertical pass of the separable form: VG groups of VR consecutive rows
     // per window column, one group per thread, every thread busy in one
@@ -36,9 +41,12 @@ struct ConvSmem {
     static constexpr int VG = 3 * IW <= NTHREADS ? 3 : 2;
     static constexpr int VR = (TH + VG - 1) / VG;
     alignas(16) float in[IH * IP];
-    float tmp[SEP ? TH * PT : 1];
+    alignas(16) float tmp[SEP ? TH * PT : 4];
     float out[TH * PO];
-    float cy[2 * R + 1], cx[2 * R + 1];
+    // separable factors, zero-padded to whole float4: each 16-byte load is one
+    // broadcast carrying four taps
+    alignas(16) float cy[NTAP4];
+    alignas(16) float cx[NTAP4];
     int off[NT];
     float wt[NT];
     int ntap;
@@ -54,9 +62,9 @@ __device__ __forceinline__ void conv_stage_taps(ConvSmem<R, SEP>& S, const Taps*
     const int tid = threadIdx.x;
     if (SEP) {
         const int rt = taps->rt;
-        for (int d = tid; d < 2 * R + 1; d += NTHREADS) {
+        for (int d = tid; d < ConvSmem<R, SEP>::NTAP4; d += NTHREADS) {
             const int e = d - R + rt;
-            const bool in = e >= 0 && e <= 2 * rt;
+            const bool in = d <= 2 * R && e >= 0 && e <= 2 * rt;
             S.cy[d] = in ? taps->cy[e] : 0.f;
             S.cx[d] = in ? taps->cx[e] : 0.f;
         }
@@ -218,10 +226,15 @@ __device__ __forceinline__ void conv_compute(ConvSmem<R, SEP>& S) {
 #pragma unroll
             for (int i = 0; i < VR; ++i) acc[i] = 0.f;
 #pragma unroll
-            for (int d = 0; d < 2 * R + 1; ++d) {
-                const float cd = S.cy[d];
+            for (int d4 = 0; d4 < 2 * R + 1; d4 += 4) {
+                const float4 c4 = *reinterpret_cast<const float4*>(S.cy + d4);
+                const float cq[4] = {c4.x, c4.y, c4.z, c4.w};
 #pragma unroll
-                for (int i = 0; i < VR; ++i) acc[i] = fmaf(cd, v[i + d], acc[i]);
+                for (int e = 0; e < 4; ++e)
+                    if (d4 + e <= 2 * R) {
+#pragma unroll
+                        for (int i = 0; i < VR; ++i) acc[i] = fmaf(cq[e], v[i + d4 + e], acc[i]);
+                    }
             }
             // rows the group before already wrote are skipped
 #pragma unroll
@@ -229,11 +242,19 @@ __device__ __forceinline__ void conv_compute(ConvSmem<R, SEP>& S) {
                 if (g < VG - 1 || i >= VG * VR - CONV_TH) S.tmp[(r0 + i) * PT + c] = acc[i];
         }
         __syncthreads();
-        // horizontal pass: one row per lane, 8 consecutive columns per warp
+        // horizontal pass: one row per lane, 8 consecutive columns per warp; the
+        // window (8 + 2R values from column 8 cg, a multiple of 4) as 16-byte loads
         const int r = lane, cg = warp;
-        float v[8 + 2 * R];
+        constexpr int NW = 8 + 2 * R, NW4 = (NW + 3) / 4;
+        float v[4 * NW4];
 #pragma unroll
-        for (int j = 0; j < 8 + 2 * R; ++j) v[j] = S.tmp[r * PT + cg * 8 + j];
+        for (int j4 = 0; j4 < NW4; ++j4) {
+            const float4 q = *reinterpret_cast<const float4*>(S.tmp + r * PT + cg * 8 + 4 * j4);
+            v[4 * j4] = q.x;
+            v[4 * j4 + 1] = q.y;
+            v[4 * j4 + 2] = q.z;
+            v[4 * j4 + 3] = q.w;
+        }
         float acc[8], lo[8], comp[8];
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
@@ -243,7 +264,8 @@ __device__ __forceinline__ void conv_compute(ConvSmem<R, SEP>& S) {
         }
 #pragma unroll
         for (int d = 0; d < 2 * R + 1; ++d) {
-            const float cd = S.cx[d];
+            const float4 c4 = *reinterpret_cast<const float4*>(S.cx + (d & ~3));
+            const float cd = (d & 3) == 0 ? c4.x : ((d & 3) == 1 ? c4.y : ((d & 3) == 2 ? c4.z : c4.w));
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
                 if (PREC) {

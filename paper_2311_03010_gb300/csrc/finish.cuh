@@ -27,7 +27,7 @@ __device__ __forceinline__ DF df_zero() { return DF{0.f, 0.f}; }
 // r = g - H u: ||r||^2, ||g||^2; the stopping limit and the test before
 // iteration 1 (Section 2 discrepancy rule and the convergence stop).
 __device__ __forceinline__ void fin_resid(Scalars* sc, DF rr2, DF gg2, double conv_tol2,
-                                          double disc2) {
+                                          double disc2, int early = 1) {
     const double rr = df_to_double(rr2), gg = df_to_double(gg2);
     sc->rr = rr;
     sc->gg = gg;
@@ -41,9 +41,11 @@ __device__ __forceinline__ void fin_resid(Scalars* sc, DF rr2, DF gg2, double co
     sc->applied = 0;
     // MR-II predicts ||r_k|| (fin_mr_b) only where the discrepancy limit is the one that binds:
     // there the residual stays within a small factor of ||r_0|| and the prediction is accurate
-    // to rounding; at a convergence limit far below ||r_0|| it would be all cancellation
-    sc->lim2spec = (disc2 > 0.0 && disc2 >= l1) ? df_from_double(lim2 * (1.0 + 1.0 / 64.0))
-                                                : DF{-1.f, 0.f};
+    // to rounding; at a convergence limit far below ||r_0|| it would be all cancellation.
+    // early = 0 never checks early, 2 checks before every step (the same result).
+    sc->lim2spec = early == 2 ? DF{3.0e38f, 0.f}
+                   : (early == 1 && disc2 > 0.0 && disc2 >= l1) ? df_from_double(lim2 * (1.0 + 1.0 / 64.0))
+                                                                 : DF{-1.f, 0.f};
     if (!(rr < 1.0e300)) sc->stopped = 3;
     else sc->stopped = (rr <= lim2) ? 1 : 0;
 }

@@ -20,17 +20,31 @@ namespace eecmg {
 // double-float, all on the FP32 pipes: GB300's FP64 pipe is narrow, and an
 // FP64 form of this made the prolongation 20x slower than its memory traffic.
 // The result is the double-float value rounded once to FP32.
+// Pi from the centre value u1(a, b) and the four exact differences d of the
+// level-(l-2) nodes around it (d00 = d(A0, B0), d01 = d(A0, B1), ...).
+__device__ __forceinline__ float pi_from(float u1c, DF d00, DF d01, DF d10, DF d11) {
+    const DF dsum = df_add2(df_add2(d00, d01), df_add2(d10, d11));
+    const DF e = df_add2(DF{u1c, 0.f}, DF{0.0625f * dsum.hi, 0.0625f * dsum.lo});
+    return __fadd_rn(e.hi, e.lo);
+}
+// The exact difference d(A, B) = u1(2A, 2B) - u2(A, B) as a double-float pair.
+__device__ __forceinline__ DF pi_diff(const float* __restrict__ u1, int w1, const float* __restrict__ u2,
+                                      int w2, int A, int B) {
+    return two_sum(u1[(size_t)(2 * A) * w1 + 2 * B], -u2[(size_t)A * w2 + B]);
+}
+// The level-(l-2) nodes (A0, A1) x (B0, B1) that Pi at (a, b) reads.
+__device__ __forceinline__ void pi_nodes(int a, int b, int h2, int w2, int& A0, int& A1, int& B0, int& B1) {
+    A0 = a >> 1;
+    B0 = b >> 1;
+    A1 = (a & 1) ? min(A0 + 1, h2 - 1) : A0;
+    B1 = (b & 1) ? min(B0 + 1, w2 - 1) : B0;
+}
 __device__ __forceinline__ float pi_at(const float* __restrict__ u1, int w1,
                                       const float* __restrict__ u2, int h2, int w2, int a, int b) {
-    const int A0 = a >> 1, B0 = b >> 1;
-    const int A1 = (a & 1) ? min(A0 + 1, h2 - 1) : A0;
-    const int B1 = (b & 1) ? min(B0 + 1, w2 - 1) : B0;
-    auto d = [&](int A, int B) -> DF {
-        return two_sum(u1[(size_t)(2 * A) * w1 + 2 * B], -u2[(size_t)A * w2 + B]);
-    };
-    const DF dsum = df_add2(df_add2(d(A0, B0), d(A0, B1)), df_add2(d(A1, B0), d(A1, B1)));
-    const DF e = df_add2(DF{u1[(size_t)a * w1 + b], 0.f}, DF{0.0625f * dsum.hi, 0.0625f * dsum.lo});
-    return __fadd_rn(e.hi, e.lo);
+    int A0, A1, B0, B1;
+    pi_nodes(a, b, h2, w2, A0, A1, B0, B1);
+    return pi_from(u1[(size_t)a * w1 + b], pi_diff(u1, w1, u2, w2, A0, B0), pi_diff(u1, w1, u2, w2, A0, B1),
+                   pi_diff(u1, w1, u2, w2, A1, B0), pi_diff(u1, w1, u2, w2, A1, B1));
 }
 // Three-point Lagrange weights at offsets 0, 1/4, 1/2, 3/4 of a level-(l-2)
 // cell spanned by the level-(l-1) triplet (2A, 2A+1, 2A+2).
@@ -107,14 +121,16 @@ __device__ __forceinline__ float smooth_value_rd(Rd rd, int h, int w, float scal
         }
     }
     const float e2s = -e1t, e2t = e1s;
+    // the slope's components along the eigenvectors: no decision depends on them, so the
+    // fast division (2 ulp) serves; the eigenvalues, which the cut tests, stay IEEE-rounded
     float gs = 0.f, gt = 0.f;
     if (l1 > thr) {
-        const float c1 = (e1s * csv + e1t * ctv) / l1;
+        const float c1 = __fdividef(e1s * csv + e1t * ctv, l1);
         gs = fmaf(c1, e1s, gs);
         gt = fmaf(c1, e1t, gt);
     }
     if (l2 > thr) {
-        const float c2 = (e2s * csv + e2t * ctv) / l2;
+        const float c2 = __fdividef(e2s * csv + e2t * ctv, l2);
         gs = fmaf(c2, e2s, gs);
         gt = fmaf(c2, e2t, gt);
     }
@@ -162,7 +178,10 @@ constexpr int PSD_CH = PSD_TH + 2, PSD_CW = PSD_TW + 2;  // c: 1
 // Pi window: n consecutive fine indices read level-(l-1) indices 2A .. 2A' + 2 with
 // A' - A <= (n + 2) / 4
 constexpr int PSD_XR = 2 * ((PSD_PH + 2) / 4) + 3, PSD_XC = 2 * ((PSD_PW + 2) / 4) + 3;
+// level-(l-2) nodes under the Pi window: rows 2A of the window and one more
+constexpr int PSD_DR = (PSD_XR - 1) / 2 + 2, PSD_DC = (PSD_XC - 1) / 2 + 2;
 struct PsdSmem {
+    float2 D[PSD_DR][PSD_DC];  // exact differences d(A, B) as (hi, lo)
     float X[PSD_XR][PSD_XC];
     float P[PSD_PH][PSD_PW];
     float S[PSD_SH][PSD_SW];
@@ -181,9 +200,27 @@ __device__ __forceinline__ void tile_psd(PsdSmem& M, const float* __restrict__ u
     const int r0 = 2 * (py0 >> 2), c0 = 2 * (px0 >> 2);
     const int nr = 2 * (((py1 - 1) >> 2) - (py0 >> 2)) + 3;
     const int nc = 2 * (((px1 - 1) >> 2) - (px0 >> 2)) + 3;
+    // the differences d(A, B) of the nodes under the window, each taken once (a node
+    // serves up to nine Pi values), then Pi from them: the same operations as pi_at
+    const int A0w = r0 >> 1, B0w = c0 >> 1;
+    const int nA = min(((min(r0 + nr - 1, h1 - 1)) >> 1) + 1, h2 - 1) - A0w + 1;
+    const int nB = min(((min(c0 + nc - 1, w1 - 1)) >> 1) + 1, w2 - 1) - B0w + 1;
+    for (int k = tid; k < nA * nB; k += NT) {
+        const int ra = k / nB, cb = k - ra * nB;
+        const DF d = pi_diff(u1, w1, u2, w2, A0w + ra, B0w + cb);
+        M.D[ra][cb] = make_float2(d.hi, d.lo);
+    }
+    __syncthreads();
     for (int k = tid; k < nr * nc; k += NT) {
         const int rr = k / nc, cc = k - rr * nc;
-        M.X[rr][cc] = pi_at(u1, w1, u2, h2, w2, min(r0 + rr, h1 - 1), min(c0 + cc, w1 - 1));
+        const int a = min(r0 + rr, h1 - 1), b = min(c0 + cc, w1 - 1);
+        int A0, A1, B0, B1;
+        pi_nodes(a, b, h2, w2, A0, A1, B0, B1);
+        auto dd = [&](int A, int B) {
+            const float2 q = M.D[A - A0w][B - B0w];
+            return DF{q.x, q.y};
+        };
+        M.X[rr][cc] = pi_from(u1[(size_t)a * w1 + b], dd(A0, B0), dd(A0, B1), dd(A1, B0), dd(A1, B1));
     }
     __syncthreads();
     // P on rows y0-3 .. y0+TH+2 and columns x0-3 .. x0+TW+2 (in-image part)

@@ -156,11 +156,18 @@ __device__ __forceinline__ void conv_compute2(ConvSmem<R, SEP>& A, ConvSmem<R, S
         }
         __syncthreads();
         const int r = lane, cg = warp;
-        float v[2][8 + 2 * R];
+        constexpr int NW4 = (8 + 2 * R + 3) / 4;
+        float v[2][4 * NW4];
 #pragma unroll
         for (int s = 0; s < 2; ++s)
 #pragma unroll
-            for (int j = 0; j < 8 + 2 * R; ++j) v[s][j] = S[s]->tmp[r * PT + cg * 8 + j];
+            for (int j4 = 0; j4 < NW4; ++j4) {
+                const float4 q = *reinterpret_cast<const float4*>(S[s]->tmp + r * PT + cg * 8 + 4 * j4);
+                v[s][4 * j4] = q.x;
+                v[s][4 * j4 + 1] = q.y;
+                v[s][4 * j4 + 2] = q.z;
+                v[s][4 * j4 + 3] = q.w;
+            }
         float acc[2][8], lo[2][8], comp[2][8];
 #pragma unroll
         for (int s = 0; s < 2; ++s)
@@ -368,9 +375,10 @@ __device__ __forceinline__ void mr2_res_body(ConvSmem<R, SEP> (&S)[2], PsdSmem& 
             conv_phase_res<R, SEP, PREC, false, true>(S, X, 0, J.u, epi);
         float v[2] = {a0, a1};
         const double ct2 = J.conv_tol2, d2 = J.disc2;
+        const int ear = J.early;
         const double b0 = (J.zero_start ? 8.0 : 12.0) + ls_detail::start_bytes(J);
         if (!sy.reduce<2>(v, [&](DF* t) {
-                fin_resid(sc, t[0], t[1], ct2, d2);
+                fin_resid(sc, t[0], t[1], ct2, d2, ear);
                 sc->bpp = b0;
             }))
             return;
@@ -581,9 +589,10 @@ __device__ __forceinline__ void cgls_res_body(ConvSmem<R, SEP> (&S)[2], PsdSmem&
             conv_phase_res<R, SEP, PREC, false, true>(S, X, 0, J.u, epi);
         float v[2] = {a0, a1};
         const double ct2 = J.conv_tol2, d2 = J.disc2;
+        const int ear = J.early;
         const double sb = ls_detail::start_bytes(J);  // the host counts the CGLS phases themselves
         if (!sy.reduce<2>(v, [&](DF* t) {
-                fin_resid(sc, t[0], t[1], ct2, d2);
+                fin_resid(sc, t[0], t[1], ct2, d2, ear);
                 sc->bpp = sb;
             }))
             return;

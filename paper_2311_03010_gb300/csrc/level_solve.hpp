@@ -23,6 +23,7 @@ struct LevelJob {
     double* partials = nullptr;
     GroupSync* gs = nullptr;
     double conv_tol2 = 0.0, disc2 = 0.0;
+    int early = 1;  // MR-II early stop check: 0 off, 1 near the limit, 2 before every step
     int h = 0, w = 0, m = 0, zero_start = 0;
     int block0 = 0, nblocks = 0;  // this job's blocks within a batched launch
     // The start of the level, run by the solve as its first phase (Algorithm 2,

@@ -63,13 +63,15 @@ struct MrVec {
     }
 };
 
-// MR-II step j on pixels 4q..4q+3 (coherent loads); returns the new r.  d_j is
-// stored as HT; u and r are updated with its unrounded value.  Every operand
-// is loaded before the first store (the stores may alias nothing the compiler
-// can see, so a load after a store would wait for it): one round trip to L2.
+// MR-II step j on pixels 4q..4q+3 (coherent loads), u alone: u += tau d_j;
+// returns the new r without storing it, nor d_j and H d_j.  This is the step
+// of an early check or of the solve's end, whose r, d_j and H d_j are dead
+// unless the solve goes on (phase B of the next iteration then stores them).
+// Every operand is loaded before the store (the stores may alias nothing the
+// compiler can see, so a load after a store would wait for it).
 template <typename HT>
-__device__ __forceinline__ float4 mr_step4(const LevelJob& J, const MrVec<HT>& M, int j, size_t q,
-                                           const StepCoef& c) {
+__device__ __forceinline__ float4 mr_step4_u(const LevelJob& J, const MrVec<HT>& M, int j, size_t q,
+                                             const StepCoef& c) {
     using IO = VecIO<HT>;
     const int sj = j & 1, sj1 = sj ^ 1;
     const float4 vj = ld4cg(M.v[sj], q), awj = ld4cg(M.aw[sj], q);
@@ -93,23 +95,20 @@ __device__ __forceinline__ float4 mr_step4(const LevelJob& J, const MrVec<HT>& M
         dj = fma4(-c.d2, dB, dj);
         hj = fma4(-c.d2, hB, hj);
     }
-    IO::st4(M.d[sj], q, dj);
-    st4(M.hd[sj], q, hj);
     st4(J.u, q, fma4(c.tau, dj, uu));
-    const float4 rv = fma4(-c.tau, hj, rr);
-    st4(J.r, q, rv);
-    return rv;
+    return fma4(-c.tau, hj, rr);
 }
 
 // Applies MR-II step j at pixel i (coherent loads, all before the stores);
-// returns the new r_i.
-template <typename HT>
+// returns the new r_i.  MODE 0: the whole step; 1: u alone (as mr_step4_u);
+// 2: the rest of a step whose u is updated (d_j, H d_j, r).
+template <typename HT, int MODE = 0>
 __device__ __forceinline__ float mr_step_px(const LevelJob& J, const MrVec<HT>& M, int j, size_t i,
                                             float dw, float d1, float d2, float dinv, float tau) {
     using IO = VecIO<HT>;
     const int sj = j & 1, sj1 = sj ^ 1;
     const float vj = ldcg(M.v[sj] + i), awj = ldcg(M.aw[sj] + i);
-    const float uu = ldcg(J.u + i), rr = ldcg(J.r + i);
+    const float uu = MODE == 2 ? 0.f : ldcg(J.u + i), rr = ldcg(J.r + i);
     float dA = 0.f, hA = 0.f, dB = 0.f, hB = 0.f;
     if (j >= 2) {
         dA = IO::ld(M.d[sj1], i);
@@ -129,11 +128,13 @@ __device__ __forceinline__ float mr_step_px(const LevelJob& J, const MrVec<HT>& 
         dj = fmaf(-d2, dB, dj);
         hj = fmaf(-d2, hB, hj);
     }
-    IO::st(M.d[sj], i, dj);
-    M.hd[sj][i] = hj;
-    J.u[i] = fmaf(tau, dj, uu);
     const float rv = fmaf(-tau, hj, rr);
-    J.r[i] = rv;
+    if (MODE != 1) {
+        IO::st(M.d[sj], i, dj);
+        M.hd[sj][i] = hj;
+        J.r[i] = rv;
+    }
+    if (MODE != 2) J.u[i] = fmaf(tau, dj, uu);
     return rv;
 }
 
@@ -254,9 +255,10 @@ __device__ __forceinline__ void mr2_body(ConvSmem<R, SEP>& S, PsdSmem& M, const 
             conv_phase<R, SEP, PREC, false>(S, J.u, h, w, nb, bid, J.g, epi);
         float v[2] = {a0, a1};
         const double ct2 = J.conv_tol2, d2 = J.disc2;
+        const int ear = J.early;
         const double b0 = (J.zero_start ? 8.0 : 12.0) + start_bytes(J);
         if (!sy.reduce<2>(v, [&](DF* t) {
-                fin_resid(sc, t[0], t[1], ct2, d2);
+                fin_resid(sc, t[0], t[1], ct2, d2, ear);
                 sc->bpp = b0;
             }))
             return;
@@ -306,11 +308,12 @@ __device__ __forceinline__ void mr2_body(ConvSmem<R, SEP>& S, PsdSmem& M, const 
                 }))
                 return;
         }
-        // phase B: pending step k-1 (unless an early check applied it), v_{k+1}, stopping
-        // rules, rotation of column k
+        // phase B: pending step k-1 (its d, H d and r only, if an early check updated u
+        // already), v_{k+1}, stopping rules, rotation of column k
         {
             const bool step = k >= 2;
             const bool apply = step && *(volatile const int*)&sc->applied != k - 1;
+            const bool rest = step && !apply;  // the early check of step k-1 did not hold
             const StepCoef c = step_coef(sc);
             // Lanczos coefficients in double-float: the update below cancels
             const float ca = vldf(&sc->f_ca), ca_lo = vldf(&sc->f_ca_lo);
@@ -327,9 +330,9 @@ __device__ __forceinline__ void mr2_body(ConvSmem<R, SEP>& S, PsdSmem& M, const 
                 float4 vj = make_float4(0.f, 0.f, 0.f, 0.f), awj = vj, uu = vj;
                 float4 dA = vj, hA = vj, dB = vj, hB = vj;
                 if (step) vj = ld4cg(K.v[sj], q);
-                if (apply) {
+                if (step) {
                     awj = ld4cg(K.aw[sj], q);
-                    uu = ld4cg(J.u, q);
+                    if (apply) uu = ld4cg(J.u, q);
                     if (j >= 2) {
                         dA = IO::ld4(K.d[sj1], q);
                         hA = ld4cg(K.hd[sj1], q);
@@ -340,7 +343,7 @@ __device__ __forceinline__ void mr2_body(ConvSmem<R, SEP>& S, PsdSmem& M, const 
                     }
                 }
                 float4 rv = rr;
-                if (apply) {  // step j = k - 1 (same operation order as mr_step4)
+                if (step) {  // step j = k - 1 (same operation order as mr_step4)
                     float4 dj = mul4(c.dw, vj);
                     float4 hj = mul4(c.dinv, awj);
                     if (j >= 2) {
@@ -353,7 +356,7 @@ __device__ __forceinline__ void mr2_body(ConvSmem<R, SEP>& S, PsdSmem& M, const 
                     }
                     IO::st4(K.d[sj], q, dj);
                     st4(K.hd[sj], q, hj);
-                    st4(J.u, q, fma4(c.tau, dj, uu));
+                    if (apply) st4(J.u, q, fma4(c.tau, dj, uu));
                     rv = fma4(-c.tau, hj, rr);
                     st4(J.r, q, rv);
                 }
@@ -366,8 +369,9 @@ __device__ __forceinline__ void mr2_body(ConvSmem<R, SEP>& S, PsdSmem& M, const 
             }
             if (bid == 0) {  // the n mod 4 tail
                 for (size_t i = 4 * n4 + threadIdx.x; i < n; i += NTHREADS) {
-                    const float rv = apply ? mr_step_px<HT>(J, K, k - 1, i, c.dw, c.d1, c.d2, c.dinv, c.tau)
-                                           : ldcg(J.r + i);
+                    const float rv = apply  ? mr_step_px<HT>(J, K, k - 1, i, c.dw, c.d1, c.d2, c.dinv, c.tau)
+                                     : rest ? mr_step_px<HT, 2>(J, K, k - 1, i, c.dw, c.d1, c.d2, c.dinv, c.tau)
+                                            : ldcg(J.r + i);
                     if (step) arr = fmaf(rv, rv, arr);
                     const float vki = ldcg(K.v[sk] + i);
                     float vn = fmaf(-ca_lo, vki, fmaf(-ca, vki, ldcg(K.aw[sk] + i)));
@@ -381,7 +385,7 @@ __device__ __forceinline__ void mr2_body(ConvSmem<R, SEP>& S, PsdSmem& M, const 
                 }
             }
             float v[3] = {arr, avv, avr};
-            const double bb = k == 1 ? 16.0 : (apply ? 40.0 + E + hist(k - 1) : 20.0);
+            const double bb = k == 1 ? 16.0 : (apply ? 40.0 + E + hist(k - 1) : 32.0 + E + hist(k - 1));
             if (!sy.reduce<3>(v, [&](DF* t) {
                     fin_mr_b(sc, k, t[0], t[1], t[2]);
                     sc->bpp += bb;
@@ -395,16 +399,16 @@ __device__ __forceinline__ void mr2_body(ConvSmem<R, SEP>& S, PsdSmem& M, const 
             float arr = 0.f;
             const size_t n4 = n >> 2;
             for (size_t q = (size_t)bid * NTHREADS + threadIdx.x; q < n4; q += stride) {
-                const float4 rv = mr_step4<HT>(J, K, k, q, c);
+                const float4 rv = mr_step4_u<HT>(J, K, k, q, c);
                 arr = dot4(rv, rv, arr);
             }
             if (bid == 0)
                 for (size_t i = 4 * n4 + threadIdx.x; i < n; i += NTHREADS) {
-                    const float rv = mr_step_px<HT>(J, K, k, i, c.dw, c.d1, c.d2, c.dinv, c.tau);
+                    const float rv = mr_step_px<HT, 1>(J, K, k, i, c.dw, c.d1, c.d2, c.dinv, c.tau);
                     arr = fmaf(rv, rv, arr);
                 }
             float v[1] = {arr};
-            const double bc = 28.0 + E + hist(k);
+            const double bc = 20.0 + hist(k);
             if (!sy.reduce<1>(v, [&](DF* t) {
                     fin_mr_check(sc, k, t[0]);
                     sc->bpp += bc;
@@ -422,16 +426,16 @@ __device__ __forceinline__ void mr2_body(ConvSmem<R, SEP>& S, PsdSmem& M, const 
         float arr = 0.f;
         const size_t n4 = n >> 2;
         for (size_t q = (size_t)bid * NTHREADS + threadIdx.x; q < n4; q += stride) {
-            const float4 rv = mr_step4<HT>(J, K, j, q, c);
+            const float4 rv = mr_step4_u<HT>(J, K, j, q, c);
             arr = dot4(rv, rv, arr);
         }
         if (bid == 0)
             for (size_t i = 4 * n4 + threadIdx.x; i < n; i += NTHREADS) {
-                const float rv = mr_step_px<HT>(J, K, j, i, c.dw, c.d1, c.d2, c.dinv, c.tau);
+                const float rv = mr_step_px<HT, 1>(J, K, j, i, c.dw, c.d1, c.d2, c.dinv, c.tau);
                 arr = fmaf(rv, rv, arr);
             }
         float v[1] = {arr};
-        const double bf = 28.0 + E + hist(j);
+        const double bf = 20.0 + hist(j);
         sy.reduce<1>(v, [&](DF* t) {
             fin_mr_final(sc, t[0]);
             sc->bpp += bf;
@@ -471,9 +475,10 @@ __device__ __forceinline__ void cgls_body(ConvSmem<R, SEP>& S, PsdSmem& M, const
             conv_phase<R, SEP, PREC, false>(S, J.u, h, w, nb, bid, J.g, epi);
         float v[2] = {a0, a1};
         const double ct2 = J.conv_tol2, d2 = J.disc2;
+        const int ear = J.early;
         const double sb = start_bytes(J);  // the host counts the CGLS phases themselves
         if (!sy.reduce<2>(v, [&](DF* t) {
-                fin_resid(sc, t[0], t[1], ct2, d2);
+                fin_resid(sc, t[0], t[1], ct2, d2, ear);
                 sc->bpp = sb;
             }))
             return;

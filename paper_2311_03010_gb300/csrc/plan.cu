@@ -300,6 +300,7 @@ eecmg_status solve_level_enqueue(eecmg_plan_s* P, int l, const float* g, float* 
         J.gs = P->gsync + l;
         J.conv_tol2 = P->conv_tol2;
         J.disc2 = L.disc2;
+        J.early = P->opt.early_check;
         J.h = L.h;
         J.w = L.w;
         J.m = m;
@@ -600,6 +601,7 @@ eecmg_status eecmg_default_options(eecmg_options* o) {
     o->persistent = 1;
     o->workspace = 1;
     o->fuse_start = 0;
+    o->early_check = 1;
     return EECMG_OK;
 }
 
@@ -623,7 +625,8 @@ eecmg_status eecmg_plan(int width, int height, int levels, const double* psf, in
     if (o.smoother < 0 || o.smoother > 1 || o.coarse_op < 0 || o.coarse_op > 1 || o.storage < 0 ||
         o.storage > 1 || o.stop < 0 || o.stop > 1 || o.prolong < 0 || o.prolong > 2 ||
         o.diffusion_steps < 0 || !(o.conv_tol >= 0.0) || !(o.s_scale >= 0.0) ||
-        o.precise_conv < -1 || o.precise_conv > 1 || o.fuse_start < 0 || o.fuse_start > 1)
+        o.precise_conv < -1 || o.precise_conv > 1 || o.fuse_start < 0 || o.fuse_start > 1 ||
+        o.early_check < 0 || o.early_check > 2)
         return set_error(EECMG_ERR_INVALID_ARG, "eecmg_plan: invalid option value");
     if (o.stop == EECMG_STOP_DISCREPANCY && (!(o.c > 0.0) || !(o.delta >= 0.0)))
         return set_error(EECMG_ERR_INVALID_ARG, "eecmg_plan: discrepancy rule needs c > 0, delta >= 0");
@@ -979,8 +982,8 @@ eecmg_status eecmg_plan_profile_read(eecmg_plan_t P, eecmg_kernel_stat* out, int
     return EECMG_OK;
 }
 
-eecmg_status eecmg_restore_batched_host(const eecmg_plan_t* plans, const float* const* g,
-                                        float* const* u, int n, cudaStream_t s) {
+static eecmg_status restore_batched_host_impl(const eecmg_plan_t* plans, const float* const* g,
+                                              float* const* u, int n, cudaStream_t s, bool sync) {
     if (n < 0 || (n > 0 && (!plans || !g || !u)))
         return set_error(EECMG_ERR_INVALID_ARG, "eecmg_restore_batched_host: bad arguments");
     if (n == 0) return EECMG_OK;
@@ -1003,8 +1006,18 @@ eecmg_status eecmg_restore_batched_host(const eecmg_plan_t* plans, const float* 
         LevelPlan& F = plans[i]->lv[plans[i]->L - 1];
         CK(cudaMemcpyAsync(u[i], F.u, sizeof(float) * plans[i]->W * plans[i]->H, cudaMemcpyDeviceToHost, s));
     }
-    CK(cudaStreamSynchronize(s));
+    if (sync) CK(cudaStreamSynchronize(s));
     return EECMG_OK;
+}
+
+eecmg_status eecmg_restore_batched_host(const eecmg_plan_t* plans, const float* const* g,
+                                        float* const* u, int n, cudaStream_t s) {
+    return restore_batched_host_impl(plans, g, u, n, s, true);
+}
+
+eecmg_status eecmg_restore_batched_host_async(const eecmg_plan_t* plans, const float* const* g,
+                                              float* const* u, int n, cudaStream_t s) {
+    return restore_batched_host_impl(plans, g, u, n, s, false);
 }
 
 eecmg_status eecmg_batch_info(const eecmg_plan_t* plans, int n, int* graph_nodes) {

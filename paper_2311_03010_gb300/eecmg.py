@@ -54,6 +54,7 @@ class eecmg_options(ctypes.Structure):
         ("persistent", ctypes.c_int),
         ("workspace", ctypes.c_int),
         ("fuse_start", ctypes.c_int),
+        ("early_check", ctypes.c_int),
     ]
 
 
@@ -90,6 +91,8 @@ _SIGS = {
     "eecmg_batch_info": [ctypes.POINTER(_VP), _I, _PI],
     "eecmg_restore_batched_host": [ctypes.POINTER(_VP), ctypes.POINTER(_VP), ctypes.POINTER(_VP), _I,
                                    _VP],
+    "eecmg_restore_batched_host_async": [ctypes.POINTER(_VP), ctypes.POINTER(_VP), ctypes.POINTER(_VP),
+                                         _I, _VP],
     "eecmg_level_partition": [_VP, _I, _PI, _PI, _PI],
     "eecmg_plan_profile": [_VP, _I],
     "eecmg_plan_profile_read": [_VP, ctypes.POINTER(eecmg_kernel_stat), _I, _PI],
@@ -338,6 +341,16 @@ def eecmg_restore_batched_host(plans, g_host, u_host, stream=None):
     hg = (_VP * n)(*[_ptr(x) for x in g_host])
     hu = (_VP * n)(*[_ptr(x) for x in u_host])
     _call("eecmg_restore_batched_host", hp, hg, hu, n, _stream(stream))
+
+
+def eecmg_restore_batched_host_async(plans, g_host, u_host, stream=None):
+    """As eecmg_restore_batched_host, queued on the stream without synchronising: the host
+    buffers (pinned, for asynchronous copies) must stay alive until the stream passes it."""
+    n = len(plans)
+    hp = (_VP * n)(*[p.handle if isinstance(p, Plan) else p for p in plans])
+    hg = (_VP * n)(*[_ptr(x) for x in g_host])
+    hu = (_VP * n)(*[_ptr(x) for x in u_host])
+    _call("eecmg_restore_batched_host_async", hp, hg, hu, n, _stream(stream))
 
 
 def eecmg_batch_info(plans):

@@ -44,7 +44,7 @@ def test_version_and_defaults(lib):
     assert (o.c, o.delta, o.diffusion_steps, o.s_scale) == (1.1, 0.0, 1, 1.0)
     assert o.conv_tol == 1e-5 and o.prolong == 0 and o.use_graph == 1 and o.persistent == 1
     assert o.precise_conv == -1  # resolved per plan: compensated where a level can run long
-    assert o.workspace == 1 and o.fuse_start == 0
+    assert o.workspace == 1 and o.fuse_start == 0 and o.early_check == 1
 
 
 @pytest.mark.parametrize("args,status", [
@@ -55,11 +55,12 @@ def test_version_and_defaults(lib):
     (dict(iters=[1, -1, 2]), 1),
     (dict(psf=np.tri(5)), 2),            # MR-II needs a centrosymmetric PSF
     (dict(storage="bf16", persistent=0), 2),  # BF16 storage needs the persistent solve
+    (dict(early_check=3), 1), (dict(fuse_start=2), 1),
 ])
 def test_plan_validation_without_gpu(lib, args, status):
     kw = dict(width=64, height=64, levels=3, psf=np.ones((3, 3)) / 9, alpha=0.2, k=10.0)
     kw.update(args)
-    opts = {k: kw.pop(k) for k in ("storage", "persistent") if k in kw}
+    opts = {k: kw.pop(k) for k in ("storage", "persistent", "early_check", "fuse_start") if k in kw}
     with pytest.raises(lib.EecmgError) as ei:
         lib.eecmg_plan(kw["width"], kw["height"], kw["levels"], kw["psf"], kw["alpha"], kw["k"],
                        kw.get("iters"), **opts)

@@ -349,6 +349,47 @@ def test_fused_level_start_is_bitwise_the_separate_start(gpu):
     assert outs[1][2] < outs[0][2]  # fewer launches per batched restoration
 
 
+def test_early_check_changes_nothing(gpu):
+    """MR-II's early stop check (R29) only moves work: with no check, the default check near
+    the limit, and a check before every step (every following phase B then completes the
+    step the check applied to u alone), the restorations and the iteration counts are bitwise
+    the same, for grid-mode levels (FP32 and BF16 storage) and the small-level solver forms,
+    alone and batched."""
+    torch, E = gpu
+    from paper_2311_03010_gb300 import synth
+
+    cases = [(p, L, smo, "fp32") for (p, L, smo) in _batch_cases()]
+    for (h, w, psf, v, seed, st) in [
+            (512, 512, synth.gaussian_psf(2.5, 7), 0.01, 2000, "fp32"),
+            (512, 512, synth.gaussian_psf(2.5, 7), 0.05, 2000, "fp32"),
+            (700, 1030, synth.motion_psf(15, 30.0), 0.01, 2001, "fp32"),
+            (512, 640, synth.gaussian_psf(2.0, 6), 0.02, 2002, "bf16")]:
+        cases.append((synth.make_problem(h, w, seed, psf, v), 5, "mr2", st))
+    outs = {}
+    for early in (0, 1, 2):
+        plans, gs, us, its = [], [], [], []
+        for (p, L, smo, st) in cases:
+            h, w = p.g.shape
+            pl = E.Plan(w, h, L, p.psf, smoother=smo, storage=st, delta=p.delta, early_check=early)
+            gd = dev(torch, p.g)
+            ud = torch.empty_like(gd)
+            pl.restore(gd, ud)
+            its.append(pl.stats()[0])
+            plans.append(pl)
+            gs.append(gd)
+            us.append(host(ud))
+        bu = [torch.empty_like(g) for g in gs]
+        E.eecmg_restore_batched([pl.handle for pl in plans], gs, bu)
+        outs[early] = (us, [host(u) for u in bu], its)
+        for pl in plans:
+            pl.close()
+    for k in range(len(cases)):
+        for early in (1, 2):
+            assert np.array_equal(outs[0][0][k], outs[early][0][k]), (k, early)
+            assert np.array_equal(outs[0][1][k], outs[early][1][k]), (k, early)
+            assert outs[0][2][k] == outs[early][2][k], (k, early)
+
+
 def test_discrepancy_stop_is_the_default(gpu, orc):
     """Default options with delta set: the same counts and bits as stop = "discrepancy"."""
     torch, E = gpu
@@ -497,6 +538,58 @@ def test_batched_host_entry_point_equals_device(gpu):
     for s_, u in zip(singles, us):
         assert np.array_equal(s_, u.numpy())
     for pl in plans:
+        pl.close()
+
+
+def test_async_host_entry_point_two_in_flight(gpu):
+    """eecmg_restore_batched_host_async on two plan sets and two streams, alternating with a
+    wait only before a set is reused (two batches in flight), gives every step the device
+    result of its images."""
+    torch, E = gpu
+    from paper_2311_03010_gb300 import synth
+
+    cases = _batch_cases()[:3]
+    p4 = synth.make_problem(600, 520, 90, synth.gaussian_psf(2.0, 6), 0.02)
+    cases.append((p4, 5, "mr2"))
+    singles = []
+    sets = [[], []]
+    for (p, L, smo) in cases:
+        h, w = p.g.shape
+        for k in range(2):
+            sets[k].append(E.Plan(w, h, L, p.psf, smoother=smo, delta=p.delta))
+        gd = dev(torch, p.g)
+        ud = torch.empty_like(gd)
+        sets[0][-1].restore(gd, ud)
+        singles.append(host(ud))
+    rng = np.random.default_rng(91)
+    steps = 6
+    # each step restores the images scaled by its own factor (a power of two: exact),
+    # so a result landing in the wrong step's buffer would show
+    scales = [float(2.0 ** rng.integers(-2, 3)) for _ in range(steps)]
+    gh = [[torch.from_numpy(np.ascontiguousarray(p.g * sc, dtype=np.float32)).pin_memory()
+           for (p, _, _) in cases] for sc in scales]
+    uh = [[torch.empty_like(g).pin_memory() for g in gh[0]] for _ in range(steps)]
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    ref = []
+    for i in range(steps):
+        k = i % 2
+        if i >= 2:
+            streams[k].synchronize()
+        E.eecmg_restore_batched_host_async([pl.handle for pl in sets[k]], gh[i], uh[i], streams[k])
+    for s_ in streams:
+        s_.synchronize()
+    for i in range(steps):
+        # the restoration is not linear in g (the stops and S, D are not), so each step is
+        # compared with a synchronous restoration of the same scaled images
+        ref = [torch.empty_like(g).pin_memory() for g in gh[i]]
+        E.eecmg_restore_batched_host([pl.handle for pl in sets[0]], gh[i], ref)
+        for a, b in zip(ref, uh[i]):
+            assert np.array_equal(a.numpy(), b.numpy()), i
+    for i in range(steps):
+        if scales[i] == 1.0:
+            for s_, u in zip(singles, uh[i]):
+                assert np.array_equal(s_, u.numpy())
+    for pl in sets[0] + sets[1]:
         pl.close()
 
 
