@@ -22,6 +22,7 @@
 // with the tick that ran its finest level, and its latency runs from
 // submission to that tick's end event on the device clock.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -43,6 +44,10 @@ namespace {
 using Clock = std::chrono::steady_clock;
 
 constexpr int RING = 2;              // ticks in flight
+// An idle scheduler spins this long on the submission counter before it sleeps,
+// so that a request arriving meanwhile starts without the thread's wake-up
+// latency (one host core stays busy while requests keep arriving).
+constexpr auto IDLE_SPIN = std::chrono::milliseconds(10);
 constexpr size_t QUEUE_CAP = 65536;  // queued (not yet admitted) requests
 constexpr int MAX_LEVELS = 30;
 constexpr int MAX_DIFFUSION = 16;    // Perona-Malik steps per level of a served request
@@ -171,6 +176,8 @@ struct eecmg_server_s {
     uint64_t next_ticket = 1;
     size_t outstanding = 0;
     bool stop = false;
+    std::atomic<uint64_t> submitted{0};  // requests queued so far (read while spinning)
+    std::atomic<bool> stopping{false};
     eecmg_status fatal = EECMG_OK;
     std::string fatal_msg;
     std::thread th;
@@ -449,9 +456,17 @@ void scheduler(eecmg_server_s* S) {
         std::vector<Request*> admitted;
         {
             std::unique_lock<std::mutex> lk(S->mu);
-            S->cv.wait(lk, [&] {
-                return S->stop || !S->queue.empty() || !S->active.empty() || any_busy(S);
-            });
+            auto ready = [&] { return S->stop || !S->queue.empty() || !S->active.empty() || any_busy(S); };
+            if (!ready()) {
+                const uint64_t seen = S->submitted.load(std::memory_order_relaxed);
+                lk.unlock();
+                const auto t0 = Clock::now();
+                while (S->submitted.load(std::memory_order_acquire) == seen &&
+                       !S->stopping.load(std::memory_order_acquire) && Clock::now() - t0 < IDLE_SPIN)
+                    std::this_thread::yield();
+                lk.lock();
+            }
+            S->cv.wait(lk, ready);
             if (S->queue.empty() && S->active.empty() && !any_busy(S)) {
                 if (S->stop) break;
                 continue;
@@ -599,6 +614,7 @@ eecmg_status eecmg_server_submit(eecmg_server_t S, eecmg_plan_t P, const float* 
         S->queue.push_back(r);
         ++S->outstanding;
         *ticket = r->ticket;
+        S->submitted.fetch_add(1, std::memory_order_release);
     }
     S->cv.notify_one();
     return EECMG_OK;
@@ -630,6 +646,7 @@ eecmg_status eecmg_server_destroy(eecmg_server_t S) {
         std::unique_lock<std::mutex> lk(S->mu);
         S->cv_done.wait(lk, [&] { return S->outstanding == 0; });
         S->stop = true;
+        S->stopping.store(true, std::memory_order_release);
     }
     S->cv.notify_all();
     if (S->th.joinable()) S->th.join();
