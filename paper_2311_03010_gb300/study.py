@@ -16,8 +16,12 @@ m_l N_l / N_L) and the GPU time of one restoration:
   * eecmg-disc-uncapped  the discrepancy rule with caps of 1000 iterations;
   * iecmg-p / iecmg-l    Algorithm 1 (quadratic / linear prolongation), with
                  the discrepancy rule;
-  * mr2-disc     MR-II on the finest grid alone, from zero, stopped by the
-                 discrepancy rule (cap 1000);
+  * eecmg-disc-renorm  eecmg-disc with the coarse PSFs rescaled to the fine
+                 PSF's sum instead of the RMS-adjoint Galerkin operators;
+  * eecmg-disc-cgls    eecmg-disc with CGLS as the level smoother;
+  * mr2-disc / cgls-disc  MR-II or CGLS on the finest grid alone, from zero,
+                 stopped by the discrepancy rule (cap 1000: the standalone
+                 smoothers of Table 1);
   * mr2-same-work  MR-II on the finest grid alone with the work eecmg-disc
                  spent (rounded up to whole iterations).
 
@@ -58,7 +62,10 @@ def _variants(levels, delta):
         ("eecmg-disc-uncapped", levels, big, dict(stop="discrepancy", delta=delta)),
         ("iecmg-p", levels, None, dict(stop="discrepancy", delta=delta, prolong="iecmg_p")),
         ("iecmg-l", levels, None, dict(stop="discrepancy", delta=delta, prolong="iecmg_l")),
+        ("eecmg-disc-renorm", levels, None, dict(stop="discrepancy", delta=delta, coarse_op="renorm")),
+        ("eecmg-disc-cgls", levels, None, dict(stop="discrepancy", delta=delta, smoother="cgls")),
         ("mr2-disc", 1, [1000], dict(stop="discrepancy", delta=delta)),
+        ("cgls-disc", 1, [1000], dict(stop="discrepancy", delta=delta, smoother="cgls")),
     ]
 
 
@@ -102,7 +109,7 @@ def run(cases=None):
         pg = psnr(p.g, p.u)
         disc_work = None
         for (var, levels, iters, opts) in _variants(L, p.delta):
-            u, it, work, ms = restore(torch, eecmg, p.g, psf, levels, iters, dict(opts, smoother=smo))
+            u, it, work, ms = restore(torch, eecmg, p.g, psf, levels, iters, dict(dict(smoother=smo), **opts))
             if var == "eecmg-disc":
                 disc_work = work
             rows.append((name, var, pg, psnr(u, p.u), it, work, ms))
