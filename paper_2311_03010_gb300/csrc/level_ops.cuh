@@ -81,9 +81,10 @@ __device__ __forceinline__ float smooth_value_rd(Rd rd, int h, int w, float scal
             ts[k] = (float)t;
             vs[k] = v;
             W += wt;
-            sb = fmaf(wt, (float)s, sb);
-            tb = fmaf(wt, (float)t, tb);
-            vb = fmaf(wt, v, vb);
+            // a zero offset (or the centre's v = 0) adds exactly nothing: no FMA for it
+            if (s != 0) sb = fmaf(wt, (float)s, sb);
+            if (t != 0) tb = fmaf(wt, (float)t, tb);
+            if (!ctr) vb = fmaf(wt, v, vb);
         }
     }
     const float inv_w = 1.f / W;  // W >= 1: the centre always has weight 1
