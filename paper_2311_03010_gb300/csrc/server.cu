@@ -20,7 +20,8 @@
 // launched alone, so a served result is bitwise the result of eecmg_restore
 // on the request's plan.  Two ticks may be in flight; a request completes
 // with the tick that ran its finest level, and its latency runs from
-// submission to that tick's end event on the device clock.
+// submission to the end of its result's copy (right after the round of the
+// tick that ran that level) on the device clock.
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -71,13 +72,13 @@ size_t round256(size_t b) { return (b + 255) / 256 * 256; }
 // most 3 + MAX_DIFFUSION items (the start of its cascade step: zero start, or
 // the fused prolongation chain or prolongation, smoothing and the diffusion
 // steps) and one level-solve job of at most max(16, 3 x SMs) blocks, and one
-// item for the copy of its result; there are at most 4 + MAX_ROUNDS x (7 +
-// MAX_DIFFUSION) operation groups and one wave per job, each table rounded up
-// to 256 bytes.
+// item for the copy of its result; there are at most 4 + MAX_ROUNDS x (8 +
+// MAX_DIFFUSION) operation groups (a round's result copies are a group of their
+// own) and one wave per job, each table rounded up to 256 bytes.
 size_t tick_table_bound(int max_slots, int nsm) {
     const size_t slots = (size_t)max_slots;
     const size_t items = slots * (MAX_LEVELS + 2 + (size_t)MAX_ROUNDS * (3 + MAX_DIFFUSION));
-    const size_t groups = 4 + (size_t)MAX_ROUNDS * (7 + MAX_DIFFUSION);
+    const size_t groups = 4 + (size_t)MAX_ROUNDS * (8 + MAX_DIFFUSION);
     const size_t jobs = slots * MAX_ROUNDS;
     const size_t job_blocks = std::max<size_t>(16, 3 * (size_t)nsm);
     return items * sizeof(OpItem) + 256 * groups + jobs * (sizeof(LevelJob) + 256) +
@@ -138,6 +139,7 @@ struct Request {
     size_t off = 0, bytes = 0;
     int sidx = -1;      // status area
     int step = 0;       // next cascade step
+    int fin_round = 0;  // the round of its last tick that ran its finest level
 };
 
 struct Result {
@@ -159,6 +161,7 @@ struct eecmg_server_s {
     char* d_ring = nullptr;  // RING x ring_bytes, device
     char* h_ring = nullptr;  // RING x ring_bytes, pinned host
     cudaEvent_t ev[RING] = {};
+    cudaEvent_t rev[RING][MAX_ROUNDS] = {};  // end of each round's finishing requests' copies
     bool busy[RING] = {};
     std::vector<Request*> fin[RING];
     // per-slot status areas (pinned): every level's Scalars, then GroupSync
@@ -225,7 +228,11 @@ char* stat_area(eecmg_server_s* S, int sidx) { return S->h_stat + (size_t)sidx *
 eecmg_status enqueue_tick(eecmg_server_s* S, const std::vector<Request*>& admitted, int k,
                           std::vector<Request*>& finishing, std::vector<int>& advance) {
     cudaStream_t s = S->stream;
-    std::vector<OpGroup> pre, post;  // launch groups before the rounds / after them
+    std::vector<OpGroup> pre;  // launch groups before the rounds
+    // per round, the result copies of the requests whose finest level ran in it: they are
+    // launched right after that round, so a request's result does not wait for the rounds
+    // the tick runs after it for other requests' small levels
+    std::vector<std::vector<OpGroup>> rpost;
     // admissions: the data copied in, its pyramid restricted, scalars zeroed
     std::vector<eecmg_plan_s*> adm;
     for (Request* r : admitted) {
@@ -262,6 +269,7 @@ eecmg_status enqueue_tick(eecmg_server_s* S, const std::vector<Request*>& admitt
         items.reserve(cur.size());
         for (int i : cur) items.push_back({&S->active[i]->slot, S->active[i]->step + round});
         rops.emplace_back();
+        rpost.emplace_back();
         step_ops(items, rops.back());
         rwaves.emplace_back();
         eecmg_status e = plan_waves(items, rwaves.back());
@@ -279,7 +287,8 @@ eecmg_status enqueue_tick(eecmg_server_s* S, const std::vector<Request*>& admitt
                 c.out = r->u;
                 c.h = F.h;
                 c.w = F.w;
-                add_op(post, 0, OP_COPY, c);
+                add_op(rpost.back(), 0, OP_COPY, c);
+                r->fin_round = round;
                 finishing.push_back(r);
             } else if ((long long)P.lv[st + 1].h * P.lv[st + 1].w <= SMALL_LEVEL_PX) {
                 next.push_back(i);
@@ -293,7 +302,7 @@ eecmg_status enqueue_tick(eecmg_server_s* S, const std::vector<Request*>& admitt
         for (auto& g : gs) need += round256(sizeof(OpItem) * g.items.size());
     };
     groups_need(pre);
-    groups_need(post);
+    for (auto& rp : rpost) groups_need(rp);
     for (auto& ro : rops) groups_need(ro);
     for (auto& ws : rwaves)
         for (auto& w : ws)
@@ -326,10 +335,12 @@ eecmg_status enqueue_tick(eecmg_server_s* S, const std::vector<Request*>& admitt
         }
         return true;
     };
-    std::vector<Placed> pre_l, post_l;
+    std::vector<Placed> pre_l;
+    std::vector<std::vector<Placed>> rpost_l(rpost.size());
     std::vector<std::vector<Placed>> rops_l(rops.size());
     std::vector<std::vector<size_t>> jo(rwaves.size()), bo(rwaves.size());
-    bool fits = place_groups(pre, pre_l) && place_groups(post, post_l);
+    bool fits = place_groups(pre, pre_l);
+    for (size_t r = 0; r < rpost.size() && fits; ++r) fits = place_groups(rpost[r], rpost_l[r]);
     for (size_t r = 0; r < rops.size() && fits; ++r) fits = place_groups(rops[r], rops_l[r]);
     for (size_t r = 0; r < rwaves.size() && fits; ++r) {
         const auto& waves = rwaves[r];
@@ -354,15 +365,19 @@ eecmg_status enqueue_tick(eecmg_server_s* S, const std::vector<Request*>& admitt
                                    (int)W.jobs.size(), W.blocks, W.rt, W.sep, W.prec, W.cgls, W.bf16,
                                    W.cluster, W.resident, s));
         }
-    }
-    for (const Placed& p : post_l)
-        SCK(launch_ops_batch(p.op, (const OpItem*)(d + p.at), p.n, p.blocks, s));
-    for (Request* r : finishing) {
-        eecmg_plan_s& P = r->slot;
-        char* a = stat_area(S, r->sidx);
-        SCK(cudaMemcpyAsync(a, P.sc, sizeof(Scalars) * P.L, cudaMemcpyDeviceToHost, s));
-        SCK(cudaMemcpyAsync(a + sizeof(Scalars) * MAX_LEVELS, P.gsync, sizeof(GroupSync) * P.L,
-                            cudaMemcpyDeviceToHost, s));
+        bool any = false;
+        for (const Placed& p : rpost_l[r])
+            SCK(launch_ops_batch(p.op, (const OpItem*)(d + p.at), p.n, p.blocks, s));
+        for (Request* q : finishing) {
+            if (q->fin_round != (int)r) continue;
+            any = true;
+            eecmg_plan_s& P = q->slot;
+            char* a = stat_area(S, q->sidx);
+            SCK(cudaMemcpyAsync(a, P.sc, sizeof(Scalars) * P.L, cudaMemcpyDeviceToHost, s));
+            SCK(cudaMemcpyAsync(a + sizeof(Scalars) * MAX_LEVELS, P.gsync, sizeof(GroupSync) * P.L,
+                                cudaMemcpyDeviceToHost, s));
+        }
+        if (any) SCK(cudaEventRecord(S->rev[k][r], s));
     }
     SCK(cudaEventRecord(S->ev[k], s));
     return EECMG_OK;
@@ -382,17 +397,23 @@ eecmg_status request_status(eecmg_server_s* S, const Request* r) {
 
 // Waits for tick slot k and completes the requests that finished in it.
 void complete(eecmg_server_s* S, int k) {
-    cudaError_t e = cudaEventSynchronize(S->ev[k]);
-    float ms = 0.f;
-    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, S->base_ev, S->ev[k]);
-    const Clock::time_point t_done =
-        S->base_host + std::chrono::duration_cast<Clock::duration>(std::chrono::duration<double, std::milli>(ms));
+    const cudaError_t e = cudaEventSynchronize(S->ev[k]);
+    // a request's result is ready at the end of its round's copies
+    auto done_at = [&](const Request* r, cudaError_t* err) {
+        float ms = 0.f;
+        *err = cudaEventElapsedTime(&ms, S->base_ev, S->rev[k][r->fin_round]);
+        return S->base_host +
+               std::chrono::duration_cast<Clock::duration>(std::chrono::duration<double, std::milli>(ms));
+    };
     {
         std::lock_guard<std::mutex> lk(S->mu);
         for (Request* r : S->fin[k]) {
+            cudaError_t er = e;
+            Clock::time_point t_done = S->base_host;
+            if (er == cudaSuccess) t_done = done_at(r, &er);
             Result& res = S->results[r->ticket];
             res.done = 1;
-            res.st = e == cudaSuccess ? request_status(S, r) : EECMG_ERR_CUDA;
+            res.st = er == cudaSuccess ? request_status(S, r) : EECMG_ERR_CUDA;
             res.latency_ms = std::chrono::duration<double, std::milli>(t_done - r->t_submit).count();
             S->arena.release(r->off, r->bytes);
             S->free_sidx.push_back(r->sidx);
@@ -519,6 +540,9 @@ void free_server(eecmg_server_s* S) {
     if (S->stream) cudaStreamSynchronize(S->stream);
     for (int k = 0; k < RING; ++k)
         if (S->ev[k]) cudaEventDestroy(S->ev[k]);
+    for (int k = 0; k < RING; ++k)
+        for (int r = 0; r < MAX_ROUNDS; ++r)
+            if (S->rev[k][r]) cudaEventDestroy(S->rev[k][r]);
     if (S->base_ev) cudaEventDestroy(S->base_ev);
     if (S->stream) cudaStreamDestroy(S->stream);
     if (S->d_ring) cudaFree(S->d_ring);
@@ -564,6 +588,8 @@ eecmg_status eecmg_server_create(size_t mem_budget_bytes, int max_slots, eecmg_s
     if (e == cudaSuccess) e = cudaMallocHost((void**)&S->h_ring, RING * S->ring_bytes);
     if (e == cudaSuccess) e = cudaMallocHost((void**)&S->h_stat, S->stat_stride * max_slots);
     for (int k = 0; k < RING && e == cudaSuccess; ++k) e = cudaEventCreate(&S->ev[k]);
+    for (int k = 0; k < RING && e == cudaSuccess; ++k)
+        for (int r = 0; r < MAX_ROUNDS && e == cudaSuccess; ++r) e = cudaEventCreate(&S->rev[k][r]);
     if (e == cudaSuccess) e = cudaEventCreate(&S->base_ev);
     if (e == cudaSuccess) e = cudaEventRecord(S->base_ev, S->stream);
     if (e == cudaSuccess) e = cudaEventSynchronize(S->base_ev);
