@@ -140,6 +140,7 @@ struct Request {
     int sidx = -1;      // status area
     int step = 0;       // next cascade step
     int fin_round = 0;  // the round of its last tick that ran its finest level
+    bool direct = false;  // the finest level works in the caller's g and u (no copies)
 };
 
 struct Result {
@@ -215,6 +216,16 @@ void bind_slot(Request* r, char* ws) {
     S.max_blocks = T.max_blocks;
     S.owns_ws = false;
     bind_workspace(&S, ws);
+    // The finest level reads the caller's data and writes the caller's result in place (both
+    // stay valid until the request completes; the solver never writes g): no copy in, no
+    // copy out.  Overlapping buffers keep the workspace's own level and the two copies.
+    const uintptr_t g0 = reinterpret_cast<uintptr_t>(r->g), u0 = reinterpret_cast<uintptr_t>(r->u);
+    const uintptr_t nb = sizeof(float) * (uintptr_t)S.W * (uintptr_t)S.H;
+    r->direct = g0 + nb <= u0 || u0 + nb <= g0;
+    if (r->direct) {
+        S.lv[S.L - 1].g = const_cast<float*>(r->g);
+        S.lv[S.L - 1].u = r->u;
+    }
 }
 
 char* stat_area(eecmg_server_s* S, int sidx) { return S->h_stat + (size_t)sidx * S->stat_stride; }
@@ -240,12 +251,14 @@ eecmg_status enqueue_tick(eecmg_server_s* S, const std::vector<Request*>& admitt
         SCK(cudaMemcpyAsync(P.dtaps, r->tmpl->htaps.data(), sizeof(Taps) * 2 * P.L,
                             cudaMemcpyHostToDevice, s));
         LevelPlan& F = P.lv[P.L - 1];
-        OpItem in;
-        in.a = r->g;
-        in.out = F.g;
-        in.h = F.h;
-        in.w = F.w;
-        add_op(pre, 0, OP_COPY, in);
+        if (!r->direct) {
+            OpItem in;
+            in.a = r->g;
+            in.out = F.g;
+            in.h = F.h;
+            in.w = F.w;
+            add_op(pre, 0, OP_COPY, in);
+        }
         adm.push_back(&P);
     }
     restrict_ops(adm, pre);
@@ -281,13 +294,15 @@ eecmg_status enqueue_tick(eecmg_server_s* S, const std::vector<Request*>& admitt
             const int st = r->step + round;
             advance[i] += 1;
             if (st == P.L - 1) {
-                LevelPlan& F = P.lv[P.L - 1];
-                OpItem c;
-                c.a = F.u;
-                c.out = r->u;
-                c.h = F.h;
-                c.w = F.w;
-                add_op(rpost.back(), 0, OP_COPY, c);
+                if (!r->direct) {
+                    LevelPlan& F = P.lv[P.L - 1];
+                    OpItem c;
+                    c.a = F.u;
+                    c.out = r->u;
+                    c.h = F.h;
+                    c.w = F.w;
+                    add_op(rpost.back(), 0, OP_COPY, c);
+                }
                 r->fin_round = round;
                 finishing.push_back(r);
             } else if ((long long)P.lv[st + 1].h * P.lv[st + 1].w <= SMALL_LEVEL_PX) {

@@ -99,6 +99,31 @@ def test_served_results_equal_alone(gpu, orc):
         r[3].close()
 
 
+def test_served_in_place_and_aliased_buffers(gpu):
+    """The server solves a request's finest level in the caller's buffers when g and u are
+    disjoint, and through its own workspace and two copies when they overlap (u_out = g_delta,
+    as eecmg_restore allows): both give the plan's own result bitwise, mixed in one batch."""
+    torch, E = gpu
+    reqs = _setup(torch, E)
+    srv = E.Server(4 << 30, 8)
+    outs, tickets = [], []
+    for i, r in enumerate(reqs):
+        if i % 2:
+            buf = r[4].clone()  # aliased: the result overwrites the data in place
+            tickets.append(srv.submit(r[3], buf, buf))
+        else:
+            buf = torch.full_like(r[4], float("nan"))
+            tickets.append(srv.submit(r[3], r[4], buf))
+        outs.append(buf)
+    srv.drain()
+    for i, r in enumerate(reqs):
+        assert srv.poll(tickets[i])[0]
+        assert np.array_equal(host(outs[i]), r[5]), i
+    srv.close()
+    for r in reqs:
+        r[3].close()
+
+
 def test_memory_admission_and_single_slot(gpu):
     """A budget that holds one request at a time, or one slot, still serves all."""
     torch, E = gpu
