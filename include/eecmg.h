@@ -249,8 +249,14 @@ eecmg_status eecmg_restore_batched_host_async(const eecmg_plan_t *plans, const f
  * the persistent level solve and not be profiling.  The first call with a
  * given set of plans builds device job tables and a CUDA graph for it (an
  * allocation; make it before any stream capture); later calls replay it.
- * Destroying any of the plans drops the cached batch.  Asynchronous on
- * `stream`.  Errors: INVALID_ARG, OOM, CUDA.
+ * Destroying any of the plans drops the cached batch.  Image i's finest
+ * level is solved in g[i] and u[i] themselves (g is only read) when u[i]
+ * overlaps no g[j] and no other u[j]; otherwise g[i] is copied into the
+ * plan's workspace first and the result copied out after the batch, so
+ * u[i] may alias g[i] or another image's input.  When the buffers differ
+ * from the previous call's, the job tables are rebound (a small upload on
+ * `stream` ahead of the batch).  Asynchronous on `stream`.  Errors:
+ * INVALID_ARG, OOM, CUDA.
  */
 eecmg_status eecmg_restore_batched(const eecmg_plan_t *plans, const float *const *g,
                                    float *const *u, int n, cudaStream_t stream);

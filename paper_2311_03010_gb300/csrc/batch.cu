@@ -15,6 +15,8 @@
 // The whole batch is captured once as a CUDA graph per set of plans and
 // replayed; inputs are copied into the plans' workspaces outside the graph.
 #include <algorithm>
+#include <cstddef>
+#include <cstring>
 #include <cstdint>
 #include <map>
 #include <memory>
@@ -279,6 +281,22 @@ struct BatchCtx {
     // cascade step timed_step (-1: none).
     int timed_step = -1;
     cudaEvent_t tev[2] = {nullptr, nullptr};
+    // Image binding: the finest level of plan i reads bound_g[i] and writes bound_u[i] (its
+    // workspace's own buffers, or the caller's).  sites: where the tables hold those two
+    // pointers (byte offset of the 8-byte field in the table image, found at build time,
+    // when every such field still holds its plan's own workspace buffer).  h_img: a pinned
+    // copy of the table image, patched and uploaded when a binding changes.
+    struct Site {
+        size_t off;
+        int plan;
+        bool isu;
+    };
+    std::vector<Site> sites;
+    std::vector<const float*> bound_g;
+    std::vector<float*> bound_u;
+    char* h_img = nullptr;
+    size_t img_bytes = 0;
+    cudaEvent_t ev_up = nullptr;
     ~BatchCtx() {
         if (gexec) cudaGraphExecDestroy(gexec);
         if (cap_stream) cudaStreamDestroy(cap_stream);
@@ -288,6 +306,8 @@ struct BatchCtx {
         for (cudaEvent_t e : tev)
             if (e) cudaEventDestroy(e);
         if (dmem) cudaFree(dmem);
+        if (h_img) cudaFreeHost(h_img);
+        if (ev_up) cudaEventDestroy(ev_up);
     }
 };
 
@@ -337,9 +357,29 @@ eecmg_status build_ctx(BatchCtx& C) {
             bytes += (sizeof(LevelJob) * w.jobs.size() + 255) / 256 * 256;
             bytes += (sizeof(unsigned short) * w.block_job.size() + 255) / 256 * 256;
         }
-    cudaError_t e = cudaMalloc(&C.dmem, bytes ? bytes : 256);
+    const size_t img = bytes ? bytes : 256;
+    cudaError_t e = cudaMalloc(&C.dmem, img);
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&C.h_img, img);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&C.ev_up, cudaEventDisableTiming);
     if (e != cudaSuccess) return set_error(EECMG_ERR_OOM, "eecmg_restore_batched: job tables");
+    C.img_bytes = img;
+    std::memset(C.h_img, 0, img);
     char* p = (char*)C.dmem;
+    const size_t np = C.plans.size();
+    C.bound_g.resize(np);
+    C.bound_u.resize(np);
+    for (size_t i = 0; i < np; ++i) {
+        const LevelPlan& F = C.plans[i]->lv[C.plans[i]->L - 1];
+        C.bound_g[i] = F.g;
+        C.bound_u[i] = F.u;
+    }
+    // a pointer field at image offset off that holds some plan's finest g or u is a site
+    auto note = [&](size_t off, const void* v) {
+        for (size_t i = 0; i < np; ++i) {
+            if (v == C.bound_g[i]) C.sites.push_back({off, (int)i, false});
+            if (v == C.bound_u[i]) C.sites.push_back({off, (int)i, true});
+        }
+    };
     auto upload_groups = [&](std::vector<OpGroup>& gs, std::vector<OpLaunch>& out) -> cudaError_t {
         for (auto& g : gs) {
             if (g.items.empty() || g.op < 0) continue;
@@ -348,9 +388,14 @@ eecmg_status build_ctx(BatchCtx& C) {
             L.blocks = place_items(g);
             L.n = (int)g.items.size();
             L.d_items = (const OpItem*)p;
-            cudaError_t err = cudaMemcpy(p, g.items.data(), sizeof(OpItem) * g.items.size(),
-                                         cudaMemcpyHostToDevice);
-            if (err != cudaSuccess) return err;
+            const size_t base = (size_t)(p - (char*)C.dmem);
+            std::memcpy(C.h_img + base, g.items.data(), sizeof(OpItem) * g.items.size());
+            for (size_t k = 0; k < g.items.size(); ++k) {
+                const size_t o = base + k * sizeof(OpItem);
+                note(o + offsetof(OpItem, a), g.items[k].a);
+                note(o + offsetof(OpItem, b), g.items[k].b);
+                note(o + offsetof(OpItem, out), g.items[k].out);
+            }
             p += (sizeof(OpItem) * g.items.size() + 255) / 256 * 256;
             out.push_back(L);
         }
@@ -359,20 +404,25 @@ eecmg_status build_ctx(BatchCtx& C) {
     e = upload_groups(rgroups, C.restrict_ops);
     C.step_ops.assign(maxL, {});
     for (int s = 0; s < maxL && e == cudaSuccess; ++s) e = upload_groups(sgroups[s], C.step_ops[s]);
-    if (e != cudaSuccess) return set_error(EECMG_ERR_CUDA, "eecmg_restore_batched: op upload");
     C.steps.assign(maxL, {});
     for (int s = 0; s < maxL; ++s)
         for (auto& w : hsteps[s]) {
             Wave dw;
             dw.d_jobs = (const LevelJob*)p;
-            e = cudaMemcpy(p, w.jobs.data(), sizeof(LevelJob) * w.jobs.size(), cudaMemcpyHostToDevice);
+            size_t base = (size_t)(p - (char*)C.dmem);
+            std::memcpy(C.h_img + base, w.jobs.data(), sizeof(LevelJob) * w.jobs.size());
+            for (size_t k = 0; k < w.jobs.size(); ++k) {
+                const size_t o = base + k * sizeof(LevelJob);
+                note(o + offsetof(LevelJob, g), w.jobs[k].g);
+                note(o + offsetof(LevelJob, u), w.jobs[k].u);
+                note(o + offsetof(LevelJob, s_u1), w.jobs[k].s_u1);
+                note(o + offsetof(LevelJob, s_u2), w.jobs[k].s_u2);
+            }
             p += (sizeof(LevelJob) * w.jobs.size() + 255) / 256 * 256;
             dw.d_block_job = (const unsigned short*)p;
-            if (e == cudaSuccess)
-                e = cudaMemcpy(p, w.block_job.data(), sizeof(unsigned short) * w.block_job.size(),
-                               cudaMemcpyHostToDevice);
+            base = (size_t)(p - (char*)C.dmem);
+            std::memcpy(C.h_img + base, w.block_job.data(), sizeof(unsigned short) * w.block_job.size());
             p += (sizeof(unsigned short) * w.block_job.size() + 255) / 256 * 256;
-            if (e != cudaSuccess) return set_error(EECMG_ERR_CUDA, "eecmg_restore_batched: job upload");
             dw.njobs = (int)w.jobs.size();
             dw.blocks = w.blocks;
             dw.rt = w.rt;
@@ -384,6 +434,8 @@ eecmg_status build_ctx(BatchCtx& C) {
             dw.resident = w.resident;
             C.steps[s].push_back(dw);
         }
+    e = cudaMemcpy(C.dmem, C.h_img, img, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return set_error(EECMG_ERR_CUDA, "eecmg_restore_batched: table upload");
     e = cudaStreamCreateWithFlags(&C.cap_stream, cudaStreamNonBlocking);
     if (e != cudaSuccess) return set_error(EECMG_ERR_CUDA, "eecmg_restore_batched: stream");
     C.fork01 = maxL >= 2;
@@ -477,11 +529,43 @@ eecmg_status restore_batched_impl(const eecmg_plan_t* plans, const float* const*
     }
     touch_batch(key);
     BatchCtx& C = *it->second;
+    // Each finest level works in the caller's g and u directly when its u overlaps no image's
+    // g and no other image's u (the solvers never write g); otherwise it goes through the
+    // workspace's own level buffers, with a copy in and a copy out.
+    std::vector<char> inplace(n);
+    auto span = [&](const void* ptr, int i) {
+        const uintptr_t a0 = reinterpret_cast<uintptr_t>(ptr);
+        return std::make_pair(a0, a0 + sizeof(float) * (uintptr_t)plans[i]->W * (uintptr_t)plans[i]->H);
+    };
+    auto overlap = [](std::pair<uintptr_t, uintptr_t> x, std::pair<uintptr_t, uintptr_t> y) {
+        return x.first < y.second && y.first < x.second;
+    };
+    for (int i = 0; i < n; ++i) {
+        bool ok = true;
+        for (int j = 0; j < n && ok; ++j)
+            ok = !overlap(span(u[i], i), span(g[j], j)) && (j == i || !overlap(span(u[i], i), span(u[j], j)));
+        inplace[i] = ok;
+    }
+    bool rebind = false;
     for (int i = 0; i < n; ++i) {
         eecmg_plan_s* P = plans[i];
         LevelPlan& F = P->lv[P->L - 1];
-        if (g[i] != F.g)
+        const float* bg = inplace[i] ? g[i] : F.g;
+        float* bu = inplace[i] ? u[i] : F.u;
+        if (bg != C.bound_g[i] || bu != C.bound_u[i]) rebind = true;
+        C.bound_g[i] = bg;
+        C.bound_u[i] = bu;
+        if (!inplace[i])
             BCK(cudaMemcpyAsync(F.g, g[i], sizeof(float) * P->W * P->H, cudaMemcpyDeviceToDevice, s));
+    }
+    if (rebind) {  // patch the pointer sites and upload the tables ahead of this launch
+        BCK(cudaEventSynchronize(C.ev_up));  // the previous upload has read the pinned image
+        for (const BatchCtx::Site& st : C.sites) {
+            const void* v = st.isu ? (const void*)C.bound_u[st.plan] : (const void*)C.bound_g[st.plan];
+            std::memcpy(C.h_img + st.off, &v, sizeof(v));
+        }
+        BCK(cudaMemcpyAsync(C.dmem, C.h_img, C.img_bytes, cudaMemcpyHostToDevice, s));
+        BCK(cudaEventRecord(C.ev_up, s));
     }
     if (!C.gexec) {
         BCK(cudaStreamBeginCapture(C.cap_stream, cudaStreamCaptureModeThreadLocal));
@@ -516,7 +600,7 @@ eecmg_status restore_batched_impl(const eecmg_plan_t* plans, const float* const*
     for (int i = 0; i < n; ++i) {
         eecmg_plan_s* P = plans[i];
         LevelPlan& F = P->lv[P->L - 1];
-        if (u[i] != F.u)
+        if (!inplace[i] && u[i] != F.u)
             BCK(cudaMemcpyAsync(u[i], F.u, sizeof(float) * P->W * P->H, cudaMemcpyDeviceToDevice, s));
         P->last_stream = s;
     }

@@ -519,6 +519,48 @@ def test_batched_is_bitwise_the_single_result(gpu, orc):
         pl.close()
 
 
+def test_batched_in_place_rebinding_and_aliasing(gpu):
+    """eecmg_restore_batched solves each finest level in the caller's buffers: across calls
+    that change the buffers (the job tables are rebound), with an image restored in place
+    (u = g) and an output that is another image's input (the copy-through fallback keeps
+    every input intact until it is read), every result is bitwise the image's own."""
+    torch, E = gpu
+    cases = _batch_cases()[:4]
+    plans, gs, singles = [], [], []
+    for (p, L, smo) in cases:
+        h, w = p.g.shape
+        pl = E.Plan(w, h, L, p.psf, smoother=smo, delta=p.delta)
+        gd = dev(torch, p.g)
+        ud = torch.empty_like(gd)
+        pl.restore(gd, ud)
+        singles.append(host(ud))
+        plans.append(pl)
+        gs.append(gd)
+    hs = [pl.handle for pl in plans]
+    for rep in range(3):  # fresh output buffers every call: the tables are rebound each time
+        us = [torch.full_like(g, float("nan")) for g in gs]
+        E.eecmg_restore_batched(hs, gs, us)
+        for k, u in enumerate(us):
+            assert np.array_equal(singles[k], host(u)), (rep, k)
+    # image 0 in place (u = g); image 1 writes its result over image 2's input
+    g0 = gs[0].clone()
+    g2 = gs[2].clone()
+    assert gs[1].numel() <= g2.numel()
+    out1 = g2.view(-1)[: gs[1].numel()].view(gs[1].shape)  # the head of image 2's input
+    ins = [g0, gs[1], g2, gs[3]]
+    outs = [g0, out1, torch.empty_like(gs[2]), torch.empty_like(gs[3])]
+    E.eecmg_restore_batched(hs, ins, outs)
+    for k, u in enumerate(outs):
+        assert np.array_equal(singles[k], host(u)), k
+    # and back to the plain binding
+    us = [torch.empty_like(g) for g in gs]
+    E.eecmg_restore_batched(hs, gs, us)
+    for k, u in enumerate(us):
+        assert np.array_equal(singles[k], host(u)), ("after", k)
+    for pl in plans:
+        pl.close()
+
+
 def test_batched_host_entry_point_equals_device(gpu):
     """eecmg_restore_batched_host (pinned host buffers, one sync) gives the device results."""
     torch, E = gpu
