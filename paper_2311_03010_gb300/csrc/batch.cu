@@ -13,7 +13,9 @@
 // restriction and the prolongation chain run before each step as one launch
 // per kind of operation over all images (k_ops_batch).
 // The whole batch is captured once as a CUDA graph per set of plans and
-// replayed; inputs are copied into the plans' workspaces outside the graph.
+// replayed.  The graph's kernels read their buffers from device job tables, so
+// each image's finest level runs in the caller's g and u: the table fields that
+// name them are rebound when the caller's buffers change (see BatchCtx).
 #include <algorithm>
 #include <cstddef>
 #include <cstring>
