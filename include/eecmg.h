@@ -423,17 +423,22 @@ eecmg_status eecmg_residual_noalloc(int width, int height, const double *psf, in
  * up to 16 blocks that exchange their sums through distributed shared memory
  * and stream the vectors through L2; larger levels run as a cooperative grid
  * of max(32x64 tiles, pixels / px_per_block) blocks, at most blocks_per_sm
- * per SM.  Process-wide.  Initial values: the GB300 optimum of measured
- * sweeps (resident_max_tiles 32, cluster_max_px 16384, px_per_block 2048,
- * blocks_per_sm 2), overridable by the environment variables
- * EECMG_RESIDENT_MAX_TILES, EECMG_CLUSTER_MAX_PX, EECMG_PX_PER_BLOCK,
- * EECMG_BLOCKS_PER_SM read at first use.
+ * per SM.  The fused start of a prolonged level runs on tiles of psd_tile_h
+ * x 64 pixels (16 rows give small levels more blocks; its result does not
+ * depend on the tile).  Process-wide.  Initial values: the GB300 optimum of
+ * measured sweeps (resident_max_tiles 32, cluster_max_px 16384, px_per_block
+ * 2048, blocks_per_sm 2, psd_tile_h 32), overridable by the environment
+ * variables EECMG_RESIDENT_MAX_TILES, EECMG_CLUSTER_MAX_PX,
+ * EECMG_PX_PER_BLOCK, EECMG_BLOCKS_PER_SM, EECMG_PSD_TILE_H read at first
+ * use.
  */
 typedef struct {
     long long cluster_max_px; /* >= 0; 0 = never cluster mode                 */
     int px_per_block;         /* 1024 .. 4194304                              */
     int blocks_per_sm;        /* 1 .. 3                                       */
     int resident_max_tiles;   /* 0 .. 32; 0 = never shared-memory resident     */
+    int psd_tile_h;           /* 16 or 32: rows of the fused level start's
+                                 64-column tiles (Algorithm 2, Step 2)        */
 } eecmg_tuning;
 
 eecmg_status eecmg_get_tuning(eecmg_tuning *out);

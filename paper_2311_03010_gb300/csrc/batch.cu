@@ -116,6 +116,7 @@ void add_op(std::vector<OpGroup>& groups, size_t gi, int op, OpItem it) {
     if (groups.size() <= gi) groups.resize(gi + 1);
     groups[gi].op = op;
     it.bx = op_blocks_x(op, it.w);
+    if (op == OP_PSD) it.th = psd_tile_rows();
     groups[gi].items.push_back(it);
 }
 

@@ -94,8 +94,10 @@ struct OpItem {
     int h = 0, w = 0, h1 = 0, w1 = 0, h2 = 0, w2 = 0;
     float p0 = 0.f, p1 = 0.f, s0 = 0.f;
     int bx = 0, block0 = 0;
+    int th = 0;  // OP_PSD: rows of the item's tiles
 };
 int op_blocks(int op, int h, int w);  // blocks of operation kind op covering an h x w output
+int psd_tile_rows();                  // rows of the fused level start's tiles (process-wide tuning)
 int op_blocks_x(int op, int w);       // of which along x
 cudaError_t launch_ops_batch(int op, const OpItem* d_items, int n, int total_blocks, cudaStream_t s);
 

@@ -196,11 +196,14 @@ __global__ void __launch_bounds__(BX* BY) k_denoise(const float* __restrict__ in
 __global__ void __launch_bounds__(BX* BY) k_psd(const float* __restrict__ u1, int h1, int w1,
                                                const float* __restrict__ u2, int h2, int w2,
                                                float* __restrict__ out, int h, int w, float scale,
-                                               float tau, float inv_k2) {
+                                               float tau, float inv_k2, int th) {
     __shared__ PsdSmem M;
-    const int y0 = blockIdx.y * PSD_TH, x0 = blockIdx.x * PSD_TW;
-    tile_psd(M, u1, h1, w1, u2, h2, w2, h, w, scale, tau, inv_k2, y0, x0,
-             [&](int rr, int cc, float v) { out[(size_t)(y0 + rr) * w + x0 + cc] = v; });
+    const int y0 = blockIdx.y * th, x0 = blockIdx.x * PSD_TW;
+    auto store = [&](int rr, int cc, float v) { out[(size_t)(y0 + rr) * w + x0 + cc] = v; };
+    if (th == 16)
+        tile_psd<16>(M, u1, h1, w1, u2, h2, w2, h, w, scale, tau, inv_k2, y0, x0, store);
+    else
+        tile_psd<PSD_TH>(M, u1, h1, w1, u2, h2, w2, h, w, scale, tau, inv_k2, y0, x0, store);
 }
 
 // Many operations of one kind in one launch (the server's ticks): block b
@@ -229,12 +232,16 @@ __global__ void __launch_bounds__(BX* BY) k_ops_batch(const OpItem* __restrict__
         tile_prolong(it.a, it.h1, it.w1, it.b, it.h2, it.w2, it.out, it.h, it.w, by * BY, bx * BX);
     if constexpr (OP == OP_PSD) {
         __shared__ PsdSmem M;
-        // this block's tile of the 32 x 64 grid (bx counts PSD_TW-wide tiles)
-        const int y0 = by * PSD_TH, x0 = bx * PSD_TW;
+        // this block's tile of the th x 64 grid (bx counts PSD_TW-wide tiles)
+        const int y0 = by * it.th, x0 = bx * PSD_TW;
         float* out = it.out;
         const int w = it.w;
-        tile_psd(M, it.a, it.h1, it.w1, it.b, it.h2, it.w2, it.h, it.w, it.s0, it.p0, it.p1, y0, x0,
-                 [&](int rr, int cc, float v) { out[(size_t)(y0 + rr) * w + x0 + cc] = v; });
+        auto store = [&](int rr, int cc, float v) { out[(size_t)(y0 + rr) * w + x0 + cc] = v; };
+        if (it.th == 16)
+            tile_psd<16>(M, it.a, it.h1, it.w1, it.b, it.h2, it.w2, it.h, it.w, it.s0, it.p0, it.p1, y0, x0, store);
+        else
+            tile_psd<PSD_TH>(M, it.a, it.h1, it.w1, it.b, it.h2, it.w2, it.h, it.w, it.s0, it.p0, it.p1, y0, x0,
+                             store);
     }
     if constexpr (OP == OP_ZERO || OP == OP_COPY) {
         if (y < it.h && x < it.w) it.out[(size_t)y * it.w + x] = OP == OP_ZERO ? 0.f : it.a[(size_t)y * it.w + x];
@@ -274,8 +281,9 @@ cudaError_t launch_prolong(const float* u1, int h1, int w1, const float* u2, int
 cudaError_t launch_psd(const float* u1, int h1, int w1, const float* u2, int h2, int w2, float* out,
                        int h, int w, float scale, float tau, float kpm, cudaStream_t s) {
     if (h <= 0 || w <= 0) return cudaSuccess;
-    const dim3 grid((w + PSD_TW - 1) / PSD_TW, (h + PSD_TH - 1) / PSD_TH);
-    k_psd<<<grid, dim3(BX, BY), 0, s>>>(u1, h1, w1, u2, h2, w2, out, h, w, scale, tau, 1.f / (kpm * kpm));
+    const int th = psd_tile_rows();
+    const dim3 grid((w + PSD_TW - 1) / PSD_TW, (h + th - 1) / th);
+    k_psd<<<grid, dim3(BX, BY), 0, s>>>(u1, h1, w1, u2, h2, w2, out, h, w, scale, tau, 1.f / (kpm * kpm), th);
     return cudaGetLastError();
 }
 
@@ -308,7 +316,7 @@ cudaError_t launch_denoise(const float* in, float* out, int h, int w, float tau,
 
 int op_blocks(int op, int h, int w) {
     if (h <= 0 || w <= 0) return 0;
-    if (op == OP_PSD) return ((w + PSD_TW - 1) / PSD_TW) * ((h + PSD_TH - 1) / PSD_TH);
+    if (op == OP_PSD) return ((w + PSD_TW - 1) / PSD_TW) * ((h + psd_tile_rows() - 1) / psd_tile_rows());
     const dim3 g = grid2(h, w);
     return (int)(g.x * g.y);
 }

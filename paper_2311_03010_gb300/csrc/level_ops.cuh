@@ -163,13 +163,14 @@ __device__ __forceinline__ float denoise_value_rd(Ud in, Cd c, int h, int w, flo
     return fmaf(tau, f, uc);
 }
 // The start of a prolonged level (Algorithm 2, Step 2) in one pass: D(S(P(Pi(u1, u2)))) for
-// one PSD_TH x PSD_TW block of fine pixels at (y0, x0).  D needs S's output with a 2-pixel halo
+// one TH x PSD_TW block of fine pixels at (y0, x0), TH <= PSD_TH (the shared-memory stages are
+// sized for PSD_TH rows; a block's result does not depend on TH).  D needs S's output with a 2-pixel halo
 // (its own 4 neighbours and their diffusivities), S needs P's with a 1-pixel halo beyond that,
 // and P the level-(l-1) window of Pi values its triplets read; each stage is computed for its
 // whole region into shared memory (pixels outside the image are never read), with the
 // per-pixel arithmetic of k_prolong, k_smooth and k_denoise, so the result equals those three
 // kernels in sequence bitwise, while the two intermediate images never leave the SM.  Halo
-// work: P on 1.30x, S on 1.20x, c on 1.10x the block's pixels.  Called by every thread of a
+// work at TH = 32: P on 1.30x, S on 1.20x, c on 1.10x the block's pixels.  Called by every thread of a
 // 256-thread block; store(rr, cc, v) receives the block's in-image outputs (row rr, column cc of
 // the tile).
 constexpr int PSD_TH = 32, PSD_TW = 64, PSD_THREADS = 256;
@@ -188,16 +189,18 @@ struct PsdSmem {
     float S[PSD_SH][PSD_SW];
     float C[PSD_CH][PSD_CW];
 };
-template <class Store>
+template <int TH = PSD_TH, class Store>
 __device__ __forceinline__ void tile_psd(PsdSmem& M, const float* __restrict__ u1, int h1, int w1,
                                          const float* __restrict__ u2, int h2, int w2, int h, int w,
                                          float scale, float tau, float inv_k2, int y0, int x0,
                                          Store&& store) {
+    static_assert(TH >= 1 && TH <= PSD_TH, "the stages are sized for PSD_TH rows");
+    constexpr int th = TH;
     const int tid = threadIdx.y * blockDim.x + threadIdx.x;
     constexpr int NT = PSD_THREADS;
     // fine region of P (clipped to the image) and its Pi window
     const int py0 = max(y0 - 3, 0), px0 = max(x0 - 3, 0);
-    const int py1 = min(y0 + PSD_TH + 3, h), px1 = min(x0 + PSD_TW + 3, w);  // exclusive
+    const int py1 = min(y0 + th + 3, h), px1 = min(x0 + PSD_TW + 3, w);  // exclusive
     const int r0 = 2 * (py0 >> 2), c0 = 2 * (px0 >> 2);
     const int nr = 2 * (((py1 - 1) >> 2) - (py0 >> 2)) + 3;
     const int nc = 2 * (((px1 - 1) >> 2) - (px0 >> 2)) + 3;
@@ -225,7 +228,7 @@ __device__ __forceinline__ void tile_psd(PsdSmem& M, const float* __restrict__ u
     }
     __syncthreads();
     // P on rows y0-3 .. y0+TH+2 and columns x0-3 .. x0+TW+2 (in-image part)
-    for (int k = tid; k < PSD_PH * PSD_PW; k += NT) {
+    for (int k = tid; k < (th + 6) * PSD_PW; k += NT) {
         const int rr = k / PSD_PW, cc = k - rr * PSD_PW;
         const int y = y0 - 3 + rr, x = x0 - 3 + cc;
         float acc = 0.f;
@@ -246,14 +249,14 @@ __device__ __forceinline__ void tile_psd(PsdSmem& M, const float* __restrict__ u
     __syncthreads();
     auto pr = [&](int a, int b) { return M.P[a - y0 + 3][b - x0 + 3]; };
     // a block whose P region lies inside the image needs no bounds tests in S (most blocks)
-    const bool interior = y0 >= 3 && x0 >= 3 && y0 + PSD_TH + 3 <= h && x0 + PSD_TW + 3 <= w;
+    const bool interior = y0 >= 3 && x0 >= 3 && y0 + th + 3 <= h && x0 + PSD_TW + 3 <= w;
     if (interior) {
-        for (int k = tid; k < PSD_SH * PSD_SW; k += NT) {
+        for (int k = tid; k < (th + 4) * PSD_SW; k += NT) {
             const int rr = k / PSD_SW, cc = k - rr * PSD_SW;
             M.S[rr][cc] = smooth_value_rd<false>(pr, h, w, scale, y0 - 2 + rr, x0 - 2 + cc);
         }
     } else {
-        for (int k = tid; k < PSD_SH * PSD_SW; k += NT) {
+        for (int k = tid; k < (th + 4) * PSD_SW; k += NT) {
             const int rr = k / PSD_SW, cc = k - rr * PSD_SW;
             const int y = y0 - 2 + rr, x = x0 - 2 + cc;
             M.S[rr][cc] = (y >= 0 && y < h && x >= 0 && x < w) ? smooth_value_rd(pr, h, w, scale, y, x) : 0.f;
@@ -261,14 +264,14 @@ __device__ __forceinline__ void tile_psd(PsdSmem& M, const float* __restrict__ u
     }
     __syncthreads();
     auto sr = [&](int a, int b) { return M.S[a - y0 + 2][b - x0 + 2]; };
-    for (int k = tid; k < PSD_CH * PSD_CW; k += NT) {
+    for (int k = tid; k < (th + 2) * PSD_CW; k += NT) {
         const int rr = k / PSD_CW, cc = k - rr * PSD_CW;
         const int y = y0 - 1 + rr, x = x0 - 1 + cc;
         M.C[rr][cc] = (y >= 0 && y < h && x >= 0 && x < w) ? pm_c_rd(sr, h, w, y, x, inv_k2) : 0.f;
     }
     __syncthreads();
     auto cr = [&](int a, int b) { return M.C[a - y0 + 1][b - x0 + 1]; };
-    for (int k = tid; k < PSD_TH * PSD_TW; k += NT) {
+    for (int k = tid; k < th * PSD_TW; k += NT) {
         const int rr = k / PSD_TW, cc = k - rr * PSD_TW;
         const int y = y0 + rr, x = x0 + cc;
         if (y < h && x < w) store(rr, cc, denoise_value_rd(sr, cr, h, w, tau, y, x));

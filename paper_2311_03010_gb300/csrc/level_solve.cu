@@ -78,7 +78,7 @@ int resident_cluster_limit(int T) {
 
 namespace {
 
-std::atomic<int> g_px_per_block{0}, g_blocks_per_sm{0}, g_resident_max_tiles{0};
+std::atomic<int> g_px_per_block{0}, g_blocks_per_sm{0}, g_resident_max_tiles{0}, g_psd_tile_h{32};
 std::atomic<long long> g_cluster_max_px{-1};
 
 void tuning_init() {
@@ -87,11 +87,13 @@ void tuning_init() {
     const char* b = std::getenv("EECMG_CLUSTER_MAX_PX");
     const char* c = std::getenv("EECMG_BLOCKS_PER_SM");
     const char* d = std::getenv("EECMG_RESIDENT_MAX_TILES");
+    const char* e = std::getenv("EECMG_PSD_TILE_H");
     Tuning t;
     if (a) t.px_per_block = std::atoi(a);
     if (b) t.cluster_max_px = std::atoll(b);
     if (c) t.blocks_per_sm = std::atoi(c);
     if (d) t.resident_max_tiles = std::atoi(d);
+    if (e) t.psd_tile_h = std::atoi(e);
     set_tuning_raw(t);
 }
 
@@ -100,7 +102,7 @@ void tuning_init() {
 bool tuning_valid(const Tuning& t) {
     return t.px_per_block >= 1024 && t.px_per_block <= (1 << 22) && t.cluster_max_px >= 0 &&
            t.blocks_per_sm >= 1 && t.blocks_per_sm <= 3 && t.resident_max_tiles >= 0 &&
-           t.resident_max_tiles <= CLUSTER_MAX * RES_TMAX;
+           t.resident_max_tiles <= CLUSTER_MAX * RES_TMAX && (t.psd_tile_h == 16 || t.psd_tile_h == 32);
 }
 
 void set_tuning_raw(const Tuning& t0) {
@@ -112,6 +114,7 @@ void set_tuning_raw(const Tuning& t0) {
     const int rmt = CLUSTER_MAX * RES_TMAX;
     t.resident_max_tiles = t.resident_max_tiles < 0 ? 0 : (t.resident_max_tiles > rmt ? rmt : t.resident_max_tiles);
     g_resident_max_tiles.store(t.resident_max_tiles);
+    g_psd_tile_h.store(t.psd_tile_h == 16 ? 16 : 32);
     g_cluster_max_px.store(t.cluster_max_px);
     g_blocks_per_sm.store(t.blocks_per_sm);
     g_px_per_block.store(t.px_per_block);
@@ -124,8 +127,11 @@ Tuning get_tuning() {
     t.cluster_max_px = g_cluster_max_px.load();
     t.blocks_per_sm = g_blocks_per_sm.load();
     t.resident_max_tiles = g_resident_max_tiles.load();
+    t.psd_tile_h = g_psd_tile_h.load();
     return t;
 }
+
+int psd_tile_rows() { return get_tuning().psd_tile_h; }
 
 // Blocks of a grid-mode level solve: the larger of the 32 x 64 tile count and
 // pixels / px_per_block, at most blocks_per_sm per SM (the MR-II solvers fit

@@ -79,6 +79,7 @@ struct Tuning {
     int blocks_per_sm = 2;             // grid mode: at most this many blocks per SM (1..3)
     int resident_max_tiles = 32;       // FP32 levels of at most this many 32 x 64 tiles
                                        // run shared-memory resident (0 = never, <= 32)
+    int psd_tile_h = 32;               // rows of the fused level start's 64-column tiles (16, 32)
 };
 Tuning get_tuning();
 void set_tuning_raw(const Tuning& t);  // no liveness check (see eecmg_set_tuning)

@@ -25,6 +25,7 @@ eecmg_tuning to_c(const Tuning& t) {
     c.px_per_block = t.px_per_block;
     c.blocks_per_sm = t.blocks_per_sm;
     c.resident_max_tiles = t.resident_max_tiles;
+    c.psd_tile_h = t.psd_tile_h;
     return c;
 }
 
@@ -34,6 +35,7 @@ Tuning from_c(const eecmg_tuning& c) {
     t.px_per_block = c.px_per_block;
     t.blocks_per_sm = c.blocks_per_sm;
     t.resident_max_tiles = c.resident_max_tiles;
+    t.psd_tile_h = c.psd_tile_h;
     return t;
 }
 
@@ -135,13 +137,14 @@ eecmg_status eecmg_autotune(const eecmg_plan_t* plans, const float* const* g, in
         float best_ms = 0.f;
         if (st == EECMG_OK) st = time_tuning(R, g, reps, s, cur, &best_ms);
         // coordinate search: resident threshold, cluster threshold, pixels per
-        // block, then blocks per SM
+        // block, blocks per SM, then the rows of the fused level start's tiles
         const int rmt[] = {0, 16, 32};
         const long long cmax[] = {0, 4096, 16384, 65536, 262144};
         const int ppb[] = {1024, 2048, 4096};
         const int bps[] = {1, 2, 3};
-        for (int axis = 0; axis < 4 && st == EECMG_OK; ++axis) {
-            const int nc = axis == 1 ? 5 : 3;  // rmt, ppb and bps have 3 candidates
+        const int pth[] = {16, 32};
+        for (int axis = 0; axis < 5 && st == EECMG_OK; ++axis) {
+            const int nc = axis == 1 ? 5 : (axis == 4 ? 2 : 3);
             Tuning base = cur;
             for (int c = 0; c < nc && st == EECMG_OK; ++c) {
                 Tuning t = base;
@@ -149,8 +152,10 @@ eecmg_status eecmg_autotune(const eecmg_plan_t* plans, const float* const* g, in
                 if (axis == 1) t.cluster_max_px = cmax[c];
                 if (axis == 2) t.px_per_block = ppb[c];
                 if (axis == 3) t.blocks_per_sm = bps[c];
+                if (axis == 4) t.psd_tile_h = pth[c];
                 if (t.cluster_max_px == base.cluster_max_px && t.px_per_block == base.px_per_block &&
-                    t.blocks_per_sm == base.blocks_per_sm && t.resident_max_tiles == base.resident_max_tiles)
+                    t.blocks_per_sm == base.blocks_per_sm && t.resident_max_tiles == base.resident_max_tiles &&
+                    t.psd_tile_h == base.psd_tile_h)
                     continue;  // already timed
                 float ms = 0.f;
                 st = time_tuning(R, g, reps, s, t, &ms);

@@ -60,7 +60,8 @@ class eecmg_options(ctypes.Structure):
 
 class eecmg_tuning(ctypes.Structure):
     _fields_ = [("cluster_max_px", ctypes.c_longlong), ("px_per_block", ctypes.c_int),
-                ("blocks_per_sm", ctypes.c_int), ("resident_max_tiles", ctypes.c_int)]
+                ("blocks_per_sm", ctypes.c_int), ("resident_max_tiles", ctypes.c_int),
+                ("psd_tile_h", ctypes.c_int)]
 
 
 class eecmg_kernel_stat(ctypes.Structure):
@@ -331,7 +332,8 @@ def eecmg_residual_noalloc(width, height, psf, g, u, r, norms, stream=None):
 
 def _tuning_dict(t):
     return {"cluster_max_px": t.cluster_max_px, "px_per_block": t.px_per_block,
-            "blocks_per_sm": t.blocks_per_sm, "resident_max_tiles": t.resident_max_tiles}
+            "blocks_per_sm": t.blocks_per_sm, "resident_max_tiles": t.resident_max_tiles,
+            "psd_tile_h": t.psd_tile_h}
 
 
 def eecmg_restore_batched_host(plans, g_host, u_host, stream=None):
@@ -384,8 +386,9 @@ def eecmg_get_tuning():
     return _tuning_dict(t)
 
 
-def eecmg_set_tuning(cluster_max_px, px_per_block, blocks_per_sm, resident_max_tiles=32):
-    t = eecmg_tuning(int(cluster_max_px), int(px_per_block), int(blocks_per_sm), int(resident_max_tiles))
+def eecmg_set_tuning(cluster_max_px, px_per_block, blocks_per_sm, resident_max_tiles=32, psd_tile_h=32):
+    t = eecmg_tuning(int(cluster_max_px), int(px_per_block), int(blocks_per_sm), int(resident_max_tiles),
+                     int(psd_tile_h))
     _call("eecmg_set_tuning", ctypes.byref(t))
 
 
