@@ -29,6 +29,16 @@ Parity status per function (what pins it; see the tests under tests/):
   cascade              pinned: PSF = delta returns g exactly; end-to-end
                        values against the paper are unpinned (the paper's
                        test image is not published).
+
+The volume functions (suffix 3; arrays of shape (slices, rows, cols)) carry
+the method to 3-D, which the paper names but does not write out.  Pinned:
+with one slice and a one-slice PSF each equals its pinned 2-D function;
+permuting the three axes of the input (and of the PSF) permutes the output
+the same way, which ties the slice axis to the pinned row and column axes;
+apply_H3 equals scipy.ndimage.convolve with zero fill; coarse_psf3 equals
+the dense R H R^* product; quadratic3 is exact on triquadratics; smooth3
+equals a per-voxel weighted lstsq (numpy) and keeps affine volumes;
+denoise3 conserves the sum and keeps constants.
 """
 from __future__ import annotations
 
@@ -88,6 +98,8 @@ def _load():
             lib.or_mr2.restype = ctypes.c_int
             lib.or_cgls.restype = ctypes.c_int
             lib.or_cascade.restype = ctypes.c_int
+            lib.or_cascade3.restype = ctypes.c_int
+            lib.or_mr2_3.restype = ctypes.c_int
             lib.or_max_threads.restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -256,3 +268,109 @@ def cascade(g, L: int, psf, tau: float = 0.2, k: float = 10.0, iters=None,
 def psnr(u, uh) -> float:
     u, uh = _f64(u), _f64(uh)
     return float(_load().or_psnr(_p(u), _p(uh), u.shape[0], u.shape[1]))
+
+
+# ---------------------------------------------------------------- volumes
+
+
+def _shape3(a):
+    assert a.ndim == 3, "volume functions take (slices, rows, cols) arrays"
+    return a.shape
+
+
+def level_sizes3(d: int, h: int, w: int, L: int):
+    ds, hs, ws = (ctypes.c_int * L)(), (ctypes.c_int * L)(), (ctypes.c_int * L)()
+    _load().or_level_sizes3(d, h, w, L, ds, hs, ws)
+    return list(ds), list(hs), list(ws)
+
+
+def restrict3(fine, dc: int, hc: int, wc: int) -> np.ndarray:
+    fine = _f64(fine)
+    out = np.zeros((dc, hc, wc))
+    _load().or_restrict3(_p(fine), *_shape3(fine), _p(out), dc, hc, wc)
+    return out
+
+
+def apply_H3(K, x) -> np.ndarray:
+    K, x = _f64(K), _f64(x)
+    y = np.zeros_like(x)
+    _load().or_apply_H3(_p(K), *_shape3(K), _p(x), *_shape3(x), _p(y))
+    return y
+
+
+def apply_HT3(K, x) -> np.ndarray:
+    K, x = _f64(K), _f64(x)
+    y = np.zeros_like(x)
+    _load().or_apply_HT3(_p(K), *_shape3(K), _p(x), *_shape3(x), _p(y))
+    return y
+
+
+def coarse_psf3(K, rho: float) -> np.ndarray:
+    K = _f64(K)
+    cs = tuple(2 * (n // 2 // 2) + 1 for n in _shape3(K))
+    out = np.zeros(cs)
+    a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _load().or_coarse_psf3(_p(K), *K.shape, ctypes.c_double(rho), _p(out), ctypes.byref(a),
+                           ctypes.byref(b), ctypes.byref(c))
+    assert (a.value, b.value, c.value) == cs
+    return out
+
+
+def mr2_3(K, g, u0=None, m=1, stop_tol=0.0, conv_tol=0.0):
+    """MR-II on a volume for at most m iterations; returns (u, iterations, ||r||_RMS)."""
+    K, g = _f64(K), _f64(g)
+    u = _f64(u0).copy() if u0 is not None else np.zeros_like(g)
+    res = ctypes.c_double()
+    k = _load().or_mr2_3(_p(K), *_shape3(K), _p(g), *_shape3(g), _p(u), int(m),
+                         ctypes.c_double(stop_tol), ctypes.c_double(conv_tol), ctypes.byref(res))
+    return u, int(k), float(res.value)
+
+
+def extrapolate3(u1, u2) -> np.ndarray:
+    u1, u2 = _f64(u1), _f64(u2)
+    out = np.zeros_like(u1)
+    _load().or_extrapolate3(_p(u1), *_shape3(u1), _p(u2), *_shape3(u2), _p(out))
+    return out
+
+
+def quadratic3(ut, d: int, h: int, w: int) -> np.ndarray:
+    ut = _f64(ut)
+    out = np.zeros((d, h, w))
+    _load().or_quadratic3(_p(ut), *_shape3(ut), _p(out), d, h, w)
+    return out
+
+
+def smooth3(u, scale: float = 1.0) -> np.ndarray:
+    u = _f64(u)
+    out = np.zeros_like(u)
+    _load().or_smooth3(_p(u), *_shape3(u), ctypes.c_double(scale), _p(out))
+    return out
+
+
+def denoise3(u, tau: float, k: float) -> np.ndarray:
+    u = _f64(u)
+    out = np.zeros_like(u)
+    _load().or_denoise3(_p(u), *_shape3(u), ctypes.c_double(tau), ctypes.c_double(k), _p(out))
+    return out
+
+
+def cascade3(g, L: int, psf, tau: float = 0.2, k: float = 10.0, iters=None,
+             coarse_op: str = "rms", stop: str = "discrepancy", c: float = 1.1,
+             delta: float = 0.0, diffusion_steps: int = 1, s_scale: float = 1.0,
+             conv_tol: float = CONV_TOL):
+    """Algorithm 2 on a volume g (MR-II); returns (u, iterations, ||r||_RMS per level)."""
+    g, psf = _f64(g), _f64(psf)
+    o = _Options(0, _COARSE[coarse_op], 0, 1 if stop == "discrepancy" else 0, c, delta,
+                 diffusion_steps, s_scale, conv_tol)
+    u = np.zeros_like(g)
+    it = (ctypes.c_int * L)()
+    res = (ctypes.c_double * L)()
+    it_arr = None
+    if iters is not None:
+        it_arr = (ctypes.c_int * L)(*[int(v) for v in iters])
+    rc = _load().or_cascade3(_p(g), *_shape3(g), int(L), _p(psf), *_shape3(psf),
+                             ctypes.c_double(tau), ctypes.c_double(k), it_arr, ctypes.byref(o),
+                             _p(u), it, res)
+    if rc != 0:
+        raise ValueError("oracle cascade3: invalid arguments")
+    return u, list(it), list(res)

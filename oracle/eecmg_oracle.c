@@ -794,3 +794,498 @@ OR_API double or_psnr(const double *u, const double *uh, int h, int w)
     }
     return 20.0 * log10(255.0 / sqrt(s / (double)N));
 }
+
+/* ------------------------------------------------------------------ */
+/* volumes (Section 6: the method carried over to three dimensions)     */
+/* ------------------------------------------------------------------ */
+
+/*
+ * The paper names 3-D problems as the next application of the method and
+ * gives no 3-D formulas, so every operator below is the 2-D one above with
+ * the third axis treated exactly like the other two.  A volume of d slices,
+ * h rows and w columns is stored x[(k*h + i)*w + j]; a PSF has kd x kh x kw
+ * entries (all odd), centred: K(o, p, q) = K[((o+rz)*kh + p+ry)*kw + q+rx].
+ * Readings (each "Reading 3-D" below): restriction injects even 0-based
+ * voxels; Eq. 14 with the RMS adjoint gives K_l(o,p,q) = rho K(2o,2p,2q),
+ * rho = N_{l+1}/N_l; Pi adds 1/4 of the trilinear interpolant of the
+ * level-(l-2) differences; P is the tensor product of the three-point
+ * quadratic rule along all three axes; S fits a hyperplane over the 3x3x3
+ * neighbourhood with the Eq. 18 weights (3x3 moment matrix, pseudo-inverse
+ * through a Jacobi eigen-decomposition); D takes the six face neighbours;
+ * the smoother is MR-II and the iteration cap is the 2-D schedule m_l.
+ * Inner products sum along rows, then over the d*h rows in order, as or_dot.
+ */
+
+OR_API void or_level_sizes3(int d, int h, int w, int L, int *ds, int *hs, int *ws)
+{
+    ds[L - 1] = d;
+    or_level_sizes(h, w, L, hs, ws);
+    for (int l = L - 1; l > 0; --l)
+        ds[l - 1] = (ds[l] + 1) / 2;
+}
+
+/* Reading 3-D: coarse (a, b, c) = fine (2a, 2b, 2c), 0-based. */
+OR_API void or_restrict3(const double *fine, int df, int hf, int wf, double *coarse, int dc,
+                         int hc, int wc)
+{
+    (void)df;
+    for (int a = 0; a < dc; ++a)
+        for (int b = 0; b < hc; ++b)
+            for (int c = 0; c < wc; ++c)
+                coarse[((size_t)a * hc + b) * wc + c] =
+                    fine[((size_t)(2 * a) * hf + 2 * b) * wf + 2 * c];
+}
+
+/*
+ * y = H x (sgn = -1: convolution, y(k,i,j) = sum K(o,p,q) x(k-o, i-p, j-q))
+ * or y = H^T x (sgn = +1: correlation, x(k+o, i+p, j+q)), zero outside the
+ * volume; the sum runs over o, then p, then q.
+ */
+static void apply3(const double *K, int kd, int kh, int kw, const double *x, int d, int h, int w,
+                   double *y, int sgn)
+{
+    const int rz = kd / 2, ry = kh / 2, rx = kw / 2;
+    int row;
+#pragma omp parallel for schedule(static)
+    for (row = 0; row < d * h; ++row) {
+        const int k = row / h, i = row % h;
+        for (int j = 0; j < w; ++j) {
+            double s = 0.0;
+            for (int o = -rz; o <= rz; ++o) {
+                const int kk = k + sgn * o;
+                if (kk < 0 || kk >= d)
+                    continue;
+                for (int p = -ry; p <= ry; ++p) {
+                    const int ii = i + sgn * p;
+                    if (ii < 0 || ii >= h)
+                        continue;
+                    for (int q = -rx; q <= rx; ++q) {
+                        const int jj = j + sgn * q;
+                        if (jj < 0 || jj >= w)
+                            continue;
+                        s += K[((size_t)(o + rz) * kh + (p + ry)) * kw + (q + rx)] *
+                             x[((size_t)kk * h + ii) * w + jj];
+                    }
+                }
+            }
+            y[(size_t)row * w + j] = s;
+        }
+    }
+}
+
+OR_API void or_apply_H3(const double *K, int kd, int kh, int kw, const double *x, int d, int h,
+                        int w, double *y)
+{
+    apply3(K, kd, kh, kw, x, d, h, w, y, -1);
+}
+
+OR_API void or_apply_HT3(const double *K, int kd, int kh, int kw, const double *x, int d, int h,
+                         int w, double *y)
+{
+    apply3(K, kd, kh, kw, x, d, h, w, y, +1);
+}
+
+/* Reading 3-D of Eq. 14: K_l(o, p, q) = rho * K_{l+1}(2o, 2p, 2q). */
+OR_API void or_coarse_psf3(const double *K, int kd, int kh, int kw, double rho, double *Kc,
+                           int *kcd, int *kch, int *kcw)
+{
+    const int rz = kd / 2, ry = kh / 2, rx = kw / 2;
+    const int cz = rz / 2, cy = ry / 2, cx = rx / 2;
+    const int cd = 2 * cz + 1, ch = 2 * cy + 1, cw = 2 * cx + 1;
+    for (int o = -cz; o <= cz; ++o)
+        for (int p = -cy; p <= cy; ++p)
+            for (int q = -cx; q <= cx; ++q)
+                Kc[((size_t)(o + cz) * ch + (p + cy)) * cw + (q + cx)] =
+                    rho * K[((size_t)(2 * o + rz) * kh + (2 * p + ry)) * kw + (2 * q + rx)];
+    *kcd = cd;
+    *kch = ch;
+    *kcw = cw;
+}
+
+/*
+ * MR-II on a volume: the same recurrence, stopping rules and breakdown test
+ * as or_mr2, with H the 3-D convolution.  With d = 1 and kd = 1 every step
+ * is the 2-D one, in the same order.
+ */
+OR_API int or_mr2_3(const double *K, int kd, int kh, int kw, const double *g, int d, int h, int w,
+                    double *u, int m, double stop_tol, double conv_tol, double *res_rms)
+{
+    const int rows = d * h;
+    const size_t N = (size_t)rows * w;
+    double *r = vec_new(N), *p = vec_new(N), *q = vec_new(N);
+    double *pp = vec_new(N), *qp = vec_new(N), *z = vec_new(N);
+    double *pn = vec_new(N), *qn = vec_new(N);
+    int k = 0;
+
+    const double conv_lim = conv_tol > 0.0 ? conv_tol * sqrt(or_dot(g, g, rows, w)) : 0.0;
+    or_apply_H3(K, kd, kh, kw, u, d, h, w, r);
+    for (size_t i = 0; i < N; ++i)
+        r[i] = g[i] - r[i];
+
+    if (m > 0 && !level_done(r, rows, w, stop_tol, conv_lim)) {
+        or_apply_H3(K, kd, kh, kw, r, d, h, w, p);
+        or_apply_H3(K, kd, kh, kw, p, d, h, w, q);
+        double qq = or_dot(q, q, rows, w);
+        if (qq > 0.0 && isfinite(qq)) {
+            double a = or_dot(r, q, rows, w) / qq;
+            for (size_t i = 0; i < N; ++i) {
+                u[i] += a * p[i];
+                r[i] -= a * q[i];
+            }
+            k = 1;
+            double qqp = 0.0;
+            while (k < m) {
+                if (level_done(r, rows, w, stop_tol, conv_lim))
+                    break;
+                or_apply_H3(K, kd, kh, kw, q, d, h, w, z);
+                double b1 = or_dot(z, q, rows, w) / qq;
+                double b2 = (k >= 2) ? or_dot(z, qp, rows, w) / qqp : 0.0;
+                for (size_t i = 0; i < N; ++i) {
+                    qn[i] = z[i] - b1 * q[i] - b2 * qp[i];
+                    pn[i] = q[i] - b1 * p[i] - b2 * pp[i];
+                }
+                double qqn = or_dot(qn, qn, rows, w);
+                if (!(qqn > 0.0) || !isfinite(qqn))
+                    break;
+                a = or_dot(r, qn, rows, w) / qqn;
+                for (size_t i = 0; i < N; ++i) {
+                    u[i] += a * pn[i];
+                    r[i] -= a * qn[i];
+                }
+                double *t;
+                t = pp; pp = p; p = pn; pn = t;
+                t = qp; qp = q; q = qn; qn = t;
+                qqp = qq;
+                qq = qqn;
+                ++k;
+            }
+        }
+    }
+    if (res_rms)
+        *res_rms = or_rms(r, rows, w);
+    free(r); free(p); free(q); free(pp); free(qp); free(z); free(pn); free(qn);
+    return k;
+}
+
+/*
+ * Pi on a volume (Reading 3-D): u^{l-1} + (1/4) * (trilinear interpolant of
+ * d = u^{l-1}|_{G_{l-2}} - u^{l-2}), i.e. the mean of d over the eight
+ * corners of the level-(l-2) cell (repeated where an index is even), with a
+ * level-(l-2) index past the last node clamped to it.
+ */
+OR_API void or_extrapolate3(const double *u1, int d1, int h1, int w1, const double *u2, int d2,
+                            int h2, int w2, double *out)
+{
+    for (int c = 0; c < d1; ++c) {
+        const int C0 = c / 2, C1 = (c & 1) ? clampi(C0 + 1, d2 - 1) : C0;
+        for (int a = 0; a < h1; ++a) {
+            const int A0 = a / 2, A1 = (a & 1) ? clampi(A0 + 1, h2 - 1) : A0;
+            for (int b = 0; b < w1; ++b) {
+                const int B0 = b / 2, B1 = (b & 1) ? clampi(B0 + 1, w2 - 1) : B0;
+                const int Cs[2] = {C0, C1}, As[2] = {A0, A1}, Bs[2] = {B0, B1};
+                double dsum = 0.0;
+                for (int x = 0; x < 2; ++x)
+                    for (int i = 0; i < 2; ++i)
+                        for (int j = 0; j < 2; ++j) {
+                            const int Cc = Cs[x], A = As[i], B = Bs[j];
+                            dsum += u1[((size_t)(2 * Cc) * h1 + 2 * A) * w1 + 2 * B] -
+                                    u2[((size_t)Cc * h2 + A) * w2 + B];
+                        }
+                const size_t o = ((size_t)c * h1 + a) * w1 + b;
+                out[o] = u1[o] + 0.25 * (0.125 * dsum);
+            }
+        }
+    }
+}
+
+/* P on a volume (Reading 3-D): the QW rule along all three axes. */
+OR_API void or_quadratic3(const double *ut, int d1, int h1, int w1, double *out, int d, int h,
+                          int w)
+{
+    int row;
+#pragma omp parallel for schedule(static)
+    for (row = 0; row < d * h; ++row) {
+        const int z = row / h, y = row % h;
+        const int Z = z / 4, tz = z % 4, Y = y / 4, ty = y % 4;
+        for (int x = 0; x < w; ++x) {
+            const int X = x / 4, tx = x % 4;
+            double s = 0.0;
+            for (int k = 0; k < 3; ++k) {
+                const int c = clampi(2 * Z + k, d1 - 1);
+                for (int i = 0; i < 3; ++i) {
+                    const int a = clampi(2 * Y + i, h1 - 1);
+                    for (int j = 0; j < 3; ++j) {
+                        const int b = clampi(2 * X + j, w1 - 1);
+                        s += QW[tz][k] * QW[ty][i] * QW[tx][j] * ut[((size_t)c * h1 + a) * w1 + b];
+                    }
+                }
+            }
+            out[(size_t)row * w + x] = s;
+        }
+    }
+}
+
+/*
+ * Eigen-decomposition of a symmetric 3 x 3 matrix by the cyclic Jacobi
+ * method (Golub & Van Loan, Matrix Computations, Sec. 8.5): rotations in the
+ * (0,1), (0,2), (1,2) planes, each zeroing its off-diagonal entry, repeated
+ * until every off-diagonal entry is zero or negligible next to the
+ * diagonal.  On return A's diagonal holds the eigenvalues and the columns of
+ * V the unit eigenvectors.
+ */
+static void jacobi3(double A[3][3], double V[3][3])
+{
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j)
+            V[i][j] = (i == j) ? 1.0 : 0.0;
+    for (int sweep = 0; sweep < 64; ++sweep) {
+        const double off = fabs(A[0][1]) + fabs(A[0][2]) + fabs(A[1][2]);
+        const double dia = fabs(A[0][0]) + fabs(A[1][1]) + fabs(A[2][2]);
+        if (off == 0.0 || off <= 1e-18 * dia)
+            break;
+        for (int p = 0; p < 2; ++p)
+            for (int q = p + 1; q < 3; ++q) {
+                if (A[p][q] == 0.0)
+                    continue;
+                /* t = tan(theta) of the smaller rotation zeroing A[p][q] */
+                const double th = (A[q][q] - A[p][p]) / (2.0 * A[p][q]);
+                const double t = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
+                const double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
+                for (int k = 0; k < 3; ++k) {        /* A <- A J (columns p, q) */
+                    const double akp = A[k][p], akq = A[k][q];
+                    A[k][p] = c * akp - s * akq;
+                    A[k][q] = s * akp + c * akq;
+                }
+                for (int k = 0; k < 3; ++k) {        /* A <- J^T A (rows p, q) */
+                    const double apk = A[p][k], aqk = A[q][k];
+                    A[p][k] = c * apk - s * aqk;
+                    A[q][k] = s * apk + c * aqk;
+                }
+                A[p][q] = A[q][p] = 0.0;
+                for (int k = 0; k < 3; ++k) {        /* V <- V J */
+                    const double vkp = V[k][p], vkq = V[k][q];
+                    V[k][p] = c * vkp - s * vkq;
+                    V[k][q] = s * vkp + c * vkq;
+                }
+            }
+    }
+}
+
+/*
+ * S on a volume (Reading 3-D): for each voxel, the weighted least-squares
+ * fit of v = a0' + g . o over its 3 x 3 x 3 neighbourhood (offsets o, values
+ * v = u(neighbour) - u(centre), weights exp(-(scale v)^2) of Eq. 18,
+ * neighbours outside the volume left out), in centred form: weighted means
+ * ob, vb, moment matrix C = sum w (o - ob)(o - ob)^T, cross vector
+ * c = sum w (o - ob)(v - vb), slope = C^+ c with eigenvalues below 1e-6 W
+ * treated as zero; the output is u + vb - slope . ob.
+ */
+OR_API void or_smooth3(const double *u, int d, int h, int w, double scale, double *out)
+{
+    int row;
+#pragma omp parallel for schedule(static)
+    for (row = 0; row < d * h; ++row) {
+        const int k = row / h, i = row % h;
+        for (int j = 0; j < w; ++j) {
+            const double uc = u[((size_t)k * h + i) * w + j];
+            double ws[27], os[27][3], vs[27];
+            int n = 0;
+            for (int r = -1; r <= 1; ++r)
+                for (int s = -1; s <= 1; ++s)
+                    for (int t = -1; t <= 1; ++t) {
+                        const int kk = k + r, ii = i + s, jj = j + t;
+                        if (kk < 0 || kk >= d || ii < 0 || ii >= h || jj < 0 || jj >= w)
+                            continue;
+                        const double v = u[((size_t)kk * h + ii) * w + jj] - uc;
+                        const double e = scale * v;
+                        ws[n] = exp(-e * e);
+                        os[n][0] = r;
+                        os[n][1] = s;
+                        os[n][2] = t;
+                        vs[n] = v;
+                        ++n;
+                    }
+            double W = 0.0, ob[3] = {0, 0, 0}, vb = 0.0;
+            for (int m = 0; m < n; ++m) {
+                W += ws[m];
+                for (int a = 0; a < 3; ++a)
+                    ob[a] += ws[m] * os[m][a];
+                vb += ws[m] * vs[m];
+            }
+            for (int a = 0; a < 3; ++a)
+                ob[a] /= W;
+            vb /= W;
+            double C[3][3] = {{0}}, cv[3] = {0, 0, 0};
+            for (int m = 0; m < n; ++m) {
+                double dd[3];
+                for (int a = 0; a < 3; ++a)
+                    dd[a] = os[m][a] - ob[a];
+                const double dv = vs[m] - vb;
+                for (int a = 0; a < 3; ++a) {
+                    for (int b = 0; b < 3; ++b)
+                        C[a][b] += ws[m] * dd[a] * dd[b];
+                    cv[a] += ws[m] * dd[a] * dv;
+                }
+            }
+            double V[3][3];
+            jacobi3(C, V);
+            const double thr = 1e-6 * W;
+            double g[3] = {0, 0, 0};
+            for (int e = 0; e < 3; ++e) {
+                const double lam = C[e][e];
+                if (!(lam > thr))
+                    continue;
+                const double ce = (V[0][e] * cv[0] + V[1][e] * cv[1] + V[2][e] * cv[2]) / lam;
+                for (int a = 0; a < 3; ++a)
+                    g[a] += ce * V[a][e];
+            }
+            out[((size_t)k * h + i) * w + j] = uc + vb - (g[0] * ob[0] + g[1] * ob[1] + g[2] * ob[2]);
+        }
+    }
+}
+
+/*
+ * D on a volume (Reading 3-D): one explicit Perona-Malik step with the six
+ * face neighbours, |grad u| by central differences along the three axes
+ * (an out-of-volume neighbour replaced by the centre), and no flux through
+ * the volume's faces; the flux terms are summed slice-, row-, then column-
+ * neighbours.
+ */
+OR_API void or_denoise3(const double *u, int d, int h, int w, double tau, double kpm, double *out)
+{
+    const size_t N = (size_t)d * h * w, sl = (size_t)h * w;
+    double *c = vec_new(N);
+    int row;
+#pragma omp parallel for schedule(static)
+    for (row = 0; row < d * h; ++row) {
+        const int k = row / h, i = row % h;
+        for (int j = 0; j < w; ++j) {
+            const size_t o = (size_t)row * w + j;
+            const double uc = u[o];
+            const double ub = (k + 1 < d) ? u[o + sl] : uc, ua = (k - 1 >= 0) ? u[o - sl] : uc;
+            const double us = (i + 1 < h) ? u[o + w] : uc, un = (i - 1 >= 0) ? u[o - w] : uc;
+            const double ue = (j + 1 < w) ? u[o + 1] : uc, uw = (j - 1 >= 0) ? u[o - 1] : uc;
+            const double gx = 0.5 * (ue - uw), gy = 0.5 * (us - un), gz = 0.5 * (ub - ua);
+            c[o] = 1.0 / (1.0 + (gx * gx + gy * gy + gz * gz) / (kpm * kpm));
+        }
+    }
+#pragma omp parallel for schedule(static)
+    for (row = 0; row < d * h; ++row) {
+        const int k = row / h, i = row % h;
+        for (int j = 0; j < w; ++j) {
+            const size_t o = (size_t)row * w + j;
+            const double uc = u[o], cc = c[o];
+            double f = 0.0;
+            if (k + 1 < d) f += 0.5 * (c[o + sl] + cc) * (u[o + sl] - uc);
+            if (k - 1 >= 0) f += 0.5 * (c[o - sl] + cc) * (u[o - sl] - uc);
+            if (i + 1 < h) f += 0.5 * (c[o + w] + cc) * (u[o + w] - uc);
+            if (i - 1 >= 0) f += 0.5 * (c[o - w] + cc) * (u[o - w] - uc);
+            if (j + 1 < w) f += 0.5 * (c[o + 1] + cc) * (u[o + 1] - uc);
+            if (j - 1 >= 0) f += 0.5 * (c[o - 1] + cc) * (u[o - 1] - uc);
+            out[o] = uc + tau * f;
+        }
+    }
+    free(c);
+}
+
+/*
+ * EECMG (Algorithm 2) on a volume, the steps of or_cascade with the 3-D
+ * operators above.  Only o->smoother = OR_MR2 and o->prolong = OR_EECMG are
+ * defined here; coarse_op, stop, c, delta, diffusion_steps, s_scale and
+ * conv_tol mean what they mean in 2-D.  Returns 0, or -1 on invalid
+ * arguments.
+ */
+OR_API int or_cascade3(const double *g, int d, int h, int w, int L, const double *psf, int kd,
+                       int kh, int kw, double tau, double kpm, const int *iters,
+                       const or_options *o, double *u_out, int *it_done, double *res_rms)
+{
+    if (L < 1 || d < 1 || h < 1 || w < 1 || !(kd & 1) || !(kh & 1) || !(kw & 1) ||
+        o->smoother != OR_MR2 || o->prolong != OR_EECMG)
+        return -1;
+    int *ds = (int *)malloc(sizeof(int) * L), *hs = (int *)malloc(sizeof(int) * L);
+    int *ws = (int *)malloc(sizeof(int) * L), *m = (int *)malloc(sizeof(int) * L);
+    or_level_sizes3(d, h, w, L, ds, hs, ws);
+    if (iters)
+        memcpy(m, iters, sizeof(int) * L);
+    else
+        or_schedule(L, m);
+
+    double **gl = (double **)calloc(L, sizeof(double *));
+    double **ul = (double **)calloc(L, sizeof(double *));
+    double **Kl = (double **)calloc(L, sizeof(double *));
+    int *kdl = (int *)malloc(sizeof(int) * L), *khl = (int *)malloc(sizeof(int) * L);
+    int *kwl = (int *)malloc(sizeof(int) * L);
+    size_t *Nl = (size_t *)malloc(sizeof(size_t) * L);
+
+    for (int l = 0; l < L; ++l) {
+        Nl[l] = (size_t)ds[l] * hs[l] * ws[l];
+        gl[l] = vec_new(Nl[l]);
+        ul[l] = vec_new(Nl[l]);
+    }
+    memcpy(gl[L - 1], g, sizeof(double) * Nl[L - 1]);
+    for (int l = L - 1; l > 0; --l)
+        or_restrict3(gl[l], ds[l], hs[l], ws[l], gl[l - 1], ds[l - 1], hs[l - 1], ws[l - 1]);
+
+    Kl[L - 1] = vec_new((size_t)kd * kh * kw);
+    memcpy(Kl[L - 1], psf, sizeof(double) * (size_t)kd * kh * kw);
+    kdl[L - 1] = kd;
+    khl[L - 1] = kh;
+    kwl[L - 1] = kw;
+    double sum_fine = 0.0;
+    for (int i = 0; i < kd * kh * kw; ++i)
+        sum_fine += psf[i];
+    for (int l = L - 1; l > 0; --l) {
+        const double rho = (double)Nl[l] / (double)Nl[l - 1];
+        const int cd = 2 * (kdl[l] / 2 / 2) + 1, ch = 2 * (khl[l] / 2 / 2) + 1;
+        const int cw = 2 * (kwl[l] / 2 / 2) + 1;
+        Kl[l - 1] = vec_new((size_t)cd * ch * cw);
+        or_coarse_psf3(Kl[l], kdl[l], khl[l], kwl[l], rho, Kl[l - 1], &kdl[l - 1], &khl[l - 1],
+                       &kwl[l - 1]);
+        if (o->coarse_op == OR_GALERKIN_RENORM) {
+            double s = 0.0;
+            const int n = kdl[l - 1] * khl[l - 1] * kwl[l - 1];
+            for (int i = 0; i < n; ++i)
+                s += Kl[l - 1][i];
+            if (s != 0.0 && !psf_is_zero(Kl[l - 1], n))
+                for (int i = 0; i < n; ++i)
+                    Kl[l - 1][i] *= sum_fine / s;
+        }
+    }
+
+    const double tol = o->stop == 1 ? o->c * o->delta : 0.0;
+    for (int l = 0; l < L; ++l) {
+        const size_t N = Nl[l];
+        if (l >= 2) {
+            double *ut = vec_new(N), *tmp = vec_new(N), *ue = vec_new(Nl[l - 1]);
+            or_extrapolate3(ul[l - 1], ds[l - 1], hs[l - 1], ws[l - 1], ul[l - 2], ds[l - 2],
+                            hs[l - 2], ws[l - 2], ue);
+            or_quadratic3(ue, ds[l - 1], hs[l - 1], ws[l - 1], ut, ds[l], hs[l], ws[l]);
+            or_smooth3(ut, ds[l], hs[l], ws[l], o->s_scale, tmp);
+            for (int s = 0; s < o->diffusion_steps; ++s) {
+                or_denoise3(tmp, ds[l], hs[l], ws[l], tau, kpm, ut);
+                memcpy(tmp, ut, sizeof(double) * N);
+            }
+            memcpy(ul[l], tmp, sizeof(double) * N);
+            free(ut);
+            free(tmp);
+            free(ue);
+        }
+        double res = 0.0;
+        const int it = or_mr2_3(Kl[l], kdl[l], khl[l], kwl[l], gl[l], ds[l], hs[l], ws[l], ul[l],
+                                m[l], tol, o->conv_tol, &res);
+        if (it_done)
+            it_done[l] = it;
+        if (res_rms)
+            res_rms[l] = res;
+    }
+    memcpy(u_out, ul[L - 1], sizeof(double) * Nl[L - 1]);
+
+    for (int l = 0; l < L; ++l) {
+        free(gl[l]);
+        free(ul[l]);
+        free(Kl[l]);
+    }
+    free(gl); free(ul); free(Kl); free(kdl); free(khl); free(kwl); free(Nl);
+    free(ds); free(hs); free(ws); free(m);
+    return 0;
+}

@@ -37,6 +37,9 @@ __all__ = [
     "make_problem",
     "batch_specs",
     "arrival_trace",
+    "synthetic_volume",
+    "gaussian_psf3",
+    "make_volume_problem",
 ]
 
 
@@ -249,3 +252,63 @@ def arrival_trace(n: int, rate: float, seed: int, smin: int = 256, smax: int = 4
         out.append({"t": float(t[i]), "h": s, "w": s, "psf": psf,
                     "v": float(rng.uniform(vmin, vmax)), "seed": seed + i})
     return out
+
+
+# ---------------------------------------------------------------- volumes
+
+
+def synthetic_volume(d: int, h: int, w: int, seed: int) -> np.ndarray:
+    """A seeded FP64 test volume of shape (d, h, w) with values in [0, 255].
+
+    The 3-D counterpart of ``synthetic_image``: constant background, n_box
+    axis-aligned boxes and n_ell ellipsoids (centres uniform, semi-axes 2.5-20
+    % of each side, intensity uniform in [0, 255], painted in order), plus a
+    linear gradient along a random direction with a total swing uniform in
+    [20, 60] grey levels.  Clipped to [0, 255].  n_box = 4 + voxels/2^21 and
+    n_ell = 3 + voxels/2^21, each capped at 64.
+    """
+    rng = np.random.default_rng(seed)
+    vol = np.full((d, h, w), rng.uniform(0.0, 255.0), dtype=np.float64)
+    nvox = d * h * w
+    n_box = min(64, 4 + nvox // (1 << 21))
+    n_ell = min(64, 3 + nvox // (1 << 21))
+    zz = np.arange(d, dtype=np.float64)[:, None, None]
+    yy = np.arange(h, dtype=np.float64)[None, :, None]
+    xx = np.arange(w, dtype=np.float64)[None, None, :]
+    for _ in range(n_box):
+        c = [rng.uniform(0, n) for n in (d, h, w)]
+        r = [0.5 * rng.uniform(0.05, 0.40) * n for n in (d, h, w)]
+        val = rng.uniform(0.0, 255.0)
+        m = (np.abs(zz - c[0]) <= r[0]) & (np.abs(yy - c[1]) <= r[1]) & (np.abs(xx - c[2]) <= r[2])
+        vol[m] = val
+    for _ in range(n_ell):
+        c = [rng.uniform(0, n) for n in (d, h, w)]
+        r = [max(0.5, 0.5 * rng.uniform(0.05, 0.40) * n) for n in (d, h, w)]
+        val = rng.uniform(0.0, 255.0)
+        m = ((zz - c[0]) / r[0]) ** 2 + ((yy - c[1]) / r[1]) ** 2 + ((xx - c[2]) / r[2]) ** 2 <= 1.0
+        vol[m] = val
+    swing = rng.uniform(20.0, 60.0)
+    dirn = rng.standard_normal(3)
+    dirn /= np.linalg.norm(dirn)
+    span = sum(abs(dirn[i]) * max(n - 1, 1) for i, n in enumerate((d, h, w)))
+    grad = (dirn[0] * zz + dirn[1] * yy + dirn[2] * xx) * (swing / span)
+    vol += grad - grad.mean()
+    np.clip(vol, 0.0, 255.0, out=vol)
+    return vol
+
+
+def gaussian_psf3(sigma: float, band: int) -> np.ndarray:
+    """Separable 3-D Gaussian PSF of size (2*band+1)^3, FP64, sum 1 (h (x) h (x) h)."""
+    i = np.arange(-band, band + 1, dtype=np.float64)
+    h = np.exp(-(i * i) / (2.0 * sigma * sigma))
+    h /= h.sum()
+    return h[:, None, None] * h[None, :, None] * h[None, None, :]
+
+
+def make_volume_problem(d, h, w, seed, psf, v, noise_seed=None) -> Problem:
+    """A volume restoration problem: ``synthetic_volume`` degraded by ``degrade``."""
+    u = synthetic_volume(d, h, w, seed)
+    ns = seed + 1 if noise_seed is None else noise_seed
+    g, delta = degrade(u, psf, v, ns)
+    return Problem(u=u, psf=psf, g=g, delta=delta, v=v,
+                   meta={"d": d, "h": h, "w": w, "seed": seed, "noise_seed": ns})
