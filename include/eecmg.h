@@ -528,6 +528,105 @@ eecmg_status eecmg_server_drain(eecmg_server_t srv);
 /* Drains, stops the scheduler thread and frees all device memory. */
 eecmg_status eecmg_server_destroy(eecmg_server_t srv);
 
+/* ------------------------------------------------------------------ */
+/* Volumes: the method on 3-D data (the paper's Section 6 names volumes  */
+/* as the next application; every operator carries over with the slice  */
+/* axis treated exactly like the row and column axes).                  */
+/* ------------------------------------------------------------------ */
+
+/* Largest PSF radius per axis for volumes (PSF up to 13 x 13 x 13). */
+#define EECMG_VOL_MAX_RADIUS 6
+
+typedef struct eecmg_vol_s *eecmg_vol_t;
+
+/*
+ * Creates a restoration plan for width x height x depth volumes, stored
+ * slice-major: x[(k * height + i) * width + j] (FP32, [0, 255] grey scale).
+ * The cascade is Algorithm 2 with, per level:
+ *   restriction  coarse (a, b, c) = fine (2a, 2b, 2c) (Eqs. 12-13 per axis);
+ *   H_l          zero-boundary 3-D convolution with
+ *                K_l(o, p, q) = rho K_{l+1}(2o, 2p, 2q), rho = N_{l+1} / N_l
+ *                (Eq. 14 with the RMS adjoint; GALERKIN_RENORM rescales to the
+ *                fine PSF's sum);
+ *   Pi           u^{l-1} + 1/4 of the trilinear interpolant of the level-(l-2)
+ *                differences (Section 3.2 per axis);
+ *   P            the three-point quadratic rule along all three axes;
+ *   S            weighted least-squares hyperplane fit over the 3 x 3 x 3
+ *                neighbourhood with the weights of Eq. 18 (Section 3.3);
+ *   D            explicit Perona-Malik steps (Eqs. 20-24) with the six face
+ *                neighbours;
+ *   C_l^m        MR-II with the stopping rules of eecmg_options.
+ * Each side of a coarser level is ceil(side / 2).  psf: host FP64, psf_d x
+ * psf_h x psf_w (slice-major), odd sides, radius <= EECMG_VOL_MAX_RADIUS per
+ * axis, positive sum, centrosymmetric (MR-II needs H symmetric); copied.  A
+ * PSF that is an outer product of three vectors runs as three 1-D passes.
+ * alpha is the Perona-Malik step tau, 0 <= alpha <= 0.25 as for images (the
+ * step keeps the discrete maximum principle for alpha <= 1/6); k > 0.  iters: `levels` caps m_l (coarsest first) or
+ * NULL for the economy schedule of Section 2.  opt: NULL for the defaults;
+ * smoother must be MR2, prolong EECMG, storage FP32, workspace 1 (else
+ * UNSUPPORTED); use_graph selects one CUDA graph per plan; the other fields
+ * mean what they mean for images (precise_conv, persistent, fuse_start and
+ * early_check are ignored: every level solve is one cooperative launch).
+ * The plan allocates its workspace on the current device: the data and
+ * solution pyramids plus eight solver vectors of the finest size.
+ * Errors: INVALID_ARG, UNSUPPORTED, OOM, CUDA.
+ */
+eecmg_status eecmg_vol_plan(int width, int height, int depth, int levels, const double *psf,
+                            int psf_w, int psf_h, int psf_d, double alpha, double k,
+                            const int *iters, const eecmg_options *opt, eecmg_vol_t *out);
+
+/* Releases the plan and its device memory (synchronises the device first). */
+eecmg_status eecmg_vol_plan_destroy(eecmg_vol_t plan);
+
+/*
+ * Plan geometry: per level (coarsest first; NULL outputs skipped) the sides
+ * and the scheduled cap m_l, plus the workspace bytes.  INVALID_ARG for NULL.
+ */
+eecmg_status eecmg_vol_plan_info(eecmg_vol_t plan, int *levels, int *level_w, int *level_h,
+                                 int *level_d, int *iters, size_t *workspace_bytes);
+
+/*
+ * Restores one volume (Algorithm 2).  g_delta and u_out: device buffers of
+ * depth x height x width floats; they may alias (g is copied into the
+ * workspace first).  Asynchronous on `stream`.  Errors: INVALID_ARG, CUDA.
+ */
+eecmg_status eecmg_vol_restore(eecmg_vol_t plan, const float *g_delta, float *u_out,
+                               cudaStream_t stream);
+
+/* As eecmg_vol_restore with HOST buffers; synchronises `stream`. */
+eecmg_status eecmg_vol_restore_host(eecmg_vol_t plan, const float *g_host, float *u_host,
+                                    cudaStream_t stream);
+
+/*
+ * Per level (coarsest first) of the last restoration or level solve: the
+ * iterations run and ||g_l - H_l u_l||_RMS.  Synchronises the device.
+ * TIMEOUT if a level solve's bounded grid barrier gave up.
+ */
+eecmg_status eecmg_vol_plan_stats(eecmg_vol_t plan, int *iters_done, double *res_rms);
+
+/* Operators of one level, for tests and composition (device buffers of the
+ * level's size, not aliased; asynchronous on `stream`):
+ *   apply_H      y = H_l x (transpose = 0) or H_l^T x;
+ *   restrict     coarse = level `level`'s injection of level level+1's fine;
+ *   start_level  out = D(S(P(Pi(u1, u2)))), u1 on level-1, u2 on level-2
+ *                (level >= 2), with the plan's diffusion_steps;
+ *   smooth       y = S(x);  denoise  y = one Perona-Malik step of x;
+ *   level_solve  u <- C_l^m u (MR-II from the start in u, at most m
+ *                iterations, the plan's stopping rules); see plan_stats.
+ * Errors: INVALID_ARG (level, buffers), CUDA. */
+eecmg_status eecmg_vol_apply_H(eecmg_vol_t plan, int level, const float *x, float *y,
+                               int transpose, cudaStream_t stream);
+eecmg_status eecmg_vol_restrict(eecmg_vol_t plan, int level, const float *fine, float *coarse,
+                                cudaStream_t stream);
+eecmg_status eecmg_vol_start_level(eecmg_vol_t plan, int level, const float *u1,
+                                   const float *u2, float *out, cudaStream_t stream);
+eecmg_status eecmg_vol_smooth(eecmg_vol_t plan, int level, const float *x, float *y,
+                              cudaStream_t stream);
+eecmg_status eecmg_vol_denoise(eecmg_vol_t plan, int level, const float *x, float *y,
+                               cudaStream_t stream);
+eecmg_status eecmg_vol_level_solve(eecmg_vol_t plan, int level, const float *g, float *u, int m,
+                                   cudaStream_t stream);
+
 /* Thread-local description of the last error (never NULL). */
 const char *eecmg_last_error(void);
 

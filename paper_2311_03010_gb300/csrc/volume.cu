@@ -1,0 +1,1216 @@
+// volume.cu -- EECMG on volumes (Algorithm 2 with every operator carried over
+// to three dimensions; the paper names volumes as the method's next
+// application without writing the 3-D operators out).
+//
+// The slice axis is treated exactly like the row and column axes:
+//   restriction  coarse (a, b, c) = fine (2a, 2b, 2c)                (Eqs. 12-13)
+//   H_l          zero-boundary 3-D convolution, K_l(o,p,q) = rho K(2o,2p,2q),
+//                rho = N_{l+1} / N_l                                  (Eq. 14)
+//   Pi           u^{l-1} + 1/4 of the trilinear interpolant of the level-(l-2)
+//                differences                                         (Section 3.2)
+//   P            the three-point quadratic rule along all three axes (Section 3.2)
+//   S            weighted hyperplane fit over the 3x3x3 neighbourhood with the
+//                Eq. 18 weights, pseudo-inverse of the 3x3 moment matrix
+//                (eigenvalues under 1e-6 W dropped)                  (Section 3.3)
+//   D            one explicit Perona-Malik step with six face neighbours
+//                                                                    (Section 4)
+//   C_l^m        MR-II with the discrepancy stop of Section 2 and m_l as its cap.
+//
+// GPU design.  A volume of d x h x w voxels is stored slice-major, x[(k h + i)
+// w + j]; every level vector of the workspace is padded with zeros to a
+// multiple of 4 voxels so the vector phases run on float4.  Each level solve is
+// ONE cooperative launch (all blocks co-resident): its phases are separated by
+// the grid barrier with the fused deterministic reduction of persistent.cuh
+// (every block sums all blocks' partials in a fixed order and keeps its own
+// replica of the scalars), so the m_l iterations never return to the host and
+// the stop decision is taken on the device.  The convolution phases loop over
+// 8 x 8 x 32 output tiles: a tile and its halo are staged in shared memory and
+// a separable PSF runs as three passes (columns, rows, slices) inside the tile;
+// a general PSF runs its non-zero taps from the staged tile.  The level start
+// (Pi, P, S, D) is a chain of voxel-parallel kernels.  The cascade is captured
+// once as a CUDA graph.
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/eecmg.h"
+#include "common.cuh"
+#include "persistent.cuh"
+#include "plan.hpp"
+
+namespace eecmg {
+namespace vol {
+
+constexpr int VR = EECMG_VOL_MAX_RADIUS;
+constexpr int VK = 2 * VR + 1;
+constexpr int TX = 32, TY = 8, TZ = 8;  // output tile (columns, rows, slices)
+
+// Taps of one level in correlation form, y(v) = sum_d C(d) x(v + d), C(d) = K(-d).
+struct VolTaps {
+    int rz, ry, rx;
+    int sep;                       // 1: C = cz (x) cy (x) cx
+    float cz[VK], cy[VK], cx[VK];  // factors, index d + r
+    int ntap;                      // general form: taps in the job's tap list
+};
+
+struct VolJob {
+    int d, h, w;
+    long long n;    // voxels
+    long long n4;   // padded voxels / 4
+    const float* g;
+    float* u;
+    float* R;
+    float* P[3];
+    float* Q[3];
+    float* Z;
+    VolTaps taps;
+    const int4* gtaps;  // general form: (dz, dy, dx, weight bits)
+    int m;
+    int zero_start;
+    double stop_tol;    // discrepancy: stop once ||r||_RMS <= stop_tol (0: off)
+    double conv_tol;    // stop once ||r|| <= conv_tol ||g|| (0: off)
+    double* partials;
+    GroupSync* gs;
+    double* out;        // [0] iterations, [1] ||r||^2, [2] stop reason
+};
+
+// Per-block replica of the solve's scalars (identical in every block).
+struct VolScal {
+    double rr, gg, qq, qqp, qqn, a, b1, b2;
+    int k, done;
+};
+
+// -------------------------------------------------------------------- tile
+
+__host__ __device__ inline int tile_in_floats(const VolTaps& t) {
+    return (TZ + 2 * t.rz) * (TY + 2 * t.ry) * (TX + 2 * t.rx);
+}
+__host__ __device__ inline int tile_mid_floats(const VolTaps& t) {
+    return t.sep ? (TZ + 2 * t.rz) * (TY + 2 * t.ry) * TX : 0;
+}
+inline size_t tile_smem_bytes(const VolTaps& t) {
+    return sizeof(float) * (size_t)(tile_in_floats(t) + tile_mid_floats(t));
+}
+
+// H x for one tile (tile index t of the job's tiling): stages x with its halo
+// (zero outside the volume), convolves, and calls epi(voxel index, (H x)(v))
+// for each in-volume output of the tile.  All threads of the block call it.
+template <class Epi>
+__device__ __forceinline__ void conv_tile(const VolJob& J, const float* __restrict__ x, int t,
+                                          float* sm, Epi&& epi) {
+    const VolTaps& T = J.taps;
+    const int ntx = (J.w + TX - 1) / TX, nty = (J.h + TY - 1) / TY;
+    const int x0 = (t % ntx) * TX, y0 = ((t / ntx) % nty) * TY, z0 = (t / ntx / nty) * TZ;
+    const int NZ = TZ + 2 * T.rz, NY = TY + 2 * T.ry, AX = TX + 2 * T.rx;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float* A = sm;
+    // stage x[z0 - rz .. , y0 - ry .. , x0 - rx ..] (zero fill outside)
+    for (int row = warp; row < NZ * NY; row += NTHREADS / 32) {
+        const int za = row / NY, ya = row - za * NY;
+        const int gz = z0 - T.rz + za, gy = y0 - T.ry + ya;
+        const bool rin = gz >= 0 && gz < J.d && gy >= 0 && gy < J.h;
+        const float* src = x + ((long long)gz * J.h + gy) * J.w;
+        for (int xa = lane; xa < AX; xa += 32) {
+            const int gx = x0 - T.rx + xa;
+            A[row * AX + xa] = (rin && gx >= 0 && gx < J.w) ? __ldcg(src + gx) : 0.f;
+        }
+    }
+    __syncthreads();
+    const int xo = lane;
+    if (T.sep) {
+        float* B = sm + tile_in_floats(T);
+        // columns: B[z][y][x] = sum_dx cx A[z][y][x + rx + dx], all staged rows
+        for (int row = warp; row < NZ * NY; row += NTHREADS / 32) {
+            const float* a = A + row * AX + xo;
+            float s = 0.f;
+            for (int q = 0; q <= 2 * T.rx; ++q) s = fmaf(T.cx[q], a[q], s);
+            B[row * TX + xo] = s;
+        }
+        __syncthreads();
+        // rows: C[z][y][x] = sum_dy cy B[z][y + ry + dy][x], C over A's space
+        float* C = A;
+        for (int row = warp; row < NZ * TY; row += NTHREADS / 32) {
+            const int za = row / TY, yo = row - za * TY;
+            const float* b = B + (za * NY + yo) * TX + xo;
+            float s = 0.f;
+            for (int p = 0; p <= 2 * T.ry; ++p) s = fmaf(T.cy[p], b[p * TX], s);
+            C[row * TX + xo] = s;
+        }
+        __syncthreads();
+        // slices: out[z][y][x] = sum_dz cz C[z + rz + dz][y][x]
+        for (int row = warp; row < TZ * TY; row += NTHREADS / 32) {
+            const int zo = row / TY, yo = row - zo * TY;
+            const int gz = z0 + zo, gy = y0 + yo, gx = x0 + xo;
+            const float* c = C + (zo * TY + yo) * TX + xo;
+            float s = 0.f;
+            for (int o = 0; o <= 2 * T.rz; ++o) s = fmaf(T.cz[o], c[o * TY * TX], s);
+            if (gz < J.d && gy < J.h && gx < J.w) epi(((long long)gz * J.h + gy) * J.w + gx, s);
+        }
+    } else {
+        for (int row = warp; row < TZ * TY; row += NTHREADS / 32) {
+            const int zo = row / TY, yo = row - zo * TY;
+            const int gz = z0 + zo, gy = y0 + yo, gx = x0 + xo;
+            const float* a = A + ((zo + T.rz) * NY + yo + T.ry) * AX + xo + T.rx;
+            float s = 0.f;
+            for (int k = 0; k < T.ntap; ++k) {
+                const int4 tp = __ldg(J.gtaps + k);
+                s = fmaf(__int_as_float(tp.w), a[(tp.x * NY + tp.y) * AX + tp.z], s);
+            }
+            if (gz < J.d && gy < J.h && gx < J.w) epi(((long long)gz * J.h + gy) * J.w + gx, s);
+        }
+    }
+    __syncthreads();  // the next tile restages A
+}
+
+__device__ __forceinline__ int num_tiles(const VolJob& J) {
+    return ((J.w + TX - 1) / TX) * ((J.h + TY - 1) / TY) * ((J.d + TZ - 1) / TZ);
+}
+
+// per-thread compensated sum (cascaded: the rounding errors are kept in lo)
+__device__ __forceinline__ void acc_add(DF& a, float v) {
+    const DF s = two_sum(a.hi, v);
+    a.hi = s.hi;
+    a.lo += s.lo;
+}
+
+__device__ __forceinline__ double tot2(const DF (&t)[4], int j) {
+    return df_to_double(t[2 * j]) + df_to_double(t[2 * j + 1]);
+}
+
+// ------------------------------------------------------------- level solve
+
+// Stop test of the oracle's level smoother, checked before every iteration.
+__device__ __forceinline__ bool level_done(const VolJob& J, double rr, double gg) {
+    if (J.stop_tol > 0.0 && sqrt(rr / (double)J.n) <= J.stop_tol) return true;
+    if (J.conv_tol > 0.0 && sqrt(rr) <= J.conv_tol * sqrt(gg)) return true;
+    return false;
+}
+
+__device__ __forceinline__ bool pos_finite(double x) { return x > 0.0 && isfinite(x); }
+
+// MR-II (the three-term recurrence of the oracle's level smoother):
+//   r0 = g - H u0;  p1 = H r0, q1 = H p1, a = <r,q>/<q,q>, u += a p, r -= a q;
+//   then while k < m and the stop test fails:
+//   z = H q_k, b1 = <z,q_k>/<q_k,q_k>, b2 = <z,q_{k-1}>/<q_{k-1},q_{k-1}> (k >= 2),
+//   q_{k+1} = z - b1 q_k - b2 q_{k-1}, p_{k+1} = q_k - b1 p_k - b2 p_{k-1},
+//   a = <r,q_{k+1}>/<q_{k+1},q_{k+1}>, u += a p_{k+1}, r -= a q_{k+1}.
+// p and q live in rings of three buffers: p_k = P[(k - 1) % 3].
+__global__ void __launch_bounds__(NTHREADS) k_vol_mr2(VolJob J) {
+    extern __shared__ __align__(16) float sm[];
+    __shared__ VolScal S;
+    const unsigned int nb = gridDim.x, bid = blockIdx.x;
+    const int ntiles = num_tiles(J);
+    const long long gtid = (long long)bid * NTHREADS + threadIdx.x, gstr = (long long)nb * NTHREADS;
+    unsigned int phase = 0;
+    bool ok = true;
+    auto reduce = [&](const DF (&acc)[2], auto&& fin) {
+        float v[4] = {acc[0].hi, acc[0].lo, acc[1].hi, acc[1].lo};
+        return grid_reduce<4>(v, J.partials, J.gs, nb, bid, phase++, fin);
+    };
+    float4* u4 = reinterpret_cast<float4*>(J.u);
+    float4* r4 = reinterpret_cast<float4*>(J.R);
+    const float4* g4 = reinterpret_cast<const float4*>(J.g);
+
+    // r0 = g - H u0 (a zero start writes u = 0, r = g); ||r||^2, ||g||^2
+    {
+        // the vector phases run on whole float4s: zero the (at most 3) padding
+        // voxels past n of every vector this solve reads, whatever an earlier
+        // use of the shared buffers left there
+        const long long pad = 4 * J.n4 - J.n;
+        if (gtid < pad) {
+            const long long i = J.n + gtid;
+            J.u[i] = 0.f;
+            J.R[i] = 0.f;
+            J.Z[i] = 0.f;
+#pragma unroll
+            for (int b = 0; b < 3; ++b) {
+                J.P[b][i] = 0.f;
+                J.Q[b][i] = 0.f;
+            }
+        }
+        DF acc[2] = {{0.f, 0.f}, {0.f, 0.f}};
+        if (J.zero_start) {
+            for (long long i = gtid; i < J.n4; i += gstr) {
+                const float4 g = __ldcg(g4 + i);
+                u4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+                r4[i] = g;
+                acc_add(acc[0], dot4(g, g, 0.f));
+                acc_add(acc[1], dot4(g, g, 0.f));
+            }
+        } else {
+            for (int t = bid; t < ntiles; t += nb)
+                conv_tile(J, J.u, t, sm, [&](long long i, float hx) {
+                    const float g = __ldcg(J.g + i);
+                    const float r = g - hx;
+                    J.R[i] = r;
+                    acc_add(acc[0], r * r);
+                    acc_add(acc[1], g * g);
+                });
+        }
+        ok = reduce(acc, [&](const DF (&t)[4]) {
+            S.rr = tot2(t, 0);
+            S.gg = tot2(t, 1);
+            S.k = 0;
+            S.done = (J.m <= 0 || level_done(J, S.rr, S.gg)) ? 1 : 0;
+        });
+    }
+    if (ok && !S.done) {
+        // p1 = H r0
+        for (int t = bid; t < ntiles; t += nb)
+            conv_tile(J, J.R, t, sm, [&](long long i, float hx) { J.P[0][i] = hx; });
+        DF none[2] = {{0.f, 0.f}, {0.f, 0.f}};
+        ok = reduce(none, [&](const DF (&)[4]) {});
+    }
+    if (ok && !S.done) {
+        // q1 = H p1; <q,q>, <r,q>
+        DF acc[2] = {{0.f, 0.f}, {0.f, 0.f}};
+        for (int t = bid; t < ntiles; t += nb)
+            conv_tile(J, J.P[0], t, sm, [&](long long i, float hx) {
+                J.Q[0][i] = hx;
+                acc_add(acc[0], hx * hx);
+                acc_add(acc[1], __ldcg(J.R + i) * hx);
+            });
+        ok = reduce(acc, [&](const DF (&t)[4]) {
+            const double qq = tot2(t, 0), rq = tot2(t, 1);
+            if (!pos_finite(qq)) {
+                S.done = 2;
+            } else {
+                S.qq = qq;
+                S.a = rq / qq;
+            }
+        });
+    }
+    if (ok && !S.done) {
+        // u += a p1, r -= a q1; ||r||^2
+        DF acc[2] = {{0.f, 0.f}, {0.f, 0.f}};
+        const float a = (float)S.a;
+        const float4* p4 = reinterpret_cast<const float4*>(J.P[0]);
+        const float4* q4 = reinterpret_cast<const float4*>(J.Q[0]);
+        for (long long i = gtid; i < J.n4; i += gstr) {
+            const float4 p = __ldcg(p4 + i), q = __ldcg(q4 + i), u = __ldcg(u4 + i),
+                         r = __ldcg(r4 + i);
+            const float4 rn = fma4(-a, q, r);
+            u4[i] = fma4(a, p, u);
+            r4[i] = rn;
+            acc_add(acc[0], dot4(rn, rn, 0.f));
+        }
+        ok = reduce(acc, [&](const DF (&t)[4]) {
+            S.rr = tot2(t, 0);
+            S.k = 1;
+            S.qqp = 0.0;
+            S.done = (S.k >= J.m || level_done(J, S.rr, S.gg)) ? 1 : 0;
+        });
+    }
+    while (ok && !S.done) {
+        const int k = S.k;
+        const int cur = (k - 1) % 3, prv = (k + 1) % 3, nxt = k % 3;
+        const float* q = J.Q[cur];
+        const float* qp = J.Q[prv];
+        const bool two = k >= 2;
+        // z = H q_k; <z, q_k>, <z, q_{k-1}>
+        {
+            DF acc[2] = {{0.f, 0.f}, {0.f, 0.f}};
+            for (int t = bid; t < ntiles; t += nb)
+                conv_tile(J, q, t, sm, [&](long long i, float hx) {
+                    J.Z[i] = hx;
+                    acc_add(acc[0], hx * __ldcg(q + i));
+                    if (two) acc_add(acc[1], hx * __ldcg(qp + i));
+                });
+            ok = reduce(acc, [&](const DF (&t)[4]) {
+                S.b1 = tot2(t, 0) / S.qq;
+                S.b2 = two ? tot2(t, 1) / S.qqp : 0.0;
+            });
+            if (!ok) break;
+        }
+        // q_{k+1}, p_{k+1}; <q_{k+1}, q_{k+1}>, <r, q_{k+1}>
+        {
+            DF acc[2] = {{0.f, 0.f}, {0.f, 0.f}};
+            const float b1 = (float)S.b1, b2 = (float)S.b2;
+            const float4* z4 = reinterpret_cast<const float4*>(J.Z);
+            const float4* qc = reinterpret_cast<const float4*>(J.Q[cur]);
+            const float4* qo = reinterpret_cast<const float4*>(J.Q[prv]);
+            const float4* pc = reinterpret_cast<const float4*>(J.P[cur]);
+            const float4* po = reinterpret_cast<const float4*>(J.P[prv]);
+            float4* qn = reinterpret_cast<float4*>(J.Q[nxt]);
+            float4* pn = reinterpret_cast<float4*>(J.P[nxt]);
+            for (long long i = gtid; i < J.n4; i += gstr) {
+                const float4 z = __ldcg(z4 + i), qv = __ldcg(qc + i), pv = __ldcg(pc + i),
+                             r = __ldcg(r4 + i);
+                float4 a = fma4(-b1, qv, z), b = fma4(-b1, pv, qv);
+                if (two) {
+                    a = fma4(-b2, __ldcg(qo + i), a);
+                    b = fma4(-b2, __ldcg(po + i), b);
+                }
+                qn[i] = a;
+                pn[i] = b;
+                acc_add(acc[0], dot4(a, a, 0.f));
+                acc_add(acc[1], dot4(r, a, 0.f));
+            }
+            ok = reduce(acc, [&](const DF (&t)[4]) {
+                const double qqn = tot2(t, 0), rqn = tot2(t, 1);
+                if (!pos_finite(qqn)) {
+                    S.done = 2;
+                } else {
+                    S.qqn = qqn;
+                    S.a = rqn / qqn;
+                }
+            });
+            if (!ok || S.done) break;
+        }
+        // u += a p_{k+1}, r -= a q_{k+1}; ||r||^2
+        {
+            DF acc[2] = {{0.f, 0.f}, {0.f, 0.f}};
+            const float a = (float)S.a;
+            const float4* pn = reinterpret_cast<const float4*>(J.P[nxt]);
+            const float4* qn = reinterpret_cast<const float4*>(J.Q[nxt]);
+            for (long long i = gtid; i < J.n4; i += gstr) {
+                const float4 p = __ldcg(pn + i), qv = __ldcg(qn + i), u = __ldcg(u4 + i),
+                             r = __ldcg(r4 + i);
+                const float4 rn = fma4(-a, qv, r);
+                u4[i] = fma4(a, p, u);
+                r4[i] = rn;
+                acc_add(acc[0], dot4(rn, rn, 0.f));
+            }
+            ok = reduce(acc, [&](const DF (&t)[4]) {
+                S.rr = tot2(t, 0);
+                S.qqp = S.qq;
+                S.qq = S.qqn;
+                S.k = S.k + 1;
+                S.done = (S.k >= J.m || level_done(J, S.rr, S.gg)) ? 1 : 0;
+            });
+        }
+    }
+    if (bid == 0 && threadIdx.x == 0) {
+        J.out[0] = S.k;
+        J.out[1] = S.rr;
+        J.out[2] = ok ? S.done : -1;
+    }
+    grid_exit(J.gs, nb);
+}
+
+// H x (or H^T x with the transposed taps) of a whole level, one tile per block.
+__global__ void __launch_bounds__(NTHREADS) k_vol_apply(VolJob J, const float* __restrict__ x,
+                                                        float* __restrict__ y) {
+    extern __shared__ __align__(16) float sm[];
+    conv_tile(J, x, blockIdx.x, sm, [&](long long i, float hx) { y[i] = hx; });
+}
+
+// ------------------------------------------------------------ level start
+
+__global__ void k_vol_restrict(const float* __restrict__ f, int hf, int wf, float* __restrict__ c,
+                               int dc, int hc, int wc) {
+    const long long n = (long long)dc * hc * wc;
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < n;
+         v += (long long)gridDim.x * blockDim.x) {
+        const int b = (int)(v % wc);
+        const long long r = v / wc;
+        const int a = (int)(r % hc), s = (int)(r / hc);
+        c[v] = f[((long long)(2 * s) * hf + 2 * a) * wf + 2 * b];
+    }
+}
+
+// Pi: out = u1 + (1/4) * mean of the level-(l-2) differences d over the cell's
+// eight corners (indices past the last level-(l-2) node clamp to it).
+__global__ void k_vol_pi(const float* __restrict__ u1, int d1, int h1, int w1,
+                         const float* __restrict__ u2, int d2, int h2, int w2,
+                         float* __restrict__ out) {
+    const long long n = (long long)d1 * h1 * w1;
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < n;
+         v += (long long)gridDim.x * blockDim.x) {
+        const int b = (int)(v % w1);
+        const long long rr = v / w1;
+        const int a = (int)(rr % h1), c = (int)(rr / h1);
+        const int C0 = c >> 1, C1 = (c & 1) ? min(C0 + 1, d2 - 1) : C0;
+        const int A0 = a >> 1, A1 = (a & 1) ? min(A0 + 1, h2 - 1) : A0;
+        const int B0 = b >> 1, B1 = (b & 1) ? min(B0 + 1, w2 - 1) : B0;
+        const int Cs[2] = {C0, C1}, As[2] = {A0, A1}, Bs[2] = {B0, B1};
+        float s = 0.f;
+#pragma unroll
+        for (int x = 0; x < 2; ++x)
+#pragma unroll
+            for (int i = 0; i < 2; ++i)
+#pragma unroll
+                for (int j = 0; j < 2; ++j)
+                    s += __ldg(u1 + ((long long)(2 * Cs[x]) * h1 + 2 * As[i]) * w1 + 2 * Bs[j]) -
+                         __ldg(u2 + ((long long)Cs[x] * h2 + As[i]) * w2 + Bs[j]);
+        out[v] = u1[v] + 0.03125f * s;
+    }
+}
+
+__constant__ float c_vqw[4][3] = {
+    {1.f, 0.f, 0.f}, {0.375f, 0.75f, -0.125f}, {0.f, 1.f, 0.f}, {-0.125f, 0.75f, 0.375f}};
+
+// P: the three-point quadratic rule along all three axes (clamped indices).
+__global__ void k_vol_quad(const float* __restrict__ ut, int d1, int h1, int w1,
+                           float* __restrict__ out, int d, int h, int w) {
+    const long long n = (long long)d * h * w;
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < n;
+         v += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(v % w);
+        const long long rr = v / w;
+        const int y = (int)(rr % h), z = (int)(rr / h);
+        const int tz = z & 3, ty = y & 3, tx = x & 3;
+        const int Z = (z >> 2) * 2, Y = (y >> 2) * 2, X = (x >> 2) * 2;
+        int xs[3];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) xs[j] = min(X + j, w1 - 1);
+        float s = 0.f;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const float wz = c_vqw[tz][k];
+            if (wz == 0.f) continue;
+            const int c = min(Z + k, d1 - 1);
+            float sy = 0.f;
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                const float wy = c_vqw[ty][i];
+                if (wy == 0.f) continue;
+                const float* row = ut + ((long long)c * h1 + min(Y + i, h1 - 1)) * w1;
+                float sx = 0.f;
+#pragma unroll
+                for (int j = 0; j < 3; ++j) sx = fmaf(c_vqw[tx][j], __ldg(row + xs[j]), sx);
+                sy = fmaf(wy, sx, sy);
+            }
+            s = fmaf(wz, sy, s);
+        }
+        out[v] = s;
+    }
+}
+
+// Eigen-decomposition of the symmetric 3x3 A by cyclic Jacobi rotations
+// (Golub & Van Loan, Sec. 8.5); A's diagonal receives the eigenvalues and the
+// columns of V the eigenvectors.  Four sweeps: the off-diagonal mass falls
+// quadratically, far below FP32 resolution for a 3x3 matrix.
+__device__ __forceinline__ void jacobi3f(float A[3][3], float V[3][3]) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) V[i][j] = i == j ? 1.f : 0.f;
+#pragma unroll
+    for (int sweep = 0; sweep < 4; ++sweep) {
+#pragma unroll
+        for (int pq = 0; pq < 3; ++pq) {
+            const int p = pq == 2 ? 1 : 0, q = pq == 0 ? 1 : 2;
+            const float apq = A[p][q];
+            if (apq == 0.f) continue;
+            const float th = (A[q][q] - A[p][p]) / (2.f * apq);
+            const float t = copysignf(1.f, th) / (fabsf(th) + sqrtf(fmaf(th, th, 1.f)));
+            const float c = rsqrtf(fmaf(t, t, 1.f)), s = t * c;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const float akp = A[k][p], akq = A[k][q];
+                A[k][p] = c * akp - s * akq;
+                A[k][q] = s * akp + c * akq;
+            }
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const float apk = A[p][k], aqk = A[q][k];
+                A[p][k] = c * apk - s * aqk;
+                A[q][k] = s * apk + c * aqk;
+            }
+            A[p][q] = A[q][p] = 0.f;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const float vkp = V[k][p], vkq = V[k][q];
+                V[k][p] = c * vkp - s * vkq;
+                V[k][q] = s * vkp + c * vkq;
+            }
+        }
+    }
+}
+
+// S: per voxel, the weighted hyperplane fit over the in-volume 3x3x3
+// neighbourhood (weights exp(-(scale v)^2), v = neighbour - centre) in centred
+// form; the output is u + vb - slope . ob with slope = C^+ c.
+__global__ void k_vol_smooth(const float* __restrict__ u, int d, int h, int w, float scale,
+                             float* __restrict__ out) {
+    const long long n = (long long)d * h * w;
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < n;
+         v += (long long)gridDim.x * blockDim.x) {
+        const int j = (int)(v % w);
+        const long long rr = v / w;
+        const int i = (int)(rr % h), k = (int)(rr / h);
+        const float uc = u[v];
+        float W = 0.f, o0 = 0.f, o1 = 0.f, o2 = 0.f, vb = 0.f;
+        float m00 = 0.f, m01 = 0.f, m02 = 0.f, m11 = 0.f, m12 = 0.f, m22 = 0.f;
+        float c0 = 0.f, c1 = 0.f, c2 = 0.f;
+        // raw weighted moments; centred afterwards (offsets are small integers)
+#pragma unroll
+        for (int r = -1; r <= 1; ++r) {
+            if (k + r < 0 || k + r >= d) continue;
+#pragma unroll
+            for (int s = -1; s <= 1; ++s) {
+                if (i + s < 0 || i + s >= h) continue;
+                const float* row = u + ((long long)(k + r) * h + i + s) * w + j;
+#pragma unroll
+                for (int t = -1; t <= 1; ++t) {
+                    if (j + t < 0 || j + t >= w) continue;
+                    const float val = __ldg(row + t) - uc;
+                    const float e = scale * val;
+                    const float wt = (r == 0 && s == 0 && t == 0) ? 1.f : __expf(-e * e);
+                    W += wt;
+                    const float wv = wt * val;
+                    vb += wv;
+                    if (r) { o0 = fmaf(wt, (float)r, o0); m00 += wt; c0 = fmaf(wv, (float)r, c0); }
+                    if (s) { o1 = fmaf(wt, (float)s, o1); m11 += wt; c1 = fmaf(wv, (float)s, c1); }
+                    if (t) { o2 = fmaf(wt, (float)t, o2); m22 += wt; c2 = fmaf(wv, (float)t, c2); }
+                    if (r && s) m01 = fmaf(wt, (float)(r * s), m01);
+                    if (r && t) m02 = fmaf(wt, (float)(r * t), m02);
+                    if (s && t) m12 = fmaf(wt, (float)(s * t), m12);
+                }
+            }
+        }
+        const float iW = 1.f / W;
+        o0 *= iW; o1 *= iW; o2 *= iW; vb *= iW;
+        // centred moments: sum w (o - ob)(o' - ob') = sum w o o' - W ob ob'
+        float A[3][3];
+        A[0][0] = fmaf(-W * o0, o0, m00);
+        A[1][1] = fmaf(-W * o1, o1, m11);
+        A[2][2] = fmaf(-W * o2, o2, m22);
+        A[0][1] = A[1][0] = fmaf(-W * o0, o1, m01);
+        A[0][2] = A[2][0] = fmaf(-W * o0, o2, m02);
+        A[1][2] = A[2][1] = fmaf(-W * o1, o2, m12);
+        // sum w (o - ob)(v - vb) = sum w o v - W ob vb
+        const float cv0 = fmaf(-W * o0, vb, c0), cv1 = fmaf(-W * o1, vb, c1),
+                    cv2 = fmaf(-W * o2, vb, c2);
+        float V[3][3];
+        jacobi3f(A, V);
+        const float thr = 1e-6f * W;
+        float g0 = 0.f, g1 = 0.f, g2 = 0.f;
+#pragma unroll
+        for (int e = 0; e < 3; ++e) {
+            const float lam = A[e][e];
+            if (!(lam > thr)) continue;
+            const float ce = (V[0][e] * cv0 + V[1][e] * cv1 + V[2][e] * cv2) / lam;
+            g0 = fmaf(ce, V[0][e], g0);
+            g1 = fmaf(ce, V[1][e], g1);
+            g2 = fmaf(ce, V[2][e], g2);
+        }
+        out[v] = uc + vb - (g0 * o0 + g1 * o1 + g2 * o2);
+    }
+}
+
+// D, first half: the diffusivity c = 1 / (1 + |grad u|^2 / k^2), central
+// differences, an out-of-volume neighbour replaced by the centre.
+__global__ void k_vol_pm_c(const float* __restrict__ u, int d, int h, int w, float ik2,
+                           float* __restrict__ c) {
+    const long long n = (long long)d * h * w, sl = (long long)h * w;
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < n;
+         v += (long long)gridDim.x * blockDim.x) {
+        const int j = (int)(v % w);
+        const long long rr = v / w;
+        const int i = (int)(rr % h), k = (int)(rr / h);
+        const float uc = u[v];
+        const float ub = k + 1 < d ? u[v + sl] : uc, ua = k > 0 ? u[v - sl] : uc;
+        const float us = i + 1 < h ? u[v + w] : uc, un = i > 0 ? u[v - w] : uc;
+        const float ue = j + 1 < w ? u[v + 1] : uc, uw = j > 0 ? u[v - 1] : uc;
+        const float gx = 0.5f * (ue - uw), gy = 0.5f * (us - un), gz = 0.5f * (ub - ua);
+        c[v] = 1.f / (1.f + (gx * gx + gy * gy + gz * gz) * ik2);
+    }
+}
+
+// D, second half: u' = u + tau sum over in-volume face neighbours of
+// (c_nb + c) / 2 (u_nb - u) (no flux through the volume's faces).
+__global__ void k_vol_pm_step(const float* __restrict__ u, const float* __restrict__ c, int d,
+                              int h, int w, float tau, float* __restrict__ out) {
+    const long long n = (long long)d * h * w, sl = (long long)h * w;
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < n;
+         v += (long long)gridDim.x * blockDim.x) {
+        const int j = (int)(v % w);
+        const long long rr = v / w;
+        const int i = (int)(rr % h), k = (int)(rr / h);
+        const float uc = u[v], cc = c[v];
+        float f = 0.f;
+        if (k + 1 < d) f = fmaf(0.5f * (c[v + sl] + cc), u[v + sl] - uc, f);
+        if (k > 0) f = fmaf(0.5f * (c[v - sl] + cc), u[v - sl] - uc, f);
+        if (i + 1 < h) f = fmaf(0.5f * (c[v + w] + cc), u[v + w] - uc, f);
+        if (i > 0) f = fmaf(0.5f * (c[v - w] + cc), u[v - w] - uc, f);
+        if (j + 1 < w) f = fmaf(0.5f * (c[v + 1] + cc), u[v + 1] - uc, f);
+        if (j > 0) f = fmaf(0.5f * (c[v - 1] + cc), u[v - 1] - uc, f);
+        out[v] = fmaf(tau, f, uc);
+    }
+}
+
+}  // namespace vol
+}  // namespace eecmg
+
+// ====================================================================== host
+
+using namespace eecmg;
+using namespace eecmg::vol;
+
+struct eecmg_vol_s {
+    int W = 0, H = 0, D = 0, L = 0;
+    double tau = 0.2, kpm = 10.0;
+    eecmg_options opt{};
+    int device = 0, sms = 0;
+    std::vector<int> ds, hs, ws, m;
+    std::vector<long long> n, n4;
+    std::vector<VolTaps> taps, tapsT;                  // H_l and H_l^T
+    std::vector<std::vector<int4>> gt, gtT;            // general-form tap lists (host)
+    char* wsp = nullptr;
+    size_t ws_bytes = 0;
+    std::vector<float*> g, u;                          // per level (padded)
+    float* vec[8] = {};                                // R, P0..2, Q0..2, Z (finest size)
+    int4* dtaps = nullptr;                             // all tap lists, [2l] H, [2l+1] H^T
+    std::vector<size_t> dtap_off;
+    GroupSync* gs = nullptr;                           // one per level
+    double* partials = nullptr;
+    double* out = nullptr;                             // 4 doubles per level
+    std::vector<int> grid;                             // level solve blocks
+    cudaStream_t cap = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+};
+
+namespace {
+
+#define VCK(call)                                                                           \
+    do {                                                                                    \
+        cudaError_t e_ = (call);                                                            \
+        if (e_ != cudaSuccess)                                                              \
+            return set_error(EECMG_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+// Correlation-form taps of the PSF K (kd x kh x kw): C(d) = K(-d) for H,
+// C(d) = K(d) for H^T.  A PSF that is an outer product of three vectors (to
+// FP64 rounding) is stored as its three factors.
+void make_vol_taps(const std::vector<double>& K, int kd, int kh, int kw, bool transpose,
+                   VolTaps* t, std::vector<int4>* list) {
+    std::memset(t, 0, sizeof(VolTaps));
+    const int rz = kd / 2, ry = kh / 2, rx = kw / 2;
+    t->rz = rz;
+    t->ry = ry;
+    t->rx = rx;
+    auto C = [&](int o, int p, int q) {
+        if (!transpose) { o = -o; p = -p; q = -q; }
+        return K[((size_t)(o + rz) * kh + (p + ry)) * kw + (q + rx)];
+    };
+    int o0 = 0, p0 = 0, q0 = 0;
+    double mx = -1.0;
+    for (int o = -rz; o <= rz; ++o)
+        for (int p = -ry; p <= ry; ++p)
+            for (int q = -rx; q <= rx; ++q)
+                if (std::fabs(C(o, p, q)) > mx) {
+                    mx = std::fabs(C(o, p, q));
+                    o0 = o;
+                    p0 = p;
+                    q0 = q;
+                }
+    bool sep = mx > 0.0;
+    if (sep) {
+        // C(o,p,q) = a(o) b(p) c(q) through the largest entry k0:
+        // a(o) = C(o,p0,q0), b(p) = C(o0,p,q0) / k0, c(q) = C(o0,p0,q) / k0
+        const double k0 = C(o0, p0, q0);
+        std::vector<double> a(kd), b(kh), c(kw);
+        for (int o = -rz; o <= rz; ++o) a[o + rz] = C(o, p0, q0);
+        for (int p = -ry; p <= ry; ++p) b[p + ry] = C(o0, p, q0) / k0;
+        for (int q = -rx; q <= rx; ++q) c[q + rx] = C(o0, p0, q) / k0;
+        for (int o = -rz; o <= rz && sep; ++o)
+            for (int p = -ry; p <= ry && sep; ++p)
+                for (int q = -rx; q <= rx; ++q)
+                    if (std::fabs(C(o, p, q) - a[o + rz] * b[p + ry] * c[q + rx]) > 1e-12 * mx) {
+                        sep = false;
+                        break;
+                    }
+        if (sep) {
+            for (int o = 0; o < kd; ++o) t->cz[o] = (float)a[o];
+            for (int p = 0; p < kh; ++p) t->cy[p] = (float)b[p];
+            for (int q = 0; q < kw; ++q) t->cx[q] = (float)c[q];
+        }
+    }
+    t->sep = sep ? 1 : 0;
+    list->clear();
+    if (!sep) {
+        for (int o = -rz; o <= rz; ++o)
+            for (int p = -ry; p <= ry; ++p)
+                for (int q = -rx; q <= rx; ++q) {
+                    const double v = C(o, p, q);
+                    if (v == 0.0) continue;
+                    float f = (float)v;
+                    int bits;
+                    std::memcpy(&bits, &f, 4);
+                    // offsets into the staged tile relative to the output voxel
+                    list->push_back(make_int4(o, p, q, bits));
+                }
+    }
+    t->ntap = (int)list->size();
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+int blocks_for(long long n) {
+    long long b = (n + 255) / 256;
+    return (int)(b < 1 ? 1 : (b > 152 * 16 ? 152 * 16 : b));
+}
+
+VolJob make_job(eecmg_vol_s* P, int l, bool transpose) {
+    VolJob J{};
+    J.d = P->ds[l];
+    J.h = P->hs[l];
+    J.w = P->ws[l];
+    J.n = P->n[l];
+    J.n4 = P->n4[l];
+    J.g = P->g[l];
+    J.u = P->u[l];
+    J.R = P->vec[0];
+    for (int i = 0; i < 3; ++i) {
+        J.P[i] = P->vec[1 + i];
+        J.Q[i] = P->vec[4 + i];
+    }
+    J.Z = P->vec[7];
+    J.taps = transpose ? P->tapsT[l] : P->taps[l];
+    J.gtaps = P->dtaps + P->dtap_off[2 * l + (transpose ? 1 : 0)];
+    // general-form offsets index the staged tile: (dz + rz) NY AX + ...; the
+    // kernel adds the output's own position, so store dz, dy, dx as they are
+    J.m = P->m[l];
+    J.stop_tol = P->opt.stop == EECMG_STOP_DISCREPANCY ? P->opt.c * P->opt.delta : 0.0;
+    J.conv_tol = P->opt.conv_tol;
+    J.partials = P->partials;
+    J.gs = P->gs + l;
+    J.out = P->out + 4 * l;
+    return J;
+}
+
+int level_tiles(const VolJob& J) {
+    return ((J.w + TX - 1) / TX) * ((J.h + TY - 1) / TY) * ((J.d + TZ - 1) / TZ);
+}
+
+eecmg_status launch_solve(eecmg_vol_s* P, int l, bool zero_start, cudaStream_t s) {
+    VolJob J = make_job(P, l, false);
+    J.zero_start = zero_start ? 1 : 0;
+    void* args[] = {&J};
+    const size_t smem = tile_smem_bytes(J.taps);
+    VCK(cudaLaunchCooperativeKernel((const void*)k_vol_mr2, dim3(P->grid[l]), dim3(NTHREADS), args,
+                                    smem, s));
+    return EECMG_OK;
+}
+
+eecmg_status launch_apply(eecmg_vol_s* P, int l, bool transpose, const float* x, float* y,
+                          cudaStream_t s) {
+    VolJob J = make_job(P, l, transpose);
+    const size_t smem = tile_smem_bytes(J.taps);
+    k_vol_apply<<<level_tiles(J), NTHREADS, smem, s>>>(J, x, y);
+    VCK(cudaGetLastError());
+    return EECMG_OK;
+}
+
+// D(S(P(Pi(u1, u2)))) of level l (l >= 2) into out; uses R, Z, P0, Q0 as
+// temporaries (none of them is live between level solves).
+eecmg_status launch_start(eecmg_vol_s* P, int l, const float* u1, const float* u2, float* out,
+                          cudaStream_t s) {
+    const int d1 = P->ds[l - 1], h1 = P->hs[l - 1], w1 = P->ws[l - 1];
+    const int d = P->ds[l], h = P->hs[l], w = P->ws[l];
+    float* ue = P->vec[4];   // Q0: Pi on level l-1
+    float* ut = P->vec[0];   // R: P(Pi)
+    float* sa = P->vec[1];   // P0
+    float* cc = P->vec[7];   // Z: diffusivity
+    k_vol_pi<<<blocks_for(P->n[l - 1]), 256, 0, s>>>(u1, d1, h1, w1, u2, P->ds[l - 2], P->hs[l - 2],
+                                                    P->ws[l - 2], ue);
+    k_vol_quad<<<blocks_for(P->n[l]), 256, 0, s>>>(ue, d1, h1, w1, ut, d, h, w);
+    const int steps = P->opt.diffusion_steps;
+    float* cur = steps == 0 ? out : sa;
+    k_vol_smooth<<<blocks_for(P->n[l]), 256, 0, s>>>(ut, d, h, w, (float)P->opt.s_scale, cur);
+    const float ik2 = (float)(1.0 / (P->kpm * P->kpm));
+    for (int st = 0; st < steps; ++st) {
+        float* nxt = st == steps - 1 ? out : (cur == sa ? ut : sa);
+        k_vol_pm_c<<<blocks_for(P->n[l]), 256, 0, s>>>(cur, d, h, w, ik2, cc);
+        k_vol_pm_step<<<blocks_for(P->n[l]), 256, 0, s>>>(cur, cc, d, h, w, (float)P->tau, nxt);
+        cur = nxt;
+    }
+    VCK(cudaGetLastError());
+    return EECMG_OK;
+}
+
+eecmg_status cascade(eecmg_vol_s* P, cudaStream_t s) {
+    const int L = P->L;
+    for (int l = L - 1; l > 0; --l) {
+        k_vol_restrict<<<blocks_for(P->n[l - 1]), 256, 0, s>>>(P->g[l], P->hs[l], P->ws[l],
+                                                             P->g[l - 1], P->ds[l - 1],
+                                                             P->hs[l - 1], P->ws[l - 1]);
+        VCK(cudaGetLastError());
+    }
+    for (int l = 0; l < L; ++l) {
+        if (l >= 2) {
+            eecmg_status st = launch_start(P, l, P->u[l - 1], P->u[l - 2], P->u[l], s);
+            if (st != EECMG_OK) return st;
+        }
+        eecmg_status st = launch_solve(P, l, l < 2, s);
+        if (st != EECMG_OK) return st;
+    }
+    return EECMG_OK;
+}
+
+// The cascade on the workspace's g_L (filled by the caller), as one CUDA graph
+// captured at the first call (use_graph) or as plain launches.
+eecmg_status run_cascade(eecmg_vol_s* P, cudaStream_t s) {
+    if (!P->opt.use_graph) return cascade(P, s);
+    if (!P->gexec) {
+        VCK(cudaStreamBeginCapture(P->cap, cudaStreamCaptureModeThreadLocal));
+        eecmg_status st = cascade(P, P->cap);
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamEndCapture(P->cap, &graph);
+        if (st != EECMG_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return st;
+        }
+        if (e != cudaSuccess)
+            return set_error(EECMG_ERR_CUDA, std::string("volume graph capture: ") + cudaGetErrorString(e));
+        e = cudaGraphInstantiate(&P->gexec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            P->gexec = nullptr;
+            return set_error(EECMG_ERR_CUDA, std::string("volume graph instantiate: ") + cudaGetErrorString(e));
+        }
+    }
+    VCK(cudaGraphLaunch(P->gexec, s));
+    return EECMG_OK;
+}
+
+eecmg_status check_level(eecmg_vol_s* P, int level, const char* who) {
+    if (!P) return set_error(EECMG_ERR_INVALID_ARG, std::string(who) + ": NULL plan");
+    if (level < 0 || level >= P->L)
+        return set_error(EECMG_ERR_INVALID_ARG, std::string(who) + ": level out of range");
+    return EECMG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+eecmg_status eecmg_vol_plan(int width, int height, int depth, int levels, const double* psf,
+                            int psf_w, int psf_h, int psf_d, double alpha, double k,
+                            const int* iters, const eecmg_options* opt, eecmg_vol_t* out) {
+    if (!out) return set_error(EECMG_ERR_INVALID_ARG, "eecmg_vol_plan: out is NULL");
+    *out = nullptr;
+    if (width < 1 || height < 1 || depth < 1 || levels < 1 || levels > 16)
+        return set_error(EECMG_ERR_INVALID_ARG, "eecmg_vol_plan: bad volume size or levels");
+    if ((long long)width * height * depth > (1LL << 31))
+        return set_error(EECMG_ERR_INVALID_ARG, "eecmg_vol_plan: volume above 2^31 voxels");
+    if (!psf || psf_w < 1 || psf_h < 1 || psf_d < 1 || !(psf_w & 1) || !(psf_h & 1) || !(psf_d & 1) ||
+        psf_w / 2 > VR || psf_h / 2 > VR || psf_d / 2 > VR)
+        return set_error(EECMG_ERR_INVALID_ARG,
+                         "eecmg_vol_plan: PSF sides must be odd with radius <= EECMG_VOL_MAX_RADIUS");
+    if (!(alpha >= 0.0 && alpha <= 0.25) || !(k > 0.0))
+        return set_error(EECMG_ERR_INVALID_ARG, "eecmg_vol_plan: need 0 <= alpha <= 0.25 and k > 0");
+    eecmg_options o;
+    eecmg_default_options(&o);
+    if (opt) o = *opt;
+    if (o.smoother != EECMG_SMOOTHER_MR2 || o.prolong != EECMG_PROLONG_EECMG ||
+        o.storage != EECMG_STORAGE_FP32 || !o.workspace)
+        return set_error(EECMG_ERR_UNSUPPORTED,
+                         "eecmg_vol_plan: volumes run MR-II, Algorithm 2, FP32, with a workspace");
+    if ((o.coarse_op != EECMG_COARSE_GALERKIN_RMS && o.coarse_op != EECMG_COARSE_GALERKIN_RENORM) ||
+        (o.stop != EECMG_STOP_FIXED && o.stop != EECMG_STOP_DISCREPANCY) || !(o.c > 1.0) ||
+        !(o.delta >= 0.0) || o.diffusion_steps < 0 || o.diffusion_steps > 64 || !(o.conv_tol >= 0.0) ||
+        !std::isfinite(o.s_scale))
+        return set_error(EECMG_ERR_INVALID_ARG, "eecmg_vol_plan: invalid option");
+    const int nk = psf_w * psf_h * psf_d;
+    std::vector<double> K(psf, psf + nk);
+    double ksum = 0.0;
+    for (double v : K) {
+        if (!std::isfinite(v)) return set_error(EECMG_ERR_INVALID_ARG, "eecmg_vol_plan: PSF not finite");
+        ksum += v;
+    }
+    if (!(ksum > 0.0)) return set_error(EECMG_ERR_INVALID_ARG, "eecmg_vol_plan: PSF sum must be positive");
+    for (int i = 0; i < nk; ++i)  // MR-II needs H symmetric: K(d) = K(-d)
+        if (std::fabs(K[i] - K[nk - 1 - i]) > 1e-12 * std::fabs(ksum))
+            return set_error(EECMG_ERR_UNSUPPORTED, "eecmg_vol_plan: MR-II needs a centrosymmetric PSF");
+    if (iters)
+        for (int l = 0; l < levels; ++l)
+            if (iters[l] < 0) return set_error(EECMG_ERR_INVALID_ARG, "eecmg_vol_plan: iters < 0");
+
+    auto* P = new eecmg_vol_s();
+    P->W = width;
+    P->H = height;
+    P->D = depth;
+    P->L = levels;
+    P->tau = alpha;
+    P->kpm = k;
+    P->opt = o;
+    const int L = levels;
+    P->ds.resize(L);
+    P->hs.resize(L);
+    P->ws.resize(L);
+    P->m.resize(L);
+    P->ds[L - 1] = depth;
+    P->hs[L - 1] = height;
+    P->ws[L - 1] = width;
+    for (int l = L - 1; l > 0; --l) {
+        P->ds[l - 1] = (P->ds[l] + 1) / 2;
+        P->hs[l - 1] = (P->hs[l] + 1) / 2;
+        P->ws[l - 1] = (P->ws[l] + 1) / 2;
+    }
+    for (int l = 0; l < L; ++l) P->m[l] = iters ? iters[l] : schedule_m(L, l + 1);
+    P->n.resize(L);
+    P->n4.resize(L);
+    for (int l = 0; l < L; ++l) {
+        P->n[l] = (long long)P->ds[l] * P->hs[l] * P->ws[l];
+        P->n4[l] = (P->n[l] + 3) / 4;
+    }
+    // level PSFs (Eq. 14 in 3-D; RENORM rescales to the fine PSF's sum)
+    std::vector<std::vector<double>> Kl(L);
+    std::vector<int> kdl(L), khl(L), kwl(L);
+    Kl[L - 1] = K;
+    kdl[L - 1] = psf_d;
+    khl[L - 1] = psf_h;
+    kwl[L - 1] = psf_w;
+    for (int l = L - 1; l > 0; --l) {
+        const double rho = (double)P->n[l] / (double)P->n[l - 1];
+        const int rz = kdl[l] / 2, ry = khl[l] / 2, rx = kwl[l] / 2;
+        const int cz = rz / 2, cy = ry / 2, cx = rx / 2;
+        kdl[l - 1] = 2 * cz + 1;
+        khl[l - 1] = 2 * cy + 1;
+        kwl[l - 1] = 2 * cx + 1;
+        Kl[l - 1].assign((size_t)kdl[l - 1] * khl[l - 1] * kwl[l - 1], 0.0);
+        for (int a = -cz; a <= cz; ++a)
+            for (int b = -cy; b <= cy; ++b)
+                for (int c = -cx; c <= cx; ++c)
+                    Kl[l - 1][((size_t)(a + cz) * khl[l - 1] + (b + cy)) * kwl[l - 1] + (c + cx)] =
+                        rho * Kl[l][((size_t)(2 * a + rz) * khl[l] + (2 * b + ry)) * kwl[l] + (2 * c + rx)];
+        if (o.coarse_op == EECMG_COARSE_GALERKIN_RENORM) {
+            double s = 0.0;
+            bool nz = false;
+            for (double v : Kl[l - 1]) {
+                s += v;
+                nz = nz || v != 0.0;
+            }
+            if (s != 0.0 && nz)
+                for (double& v : Kl[l - 1]) v *= ksum / s;
+        }
+    }
+    P->taps.resize(L);
+    P->tapsT.resize(L);
+    P->gt.resize(L);
+    P->gtT.resize(L);
+    size_t ntaps = 0;
+    for (int l = 0; l < L; ++l) {
+        make_vol_taps(Kl[l], kdl[l], khl[l], kwl[l], false, &P->taps[l], &P->gt[l]);
+        make_vol_taps(Kl[l], kdl[l], khl[l], kwl[l], true, &P->tapsT[l], &P->gtT[l]);
+        ntaps += P->gt[l].size() + P->gtT[l].size() + 2;
+    }
+    // workspace: g and u per level, 8 solver vectors, taps, barriers, partials
+    eecmg_status st = EECMG_OK;
+    cudaError_t e = cudaGetDevice(&P->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&P->sms, cudaDevAttrMultiProcessorCount, P->device);
+    if (e != cudaSuccess) {
+        delete P;
+        return set_error(EECMG_ERR_CUDA, std::string("eecmg_vol_plan: ") + cudaGetErrorString(e));
+    }
+    P->grid.resize(L);
+    int maxgrid = 1;
+    for (int l = 0; l < L; ++l) {
+        const size_t smem = tile_smem_bytes(P->taps[l]);
+        e = cudaFuncSetAttribute(k_vol_mr2, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_vol_apply, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        int per = 0;
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_vol_mr2, NTHREADS, smem);
+        if (e != cudaSuccess || per < 1) {
+            delete P;
+            return set_error(EECMG_ERR_CUDA, "eecmg_vol_plan: level solve does not fit an SM");
+        }
+        VolJob J{};
+        J.d = P->ds[l];
+        J.h = P->hs[l];
+        J.w = P->ws[l];
+        const long long want = std::max<long long>(level_tiles(J), (P->n4[l] + NTHREADS - 1) / NTHREADS);
+        const long long cap = (long long)per * P->sms;
+        P->grid[l] = (int)std::max<long long>(1, std::min(want, cap));
+        maxgrid = std::max(maxgrid, P->grid[l]);
+    }
+    size_t off = 0;
+    std::vector<size_t> goff(L), uoff(L), voff(8);
+    for (int l = 0; l < L; ++l) {
+        goff[l] = off;
+        off = align256(off + (size_t)P->n4[l] * 16);
+        uoff[l] = off;
+        off = align256(off + (size_t)P->n4[l] * 16);
+    }
+    for (int i = 0; i < 8; ++i) {
+        voff[i] = off;
+        off = align256(off + (size_t)P->n4[L - 1] * 16);
+    }
+    const size_t taps_off = off;
+    off = align256(off + ntaps * sizeof(int4));
+    const size_t gs_off = off;
+    off = align256(off + (size_t)L * sizeof(GroupSync));
+    const size_t out_off = off;
+    off = align256(off + (size_t)L * 4 * sizeof(double));
+    const size_t part_off = off;
+    off = align256(off + (size_t)2 * maxgrid * NPART * sizeof(double));
+    e = cudaMalloc((void**)&P->wsp, off);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        delete P;
+        return set_error(EECMG_ERR_OOM, "eecmg_vol_plan: workspace allocation failed");
+    }
+    P->ws_bytes = off;
+    e = cudaMemset(P->wsp, 0, off);
+    P->g.resize(L);
+    P->u.resize(L);
+    for (int l = 0; l < L; ++l) {
+        P->g[l] = (float*)(P->wsp + goff[l]);
+        P->u[l] = (float*)(P->wsp + uoff[l]);
+    }
+    for (int i = 0; i < 8; ++i) P->vec[i] = (float*)(P->wsp + voff[i]);
+    P->dtaps = (int4*)(P->wsp + taps_off);
+    P->gs = (GroupSync*)(P->wsp + gs_off);
+    P->out = (double*)(P->wsp + out_off);
+    P->partials = (double*)(P->wsp + part_off);
+    std::vector<int4> all;
+    P->dtap_off.resize(2 * L);
+    for (int l = 0; l < L; ++l) {
+        P->dtap_off[2 * l] = all.size();
+        all.insert(all.end(), P->gt[l].begin(), P->gt[l].end());
+        all.push_back(make_int4(0, 0, 0, 0));
+        P->dtap_off[2 * l + 1] = all.size();
+        all.insert(all.end(), P->gtT[l].begin(), P->gtT[l].end());
+        all.push_back(make_int4(0, 0, 0, 0));
+    }
+    if (e == cudaSuccess)
+        e = cudaMemcpy(P->dtaps, all.data(), all.size() * sizeof(int4), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&P->cap, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        st = set_error(EECMG_ERR_CUDA, std::string("eecmg_vol_plan: ") + cudaGetErrorString(e));
+        cudaFree(P->wsp);
+        delete P;
+        return st;
+    }
+    *out = P;
+    return EECMG_OK;
+}
+
+eecmg_status eecmg_vol_plan_destroy(eecmg_vol_t P) {
+    if (!P) return EECMG_OK;
+    cudaDeviceSynchronize();
+    if (P->gexec) cudaGraphExecDestroy(P->gexec);
+    if (P->cap) cudaStreamDestroy(P->cap);
+    if (P->wsp) cudaFree(P->wsp);
+    delete P;
+    return EECMG_OK;
+}
+
+eecmg_status eecmg_vol_plan_info(eecmg_vol_t P, int* levels, int* level_w, int* level_h,
+                                 int* level_d, int* iters, size_t* workspace_bytes) {
+    if (!P) return set_error(EECMG_ERR_INVALID_ARG, "eecmg_vol_plan_info: NULL plan");
+    if (levels) *levels = P->L;
+    for (int l = 0; l < P->L; ++l) {
+        if (level_w) level_w[l] = P->ws[l];
+        if (level_h) level_h[l] = P->hs[l];
+        if (level_d) level_d[l] = P->ds[l];
+        if (iters) iters[l] = P->m[l];
+    }
+    if (workspace_bytes) *workspace_bytes = P->ws_bytes;
+    return EECMG_OK;
+}
+
+eecmg_status eecmg_vol_restore(eecmg_vol_t P, const float* g, float* u, cudaStream_t s) {
+    if (!P || !g || !u) return set_error(EECMG_ERR_INVALID_ARG, "eecmg_vol_restore: NULL argument");
+    const size_t bytes = (size_t)P->n[P->L - 1] * sizeof(float);
+    VCK(cudaMemcpyAsync(P->g[P->L - 1], g, bytes, cudaMemcpyDeviceToDevice, s));
+    eecmg_status st = run_cascade(P, s);
+    if (st != EECMG_OK) return st;
+    VCK(cudaMemcpyAsync(u, P->u[P->L - 1], bytes, cudaMemcpyDeviceToDevice, s));
+    return EECMG_OK;
+}
+
+eecmg_status eecmg_vol_restore_host(eecmg_vol_t P, const float* g_host, float* u_host,
+                                    cudaStream_t s) {
+    if (!P || !g_host || !u_host)
+        return set_error(EECMG_ERR_INVALID_ARG, "eecmg_vol_restore_host: NULL argument");
+    const size_t bytes = (size_t)P->n[P->L - 1] * sizeof(float);
+    VCK(cudaMemcpyAsync(P->g[P->L - 1], g_host, bytes, cudaMemcpyHostToDevice, s));
+    eecmg_status st = run_cascade(P, s);
+    if (st != EECMG_OK) return st;
+    VCK(cudaMemcpyAsync(u_host, P->u[P->L - 1], bytes, cudaMemcpyDeviceToHost, s));
+    VCK(cudaStreamSynchronize(s));
+    return EECMG_OK;
+}
+
+eecmg_status eecmg_vol_plan_stats(eecmg_vol_t P, int* iters_done, double* res_rms) {
+    if (!P) return set_error(EECMG_ERR_INVALID_ARG, "eecmg_vol_plan_stats: NULL plan");
+    VCK(cudaDeviceSynchronize());
+    std::vector<double> h(4 * (size_t)P->L);
+    VCK(cudaMemcpy(h.data(), P->out, h.size() * sizeof(double), cudaMemcpyDeviceToHost));
+    std::vector<GroupSync> gs(P->L);
+    VCK(cudaMemcpy(gs.data(), P->gs, gs.size() * sizeof(GroupSync), cudaMemcpyDeviceToHost));
+    for (int l = 0; l < P->L; ++l) {
+        if (iters_done) iters_done[l] = (int)h[4 * l];
+        if (res_rms) res_rms[l] = std::sqrt(h[4 * l + 1] / (double)P->n[l]);
+        if (gs[l].err) return set_error(EECMG_ERR_TIMEOUT, "eecmg_vol_plan_stats: a grid barrier timed out");
+    }
+    return EECMG_OK;
+}
+
+eecmg_status eecmg_vol_apply_H(eecmg_vol_t P, int level, const float* x, float* y, int transpose,
+                               cudaStream_t s) {
+    eecmg_status st = check_level(P, level, "eecmg_vol_apply_H");
+    if (st != EECMG_OK) return st;
+    if (!x || !y || x == y) return set_error(EECMG_ERR_INVALID_ARG, "eecmg_vol_apply_H: bad buffers");
+    return launch_apply(P, level, transpose != 0, x, y, s);
+}
+
+eecmg_status eecmg_vol_start_level(eecmg_vol_t P, int level, const float* u1, const float* u2,
+                                   float* out, cudaStream_t s) {
+    eecmg_status st = check_level(P, level, "eecmg_vol_start_level");
+    if (st != EECMG_OK) return st;
+    if (level < 2 || !u1 || !u2 || !out)
+        return set_error(EECMG_ERR_INVALID_ARG, "eecmg_vol_start_level: needs level >= 2 and buffers");
+    return launch_start(P, level, u1, u2, out, s);
+}
+
+eecmg_status eecmg_vol_smooth(eecmg_vol_t P, int level, const float* x, float* y, cudaStream_t s) {
+    eecmg_status st = check_level(P, level, "eecmg_vol_smooth");
+    if (st != EECMG_OK) return st;
+    if (!x || !y || x == y) return set_error(EECMG_ERR_INVALID_ARG, "eecmg_vol_smooth: bad buffers");
+    k_vol_smooth<<<blocks_for(P->n[level]), 256, 0, s>>>(x, P->ds[level], P->hs[level], P->ws[level],
+                                                        (float)P->opt.s_scale, y);
+    VCK(cudaGetLastError());
+    return EECMG_OK;
+}
+
+eecmg_status eecmg_vol_denoise(eecmg_vol_t P, int level, const float* x, float* y, cudaStream_t s) {
+    eecmg_status st = check_level(P, level, "eecmg_vol_denoise");
+    if (st != EECMG_OK) return st;
+    if (!x || !y || x == y) return set_error(EECMG_ERR_INVALID_ARG, "eecmg_vol_denoise: bad buffers");
+    const int d = P->ds[level], h = P->hs[level], w = P->ws[level];
+    k_vol_pm_c<<<blocks_for(P->n[level]), 256, 0, s>>>(x, d, h, w, (float)(1.0 / (P->kpm * P->kpm)),
+                                                      P->vec[7]);
+    k_vol_pm_step<<<blocks_for(P->n[level]), 256, 0, s>>>(x, P->vec[7], d, h, w, (float)P->tau, y);
+    VCK(cudaGetLastError());
+    return EECMG_OK;
+}
+
+eecmg_status eecmg_vol_restrict(eecmg_vol_t P, int level, const float* fine, float* coarse,
+                                cudaStream_t s) {
+    eecmg_status st = check_level(P, level, "eecmg_vol_restrict");
+    if (st != EECMG_OK) return st;
+    if (level >= P->L - 1 || !fine || !coarse)
+        return set_error(EECMG_ERR_INVALID_ARG, "eecmg_vol_restrict: level must be below the finest");
+    k_vol_restrict<<<blocks_for(P->n[level]), 256, 0, s>>>(fine, P->hs[level + 1], P->ws[level + 1],
+                                                          coarse, P->ds[level], P->hs[level],
+                                                          P->ws[level]);
+    VCK(cudaGetLastError());
+    return EECMG_OK;
+}
+
+eecmg_status eecmg_vol_level_solve(eecmg_vol_t P, int level, const float* g, float* u, int m,
+                                   cudaStream_t s) {
+    eecmg_status st = check_level(P, level, "eecmg_vol_level_solve");
+    if (st != EECMG_OK) return st;
+    if (!g || !u || m < 0) return set_error(EECMG_ERR_INVALID_ARG, "eecmg_vol_level_solve: bad arguments");
+    const size_t bytes = (size_t)P->n[level] * sizeof(float);
+    VCK(cudaMemcpyAsync(P->g[level], g, bytes, cudaMemcpyDeviceToDevice, s));
+    VCK(cudaMemcpyAsync(P->u[level], u, bytes, cudaMemcpyDeviceToDevice, s));
+    const int keep = P->m[level];
+    P->m[level] = m;
+    st = launch_solve(P, level, false, s);
+    P->m[level] = keep;
+    if (st != EECMG_OK) return st;
+    VCK(cudaMemcpyAsync(u, P->u[level], bytes, cudaMemcpyDeviceToDevice, s));
+    return EECMG_OK;
+}
+
+}  // extern "C"

@@ -117,6 +117,19 @@ _SIGS = {
     "eecmg_server_poll": [_VP, ctypes.c_uint64, _PI, _PD],
     "eecmg_server_drain": [_VP],
     "eecmg_server_destroy": [_VP],
+    "eecmg_vol_plan": [_I, _I, _I, _I, _PD, _I, _I, _I, _D, _D, _PI, ctypes.POINTER(eecmg_options),
+                       ctypes.POINTER(_VP)],
+    "eecmg_vol_plan_destroy": [_VP],
+    "eecmg_vol_plan_info": [_VP, _PI, _PI, _PI, _PI, _PI, ctypes.POINTER(ctypes.c_size_t)],
+    "eecmg_vol_restore": [_VP, _VP, _VP, _VP],
+    "eecmg_vol_restore_host": [_VP, _VP, _VP, _VP],
+    "eecmg_vol_plan_stats": [_VP, _PI, _PD],
+    "eecmg_vol_apply_H": [_VP, _I, _VP, _VP, _I, _VP],
+    "eecmg_vol_restrict": [_VP, _I, _VP, _VP, _VP],
+    "eecmg_vol_start_level": [_VP, _I, _VP, _VP, _VP, _VP],
+    "eecmg_vol_smooth": [_VP, _I, _VP, _VP, _VP],
+    "eecmg_vol_denoise": [_VP, _I, _VP, _VP, _VP],
+    "eecmg_vol_level_solve": [_VP, _I, _VP, _VP, _I, _VP],
     "eecmg_last_error": [],
     "eecmg_version": [],
 }
@@ -442,6 +455,110 @@ def eecmg_server_drain(srv):
 
 def eecmg_server_destroy(srv):
     _call("eecmg_server_destroy", srv)
+
+
+# ---------------------------------------------------------------- volumes
+
+
+def eecmg_vol_plan(width, height, depth, levels, psf, alpha=0.2, k=10.0, iters=None, opt=None,
+                   **kw):
+    """Volume plan handle (int); psf is a (depth, rows, cols) FP64 array."""
+    psf = np.ascontiguousarray(psf, dtype=np.float64)
+    if psf.ndim != 3:
+        raise ValueError("a volume PSF is a 3-D array (slices, rows, cols)")
+    if opt is None:
+        opt = eecmg_default_options(**kw)
+    it = None
+    if iters is not None:
+        if len(iters) != levels:
+            raise ValueError("iters needs one entry per level")
+        it = (ctypes.c_int * levels)(*[int(v) for v in iters])
+    h = _VP()
+    _call("eecmg_vol_plan", int(width), int(height), int(depth), int(levels),
+          psf.ctypes.data_as(_PD), psf.shape[2], psf.shape[1], psf.shape[0], float(alpha),
+          float(k), it, ctypes.byref(opt), ctypes.byref(h))
+    return h.value
+
+
+def eecmg_vol_plan_destroy(plan):
+    _call("eecmg_vol_plan_destroy", plan)
+
+
+def eecmg_vol_plan_info(plan):
+    n = _I()
+    _call("eecmg_vol_plan_info", plan, ctypes.byref(n), None, None, None, None, None)
+    L = n.value
+    w, hh, dd, m = (_I * L)(), (_I * L)(), (_I * L)(), (_I * L)()
+    ws = ctypes.c_size_t()
+    _call("eecmg_vol_plan_info", plan, None, w, hh, dd, m, ctypes.byref(ws))
+    return {"levels": L, "w": list(w), "h": list(hh), "d": list(dd), "iters": list(m),
+            "workspace_bytes": ws.value}
+
+
+def eecmg_vol_restore(plan, g, u, stream=None):
+    _call("eecmg_vol_restore", plan, _ptr(g), _ptr(u), _stream(stream))
+
+
+def eecmg_vol_restore_host(plan, g, u, stream=None):
+    _call("eecmg_vol_restore_host", plan, _ptr(g), _ptr(u), _stream(stream))
+
+
+def eecmg_vol_plan_stats(plan):
+    L = eecmg_vol_plan_info(plan)["levels"]
+    it = (_I * L)()
+    res = (_D * L)()
+    _call("eecmg_vol_plan_stats", plan, it, res)
+    return list(it), list(res)
+
+
+def eecmg_vol_apply_H(plan, level, x, y, transpose=0, stream=None):
+    _call("eecmg_vol_apply_H", plan, int(level), _ptr(x), _ptr(y), int(transpose), _stream(stream))
+
+
+def eecmg_vol_restrict(plan, level, fine, coarse, stream=None):
+    _call("eecmg_vol_restrict", plan, int(level), _ptr(fine), _ptr(coarse), _stream(stream))
+
+
+def eecmg_vol_start_level(plan, level, u1, u2, out, stream=None):
+    _call("eecmg_vol_start_level", plan, int(level), _ptr(u1), _ptr(u2), _ptr(out),
+          _stream(stream))
+
+
+def eecmg_vol_smooth(plan, level, x, y, stream=None):
+    _call("eecmg_vol_smooth", plan, int(level), _ptr(x), _ptr(y), _stream(stream))
+
+
+def eecmg_vol_denoise(plan, level, x, y, stream=None):
+    _call("eecmg_vol_denoise", plan, int(level), _ptr(x), _ptr(y), _stream(stream))
+
+
+def eecmg_vol_level_solve(plan, level, g, u, m, stream=None):
+    _call("eecmg_vol_level_solve", plan, int(level), _ptr(g), _ptr(u), int(m), _stream(stream))
+
+
+class VolumePlan:
+    """Owning wrapper of a volume plan (eecmg_vol_plan / eecmg_vol_plan_destroy)."""
+
+    def __init__(self, width, height, depth, levels, psf, alpha=0.2, k=10.0, iters=None, **opts):
+        self.h = eecmg_vol_plan(width, height, depth, levels, psf, alpha, k, iters, **opts)
+        self.info = eecmg_vol_plan_info(self.h)
+
+    def close(self):
+        if self.h:
+            eecmg_vol_plan_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def restore(self, g, u, stream=None):
+        eecmg_vol_restore(self.h, g, u, stream)
+
+    def stats(self):
+        return eecmg_vol_plan_stats(self.h)
 
 
 class Plan:

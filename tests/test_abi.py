@@ -85,3 +85,34 @@ def test_server_arguments_checked_before_any_device_call(lib):
             fn(*args)
         assert ei.value.status == 1
     lib.eecmg_server_destroy(None)  # NULL is a no-op
+
+
+def test_volume_plan_validation(lib):
+    """eecmg_vol_plan checks sizes, PSF and options on the host, before any CUDA call."""
+    from paper_2311_03010_gb300 import synth
+
+    g = synth.gaussian_psf3(1.5, 3)
+    def code(**kw):
+        args = dict(width=16, height=16, depth=16, levels=3, psf=g)
+        args.update(kw)
+        try:
+            h = lib.eecmg_vol_plan(args.pop("width"), args.pop("height"), args.pop("depth"),
+                                   args.pop("levels"), args.pop("psf"), **args)
+        except lib.EecmgError as e:
+            return e.status
+        raise AssertionError(f"accepted {kw} ({h})")
+
+    assert code(width=0) == 1
+    assert code(levels=0) == 1
+    assert code(psf=np.ones((2, 3, 3))) == 1                        # even side
+    assert code(psf=synth.gaussian_psf3(2.0, 7)) == 1               # radius 7 > 6
+    assert code(psf=-g) == 1                                        # non-positive sum
+    assert code(alpha=0.3) == 1                                     # above 0.25
+    assert code(k=0.0) == 1
+    ns = np.random.default_rng(1).uniform(0, 1, (3, 3, 3))
+    assert code(psf=ns) == 2                                        # MR-II, not centrosymmetric
+    assert code(smoother="cgls") == 2
+    assert code(prolong="iecmg_p") == 2
+    assert code(storage="bf16") == 2
+    assert code(iters=[1, -1, 1]) == 1
+    assert code(c=1.0) == 1
