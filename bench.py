@@ -32,6 +32,15 @@ the Krylov vectors, and ``serving``: a 2000-request
 Poisson trace through the continuous-batching server and through the plain
 per-image loop (and its first 400 requests with the other storage type).
 
+``volume``: the method on volumes (Algorithm 2 with the 3-D operators), a
+256 x 256 x 256 synthetic volume, separable Gaussian PSF sigma = 1.5 on
+7 x 7 x 7, 1 % noise, 4 levels: Mvoxel/s (device and end to end through
+eecmg_vol_restore_host), the finest level solve's roofline (algorithmic
+bytes over its event-timed duration in an eager restoration), parity against
+the oracle on a 64^3 volume of the same recipe plus the 256^3 residual
+recomputed by the oracle, and the oracle's own Mvoxel/s.  ``--volume-only``
+prints that object alone (one JSON line).
+
 ``--impl reference`` times the CPU oracle itself on the same workload.
 """
 from __future__ import annotations
@@ -421,6 +430,119 @@ def extra_leg(torch, eecmg, stream, name, args, world, flush, oracle_ok, extra=N
     return out
 
 
+VOLUME = {"workload": "256x256x256-gauss1.5-L4", "n": 256, "levels": 4, "sigma": 1.5, "band": 3,
+          "noise": 0.01, "seed": 340, "parity_n": 64, "parity_seed": 341}
+
+
+def volume_leg(torch, eecmg, stream, flush, steps, warmup, peak, oracle_ok):
+    """The volume cascade: device and end-to-end Mvoxel/s, finest-solve roofline, parity."""
+    from paper_2311_03010_gb300 import synth
+
+    V = VOLUME
+    n, L = V["n"], V["levels"]
+    psf = synth.gaussian_psf3(V["sigma"], V["band"])
+    p = synth.make_volume_problem(n, n, n, V["seed"], psf, V["noise"])
+    plan = eecmg.VolumePlan(n, n, n, L, psf, delta=p.delta)
+    gd = torch.from_numpy(p.g).cuda()
+    ud = torch.empty_like(gd)
+    for _ in range(max(3, warmup)):
+        plan.restore(gd, ud, stream)
+    torch.cuda.synchronize()
+    steps = max(steps, 5)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ms = []
+    for _ in range(steps):
+        flush.zero_()
+        e0.record(stream)
+        plan.restore(gd, ud, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    tot = sum(ms)
+    it, res = plan.stats()
+    vox = n ** 3
+    out = {"workload": V["workload"], "value": vox * steps / tot / 1e3, "unit": "Mvoxel/s",
+           "steps": steps, "ms_per_step": tot / steps, "iters": it, "caps": plan.info["iters"],
+           "res_rms": res, "delta": p.delta, "l2": "flushed between steps",
+           "psf": f"separable Gaussian sigma {V['sigma']} on {2 * V['band'] + 1}^3",
+           # restrictions, level solves, and Pi, P, S and one D (two kernels) per started level
+           "gpu_launches_per_step": (L - 1) + L + 5 * max(0, L - 2)}
+    # end to end: pinned host buffers, copies inside the timed region
+    gh = torch.from_numpy(p.g).pin_memory()
+    uh = torch.empty_like(gh).pin_memory()
+    eecmg.eecmg_vol_restore_host(plan.h, gh, uh, stream)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        eecmg.eecmg_vol_restore_host(plan.h, gh, uh, stream)
+    e2e_s = time.perf_counter() - t0
+    out["e2e"] = {"value": vox * steps / e2e_s / 1e6, "unit": "Mvoxel/s",
+                  "h2d_bytes_per_step": vox * 4, "d2h_bytes_per_step": vox * 4,
+                  "api": "eecmg_vol_restore_host", "equals_device_result": bool(
+                      torch.equal(uh, ud.cpu()))}
+    # roofline of the finest level solve: eager restoration with event pairs
+    eecmg.eecmg_vol_plan_profile(plan.h, 1)
+    sol_ms, sol_b = [], []
+    for _ in range(3):
+        flush.zero_()
+        plan.restore(gd, ud, stream)
+        st_ms, s_ms, s_b = eecmg.eecmg_vol_plan_profile_read(plan.h)
+        sol_ms.append(s_ms[-1])
+        sol_b.append(s_b[-1])
+    eecmg.eecmg_vol_plan_profile(plan.h, 0)
+    kms = statistics.median(sol_ms)
+    achieved = sol_b[0] / (kms * 1e-3) / 1e9
+    out["roofline"] = {"bound": "hbm", "kernel": "k_vol_mr2, finest level solve", "achieved": achieved,
+                       "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                       "bytes_per_launch": sol_b[0], "ms_per_launch": kms,
+                       "share_of_step": kms / (tot / steps), "level_start_ms": st_ms,
+                       "level_solve_ms": s_ms, "traffic": None,
+                       "method": "event pair around the launch in an eager restoration (median of 3)"}
+    if oracle_ok:
+        import oracle
+
+        oracle.set_threads(host_threads())
+        u = ud.double().cpu().numpy()
+        r = p.g.astype(np.float64) - oracle.apply_H3(psf, u)
+        res_or = float(np.sqrt(np.mean(r * r)))
+        m = V["parity_n"]
+        q = synth.make_volume_problem(m, m, m, V["parity_seed"], psf, V["noise"])
+        pq = eecmg.VolumePlan(m, m, m, L, psf, delta=q.delta)
+        gq = torch.from_numpy(q.g).cuda()
+        uq = torch.empty_like(gq)
+        pq.restore(gq, uq, stream)
+        itq, _ = pq.stats()
+        pq.close()
+        t0 = time.perf_counter()
+        ref, rit, _ = oracle.cascade3(q.g.astype(np.float64), L, psf, delta=q.delta)
+        t_or = time.perf_counter() - t0
+        n_or = 1
+        while t_or < 5.0:
+            t0 = time.perf_counter()
+            oracle.cascade3(q.g.astype(np.float64), L, psf, delta=q.delta)
+            t_or += time.perf_counter() - t0
+            n_or += 1
+        uqh = uq.double().cpu().numpy()
+        flat = lambda a: a.reshape(a.shape[0], -1)
+        out["parity"] = {
+            "volume": f"{m}^3, same recipe (seed {V['parity_seed']})",
+            "rel_l2": float(np.linalg.norm(uqh - ref) / np.linalg.norm(ref)),
+            "iters": itq, "oracle_iters": rit,
+            "psnr_db": float(oracle.psnr(flat(uqh), flat(q.u))),
+            "oracle_psnr_db": float(oracle.psnr(flat(ref), flat(q.u))),
+            "psnr_g_db": float(oracle.psnr(flat(q.g.astype(np.float64)), flat(q.u))),
+            "full_size_residual": {"reported": res[-1], "oracle_recomputed": res_or},
+            "full_size_psnr_db": float(oracle.psnr(flat(u), flat(p.u))),
+            "full_size_psnr_g_db": float(oracle.psnr(flat(p.g.astype(np.float64)), flat(p.u))),
+            "tolerance": {"rel_l2": 1e-4}}
+        out["cpu_baseline"] = {"value": n_or * m ** 3 / t_or / 1e6, "unit": "Mvoxel/s",
+                               "cores": host_threads(), "kind": "oracle",
+                               "sample": f"{n_or} whole {m}^3 cascades (FP64 C oracle, OpenMP)"}
+        oracle.set_threads(1)
+    plan.close()
+    return out
+
+
 def serving_leg(torch, eecmg, stream, storage, n_req=2000, rate=200.0, seed=5000, chunk=400,
                 budget=64 << 30, slots=64):
     """Serving form: a Poisson stream of restore requests (sizes 256^2..4096^2
@@ -596,6 +718,8 @@ def main():
     ap.add_argument("--no-legs", action="store_true", help="skip the extra legs (512^2, batch64, fused start)")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=2000)
+    ap.add_argument("--no-volume", action="store_true", help="skip the volume leg")
+    ap.add_argument("--volume-only", action="store_true", help="run only the volume leg")
     args = ap.parse_args()
 
     from paper_2311_03010_gb300 import replicas
@@ -620,6 +744,14 @@ def main():
     name = args.workload
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    if args.volume_only:
+        if rank == 0:
+            pk, _ = peaks()
+            vol = volume_leg(torch, eecmg, stream, flush, args.steps or 10, args.warmup, pk,
+                             not args.no_cpu_baseline)
+            print(json.dumps({"volume": vol}), flush=True)
+        replicas.finalize(world)
+        return
     leg = Leg(torch, eecmg, stream, name, args, autotune=not args.no_autotune)
 
     def barrier():
@@ -745,6 +877,10 @@ def main():
         other = "bf16" if args.storage == "fp32" else "fp32"
         serving[f"variant_{other}"] = serving_leg(torch, eecmg, stream, other, n_req=400)
 
+    volume = None
+    if not args.no_volume and rank == 0:
+        volume = volume_leg(torch, eecmg, stream, flush, 10, args.warmup, peak, oracle_ok)
+
     if rank == 0:
         out = {
             "metric": METRIC,
@@ -766,6 +902,7 @@ def main():
             "cpu_baseline": cpu,
             "legs": legs,
             "serving": serving,
+            "volume": volume,
         }
         print(json.dumps(out), flush=True)
     replicas.finalize(world)

@@ -604,6 +604,19 @@ eecmg_status eecmg_vol_restore_host(eecmg_vol_t plan, const float *g_host, float
  */
 eecmg_status eecmg_vol_plan_stats(eecmg_vol_t plan, int *iters_done, double *res_rms);
 
+/*
+ * Per-launch timing of a volume plan.  enable = 1: later restorations launch
+ * eagerly (no graph) with an event pair around each level start and each
+ * level solve; profile_read (synchronises the device) returns per level,
+ * coarsest first, the start's and the solve's milliseconds of the last
+ * restoration and the solve's algorithmic bytes (each operand read or
+ * written once per phase, counted from the iterations it ran); NULL outputs
+ * are skipped.  INVALID_ARG if profiling is off; CUDA.
+ */
+eecmg_status eecmg_vol_plan_profile(eecmg_vol_t plan, int enable);
+eecmg_status eecmg_vol_plan_profile_read(eecmg_vol_t plan, double *start_ms, double *solve_ms,
+                                         double *solve_bytes);
+
 /* Operators of one level, for tests and composition (device buffers of the
  * level's size, not aliased; asynchronous on `stream`):
  *   apply_H      y = H_l x (transpose = 0) or H_l^T x;

@@ -29,6 +29,7 @@
 // a general PSF runs its non-zero taps from the staged tile.  The level start
 // (Pi, P, S, D) is a chain of voxel-parallel kernels.  The cascade is captured
 // once as a CUDA graph.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -46,9 +47,10 @@ constexpr int VR = EECMG_VOL_MAX_RADIUS;
 constexpr int VK = 2 * VR + 1;
 constexpr int TX = 32, TY = 8, TZ = 8;  // output tile (columns, rows, slices)
 
-// Taps of one level in correlation form, y(v) = sum_d C(d) x(v + d), C(d) = K(-d).
+// Taps of one level in correlation form, y(v) = sum_d C(d) x(v + d), C(d) = K(-d),
+// centred at r = the level PSF's largest radius (shorter axes padded with zeros).
 struct VolTaps {
-    int rz, ry, rx;
+    int r;
     int sep;                       // 1: C = cz (x) cy (x) cx
     float cz[VK], cy[VK], cx[VK];  // factors, index d + r
     int ntap;                      // general form: taps in the job's tap list
@@ -82,90 +84,151 @@ struct VolScal {
 };
 
 // -------------------------------------------------------------------- tile
+//
+// A block loops over its output tiles t = blockIdx.x, + gridDim.x, ...  The
+// input window of a tile (the tile plus an r-voxel halo, zero outside the
+// volume) is fetched with 4-byte cp.async (zero fill past the volume) into one
+// of two shared-memory buffers while the previous tile is convolved from the
+// other.  The separable form runs three passes in shared memory: columns over
+// every staged row into B, rows over B into C (C reuses the tile's own input
+// buffer), slices over C; the general form sums its tap list over the window.
 
-__host__ __device__ inline int tile_in_floats(const VolTaps& t) {
-    return (TZ + 2 * t.rz) * (TY + 2 * t.ry) * (TX + 2 * t.rx);
-}
-__host__ __device__ inline int tile_mid_floats(const VolTaps& t) {
-    return t.sep ? (TZ + 2 * t.rz) * (TY + 2 * t.ry) * TX : 0;
-}
-inline size_t tile_smem_bytes(const VolTaps& t) {
-    return sizeof(float) * (size_t)(tile_in_floats(t) + tile_mid_floats(t));
-}
-
-// H x for one tile (tile index t of the job's tiling): stages x with its halo
-// (zero outside the volume), convolves, and calls epi(voxel index, (H x)(v))
-// for each in-volume output of the tile.  All threads of the block call it.
-template <class Epi>
-__device__ __forceinline__ void conv_tile(const VolJob& J, const float* __restrict__ x, int t,
-                                          float* sm, Epi&& epi) {
-    const VolTaps& T = J.taps;
-    const int ntx = (J.w + TX - 1) / TX, nty = (J.h + TY - 1) / TY;
-    const int x0 = (t % ntx) * TX, y0 = ((t / ntx) % nty) * TY, z0 = (t / ntx / nty) * TZ;
-    const int NZ = TZ + 2 * T.rz, NY = TY + 2 * T.ry, AX = TX + 2 * T.rx;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    float* A = sm;
-    // stage x[z0 - rz .. , y0 - ry .. , x0 - rx ..] (zero fill outside)
-    for (int row = warp; row < NZ * NY; row += NTHREADS / 32) {
-        const int za = row / NY, ya = row - za * NY;
-        const int gz = z0 - T.rz + za, gy = y0 - T.ry + ya;
-        const bool rin = gz >= 0 && gz < J.d && gy >= 0 && gy < J.h;
-        const float* src = x + ((long long)gz * J.h + gy) * J.w;
-        for (int xa = lane; xa < AX; xa += 32) {
-            const int gx = x0 - T.rx + xa;
-            A[row * AX + xa] = (rin && gx >= 0 && gx < J.w) ? __ldcg(src + gx) : 0.f;
-        }
-    }
-    __syncthreads();
-    const int xo = lane;
-    if (T.sep) {
-        float* B = sm + tile_in_floats(T);
-        // columns: B[z][y][x] = sum_dx cx A[z][y][x + rx + dx], all staged rows
-        for (int row = warp; row < NZ * NY; row += NTHREADS / 32) {
-            const float* a = A + row * AX + xo;
-            float s = 0.f;
-            for (int q = 0; q <= 2 * T.rx; ++q) s = fmaf(T.cx[q], a[q], s);
-            B[row * TX + xo] = s;
-        }
-        __syncthreads();
-        // rows: C[z][y][x] = sum_dy cy B[z][y + ry + dy][x], C over A's space
-        float* C = A;
-        for (int row = warp; row < NZ * TY; row += NTHREADS / 32) {
-            const int za = row / TY, yo = row - za * TY;
-            const float* b = B + (za * NY + yo) * TX + xo;
-            float s = 0.f;
-            for (int p = 0; p <= 2 * T.ry; ++p) s = fmaf(T.cy[p], b[p * TX], s);
-            C[row * TX + xo] = s;
-        }
-        __syncthreads();
-        // slices: out[z][y][x] = sum_dz cz C[z + rz + dz][y][x]
-        for (int row = warp; row < TZ * TY; row += NTHREADS / 32) {
-            const int zo = row / TY, yo = row - zo * TY;
-            const int gz = z0 + zo, gy = y0 + yo, gx = x0 + xo;
-            const float* c = C + (zo * TY + yo) * TX + xo;
-            float s = 0.f;
-            for (int o = 0; o <= 2 * T.rz; ++o) s = fmaf(T.cz[o], c[o * TY * TX], s);
-            if (gz < J.d && gy < J.h && gx < J.w) epi(((long long)gz * J.h + gy) * J.w + gx, s);
-        }
-    } else {
-        for (int row = warp; row < TZ * TY; row += NTHREADS / 32) {
-            const int zo = row / TY, yo = row - zo * TY;
-            const int gz = z0 + zo, gy = y0 + yo, gx = x0 + xo;
-            const float* a = A + ((zo + T.rz) * NY + yo + T.ry) * AX + xo + T.rx;
-            float s = 0.f;
-            for (int k = 0; k < T.ntap; ++k) {
-                const int4 tp = __ldg(J.gtaps + k);
-                s = fmaf(__int_as_float(tp.w), a[(tp.x * NY + tp.y) * AX + tp.z], s);
-            }
-            if (gz < J.d && gy < J.h && gx < J.w) epi(((long long)gz * J.h + gy) * J.w + gx, s);
-        }
-    }
-    __syncthreads();  // the next tile restages A
-}
+template <int R>
+struct VolTile {
+    static constexpr int NZ = TZ + 2 * R, NY = TY + 2 * R, AX = TX + 2 * R;
+    static constexpr int IN = NZ * NY * AX;  // one input buffer
+    static constexpr int MID = NZ * NY * TX; // B
+    static constexpr size_t bytes(bool sep) { return sizeof(float) * (2 * (size_t)IN + (sep ? MID : 0)); }
+};
 
 __device__ __forceinline__ int num_tiles(const VolJob& J) {
     return ((J.w + TX - 1) / TX) * ((J.h + TY - 1) / TY) * ((J.d + TZ - 1) / TZ);
 }
+
+__device__ __forceinline__ void tile_origin(const VolJob& J, int t, int& x0, int& y0, int& z0) {
+    const int ntx = (J.w + TX - 1) / TX, nty = (J.h + TY - 1) / TY;
+    x0 = (t % ntx) * TX;
+    y0 = ((t / ntx) % nty) * TY;
+    z0 = (t / ntx / nty) * TZ;
+}
+
+template <int R>
+__device__ __forceinline__ void stage_tile(const VolJob& J, const float* __restrict__ x, int t, float* A) {
+    using T = VolTile<R>;
+    int x0, y0, z0;
+    tile_origin(J, t, x0, y0, z0);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned int base = (unsigned int)__cvta_generic_to_shared(A);
+    for (int row = warp; row < T::NZ * T::NY; row += NTHREADS / 32) {
+        const int za = row / T::NY, ya = row - za * T::NY;
+        const int gz = z0 - R + za, gy = y0 - R + ya;
+        const bool rin = gz >= 0 && gz < J.d && gy >= 0 && gy < J.h;
+        const float* src = x + ((long long)(rin ? gz : 0) * J.h + (rin ? gy : 0)) * J.w;
+#pragma unroll
+        for (int xa = lane; xa < T::AX; xa += 32) {
+            const int gx = x0 - R + xa;
+            const bool in = rin && gx >= 0 && gx < J.w;
+            const float* g = in ? src + gx : x;  // a valid address either way
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(
+                             base + 4u * (unsigned int)(row * T::AX + xa)),
+                         "l"(g), "r"(in ? 4 : 0)
+                         : "memory");
+        }
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+// Convolves the staged tile t (buffer A) and calls epi(voxel index, (H x)(v))
+// for every in-volume output.  Ends with __syncthreads().
+template <int R, class Epi>
+__device__ __forceinline__ void compute_tile(const VolJob& J, int t, float* A, float* B, Epi&& epi) {
+    using T = VolTile<R>;
+    const VolTaps& K = J.taps;
+    int x0, y0, z0;
+    tile_origin(J, t, x0, y0, z0);
+    const int xo = threadIdx.x & 31, warp = threadIdx.x >> 5;  // warp = output row within a slice
+    const int gx = x0 + xo, gy = y0 + warp;
+    if (K.sep) {
+        // columns: B[z][y][x] = sum_dx cx A[z][y][x + R + dx], every staged row
+        constexpr int ROWS = T::NZ * T::NY, U = 4;
+        for (int r0 = warp; r0 < ROWS; r0 += 8 * U) {
+            float s[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) s[u] = 0.f;
+#pragma unroll
+            for (int q = 0; q <= 2 * R; ++q)
+#pragma unroll
+                for (int u = 0; u < U; ++u)
+                    if (r0 + 8 * u < ROWS) s[u] = fmaf(K.cx[q], A[(r0 + 8 * u) * T::AX + xo + q], s[u]);
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+                if (r0 + 8 * u < ROWS) B[(r0 + 8 * u) * TX + xo] = s[u];
+        }
+        __syncthreads();
+        // rows: C[z][y][x] = sum_dy cy B[z][y + R + dy][x]; this warp's y, every staged slice
+        float* C = A;
+#pragma unroll
+        for (int za = 0; za < T::NZ; ++za) {
+            const float* b = B + (za * T::NY + warp) * TX + xo;
+            float s = 0.f;
+#pragma unroll
+            for (int p = 0; p <= 2 * R; ++p) s = fmaf(K.cy[p], b[p * TX], s);
+            C[(za * TY + warp) * TX + xo] = s;
+        }
+        __syncthreads();
+        // slices: out[z][y][x] = sum_dz cz C[z + R + dz][y][x]
+        float s[TZ];
+#pragma unroll
+        for (int zo = 0; zo < TZ; ++zo) {
+            s[zo] = 0.f;
+#pragma unroll
+            for (int o = 0; o <= 2 * R; ++o) s[zo] = fmaf(K.cz[o], C[((zo + o) * TY + warp) * TX + xo], s[zo]);
+        }
+        if (gy < J.h && gx < J.w) {
+#pragma unroll
+            for (int zo = 0; zo < TZ; ++zo)
+                if (z0 + zo < J.d) epi(((long long)(z0 + zo) * J.h + gy) * J.w + gx, s[zo]);
+        }
+    } else {
+        for (int zo = 0; zo < TZ; ++zo) {
+            const float* a = A + ((zo + R) * T::NY + warp + R) * T::AX + xo + R;
+            float s = 0.f;
+            for (int k = 0; k < K.ntap; ++k) {
+                const int4 tp = __ldg(J.gtaps + k);
+                s = fmaf(__int_as_float(tp.w), a[(tp.x * T::NY + tp.y) * T::AX + tp.z], s);
+            }
+            if (z0 + zo < J.d && gy < J.h && gx < J.w) epi(((long long)(z0 + zo) * J.h + gy) * J.w + gx, s);
+        }
+    }
+    __syncthreads();  // the buffers are restaged after this
+}
+
+// One convolution phase: H x over all the block's tiles, the next tile's
+// window in flight while the current one is convolved.
+template <int R, class Epi>
+__device__ __forceinline__ void conv_phase(const VolJob& J, const float* __restrict__ x, float* sm,
+                                           Epi&& epi) {
+    using T = VolTile<R>;
+    const int ntiles = num_tiles(J), nb = gridDim.x;
+    int t = blockIdx.x;
+    if (t >= ntiles) return;  // the whole block
+    float* B = sm + 2 * T::IN;
+    int buf = 0;
+    stage_tile<R>(J, x, t, sm);
+    for (; t < ntiles; t += nb) {
+        if (t + nb < ntiles) {
+            stage_tile<R>(J, x, t + nb, sm + (buf ^ 1) * T::IN);
+            asm volatile("cp.async.wait_group 1;" ::: "memory");
+        } else {
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
+        }
+        __syncthreads();
+        compute_tile<R>(J, t, sm + buf * T::IN, B, epi);
+        buf ^= 1;
+    }
+}
+
+
 
 // per-thread compensated sum (cascaded: the rounding errors are kept in lo)
 __device__ __forceinline__ void acc_add(DF& a, float v) {
@@ -176,6 +239,35 @@ __device__ __forceinline__ void acc_add(DF& a, float v) {
 
 __device__ __forceinline__ double tot2(const DF (&t)[4], int j) {
     return df_to_double(t[2 * j]) + df_to_double(t[2 * j + 1]);
+}
+
+// A vector phase over float4 elements i = gtid, gtid + gstr, ...: two elements
+// per step, every load of both issued before the first store (the stores may
+// alias nothing the loads need, but the compiler cannot prove it).
+// f(x, y) maps the NL loaded values to the NS stored ones.
+template <int NL, int NS, class F>
+__device__ __forceinline__ void vec_phase(long long n4, long long gtid, long long gstr,
+                                          const float4* const (&in)[NL], float4* const (&out)[NS],
+                                          F&& f) {
+    for (long long i = gtid; i < n4; i += 2 * gstr) {
+        const long long j = i + gstr;
+        const bool second = j < n4;
+        float4 x0[NL], x1[NL], y[NS];
+#pragma unroll
+        for (int k = 0; k < NL; ++k) x0[k] = __ldcg(in[k] + i);
+        if (second) {
+#pragma unroll
+            for (int k = 0; k < NL; ++k) x1[k] = __ldcg(in[k] + j);
+        }
+        f(x0, y);
+#pragma unroll
+        for (int k = 0; k < NS; ++k) out[k][i] = y[k];
+        if (second) {
+            f(x1, y);
+#pragma unroll
+            for (int k = 0; k < NS; ++k) out[k][j] = y[k];
+        }
+    }
 }
 
 // ------------------------------------------------------------- level solve
@@ -196,11 +288,11 @@ __device__ __forceinline__ bool pos_finite(double x) { return x > 0.0 && isfinit
 //   q_{k+1} = z - b1 q_k - b2 q_{k-1}, p_{k+1} = q_k - b1 p_k - b2 p_{k-1},
 //   a = <r,q_{k+1}>/<q_{k+1},q_{k+1}>, u += a p_{k+1}, r -= a q_{k+1}.
 // p and q live in rings of three buffers: p_k = P[(k - 1) % 3].
+template <int R>
 __global__ void __launch_bounds__(NTHREADS) k_vol_mr2(VolJob J) {
     extern __shared__ __align__(16) float sm[];
     __shared__ VolScal S;
     const unsigned int nb = gridDim.x, bid = blockIdx.x;
-    const int ntiles = num_tiles(J);
     const long long gtid = (long long)bid * NTHREADS + threadIdx.x, gstr = (long long)nb * NTHREADS;
     unsigned int phase = 0;
     bool ok = true;
@@ -239,8 +331,7 @@ __global__ void __launch_bounds__(NTHREADS) k_vol_mr2(VolJob J) {
                 acc_add(acc[1], dot4(g, g, 0.f));
             }
         } else {
-            for (int t = bid; t < ntiles; t += nb)
-                conv_tile(J, J.u, t, sm, [&](long long i, float hx) {
+            conv_phase<R>(J, J.u, sm, [&](long long i, float hx) {
                     const float g = __ldcg(J.g + i);
                     const float r = g - hx;
                     J.R[i] = r;
@@ -257,16 +348,14 @@ __global__ void __launch_bounds__(NTHREADS) k_vol_mr2(VolJob J) {
     }
     if (ok && !S.done) {
         // p1 = H r0
-        for (int t = bid; t < ntiles; t += nb)
-            conv_tile(J, J.R, t, sm, [&](long long i, float hx) { J.P[0][i] = hx; });
+        conv_phase<R>(J, J.R, sm, [&](long long i, float hx) { J.P[0][i] = hx; });
         DF none[2] = {{0.f, 0.f}, {0.f, 0.f}};
         ok = reduce(none, [&](const DF (&)[4]) {});
     }
     if (ok && !S.done) {
         // q1 = H p1; <q,q>, <r,q>
         DF acc[2] = {{0.f, 0.f}, {0.f, 0.f}};
-        for (int t = bid; t < ntiles; t += nb)
-            conv_tile(J, J.P[0], t, sm, [&](long long i, float hx) {
+        conv_phase<R>(J, J.P[0], sm, [&](long long i, float hx) {
                 J.Q[0][i] = hx;
                 acc_add(acc[0], hx * hx);
                 acc_add(acc[1], __ldcg(J.R + i) * hx);
@@ -285,16 +374,14 @@ __global__ void __launch_bounds__(NTHREADS) k_vol_mr2(VolJob J) {
         // u += a p1, r -= a q1; ||r||^2
         DF acc[2] = {{0.f, 0.f}, {0.f, 0.f}};
         const float a = (float)S.a;
-        const float4* p4 = reinterpret_cast<const float4*>(J.P[0]);
-        const float4* q4 = reinterpret_cast<const float4*>(J.Q[0]);
-        for (long long i = gtid; i < J.n4; i += gstr) {
-            const float4 p = __ldcg(p4 + i), q = __ldcg(q4 + i), u = __ldcg(u4 + i),
-                         r = __ldcg(r4 + i);
-            const float4 rn = fma4(-a, q, r);
-            u4[i] = fma4(a, p, u);
-            r4[i] = rn;
-            acc_add(acc[0], dot4(rn, rn, 0.f));
-        }
+        const float4* const in[4] = {reinterpret_cast<const float4*>(J.P[0]),
+                                     reinterpret_cast<const float4*>(J.Q[0]), u4, r4};
+        float4* const out[2] = {u4, r4};
+        vec_phase<4, 2>(J.n4, gtid, gstr, in, out, [&](const float4 (&x)[4], float4 (&y)[2]) {
+            y[0] = fma4(a, x[0], x[2]);
+            y[1] = fma4(-a, x[1], x[3]);
+            acc_add(acc[0], dot4(y[1], y[1], 0.f));
+        });
         ok = reduce(acc, [&](const DF (&t)[4]) {
             S.rr = tot2(t, 0);
             S.k = 1;
@@ -311,8 +398,7 @@ __global__ void __launch_bounds__(NTHREADS) k_vol_mr2(VolJob J) {
         // z = H q_k; <z, q_k>, <z, q_{k-1}>
         {
             DF acc[2] = {{0.f, 0.f}, {0.f, 0.f}};
-            for (int t = bid; t < ntiles; t += nb)
-                conv_tile(J, q, t, sm, [&](long long i, float hx) {
+            conv_phase<R>(J, q, sm, [&](long long i, float hx) {
                     J.Z[i] = hx;
                     acc_add(acc[0], hx * __ldcg(q + i));
                     if (two) acc_add(acc[1], hx * __ldcg(qp + i));
@@ -327,25 +413,29 @@ __global__ void __launch_bounds__(NTHREADS) k_vol_mr2(VolJob J) {
         {
             DF acc[2] = {{0.f, 0.f}, {0.f, 0.f}};
             const float b1 = (float)S.b1, b2 = (float)S.b2;
-            const float4* z4 = reinterpret_cast<const float4*>(J.Z);
-            const float4* qc = reinterpret_cast<const float4*>(J.Q[cur]);
-            const float4* qo = reinterpret_cast<const float4*>(J.Q[prv]);
-            const float4* pc = reinterpret_cast<const float4*>(J.P[cur]);
-            const float4* po = reinterpret_cast<const float4*>(J.P[prv]);
-            float4* qn = reinterpret_cast<float4*>(J.Q[nxt]);
-            float4* pn = reinterpret_cast<float4*>(J.P[nxt]);
-            for (long long i = gtid; i < J.n4; i += gstr) {
-                const float4 z = __ldcg(z4 + i), qv = __ldcg(qc + i), pv = __ldcg(pc + i),
-                             r = __ldcg(r4 + i);
-                float4 a = fma4(-b1, qv, z), b = fma4(-b1, pv, qv);
-                if (two) {
-                    a = fma4(-b2, __ldcg(qo + i), a);
-                    b = fma4(-b2, __ldcg(po + i), b);
-                }
-                qn[i] = a;
-                pn[i] = b;
-                acc_add(acc[0], dot4(a, a, 0.f));
-                acc_add(acc[1], dot4(r, a, 0.f));
+            float4* const out[2] = {reinterpret_cast<float4*>(J.Q[nxt]), reinterpret_cast<float4*>(J.P[nxt])};
+            if (two) {
+                const float4* const in[6] = {reinterpret_cast<const float4*>(J.Z),
+                                             reinterpret_cast<const float4*>(J.Q[cur]),
+                                             reinterpret_cast<const float4*>(J.P[cur]), r4,
+                                             reinterpret_cast<const float4*>(J.Q[prv]),
+                                             reinterpret_cast<const float4*>(J.P[prv])};
+                vec_phase<6, 2>(J.n4, gtid, gstr, in, out, [&](const float4 (&x)[6], float4 (&y)[2]) {
+                    y[0] = fma4(-b2, x[4], fma4(-b1, x[1], x[0]));
+                    y[1] = fma4(-b2, x[5], fma4(-b1, x[2], x[1]));
+                    acc_add(acc[0], dot4(y[0], y[0], 0.f));
+                    acc_add(acc[1], dot4(x[3], y[0], 0.f));
+                });
+            } else {
+                const float4* const in[4] = {reinterpret_cast<const float4*>(J.Z),
+                                             reinterpret_cast<const float4*>(J.Q[cur]),
+                                             reinterpret_cast<const float4*>(J.P[cur]), r4};
+                vec_phase<4, 2>(J.n4, gtid, gstr, in, out, [&](const float4 (&x)[4], float4 (&y)[2]) {
+                    y[0] = fma4(-b1, x[1], x[0]);
+                    y[1] = fma4(-b1, x[2], x[1]);
+                    acc_add(acc[0], dot4(y[0], y[0], 0.f));
+                    acc_add(acc[1], dot4(x[3], y[0], 0.f));
+                });
             }
             ok = reduce(acc, [&](const DF (&t)[4]) {
                 const double qqn = tot2(t, 0), rqn = tot2(t, 1);
@@ -362,16 +452,14 @@ __global__ void __launch_bounds__(NTHREADS) k_vol_mr2(VolJob J) {
         {
             DF acc[2] = {{0.f, 0.f}, {0.f, 0.f}};
             const float a = (float)S.a;
-            const float4* pn = reinterpret_cast<const float4*>(J.P[nxt]);
-            const float4* qn = reinterpret_cast<const float4*>(J.Q[nxt]);
-            for (long long i = gtid; i < J.n4; i += gstr) {
-                const float4 p = __ldcg(pn + i), qv = __ldcg(qn + i), u = __ldcg(u4 + i),
-                             r = __ldcg(r4 + i);
-                const float4 rn = fma4(-a, qv, r);
-                u4[i] = fma4(a, p, u);
-                r4[i] = rn;
-                acc_add(acc[0], dot4(rn, rn, 0.f));
-            }
+            const float4* const in[4] = {reinterpret_cast<const float4*>(J.P[nxt]),
+                                         reinterpret_cast<const float4*>(J.Q[nxt]), u4, r4};
+            float4* const out[2] = {u4, r4};
+            vec_phase<4, 2>(J.n4, gtid, gstr, in, out, [&](const float4 (&x)[4], float4 (&y)[2]) {
+                y[0] = fma4(a, x[0], x[2]);
+                y[1] = fma4(-a, x[1], x[3]);
+                acc_add(acc[0], dot4(y[1], y[1], 0.f));
+            });
             ok = reduce(acc, [&](const DF (&t)[4]) {
                 S.rr = tot2(t, 0);
                 S.qqp = S.qq;
@@ -390,10 +478,14 @@ __global__ void __launch_bounds__(NTHREADS) k_vol_mr2(VolJob J) {
 }
 
 // H x (or H^T x with the transposed taps) of a whole level, one tile per block.
+template <int R>
 __global__ void __launch_bounds__(NTHREADS) k_vol_apply(VolJob J, const float* __restrict__ x,
                                                         float* __restrict__ y) {
     extern __shared__ __align__(16) float sm[];
-    conv_tile(J, x, blockIdx.x, sm, [&](long long i, float hx) { y[i] = hx; });
+    stage_tile<R>(J, x, blockIdx.x, sm);
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    __syncthreads();
+    compute_tile<R>(J, blockIdx.x, sm, sm + 2 * VolTile<R>::IN, [&](long long i, float hx) { y[i] = hx; });
 }
 
 // ------------------------------------------------------------ level start
@@ -661,6 +753,11 @@ struct eecmg_vol_s {
     std::vector<int> grid;                             // level solve blocks
     cudaStream_t cap = nullptr;
     cudaGraphExec_t gexec = nullptr;
+    // optional per-launch timing (eager launches with an event pair around
+    // each level start and each level solve)
+    bool prof = false;
+    std::vector<cudaEvent_t> ev;  // [4l .. 4l+3]: start begin/end, solve begin/end
+    std::vector<int> ev_used;
 };
 
 namespace {
@@ -679,9 +776,8 @@ void make_vol_taps(const std::vector<double>& K, int kd, int kh, int kw, bool tr
                    VolTaps* t, std::vector<int4>* list) {
     std::memset(t, 0, sizeof(VolTaps));
     const int rz = kd / 2, ry = kh / 2, rx = kw / 2;
-    t->rz = rz;
-    t->ry = ry;
-    t->rx = rx;
+    const int r = std::max(rz, std::max(ry, rx));
+    t->r = r;
     auto C = [&](int o, int p, int q) {
         if (!transpose) { o = -o; p = -p; q = -q; }
         return K[((size_t)(o + rz) * kh + (p + ry)) * kw + (q + rx)];
@@ -714,9 +810,9 @@ void make_vol_taps(const std::vector<double>& K, int kd, int kh, int kw, bool tr
                         break;
                     }
         if (sep) {
-            for (int o = 0; o < kd; ++o) t->cz[o] = (float)a[o];
-            for (int p = 0; p < kh; ++p) t->cy[p] = (float)b[p];
-            for (int q = 0; q < kw; ++q) t->cx[q] = (float)c[q];
+            for (int o = 0; o < kd; ++o) t->cz[o - rz + r] = (float)a[o];
+            for (int p = 0; p < kh; ++p) t->cy[p - ry + r] = (float)b[p];
+            for (int q = 0; q < kw; ++q) t->cx[q - rx + r] = (float)c[q];
         }
     }
     t->sep = sep ? 1 : 0;
@@ -738,6 +834,23 @@ void make_vol_taps(const std::vector<double>& K, int kd, int kh, int kw, bool tr
 }
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+size_t tile_bytes(const VolTaps& t) {
+    const int NZ = TZ + 2 * t.r, NY = TY + 2 * t.r, AX = TX + 2 * t.r;
+    return sizeof(float) * (2 * (size_t)NZ * NY * AX + (t.sep ? (size_t)NZ * NY * TX : 0));
+}
+
+// The kernels instantiated for every radius 0 .. EECMG_VOL_MAX_RADIUS.
+template <int... Rs>
+struct VolKernels {
+    const void* solve[sizeof...(Rs)] = {(const void*)k_vol_mr2<Rs>...};
+    const void* apply[sizeof...(Rs)] = {(const void*)k_vol_apply<Rs>...};
+};
+const VolKernels<0, 1, 2, 3, 4, 5, 6>& vol_kernels() {
+    static_assert(VR == 6, "instantiate every radius");
+    static const VolKernels<0, 1, 2, 3, 4, 5, 6> k;
+    return k;
+}
 
 int blocks_for(long long n) {
     long long b = (n + 255) / 256;
@@ -780,18 +893,20 @@ eecmg_status launch_solve(eecmg_vol_s* P, int l, bool zero_start, cudaStream_t s
     VolJob J = make_job(P, l, false);
     J.zero_start = zero_start ? 1 : 0;
     void* args[] = {&J};
-    const size_t smem = tile_smem_bytes(J.taps);
-    VCK(cudaLaunchCooperativeKernel((const void*)k_vol_mr2, dim3(P->grid[l]), dim3(NTHREADS), args,
-                                    smem, s));
+    const size_t smem = tile_bytes(J.taps);
+    VCK(cudaLaunchCooperativeKernel(vol_kernels().solve[J.taps.r], dim3(P->grid[l]), dim3(NTHREADS),
+                                    args, smem, s));
     return EECMG_OK;
 }
 
 eecmg_status launch_apply(eecmg_vol_s* P, int l, bool transpose, const float* x, float* y,
                           cudaStream_t s) {
     VolJob J = make_job(P, l, transpose);
-    const size_t smem = tile_smem_bytes(J.taps);
-    k_vol_apply<<<level_tiles(J), NTHREADS, smem, s>>>(J, x, y);
-    VCK(cudaGetLastError());
+    const size_t smem = tile_bytes(J.taps);
+    const float* xx = x;
+    void* args[] = {&J, (void*)&xx, (void*)&y};
+    VCK(cudaLaunchKernel(vol_kernels().apply[J.taps.r], dim3(level_tiles(J)), dim3(NTHREADS), args,
+                         smem, s));
     return EECMG_OK;
 }
 
@@ -824,6 +939,12 @@ eecmg_status launch_start(eecmg_vol_s* P, int l, const float* u1, const float* u
 
 eecmg_status cascade(eecmg_vol_s* P, cudaStream_t s) {
     const int L = P->L;
+    auto mark = [&](int l, int which) -> eecmg_status {
+        if (!P->prof) return EECMG_OK;
+        VCK(cudaEventRecord(P->ev[4 * l + which], s));
+        P->ev_used[4 * l + which] = 1;
+        return EECMG_OK;
+    };
     for (int l = L - 1; l > 0; --l) {
         k_vol_restrict<<<blocks_for(P->n[l - 1]), 256, 0, s>>>(P->g[l], P->hs[l], P->ws[l],
                                                              P->g[l - 1], P->ds[l - 1],
@@ -831,20 +952,41 @@ eecmg_status cascade(eecmg_vol_s* P, cudaStream_t s) {
         VCK(cudaGetLastError());
     }
     for (int l = 0; l < L; ++l) {
+        eecmg_status st;
         if (l >= 2) {
-            eecmg_status st = launch_start(P, l, P->u[l - 1], P->u[l - 2], P->u[l], s);
+            if ((st = mark(l, 0)) != EECMG_OK) return st;
+            st = launch_start(P, l, P->u[l - 1], P->u[l - 2], P->u[l], s);
             if (st != EECMG_OK) return st;
+            if ((st = mark(l, 1)) != EECMG_OK) return st;
         }
-        eecmg_status st = launch_solve(P, l, l < 2, s);
+        if ((st = mark(l, 2)) != EECMG_OK) return st;
+        st = launch_solve(P, l, l < 2, s);
         if (st != EECMG_OK) return st;
+        if ((st = mark(l, 3)) != EECMG_OK) return st;
     }
     return EECMG_OK;
+}
+
+// Algorithmic bytes of level l's solve from the iterations it ran (each
+// operand read or written once per phase, FP32): r0 12 per voxel; p1 = H r 8;
+// q1 = H p with <r, q> 12; the first update 24; then per iteration k >= 1:
+// z = H q_k with <z, q_k> (and <z, q_{k-1}> for k >= 2) 8 (12), the new
+// directions 24 (32), the update 24.  A breakdown ends a level after the
+// phase that found it.
+double solve_bytes(const eecmg_vol_s* P, int l, int k, int reason) {
+    double b = 12.0;
+    const bool ran_first = k >= 1 || reason == 2;
+    if (ran_first) b += 8.0 + 12.0;
+    if (k >= 1) b += 24.0;
+    for (int j = 1; j < k; ++j) b += (j >= 2 ? 12.0 : 8.0) + (j >= 2 ? 32.0 : 24.0) + 24.0;
+    if (k >= 1 && reason == 2) b += (k >= 2 ? 12.0 : 8.0) + (k >= 2 ? 32.0 : 24.0);
+    return b * (double)P->n[l];
 }
 
 // The cascade on the workspace's g_L (filled by the caller), as one CUDA graph
 // captured at the first call (use_graph) or as plain launches.
 eecmg_status run_cascade(eecmg_vol_s* P, cudaStream_t s) {
-    if (!P->opt.use_graph) return cascade(P, s);
+    if (!P->opt.use_graph || P->prof) return cascade(P, s);
     if (!P->gexec) {
         VCK(cudaStreamBeginCapture(P->cap, cudaStreamCaptureModeThreadLocal));
         eecmg_status st = cascade(P, P->cap);
@@ -1000,13 +1142,16 @@ eecmg_status eecmg_vol_plan(int width, int height, int depth, int levels, const 
     P->grid.resize(L);
     int maxgrid = 1;
     for (int l = 0; l < L; ++l) {
-        const size_t smem = tile_smem_bytes(P->taps[l]);
-        e = cudaFuncSetAttribute(k_vol_mr2, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        const int r = std::max(P->taps[l].r, P->tapsT[l].r);
+        const size_t smem = std::max(tile_bytes(P->taps[l]), tile_bytes(P->tapsT[l]));
+        e = cudaFuncSetAttribute(vol_kernels().solve[r], cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
         if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_vol_apply, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+            e = cudaFuncSetAttribute(vol_kernels().apply[r], cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem);
         int per = 0;
         if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_vol_mr2, NTHREADS, smem);
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, vol_kernels().solve[r], NTHREADS, smem);
         if (e != cudaSuccess || per < 1) {
             delete P;
             return set_error(EECMG_ERR_CUDA, "eecmg_vol_plan: level solve does not fit an SM");
@@ -1087,6 +1232,7 @@ eecmg_status eecmg_vol_plan_destroy(eecmg_vol_t P) {
     cudaDeviceSynchronize();
     if (P->gexec) cudaGraphExecDestroy(P->gexec);
     if (P->cap) cudaStreamDestroy(P->cap);
+    for (cudaEvent_t e : P->ev) cudaEventDestroy(e);
     if (P->wsp) cudaFree(P->wsp);
     delete P;
     return EECMG_OK;
@@ -1210,6 +1356,36 @@ eecmg_status eecmg_vol_level_solve(eecmg_vol_t P, int level, const float* g, flo
     P->m[level] = keep;
     if (st != EECMG_OK) return st;
     VCK(cudaMemcpyAsync(u, P->u[level], bytes, cudaMemcpyDeviceToDevice, s));
+    return EECMG_OK;
+}
+
+eecmg_status eecmg_vol_plan_profile(eecmg_vol_t P, int enable) {
+    if (!P) return set_error(EECMG_ERR_INVALID_ARG, "eecmg_vol_plan_profile: NULL plan");
+    if (enable && P->ev.empty()) {
+        P->ev.resize(4 * (size_t)P->L);
+        for (auto& e : P->ev) VCK(cudaEventCreate(&e));
+    }
+    P->ev_used.assign(4 * (size_t)P->L, 0);
+    P->prof = enable != 0;
+    return EECMG_OK;
+}
+
+eecmg_status eecmg_vol_plan_profile_read(eecmg_vol_t P, double* start_ms, double* solve_ms,
+                                         double* solve_bytes_out) {
+    if (!P || !P->prof) return set_error(EECMG_ERR_INVALID_ARG, "eecmg_vol_plan_profile_read: profiling is off");
+    VCK(cudaDeviceSynchronize());
+    std::vector<double> h(4 * (size_t)P->L);
+    VCK(cudaMemcpy(h.data(), P->out, h.size() * sizeof(double), cudaMemcpyDeviceToHost));
+    for (int l = 0; l < P->L; ++l) {
+        float a = 0.f, b = 0.f;
+        if (P->ev_used[4 * l] && P->ev_used[4 * l + 1])
+            VCK(cudaEventElapsedTime(&a, P->ev[4 * l], P->ev[4 * l + 1]));
+        if (P->ev_used[4 * l + 2] && P->ev_used[4 * l + 3])
+            VCK(cudaEventElapsedTime(&b, P->ev[4 * l + 2], P->ev[4 * l + 3]));
+        if (start_ms) start_ms[l] = a;
+        if (solve_ms) solve_ms[l] = b;
+        if (solve_bytes_out) solve_bytes_out[l] = solve_bytes(P, l, (int)h[4 * l], (int)h[4 * l + 2]);
+    }
     return EECMG_OK;
 }
 

@@ -130,6 +130,8 @@ _SIGS = {
     "eecmg_vol_smooth": [_VP, _I, _VP, _VP, _VP],
     "eecmg_vol_denoise": [_VP, _I, _VP, _VP, _VP],
     "eecmg_vol_level_solve": [_VP, _I, _VP, _VP, _I, _VP],
+    "eecmg_vol_plan_profile": [_VP, _I],
+    "eecmg_vol_plan_profile_read": [_VP, _PD, _PD, _PD],
     "eecmg_last_error": [],
     "eecmg_version": [],
 }
@@ -509,6 +511,18 @@ def eecmg_vol_plan_stats(plan):
     res = (_D * L)()
     _call("eecmg_vol_plan_stats", plan, it, res)
     return list(it), list(res)
+
+
+def eecmg_vol_plan_profile(plan, enable=1):
+    _call("eecmg_vol_plan_profile", plan, int(enable))
+
+
+def eecmg_vol_plan_profile_read(plan):
+    """Per level: (start ms, solve ms, solve algorithmic bytes) of the last restoration."""
+    L = eecmg_vol_plan_info(plan)["levels"]
+    a, b, c = (_D * L)(), (_D * L)(), (_D * L)()
+    _call("eecmg_vol_plan_profile_read", plan, a, b, c)
+    return list(a), list(b), list(c)
 
 
 def eecmg_vol_apply_H(plan, level, x, y, transpose=0, stream=None):
