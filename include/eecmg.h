@@ -541,7 +541,8 @@ typedef struct eecmg_vol_s *eecmg_vol_t;
 
 /*
  * Creates a restoration plan for width x height x depth volumes, stored
- * slice-major: x[(k * height + i) * width + j] (FP32, [0, 255] grey scale).
+ * slice-major: x[(k * height + i) * width + j] (FP32, [0, 255] grey scale),
+ * at most 2^31 voxels and 65535 slices.
  * The cascade is Algorithm 2 with, per level:
  *   restriction  coarse (a, b, c) = fine (2a, 2b, 2c) (Eqs. 12-13 per axis);
  *   H_l          zero-boundary 3-D convolution with

@@ -490,84 +490,78 @@ __global__ void __launch_bounds__(NTHREADS) k_vol_apply(VolJob J, const float* _
 
 // ------------------------------------------------------------ level start
 
-__global__ void k_vol_restrict(const float* __restrict__ f, int hf, int wf, float* __restrict__ c,
-                               int dc, int hc, int wc) {
-    const long long n = (long long)dc * hc * wc;
-    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < n;
-         v += (long long)gridDim.x * blockDim.x) {
-        const int b = (int)(v % wc);
-        const long long r = v / wc;
-        const int a = (int)(r % hc), s = (int)(r / hc);
-        c[v] = f[((long long)(2 * s) * hf + 2 * a) * wf + 2 * b];
-    }
+// Voxel kernels run on a 3-D grid of 32 x 8 blocks: x = column, y = row,
+// z = slice (no index division).
+constexpr int VBX = 32, VBY = 8;
+
+#define VOXEL_INDEX(d, h, w)                                          \
+    const int j = blockIdx.x * VBX + (threadIdx.x & (VBX - 1));       \
+    const int i = blockIdx.y * VBY + (threadIdx.x / VBX);             \
+    const int k = blockIdx.z;                                         \
+    if (j >= (w) || i >= (h)) return;                                 \
+    const long long v = ((long long)k * (h) + i) * (w) + j;
+
+__global__ void __launch_bounds__(VBX * VBY) k_vol_restrict(const float* __restrict__ f, int hf, int wf,
+                                                            float* __restrict__ c, int dc, int hc, int wc) {
+    VOXEL_INDEX(dc, hc, wc)
+    c[v] = f[((long long)(2 * k) * hf + 2 * i) * wf + 2 * j];
 }
 
 // Pi: out = u1 + (1/4) * mean of the level-(l-2) differences d over the cell's
 // eight corners (indices past the last level-(l-2) node clamp to it).
-__global__ void k_vol_pi(const float* __restrict__ u1, int d1, int h1, int w1,
-                         const float* __restrict__ u2, int d2, int h2, int w2,
-                         float* __restrict__ out) {
-    const long long n = (long long)d1 * h1 * w1;
-    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < n;
-         v += (long long)gridDim.x * blockDim.x) {
-        const int b = (int)(v % w1);
-        const long long rr = v / w1;
-        const int a = (int)(rr % h1), c = (int)(rr / h1);
-        const int C0 = c >> 1, C1 = (c & 1) ? min(C0 + 1, d2 - 1) : C0;
-        const int A0 = a >> 1, A1 = (a & 1) ? min(A0 + 1, h2 - 1) : A0;
-        const int B0 = b >> 1, B1 = (b & 1) ? min(B0 + 1, w2 - 1) : B0;
-        const int Cs[2] = {C0, C1}, As[2] = {A0, A1}, Bs[2] = {B0, B1};
-        float s = 0.f;
+__global__ void __launch_bounds__(VBX * VBY) k_vol_pi(const float* __restrict__ u1, int d1, int h1, int w1,
+                                                      const float* __restrict__ u2, int d2, int h2, int w2,
+                                                      float* __restrict__ out) {
+    VOXEL_INDEX(d1, h1, w1)
+    const int c = k, a = i, b = j;
+    const int C0 = c >> 1, C1 = (c & 1) ? min(C0 + 1, d2 - 1) : C0;
+    const int A0 = a >> 1, A1 = (a & 1) ? min(A0 + 1, h2 - 1) : A0;
+    const int B0 = b >> 1, B1 = (b & 1) ? min(B0 + 1, w2 - 1) : B0;
+    const int Cs[2] = {C0, C1}, As[2] = {A0, A1}, Bs[2] = {B0, B1};
+    float s = 0.f;
 #pragma unroll
-        for (int x = 0; x < 2; ++x)
+    for (int x = 0; x < 2; ++x)
 #pragma unroll
-            for (int i = 0; i < 2; ++i)
+        for (int y = 0; y < 2; ++y)
 #pragma unroll
-                for (int j = 0; j < 2; ++j)
-                    s += __ldg(u1 + ((long long)(2 * Cs[x]) * h1 + 2 * As[i]) * w1 + 2 * Bs[j]) -
-                         __ldg(u2 + ((long long)Cs[x] * h2 + As[i]) * w2 + Bs[j]);
-        out[v] = u1[v] + 0.03125f * s;
-    }
+            for (int z = 0; z < 2; ++z)
+                s += __ldg(u1 + ((long long)(2 * Cs[x]) * h1 + 2 * As[y]) * w1 + 2 * Bs[z]) -
+                     __ldg(u2 + ((long long)Cs[x] * h2 + As[y]) * w2 + Bs[z]);
+    out[v] = u1[v] + 0.03125f * s;
 }
 
 __constant__ float c_vqw[4][3] = {
     {1.f, 0.f, 0.f}, {0.375f, 0.75f, -0.125f}, {0.f, 1.f, 0.f}, {-0.125f, 0.75f, 0.375f}};
 
 // P: the three-point quadratic rule along all three axes (clamped indices).
-__global__ void k_vol_quad(const float* __restrict__ ut, int d1, int h1, int w1,
-                           float* __restrict__ out, int d, int h, int w) {
-    const long long n = (long long)d * h * w;
-    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < n;
-         v += (long long)gridDim.x * blockDim.x) {
-        const int x = (int)(v % w);
-        const long long rr = v / w;
-        const int y = (int)(rr % h), z = (int)(rr / h);
-        const int tz = z & 3, ty = y & 3, tx = x & 3;
-        const int Z = (z >> 2) * 2, Y = (y >> 2) * 2, X = (x >> 2) * 2;
-        int xs[3];
+__global__ void __launch_bounds__(VBX * VBY) k_vol_quad(const float* __restrict__ ut, int d1, int h1, int w1,
+                                                        float* __restrict__ out, int d, int h, int w) {
+    VOXEL_INDEX(d, h, w)
+    const int tz = k & 3, ty = i & 3, tx = j & 3;
+    const int Z = (k >> 2) * 2, Y = (i >> 2) * 2, X = (j >> 2) * 2;
+    int xs[3];
 #pragma unroll
-        for (int j = 0; j < 3; ++j) xs[j] = min(X + j, w1 - 1);
-        float s = 0.f;
+    for (int q = 0; q < 3; ++q) xs[q] = min(X + q, w1 - 1);
+    float s = 0.f;
 #pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            const float wz = c_vqw[tz][k];
-            if (wz == 0.f) continue;
-            const int c = min(Z + k, d1 - 1);
-            float sy = 0.f;
+    for (int o = 0; o < 3; ++o) {
+        const float wz = c_vqw[tz][o];
+        if (wz == 0.f) continue;
+        const int c = min(Z + o, d1 - 1);
+        float sy = 0.f;
 #pragma unroll
-            for (int i = 0; i < 3; ++i) {
-                const float wy = c_vqw[ty][i];
-                if (wy == 0.f) continue;
-                const float* row = ut + ((long long)c * h1 + min(Y + i, h1 - 1)) * w1;
-                float sx = 0.f;
+        for (int p = 0; p < 3; ++p) {
+            const float wy = c_vqw[ty][p];
+            if (wy == 0.f) continue;
+            const float* row = ut + ((long long)c * h1 + min(Y + p, h1 - 1)) * w1;
+            float sx = 0.f;
 #pragma unroll
-                for (int j = 0; j < 3; ++j) sx = fmaf(c_vqw[tx][j], __ldg(row + xs[j]), sx);
-                sy = fmaf(wy, sx, sy);
-            }
-            s = fmaf(wz, sy, s);
+            for (int q = 0; q < 3; ++q) sx = fmaf(c_vqw[tx][q], __ldg(row + xs[q]), sx);
+            sy = fmaf(wy, sx, sy);
         }
-        out[v] = s;
+        s = fmaf(wz, sy, s);
     }
+    out[v] = s;
 }
 
 // Eigen-decomposition of the symmetric 3x3 A by cyclic Jacobi rotations
@@ -576,9 +570,9 @@ __global__ void k_vol_quad(const float* __restrict__ ut, int d1, int h1, int w1,
 // quadratically, far below FP32 resolution for a 3x3 matrix.
 __device__ __forceinline__ void jacobi3f(float A[3][3], float V[3][3]) {
 #pragma unroll
-    for (int i = 0; i < 3; ++i)
+    for (int a = 0; a < 3; ++a)
 #pragma unroll
-        for (int j = 0; j < 3; ++j) V[i][j] = i == j ? 1.f : 0.f;
+        for (int b = 0; b < 3; ++b) V[a][b] = a == b ? 1.f : 0.f;
 #pragma unroll
     for (int sweep = 0; sweep < 4; ++sweep) {
 #pragma unroll
@@ -590,23 +584,23 @@ __device__ __forceinline__ void jacobi3f(float A[3][3], float V[3][3]) {
             const float t = copysignf(1.f, th) / (fabsf(th) + sqrtf(fmaf(th, th, 1.f)));
             const float c = rsqrtf(fmaf(t, t, 1.f)), s = t * c;
 #pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                const float akp = A[k][p], akq = A[k][q];
-                A[k][p] = c * akp - s * akq;
-                A[k][q] = s * akp + c * akq;
+            for (int m = 0; m < 3; ++m) {
+                const float amp = A[m][p], amq = A[m][q];
+                A[m][p] = c * amp - s * amq;
+                A[m][q] = s * amp + c * amq;
             }
 #pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                const float apk = A[p][k], aqk = A[q][k];
-                A[p][k] = c * apk - s * aqk;
-                A[q][k] = s * apk + c * aqk;
+            for (int m = 0; m < 3; ++m) {
+                const float apm = A[p][m], aqm = A[q][m];
+                A[p][m] = c * apm - s * aqm;
+                A[q][m] = s * apm + c * aqm;
             }
             A[p][q] = A[q][p] = 0.f;
 #pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                const float vkp = V[k][p], vkq = V[k][q];
-                V[k][p] = c * vkp - s * vkq;
-                V[k][q] = s * vkp + c * vkq;
+            for (int m = 0; m < 3; ++m) {
+                const float vmp = V[m][p], vmq = V[m][q];
+                V[m][p] = c * vmp - s * vmq;
+                V[m][q] = s * vmp + c * vmq;
             }
         }
     }
@@ -614,62 +608,74 @@ __device__ __forceinline__ void jacobi3f(float A[3][3], float V[3][3]) {
 
 // S: per voxel, the weighted hyperplane fit over the in-volume 3x3x3
 // neighbourhood (weights exp(-(scale v)^2), v = neighbour - centre) in centred
-// form; the output is u + vb - slope . ob with slope = C^+ c.
-__global__ void k_vol_smooth(const float* __restrict__ u, int d, int h, int w, float scale,
-                             float* __restrict__ out) {
-    const long long n = (long long)d * h * w;
-    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < n;
-         v += (long long)gridDim.x * blockDim.x) {
-        const int j = (int)(v % w);
-        const long long rr = v / w;
-        const int i = (int)(rr % h), k = (int)(rr / h);
-        const float uc = u[v];
-        float W = 0.f, o0 = 0.f, o1 = 0.f, o2 = 0.f, vb = 0.f;
-        float m00 = 0.f, m01 = 0.f, m02 = 0.f, m11 = 0.f, m12 = 0.f, m22 = 0.f;
-        float c0 = 0.f, c1 = 0.f, c2 = 0.f;
-        // raw weighted moments; centred afterwards (offsets are small integers)
+// form; the output is u + vb - slope . ob with slope = C^+ c.  When
+// Gershgorin's bound puts every eigenvalue of C above 1e-2 W (far above the
+// 1e-6 W cut), C^+ = C^-1 and the slope comes from the adjugate; otherwise from
+// the Jacobi eigen-decomposition with the cut.
+__global__ void __launch_bounds__(VBX * VBY) k_vol_smooth(const float* __restrict__ u, int d, int h, int w,
+                                                          float scale, float* __restrict__ out) {
+    VOXEL_INDEX(d, h, w)
+    const float uc = u[v];
+    float W = 0.f, o0 = 0.f, o1 = 0.f, o2 = 0.f, vb = 0.f;
+    float m00 = 0.f, m01 = 0.f, m02 = 0.f, m11 = 0.f, m12 = 0.f, m22 = 0.f;
+    float c0 = 0.f, c1 = 0.f, c2 = 0.f;
+    // raw weighted moments; centred afterwards (offsets are small integers)
 #pragma unroll
-        for (int r = -1; r <= 1; ++r) {
-            if (k + r < 0 || k + r >= d) continue;
+    for (int r = -1; r <= 1; ++r) {
+        if (k + r < 0 || k + r >= d) continue;
 #pragma unroll
-            for (int s = -1; s <= 1; ++s) {
-                if (i + s < 0 || i + s >= h) continue;
-                const float* row = u + ((long long)(k + r) * h + i + s) * w + j;
+        for (int s = -1; s <= 1; ++s) {
+            if (i + s < 0 || i + s >= h) continue;
+            const float* row = u + ((long long)(k + r) * h + i + s) * w + j;
 #pragma unroll
-                for (int t = -1; t <= 1; ++t) {
-                    if (j + t < 0 || j + t >= w) continue;
-                    const float val = __ldg(row + t) - uc;
-                    const float e = scale * val;
-                    const float wt = (r == 0 && s == 0 && t == 0) ? 1.f : __expf(-e * e);
-                    W += wt;
-                    const float wv = wt * val;
-                    vb += wv;
-                    if (r) { o0 = fmaf(wt, (float)r, o0); m00 += wt; c0 = fmaf(wv, (float)r, c0); }
-                    if (s) { o1 = fmaf(wt, (float)s, o1); m11 += wt; c1 = fmaf(wv, (float)s, c1); }
-                    if (t) { o2 = fmaf(wt, (float)t, o2); m22 += wt; c2 = fmaf(wv, (float)t, c2); }
-                    if (r && s) m01 = fmaf(wt, (float)(r * s), m01);
-                    if (r && t) m02 = fmaf(wt, (float)(r * t), m02);
-                    if (s && t) m12 = fmaf(wt, (float)(s * t), m12);
-                }
+            for (int t = -1; t <= 1; ++t) {
+                if (j + t < 0 || j + t >= w) continue;
+                const float val = __ldg(row + t) - uc;
+                const float e = scale * val;
+                const float wt = (r == 0 && s == 0 && t == 0) ? 1.f : __expf(-e * e);
+                W += wt;
+                const float wv = wt * val;
+                vb += wv;
+                if (r) { o0 = fmaf(wt, (float)r, o0); m00 += wt; c0 = fmaf(wv, (float)r, c0); }
+                if (s) { o1 = fmaf(wt, (float)s, o1); m11 += wt; c1 = fmaf(wv, (float)s, c1); }
+                if (t) { o2 = fmaf(wt, (float)t, o2); m22 += wt; c2 = fmaf(wv, (float)t, c2); }
+                if (r && s) m01 = fmaf(wt, (float)(r * s), m01);
+                if (r && t) m02 = fmaf(wt, (float)(r * t), m02);
+                if (s && t) m12 = fmaf(wt, (float)(s * t), m12);
             }
         }
-        const float iW = 1.f / W;
-        o0 *= iW; o1 *= iW; o2 *= iW; vb *= iW;
-        // centred moments: sum w (o - ob)(o' - ob') = sum w o o' - W ob ob'
-        float A[3][3];
-        A[0][0] = fmaf(-W * o0, o0, m00);
-        A[1][1] = fmaf(-W * o1, o1, m11);
-        A[2][2] = fmaf(-W * o2, o2, m22);
-        A[0][1] = A[1][0] = fmaf(-W * o0, o1, m01);
-        A[0][2] = A[2][0] = fmaf(-W * o0, o2, m02);
-        A[1][2] = A[2][1] = fmaf(-W * o1, o2, m12);
-        // sum w (o - ob)(v - vb) = sum w o v - W ob vb
-        const float cv0 = fmaf(-W * o0, vb, c0), cv1 = fmaf(-W * o1, vb, c1),
-                    cv2 = fmaf(-W * o2, vb, c2);
+    }
+    const float iW = 1.f / W;
+    o0 *= iW; o1 *= iW; o2 *= iW; vb *= iW;
+    // centred moments: sum w (o - ob)(o' - ob') = sum w o o' - W ob ob'
+    float A[3][3];
+    A[0][0] = fmaf(-W * o0, o0, m00);
+    A[1][1] = fmaf(-W * o1, o1, m11);
+    A[2][2] = fmaf(-W * o2, o2, m22);
+    A[0][1] = A[1][0] = fmaf(-W * o0, o1, m01);
+    A[0][2] = A[2][0] = fmaf(-W * o0, o2, m02);
+    A[1][2] = A[2][1] = fmaf(-W * o1, o2, m12);
+    // sum w (o - ob)(v - vb) = sum w o v - W ob vb
+    const float cv0 = fmaf(-W * o0, vb, c0), cv1 = fmaf(-W * o1, vb, c1), cv2 = fmaf(-W * o2, vb, c2);
+    float g0 = 0.f, g1 = 0.f, g2 = 0.f;
+    const float gersh = fminf(A[0][0] - fabsf(A[0][1]) - fabsf(A[0][2]),
+                              fminf(A[1][1] - fabsf(A[0][1]) - fabsf(A[1][2]),
+                                    A[2][2] - fabsf(A[0][2]) - fabsf(A[1][2])));
+    if (gersh > 1e-2f * W) {
+        const float k00 = A[1][1] * A[2][2] - A[1][2] * A[1][2];
+        const float k01 = A[0][2] * A[1][2] - A[0][1] * A[2][2];
+        const float k02 = A[0][1] * A[1][2] - A[0][2] * A[1][1];
+        const float k11 = A[0][0] * A[2][2] - A[0][2] * A[0][2];
+        const float k12 = A[0][1] * A[0][2] - A[0][0] * A[1][2];
+        const float k22 = A[0][0] * A[1][1] - A[0][1] * A[0][1];
+        const float idet = 1.f / (A[0][0] * k00 + A[0][1] * k01 + A[0][2] * k02);
+        g0 = (k00 * cv0 + k01 * cv1 + k02 * cv2) * idet;
+        g1 = (k01 * cv0 + k11 * cv1 + k12 * cv2) * idet;
+        g2 = (k02 * cv0 + k12 * cv1 + k22 * cv2) * idet;
+    } else {
         float V[3][3];
         jacobi3f(A, V);
         const float thr = 1e-6f * W;
-        float g0 = 0.f, g1 = 0.f, g2 = 0.f;
 #pragma unroll
         for (int e = 0; e < 3; ++e) {
             const float lam = A[e][e];
@@ -679,49 +685,40 @@ __global__ void k_vol_smooth(const float* __restrict__ u, int d, int h, int w, f
             g1 = fmaf(ce, V[1][e], g1);
             g2 = fmaf(ce, V[2][e], g2);
         }
-        out[v] = uc + vb - (g0 * o0 + g1 * o1 + g2 * o2);
     }
+    out[v] = uc + vb - (g0 * o0 + g1 * o1 + g2 * o2);
 }
 
 // D, first half: the diffusivity c = 1 / (1 + |grad u|^2 / k^2), central
 // differences, an out-of-volume neighbour replaced by the centre.
-__global__ void k_vol_pm_c(const float* __restrict__ u, int d, int h, int w, float ik2,
-                           float* __restrict__ c) {
-    const long long n = (long long)d * h * w, sl = (long long)h * w;
-    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < n;
-         v += (long long)gridDim.x * blockDim.x) {
-        const int j = (int)(v % w);
-        const long long rr = v / w;
-        const int i = (int)(rr % h), k = (int)(rr / h);
-        const float uc = u[v];
-        const float ub = k + 1 < d ? u[v + sl] : uc, ua = k > 0 ? u[v - sl] : uc;
-        const float us = i + 1 < h ? u[v + w] : uc, un = i > 0 ? u[v - w] : uc;
-        const float ue = j + 1 < w ? u[v + 1] : uc, uw = j > 0 ? u[v - 1] : uc;
-        const float gx = 0.5f * (ue - uw), gy = 0.5f * (us - un), gz = 0.5f * (ub - ua);
-        c[v] = 1.f / (1.f + (gx * gx + gy * gy + gz * gz) * ik2);
-    }
+__global__ void __launch_bounds__(VBX * VBY) k_vol_pm_c(const float* __restrict__ u, int d, int h, int w,
+                                                        float ik2, float* __restrict__ c) {
+    VOXEL_INDEX(d, h, w)
+    const long long sl = (long long)h * w;
+    const float uc = u[v];
+    const float ub = k + 1 < d ? u[v + sl] : uc, ua = k > 0 ? u[v - sl] : uc;
+    const float us = i + 1 < h ? u[v + w] : uc, un = i > 0 ? u[v - w] : uc;
+    const float ue = j + 1 < w ? u[v + 1] : uc, uw = j > 0 ? u[v - 1] : uc;
+    const float gx = 0.5f * (ue - uw), gy = 0.5f * (us - un), gz = 0.5f * (ub - ua);
+    c[v] = 1.f / (1.f + (gx * gx + gy * gy + gz * gz) * ik2);
 }
 
 // D, second half: u' = u + tau sum over in-volume face neighbours of
 // (c_nb + c) / 2 (u_nb - u) (no flux through the volume's faces).
-__global__ void k_vol_pm_step(const float* __restrict__ u, const float* __restrict__ c, int d,
-                              int h, int w, float tau, float* __restrict__ out) {
-    const long long n = (long long)d * h * w, sl = (long long)h * w;
-    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < n;
-         v += (long long)gridDim.x * blockDim.x) {
-        const int j = (int)(v % w);
-        const long long rr = v / w;
-        const int i = (int)(rr % h), k = (int)(rr / h);
-        const float uc = u[v], cc = c[v];
-        float f = 0.f;
-        if (k + 1 < d) f = fmaf(0.5f * (c[v + sl] + cc), u[v + sl] - uc, f);
-        if (k > 0) f = fmaf(0.5f * (c[v - sl] + cc), u[v - sl] - uc, f);
-        if (i + 1 < h) f = fmaf(0.5f * (c[v + w] + cc), u[v + w] - uc, f);
-        if (i > 0) f = fmaf(0.5f * (c[v - w] + cc), u[v - w] - uc, f);
-        if (j + 1 < w) f = fmaf(0.5f * (c[v + 1] + cc), u[v + 1] - uc, f);
-        if (j > 0) f = fmaf(0.5f * (c[v - 1] + cc), u[v - 1] - uc, f);
-        out[v] = fmaf(tau, f, uc);
-    }
+__global__ void __launch_bounds__(VBX * VBY) k_vol_pm_step(const float* __restrict__ u, const float* __restrict__ c,
+                                                           int d, int h, int w, float tau,
+                                                           float* __restrict__ out) {
+    VOXEL_INDEX(d, h, w)
+    const long long sl = (long long)h * w;
+    const float uc = u[v], cc = c[v];
+    float f = 0.f;
+    if (k + 1 < d) f = fmaf(0.5f * (c[v + sl] + cc), u[v + sl] - uc, f);
+    if (k > 0) f = fmaf(0.5f * (c[v - sl] + cc), u[v - sl] - uc, f);
+    if (i + 1 < h) f = fmaf(0.5f * (c[v + w] + cc), u[v + w] - uc, f);
+    if (i > 0) f = fmaf(0.5f * (c[v - w] + cc), u[v - w] - uc, f);
+    if (j + 1 < w) f = fmaf(0.5f * (c[v + 1] + cc), u[v + 1] - uc, f);
+    if (j > 0) f = fmaf(0.5f * (c[v - 1] + cc), u[v - 1] - uc, f);
+    out[v] = fmaf(tau, f, uc);
 }
 
 }  // namespace vol
@@ -852,10 +849,9 @@ const VolKernels<0, 1, 2, 3, 4, 5, 6>& vol_kernels() {
     return k;
 }
 
-int blocks_for(long long n) {
-    long long b = (n + 255) / 256;
-    return (int)(b < 1 ? 1 : (b > 152 * 16 ? 152 * 16 : b));
-}
+// The 3-D grid of the voxel kernels for a d x h x w volume.
+dim3 vgrid(int d, int h, int w) { return dim3((w + VBX - 1) / VBX, (h + VBY - 1) / VBY, d); }
+constexpr int VTHREADS = VBX * VBY;
 
 VolJob make_job(eecmg_vol_s* P, int l, bool transpose) {
     VolJob J{};
@@ -920,17 +916,17 @@ eecmg_status launch_start(eecmg_vol_s* P, int l, const float* u1, const float* u
     float* ut = P->vec[0];   // R: P(Pi)
     float* sa = P->vec[1];   // P0
     float* cc = P->vec[7];   // Z: diffusivity
-    k_vol_pi<<<blocks_for(P->n[l - 1]), 256, 0, s>>>(u1, d1, h1, w1, u2, P->ds[l - 2], P->hs[l - 2],
+    k_vol_pi<<<vgrid(d1, h1, w1), VTHREADS, 0, s>>>(u1, d1, h1, w1, u2, P->ds[l - 2], P->hs[l - 2],
                                                     P->ws[l - 2], ue);
-    k_vol_quad<<<blocks_for(P->n[l]), 256, 0, s>>>(ue, d1, h1, w1, ut, d, h, w);
+    k_vol_quad<<<vgrid(d, h, w), VTHREADS, 0, s>>>(ue, d1, h1, w1, ut, d, h, w);
     const int steps = P->opt.diffusion_steps;
     float* cur = steps == 0 ? out : sa;
-    k_vol_smooth<<<blocks_for(P->n[l]), 256, 0, s>>>(ut, d, h, w, (float)P->opt.s_scale, cur);
+    k_vol_smooth<<<vgrid(d, h, w), VTHREADS, 0, s>>>(ut, d, h, w, (float)P->opt.s_scale, cur);
     const float ik2 = (float)(1.0 / (P->kpm * P->kpm));
     for (int st = 0; st < steps; ++st) {
         float* nxt = st == steps - 1 ? out : (cur == sa ? ut : sa);
-        k_vol_pm_c<<<blocks_for(P->n[l]), 256, 0, s>>>(cur, d, h, w, ik2, cc);
-        k_vol_pm_step<<<blocks_for(P->n[l]), 256, 0, s>>>(cur, cc, d, h, w, (float)P->tau, nxt);
+        k_vol_pm_c<<<vgrid(d, h, w), VTHREADS, 0, s>>>(cur, d, h, w, ik2, cc);
+        k_vol_pm_step<<<vgrid(d, h, w), VTHREADS, 0, s>>>(cur, cc, d, h, w, (float)P->tau, nxt);
         cur = nxt;
     }
     VCK(cudaGetLastError());
@@ -946,7 +942,7 @@ eecmg_status cascade(eecmg_vol_s* P, cudaStream_t s) {
         return EECMG_OK;
     };
     for (int l = L - 1; l > 0; --l) {
-        k_vol_restrict<<<blocks_for(P->n[l - 1]), 256, 0, s>>>(P->g[l], P->hs[l], P->ws[l],
+        k_vol_restrict<<<vgrid(P->ds[l - 1], P->hs[l - 1], P->ws[l - 1]), VTHREADS, 0, s>>>(P->g[l], P->hs[l], P->ws[l],
                                                              P->g[l - 1], P->ds[l - 1],
                                                              P->hs[l - 1], P->ws[l - 1]);
         VCK(cudaGetLastError());
@@ -1027,8 +1023,9 @@ eecmg_status eecmg_vol_plan(int width, int height, int depth, int levels, const 
     *out = nullptr;
     if (width < 1 || height < 1 || depth < 1 || levels < 1 || levels > 16)
         return set_error(EECMG_ERR_INVALID_ARG, "eecmg_vol_plan: bad volume size or levels");
-    if ((long long)width * height * depth > (1LL << 31))
-        return set_error(EECMG_ERR_INVALID_ARG, "eecmg_vol_plan: volume above 2^31 voxels");
+    if ((long long)width * height * depth > (1LL << 31) || depth > 65535)
+        return set_error(EECMG_ERR_INVALID_ARG,
+                         "eecmg_vol_plan: volume above 2^31 voxels or 65535 slices");
     if (!psf || psf_w < 1 || psf_h < 1 || psf_d < 1 || !(psf_w & 1) || !(psf_h & 1) || !(psf_d & 1) ||
         psf_w / 2 > VR || psf_h / 2 > VR || psf_d / 2 > VR)
         return set_error(EECMG_ERR_INVALID_ARG,
@@ -1311,7 +1308,7 @@ eecmg_status eecmg_vol_smooth(eecmg_vol_t P, int level, const float* x, float* y
     eecmg_status st = check_level(P, level, "eecmg_vol_smooth");
     if (st != EECMG_OK) return st;
     if (!x || !y || x == y) return set_error(EECMG_ERR_INVALID_ARG, "eecmg_vol_smooth: bad buffers");
-    k_vol_smooth<<<blocks_for(P->n[level]), 256, 0, s>>>(x, P->ds[level], P->hs[level], P->ws[level],
+    k_vol_smooth<<<vgrid(P->ds[level], P->hs[level], P->ws[level]), VTHREADS, 0, s>>>(x, P->ds[level], P->hs[level], P->ws[level],
                                                         (float)P->opt.s_scale, y);
     VCK(cudaGetLastError());
     return EECMG_OK;
@@ -1322,9 +1319,9 @@ eecmg_status eecmg_vol_denoise(eecmg_vol_t P, int level, const float* x, float* 
     if (st != EECMG_OK) return st;
     if (!x || !y || x == y) return set_error(EECMG_ERR_INVALID_ARG, "eecmg_vol_denoise: bad buffers");
     const int d = P->ds[level], h = P->hs[level], w = P->ws[level];
-    k_vol_pm_c<<<blocks_for(P->n[level]), 256, 0, s>>>(x, d, h, w, (float)(1.0 / (P->kpm * P->kpm)),
+    k_vol_pm_c<<<vgrid(d, h, w), VTHREADS, 0, s>>>(x, d, h, w, (float)(1.0 / (P->kpm * P->kpm)),
                                                       P->vec[7]);
-    k_vol_pm_step<<<blocks_for(P->n[level]), 256, 0, s>>>(x, P->vec[7], d, h, w, (float)P->tau, y);
+    k_vol_pm_step<<<vgrid(d, h, w), VTHREADS, 0, s>>>(x, P->vec[7], d, h, w, (float)P->tau, y);
     VCK(cudaGetLastError());
     return EECMG_OK;
 }
@@ -1335,7 +1332,7 @@ eecmg_status eecmg_vol_restrict(eecmg_vol_t P, int level, const float* fine, flo
     if (st != EECMG_OK) return st;
     if (level >= P->L - 1 || !fine || !coarse)
         return set_error(EECMG_ERR_INVALID_ARG, "eecmg_vol_restrict: level must be below the finest");
-    k_vol_restrict<<<blocks_for(P->n[level]), 256, 0, s>>>(fine, P->hs[level + 1], P->ws[level + 1],
+    k_vol_restrict<<<vgrid(P->ds[level], P->hs[level], P->ws[level]), VTHREADS, 0, s>>>(fine, P->hs[level + 1], P->ws[level + 1],
                                                           coarse, P->ds[level], P->hs[level],
                                                           P->ws[level]);
     VCK(cudaGetLastError());
