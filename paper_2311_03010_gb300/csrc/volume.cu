@@ -148,6 +148,14 @@ __device__ __forceinline__ void compute_tile(const VolJob& J, int t, float* A, f
     tile_origin(J, t, x0, y0, z0);
     const int xo = threadIdx.x & 31, warp = threadIdx.x >> 5;  // warp = output row within a slice
     const int gx = x0 + xo, gy = y0 + warp;
+    // the epilogue's read-only operands of this thread's outputs, fetched
+    // before the passes so that their latency hides behind the convolution
+    const bool col_in = gy < J.h && gx < J.w;
+    float2 pre[TZ];
+#pragma unroll
+    for (int zo = 0; zo < TZ; ++zo)
+        pre[zo] = (col_in && z0 + zo < J.d) ? epi.pre(((long long)(z0 + zo) * J.h + gy) * J.w + gx)
+                                            : make_float2(0.f, 0.f);
     if (K.sep) {
         // columns: B[z][y][x] = sum_dx cx A[z][y][x + R + dx], every staged row
         constexpr int ROWS = T::NZ * T::NY, U = 4;
@@ -184,12 +192,13 @@ __device__ __forceinline__ void compute_tile(const VolJob& J, int t, float* A, f
 #pragma unroll
             for (int o = 0; o <= 2 * R; ++o) s[zo] = fmaf(K.cz[o], C[((zo + o) * TY + warp) * TX + xo], s[zo]);
         }
-        if (gy < J.h && gx < J.w) {
+        if (col_in) {
 #pragma unroll
             for (int zo = 0; zo < TZ; ++zo)
-                if (z0 + zo < J.d) epi(((long long)(z0 + zo) * J.h + gy) * J.w + gx, s[zo]);
+                if (z0 + zo < J.d) epi(((long long)(z0 + zo) * J.h + gy) * J.w + gx, s[zo], pre[zo]);
         }
     } else {
+#pragma unroll
         for (int zo = 0; zo < TZ; ++zo) {
             const float* a = A + ((zo + R) * T::NY + warp + R) * T::AX + xo + R;
             float s = 0.f;
@@ -197,11 +206,25 @@ __device__ __forceinline__ void compute_tile(const VolJob& J, int t, float* A, f
                 const int4 tp = __ldg(J.gtaps + k);
                 s = fmaf(__int_as_float(tp.w), a[(tp.x * T::NY + tp.y) * T::AX + tp.z], s);
             }
-            if (z0 + zo < J.d && gy < J.h && gx < J.w) epi(((long long)(z0 + zo) * J.h + gy) * J.w + gx, s);
+            if (z0 + zo < J.d && col_in) epi(((long long)(z0 + zo) * J.h + gy) * J.w + gx, s, pre[zo]);
         }
     }
     __syncthreads();  // the buffers are restaged after this
 }
+
+// An epilogue: pre(v) loads the operands output v needs (at most two floats,
+// issued before the convolution), op(v, (H x)(v), operands) consumes them.
+template <class Pre, class Op>
+struct Epilogue {
+    Pre pre;
+    Op op;
+    __device__ __forceinline__ void operator()(long long v, float hx, float2 p) { op(v, hx, p); }
+};
+template <class Pre, class Op>
+__device__ __forceinline__ Epilogue<Pre, Op> epilogue(Pre pre, Op op) {
+    return Epilogue<Pre, Op>{pre, op};
+}
+__device__ __forceinline__ float2 no_pre(long long) { return make_float2(0.f, 0.f); }
 
 // One convolution phase: H x over all the block's tiles, the next tile's
 // window in flight while the current one is convolved.
@@ -289,7 +312,7 @@ __device__ __forceinline__ bool pos_finite(double x) { return x > 0.0 && isfinit
 //   a = <r,q_{k+1}>/<q_{k+1},q_{k+1}>, u += a p_{k+1}, r -= a q_{k+1}.
 // p and q live in rings of three buffers: p_k = P[(k - 1) % 3].
 template <int R>
-__global__ void __launch_bounds__(NTHREADS) k_vol_mr2(VolJob J) {
+__global__ void __launch_bounds__(NTHREADS, 2) k_vol_mr2(VolJob J) {
     extern __shared__ __align__(16) float sm[];
     __shared__ VolScal S;
     const unsigned int nb = gridDim.x, bid = blockIdx.x;
@@ -331,13 +354,15 @@ __global__ void __launch_bounds__(NTHREADS) k_vol_mr2(VolJob J) {
                 acc_add(acc[1], dot4(g, g, 0.f));
             }
         } else {
-            conv_phase<R>(J, J.u, sm, [&](long long i, float hx) {
-                    const float g = __ldcg(J.g + i);
+            conv_phase<R>(J, J.u, sm, epilogue(
+                [&](long long i) { return make_float2(__ldcg(J.g + i), 0.f); },
+                [&](long long i, float hx, float2 p) {
+                    const float g = p.x;
                     const float r = g - hx;
                     J.R[i] = r;
                     acc_add(acc[0], r * r);
                     acc_add(acc[1], g * g);
-                });
+                }));
         }
         ok = reduce(acc, [&](const DF (&t)[4]) {
             S.rr = tot2(t, 0);
@@ -348,18 +373,20 @@ __global__ void __launch_bounds__(NTHREADS) k_vol_mr2(VolJob J) {
     }
     if (ok && !S.done) {
         // p1 = H r0
-        conv_phase<R>(J, J.R, sm, [&](long long i, float hx) { J.P[0][i] = hx; });
+        conv_phase<R>(J, J.R, sm, epilogue(no_pre, [&](long long i, float hx, float2) { J.P[0][i] = hx; }));
         DF none[2] = {{0.f, 0.f}, {0.f, 0.f}};
         ok = reduce(none, [&](const DF (&)[4]) {});
     }
     if (ok && !S.done) {
         // q1 = H p1; <q,q>, <r,q>
         DF acc[2] = {{0.f, 0.f}, {0.f, 0.f}};
-        conv_phase<R>(J, J.P[0], sm, [&](long long i, float hx) {
+        conv_phase<R>(J, J.P[0], sm, epilogue(
+            [&](long long i) { return make_float2(__ldcg(J.R + i), 0.f); },
+            [&](long long i, float hx, float2 p) {
                 J.Q[0][i] = hx;
                 acc_add(acc[0], hx * hx);
-                acc_add(acc[1], __ldcg(J.R + i) * hx);
-            });
+                acc_add(acc[1], p.x * hx);
+            }));
         ok = reduce(acc, [&](const DF (&t)[4]) {
             const double qq = tot2(t, 0), rq = tot2(t, 1);
             if (!pos_finite(qq)) {
@@ -398,11 +425,13 @@ __global__ void __launch_bounds__(NTHREADS) k_vol_mr2(VolJob J) {
         // z = H q_k; <z, q_k>, <z, q_{k-1}>
         {
             DF acc[2] = {{0.f, 0.f}, {0.f, 0.f}};
-            conv_phase<R>(J, q, sm, [&](long long i, float hx) {
+            conv_phase<R>(J, q, sm, epilogue(
+                [&](long long i) { return make_float2(__ldcg(q + i), two ? __ldcg(qp + i) : 0.f); },
+                [&](long long i, float hx, float2 p) {
                     J.Z[i] = hx;
-                    acc_add(acc[0], hx * __ldcg(q + i));
-                    if (two) acc_add(acc[1], hx * __ldcg(qp + i));
-                });
+                    acc_add(acc[0], hx * p.x);
+                    if (two) acc_add(acc[1], hx * p.y);
+                }));
             ok = reduce(acc, [&](const DF (&t)[4]) {
                 S.b1 = tot2(t, 0) / S.qq;
                 S.b2 = two ? tot2(t, 1) / S.qqp : 0.0;
@@ -485,7 +514,8 @@ __global__ void __launch_bounds__(NTHREADS) k_vol_apply(VolJob J, const float* _
     stage_tile<R>(J, x, blockIdx.x, sm);
     asm volatile("cp.async.wait_group 0;" ::: "memory");
     __syncthreads();
-    compute_tile<R>(J, blockIdx.x, sm, sm + 2 * VolTile<R>::IN, [&](long long i, float hx) { y[i] = hx; });
+    compute_tile<R>(J, blockIdx.x, sm, sm + 2 * VolTile<R>::IN,
+                    epilogue(no_pre, [&](long long i, float hx, float2) { y[i] = hx; }));
 }
 
 // ------------------------------------------------------------ level start
