@@ -95,7 +95,10 @@ struct VolScal {
 
 template <int R>
 struct VolTile {
-    static constexpr int NZ = TZ + 2 * R, NY = TY + 2 * R, AX = TX + 2 * R;
+    // a staged row starts PADX = R rounded up to 4 voxels left of the tile, so
+    // rows are whole 16-byte chunks; voxel x of the window sits at X0 + x
+    static constexpr int PADX = (R + 3) / 4 * 4, X0 = PADX - R;
+    static constexpr int NZ = TZ + 2 * R, NY = TY + 2 * R, AX = TX + 2 * PADX;
     static constexpr int IN = NZ * NY * AX;  // one input buffer
     static constexpr int MID = NZ * NY * TX; // B
     static constexpr size_t bytes(bool sep) { return sizeof(float) * (2 * (size_t)IN + (sep ? MID : 0)); }
@@ -119,20 +122,42 @@ __device__ __forceinline__ void stage_tile(const VolJob& J, const float* __restr
     tile_origin(J, t, x0, y0, z0);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned int base = (unsigned int)__cvta_generic_to_shared(A);
-    for (int row = warp; row < T::NZ * T::NY; row += NTHREADS / 32) {
-        const int za = row / T::NY, ya = row - za * T::NY;
-        const int gz = z0 - R + za, gy = y0 - R + ya;
-        const bool rin = gz >= 0 && gz < J.d && gy >= 0 && gy < J.h;
-        const float* src = x + ((long long)(rin ? gz : 0) * J.h + (rin ? gy : 0)) * J.w;
-#pragma unroll
-        for (int xa = lane; xa < T::AX; xa += 32) {
-            const int gx = x0 - R + xa;
-            const bool in = rin && gx >= 0 && gx < J.w;
-            const float* g = in ? src + gx : x;  // a valid address either way
-            asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(
-                             base + 4u * (unsigned int)(row * T::AX + xa)),
-                         "l"(g), "r"(in ? 4 : 0)
+    if ((J.w & 3) == 0 && (reinterpret_cast<uintptr_t>(x) & 15) == 0) {
+        // 16-byte chunks: rows are 16-byte aligned in memory (w a multiple of 4,
+        // x 16-byte aligned) and a chunk is
+        // either inside the row or wholly past one of its ends (zero fill)
+        constexpr int CH = T::AX / 4;           // chunks per row
+        constexpr int RPW = 32 / CH;            // rows per warp instruction
+        constexpr int ROWS = T::NZ * T::NY;
+        const int sub = lane / CH, c = lane - sub * CH;
+        for (int r0 = warp * RPW; r0 < ROWS; r0 += (NTHREADS / 32) * RPW) {
+            const int row = r0 + sub;
+            if (sub >= RPW || row >= ROWS) continue;
+            const int za = row / T::NY, ya = row - za * T::NY;
+            const int gz = z0 - R + za, gy = y0 - R + ya, gx = x0 - T::PADX + 4 * c;
+            const bool in = gz >= 0 && gz < J.d && gy >= 0 && gy < J.h && gx >= 0 && gx < J.w;
+            const float* g = in ? x + ((long long)gz * J.h + gy) * J.w + gx : x;
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(
+                             base + 4u * (unsigned int)(row * T::AX + 4 * c)),
+                         "l"(g), "r"(in ? 16 : 0)
                          : "memory");
+        }
+    } else {
+        for (int row = warp; row < T::NZ * T::NY; row += NTHREADS / 32) {
+            const int za = row / T::NY, ya = row - za * T::NY;
+            const int gz = z0 - R + za, gy = y0 - R + ya;
+            const bool rin = gz >= 0 && gz < J.d && gy >= 0 && gy < J.h;
+            const float* src = x + ((long long)(rin ? gz : 0) * J.h + (rin ? gy : 0)) * J.w;
+#pragma unroll
+            for (int xa = lane; xa < T::AX; xa += 32) {
+                const int gx = x0 - T::PADX + xa;
+                const bool in = rin && gx >= 0 && gx < J.w;
+                const float* g = in ? src + gx : x;  // a valid address either way
+                asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(
+                                 base + 4u * (unsigned int)(row * T::AX + xa)),
+                             "l"(g), "r"(in ? 4 : 0)
+                             : "memory");
+            }
         }
     }
     asm volatile("cp.async.commit_group;" ::: "memory");
@@ -167,7 +192,7 @@ __device__ __forceinline__ void compute_tile(const VolJob& J, int t, float* A, f
             for (int q = 0; q <= 2 * R; ++q)
 #pragma unroll
                 for (int u = 0; u < U; ++u)
-                    if (r0 + 8 * u < ROWS) s[u] = fmaf(K.cx[q], A[(r0 + 8 * u) * T::AX + xo + q], s[u]);
+                    if (r0 + 8 * u < ROWS) s[u] = fmaf(K.cx[q], A[(r0 + 8 * u) * T::AX + T::X0 + xo + q], s[u]);
 #pragma unroll
             for (int u = 0; u < U; ++u)
                 if (r0 + 8 * u < ROWS) B[(r0 + 8 * u) * TX + xo] = s[u];
@@ -200,7 +225,7 @@ __device__ __forceinline__ void compute_tile(const VolJob& J, int t, float* A, f
     } else {
 #pragma unroll
         for (int zo = 0; zo < TZ; ++zo) {
-            const float* a = A + ((zo + R) * T::NY + warp + R) * T::AX + xo + R;
+            const float* a = A + ((zo + R) * T::NY + warp + R) * T::AX + T::X0 + xo + R;
             float s = 0.f;
             for (int k = 0; k < K.ntap; ++k) {
                 const int4 tp = __ldg(J.gtaps + k);
@@ -863,7 +888,7 @@ void make_vol_taps(const std::vector<double>& K, int kd, int kh, int kw, bool tr
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 size_t tile_bytes(const VolTaps& t) {
-    const int NZ = TZ + 2 * t.r, NY = TY + 2 * t.r, AX = TX + 2 * t.r;
+    const int NZ = TZ + 2 * t.r, NY = TY + 2 * t.r, AX = TX + 2 * ((t.r + 3) / 4 * 4);
     return sizeof(float) * (2 * (size_t)NZ * NY * AX + (t.sep ? (size_t)NZ * NY * TX : 0));
 }
 
