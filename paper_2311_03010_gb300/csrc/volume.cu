@@ -619,46 +619,45 @@ __global__ void __launch_bounds__(VBX * VBY) k_vol_quad(const float* __restrict_
     out[v] = s;
 }
 
-// Eigen-decomposition of the symmetric 3x3 A by cyclic Jacobi rotations
-// (Golub & Van Loan, Sec. 8.5); A's diagonal receives the eigenvalues and the
-// columns of V the eigenvectors.  Four sweeps: the off-diagonal mass falls
-// quadratically, far below FP32 resolution for a 3x3 matrix.
-__device__ __forceinline__ void jacobi3f(float A[3][3], float V[3][3]) {
-#pragma unroll
-    for (int a = 0; a < 3; ++a)
-#pragma unroll
-        for (int b = 0; b < 3; ++b) V[a][b] = a == b ? 1.f : 0.f;
+// slope . ob for slope = C^+ c (eigenvalues of C at most thr dropped), by the
+// cyclic Jacobi method (Golub & Van Loan, Sec. 8.5): rotations in the (0,1),
+// (0,2), (1,2) planes diagonalise the symmetric C; instead of accumulating
+// the eigenvector matrix V, each rotation is applied to c and ob directly, so
+// y = V^T c and z = V^T ob and the result is sum_k [lambda_k > thr] y_k z_k /
+// lambda_k.  A rotation's angle needs no correct rounding (the rotation stays
+// orthogonal to rounding whatever its angle, and the next sweep removes what
+// it left), so t uses the fast division (its denominator is at least 1).
+// Four sweeps.
+__device__ __forceinline__ float jacobi_pinv_dot(float (&A)[3][3], float (&y)[3], float (&z)[3],
+                                                 float thr) {
 #pragma unroll
     for (int sweep = 0; sweep < 4; ++sweep) {
 #pragma unroll
         for (int pq = 0; pq < 3; ++pq) {
-            const int p = pq == 2 ? 1 : 0, q = pq == 0 ? 1 : 2;
+            const int p = pq == 2 ? 1 : 0, q = pq == 0 ? 1 : 2, r = 3 - p - q;
             const float apq = A[p][q];
             if (apq == 0.f) continue;
-            const float th = (A[q][q] - A[p][p]) / (2.f * apq);
-            const float t = copysignf(1.f, th) / (fabsf(th) + sqrtf(fmaf(th, th, 1.f)));
+            const float th = (A[q][q] - A[p][p]) / (2.f * apq);  // IEEE: apq may be subnormal
+            const float t = __fdividef(copysignf(1.f, th), fabsf(th) + sqrtf(fmaf(th, th, 1.f)));
             const float c = rsqrtf(fmaf(t, t, 1.f)), s = t * c;
-#pragma unroll
-            for (int m = 0; m < 3; ++m) {
-                const float amp = A[m][p], amq = A[m][q];
-                A[m][p] = c * amp - s * amq;
-                A[m][q] = s * amp + c * amq;
-            }
-#pragma unroll
-            for (int m = 0; m < 3; ++m) {
-                const float apm = A[p][m], aqm = A[q][m];
-                A[p][m] = c * apm - s * aqm;
-                A[q][m] = s * apm + c * aqm;
-            }
+            A[p][p] = fmaf(-t, apq, A[p][p]);
+            A[q][q] = fmaf(t, apq, A[q][q]);
             A[p][q] = A[q][p] = 0.f;
-#pragma unroll
-            for (int m = 0; m < 3; ++m) {
-                const float vmp = V[m][p], vmq = V[m][q];
-                V[m][p] = c * vmp - s * vmq;
-                V[m][q] = s * vmp + c * vmq;
-            }
+            const float arp = A[r][p], arq = A[r][q];
+            A[r][p] = A[p][r] = c * arp - s * arq;
+            A[r][q] = A[q][r] = s * arp + c * arq;
+            const float yp = y[p], yq = y[q], zp = z[p], zq = z[q];
+            y[p] = c * yp - s * yq;
+            y[q] = s * yp + c * yq;
+            z[p] = c * zp - s * zq;
+            z[q] = s * zp + c * zq;
         }
     }
+    float g = 0.f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+        if (A[k][k] > thr) g = fmaf(__fdividef(y[k], A[k][k]), z[k], g);
+    return g;
 }
 
 // S: per voxel, the weighted hyperplane fit over the in-volume 3x3x3
@@ -712,10 +711,10 @@ __global__ void __launch_bounds__(VBX * VBY) k_vol_smooth(const float* __restric
     A[1][2] = A[2][1] = fmaf(-W * o1, o2, m12);
     // sum w (o - ob)(v - vb) = sum w o v - W ob vb
     const float cv0 = fmaf(-W * o0, vb, c0), cv1 = fmaf(-W * o1, vb, c1), cv2 = fmaf(-W * o2, vb, c2);
-    float g0 = 0.f, g1 = 0.f, g2 = 0.f;
     const float gersh = fminf(A[0][0] - fabsf(A[0][1]) - fabsf(A[0][2]),
                               fminf(A[1][1] - fabsf(A[0][1]) - fabsf(A[1][2]),
                                     A[2][2] - fabsf(A[0][2]) - fabsf(A[1][2])));
+    float gob;
     if (gersh > 1e-2f * W) {
         const float k00 = A[1][1] * A[2][2] - A[1][2] * A[1][2];
         const float k01 = A[0][2] * A[1][2] - A[0][1] * A[2][2];
@@ -724,24 +723,15 @@ __global__ void __launch_bounds__(VBX * VBY) k_vol_smooth(const float* __restric
         const float k12 = A[0][1] * A[0][2] - A[0][0] * A[1][2];
         const float k22 = A[0][0] * A[1][1] - A[0][1] * A[0][1];
         const float idet = 1.f / (A[0][0] * k00 + A[0][1] * k01 + A[0][2] * k02);
-        g0 = (k00 * cv0 + k01 * cv1 + k02 * cv2) * idet;
-        g1 = (k01 * cv0 + k11 * cv1 + k12 * cv2) * idet;
-        g2 = (k02 * cv0 + k12 * cv1 + k22 * cv2) * idet;
+        const float g0 = (k00 * cv0 + k01 * cv1 + k02 * cv2) * idet;
+        const float g1 = (k01 * cv0 + k11 * cv1 + k12 * cv2) * idet;
+        const float g2 = (k02 * cv0 + k12 * cv1 + k22 * cv2) * idet;
+        gob = g0 * o0 + g1 * o1 + g2 * o2;
     } else {
-        float V[3][3];
-        jacobi3f(A, V);
-        const float thr = 1e-6f * W;
-#pragma unroll
-        for (int e = 0; e < 3; ++e) {
-            const float lam = A[e][e];
-            if (!(lam > thr)) continue;
-            const float ce = (V[0][e] * cv0 + V[1][e] * cv1 + V[2][e] * cv2) / lam;
-            g0 = fmaf(ce, V[0][e], g0);
-            g1 = fmaf(ce, V[1][e], g1);
-            g2 = fmaf(ce, V[2][e], g2);
-        }
+        float y[3] = {cv0, cv1, cv2}, z[3] = {o0, o1, o2};
+        gob = jacobi_pinv_dot(A, y, z, 1e-6f * W);
     }
-    out[v] = uc + vb - (g0 * o0 + g1 * o1 + g2 * o2);
+    out[v] = uc + vb - gob;
 }
 
 // D, first half: the diffusivity c = 1 / (1 + |grad u|^2 / k^2), central
