@@ -138,6 +138,31 @@ def profiled_traffic(workload, step):
     return float(kv["dram_bytes_per_launch"]), path.replace(ROOT + os.sep, "")
 
 
+VOLUME_SOURCES = ("common.cuh", "persistent.cuh", "volume.cu")
+
+
+def volume_traffic(workload):
+    """DRAM bytes per launch of the finest volume solve from the committed ncu
+    summary, if it was taken on the current volume sources (else None, reason)."""
+    import hashlib
+
+    path = os.path.join(ROOT, "profiles", f"volume_solve_traffic_{workload}.txt")
+    if not os.path.exists(path):
+        return None, "no ncu capture of this workload"
+    kv = {}
+    for line in open(path):
+        if ":" in line:
+            k, v = line.split(":", 1)
+            kv[k.strip()] = v.strip()
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2311_03010_gb300", "csrc")
+    for f in VOLUME_SOURCES:
+        h.update(open(os.path.join(d, f), "rb").read())
+    if kv.get("volume_sources_sha256") != h.hexdigest():
+        return None, "ncu capture predates the current volume sources"
+    return float(kv["dram_bytes_per_launch"]), path.replace(ROOT + os.sep, "")
+
+
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -496,8 +521,11 @@ def volume_leg(torch, eecmg, stream, flush, steps, warmup, peak, oracle_ok):
                        "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                        "bytes_per_launch": sol_b[0], "ms_per_launch": kms,
                        "share_of_step": kms / (tot / steps), "level_start_ms": st_ms,
-                       "level_solve_ms": s_ms, "traffic": None,
+                       "level_solve_ms": s_ms, "traffic": None, "traffic_source": None,
                        "method": "event pair around the launch in an eager restoration (median of 3)"}
+    tr, tr_src = volume_traffic(V["workload"])
+    out["roofline"]["traffic"] = tr
+    out["roofline"]["traffic_source"] = tr_src
     if oracle_ok:
         import oracle
 
