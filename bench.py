@@ -138,7 +138,8 @@ def profiled_traffic(workload, step):
     return float(kv["dram_bytes_per_launch"]), path.replace(ROOT + os.sep, "")
 
 
-VOLUME_SOURCES = ("common.cuh", "persistent.cuh", "volume.cu")
+VOLUME_SOURCES = ("common.cuh", "persistent.cuh", "volume_impl.cuh", "volume_r012.cu", "volume_r34.cu",
+                  "volume_r56.cu", "volume.cu")
 
 
 def volume_traffic(workload):
