@@ -74,3 +74,18 @@ def test_clock_sampler_short_region_takes_the_nearest_sample():
     clk = _sampler_with(rows, now, now + 0.01).stop()
     assert clk["samples"] == 1 and clk["sm_mhz"] == 2070
     assert clk["window"].startswith("nearest sample")
+
+
+def test_committed_traffic_profiles_match_the_sources():
+    """The DRAM traffic the bench reports comes from committed ncu summaries; each
+    one names a hash of the kernel sources it was taken on, and a summary taken
+    on other sources is not used."""
+    import bench
+
+    tr, src = bench.profiled_traffic("4096x4096-gauss3-L5", 4)
+    assert tr is not None, src
+    assert abs(tr - 2.08e9) < 0.05e9
+    vt, vsrc = bench.volume_traffic(bench.VOLUME["workload"])
+    assert vt is not None, vsrc
+    assert abs(vt - 2.97e9) < 0.05e9
+    assert bench.volume_traffic("no-such-workload")[0] is None
