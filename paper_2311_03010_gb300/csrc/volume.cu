@@ -375,7 +375,7 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 size_t tile_bytes(const VolTaps& t) {
     const int NZ = TZ + 2 * t.r, NY = TY + 2 * t.r, AX = TX + 2 * ((t.r + 3) / 4 * 4);
-    return sizeof(float) * (2 * (size_t)NZ * NY * AX + (t.sep ? (size_t)NZ * NY * TX : 0));
+    return sizeof(float) * (2 * (size_t)NZ * NY * AX + (t.sep ? (size_t)TZ * NY * AX : 0));
 }
 
 // The kernels of every radius 0 .. EECMG_VOL_MAX_RADIUS (instantiated in the

@@ -58,11 +58,14 @@ struct VolScal {
 //
 // A block loops over its output tiles t = blockIdx.x, + gridDim.x, ...  The
 // input window of a tile (the tile plus an r-voxel halo, zero outside the
-// volume) is fetched with 4-byte cp.async (zero fill past the volume) into one
-// of two shared-memory buffers while the previous tile is convolved from the
-// other.  The separable form runs three passes in shared memory: columns over
-// every staged row into B, rows over B into C (C reuses the tile's own input
-// buffer), slices over C; the general form sums its tap list over the window.
+// volume) is fetched with cp.async (16-byte chunks where rows are 16-byte
+// aligned, else 4-byte copies; zero fill past the volume) into one of two
+// shared-memory buffers while the previous tile is convolved from the other.
+// The separable form runs three passes in shared memory: slices over every
+// staged (row, column) into B, rows over B into C (C reuses the tile's own
+// input buffer), columns over C; the first two slide a register window along
+// their axis, so each staged value is read once.  The general form sums its
+// tap list over the window.
 
 template <int R>
 struct VolTile {
@@ -71,7 +74,7 @@ struct VolTile {
     static constexpr int PADX = (R + 3) / 4 * 4, X0 = PADX - R;
     static constexpr int NZ = TZ + 2 * R, NY = TY + 2 * R, AX = TX + 2 * PADX;
     static constexpr int IN = NZ * NY * AX;  // one input buffer
-    static constexpr int MID = NZ * NY * TX; // B
+    static constexpr int MID = TZ * NY * AX; // B: the slice pass's output
     static constexpr size_t bytes(bool sep) { return sizeof(float) * (2 * (size_t)IN + (sep ? MID : 0)); }
 };
 
@@ -153,40 +156,50 @@ __device__ __forceinline__ void compute_tile(const VolJob& J, int t, float* A, f
         pre[zo] = (col_in && z0 + zo < J.d) ? epi.pre(((long long)(z0 + zo) * J.h + gy) * J.w + gx)
                                             : make_float2(0.f, 0.f);
     if (K.sep) {
-        // columns: B[z][y][x] = sum_dx cx A[z][y][x + R + dx], every staged row
-        constexpr int ROWS = T::NZ * T::NY, U = 4;
-        for (int r0 = warp; r0 < ROWS; r0 += 8 * U) {
-            float s[U];
+        // slices first: B[z][y][x] = sum_dz cz A[z + dz][y][x] for the TZ output
+        // slices, every staged (y, x) column; each thread slides a register
+        // window down its column, so a staged value is read once
+        constexpr int COLS = T::NY * T::AX;
+        for (int c = threadIdx.x; c < COLS; c += NTHREADS) {
+            float win[T::NZ];
 #pragma unroll
-            for (int u = 0; u < U; ++u) s[u] = 0.f;
+            for (int z = 0; z < T::NZ; ++z) win[z] = A[z * COLS + c];
 #pragma unroll
-            for (int q = 0; q <= 2 * R; ++q)
+            for (int zo = 0; zo < TZ; ++zo) {
+                float s = 0.f;
 #pragma unroll
-                for (int u = 0; u < U; ++u)
-                    if (r0 + 8 * u < ROWS) s[u] = fmaf(K.cx[q], A[(r0 + 8 * u) * T::AX + T::X0 + xo + q], s[u]);
-#pragma unroll
-            for (int u = 0; u < U; ++u)
-                if (r0 + 8 * u < ROWS) B[(r0 + 8 * u) * TX + xo] = s[u];
+                for (int o = 0; o <= 2 * R; ++o) s = fmaf(K.cz[o], win[zo + o], s);
+                B[zo * COLS + c] = s;
+            }
         }
         __syncthreads();
-        // rows: C[z][y][x] = sum_dy cy B[z][y + R + dy][x]; this warp's y, every staged slice
+        // rows: C[z][y][x] = sum_dy cy B[z][y + dy][x] for the TY output rows,
+        // every (z, x) column (C over the window's own buffer)
         float* C = A;
+        constexpr int COLS2 = TZ * T::AX;
+        for (int c = threadIdx.x; c < COLS2; c += NTHREADS) {
+            const int z = c / T::AX, x = c - z * T::AX;
+            const float* b = B + z * COLS + x;
+            float win[T::NY];
 #pragma unroll
-        for (int za = 0; za < T::NZ; ++za) {
-            const float* b = B + (za * T::NY + warp) * TX + xo;
-            float s = 0.f;
+            for (int y = 0; y < T::NY; ++y) win[y] = b[y * T::AX];
 #pragma unroll
-            for (int p = 0; p <= 2 * R; ++p) s = fmaf(K.cy[p], b[p * TX], s);
-            C[(za * TY + warp) * TX + xo] = s;
+            for (int yo = 0; yo < TY; ++yo) {
+                float s = 0.f;
+#pragma unroll
+                for (int p = 0; p <= 2 * R; ++p) s = fmaf(K.cy[p], win[yo + p], s);
+                C[(z * TY + yo) * T::AX + x] = s;
+            }
         }
         __syncthreads();
-        // slices: out[z][y][x] = sum_dz cz C[z + R + dz][y][x]
+        // columns: out[z][y][x] = sum_dx cx C[z][y][X0 + x + dx]
         float s[TZ];
 #pragma unroll
         for (int zo = 0; zo < TZ; ++zo) {
             s[zo] = 0.f;
+            const float* c = C + (zo * TY + warp) * T::AX + T::X0 + xo;
 #pragma unroll
-            for (int o = 0; o <= 2 * R; ++o) s[zo] = fmaf(K.cz[o], C[((zo + o) * TY + warp) * TX + xo], s[zo]);
+            for (int q = 0; q <= 2 * R; ++q) s[zo] = fmaf(K.cx[q], c[q], s[zo]);
         }
         if (col_in) {
 #pragma unroll
