@@ -116,3 +116,26 @@ def test_volume_plan_validation(lib):
     assert code(storage="bf16") == 2
     assert code(iters=[1, -1, 1]) == 1
     assert code(c=1.0) == 1
+
+
+def test_volume_entry_points_reject_a_null_plan(lib):
+    """Every volume call checks its plan on the host before touching the device."""
+    so = lib.load()
+    null = None
+    calls = [
+        ("eecmg_vol_restore", (null, null, null, null)),
+        ("eecmg_vol_restore_host", (null, null, null, null)),
+        ("eecmg_vol_plan_stats", (null, null, null)),
+        ("eecmg_vol_plan_info", (null, null, null, null, null, null, null)),
+        ("eecmg_vol_apply_H", (null, 0, null, null, 0, null)),
+        ("eecmg_vol_restrict", (null, 0, null, null, null)),
+        ("eecmg_vol_start_level", (null, 2, null, null, null, null)),
+        ("eecmg_vol_smooth", (null, 0, null, null, null)),
+        ("eecmg_vol_denoise", (null, 0, null, null, null)),
+        ("eecmg_vol_level_solve", (null, 0, null, null, 1, null)),
+        ("eecmg_vol_plan_profile", (null, 1)),
+        ("eecmg_vol_plan_profile_read", (null, null, null, null)),
+    ]
+    for name, args in calls:
+        assert getattr(so, name)(*args) == 1, name
+    assert so.eecmg_vol_plan_destroy(None) == 0
