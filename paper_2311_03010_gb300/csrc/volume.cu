@@ -25,10 +25,11 @@
 // replica of the scalars), so the m_l iterations never return to the host and
 // the stop decision is taken on the device.  The convolution phases loop over
 // 8 x 8 x 32 output tiles: a tile and its halo are staged in shared memory and
-// a separable PSF runs as three passes (columns, rows, slices) inside the tile;
-// a general PSF runs its non-zero taps from the staged tile.  The level start
-// (Pi, P, S, D) is a chain of voxel-parallel kernels.  The cascade is captured
-// once as a CUDA graph.
+// a separable PSF runs as three passes (slices, rows, columns) inside the tile;
+// a general PSF runs its non-zero taps from the staged tile (the level solve is
+// in volume_impl.cuh).  The level start (Pi, P, S, D) is a chain of
+// voxel-parallel kernels in this file.  The cascade is captured once as a CUDA
+// graph.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
