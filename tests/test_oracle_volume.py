@@ -277,3 +277,35 @@ def test_cascade3_delta_psf_returns_data(orc):
 def test_cascade3_rejects_other_smoothers(orc):
     with pytest.raises(ValueError):
         orc.cascade3(np.zeros((3, 3, 3)), 2, np.ones((2, 3, 3)))
+
+
+@pytest.mark.parametrize("shape", [(3, 4, 5), (4, 4, 4), (2, 5, 3)])
+def test_mr2_3_is_krylov_minimiser(orc, shape):
+    """MR-II on a volume: the k-th iterate is the least-squares minimiser of
+    ||g - H u|| over u0 + span{H r0, ..., H^k r0}, with H built densely from the
+    scipy zero-fill convolution (independent of the oracle's own H)."""
+    ndi = pytest.importorskip("scipy.ndimage")
+    rng = np.random.default_rng(120)
+    K = rng.uniform(0, 1, (3, 3, 3))
+    K = 0.5 * (K + K[::-1, ::-1, ::-1])
+    K[1, 1, 1] += 1.5 * K.sum()  # diagonally dominant: well conditioned
+    K /= K.sum()
+    N = int(np.prod(shape))
+    Hd = np.zeros((N, N))
+    for j in range(N):
+        e = np.zeros(N)
+        e[j] = 1.0
+        Hd[:, j] = ndi.convolve(e.reshape(shape), K, mode="constant", cval=0.0).ravel()
+    assert np.allclose(Hd, Hd.T)
+    g = rng.uniform(0, 255, shape)
+    u0 = rng.uniform(0, 255, shape)
+    r0 = g.ravel() - Hd @ u0.ravel()
+    for k in range(1, 6):
+        V = np.stack([np.linalg.matrix_power(Hd, j) @ r0 for j in range(1, k + 1)], axis=1)
+        Q, _ = np.linalg.qr(V)
+        Q, _ = np.linalg.qr(Q)
+        y, *_ = np.linalg.lstsq(Hd @ Q, r0, rcond=None)
+        exp = u0.ravel() + Q @ y
+        u, it, _ = orc.mr2_3(K, g, u0, k)
+        assert it == k
+        assert np.linalg.norm(u.ravel() - exp) <= 1e-9 * np.linalg.norm(exp)
