@@ -40,6 +40,8 @@ def psf3_cases():
     return {
         "gauss1.2": synth.gaussian_psf3(1.2, 2),
         "gauss1.5": synth.gaussian_psf3(1.5, 3),
+        "gauss1.8r4": synth.gaussian_psf3(1.8, 4),
+        "gauss1.8r5": synth.gaussian_psf3(1.8, 5),
         "gauss2max": synth.gaussian_psf3(2.0, 6),
         "aniso3x5x7": an / an.sum(),
         "nonsep3x3x5": ns / ns.sum(),
